@@ -1,0 +1,680 @@
+/*
+ * kbl_oracle.c -- FP64 CPU oracle of the kinetic-bounds limiter (arXiv
+ * 2407.20966) and of the nodal DG / FR Euler stage it sits in.
+ *
+ * TEST INFRASTRUCTURE ONLY: plain loops in the paper's order, no blocking, no
+ * fusion, no reordering beyond what the definitions state.  It shares no code
+ * with the CUDA library.  Conventions are in kbl_oracle.h.
+ */
+#include "kbl_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+int orc_nv(const orc_cfg* c) { return c->dim + 2; }
+int orc_ns(const orc_cfg* c) { return c->dim == 1 ? c->p + 1 : (c->p + 1) * (c->p + 1); }
+int orc_nfp(const orc_cfg* c) { return c->dim == 1 ? 2 : 4 * (c->p + 1); }
+int orc_nstencil(const orc_cfg* c) { return orc_ns(c) + 2 * orc_nfp(c); }
+static int nfp_face(const orc_cfg* c) { return c->dim == 1 ? 1 : c->p + 1; }
+
+/* ===================================================================== */
+/* One-dimensional polynomial tools                                       */
+/* ===================================================================== */
+
+/* Legendre polynomial P_n and its derivative by the three-term recurrence
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1} and P'_{k+1} = P'_{k-1} + (2k+1) P_k. */
+void orc_legendre(int n, double x, double* P, double* dP)
+{
+    double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+    if (n == 0) { *P = 1.0; *dP = 0.0; return; }
+    for (int k = 1; k < n; k++) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        double d2 = d0 + (2.0 * k + 1.0) * p1;
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    }
+    *P = p1; *dP = d1;
+}
+
+/* Gauss-Legendre nodes (ascending) and weights on [-1, 1]: roots of P_n by
+ * Newton's method, w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2).  These are the
+ * solution and flux points the paper uses for lines and quadrilaterals (Sec. 5). */
+int orc_gauss_legendre(int n, double* x, double* w)
+{
+    if (n < 1) return -2;
+    for (int i = 0; i < n; i++) {
+        double r = -cos(ORC_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; it++) {
+            double P, dP;
+            orc_legendre(n, r, &P, &dP);
+            double dr = P / dP;
+            r -= dr;
+            if (fabs(dr) < 1e-16) break;
+        }
+        double P, dP;
+        orc_legendre(n, r, &P, &dP);
+        x[i] = r;
+        w[i] = 2.0 / ((1.0 - r * r) * dP * dP);
+    }
+    return 0;
+}
+
+/* Lagrange basis polynomial l_j of the nodes, evaluated at x. */
+double orc_lagrange(int n, const double* nodes, int j, double x)
+{
+    double v = 1.0;
+    for (int m = 0; m < n; m++)
+        if (m != j) v *= (x - nodes[m]) / (nodes[j] - nodes[m]);
+    return v;
+}
+
+/* Derivative of l_j at x: sum over l != j of 1/(x_j - x_l) times the product
+ * of the remaining factors. */
+double orc_lagrange_deriv(int n, const double* nodes, int j, double x)
+{
+    double s = 0.0;
+    for (int l = 0; l < n; l++) {
+        if (l == j) continue;
+        double t = 1.0 / (nodes[j] - nodes[l]);
+        for (int m = 0; m < n; m++)
+            if (m != j && m != l) t *= (x - nodes[m]) / (nodes[j] - nodes[m]);
+        s += t;
+    }
+    return s;
+}
+
+/* Derivatives of the FR correction functions that recover nodal DG (Huynh's
+ * g_DG, the right and left Radau polynomials of degree p+1):
+ *   g_L = (-1)^(p+1)/2 (P_{p+1} - P_p),  g_L(-1) = 1, g_L(1) = 0,
+ *   g_R = 1/2 (P_{p+1} + P_p),           g_R(-1) = 0, g_R(1) = 1. */
+void orc_correction_deriv(int p, double x, double* dgl, double* dgr)
+{
+    double Pa, dPa, Pb, dPb;
+    orc_legendre(p + 1, x, &Pa, &dPa);
+    orc_legendre(p, x, &Pb, &dPb);
+    double sgn = ((p + 1) % 2 == 0) ? 1.0 : -1.0;
+    *dgl = 0.5 * sgn * (dPa - dPb);
+    *dgr = 0.5 * (dPa + dPb);
+}
+
+/* ===================================================================== */
+/* Euler physics                                                          */
+/* ===================================================================== */
+
+/* Ideal-gas pressure P = (gamma - 1)(E - m.m / (2 rho)), Eq. 3. */
+double orc_pressure(const orc_cfg* c, const double* w)
+{
+    int d = c->dim;
+    double mm = 0.0;
+    for (int k = 0; k < d; k++) mm += w[1 + k] * w[1 + k];
+    return (c->gamma - 1.0) * (w[d + 1] - 0.5 * mm / w[0]);
+}
+
+/* Physical flux along axis `dir`, Eq. 2: [m_dir, m U_dir + P e_dir, (E + P) U_dir]. */
+void orc_flux(const orc_cfg* c, const double* w, int dir, double* F)
+{
+    int d = c->dim;
+    double P = orc_pressure(c, w);
+    double U = w[1 + dir] / w[0];
+    F[0] = w[1 + dir];
+    for (int k = 0; k < d; k++) F[1 + k] = w[1 + k] * U + (k == dir ? P : 0.0);
+    F[d + 1] = (w[d + 1] + P) * U;
+}
+
+/* Rusanov flux with the Davis wavespeed (assumption (iv) of Sec. 4 and its
+ * remark): wl is on the minus side of the axis, wr on the plus side,
+ *   F = 1/2 (F(wl) + F(wr)) - 1/2 lambda (wr - wl),
+ *   lambda = max(|U_l| + c_l, |U_r| + c_r), c = sqrt(gamma P / rho). */
+void orc_rusanov(const orc_cfg* c, const double* wl, const double* wr, int dir,
+                 double* F)
+{
+    int nv = orc_nv(c);
+    double Fl[4], Fr[4];
+    orc_flux(c, wl, dir, Fl);
+    orc_flux(c, wr, dir, Fr);
+    double Pl = orc_pressure(c, wl), Pr = orc_pressure(c, wr);
+    double sl = fabs(wl[1 + dir] / wl[0]) + sqrt(c->gamma * Pl / wl[0]);
+    double sr = fabs(wr[1 + dir] / wr[0]) + sqrt(c->gamma * Pr / wr[0]);
+    double lam = sl > sr ? sl : sr;
+    for (int v = 0; v < nv; v++) F[v] = 0.5 * (Fl[v] + Fr[v]) - 0.5 * lam * (wr[v] - wl[v]);
+}
+
+/* ===================================================================== */
+/* Kinetic bounds                                                          */
+/* ===================================================================== */
+
+typedef struct {
+    double rho, U[2], theta, A, cI;
+} orc_maxw;
+
+/* Primitive state of a stencil node and the constants of its Maxwellian,
+ * Eq. 8:  g(u) = rho (2 pi theta)^(-d/2) exp(-|u - U|^2 / (2 theta)),
+ * theta = P / rho; and the internal-energy weight theta delta / 2 of Eq. 44,
+ * delta = 2/(gamma - 1) - d. */
+static int orc_maxwellian_of(const orc_cfg* c, const double* w, orc_maxw* g)
+{
+    int d = c->dim;
+    double P = orc_pressure(c, w);
+    if (!(w[0] > 0.0) || !(P > 0.0)) return -1;
+    g->rho = w[0];
+    for (int k = 0; k < d; k++) g->U[k] = w[1 + k] / w[0];
+    g->theta = P / w[0];
+    g->A = (d == 1) ? g->rho / sqrt(2.0 * ORC_PI * g->theta)
+                    : g->rho / (2.0 * ORC_PI * g->theta);
+    double delta = 2.0 / (c->gamma - 1.0) - d;
+    g->cI = 0.5 * delta * g->theta;
+    return 0;
+}
+
+static double orc_eval_maxwellian(int d, const orc_maxw* g, const double* u)
+{
+    double q = 0.0;
+    for (int k = 0; k < d; k++) q += (u[k] - g->U[k]) * (u[k] - g->U[k]);
+    return g->A * exp(-q / (2.0 * g->theta));
+}
+
+/* Truncated velocity domain, Eq. 45, read with the upper end at
+ * max(U + k sqrt(theta)) (the printed "-" there is a sign slip: the text before
+ * it describes U +- k sqrt(theta)).  Taken per dimension over the stencil. */
+static void orc_box(int d, double kk, int nS, const orc_maxw* g, double* lo, double* hi)
+{
+    for (int k = 0; k < d; k++) {
+        lo[k] = g[0].U[k] - kk * sqrt(g[0].theta);
+        hi[k] = g[0].U[k] + kk * sqrt(g[0].theta);
+        for (int i = 1; i < nS; i++) {
+            double a = g[i].U[k] - kk * sqrt(g[i].theta);
+            double b = g[i].U[k] + kk * sqrt(g[i].theta);
+            if (a < lo[k]) lo[k] = a;
+            if (b > hi[k]) hi[k] = b;
+        }
+    }
+}
+
+/* Equispaced velocity grid over [lo, hi] with trapezoidal weights (Sec. 3.7):
+ * u_j = lo + j h, h = (hi - lo)/(N - 1), weight h (h/2 at both ends). */
+static void orc_grid(int N, double lo, double hi, double* u, double* wq)
+{
+    double h = (hi - lo) / (N - 1);
+    for (int j = 0; j < N; j++) {
+        u[j] = lo + j * h;
+        wq[j] = (j == 0 || j == N - 1) ? 0.5 * h : h;
+    }
+}
+
+/* Add one velocity node's contribution to the moment bounds.
+ *   density  Eq. 33:  sum M f_min,            sum M f_max
+ *   momentum Eq. 35/36, per component: f_max where u_i < 0 and f_min where
+ *            u_i >= 0 for the lower bound, the other way round for the upper
+ *   energy   Eq. 34 with the internal-energy term of Eq. 42/44:
+ *            sum M (f_T 1/2 |u|^2 + f_I)
+ * lo/hi receive nv values each. */
+static void orc_accumulate(int d, double M, const double* u, double Tlo, double Thi,
+                           double Ilo, double Ihi, double* lo, double* hi)
+{
+    int nv = d + 2;
+    lo[0] += M * Tlo;
+    hi[0] += M * Thi;
+    double ke = 0.0;
+    for (int k = 0; k < d; k++) {
+        ke += 0.5 * u[k] * u[k];
+        if (u[k] < 0.0) {
+            lo[1 + k] += M * Thi * u[k];
+            hi[1 + k] += M * Tlo * u[k];
+        } else {
+            lo[1 + k] += M * Tlo * u[k];
+            hi[1 + k] += M * Thi * u[k];
+        }
+    }
+    lo[nv - 1] += M * (Tlo * ke + Ilo);
+    hi[nv - 1] += M * (Thi * ke + Ihi);
+}
+
+#define ORC_MAX_S 256
+#define ORC_MAX_NU 65536
+
+int orc_velocity_box(const orc_cfg* c, int nS, const double* S, double* lo, double* hi)
+{
+    int nv = orc_nv(c);
+    if (nS < 1 || nS > ORC_MAX_S) return -2;
+    orc_maxw g[ORC_MAX_S];
+    for (int i = 0; i < nS; i++)
+        if (orc_maxwellian_of(c, S + i * nv, &g[i])) return -1;
+    orc_box(c->dim, c->k, nS, g, lo, hi);
+    return 0;
+}
+
+/* Shared walk over the velocity grid of stencil S.  which == -1: the
+ * envelopes of Eq. 32 (with the relaxation of Eq. 40) give the bounds;
+ * which == -2 / -3: the plain moments of f_min / f_max as distributions;
+ * which >= 0: the single Maxwellian of node `which`, in the same order, so
+ * every result can be compared with the bounds term by term. */
+static int orc_walk(const orc_cfg* c, int nS, const double* S, int which,
+                    double* lo, double* hi)
+{
+    int d = c->dim, nv = orc_nv(c);
+    if (nS < 1 || nS > ORC_MAX_S) return -2;
+    int Nx = c->nu[0], Ny = d == 2 ? c->nu[1] : 1;
+    if (Nx < 2 || Nx > ORC_MAX_NU || (d == 2 && (Ny < 2 || Ny > ORC_MAX_NU))) return -2;
+    orc_maxw g[ORC_MAX_S];
+    for (int i = 0; i < nS; i++)
+        if (orc_maxwellian_of(c, S + i * nv, &g[i])) return -1;
+    double blo[2], bhi[2];
+    orc_box(d, c->k, nS, g, blo, bhi);
+    double* ux = malloc(sizeof(double) * Nx);
+    double* wx = malloc(sizeof(double) * Nx);
+    double* uy = malloc(sizeof(double) * Ny);
+    double* wy = malloc(sizeof(double) * Ny);
+    orc_grid(Nx, blo[0], bhi[0], ux, wx);
+    if (d == 2) orc_grid(Ny, blo[1], bhi[1], uy, wy);
+    else { uy[0] = 0.0; wy[0] = 1.0; }
+    for (int v = 0; v < nv; v++) lo[v] = hi[v] = 0.0;
+    double r = c->r_fac;
+    for (int jy = 0; jy < Ny; jy++) {
+        for (int jx = 0; jx < Nx; jx++) {
+            double u[2] = {ux[jx], uy[jy]};
+            double M = (d == 2) ? wx[jx] * wy[jy] : wx[jx];
+            double Tlo, Thi, Ilo, Ihi;
+            if (which < 0) {
+                /* Eq. 32: pointwise minimum and maximum over the stencil of
+                 * the translational part g and of the internal part
+                 * (theta delta / 2) g, each with its own envelope. */
+                Tlo = INFINITY; Thi = -INFINITY; Ilo = INFINITY; Ihi = -INFINITY;
+                for (int i = 0; i < nS; i++) {
+                    double gi = orc_eval_maxwellian(d, &g[i], u);
+                    double ci = g[i].cI * gi;
+                    if (gi < Tlo) Tlo = gi;
+                    if (gi > Thi) Thi = gi;
+                    if (ci < Ilo) Ilo = ci;
+                    if (ci > Ihi) Ihi = ci;
+                }
+                /* Eq. 40: relax the envelopes by (1 -+ r_fac). */
+                Tlo *= (1.0 - r); Ilo *= (1.0 - r);
+                Thi *= (1.0 + r); Ihi *= (1.0 + r);
+                /* which == -2 / -3: plain moments of f_min / f_max alone */
+                if (which == -2) { Thi = Tlo; Ihi = Ilo; }
+                if (which == -3) { Tlo = Thi; Ilo = Ihi; }
+            } else {
+                double gi = orc_eval_maxwellian(d, &g[which], u);
+                Tlo = Thi = gi;
+                Ilo = Ihi = g[which].cI * gi;
+            }
+            orc_accumulate(d, M, u, Tlo, Thi, Ilo, Ihi, lo, hi);
+        }
+    }
+    free(ux); free(wx); free(uy); free(wy);
+    return 0;
+}
+
+/* Bounds of Sec. 3.3 (Eq. 32-36, 40, 42-46) for one stencil, then the density
+ * floor of Sec. 3.8: rho_min <- max(rho_min, rho_floor). */
+int orc_bounds_stencil(const orc_cfg* c, int nS, const double* S, double* wmin,
+                       double* wmax)
+{
+    int rc = orc_walk(c, nS, S, -1, wmin, wmax);
+    if (rc) return rc;
+    if (wmin[0] < c->rho_floor) wmin[0] = c->rho_floor;
+    return 0;
+}
+
+int orc_envelope_moments(const orc_cfg* c, int nS, const double* S, int upper, double* mom)
+{
+    double hi[4];
+    return orc_walk(c, nS, S, upper ? -3 : -2, mom, hi);
+}
+
+int orc_state_moments(const orc_cfg* c, int nS, const double* S, int which, double* mom)
+{
+    if (which < 0 || which >= nS) return -2;
+    double hi[4];
+    return orc_walk(c, nS, S, which, mom, hi);
+}
+
+/* ===================================================================== */
+/* Mesh-level operations                                                  */
+/* ===================================================================== */
+
+typedef struct {
+    int n, ns, nfp, nfpf, nv;
+    double x[16], wq[16];
+    double lm[16], lp[16];      /* l_i(-1), l_i(+1) */
+    double D[16][16];           /* D[i][m] = l_m'(x_i) */
+    double gl[16], gr[16];      /* g_L'(x_i), g_R'(x_i) */
+} orc_ops;
+
+static void orc_build_ops(const orc_cfg* c, orc_ops* o)
+{
+    int n = c->p + 1;
+    o->n = n;
+    o->ns = orc_ns(c);
+    o->nfp = orc_nfp(c);
+    o->nfpf = nfp_face(c);
+    o->nv = orc_nv(c);
+    orc_gauss_legendre(n, o->x, o->wq);
+    for (int i = 0; i < n; i++) {
+        o->lm[i] = orc_lagrange(n, o->x, i, -1.0);
+        o->lp[i] = orc_lagrange(n, o->x, i, 1.0);
+        orc_correction_deriv(c->p, o->x[i], &o->gl[i], &o->gr[i]);
+        for (int m = 0; m < n; m++) o->D[i][m] = orc_lagrange_deriv(n, o->x, m, o->x[i]);
+    }
+}
+
+/* Interior values at the face points (interpolation of the element's
+ * polynomial), in the face-point order of kbl_oracle.h. */
+void orc_traces(const orc_cfg* c, const orc_mesh* m, const double* w, double* wf)
+{
+    orc_ops o;
+    orc_build_ops(c, &o);
+    int E = m->n_elem, n = o.n;
+    for (int v = 0; v < o.nv; v++) {
+        for (int e = 0; e < E; e++) {
+            const double* we = w + ((size_t)v * E + e) * o.ns;
+            double* fe = wf + ((size_t)v * E + e) * o.nfp;
+            if (c->dim == 1) {
+                double a = 0.0, b = 0.0;
+                for (int i = 0; i < n; i++) { a += o.lm[i] * we[i]; b += o.lp[i] * we[i]; }
+                fe[0] = a; fe[1] = b;
+            } else {
+                for (int k = 0; k < n; k++) {
+                    double f0 = 0, f1 = 0, f2 = 0, f3 = 0;
+                    for (int i = 0; i < n; i++) {
+                        f0 += o.lm[i] * we[k * n + i];
+                        f1 += o.lp[i] * we[k * n + i];
+                        f2 += o.lm[i] * we[i * n + k];
+                        f3 += o.lp[i] * we[i * n + k];
+                    }
+                    fe[0 * n + k] = f0; fe[1 * n + k] = f1;
+                    fe[2 * n + k] = f2; fe[3 * n + k] = f3;
+                }
+            }
+        }
+    }
+}
+
+/* Exterior value at face point fp of element e: the neighbour's interior
+ * value at the matching point, or the prescribed boundary state. */
+static void orc_exterior(const orc_cfg* c, const orc_mesh* m, const double* wf, int e,
+                         int fp, double* out)
+{
+    int nv = orc_nv(c), nfp = orc_nfp(c), nf = nfp_face(c);
+    int f = fp / nf, k = fp % nf;
+    int nb = m->nbr[e * 2 * c->dim + f];
+    for (int v = 0; v < nv; v++) {
+        if (nb >= 0) out[v] = wf[((size_t)v * m->n_elem + nb) * nfp + (f ^ 1) * nf + k];
+        else out[v] = m->bc[(-nb - 1) * nv + v];
+    }
+}
+
+/* Stencil S of element e (Sec. 5, the "numerical stencil"): its solution
+ * points, then its own face points, then the exterior values at the same
+ * face points.  S is [|S|][nv]; the first Ns + Nfp rows form the set V. */
+void orc_gather_stencil(const orc_cfg* c, const orc_mesh* m, const double* w,
+                        const double* wf, int e, double* S)
+{
+    int nv = orc_nv(c), ns = orc_ns(c), nfp = orc_nfp(c), E = m->n_elem;
+    for (int n = 0; n < ns; n++)
+        for (int v = 0; v < nv; v++) S[n * nv + v] = w[((size_t)v * E + e) * ns + n];
+    for (int fp = 0; fp < nfp; fp++)
+        for (int v = 0; v < nv; v++) S[(ns + fp) * nv + v] = wf[((size_t)v * E + e) * nfp + fp];
+    for (int fp = 0; fp < nfp; fp++) orc_exterior(c, m, wf, e, fp, S + (ns + nfp + fp) * nv);
+}
+
+int orc_bounds(const orc_cfg* c, const orc_mesh* m, const double* w, const double* wf,
+               double* bnd)
+{
+    int nv = orc_nv(c), nS = orc_nstencil(c), E = m->n_elem;
+    double* S = malloc(sizeof(double) * nS * nv);
+    int rc = 0;
+    for (int e = 0; e < E; e++) {
+        double lo[4], hi[4];
+        orc_gather_stencil(c, m, w, wf, e, S);
+        int r = orc_bounds_stencil(c, nS, S, lo, hi);
+        if (r) { rc = r; for (int v = 0; v < nv; v++) { lo[v] = NAN; hi[v] = NAN; } }
+        for (int v = 0; v < nv; v++) {
+            bnd[(size_t)v * E + e] = lo[v];
+            bnd[((size_t)nv + v) * E + e] = hi[v];
+        }
+    }
+    free(S);
+    return rc;
+}
+
+/* FR right-hand side -div F (Sec. 2.3 and Sec. 5): Gauss-Legendre solution and
+ * flux points, the correction functions g_DG, Rusanov common flux, affine
+ * Cartesian elements.  Along each axis, at solution point x_i of a line of
+ * points:
+ *   dF/dxi = sum_m D_im F_m + g_L'(x_i) (Fc_L - F^D_L) + g_R'(x_i) (Fc_R - F^D_R),
+ * where F^D is the interpolated discontinuous flux at the face point, and
+ * R = -sum_axes (2 / h_axis) dF/dxi. */
+void orc_rhs(const orc_cfg* c, const orc_mesh* m, const double* w, const double* wf,
+             double* R)
+{
+    orc_ops o;
+    orc_build_ops(c, &o);
+    int d = c->dim, nv = o.nv, ns = o.ns, nfp = o.nfp, nf = o.nfpf, n = o.n;
+    int E = m->n_elem;
+    double* W = malloc(sizeof(double) * ns * nv);
+    double* F = malloc(sizeof(double) * d * ns * nv);    /* F[dir][node][v] */
+    double* J = malloc(sizeof(double) * nfp * nv);       /* Fc - F^D per face point */
+    for (int e = 0; e < E; e++) {
+        for (int nd = 0; nd < ns; nd++)
+            for (int v = 0; v < nv; v++) W[nd * nv + v] = w[((size_t)v * E + e) * ns + nd];
+        for (int dir = 0; dir < d; dir++)
+            for (int nd = 0; nd < ns; nd++) orc_flux(c, W + nd * nv, dir, F + (dir * ns + nd) * nv);
+        for (int fp = 0; fp < nfp; fp++) {
+            int f = fp / nf, k = fp % nf, dir = f / 2, side = f % 2;
+            double wi[4], we[4], Fc[4], FD[4];
+            for (int v = 0; v < nv; v++) wi[v] = wf[((size_t)v * E + e) * nfp + fp];
+            orc_exterior(c, m, wf, e, fp, we);
+            if (side == 0) orc_rusanov(c, we, wi, dir, Fc);
+            else orc_rusanov(c, wi, we, dir, Fc);
+            const double* l = side == 0 ? o.lm : o.lp;
+            for (int v = 0; v < nv; v++) {
+                double s = 0.0;
+                for (int i = 0; i < n; i++) {
+                    /* points along this face's normal line through point k */
+                    int nd = (d == 1) ? i : (dir == 0 ? k * n + i : i * n + k);
+                    s += l[i] * F[(dir * ns + nd) * nv + v];
+                }
+                FD[v] = s;
+                J[fp * nv + v] = Fc[v] - FD[v];
+            }
+        }
+        for (int nd = 0; nd < ns; nd++) {
+            int i = (d == 1) ? nd : nd % n, j = (d == 1) ? 0 : nd / n;
+            for (int v = 0; v < nv; v++) {
+                double dx = 0.0;
+                for (int mm = 0; mm < n; mm++) {
+                    int q = (d == 1) ? mm : j * n + mm;
+                    dx += o.D[i][mm] * F[(0 * ns + q) * nv + v];
+                }
+                dx += o.gl[i] * J[(0 * nf + j) * nv + v] + o.gr[i] * J[(1 * nf + j) * nv + v];
+                double r = -(2.0 / m->h[e * d + 0]) * dx;
+                if (d == 2) {
+                    double dy = 0.0;
+                    for (int mm = 0; mm < n; mm++) dy += o.D[j][mm] * F[(1 * ns + mm * n + i) * nv + v];
+                    dy += o.gl[j] * J[(2 * nf + i) * nv + v] + o.gr[j] * J[(3 * nf + i) * nv + v];
+                    r -= (2.0 / m->h[e * d + 1]) * dy;
+                }
+                R[((size_t)v * E + e) * ns + nd] = r;
+            }
+        }
+    }
+    free(W); free(F); free(J);
+}
+
+/* Limiting of one element, Sec. 3.4 and Sec. 3.8.
+ *  mean   : positive-quadrature mean with Gauss-Legendre weights (Eq. 13 and
+ *           assumption (iii)(a) of Sec. 4)
+ *  alpha_i: Eq. 37 per component over V = solution points + face points,
+ *           with the epsilon rule stated under it
+ *  alpha  : alpha_min = min_i alpha_i (Eq. 39), w~ = mean + alpha (w - mean)
+ *           (Eq. 38); at face points w~ = mean + alpha (wf - mean)
+ *  P      : P_min over V of w~ (Eq. 47); if below p_floor,
+ *           alpha_P = |(p_floor - P(mean)) / (P_min - P(mean))| (Eq. 49) and
+ *           w~~ = mean + alpha_P (w~ - mean) (Eq. 48).  When P(mean) itself is
+ *           not above p_floor, alpha_P is taken as 0. */
+void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
+                       const double* wmin, const double* wmax, double* alpha_out)
+{
+    int d = c->dim, nv = orc_nv(c), ns = orc_ns(c), nfp = orc_nfp(c), n = c->p + 1;
+    double xg[16], wg[16];
+    orc_gauss_legendre(n, xg, wg);
+    double mean[4];
+    for (int v = 0; v < nv; v++) {
+        double s = 0.0, sw = 0.0;
+        for (int nd = 0; nd < ns; nd++) {
+            double W = (d == 1) ? wg[nd] : wg[nd % n] * wg[nd / n];
+            s += W * wel[v * ns + nd];
+            sw += W;
+        }
+        mean[v] = s / sw;
+    }
+    double alpha = 1.0;
+    for (int v = 0; v < nv; v++) {
+        double mx = wel[v * ns], mn = wel[v * ns];
+        for (int nd = 1; nd < ns; nd++) {
+            double x = wel[v * ns + nd];
+            if (x > mx) mx = x;
+            if (x < mn) mn = x;
+        }
+        for (int fp = 0; fp < nfp; fp++) {
+            double x = wfel[v * nfp + fp];
+            if (x > mx) mx = x;
+            if (x < mn) mn = x;
+        }
+        double dmax = mx - mean[v], dmin = mn - mean[v];
+        double a;
+        if (fabs(dmin) < c->eps || fabs(dmax) < c->eps) {
+            a = c->eps_rule ? 1.0 : 0.0;
+        } else {
+            a = 1.0;
+            double t1 = fabs((wmax[v] - mean[v]) / dmax);
+            double t2 = fabs((wmin[v] - mean[v]) / dmin);
+            if (t1 < a) a = t1;
+            if (t2 < a) a = t2;
+        }
+        if (a < alpha) alpha = a;
+    }
+    double* wt = malloc(sizeof(double) * nv * ns);
+    double* wtf = malloc(sizeof(double) * nv * nfp);
+    for (int v = 0; v < nv; v++) {
+        for (int nd = 0; nd < ns; nd++) wt[v * ns + nd] = mean[v] + alpha * (wel[v * ns + nd] - mean[v]);
+        for (int fp = 0; fp < nfp; fp++) wtf[v * nfp + fp] = mean[v] + alpha * (wfel[v * nfp + fp] - mean[v]);
+    }
+    double pmin = INFINITY, q[4];
+    for (int nd = 0; nd < ns; nd++) {
+        for (int v = 0; v < nv; v++) q[v] = wt[v * ns + nd];
+        double P = orc_pressure(c, q);
+        if (P < pmin) pmin = P;
+    }
+    for (int fp = 0; fp < nfp; fp++) {
+        for (int v = 0; v < nv; v++) q[v] = wtf[v * nfp + fp];
+        double P = orc_pressure(c, q);
+        if (P < pmin) pmin = P;
+    }
+    double aP = 1.0;
+    if (pmin < c->p_floor) {
+        double Pbar = orc_pressure(c, mean);
+        aP = (Pbar > c->p_floor) ? fabs((c->p_floor - Pbar) / (pmin - Pbar)) : 0.0;
+        for (int v = 0; v < nv; v++)
+            for (int nd = 0; nd < ns; nd++) wel[v * ns + nd] = mean[v] + aP * (wt[v * ns + nd] - mean[v]);
+    } else {
+        memcpy(wel, wt, sizeof(double) * nv * ns);
+    }
+    free(wt); free(wtf);
+    if (alpha_out) { alpha_out[0] = alpha; alpha_out[1] = aP; }
+}
+
+void orc_limit(const orc_cfg* c, const orc_mesh* m, double* w, const double* bnd,
+               double* alpha)
+{
+    int nv = orc_nv(c), ns = orc_ns(c), nfp = orc_nfp(c), E = m->n_elem;
+    double* wf = malloc(sizeof(double) * (size_t)nv * E * nfp);
+    orc_traces(c, m, w, wf);
+    double* wel = malloc(sizeof(double) * nv * ns);
+    double* wfel = malloc(sizeof(double) * nv * nfp);
+    for (int e = 0; e < E; e++) {
+        double lo[4], hi[4], a[2];
+        for (int v = 0; v < nv; v++) {
+            for (int nd = 0; nd < ns; nd++) wel[v * ns + nd] = w[((size_t)v * E + e) * ns + nd];
+            for (int fp = 0; fp < nfp; fp++) wfel[v * nfp + fp] = wf[((size_t)v * E + e) * nfp + fp];
+            lo[v] = bnd[(size_t)v * E + e];
+            hi[v] = bnd[((size_t)nv + v) * E + e];
+        }
+        orc_limit_element(c, wel, wfel, lo, hi, a);
+        for (int v = 0; v < nv; v++)
+            for (int nd = 0; nd < ns; nd++) w[((size_t)v * E + e) * ns + nd] = wel[v * ns + nd];
+        if (alpha) { alpha[e] = a[0]; alpha[E + e] = a[1]; }
+    }
+    free(wf); free(wel); free(wfel);
+}
+
+/* Shu-Osher form of SSP-RK3 (Gottlieb et al. 2001, as used in Sec. 5):
+ *   s = 0: w1 = w_n + dt R(w_n)
+ *   s = 1: w2 = 3/4 w_n + 1/4 (w1 + dt R(w1))
+ *   s = 2: w3 = 1/3 w_n + 2/3 (w2 + dt R(w2)) */
+void orc_stage_combine(const orc_cfg* c, const orc_mesh* m, int s, const double* wn,
+                       const double* ws, const double* R, double dt, double* wout)
+{
+    size_t N = (size_t)orc_nv(c) * m->n_elem * orc_ns(c);
+    for (size_t i = 0; i < N; i++) {
+        double t = ws[i] + dt * R[i];
+        if (s == 0) wout[i] = t;
+        else if (s == 1) wout[i] = 0.75 * wn[i] + 0.25 * t;
+        else wout[i] = (1.0 / 3.0) * wn[i] + (2.0 / 3.0) * t;
+    }
+}
+
+/* Time step (the paper does not state its rule): dt = cfl * min over elements,
+ * solution points and axes of h_axis / (|U_axis| + c). */
+double orc_dt(const orc_cfg* c, const orc_mesh* m, const double* w, double cfl)
+{
+    int d = c->dim, nv = orc_nv(c), ns = orc_ns(c), E = m->n_elem;
+    double best = INFINITY;
+    for (int e = 0; e < E; e++) {
+        for (int nd = 0; nd < ns; nd++) {
+            double q[4];
+            for (int v = 0; v < nv; v++) q[v] = w[((size_t)v * E + e) * ns + nd];
+            double P = orc_pressure(c, q);
+            double a = sqrt(c->gamma * P / q[0]);
+            for (int k = 0; k < d; k++) {
+                double t = m->h[e * d + k] / (fabs(q[1 + k] / q[0]) + a);
+                if (t < best) best = t;
+            }
+        }
+    }
+    return cfl * best;
+}
+
+/* One time step of the method overview, Sec. 3.9, applied at every SSP-RK3
+ * stage: bounds from the stage's input state (steps 1-3), advance (4), limit
+ * (5-8). */
+int orc_ssprk3_step(const orc_cfg* c, const orc_mesh* m, double* w, double dt,
+                    double* alpha)
+{
+    int nv = orc_nv(c), ns = orc_ns(c), nfp = orc_nfp(c), E = m->n_elem;
+    size_t N = (size_t)nv * E * ns;
+    double* wn = malloc(sizeof(double) * N);
+    double* ws = malloc(sizeof(double) * N);
+    double* wo = malloc(sizeof(double) * N);
+    double* R = malloc(sizeof(double) * N);
+    double* wf = malloc(sizeof(double) * (size_t)nv * E * nfp);
+    double* bnd = malloc(sizeof(double) * 2 * (size_t)nv * E);
+    memcpy(wn, w, sizeof(double) * N);
+    memcpy(ws, w, sizeof(double) * N);
+    int rc = 0;
+    for (int s = 0; s < 3; s++) {
+        orc_traces(c, m, ws, wf);
+        int r = orc_bounds(c, m, ws, wf, bnd);
+        if (r) rc = r;
+        orc_rhs(c, m, ws, wf, R);
+        orc_stage_combine(c, m, s, wn, ws, R, dt, wo);
+        orc_limit(c, m, wo, bnd, s == 2 ? alpha : NULL);
+        memcpy(ws, wo, sizeof(double) * N);
+    }
+    memcpy(w, ws, sizeof(double) * N);
+    free(wn); free(ws); free(wo); free(R); free(wf); free(bnd);
+    return rc;
+}

@@ -1,0 +1,240 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds problem set-ups only: Cartesian mesh connectivity, initial
+conditions written as functions of position, and random admissible states.  It
+holds none of the limiter's or the FR scheme's arithmetic; in particular the
+reference-element node positions are always passed in by the caller, so each
+side (the CUDA library or the CPU checker) supplies its own.
+
+Layouts: solution ``w[nv][E][Ns]`` with Ns = (p+1)^d nodes per element, x index
+fastest; ``nbr[E][2d]`` faces ordered (-x, +x, -y, +y); a negative ``nbr`` is a
+boundary face whose exterior state is ``bc[-(nbr+1)]``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def conservative(rho, u, p, gamma=GAMMA):
+    """(rho, u[d], P) -> (rho, rho u[d], P/(gamma-1) + rho |u|^2 / 2); u is a list of arrays."""
+    rho = np.asarray(rho, dtype=np.float64)
+    mom = [rho * np.asarray(ui, dtype=np.float64) for ui in u]
+    ke = 0.5 * rho * sum(np.asarray(ui, dtype=np.float64) ** 2 for ui in u)
+    return np.stack([rho, *mom, np.asarray(p, dtype=np.float64) / (gamma - 1.0) + ke])
+
+
+@dataclass
+class CartMesh:
+    dim: int
+    n: tuple            # elements per axis
+    lo: tuple           # domain lower corner
+    hi: tuple           # domain upper corner
+    nbr: np.ndarray     # [E][2d] int32
+    h: np.ndarray       # [E][d]
+    centers: np.ndarray  # [E][d]
+    bc: np.ndarray = field(default_factory=lambda: np.zeros((1, 4)))
+
+    @property
+    def n_elem(self):
+        return self.nbr.shape[0]
+
+
+def mesh_1d(n, x0, x1, periodic=False, bc_left=0, bc_right=1):
+    """Uniform line mesh; boundary faces get ids bc_left / bc_right unless periodic."""
+    e = np.arange(n)
+    nbr = np.stack([e - 1, e + 1], axis=1).astype(np.int32)
+    if periodic:
+        nbr[0, 0], nbr[-1, 1] = n - 1, 0
+    else:
+        nbr[0, 0], nbr[-1, 1] = -(bc_left + 1), -(bc_right + 1)
+    hx = (x1 - x0) / n
+    h = np.full((n, 1), hx)
+    centers = (x0 + (e + 0.5) * hx)[:, None]
+    return CartMesh(1, (n,), (x0,), (x1,), nbr, h, centers)
+
+
+def mesh_2d(nx, ny, x0, x1, y0, y1, periodic=(False, False), bc_of_face=None):
+    """Uniform quad mesh, element e = iy * nx + ix.
+
+    ``bc_of_face(ix, iy, f)`` gives the boundary id of a boundary face (default 0).
+    """
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ix, iy = ix.ravel(), iy.ravel()
+    E = nx * ny
+    nbr = np.zeros((E, 4), dtype=np.int64)
+    for f, (dx, dy) in enumerate(((-1, 0), (1, 0), (0, -1), (0, 1))):
+        jx, jy = ix + dx, iy + dy
+        if periodic[0]:
+            jx = jx % nx
+        if periodic[1]:
+            jy = jy % ny
+        inside = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny)
+        nb = np.where(inside, jy * nx + jx, 0)
+        if bc_of_face is None:
+            ids = np.zeros(E, dtype=np.int64)
+        else:
+            ids = np.array([bc_of_face(a, b, f) for a, b in zip(ix, iy)], dtype=np.int64)
+        nbr[:, f] = np.where(inside, nb, -(ids + 1))
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    h = np.tile([hx, hy], (E, 1)).astype(np.float64)
+    centers = np.stack([x0 + (ix + 0.5) * hx, y0 + (iy + 0.5) * hy], axis=1)
+    return CartMesh(2, (nx, ny), (x0, y0), (x1, y1), nbr.astype(np.int32), h, centers)
+
+
+def node_coords(mesh: CartMesh, xi):
+    """Physical coordinates of the solution nodes; xi are the 1D reference nodes on [-1, 1]."""
+    xi = np.asarray(xi, dtype=np.float64)
+    if mesh.dim == 1:
+        x = mesh.centers[:, 0:1] + 0.5 * mesh.h[:, 0:1] * xi[None, :]
+        return (x,)
+    n = len(xi)
+    X = np.tile(xi, n)          # i fastest
+    Y = np.repeat(xi, n)
+    x = mesh.centers[:, 0:1] + 0.5 * mesh.h[:, 0:1] * X[None, :]
+    y = mesh.centers[:, 1:2] + 0.5 * mesh.h[:, 1:2] * Y[None, :]
+    return x, y
+
+
+# ---------------------------------------------------------------------------
+# Problem set-ups
+# ---------------------------------------------------------------------------
+def sod(n=200, gamma=GAMMA):
+    """Sod shock tube on [0, 1] (Sec. 6.1): (1, 0, 1) left of 0.5, (0.125, 0, 0.1) right."""
+    mesh = mesh_1d(n, 0.0, 1.0, periodic=False, bc_left=0, bc_right=1)
+    left = conservative(1.0, [0.0], 1.0, gamma)
+    right = conservative(0.125, [0.0], 0.1, gamma)
+    mesh.bc = np.stack([left, right]).astype(np.float64)
+
+    def ic(x):
+        return np.where(x <= 0.5, left[:, None, None], right[:, None, None])
+    return mesh, ic
+
+
+def density_pulse(n, gamma=GAMMA, sigma=500.0):
+    """Smooth convecting pulse on periodic [-0.5, 0.5] (Sec. 6.2): rho = 1 + exp(-sigma x^2), u = 1, P = 1."""
+    mesh = mesh_1d(n, -0.5, 0.5, periodic=True)
+
+    def ic(x, t=0.0):
+        xs = (x - t + 0.5) % 1.0 - 0.5
+        return conservative(1.0 + np.exp(-sigma * xs * xs), [np.ones_like(xs)], np.ones_like(xs), gamma)
+    return mesh, ic
+
+
+def isentropic_vortex(n=128, gamma=GAMMA, beta=5.0, L=10.0, u0=1.0, v0=1.0):
+    """Isentropic vortex on periodic [0, L]^2, mean flow (u0, v0), strength beta, centre (L/2, L/2).
+
+    Velocity perturbation beta/(2 pi) exp((1 - r^2)/2) (-(y-yc), x-xc); temperature
+    T = 1 - (gamma-1) beta^2 / (8 gamma pi^2) exp(1 - r^2); rho = T^(1/(gamma-1)), P = rho^gamma.
+    The exact solution is the initial field translated by (u0, v0) t.
+    """
+    mesh = mesh_2d(n, n, 0.0, L, 0.0, L, periodic=(True, True))
+
+    def ic(x, y, t=0.0):
+        xc = (x - u0 * t) % L - L / 2
+        yc = (y - v0 * t) % L - L / 2
+        r2 = xc * xc + yc * yc
+        a = beta / (2 * math.pi) * np.exp(0.5 * (1 - r2))
+        T = 1 - (gamma - 1) * beta * beta / (8 * gamma * math.pi ** 2) * np.exp(1 - r2)
+        rho = T ** (1 / (gamma - 1))
+        return conservative(rho, [u0 - a * yc, v0 + a * xc], rho ** gamma, gamma)
+    return mesh, ic
+
+
+def sedov(n=512, gamma=GAMMA, rho0=1.0, p_amb=1e-6, e_total=1.0, L=1.2):
+    """Sedov-type blast on [-L, L]^2 (Sec. 6.6 layout): ambient (rho0, 0, p_amb), total energy
+    e_total deposited uniformly in the four elements touching the centre (n must be even)."""
+    assert n % 2 == 0
+    mesh = mesh_2d(n, n, -L, L, -L, L)
+    amb = conservative(rho0, [0.0, 0.0], p_amb, gamma)
+    mesh.bc = amb[None, :].astype(np.float64)
+    hx = 2 * L / n
+    p_c = (gamma - 1) * (e_total / 4) / (hx * hx)
+    centre = np.zeros(mesh.n_elem, dtype=bool)
+    c0 = n // 2 - 1
+    for iy in (c0, c0 + 1):
+        for ix in (c0, c0 + 1):
+            centre[iy * n + ix] = True
+
+    def ic(x, y):
+        w = np.broadcast_to(amb[:, None, None], (4,) + x.shape).copy()
+        hot = conservative(rho0, [0.0, 0.0], p_c, gamma)
+        w[:, centre, :] = hot[:, None]
+        return w
+    return mesh, ic
+
+
+def four_quadrant_states(rng, gamma=GAMMA):
+    """Four quadrant states (rho, u, v, P) with rho, P ~ U[0.1, 2], u, v ~ U[-1, 1]; order
+    (x<0.5,y<0.5), (x>=0.5,y<0.5), (x<0.5,y>=0.5), (x>=0.5,y>=0.5)."""
+    rho = rng.uniform(0.1, 2.0, 4)
+    P = rng.uniform(0.1, 2.0, 4)
+    u = rng.uniform(-1.0, 1.0, 4)
+    v = rng.uniform(-1.0, 1.0, 4)
+    return conservative(rho, [u, v], P, gamma).T.copy()   # [4][nv]
+
+
+def four_quadrant(n, states):
+    """One four-quadrant Riemann problem on [0, 1]^2 with n x n elements; each boundary face
+    takes the state of the quadrant it lies in (Dirichlet)."""
+    def q(ix, iy):
+        return int(ix >= n // 2) + 2 * int(iy >= n // 2)
+    mesh = mesh_2d(n, n, 0.0, 1.0, 0.0, 1.0, bc_of_face=lambda ix, iy, f: q(ix, iy))
+    mesh.bc = np.asarray(states, dtype=np.float64)
+
+    def ic(x, y):
+        qi = (x >= 0.5).astype(int) + 2 * (y >= 0.5).astype(int)
+        return np.asarray(states).T[:, qi]
+    return mesh, ic
+
+
+def nodal_field(mesh: CartMesh, xi, ic):
+    """w[nv][E][Ns] = ic evaluated at the solution nodes built from reference nodes xi."""
+    return np.ascontiguousarray(ic(*node_coords(mesh, xi)), dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Random admissible data
+# ---------------------------------------------------------------------------
+def random_states(rng, n, dim, rho=(0.1, 2.0), vel=(-1.0, 1.0), p=(0.1, 2.0), gamma=GAMMA):
+    """n random admissible conservative states, shape [n][d+2]."""
+    r = rng.uniform(*rho, n)
+    u = [rng.uniform(*vel, n) for _ in range(dim)]
+    P = rng.uniform(*p, n)
+    return conservative(r, u, P, gamma).T.copy()
+
+
+def random_smooth_field(rng, mesh: CartMesh, xi, amp=0.3, gamma=GAMMA, modes=3):
+    """A smooth random admissible field: a sum of a few low Fourier modes in rho, u, v, P."""
+    X = node_coords(mesh, xi)
+    L = [mesh.hi[k] - mesh.lo[k] for k in range(mesh.dim)]
+
+    def field_(base, a):
+        f = np.full(X[0].shape, base, dtype=np.float64)
+        for _ in range(modes):
+            ph = rng.uniform(0, 2 * math.pi)
+            arg = ph
+            for k in range(mesh.dim):
+                arg = arg + 2 * math.pi * rng.integers(1, 4) * (X[k] - mesh.lo[k]) / L[k]
+            f = f + a * rng.uniform(-1, 1) * np.sin(arg)
+        return f
+    rho = field_(1.0, amp / modes)
+    u = [field_(0.0, 0.5) for _ in range(mesh.dim)]
+    P = field_(1.0, amp / modes)
+    return np.ascontiguousarray(conservative(rho, u, P, gamma))
+
+
+def random_discontinuous_field(rng, mesh: CartMesh, xi, gamma=GAMMA, jump=0.5):
+    """Smooth field plus random per-element jumps and node noise: exercises the limiter."""
+    w = random_smooth_field(rng, mesh, xi, gamma=gamma)
+    E, ns = w.shape[1], w.shape[2]
+    rho = w[0] * (1 + jump * rng.uniform(-0.5, 0.5, (E, 1))) * (1 + 0.2 * rng.uniform(-1, 1, (E, ns)))
+    vel = [w[1 + k] / w[0] + 0.3 * rng.uniform(-1, 1, (E, ns)) for k in range(mesh.dim)]
+    ke_old = 0.5 * sum((w[1 + k] / w[0]) ** 2 for k in range(mesh.dim)) * w[0]
+    P = (gamma - 1) * (w[-1] - ke_old) * (1 + jump * rng.uniform(-0.5, 0.5, (E, 1)))
+    P = P * (1 + 0.2 * rng.uniform(-1, 1, (E, ns)))
+    return np.ascontiguousarray(conservative(rho, vel, P, gamma))
