@@ -1,0 +1,339 @@
+"""Benchmark: limited element-stages per second of the kinetic-bounds limiter path.
+
+One step = one SSP-RK3 time step of the whole path on the device (device time step,
+then per stage: face traces, kinetic bounds, FR residual, stage update fused with the
+limiter), i.e. 3 element-stages per element.  Default workload: the isentropic vortex
+on a periodic 128 x 128 quad mesh, P3, 32 x 32 velocity grid, FP32-mixed bounds (the
+FP64 path is timed beside it).  Inputs are resident in HBM; L2 (129 MB) is flushed
+between timed steps because the state (8.4 MB) would otherwise stay cached.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload vortex|sedov|sod] [--precision fp32|fp64]
+
+Multi-GPU runs (torchrun) are replicas: every rank runs the same workload and
+`value` is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "limited element-stages/sec (bounds+limit+RHS) on 1 GB300, FP32 vs FP64; % roofline"
+UNIT = "element-stages/s"
+SMS = 152
+SM_MAX_MHZ = 2070.0
+# FP32 min/max: 64 three-input FMNMX instructions per clock per SM (measured), each
+# two comparisons -> 128 comparisons per clock per SM.
+CMP_PER_CLK_SM = 128.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def workload(name):
+    from paper_2407_20966_gb300 import inputs
+    if name == "vortex":
+        mesh, ic = inputs.isentropic_vortex(128)
+        return dict(name="isentropic vortex 128x128 P3, 32x32 velocity grid, periodic",
+                    dim=2, p=3, nu=(32, 32), mesh=mesh, ic=ic, cfl=0.1)
+    if name == "sedov":
+        mesh, ic = inputs.sedov(512)
+        return dict(name="Sedov blast 512x512 P2, 32x32 velocity grid", dim=2, p=2, nu=(32, 32),
+                    mesh=mesh, ic=ic, cfl=0.1)
+    mesh, ic = inputs.sod(200)
+    return dict(name="Sod shock tube 200 P3, 64 velocity points", dim=1, p=3, nu=(64,), mesh=mesh,
+                ic=ic, cfl=0.1)
+
+
+def stencil_size(wl):
+    n = wl["p"] + 1
+    ns = n ** wl["dim"]
+    nfp = 2 if wl["dim"] == 1 else 4 * n
+    return ns + 2 * nfp
+
+
+def nu_total(wl):
+    return int(np.prod(wl["nu"]))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[2:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        sm = sorted(r[0] for r in rows)
+        loaded = [s for s in sm if s > 0.5 * rows[0][1]] or sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": rows[0][1], "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_2407_20966_gb300 import build, inputs, kbl
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = workload(args.workload)
+    precision = kbl.FP32_MIXED if args.precision == "fp32" else kbl.FP64
+    mesh = wl["mesh"]
+    E = mesh.n_elem
+
+    def make_ctx(prec):
+        ctx = kbl.Context(dim=wl["dim"], p=wl["p"], nu=wl["nu"], precision=prec)
+        ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+        return ctx
+
+    ctx = make_ctx(precision)
+    xi = ctx.operator(kbl.OP_NODES)
+    w0 = inputs.nodal_field(mesh, xi, wl["ic"])
+    w_dev = torch.from_numpy(w0).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed_steps(c, w, K, W):
+        c.set_time(0.0)
+        for _ in range(W):
+            c.step(w, wl["cfl"])
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = c.launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            c.step(w, wl["cfl"])
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        c.check()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, c.launch_count() - l0
+
+    with ClockSampler(dev.index) as clk:
+        ms, launches = timed_steps(ctx, w_dev, args.steps, args.warmup)
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = E * 3 * args.steps * world
+    value = units / (ms * 1e-3)
+
+    # dominant kernel: the bounds kernel, timed per launch with events on the launching
+    # stream, same workload and launch configuration as inside the step
+    wf = torch.zeros((ctx.nv, E, ctx.nfp), dtype=torch.float64, device=dev)
+    bnd = torch.zeros((2, ctx.nv, E), dtype=torch.float64, device=dev)
+    w_dev.copy_(torch.from_numpy(w0))
+    ctx.traces(w_dev, wf)
+    for _ in range(3):
+        ctx.bounds(w_dev, wf, bnd)
+    kb = max(10, args.steps)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kb)]
+    for k in range(kb):
+        flush.zero_()
+        evs[k][0].record(stream)
+        ctx.bounds(w_dev, wf, bnd)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    bounds_ms = sum(a.elapsed_time(b) for a, b in evs) / kb
+    nS, NU = stencil_size(wl), nu_total(wl)
+    cmp_per_launch = 4.0 * nS * NU * E           # min and max of g and of C g per (state, node)
+    achieved = cmp_per_launch / (bounds_ms * 1e-3) / 1e12
+    peak = CMP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcmp/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_bounds2d_f32" if (
+                    wl["dim"] == 2 and precision == kbl.FP32_MIXED) else "bounds",
+                "bounds_ms_per_launch": round(bounds_ms, 4),
+                "peak_source": "152 SMs x 2070 MHz x 64 three-input FMNMX/clk/SM x 2 comparisons"}
+
+    # FP64 leg (same workload, FP64 bounds)
+    fp64 = None
+    if not args.no_fp64_leg and precision != kbl.FP64:
+        c64 = make_ctx(kbl.FP64)
+        w64 = torch.from_numpy(w0).to(dev)
+        k64 = max(3, min(args.steps, 10))
+        ms64, _ = timed_steps(c64, w64, k64, 1)
+        fp64 = {"value": E * 3 * k64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / k64}
+        c64.close()
+
+    # end to end through the C-ABI with host buffers (pinned), per step: H2D, step, D2H
+    w_pin = torch.from_numpy(w0).pin_memory()
+    out_pin = torch.empty_like(w_pin).pin_memory()
+    win, wout = w_pin.numpy(), out_pin.numpy()
+    ctx.set_time(0.0)
+    ctx.run_host(win, wout, 1, wl["cfl"])
+    ke = max(5, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.run_host(win, wout, 1, wl["cfl"])
+    e2e_s = (time.perf_counter() - t0) / ke
+    nbytes = w0.nbytes
+    e2e = {"value": E * 3 / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if precision == kbl.FP32_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "elements": E, "stages_per_step": 3,
+                       "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "fp64": fp64, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    return line, w0, wl
+
+
+# ---------------------------------------------------------------------------
+# CPU checker timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, budget_s=12.0):
+    """Time the FP64 CPU checker on a bounded sample of the workload: a 16 x 16 block of
+    elements of the 2D mesh (periodic within the block), or the whole 1D mesh; single thread."""
+    import oracle as orc
+    from paper_2407_20966_gb300 import inputs
+    orc.build()
+    cfg = orc.Config(dim=wl["dim"], p=wl["p"], nu=tuple(wl["nu"]))
+    xi, _ = orc.gauss_legendre(wl["p"] + 1)
+    mesh = wl["mesh"]
+    if wl["dim"] == 2:
+        nx = mesh.n[0]
+        b = 16
+        i0 = max(0, nx // 2 - b // 2)
+        sub = inputs.mesh_2d(b, b, 0.0, 1.0, 0.0, 1.0, periodic=(True, True))
+        ids = np.array([(i0 + iy) * nx + (i0 + ix) for iy in range(b) for ix in range(b)])
+        w = inputs.nodal_field(mesh, xi, wl["ic"])[:, ids, :]
+        om = orc.Mesh(sub.nbr, mesh.h[ids], mesh.bc)
+        desc = f"{b}x{b} element block of the workload, periodic within the block"
+    else:
+        w = inputs.nodal_field(mesh, xi, wl["ic"])
+        om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+        desc = "whole mesh"
+    w = np.ascontiguousarray(w)
+    dt = orc.dt(cfg, om, w, wl["cfl"])
+    n, t0 = 0, time.perf_counter()
+    while True:
+        w, _ = orc.ssprk3_step(cfg, om, w, dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 200:
+            break
+    value = om.n_elem * 3 * n / el
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} SSP-RK3 steps on a {desc} ({om.n_elem} elements), {el:.1f} s"}
+
+
+def run_reference(args, rank):
+    wl = workload(args.workload)
+    budget = max(5.0, min(60.0, 4.0 * (args.steps + args.warmup)))
+    cb = oracle_sample(wl, budget_s=budget)
+    return {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["name"]}, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    line, w0, wl = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample(wl, budget_s=12.0)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

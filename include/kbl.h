@@ -1,0 +1,183 @@
+/*
+ * kbl.h -- C ABI of libkbl, a GB300 (sm_103a) implementation of the kinetic
+ * bounds and limiting of Dzanic & Martinelli, "High-order limiting methods
+ * using maximum principle bounds derived from the Boltzmann equation I: Euler
+ * equations" (arXiv 2407.20966), inside an explicit Gauss-Legendre flux
+ * reconstruction (nodal DG) Euler SSP-RK3 stage.
+ *
+ * Every compute call runs hand-written CUDA kernels on the context's stream;
+ * there is no CPU fallback.  Calls are asynchronous unless stated otherwise.
+ *
+ * Conventions
+ *   d      dimension, 1 or 2; nv = d + 2 components (rho, m_x[, m_y], E).
+ *   p      order 1..5; Ns = (p+1)^d Gauss-Legendre solution points per
+ *          element, x index fastest (node j*(p+1) + i).
+ *   faces  1D: 0 = -x, 1 = +x, one point each.  2D: 0 = -x, 1 = +x, 2 = -y,
+ *          3 = +y, p+1 Gauss-Legendre points each, ordered by increasing
+ *          coordinate along the face; face point f*(p+1) + k.  Nfp = 2 (1D)
+ *          or 4(p+1) (2D).
+ *   stencil (Sec. 5 of the paper): S = the Ns solution points, the Nfp own
+ *          face points, then the exterior values at the same Nfp points;
+ *          |S| = Ns + 2 Nfp.  The limiting set V is the first Ns + Nfp.
+ *   layouts (all FP64, C order, device memory unless a name says host):
+ *          solution  w  [nv][E][Ns]
+ *          traces    wf [nv][E][Nfp]   interior value at each face point
+ *          residual  R  [nv][E][Ns]    R = -div F (FR with g_DG correction)
+ *          bounds    bnd[2][nv][E]     bnd[0] lower, bnd[1] upper
+ *          alpha     [2][E]            alpha_min (Eq. 39), alpha_P (Eq. 49)
+ *   mesh   axis-aligned Cartesian elements.  nbr[E][2d] >= 0 is the element
+ *          across face f, matched to its face f^1 with the same point order;
+ *          nbr < 0 marks a boundary face with exterior state bc[-(nbr+1)].
+ *
+ * Ownership: the caller owns every array passed in; the library owns its
+ * context, its copy of the mesh and its scratch space (allocated by
+ * kbl_mesh_upload, freed by kbl_destroy).
+ *
+ * Errors: every call returns kbl_status and never aborts or traps.
+ * KBL_EINVAL for bad arguments (nothing is launched); KBL_ECUDA when a CUDA
+ * call fails; a device-side check that meets a non-physical stencil state
+ * (rho <= 0 or P <= 0) writes NaN bounds for that element and raises a flag
+ * that kbl_check / kbl_read_counters report as KBL_ENONPHYSICAL.
+ * kbl_last_error gives a message for the last failure of a context.
+ */
+#ifndef KBL_H
+#define KBL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KBL_OK = 0,
+    KBL_EINVAL = 1,
+    KBL_ENONPHYSICAL = 2,
+    KBL_ECUDA = 3,
+    KBL_ENOMEM = 4,
+    KBL_ETIMEOUT = 5,
+    KBL_ESTATE = 6
+} kbl_status;
+
+/* Arithmetic of the bounds kernel (the rest of the path is FP64 in both).
+ * KBL_FP64: Maxwellians, envelopes and velocity sums in FP64.
+ * KBL_FP32_MIXED: Maxwellians, envelopes and velocity sums in FP32 with
+ *   compensated sums across threads; primitive states (pressure), the box,
+ *   the density floor, the limiting factors and the pressure checks in FP64. */
+typedef enum { KBL_FP64 = 0, KBL_FP32_MIXED = 1 } kbl_precision;
+
+typedef struct {
+    int dim;          /* 1 or 2 */
+    int p;            /* polynomial order, 1..5 */
+    int nu[2];        /* velocity points per axis (Sec. 3.7); 2D: 8, 16, 32 or 64; 1D: 2..4096 */
+    double gamma;     /* ratio of specific heats */
+    double k;         /* box half-width in thermal units, Eq. 45 (4 in Sec. 5) */
+    double r_fac;     /* relaxation of the envelopes, Eq. 40 (1e-3; 0 = strict) */
+    double eps;       /* threshold of the alpha rule stated under Eq. 37 (1e-13) */
+    double rho_floor; /* density floor on rho_min, Sec. 3.8 (1e-12) */
+    double p_floor;   /* pressure floor of Eq. 47-49 (1e-12) */
+    int eps_rule;     /* 0: alpha_i = 0 when |min_V - mean| or |max_V - mean| < eps
+                         (as printed); 1: such a component is skipped */
+    int precision;    /* kbl_precision */
+} kbl_config;
+
+typedef struct kbl_ctx kbl_ctx;
+
+typedef struct {
+    int32_t nonphysical;      /* a stencil state with rho <= 0 or P <= 0 was met */
+    int32_t timeout;          /* a bounded device wait gave up */
+    int64_t limited_elements; /* elements with alpha_min < 1 in the last stage run */
+    int64_t pressure_relimits;/* elements where the step of Eq. 48 was taken */
+} kbl_counters;
+
+/* Fill cfg with the paper's defaults for dimension d and order p: gamma 1.4,
+ * k = 4, nu = 32 per axis in 2D and 64 in 1D, r_fac = 1e-3, eps = 1e-13,
+ * floors 1e-12, eps_rule 0, FP64. */
+kbl_status kbl_config_default(kbl_config* cfg, int dim, int p);
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream).  Synchronous.  *out is NULL on failure. */
+kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream);
+kbl_status kbl_destroy(kbl_ctx* ctx);
+kbl_status kbl_set_stream(kbl_ctx* ctx, void* cuda_stream);
+const char* kbl_last_error(const kbl_ctx* ctx);
+int kbl_nv(const kbl_ctx* ctx);
+int kbl_ns(const kbl_ctx* ctx);
+int kbl_nfp(const kbl_ctx* ctx);
+int kbl_nstencil(const kbl_ctx* ctx);
+
+/* Upload a mesh (HOST arrays, copied; synchronous) and size the scratch
+ * space: nbr[E][2d], h[E][d] element widths (> 0), bc[n_bc][nv] boundary
+ * states.  Every negative nbr must name a valid boundary id.  n_elem may be 0. */
+kbl_status kbl_mesh_upload(kbl_ctx* ctx, int n_elem, const int32_t* nbr_host,
+                           const double* h_host, int n_bc, const double* bc_host);
+
+/* Copy one of the library's FR operators to a HOST buffer of n doubles:
+ * 0 nodes x[p+1], 1 weights[p+1], 2 l_i(-1)[p+1], 3 l_i(+1)[p+1],
+ * 4 D[p+1][p+1] with D[i][m] = l_m'(x_i), 5 g_L'(x_i)[p+1], 6 g_R'(x_i)[p+1]. */
+kbl_status kbl_get_operator(const kbl_ctx* ctx, int which, double* host_out, int n);
+
+/* Interior values at the face points: wf = interpolation of w (Sec. 2.3). */
+kbl_status kbl_traces(kbl_ctx* ctx, const double* w, double* wf);
+
+/* Gather the stencil of elements e0 .. e0+n-1 into S[n][|S|][nv] (a plain
+ * copy of values of w, wf and the boundary states: bit-exact). */
+kbl_status kbl_gather_stencil(kbl_ctx* ctx, const double* w, const double* wf,
+                              int e0, int n, double* S);
+
+/* Kinetic bounds of every element (Sec. 3.3-3.8): Maxwellians of the stencil
+ * states (Eq. 8), their pointwise envelopes (Eq. 32) relaxed by r_fac (Eq. 40)
+ * with separate envelopes for the translational and internal-energy parts
+ * (Eq. 44), trapezoidal sums on the per-element box of Eq. 45 (Eq. 33-36, 46),
+ * then rho_min <- max(rho_min, rho_floor). */
+kbl_status kbl_bounds(kbl_ctx* ctx, const double* w, const double* wf, double* bnd);
+
+/* FR residual R = -div F with Rusanov interface fluxes (assumption (iv) of
+ * Sec. 4) and the g_DG correction; wf must hold the traces of w. */
+kbl_status kbl_rhs(kbl_ctx* ctx, const double* w, const double* wf, double* R);
+
+/* Limit w in place against bnd (Eq. 37-39, then Eq. 47-49); alpha may be NULL. */
+kbl_status kbl_limit(kbl_ctx* ctx, double* w, const double* bnd, double* alpha);
+
+/* One SSP-RK3 stage s in {0,1,2} (Shu-Osher form) fused with the limiter:
+ * wout = limit(a_s wn + b_s (ws + dt R), bnd), dt read from the device scalar
+ * dt_dev.  wout may alias wn.  alpha may be NULL. */
+kbl_status kbl_stage(kbl_ctx* ctx, int s, const double* wn, const double* ws,
+                     const double* R, const double* bnd, const double* dt_dev,
+                     double* wout, double* alpha);
+
+/* dt_dev (device scalar) = cfl * min over elements, solution points and axes
+ * of h / (|U_axis| + c). */
+kbl_status kbl_dt(kbl_ctx* ctx, const double* w, double cfl, double* dt_dev);
+
+/* One full time step on device data: dt from w (clipped so the context's
+ * time does not pass its end time), then three stages, each computing traces,
+ * bounds and residual of its input and applying kbl_stage.  w is replaced by
+ * the new solution.  Uses the context's scratch; launched as a CUDA graph
+ * after the first call with a given w. */
+kbl_status kbl_step(kbl_ctx* ctx, double* w, double cfl);
+
+/* Time of the context (device scalars): set t and the end time (INFINITY for
+ * none); kbl_time_sync reads t back (synchronous). */
+kbl_status kbl_set_time(kbl_ctx* ctx, double t, double t_end);
+kbl_status kbl_time_sync(kbl_ctx* ctx, double* t_host);
+
+/* End-to-end run on HOST buffers: copy w_host_in to the device, take n_steps
+ * steps of kbl_step, copy the result to w_host_out (may alias w_host_in).
+ * Synchronous.  Device buffers are the context's own. */
+kbl_status kbl_run_host(kbl_ctx* ctx, const double* w_host_in, double* w_host_out,
+                        int n_steps, double cfl);
+
+/* Wait for the context's stream and report device-side flags (then clear
+ * them): KBL_ENONPHYSICAL if a non-physical state was met. */
+kbl_status kbl_check(kbl_ctx* ctx);
+kbl_status kbl_read_counters(kbl_ctx* ctx, kbl_counters* out);
+
+/* Number of kernel launches the context has issued (graph launches count
+ * the kernels inside them). */
+int64_t kbl_launch_count(const kbl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

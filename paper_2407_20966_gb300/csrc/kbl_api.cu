@@ -1,0 +1,517 @@
+// kbl_api.cu -- host implementation of the C ABI declared in include/kbl.h.
+//
+// The FR operators are built here in FP64: Gauss-Legendre nodes and weights
+// by the Golub-Welsch eigenvalue method (cyclic Jacobi rotations on the
+// Legendre Jacobi matrix), interpolation and differentiation by the
+// barycentric Lagrange formulas, and the g_DG correction derivatives from the
+// nodal-DG lifting identity g_L'(x_i) = -l_i(-1) / w_i, g_R'(x_i) = l_i(1) / w_i
+// that holds for Gauss-Legendre solution points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kbl_internal.cuh"
+
+namespace {
+
+// ---- FR operators --------------------------------------------------------
+void jacobi_eigen(int n, double* A /* n*n, symmetric, destroyed */, double* V /* n*n, columns */)
+{
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++) off += A[i * n + j] * A[i * n + j];
+        if (off < 1e-40) break;
+        for (int p = 0; p < n; p++) {
+            for (int q = p + 1; q < n; q++) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; k++) {  // A <- A J
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {  // A <- J^T A
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) {  // V <- V J
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+}
+
+void build_ops(int p, FrOps& o)
+{
+    const int n = p + 1;
+    std::memset(&o, 0, sizeof(o));
+    o.n = n;
+    // Golub-Welsch: eigenvalues of the symmetric Jacobi matrix of the Legendre
+    // recurrence are the nodes; weights are 2 * (first eigenvector entry)^2.
+    double A[KBL_NMAX * KBL_NMAX] = {0}, V[KBL_NMAX * KBL_NMAX];
+    for (int k = 1; k < n; k++) {
+        const double b = k / std::sqrt(4.0 * k * k - 1.0);
+        A[(k - 1) * n + k] = b;
+        A[k * n + (k - 1)] = b;
+    }
+    jacobi_eigen(n, A, V);
+    int order[KBL_NMAX];
+    for (int i = 0; i < n; i++) order[i] = i;
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++)
+            if (A[order[j] * n + order[j]] < A[order[i] * n + order[i]]) std::swap(order[i], order[j]);
+    for (int i = 0; i < n; i++) {
+        const int k = order[i];
+        o.x[i] = A[k * n + k];
+        o.wq[i] = 2.0 * V[0 * n + k] * V[0 * n + k];
+    }
+    if (n % 2 == 1) o.x[n / 2] = 0.0;  // the middle node of an odd rule is exactly 0
+    for (int i = 0; i < n / 2; i++) {   // symmetrise the rule
+        const double xs = 0.5 * (o.x[n - 1 - i] - o.x[i]);
+        const double ws = 0.5 * (o.wq[n - 1 - i] + o.wq[i]);
+        o.x[i] = -xs; o.x[n - 1 - i] = xs;
+        o.wq[i] = ws; o.wq[n - 1 - i] = ws;
+    }
+    // barycentric weights
+    double lam[KBL_NMAX];
+    for (int j = 0; j < n; j++) {
+        double prod = 1.0;
+        for (int m = 0; m < n; m++)
+            if (m != j) prod *= (o.x[j] - o.x[m]);
+        lam[j] = 1.0 / prod;
+    }
+    for (int side = 0; side < 2; side++) {
+        const double x = side ? 1.0 : -1.0;
+        double den = 0.0;
+        for (int k = 0; k < n; k++) den += lam[k] / (x - o.x[k]);
+        for (int j = 0; j < n; j++) {
+            const double val = (lam[j] / (x - o.x[j])) / den;
+            if (side) o.lp[j] = val;
+            else o.lm[j] = val;
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        double diag = 0.0;
+        for (int j = 0; j < n; j++) {
+            if (j == i) continue;
+            o.D[i][j] = (lam[j] / lam[i]) / (o.x[i] - o.x[j]);
+            diag -= o.D[i][j];
+        }
+        o.D[i][i] = diag;
+    }
+    for (int i = 0; i < n; i++) {
+        o.gl[i] = -o.lm[i] / o.wq[i];
+        o.gr[i] = o.lp[i] / o.wq[i];
+    }
+}
+
+kbl_status fail(kbl_ctx* c, kbl_status st, const char* msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+kbl_status cuda_fail(kbl_ctx* c, cudaError_t e, const char* where)
+{
+    if (c) {
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return KBL_ECUDA;
+}
+
+// Post-launch check of a launcher result.
+kbl_status after_launch(kbl_ctx* c, int n, const char* where)
+{
+    if (n < 0) return fail(c, KBL_EINVAL, "order/dimension not compiled in");
+    c->launches += n;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return KBL_OK;
+}
+
+void free_mesh(kbl_ctx* c)
+{
+    double** bufs[] = {&c->d_h, &c->d_bc, &c->d_wf, &c->d_R, &c->d_bnd, &c->d_wa, &c->d_wb, &c->d_whost};
+    for (double** b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    if (c->d_nbr) cudaFree(c->d_nbr);
+    c->d_nbr = nullptr;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_w = nullptr;
+    c->mesh_ready = false;
+}
+
+bool ready(kbl_ctx* c) { return c && c->mesh_ready; }
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// Issue one full SSP-RK3 step on stream s (used directly and for capture).
+int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s)
+{
+    int n = 0, r;
+    if ((r = launch_dt(c, w, cfl, c->d_scal, 1, s)) < 0) return -1;
+    n += r;
+    const double* wn = w;
+    const double* ws = w;
+    double* outs[3] = {c->d_wa, c->d_wb, w};
+    for (int st = 0; st < 3; st++) {
+        if ((r = launch_traces(c, ws, c->d_wf, s)) < 0) return -1;
+        n += r;
+        if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
+        n += r;
+        if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
+        n += r;
+        if ((r = launch_stage(c, 0, st, wn, ws, c->d_R, c->d_bnd, c->d_scal, outs[st], nullptr, s)) < 0)
+            return -1;
+        n += r;
+        ws = outs[st];
+    }
+    n += launch_time_advance(c, s);
+    return n;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+kbl_status kbl_config_default(kbl_config* cfg, int dim, int p)
+{
+    if (!cfg || (dim != 1 && dim != 2) || p < 1 || p > KBL_PMAX) return KBL_EINVAL;
+    cfg->dim = dim;
+    cfg->p = p;
+    cfg->nu[0] = dim == 1 ? 64 : 32;
+    cfg->nu[1] = dim == 1 ? 1 : 32;
+    cfg->gamma = 1.4;
+    cfg->k = 4.0;
+    cfg->r_fac = 1e-3;
+    cfg->eps = 1e-13;
+    cfg->rho_floor = 1e-12;
+    cfg->p_floor = 1e-12;
+    cfg->eps_rule = 0;
+    cfg->precision = KBL_FP64;
+    return KBL_OK;
+}
+
+kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
+{
+    if (!out) return KBL_EINVAL;
+    *out = nullptr;
+    if (!cfg) return KBL_EINVAL;
+    if (cfg->dim != 1 && cfg->dim != 2) return KBL_EINVAL;
+    if (cfg->p < 1 || cfg->p > KBL_PMAX) return KBL_EINVAL;
+    if (cfg->dim == 2) {
+        const int nx = cfg->nu[0];
+        if (cfg->nu[1] != nx || (nx != 8 && nx != 16 && nx != 32 && nx != 64)) return KBL_EINVAL;
+    } else if (cfg->nu[0] < 2 || cfg->nu[0] > 4096) {
+        return KBL_EINVAL;
+    }
+    if (!(cfg->gamma > 1.0) || !(cfg->k > 0.0) || !(cfg->r_fac >= 0.0 && cfg->r_fac < 1.0) ||
+        !(cfg->eps >= 0.0) || !(cfg->rho_floor >= 0.0) || !(cfg->p_floor >= 0.0))
+        return KBL_EINVAL;
+    if (cfg->precision != KBL_FP64 && cfg->precision != KBL_FP32_MIXED) return KBL_EINVAL;
+    kbl_ctx* c = new (std::nothrow) kbl_ctx();
+    if (!c) return KBL_ENOMEM;
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->phys.gamma = cfg->gamma;
+    c->phys.k = cfg->k;
+    c->phys.r_fac = cfg->r_fac;
+    c->phys.eps = cfg->eps;
+    c->phys.rho_floor = cfg->rho_floor;
+    c->phys.p_floor = cfg->p_floor;
+    c->phys.eps_rule = cfg->eps_rule;
+    c->phys.nu[0] = cfg->nu[0];
+    c->phys.nu[1] = cfg->dim == 2 ? cfg->nu[1] : 1;
+    build_ops(cfg->p, c->ops);
+    const int n = cfg->p + 1;
+    c->nv = cfg->dim + 2;
+    c->ns = cfg->dim == 1 ? n : n * n;
+    c->nfp = cfg->dim == 1 ? 2 : 4 * n;
+    c->nsten = c->ns + 2 * c->nfp;
+    cudaError_t e;
+    if ((e = dalloc(&c->d_scal, 3)) != cudaSuccess || (e = dalloc(&c->d_dtbits, 1)) != cudaSuccess ||
+        (e = dalloc(&c->d_flags, 1)) != cudaSuccess) {
+        kbl_destroy(c);
+        return KBL_ECUDA;
+    }
+    const double scal[3] = {0.0, 0.0, INFINITY};
+    if ((e = cudaMemcpy(c->d_scal, scal, sizeof(scal), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c->d_flags, 0, sizeof(DevFlags))) != cudaSuccess) {
+        kbl_destroy(c);
+        return KBL_ECUDA;
+    }
+    *out = c;
+    return KBL_OK;
+}
+
+kbl_status kbl_destroy(kbl_ctx* c)
+{
+    if (!c) return KBL_EINVAL;
+    free_mesh(c);
+    if (c->d_scal) cudaFree(c->d_scal);
+    if (c->d_dtbits) cudaFree(c->d_dtbits);
+    if (c->d_flags) cudaFree(c->d_flags);
+    delete c;
+    return KBL_OK;
+}
+
+kbl_status kbl_set_stream(kbl_ctx* c, void* s)
+{
+    if (!c) return KBL_EINVAL;
+    c->stream = (cudaStream_t)s;
+    return KBL_OK;
+}
+
+const char* kbl_last_error(const kbl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+int kbl_nv(const kbl_ctx* c) { return c ? c->nv : -1; }
+int kbl_ns(const kbl_ctx* c) { return c ? c->ns : -1; }
+int kbl_nfp(const kbl_ctx* c) { return c ? c->nfp : -1; }
+int kbl_nstencil(const kbl_ctx* c) { return c ? c->nsten : -1; }
+int64_t kbl_launch_count(const kbl_ctx* c) { return c ? c->launches : -1; }
+
+kbl_status kbl_mesh_upload(kbl_ctx* c, int n_elem, const int32_t* nbr, const double* h, int n_bc,
+                           const double* bc)
+{
+    if (!c) return KBL_EINVAL;
+    const int d = c->cfg.dim, nv = c->nv;
+    if (n_elem < 0 || n_bc < 0) return fail(c, KBL_EINVAL, "negative size");
+    if (n_elem > 0 && (!nbr || !h)) return fail(c, KBL_EINVAL, "null mesh array");
+    if (n_bc > 0 && !bc) return fail(c, KBL_EINVAL, "null boundary states");
+    for (long i = 0; i < (long)n_elem * 2 * d; i++) {
+        const int b = nbr[i];
+        if (b >= n_elem || (b < 0 && -(b + 1) >= n_bc))
+            return fail(c, KBL_EINVAL, "neighbour index or boundary id out of range");
+    }
+    for (long i = 0; i < (long)n_elem * d; i++)
+        if (!(h[i] > 0.0)) return fail(c, KBL_EINVAL, "element width must be positive");
+    cudaStreamSynchronize(c->stream);
+    free_mesh(c);
+    c->E = n_elem;
+    c->n_bc = n_bc;
+    const size_t E = (size_t)n_elem;
+    cudaError_t e;
+    if ((e = dalloc(&c->d_nbr, E * 2 * d)) != cudaSuccess || (e = dalloc(&c->d_h, E * d)) != cudaSuccess ||
+        (e = dalloc(&c->d_bc, (size_t)n_bc * nv)) != cudaSuccess ||
+        (e = dalloc(&c->d_wf, E * nv * c->nfp)) != cudaSuccess ||
+        (e = dalloc(&c->d_R, E * nv * c->ns)) != cudaSuccess ||
+        (e = dalloc(&c->d_bnd, E * nv * 2)) != cudaSuccess ||
+        (e = dalloc(&c->d_wa, E * nv * c->ns)) != cudaSuccess ||
+        (e = dalloc(&c->d_wb, E * nv * c->ns)) != cudaSuccess ||
+        (e = dalloc(&c->d_whost, E * nv * c->ns)) != cudaSuccess) {
+        free_mesh(c);
+        c->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? KBL_ENOMEM : KBL_ECUDA;
+    }
+    if (n_elem > 0) {
+        if ((e = cudaMemcpy(c->d_nbr, nbr, E * 2 * d * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(c->d_h, h, E * d * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_mesh(c);
+            return cuda_fail(c, e, "mesh copy");
+        }
+    }
+    if (n_bc > 0 && (e = cudaMemcpy(c->d_bc, bc, (size_t)n_bc * nv * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_mesh(c);
+        return cuda_fail(c, e, "boundary copy");
+    }
+    c->mesh_ready = true;
+    return KBL_OK;
+}
+
+kbl_status kbl_get_operator(const kbl_ctx* c, int which, double* out, int n)
+{
+    if (!c || !out) return KBL_EINVAL;
+    const int np = c->ops.n;
+    const int need = (which == 4) ? np * np : np;
+    if (which < 0 || which > 6 || n < need) return KBL_EINVAL;
+    for (int i = 0; i < np; i++) {
+        switch (which) {
+            case 0: out[i] = c->ops.x[i]; break;
+            case 1: out[i] = c->ops.wq[i]; break;
+            case 2: out[i] = c->ops.lm[i]; break;
+            case 3: out[i] = c->ops.lp[i]; break;
+            case 4: for (int m = 0; m < np; m++) out[i * np + m] = c->ops.D[i][m]; break;
+            case 5: out[i] = c->ops.gl[i]; break;
+            case 6: out[i] = c->ops.gr[i]; break;
+        }
+    }
+    return KBL_OK;
+}
+
+kbl_status kbl_traces(kbl_ctx* c, const double* w, double* wf)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (c->E > 0 && (!w || !wf)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_traces(c, w, wf, c->stream), "traces");
+}
+
+kbl_status kbl_gather_stencil(kbl_ctx* c, const double* w, const double* wf, int e0, int n, double* S)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (e0 < 0 || n < 0 || (long)e0 + n > c->E) return fail(c, KBL_EINVAL, "element range");
+    if (n > 0 && (!w || !wf || !S)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_gather(c, w, wf, e0, n, S, c->stream), "gather");
+}
+
+kbl_status kbl_bounds(kbl_ctx* c, const double* w, const double* wf, double* bnd)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (c->E > 0 && (!w || !wf || !bnd)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_bounds(c, w, wf, bnd, c->stream), "bounds");
+}
+
+kbl_status kbl_rhs(kbl_ctx* c, const double* w, const double* wf, double* R)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (c->E > 0 && (!w || !wf || !R)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_rhs(c, w, wf, R, c->stream), "rhs");
+}
+
+kbl_status kbl_limit(kbl_ctx* c, double* w, const double* bnd, double* alpha)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (c->E > 0 && (!w || !bnd)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_stage(c, 1, 0, w, w, nullptr, bnd, nullptr, w, alpha, c->stream), "limit");
+}
+
+kbl_status kbl_stage(kbl_ctx* c, int s, const double* wn, const double* ws, const double* R,
+                     const double* bnd, const double* dt_dev, double* wout, double* alpha)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (s < 0 || s > 2) return fail(c, KBL_EINVAL, "stage must be 0, 1 or 2");
+    if (c->E > 0 && (!wn || !ws || !R || !bnd || !dt_dev || !wout)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_stage(c, 0, s, wn, ws, R, bnd, dt_dev, wout, alpha, c->stream), "stage");
+}
+
+kbl_status kbl_dt(kbl_ctx* c, const double* w, double cfl, double* dt_dev)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (!dt_dev || (c->E > 0 && !w) || !(cfl > 0.0)) return fail(c, KBL_EINVAL, "bad argument");
+    // the context's end time is not applied here: dt_dev gets cfl * min(h / (|U| + c))
+    return after_launch(c, launch_dt(c, w, cfl, dt_dev, 0, c->stream), "dt");
+}
+
+kbl_status kbl_set_time(kbl_ctx* c, double t, double t_end)
+{
+    if (!c) return KBL_EINVAL;
+    const double v[2] = {t, t_end};
+    cudaError_t e = cudaMemcpyAsync(c->d_scal + 1, v, sizeof(v), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_time");
+    return KBL_OK;
+}
+
+kbl_status kbl_time_sync(kbl_ctx* c, double* t)
+{
+    if (!c || !t) return KBL_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(t, c->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "time_sync");
+    return KBL_OK;
+}
+
+kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if ((c->E > 0 && !w) || !(cfl > 0.0)) return fail(c, KBL_EINVAL, "bad argument");
+    if (c->E == 0) return KBL_OK;
+    if (!(c->graph && c->graph_w == w && c->graph_cfl == cfl)) {
+        if (c->graph) cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(c, e, "begin capture");
+        }
+        const int n = issue_step(c, w, cfl, cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (n < 0) {
+            if (g) cudaGraphDestroy(g);
+            return fail(c, KBL_EINVAL, "order/dimension not compiled in");
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return cuda_fail(c, e, "instantiate");
+        }
+        c->graph_w = w;
+        c->graph_cfl = cfl;
+        c->graph_kernels = n;
+    }
+    cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c->launches += c->graph_kernels;
+    return KBL_OK;
+}
+
+kbl_status kbl_run_host(kbl_ctx* c, const double* win, double* wout, int n_steps, double cfl)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (n_steps < 0 || !(cfl > 0.0) || (c->E > 0 && (!win || !wout))) return fail(c, KBL_EINVAL, "bad argument");
+    const size_t bytes = (size_t)c->E * c->nv * c->ns * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(c->d_whost, win, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "H2D");
+    for (int i = 0; i < n_steps; i++) {
+        kbl_status st = kbl_step(c, c->d_whost, cfl);
+        if (st != KBL_OK) return st;
+    }
+    e = cudaMemcpyAsync(wout, c->d_whost, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "D2H");
+    return KBL_OK;
+}
+
+kbl_status kbl_read_counters(kbl_ctx* c, kbl_counters* out)
+{
+    if (!c || !out) return KBL_EINVAL;
+    DevFlags f;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&f, c->d_flags, sizeof(f), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, sizeof(DevFlags));
+    if (e != cudaSuccess) return cuda_fail(c, e, "counters");
+    out->nonphysical = f.nonphysical;
+    out->timeout = f.timeout;
+    out->limited_elements = (int64_t)f.limited;
+    out->pressure_relimits = (int64_t)f.prelimit;
+    if (f.timeout) return fail(c, KBL_ETIMEOUT, "a bounded device wait gave up");
+    if (f.nonphysical) return fail(c, KBL_ENONPHYSICAL, "non-physical stencil state (rho <= 0 or P <= 0)");
+    return KBL_OK;
+}
+
+kbl_status kbl_check(kbl_ctx* c)
+{
+    kbl_counters k;
+    return kbl_read_counters(c, &k);
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// kbl_internal.cuh -- shared declarations of the libkbl CUDA sources.
+//
+// Layout and indexing conventions are those of include/kbl.h.  Everything here
+// is internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "kbl.h"
+
+#define KBL_PMAX 5
+#define KBL_NMAX (KBL_PMAX + 1)
+
+// Reference-element FR operators of one order, passed to kernels by value.
+struct FrOps {
+    int n;                                  // p + 1
+    double x[KBL_NMAX], wq[KBL_NMAX];       // Gauss-Legendre nodes, weights
+    double lm[KBL_NMAX], lp[KBL_NMAX];      // l_i(-1), l_i(+1)
+    double D[KBL_NMAX][KBL_NMAX];           // D[i][m] = l_m'(x_i)
+    double gl[KBL_NMAX], gr[KBL_NMAX];      // g_L'(x_i), g_R'(x_i)
+};
+
+// Physical and method constants, passed by value.
+struct Phys {
+    double gamma, k, r_fac, eps, rho_floor, p_floor;
+    int eps_rule;
+    int nu[2];
+};
+
+struct MeshDev {
+    int E;
+    const int* nbr;     // [E][2d]
+    const double* h;    // [E][d]
+    const double* bc;   // [n_bc][nv]
+    int n_bc;
+};
+
+struct DevFlags {
+    int nonphysical;
+    int timeout;
+    unsigned long long limited;
+    unsigned long long prelimit;
+};
+
+struct kbl_ctx {
+    kbl_config cfg;
+    Phys phys;
+    FrOps ops;
+    cudaStream_t stream = nullptr;
+    int nv = 0, ns = 0, nfp = 0, nsten = 0;
+    int E = 0, n_bc = 0;
+    bool mesh_ready = false;
+    // mesh copy
+    int* d_nbr = nullptr;
+    double* d_h = nullptr;
+    double* d_bc = nullptr;
+    // scratch
+    double* d_wf = nullptr;     // [nv][E][Nfp]
+    double* d_R = nullptr;      // [nv][E][Ns]
+    double* d_bnd = nullptr;    // [2][nv][E]
+    double* d_wa = nullptr;     // stage buffers [nv][E][Ns]
+    double* d_wb = nullptr;
+    double* d_whost = nullptr;  // device copy used by kbl_run_host
+    double* d_scal = nullptr;   // [0] dt, [1] t, [2] t_end
+    unsigned long long* d_dtbits = nullptr;
+    DevFlags* d_flags = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    // graph of kbl_step, keyed by (w, cfl)
+    cudaGraphExec_t graph = nullptr;
+    double* graph_w = nullptr;
+    double graph_cfl = 0.0;
+    int graph_kernels = 0;
+};
+
+MeshDev mesh_of(const kbl_ctx* c);
+
+// ---- launchers (kbl_fr.cu, kbl_bounds.cu, kbl_limit.cu) ------------------
+// Each returns the number of kernels it launched, or -1 if the (dim, p)
+// combination is not compiled in.
+int launch_traces(const kbl_ctx* c, const double* w, double* wf, cudaStream_t s);
+int launch_gather(const kbl_ctx* c, const double* w, const double* wf, int e0, int n,
+                  double* S, cudaStream_t s);
+int launch_rhs(const kbl_ctx* c, const double* w, const double* wf, double* R, cudaStream_t s);
+// dt_out <- cfl * min(h / (|U| + c)); with clip, also <= t_end - t of the context
+int launch_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int clip, cudaStream_t s);
+int launch_time_advance(const kbl_ctx* c, cudaStream_t s);
+int launch_bounds(const kbl_ctx* c, const double* w, const double* wf, double* bnd,
+                  cudaStream_t s);
+// mode 0: RK stage s fused with the limiter; mode 1: limiter only (ws = w in place)
+int launch_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const double* ws,
+                 const double* R, const double* bnd, const double* dt, double* wout,
+                 double* alpha, cudaStream_t s);
+
+// ---- device helpers ----------------------------------------------------------
+#define KBL_PI 3.14159265358979323846
+
+template <int DIM>
+__device__ __forceinline__ double kbl_pressure(const double* q, double gm1)
+{
+    double mm = q[1] * q[1];
+    if (DIM == 2) mm += q[2] * q[2];
+    return gm1 * (q[DIM + 1] - 0.5 * mm / q[0]);
+}
+
+// Flux along axis `dir` (Eq. 2).
+template <int DIM>
+__device__ __forceinline__ void kbl_flux(const double* q, int dir, double gm1, double* F)
+{
+    const double P = kbl_pressure<DIM>(q, gm1);
+    const double u = q[1 + dir] / q[0];
+    F[0] = q[1 + dir];
+    F[1] = q[1] * u + (dir == 0 ? P : 0.0);
+    if (DIM == 2) F[2] = q[2] * u + (dir == 1 ? P : 0.0);
+    F[DIM + 1] = (q[DIM + 1] + P) * u;
+}
+
+// Rusanov flux with the Davis wavespeed; ql on the minus side of the axis.
+template <int DIM>
+__device__ __forceinline__ void kbl_rusanov(const double* ql, const double* qr, int dir,
+                                            double gamma, double* F)
+{
+    constexpr int NV = DIM + 2;
+    const double gm1 = gamma - 1.0;
+    double Fl[NV], Fr[NV];
+    kbl_flux<DIM>(ql, dir, gm1, Fl);
+    kbl_flux<DIM>(qr, dir, gm1, Fr);
+    const double Pl = kbl_pressure<DIM>(ql, gm1), Pr = kbl_pressure<DIM>(qr, gm1);
+    const double sl = fabs(ql[1 + dir] / ql[0]) + sqrt(gamma * Pl / ql[0]);
+    const double sr = fabs(qr[1 + dir] / qr[0]) + sqrt(gamma * Pr / qr[0]);
+    const double lam = fmax(sl, sr);
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v] = 0.5 * (Fl[v] + Fr[v]) - 0.5 * lam * (qr[v] - ql[v]);
+}
+
+// Exterior value of component v at face point fp of element e.
+template <int DIM, int N>
+__device__ __forceinline__ double kbl_exterior(const double* __restrict__ wf, const MeshDev& m,
+                                               int e, int fp, int v)
+{
+    constexpr int NFPF = (DIM == 1) ? 1 : N;
+    constexpr int NFP = (DIM == 1) ? 2 : 4 * N;
+    const int f = fp / NFPF, k = fp - f * NFPF;
+    const int nb = m.nbr[e * 2 * DIM + f];
+    if (nb >= 0) return wf[((size_t)v * m.E + nb) * NFP + (f ^ 1) * NFPF + k];
+    return m.bc[(-nb - 1) * (DIM + 2) + v];
+}
+
+template <int DIM>
+__host__ __device__ constexpr int kbl_ns(int n) { return DIM == 1 ? n : n * n; }
+template <int DIM>
+__host__ __device__ constexpr int kbl_nfp(int n) { return DIM == 1 ? 2 : 4 * n; }
+
+// Dispatch a templated launcher over (DIM, N = p + 1).
+#define KBL_DISPATCH(DIMV, NV_, FN, ...)                                   \
+    do {                                                                   \
+        if ((DIMV) == 1) {                                                 \
+            switch (NV_) {                                                 \
+                case 2: return FN<1, 2>(__VA_ARGS__);                      \
+                case 3: return FN<1, 3>(__VA_ARGS__);                      \
+                case 4: return FN<1, 4>(__VA_ARGS__);                      \
+                case 5: return FN<1, 5>(__VA_ARGS__);                      \
+                case 6: return FN<1, 6>(__VA_ARGS__);                      \
+            }                                                              \
+        } else {                                                           \
+            switch (NV_) {                                                 \
+                case 2: return FN<2, 2>(__VA_ARGS__);                      \
+                case 3: return FN<2, 3>(__VA_ARGS__);                      \
+                case 4: return FN<2, 4>(__VA_ARGS__);                      \
+                case 5: return FN<2, 5>(__VA_ARGS__);                      \
+                case 6: return FN<2, 6>(__VA_ARGS__);                      \
+            }                                                              \
+        }                                                                  \
+        return -1;                                                         \
+    } while (0)

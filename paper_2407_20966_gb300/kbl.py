@@ -1,0 +1,243 @@
+"""ctypes binding of libkbl (include/kbl.h): argument marshalling only.
+
+Every compute call goes straight to the CUDA library; there is no CPU path.
+Device arrays are torch CUDA float64 tensors (contiguous), host arrays are
+numpy.  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkbl.so")
+
+OK, EINVAL, ENONPHYSICAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = range(7)
+FP64, FP32_MIXED = 0, 1
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENONPHYSICAL", 3: "ECUDA", 4: "ENOMEM", 5: "ETIMEOUT",
+           6: "ESTATE"}
+
+# FR operator ids of kbl_get_operator
+OP_NODES, OP_WEIGHTS, OP_LMINUS, OP_LPLUS, OP_D, OP_GL, OP_GR = range(7)
+
+
+class KblError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class KblConfig(C.Structure):
+    _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nu", C.c_int * 2), ("gamma", C.c_double),
+                ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
+                ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
+                ("precision", C.c_int)]
+
+
+class KblCounters(C.Structure):
+    _fields_ = [("nonphysical", C.c_int32), ("timeout", C.c_int32),
+                ("limited_elements", C.c_int64), ("pressure_relimits", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); mirrors include/kbl.h
+_P = C.c_void_p
+_SIGS = {
+    "kbl_config_default": (C.c_int, [C.POINTER(KblConfig), C.c_int, C.c_int]),
+    "kbl_create": (C.c_int, [C.POINTER(_P), C.POINTER(KblConfig), _P]),
+    "kbl_destroy": (C.c_int, [_P]),
+    "kbl_set_stream": (C.c_int, [_P, _P]),
+    "kbl_last_error": (C.c_char_p, [_P]),
+    "kbl_nv": (C.c_int, [_P]),
+    "kbl_ns": (C.c_int, [_P]),
+    "kbl_nfp": (C.c_int, [_P]),
+    "kbl_nstencil": (C.c_int, [_P]),
+    "kbl_mesh_upload": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "kbl_get_operator": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "kbl_traces": (C.c_int, [_P, _P, _P]),
+    "kbl_gather_stencil": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P]),
+    "kbl_bounds": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_rhs": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_limit": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_stage": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "kbl_dt": (C.c_int, [_P, _P, C.c_double, _P]),
+    "kbl_step": (C.c_int, [_P, _P, C.c_double]),
+    "kbl_set_time": (C.c_int, [_P, C.c_double, C.c_double]),
+    "kbl_time_sync": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "kbl_run_host": (C.c_int, [_P, _P, _P, C.c_int, C.c_double]),
+    "kbl_check": (C.c_int, [_P]),
+    "kbl_read_counters": (C.c_int, [_P, C.POINTER(KblCounters)]),
+    "kbl_launch_count": (C.c_int64, [_P]),
+}
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def load(path: str | None = None):
+    """Load libkbl.so (build it first with paper_2407_20966_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise KblError(ESTATE, f"{p} not found: build the CUDA library first "
+                                       "(python -m paper_2407_20966_gb300.build)")
+            lib = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _dev(t, name="array"):
+    """Device pointer of a contiguous CUDA float64 tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype, name="array"):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _current_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One method configuration bound to one CUDA stream and (after mesh_upload) one mesh."""
+
+    def __init__(self, dim=2, p=3, nu=None, precision=FP64, stream=None, **overrides):
+        lib = load()
+        cfg = KblConfig()
+        self._check_static(lib.kbl_config_default(C.byref(cfg), dim, p), "config_default")
+        if nu is not None:
+            nu = list(nu) + [nu[0]] * (2 - len(nu))
+            cfg.nu[0], cfg.nu[1] = nu[0], (nu[1] if dim == 2 else 1)
+        cfg.precision = precision
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        h = C.c_void_p()
+        s = stream if stream is not None else _current_stream()
+        self._check_static(lib.kbl_create(C.byref(h), C.byref(cfg), s), "create")
+        self._h = h
+        self._lib = lib
+        self.dim, self.p = dim, p
+        self.nv = lib.kbl_nv(h)
+        self.ns = lib.kbl_ns(h)
+        self.nfp = lib.kbl_nfp(h)
+        self.nstencil = lib.kbl_nstencil(h)
+        self.E = 0
+
+    @staticmethod
+    def _check_static(st, what):
+        if st != OK:
+            raise KblError(st, what)
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self._lib.kbl_last_error(self._h)
+            raise KblError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kbl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- set-up --------------------------------------------------------
+    def set_stream(self, stream=None):
+        self._check(self._lib.kbl_set_stream(self._h, stream if stream is not None else _current_stream()),
+                    "set_stream")
+
+    def mesh_upload(self, nbr, h, bc=None):
+        nbr, pn = _host(nbr, np.int32)
+        hh, ph = _host(h, np.float64)
+        bc = np.zeros((0, self.nv)) if bc is None else bc
+        bc, pb = _host(bc, np.float64)
+        E = nbr.shape[0]
+        self._check(self._lib.kbl_mesh_upload(self._h, E, pn, ph, bc.shape[0] if bc.size else 0, pb),
+                    "mesh_upload")
+        self.E = E
+
+    def operator(self, which):
+        n = (self.p + 1) ** 2 if which == OP_D else self.p + 1
+        out = np.zeros(n)
+        self._check(self._lib.kbl_get_operator(self._h, which, out.ctypes.data_as(C.c_void_p), n),
+                    "get_operator")
+        return out.reshape(self.p + 1, self.p + 1) if which == OP_D else out
+
+    # ---- compute (device tensors) -------------------------------------
+    def traces(self, w, wf):
+        self._check(self._lib.kbl_traces(self._h, _dev(w, "w"), _dev(wf, "wf")), "traces")
+
+    def gather_stencil(self, w, wf, e0, n, S):
+        self._check(self._lib.kbl_gather_stencil(self._h, _dev(w), _dev(wf), e0, n, _dev(S)), "gather")
+
+    def bounds(self, w, wf, bnd):
+        self._check(self._lib.kbl_bounds(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(bnd, "bnd")), "bounds")
+
+    def rhs(self, w, wf, R):
+        self._check(self._lib.kbl_rhs(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(R, "R")), "rhs")
+
+    def limit(self, w, bnd, alpha=None):
+        self._check(self._lib.kbl_limit(self._h, _dev(w, "w"), _dev(bnd, "bnd"), _dev(alpha)), "limit")
+
+    def stage(self, s, wn, ws, R, bnd, dt_dev, wout, alpha=None):
+        self._check(self._lib.kbl_stage(self._h, s, _dev(wn), _dev(ws), _dev(R), _dev(bnd), _dev(dt_dev),
+                                        _dev(wout), _dev(alpha)), "stage")
+
+    def dt(self, w, cfl, dt_dev):
+        self._check(self._lib.kbl_dt(self._h, _dev(w), float(cfl), _dev(dt_dev)), "dt")
+
+    def step(self, w, cfl):
+        self._check(self._lib.kbl_step(self._h, _dev(w, "w"), float(cfl)), "step")
+
+    def set_time(self, t, t_end=float("inf")):
+        self._check(self._lib.kbl_set_time(self._h, float(t), float(t_end)), "set_time")
+
+    def time(self):
+        t = C.c_double()
+        self._check(self._lib.kbl_time_sync(self._h, C.byref(t)), "time_sync")
+        return t.value
+
+    def run_host(self, w_in: np.ndarray, w_out: np.ndarray, n_steps, cfl):
+        for a in (w_in, w_out):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("host arrays must be contiguous float64")
+        self._check(self._lib.kbl_run_host(self._h, w_in.ctypes.data_as(C.c_void_p),
+                                           w_out.ctypes.data_as(C.c_void_p), int(n_steps), float(cfl)),
+                    "run_host")
+
+    def check(self):
+        self._check(self._lib.kbl_check(self._h), "check")
+
+    def counters(self):
+        k = KblCounters()
+        st = self._lib.kbl_read_counters(self._h, C.byref(k))
+        return st, {f: getattr(k, f) for f, _ in KblCounters._fields_}
+
+    def launch_count(self):
+        return int(self._lib.kbl_launch_count(self._h))

@@ -1,0 +1,295 @@
+"""GPU parity: every entry point of the C-ABI against the CPU checker on the same seeded inputs.
+
+Bar: bit-exact for the stencil gather (plain index work); 1e-12 relative for FP64 bounds,
+residuals and limited states; 1e-5 relative for the FP32 bounds.  Sizes span several
+thread blocks with a ragged tail; edge cases: an empty mesh, a one-element periodic mesh,
+a non-physical state.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import (TOL_FP32, TOL_FP64, both, bounds_error, mesh_and_field,
+                               state_error, to_dev, upload, zeros_dev)
+
+pytestmark = pytest.mark.gpu
+
+CASES_2D = [  # (p, nu, elements per side)
+    (3, 32, (13, 11)),
+    (2, 32, (9, 7)),
+    (1, 16, (5, 17)),
+    (4, 8, (6, 5)),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_20966_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("dim,p", [(1, 3), (2, 3), (2, 2), (2, 4)])
+def test_operators_match_checker(orc, dim, p):
+    from paper_2407_20966_gb300 import kbl
+    ctx, _ = both(orc, dim, p, (64,) if dim == 1 else (32, 32))
+    x, wq = orc.gauss_legendre(p + 1)
+    np.testing.assert_allclose(ctx.operator(kbl.OP_NODES), x, rtol=0, atol=2e-15)
+    np.testing.assert_allclose(ctx.operator(kbl.OP_WEIGHTS), wq, rtol=0, atol=2e-15)
+    lm = [orc.lagrange(x, j, -1.0) for j in range(p + 1)]
+    np.testing.assert_allclose(ctx.operator(kbl.OP_LMINUS), lm, rtol=0, atol=1e-13)
+    D = [[orc.lagrange_deriv(x, m, x[i]) for m in range(p + 1)] for i in range(p + 1)]
+    np.testing.assert_allclose(ctx.operator(kbl.OP_D), D, rtol=0, atol=1e-12)
+    gl = [orc.correction_deriv(p, xi)[0] for xi in x]
+    np.testing.assert_allclose(ctx.operator(kbl.OP_GL), gl, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (7, 5)), (2, 1, (3, 9))])
+def test_traces_and_gather(orc, dim, p, n):
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16))
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=1)
+    om = upload(ctx, orc, mesh)
+    wf_ref = orc.traces(ocfg, om, w)
+    wd = to_dev(w)
+    wf = zeros_dev(*wf_ref.shape)
+    ctx.traces(wd, wf)
+    np.testing.assert_allclose(wf.cpu().numpy(), wf_ref, rtol=1e-14, atol=1e-14)
+    # gather is a copy: bit-exact given the same traces
+    E = mesh.n_elem
+    S = zeros_dev(E, ocfg.nstencil, ocfg.nv)
+    ctx.gather_stencil(wd, to_dev(wf_ref), 0, E, S)
+    S = S.cpu().numpy()
+    for e in range(E):
+        np.testing.assert_array_equal(S[e], orc.gather_stencil(ocfg, om, w, wf_ref, e))
+
+
+def _bounds_case(orc, dim, p, nu, n, precision, seed, kind="disc", **kw):
+    ctx, ocfg = both(orc, dim, p, nu, precision=precision, **kw)
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=seed, kind=kind)
+    om = upload(ctx, orc, mesh)
+    wf = orc.traces(ocfg, om, w)
+    ref = orc.bounds(ocfg, om, w, wf)
+    bnd = zeros_dev(2, ocfg.nv, mesh.n_elem)
+    ctx.bounds(to_dev(w), to_dev(wf), bnd)
+    ctx.check()
+    return bounds_error(bnd.cpu().numpy(), ref), ref
+
+
+@pytest.mark.parametrize("p,nu,n", CASES_2D)
+def test_bounds_fp64_2d(orc, p, nu, n):
+    err, _ = _bounds_case(orc, 2, p, (nu, nu), n, 0, seed=p)
+    assert err.max() < TOL_FP64, err.max()
+
+
+@pytest.mark.parametrize("p,nu,n", [(3, 64, 41), (2, 200, 9), (5, 33, 4), (1, 2048, 3)])
+def test_bounds_fp64_1d(orc, p, nu, n):
+    err, _ = _bounds_case(orc, 1, p, (nu,), n, 0, seed=10 + p)
+    assert err.max() < TOL_FP64, err.max()
+
+
+@pytest.mark.parametrize("p,nu,n", CASES_2D)
+def test_bounds_fp32_2d(orc, p, nu, n):
+    err, _ = _bounds_case(orc, 2, p, (nu, nu), n, 1, seed=20 + p)
+    assert err.max() < TOL_FP32, err.max()
+
+
+@pytest.mark.parametrize("p,nu,n", [(3, 64, 41), (2, 200, 9), (1, 2048, 3)])
+def test_bounds_fp32_1d(orc, p, nu, n):
+    err, _ = _bounds_case(orc, 1, p, (nu,), n, 1, seed=30 + p)
+    assert err.max() < TOL_FP32, err.max()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_FP32)])
+def test_bounds_strict_mode_and_eps_rule(orc, precision, tol):
+    """Strict bounds (r_fac = 0, k = 8; Sec. 3.5, Sec. 5) and the skip reading of the epsilon rule."""
+    err, _ = _bounds_case(orc, 2, 3, (32, 32), (5, 4), precision, seed=41, r_fac=0.0, k=8.0, eps_rule=1)
+    assert err.max() < tol, err.max()
+
+
+@pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7)), (2, 2, (4, 13)), (2, 5, (3, 3))])
+def test_rhs(orc, dim, p, n):
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16))
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=50 + p)
+    om = upload(ctx, orc, mesh)
+    wf = orc.traces(ocfg, om, w)
+    ref = orc.rhs(ocfg, om, w, wf)
+    R = zeros_dev(*w.shape)
+    ctx.rhs(to_dev(w), to_dev(wf), R)
+    err = np.abs(R.cpu().numpy() - ref) / np.abs(ref).max()
+    assert err.max() < TOL_FP64, err.max()
+
+
+@pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7)), (2, 2, (4, 13))])
+def test_limit(orc, dim, p, n):
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16))
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=60 + p, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    bnd = orc.bounds(ocfg, om, w, orc.traces(ocfg, om, w))
+    rng = np.random.default_rng(3)
+    w2 = w * (1 + 0.3 * rng.uniform(-1, 1, w.shape))   # rough data against smooth bounds
+    ref, a_ref = orc.limit(ocfg, om, w2, bnd)
+    wd = to_dev(w2)
+    alpha = zeros_dev(2, mesh.n_elem)
+    ctx.limit(wd, to_dev(bnd), alpha)
+    assert state_error(wd.cpu().numpy(), ref).max() < TOL_FP64
+    np.testing.assert_allclose(alpha.cpu().numpy(), a_ref, rtol=1e-10, atol=1e-12)
+    assert (a_ref[0] < 1).any()
+
+
+def test_pressure_relimit_path(orc):
+    """Elements with negative pressure at some nodes exercise Eq. 47-49 on both sides."""
+    ctx, ocfg = both(orc, 2, 2, (16, 16))
+    mesh, w = mesh_and_field(orc, 2, 2, (6, 5), seed=70, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    bnd = orc.bounds(ocfg, om, w, orc.traces(ocfg, om, w))
+    bnd[0] -= 10.0   # wide bounds: only the pressure step acts
+    bnd[1] += 10.0
+    w2 = w.copy()
+    w2[1, ::3, 0] *= 6.0   # kinetic energy above total energy at one node
+    ref, a_ref = orc.limit(ocfg, om, w2, bnd)
+    assert (a_ref[1] < 1).any()
+    wd = to_dev(w2)
+    alpha = zeros_dev(2, mesh.n_elem)
+    ctx.limit(wd, to_dev(bnd), alpha)
+    assert state_error(wd.cpu().numpy(), ref).max() < TOL_FP64
+    np.testing.assert_allclose(alpha.cpu().numpy(), a_ref, rtol=1e-10, atol=1e-12)
+    st, c = ctx.counters()
+    assert c["pressure_relimits"] == int((a_ref[1] < 1).sum())
+
+
+@pytest.mark.parametrize("s", [0, 1, 2])
+def test_stage(orc, s):
+    ctx, ocfg = both(orc, 2, 3, (16, 16))
+    mesh, w = mesh_and_field(orc, 2, 3, (7, 6), seed=80 + s, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    wf = orc.traces(ocfg, om, w)
+    bnd = orc.bounds(ocfg, om, w, wf)
+    R = orc.rhs(ocfg, om, w, wf)
+    wn = w * 1.01
+    dt = 0.2 * orc.dt(ocfg, om, w, 0.1)
+    ref = orc.stage_combine(ocfg, om, s, wn, w, R, dt)
+    ref, _ = orc.limit(ocfg, om, ref, bnd)
+    out = zeros_dev(*w.shape)
+    ctx.stage(s, to_dev(wn), to_dev(w), to_dev(R), to_dev(bnd), to_dev(np.array([dt])), out)
+    assert state_error(out.cpu().numpy(), ref).max() < TOL_FP64
+
+
+@pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7))])
+def test_dt(orc, dim, p, n):
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16))
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=90)
+    om = upload(ctx, orc, mesh)
+    d = zeros_dev(1)
+    ctx.dt(to_dev(w), 0.3, d)
+    assert d.item() == pytest.approx(orc.dt(ocfg, om, w, 0.3), rel=1e-14)
+
+
+@pytest.mark.parametrize("dim,p,n,nu,precision", [
+    (1, 3, 40, (64,), 0), (2, 3, (8, 6), (32, 32), 0), (2, 2, (6, 9), (16, 16), 0),
+    (1, 3, 40, (64,), 1), (2, 3, (8, 6), (32, 32), 1)])
+def test_full_step(orc, dim, p, n, nu, precision):
+    """One SSP-RK3 step with bounds and limiting after each stage (Sec. 3.9), from the same
+    state; the device time step is compared too."""
+    ctx, ocfg = both(orc, dim, p, nu, precision=precision)
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=100 + p, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    dt = orc.dt(ocfg, om, w, 0.1)
+    ref, _ = orc.ssprk3_step(ocfg, om, w, dt)
+    wd = to_dev(w)
+    ctx.set_time(0.0)
+    ctx.step(wd, 0.1)
+    assert ctx.time() == pytest.approx(dt, rel=1e-14)
+    tol = TOL_FP64 if precision == 0 else TOL_FP32
+    assert state_error(wd.cpu().numpy(), ref).max() < tol
+    ctx.check()
+
+
+def test_sod_steps_and_end_time(orc):
+    """Config of the 1D shock tube (Sec. 6.1 set-up, 200 P3 elements, 64 velocity points): the
+    steps to a short end time against the checker, the last one clipped to the end time."""
+    from paper_2407_20966_gb300 import inputs
+    mesh, ic = inputs.sod(200)
+    ctx, ocfg = both(orc, 1, 3, (64,))
+    om = upload(ctx, orc, mesh)
+    xi, _ = orc.gauss_legendre(4)
+    w = inputs.nodal_field(mesh, xi, ic)
+    t_end = 9.5 * orc.dt(ocfg, om, w, 0.1)
+    ref, t, nsteps = w.copy(), 0.0, 0
+    while t < t_end - 1e-15:
+        dt = min(orc.dt(ocfg, om, ref, 0.1), t_end - t)
+        ref, _ = orc.ssprk3_step(ocfg, om, ref, dt)
+        t += dt
+        nsteps += 1
+    wd = to_dev(w)
+    ctx.set_time(0.0, t_end)
+    for _ in range(nsteps):
+        ctx.step(wd, 0.1)
+    assert ctx.time() == pytest.approx(t_end, rel=1e-13)
+    assert state_error(wd.cpu().numpy(), ref).max() < 1e-11
+
+
+def test_run_host_matches_device_steps(orc):
+    ctx, ocfg = both(orc, 2, 2, (16, 16), precision=1)
+    mesh, w = mesh_and_field(orc, 2, 2, (5, 6), seed=5, kind="smooth")
+    upload(ctx, orc, mesh)
+    out = np.zeros_like(w)
+    ctx.set_time(0.0)
+    ctx.run_host(w, out, 3, 0.1)
+    wd = to_dev(w)
+    ctx.set_time(0.0)
+    for _ in range(3):
+        ctx.step(wd, 0.1)
+    np.testing.assert_array_equal(out, wd.cpu().numpy())
+
+
+def test_empty_mesh_and_single_periodic_element(orc):
+    ctx, ocfg = both(orc, 2, 3, (16, 16))
+    ctx.mesh_upload(np.zeros((0, 4), np.int32), np.zeros((0, 2)), None)
+    e = zeros_dev(0)
+    ctx.traces(e, e)
+    ctx.bounds(e, e, e)
+    ctx.step(e, 0.1)
+    ctx.check()
+    from paper_2407_20966_gb300 import inputs
+    mesh = inputs.mesh_2d(1, 1, 0, 1, 0, 1, periodic=(True, True))
+    om = upload(ctx, orc, mesh)
+    xi, _ = orc.gauss_legendre(4)
+    rng = np.random.default_rng(0)
+    base = inputs.random_states(rng, 1, 2)[0]
+    w = np.ascontiguousarray(base[:, None, None] * (1 + 0.05 * rng.uniform(-1, 1, (4, 1, 16))))
+    wf = orc.traces(ocfg, om, w)
+    ref = orc.bounds(ocfg, om, w, wf)
+    bnd = zeros_dev(2, 4, 1)
+    ctx.bounds(to_dev(w), to_dev(wf), bnd)
+    assert bounds_error(bnd.cpu().numpy(), ref).max() < TOL_FP64
+
+
+def test_nonphysical_state_is_reported(orc):
+    from paper_2407_20966_gb300 import kbl
+    ctx, ocfg = both(orc, 2, 2, (16, 16))
+    mesh, w = mesh_and_field(orc, 2, 2, (4, 4), seed=7, kind="smooth")
+    upload(ctx, orc, mesh)
+    w[3, 5, 2] = -1.0      # negative energy -> negative pressure at one node of element 5
+    wd = to_dev(w)
+    wf = zeros_dev(4, mesh.n_elem, 12)
+    ctx.traces(wd, wf)
+    bnd = zeros_dev(2, 4, mesh.n_elem)
+    ctx.bounds(wd, wf, bnd)
+    with pytest.raises(kbl.KblError) as ei:
+        ctx.check()
+    assert ei.value.status == kbl.ENONPHYSICAL
+    b = bnd.cpu().numpy()
+    assert np.isnan(b[:, :, 5]).all()
+    ctx.check()   # flags were cleared
+
+
+def test_bad_arguments_rejected(orc):
+    from paper_2407_20966_gb300 import kbl
+    ctx, _ = both(orc, 2, 3, (16, 16))
+    with pytest.raises(kbl.KblError):
+        ctx.traces(zeros_dev(1), zeros_dev(1))          # no mesh yet
+    with pytest.raises(kbl.KblError):
+        ctx.mesh_upload(np.array([[5, 0, 0, 0]]), np.ones((1, 2)), None)   # neighbour out of range
+    with pytest.raises(kbl.KblError):
+        ctx.mesh_upload(np.array([[-3, 0, 0, 0]]), np.ones((1, 2)), np.ones((1, 4)))  # bad bc id
