@@ -177,6 +177,35 @@ kbl_status kbl_read_counters(kbl_ctx* ctx, kbl_counters* out);
  * the kernels inside them). */
 int64_t kbl_launch_count(const kbl_ctx* ctx);
 
+/* Element bounds without any device allocation.  The paper has no
+ * counterpart to this call; it exists for callers that cannot call
+ * cudaMalloc: applications that hand all device memory to their own pool at
+ * start-up and forbid side allocations, and time-critical loops that cannot
+ * afford the implicit device synchronisation of cudaMalloc / cudaFree.  A
+ * context (kbl_create, kbl_mesh_upload) allocates, so this call takes no
+ * context: the caller passes the configuration (host struct) and every array
+ * on the device -- nbr_dev[E][2d] (int32, the layout of kbl_mesh_upload, which
+ * this call does not validate: out-of-range entries are undefined behaviour),
+ * bc_dev[n_bc][nv], the solution w_dev[nv][E][Ns] and the output
+ * bnd_dev[2][nv][E] -- and the stream.  The result equals kbl_traces followed by
+ * kbl_bounds of a context with the same configuration and mesh (the same
+ * kernels run).  The face traces needed as scratch live in one file-scope
+ * device array of 2^20 doubles (8 MiB) that every GPU loading the library
+ * keeps until the process exits, so n_elem * (d+2) * Nfp must not exceed
+ * 1048576 (16384 two-dimensional P3 elements); larger meshes, like bad
+ * configurations, return KBL_EINVAL before anything is launched.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.  Asynchronous;
+ * a non-physical stencil state gives NaN bounds for its element.  The first
+ * call on each device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array, which
+ * keeps the last call's contents: calls that overlap on the GPU (different
+ * streams, or host threads on the same device) race on it and must be
+ * serialised by the caller. */
+kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, const int32_t* nbr_dev,
+                              int n_bc, const double* bc_dev, const double* w_dev,
+                              double* bnd_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

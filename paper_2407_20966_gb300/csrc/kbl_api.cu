@@ -193,6 +193,8 @@ int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s)
 
 }  // namespace
 
+void kbl_build_fr_ops(int p, FrOps& o) { build_ops(p, o); }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -78,6 +78,9 @@ struct kbl_ctx {
 
 MeshDev mesh_of(const kbl_ctx* c);
 
+// FR operators of order p (host, FP64); defined in kbl_api.cu.
+void kbl_build_fr_ops(int p, FrOps& o);
+
 // ---- launchers (kbl_fr.cu, kbl_bounds.cu, kbl_limit.cu) ------------------
 // Each returns the number of kernels it launched, or -1 if the (dim, p)
 // combination is not compiled in.

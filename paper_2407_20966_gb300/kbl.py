@@ -73,6 +73,7 @@ _SIGS = {
     "kbl_check": (C.c_int, [_P]),
     "kbl_read_counters": (C.c_int, [_P, C.POINTER(KblCounters)]),
     "kbl_launch_count": (C.c_int64, [_P]),
+    "kbl_bounds_noalloc": (C.c_int, [C.POINTER(KblConfig), C.c_int, _P, C.c_int, _P, _P, _P, _P]),
 }
 
 
@@ -241,3 +242,26 @@ class Context:
 
     def launch_count(self):
         return int(self._lib.kbl_launch_count(self._h))
+
+
+def _dev_any(t, dtype_name, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    if str(t.dtype) != dtype_name:
+        raise TypeError(f"{name} must be {dtype_name}")
+    return C.c_void_p(t.data_ptr())
+
+
+def bounds_noalloc(cfg: KblConfig, nbr, bc, w, bnd, stream=None):
+    """Element bounds with no device allocation (kbl_bounds_noalloc): nbr int32 [E][2d],
+    bc float64 [n_bc][nv], w float64 [nv][E][Ns] and bnd float64 [2][nv][E], all CUDA tensors."""
+    lib = load()
+    E = int(nbr.shape[0])
+    n_bc = int(bc.shape[0]) if bc is not None and bc.numel() else 0
+    pb = _dev_any(bc, "torch.float64", "bc") if n_bc else None
+    st = lib.kbl_bounds_noalloc(C.byref(cfg), E, _dev_any(nbr, "torch.int32", "nbr"), n_bc, pb,
+                                _dev_any(w, "torch.float64", "w"), _dev_any(bnd, "torch.float64", "bnd"),
+                                stream if stream is not None else _current_stream())
+    if st != OK:
+        raise KblError(st, "bounds_noalloc")
