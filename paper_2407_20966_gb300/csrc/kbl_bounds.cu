@@ -29,9 +29,10 @@
 // FP64 kernels: the min/max run on the integer pipe as unsigned 64-bit
 // compares of the bit patterns (all values are >= +0, where integer order is
 // value order), because the GB300 FP64 pipe is ~1/76 of FP32.
-// FP32 kernels: primitive states, box and grid in FP64; velocities are taken
-// relative to the box centre before rounding to FP32; pairs of states share
-// one packed multiply (__fmul2_rn) and one three-input min/max; per-block
+// FP32 kernels: FP64 only for X = rho E - |m|^2/2 (rho P / (gamma-1)) with its
+// positivity test and for assembling the final bounds; velocities are taken
+// relative to the box centre inside the exponentials; pairs of states share
+// one packed multiply (__fmul2_rn) and one three-input min/max; per-warp
 // partial sums are combined with error-free (TwoSum) compensation.
 #include <cfloat>
 
@@ -354,7 +355,11 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
 }
 
 // ---------------------------------------------------------------------------
-// 2D, FP32 envelopes and sums (FP64 primitives, box, grid and finalisation)
+// 2D, FP32 envelopes and sums.  FP64 is used only where the path needs it:
+// X = rho E - |m|^2 / 2 (= rho P / (gamma - 1), the cancellation-prone,
+// positivity-deciding quantity) and its sign test, and the final assembly of
+// the bounds.  Everything else per state (U, theta, A, C, the box) is FP32,
+// because the GB300 FP64 pipe runs at ~1/76 of the FP32 rate.
 // ---------------------------------------------------------------------------
 template <int NX>
 struct B2f32 {
@@ -369,32 +374,101 @@ struct StateF {
     float A, C;
 };
 
+// Compensated per-warp partial sums of K floats -> sred[wid][0..K) hi, [K..2K) lo.
+template <int K>
+__device__ __forceinline__ void warp_sum_f32c(const float (&a)[K], float* sred)
+{
+    float hi[K], lo[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        hi[k] = a[k];
+        lo[k] = 0.0f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi[k], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo[k], o);
+            float sh, e;
+            two_sum(hi[k], oh, sh, e);
+            hi[k] = sh;
+            lo[k] = __fadd_rn(__fadd_rn(lo[k], ol), e);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            sred[wid * 2 * K + k] = hi[k];
+            sred[wid * 2 * K + K + k] = lo[k];
+        }
+    }
+}
+
 template <int N, int NX>
 __global__ void __launch_bounds__(B2f32<NX>::NT)
 k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
                double* __restrict__ bnd, DevFlags* flags)
 {
     constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP, NV = 4;
-    constexpr int NSTP = (NST + 1) & ~1;         // padded to pairs
+    constexpr int NSTP = (NST + 1) & ~1;         // padded to pairs (the last state repeated)
+    constexpr int NPAIR = NSTP / 2;
     constexpr int TX = B2f32<NX>::TX, TPA = B2f32<NX>::TPA, NT = B2f32<NX>::NT;
     constexpr int NW = (NT + 31) / 32;
-    constexpr int CP = CH / 2;                   // pairs per chunk
+    constexpr int K = 12;
     __shared__ double sS[NST][NV];
-    __shared__ StatePrim sP[NST];
     __shared__ StateF sF[NSTP];
-    __shared__ __align__(16) float2 sEx[CP][NX], sExc[CP][NX], sEy[CP][NX];
+    __shared__ __align__(16) float2 sEx[NPAIR][NX], sExc[NPAIR][NX], sEy[NPAIR][NX];
     __shared__ float srx[NX], sry[NX];          // grid relative to the box centre
     __shared__ float sux[NX], suy[NX], sqx[NX], sqy[NX], skx[NX], sky[NX];
-    __shared__ double sbox[4];
+    __shared__ float sbox[NW][4];
     __shared__ int sbad;
-    __shared__ float sred[NW * 24];
+    __shared__ float sred[NW * 2 * K];
+    __shared__ double sfin[K];
 
-    const int e = blockIdx.x, tid = threadIdx.x;
+    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) sbad = 0;
     gather_states<2, N, NT>(w, wf, m, e, sS);
     __syncthreads();
-    for (int i = tid; i < NST; i += NT)
-        if (!prim_of<2>(sS[i], ph, sP[i])) atomicOr(&sbad, 1);
+
+    // 1. primitive state of each stencil node, box candidates
+    const float gm1 = (float)(ph.gamma - 1.0), kk = (float)ph.k;
+    const float half_delta = 0.5f * (float)(2.0 / (ph.gamma - 1.0) - 2.0);
+    float blx = FLT_MAX, bly = FLT_MAX, bhx = -FLT_MAX, bhy = -FLT_MAX;
+    int bad = 0;
+    for (int i = tid; i < NSTP; i += NT) {
+        const double* q = sS[i < NST ? i : NST - 1];
+        const double X = fma(q[3], q[0], -0.5 * fma(q[2], q[2], q[1] * q[1]));
+        if (!(q[0] > 0.0) || !(X > 0.0)) bad = 1;
+        const float r = (float)q[0], inv = 1.0f / r;
+        const float ux = (float)q[1] * inv, uy = (float)q[2] * inv;
+        const float th = gm1 * ((float)X * inv) * inv;
+        const float sq = sqrtf(th);
+        StateF f;
+        f.Ux = ux;
+        f.Uy = uy;
+        f.kx = (0.5f * LOG2E) / th;
+        f.A = r / (6.283185307179586f * th);
+        f.C = half_delta * th;
+        sF[i] = f;
+        blx = fminf(blx, ux - kk * sq);
+        bhx = fmaxf(bhx, ux + kk * sq);
+        bly = fminf(bly, uy - kk * sq);
+        bhy = fmaxf(bhy, uy + kk * sq);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        blx = fminf(blx, __shfl_xor_sync(0xffffffffu, blx, o));
+        bhx = fmaxf(bhx, __shfl_xor_sync(0xffffffffu, bhx, o));
+        bly = fminf(bly, __shfl_xor_sync(0xffffffffu, bly, o));
+        bhy = fmaxf(bhy, __shfl_xor_sync(0xffffffffu, bhy, o));
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        sbox[wid][0] = blx; sbox[wid][1] = bhx; sbox[wid][2] = bly; sbox[wid][3] = bhy;
+        if (bad) atomicOr(&sbad, 1);
+    }
     __syncthreads();
     if (sbad) {
         if (tid == 0) {
@@ -403,36 +477,44 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
         }
         return;
     }
-    if (tid < 4) {
-        const int d = tid >> 1, up = tid & 1;
-        double b = up ? sP[0].U[d] + ph.k * sP[0].sq : sP[0].U[d] - ph.k * sP[0].sq;
-        for (int i = 1; i < NST; i++) {
-            const double c = up ? sP[i].U[d] + ph.k * sP[i].sq : sP[i].U[d] - ph.k * sP[i].sq;
-            b = up ? fmax(b, c) : fmin(b, c);
-        }
-        sbox[tid] = b;
+    float lox = sbox[0][0], hix = sbox[0][1], loy = sbox[0][2], hiy = sbox[0][3];
+#pragma unroll
+    for (int q = 1; q < NW; q++) {
+        lox = fminf(lox, sbox[q][0]); hix = fmaxf(hix, sbox[q][1]);
+        loy = fminf(loy, sbox[q][2]); hiy = fmaxf(hiy, sbox[q][3]);
+    }
+    const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy);
+    const float hx = (hix - lox) / (float)(NX - 1), hy = (hiy - loy) / (float)(NX - 1);
+
+    // 2. grid (relative to the centre for the Maxwellians, absolute for the moments)
+    for (int j = tid; j < NX; j += NT) {
+        const float t = (float)j - 0.5f * (float)(NX - 1);
+        const float q = (j == 0 || j == NX - 1) ? 0.5f : 1.0f;
+        const float rx = t * hx, ry = t * hy;
+        const float ux = cx + rx, uy = cy + ry;
+        srx[j] = rx; sry[j] = ry;
+        sux[j] = ux; suy[j] = uy;
+        sqx[j] = q; sqy[j] = q;
+        skx[j] = 0.5f * ux * ux; sky[j] = 0.5f * uy * uy;
     }
     __syncthreads();
-    const double cx = 0.5 * (sbox[0] + sbox[1]), cy = 0.5 * (sbox[2] + sbox[3]);
-    const double hx = (sbox[1] - sbox[0]) / (NX - 1), hy = (sbox[3] - sbox[2]) / (NX - 1);
-    for (int j = tid; j < 2 * NX; j += NT) {
-        const int d = j / NX, jj = j % NX;
-        const double lo = sbox[2 * d], h = d ? hy : hx, c = d ? cy : cx;
-        const double u = lo + jj * h;
-        const float q = (jj == 0 || jj == NX - 1) ? 0.5f : 1.0f;
-        if (d == 0) { sux[jj] = (float)u; srx[jj] = (float)(u - c); sqx[jj] = q; skx[jj] = (float)(0.5 * u * u); }
-        else { suy[jj] = (float)u; sry[jj] = (float)(u - c); sqy[jj] = q; sky[jj] = (float)(0.5 * u * u); }
+    // 3. row tables of every state: Ex = A exp2(-(ux-Ux)^2 kx), C Ex, Ey = exp2(-(uy-Uy)^2 kx)
+    for (int idx = tid; idx < NSTP * NX; idx += NT) {
+        const int i = idx / NX, j = idx % NX;
+        const StateF s = sF[i];
+        const float dx = srx[j] - (s.Ux - cx), dy = sry[j] - (s.Uy - cy);
+        const float ex = s.A * fast_exp2(-(dx * dx) * s.kx);
+        const float ey = fast_exp2(-(dy * dy) * s.kx);
+        float* px = reinterpret_cast<float*>(&sEx[i >> 1][j]);
+        float* pc = reinterpret_cast<float*>(&sExc[i >> 1][j]);
+        float* py = reinterpret_cast<float*>(&sEy[i >> 1][j]);
+        px[i & 1] = ex;
+        pc[i & 1] = s.C * ex;
+        py[i & 1] = ey;
     }
-    for (int i = tid; i < NSTP; i += NT) {
-        const StatePrim& s = sP[i < NST ? i : NST - 1];   // odd count: repeat the last state
-        StateF f;
-        f.Ux = (float)(s.U[0] - cx);
-        f.Uy = (float)(s.U[1] - cy);
-        f.kx = (float)(1.4426950408889634 / (2.0 * s.th));
-        f.A = (float)s.A;
-        f.C = (float)s.C;
-        sF[i] = f;
-    }
+    __syncthreads();
+    // 4. envelopes on this thread's TX x TX tile: packed products of a pair of states,
+    //    three-input min/max
     const int tx = tid % TPA, ty = tid / TPA;
     float tlo[TX][TX], thi[TX][TX], ilo[TX][TX], ihi[TX][TX];
 #pragma unroll
@@ -442,49 +524,31 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
             tlo[a][b] = FLT_MAX; ilo[a][b] = FLT_MAX;
             thi[a][b] = 0.0f; ihi[a][b] = 0.0f;
         }
-    for (int c0 = 0; c0 < NSTP; c0 += CH) {
-        const int nc = min(CH, NSTP - c0);      // even
-        __syncthreads();
-        for (int idx = tid; idx < nc * NX; idx += NT) {
-            const int i = idx / NX, j = idx % NX;
-            const StateF s = sF[c0 + i];
-            const float dx = srx[j] - s.Ux, dy = sry[j] - s.Uy;
-            const float ex = s.A * fast_exp2(-(dx * dx) * s.kx);
-            const float ey = fast_exp2(-(dy * dy) * s.kx);
-            float* px = reinterpret_cast<float*>(&sEx[i >> 1][j]);
-            float* pc = reinterpret_cast<float*>(&sExc[i >> 1][j]);
-            float* py = reinterpret_cast<float*>(&sEy[i >> 1][j]);
-            px[i & 1] = ex;
-            pc[i & 1] = s.C * ex;
-            py[i & 1] = ey;
-        }
-        __syncthreads();
-        const int np = nc >> 1;
-        for (int pi = 0; pi < np; pi++) {
-            float2 ex[TX], exc[TX], ey[TX];
+#pragma unroll 2
+    for (int pi = 0; pi < NPAIR; pi++) {
+        float2 ex[TX], exc[TX], ey[TX];
 #pragma unroll
-            for (int a = 0; a < TX; a++) {
-                ex[a] = sEx[pi][tx * TX + a];
-                exc[a] = sExc[pi][tx * TX + a];
-                ey[a] = sEy[pi][ty * TX + a];
+        for (int a = 0; a < TX; a++) {
+            ex[a] = sEx[pi][tx * TX + a];
+            exc[a] = sExc[pi][tx * TX + a];
+            ey[a] = sEy[pi][ty * TX + a];
+        }
+#pragma unroll
+        for (int a = 0; a < TX; a++)
+#pragma unroll
+            for (int b = 0; b < TX; b++) {
+                const float2 g = __fmul2_rn(ex[a], ey[b]);
+                const float2 cg = __fmul2_rn(exc[a], ey[b]);
+                tlo[a][b] = fmin3(tlo[a][b], g.x, g.y);
+                thi[a][b] = fmax3(thi[a][b], g.x, g.y);
+                ilo[a][b] = fmin3(ilo[a][b], cg.x, cg.y);
+                ihi[a][b] = fmax3(ihi[a][b], cg.x, cg.y);
             }
-#pragma unroll
-            for (int a = 0; a < TX; a++)
-#pragma unroll
-                for (int b = 0; b < TX; b++) {
-                    const float2 g = __fmul2_rn(ex[a], ey[b]);
-                    const float2 cg = __fmul2_rn(exc[a], ey[b]);
-                    tlo[a][b] = fmin3(tlo[a][b], g.x, g.y);
-                    thi[a][b] = fmax3(thi[a][b], g.x, g.y);
-                    ilo[a][b] = fmin3(ilo[a][b], cg.x, cg.y);
-                    ihi[a][b] = fmax3(ihi[a][b], cg.x, cg.y);
-                }
-        }
     }
-    // per-thread sums with weights q (1 or 1/2); the factor hx*hy is applied in FP64
-    float acc[12];
+    // 5. moments with weights q (1 or 1/2); hx * hy and the relaxation are applied in FP64
+    float acc[K];
 #pragma unroll
-    for (int k = 0; k < 12; k++) acc[k] = 0.0f;
+    for (int k = 0; k < K; k++) acc[k] = 0.0f;
 #pragma unroll
     for (int a = 0; a < TX; a++)
 #pragma unroll
@@ -504,9 +568,37 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
             acc[10] += Tl * ke + Il;
             acc[11] += Th * ke + Ih;
         }
-    double tot[12];
-    block_sum_f32c<12, NT>(acc, tot, sred);
-    if (tid == 0) finalize_bounds<2>(tot, hx * hy, ph, bnd, m.E, e);
+    warp_sum_f32c<K>(acc, sred);
+    __syncthreads();
+    // 6. assemble the bounds in FP64, one raw sum per lane
+    if (tid < K) {
+        float hi = sred[tid], lo = sred[K + tid];
+#pragma unroll
+        for (int q = 1; q < NW; q++) {
+            float s2, e2;
+            two_sum(hi, sred[q * 2 * K + tid], s2, e2);
+            hi = s2;
+            lo = lo + sred[q * 2 * K + K + tid] + e2;
+        }
+        // raw index -> relaxation sign: lower-bound terms take (1 - r), upper (1 + r)
+        // [Tlo, Thi, nx_hi, nx_lo, px_lo, px_hi, ny_hi, ny_lo, py_lo, py_hi, E_lo, E_hi]
+        const bool upper_env = (tid == 1) || (tid == 2) || (tid == 5) || (tid == 6) || (tid == 9) || (tid == 11);
+        const double rel = upper_env ? 1.0 + ph.r_fac : 1.0 - ph.r_fac;
+        sfin[tid] = rel * (((double)hx * (double)hy) * ((double)hi + (double)lo));
+    }
+    __syncthreads();
+    if (tid < 2 * NV) {
+        const int v = tid % NV, up = tid / NV;
+        double val;
+        if (v == 0) val = up ? sfin[1] : sfin[0];
+        else if (v == NV - 1) val = up ? sfin[11] : sfin[10];
+        else {
+            const int b0 = 2 + 4 * (v - 1);
+            val = up ? sfin[b0 + 1] + sfin[b0 + 3] : sfin[b0 + 0] + sfin[b0 + 2];
+        }
+        if (v == 0 && !up && val < ph.rho_floor) val = ph.rho_floor;
+        bnd[((size_t)up * NV + v) * m.E + e] = val;
+    }
 }
 
 // ---------------------------------------------------------------------------
