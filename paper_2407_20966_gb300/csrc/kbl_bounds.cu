@@ -38,6 +38,10 @@
 
 #include "kbl_internal.cuh"
 
+#ifndef KBL_BOUNDS_MINB
+#define KBL_BOUNDS_MINB 10
+#endif
+
 namespace {
 
 constexpr int CH = 16;  // states per table chunk
@@ -366,65 +370,80 @@ struct B2f32 {
     static constexpr int TX = (NX >= 32) ? 4 : (NX >= 16 ? 2 : 1);
     static constexpr int TPA = NX / TX;
     static constexpr int NT = TPA * TPA;
+    static constexpr int MINB = NT == 64 ? KBL_BOUNDS_MINB : 1;   // resident blocks per SM to aim for
+    // table position of grid index j: with 4 nodes per thread the two float2
+    // halves of a thread's tile are stored NX/2 apart, so the 16-byte loads of
+    // the threads of a warp are contiguous (no shared-memory bank conflicts)
+    __host__ __device__ static constexpr int pos(int j)
+    {
+        return TX == 4 ? ((j & 3) >> 1) * (NX / 2) + (j >> 2) * 2 + (j & 1) : j;
+    }
 };
 
-struct StateF {
-    float Ux, Uy;   // velocity relative to the box centre
-    float kx;       // log2(e) / (2 theta)
-    float A, C;
-};
-
-// Compensated per-warp partial sums of K floats -> sred[wid][0..K) hi, [K..2K) lo.
-template <int K>
-__device__ __forceinline__ void warp_sum_f32c(const float (&a)[K], float* sred)
+// Compensated warp reduce-scatter of 16 values: afterwards lane L (even) holds
+// sum over the warp of value L / 2 as hi + lo.  16 exchanges instead of 16 x 5.
+__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], float& out_hi, float& out_lo)
 {
-    float hi[K], lo[K];
+    const int lane = threadIdx.x & 31;
+    float hi[8], lo[8];
+    {   // offset 16: keep the upper 8 values on lanes with bit 4 set
+        const bool up = lane & 16;
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        hi[k] = a[k];
-        lo[k] = 0.0f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const float oh = __shfl_xor_sync(0xffffffffu, hi[k], o);
-            const float ol = __shfl_xor_sync(0xffffffffu, lo[k], o);
-            float sh, e;
-            two_sum(hi[k], oh, sh, e);
-            hi[k] = sh;
-            lo[k] = __fadd_rn(__fadd_rn(lo[k], ol), e);
+        for (int k = 0; k < 8; k++) {
+            const float keep = up ? v[8 + k] : v[k];
+            const float send = up ? v[k] : v[8 + k];
+            const float o = __shfl_xor_sync(0xffffffffu, send, 16);
+            two_sum(keep, o, hi[k], lo[k]);
         }
     }
-    if ((threadIdx.x & 31) == 0) {
-        const int wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            sred[wid * 2 * K + k] = hi[k];
-            sred[wid * 2 * K + K + k] = lo[k];
+    for (int step = 0; step < 3; step++) {   // offsets 8, 4, 2
+        const int off = 8 >> step;
+        const int n = 4 >> step;              // values kept after this step
+        const bool up = lane & off;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (k >= n) break;
+            const float kh = up ? hi[n + k] : hi[k], sh = up ? hi[k] : hi[n + k];
+            const float kl = up ? lo[n + k] : lo[k], sl = up ? lo[k] : lo[n + k];
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, off);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl, off);
+            float s2, e2;
+            two_sum(kh, oh, s2, e2);
+            hi[k] = s2;
+            lo[k] = kl + ol + e2;
         }
     }
+    const float oh = __shfl_xor_sync(0xffffffffu, hi[0], 1);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo[0], 1);
+    float s2, e2;
+    two_sum(hi[0], oh, s2, e2);
+    out_hi = s2;
+    out_lo = lo[0] + ol + e2;
 }
 
 template <int N, int NX>
-__global__ void __launch_bounds__(B2f32<NX>::NT)
+__global__ void __launch_bounds__(B2f32<NX>::NT, B2f32<NX>::MINB)
 k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
                double* __restrict__ bnd, DevFlags* flags)
 {
+    using SH = B2f32<NX>;
     constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP, NV = 4;
     constexpr int NSTP = (NST + 1) & ~1;         // padded to pairs (the last state repeated)
     constexpr int NPAIR = NSTP / 2;
-    constexpr int TX = B2f32<NX>::TX, TPA = B2f32<NX>::TPA, NT = B2f32<NX>::NT;
+    constexpr int TX = SH::TX, TPA = SH::TPA, NT = SH::NT;
     constexpr int NW = (NT + 31) / 32;
     constexpr int K = 12;
     __shared__ double sS[NST][NV];
-    __shared__ StateF sF[NSTP];
+    // per state (SoA, so that a pair of states is one 8-byte load): velocity, -log2(e)/(2 theta), A, C
+    __shared__ __align__(8) float sUx[NSTP], sUy[NSTP], sKx[NSTP], sA[NSTP], sC[NSTP];
     __shared__ __align__(16) float2 sEx[NPAIR][NX], sExc[NPAIR][NX], sEy[NPAIR][NX];
     __shared__ float srx[NX], sry[NX];          // grid relative to the box centre
-    __shared__ float sux[NX], suy[NX], sqx[NX], sqy[NX], skx[NX], sky[NX];
+    // per-node moment coefficients: x: q, q u, 1/2 u^2 ; y: q, q 1/2 u^2, q u (u<0), q u (u>=0)
+    __shared__ float sqx[NX], squx[NX], skx[NX], sqy[NX], sqky[NX], squyn[NX], squyp[NX];
     __shared__ float sbox[NW][4];
     __shared__ int sbad;
-    __shared__ float sred[NW * 2 * K];
+    __shared__ float sred[NW][16][2];
     __shared__ double sfin[K];
 
     const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -445,13 +464,11 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
         const float ux = (float)q[1] * inv, uy = (float)q[2] * inv;
         const float th = gm1 * ((float)X * inv) * inv;
         const float sq = sqrtf(th);
-        StateF f;
-        f.Ux = ux;
-        f.Uy = uy;
-        f.kx = (0.5f * LOG2E) / th;
-        f.A = r / (6.283185307179586f * th);
-        f.C = half_delta * th;
-        sF[i] = f;
+        sUx[i] = ux;
+        sUy[i] = uy;
+        sKx[i] = -(0.5f * LOG2E) / th;
+        sA[i] = r / (6.283185307179586f * th);
+        sC[i] = half_delta * th;
         blx = fminf(blx, ux - kk * sq);
         bhx = fmaxf(bhx, ux + kk * sq);
         bly = fminf(bly, uy - kk * sq);
@@ -486,31 +503,51 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
     const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy);
     const float hx = (hix - lox) / (float)(NX - 1), hy = (hiy - loy) / (float)(NX - 1);
 
-    // 2. grid (relative to the centre for the Maxwellians, absolute for the moments)
+    // 2. state velocities and grid relative to the box centre (for the Maxwellians,
+    //    which keeps FP32 differences small), absolute grid for the moments
+    for (int i = tid; i < NSTP; i += NT) {
+        sUx[i] -= cx;
+        sUy[i] -= cy;
+    }
     for (int j = tid; j < NX; j += NT) {
         const float t = (float)j - 0.5f * (float)(NX - 1);
         const float q = (j == 0 || j == NX - 1) ? 0.5f : 1.0f;
         const float rx = t * hx, ry = t * hy;
         const float ux = cx + rx, uy = cy + ry;
-        srx[j] = rx; sry[j] = ry;
-        sux[j] = ux; suy[j] = uy;
-        sqx[j] = q; sqy[j] = q;
-        skx[j] = 0.5f * ux * ux; sky[j] = 0.5f * uy * uy;
+        srx[j] = rx;
+        sry[j] = ry;
+        sqx[j] = q;
+        squx[j] = q * ux;
+        skx[j] = 0.5f * ux * ux;
+        sqy[j] = q;
+        sqky[j] = q * (0.5f * uy * uy);
+        squyn[j] = uy < 0.0f ? q * uy : 0.0f;
+        squyp[j] = uy < 0.0f ? 0.0f : q * uy;
     }
     __syncthreads();
-    // 3. row tables of every state: Ex = A exp2(-(ux-Ux)^2 kx), C Ex, Ey = exp2(-(uy-Uy)^2 kx)
-    for (int idx = tid; idx < NSTP * NX; idx += NT) {
-        const int i = idx / NX, j = idx % NX;
-        const StateF s = sF[i];
-        const float dx = srx[j] - (s.Ux - cx), dy = sry[j] - (s.Uy - cy);
-        const float ex = s.A * fast_exp2(-(dx * dx) * s.kx);
-        const float ey = fast_exp2(-(dy * dy) * s.kx);
-        float* px = reinterpret_cast<float*>(&sEx[i >> 1][j]);
-        float* pc = reinterpret_cast<float*>(&sExc[i >> 1][j]);
-        float* py = reinterpret_cast<float*>(&sEy[i >> 1][j]);
-        px[i & 1] = ex;
-        pc[i & 1] = s.C * ex;
-        py[i & 1] = ey;
+    // 3. row tables of every state, two states per packed instruction:
+    //    Ex = A exp2(-(ux-Ux)^2 kx), C Ex, Ey = exp2(-(uy-Uy)^2 kx)
+    {
+        constexpr int ROWS = NT / NX > 0 ? NT / NX : 1;
+        const int j = tid % NX;
+        const int pj = SH::pos(j);
+        const float2 rx = make_float2(srx[j], srx[j]);
+        const float2 ry = make_float2(sry[j], sry[j]);
+        for (int pr = tid / NX; pr < NPAIR; pr += ROWS) {
+            const float2 ux = reinterpret_cast<const float2*>(sUx)[pr];
+            const float2 uy = reinterpret_cast<const float2*>(sUy)[pr];
+            const float2 kx = reinterpret_cast<const float2*>(sKx)[pr];
+            const float2 A = reinterpret_cast<const float2*>(sA)[pr];
+            const float2 C = reinterpret_cast<const float2*>(sC)[pr];
+            const float2 dx = __fadd2_rn(rx, make_float2(-ux.x, -ux.y));
+            const float2 dy = __fadd2_rn(ry, make_float2(-uy.x, -uy.y));
+            const float2 ax = __fmul2_rn(__fmul2_rn(dx, dx), kx);
+            const float2 ay = __fmul2_rn(__fmul2_rn(dy, dy), kx);
+            const float2 ex = __fmul2_rn(make_float2(fast_exp2(ax.x), fast_exp2(ax.y)), A);
+            sEx[pr][pj] = ex;
+            sExc[pr][pj] = __fmul2_rn(ex, C);
+            sEy[pr][pj] = make_float2(fast_exp2(ay.x), fast_exp2(ay.y));
+        }
     }
     __syncthreads();
     // 4. envelopes on this thread's TX x TX tile: packed products of a pair of states,
@@ -529,9 +566,9 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
         float2 ex[TX], exc[TX], ey[TX];
 #pragma unroll
         for (int a = 0; a < TX; a++) {
-            ex[a] = sEx[pi][tx * TX + a];
-            exc[a] = sExc[pi][tx * TX + a];
-            ey[a] = sEy[pi][ty * TX + a];
+            ex[a] = sEx[pi][SH::pos(tx * TX + a)];
+            exc[a] = sExc[pi][SH::pos(tx * TX + a)];
+            ey[a] = sEy[pi][SH::pos(ty * TX + a)];
         }
 #pragma unroll
         for (int a = 0; a < TX; a++)
@@ -545,43 +582,67 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
                 ihi[a][b] = fmax3(ihi[a][b], cg.x, cg.y);
             }
     }
-    // 5. moments with weights q (1 or 1/2); hx * hy and the relaxation are applied in FP64
-    float acc[K];
+    // 5. moments: column sums over this thread's y nodes, then the x weights.
+    //    raw = [Tlo, Thi, nx_hi, nx_lo, px_lo, px_hi, ny_hi, ny_lo, py_lo, py_hi, E_lo, E_hi]
+    //    (n/p: u < 0 / u >= 0 part of the momentum sums; hx hy and the
+    //    relaxation are applied in FP64 at the end)
+    float acc[16];
 #pragma unroll
-    for (int k = 0; k < K; k++) acc[k] = 0.0f;
+    for (int k = 0; k < 16; k++) acc[k] = 0.0f;
 #pragma unroll
-    for (int a = 0; a < TX; a++)
+    for (int a = 0; a < TX; a++) {
+        float cTl = 0.f, cTh = 0.f, cIl = 0.f, cIh = 0.f, cKl = 0.f, cKh = 0.f;
+        float cNh = 0.f, cNl = 0.f, cPl = 0.f, cPh = 0.f;
 #pragma unroll
         for (int b = 0; b < TX; b++) {
-            const int jx = tx * TX + a, jy = ty * TX + b;
-            const float q = sqx[jx] * sqy[jy];
-            const float ux = sux[jx], uy = suy[jy];
-            const float Tl = q * tlo[a][b], Th = q * thi[a][b];
-            const float Il = q * ilo[a][b], Ih = q * ihi[a][b];
-            acc[0] += Tl;
-            acc[1] += Th;
-            if (ux < 0.0f) { acc[2] += Th * ux; acc[3] += Tl * ux; }
-            else { acc[4] += Tl * ux; acc[5] += Th * ux; }
-            if (uy < 0.0f) { acc[6] += Th * uy; acc[7] += Tl * uy; }
-            else { acc[8] += Tl * uy; acc[9] += Th * uy; }
-            const float ke = skx[jx] + sky[jy];
-            acc[10] += Tl * ke + Il;
-            acc[11] += Th * ke + Ih;
+            const int jy = ty * TX + b;
+            const float qy = sqy[jy], qk = sqky[jy], qn = squyn[jy], qp = squyp[jy];
+            const float Tl = tlo[a][b], Th = thi[a][b];
+            cTl = fmaf(qy, Tl, cTl);
+            cTh = fmaf(qy, Th, cTh);
+            cIl = fmaf(qy, ilo[a][b], cIl);
+            cIh = fmaf(qy, ihi[a][b], cIh);
+            cKl = fmaf(qk, Tl, cKl);
+            cKh = fmaf(qk, Th, cKh);
+            cNh = fmaf(qn, Th, cNh);
+            cNl = fmaf(qn, Tl, cNl);
+            cPl = fmaf(qp, Tl, cPl);
+            cPh = fmaf(qp, Th, cPh);
         }
-    warp_sum_f32c<K>(acc, sred);
+        const int jx = tx * TX + a;
+        const float qx = sqx[jx], qux = squx[jx], kx = skx[jx];
+        const float qn = squx[jx] < 0.0f ? qux : 0.0f, qp = squx[jx] < 0.0f ? 0.0f : qux;
+        acc[0] = fmaf(qx, cTl, acc[0]);
+        acc[1] = fmaf(qx, cTh, acc[1]);
+        acc[2] = fmaf(qn, cTh, acc[2]);
+        acc[3] = fmaf(qn, cTl, acc[3]);
+        acc[4] = fmaf(qp, cTl, acc[4]);
+        acc[5] = fmaf(qp, cTh, acc[5]);
+        acc[6] = fmaf(qx, cNh, acc[6]);
+        acc[7] = fmaf(qx, cNl, acc[7]);
+        acc[8] = fmaf(qx, cPl, acc[8]);
+        acc[9] = fmaf(qx, cPh, acc[9]);
+        acc[10] = fmaf(qx, fmaf(kx, cTl, cKl + cIl), acc[10]);
+        acc[11] = fmaf(qx, fmaf(kx, cTh, cKh + cIh), acc[11]);
+    }
+    float rh, rl;
+    warp_reduce_scatter16(acc, rh, rl);
+    if ((lane & 1) == 0 && (lane >> 1) < K) {
+        sred[wid][lane >> 1][0] = rh;
+        sred[wid][lane >> 1][1] = rl;
+    }
     __syncthreads();
     // 6. assemble the bounds in FP64, one raw sum per lane
     if (tid < K) {
-        float hi = sred[tid], lo = sred[K + tid];
+        float hi = sred[0][tid][0], lo = sred[0][tid][1];
 #pragma unroll
         for (int q = 1; q < NW; q++) {
             float s2, e2;
-            two_sum(hi, sred[q * 2 * K + tid], s2, e2);
+            two_sum(hi, sred[q][tid][0], s2, e2);
             hi = s2;
-            lo = lo + sred[q * 2 * K + K + tid] + e2;
+            lo = lo + sred[q][tid][1] + e2;
         }
-        // raw index -> relaxation sign: lower-bound terms take (1 - r), upper (1 + r)
-        // [Tlo, Thi, nx_hi, nx_lo, px_lo, px_hi, ny_hi, ny_lo, py_lo, py_hi, E_lo, E_hi]
+        // lower-bound terms take (1 - r), upper-bound terms (1 + r)
         const bool upper_env = (tid == 1) || (tid == 2) || (tid == 5) || (tid == 6) || (tid == 9) || (tid == 11);
         const double rel = upper_env ? 1.0 + ph.r_fac : 1.0 - ph.r_fac;
         sfin[tid] = rel * (((double)hx * (double)hy) * ((double)hi + (double)lo));

@@ -13,9 +13,11 @@ namespace {
 // ---------------------------------------------------------------------------
 // traces: wf[v][e][fp] = sum_i l_i(+-1) w[v][e][line(fp, i)]
 // One thread per (element, face point); the interpolation weights are uniform
-// across the warp, so they are read from the parameter block.
+// across the warp, so they are read from the parameter block.  T is the
+// arithmetic type (double for the FP64 path, float for the FP32-mixed path);
+// storage is FP64 in both.
 // ---------------------------------------------------------------------------
-template <int DIM, int N>
+template <int DIM, int N, typename T>
 __global__ void __launch_bounds__(256) k_traces(const double* __restrict__ w, double* __restrict__ wf,
                                                 int E, FrOps ops)
 {
@@ -30,14 +32,14 @@ __global__ void __launch_bounds__(256) k_traces(const double* __restrict__ w, do
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         const double* we = w + ((size_t)v * E + e) * NS;
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int i = 0; i < N; i++) {
-            const double l = plus ? ops.lp[i] : ops.lm[i];
+            const T l = (T)(plus ? ops.lp[i] : ops.lm[i]);
             const int nd = along_x ? k * N + i : i * N + k;
-            s += l * we[(DIM == 1) ? i : nd];
+            s += l * (T)we[(DIM == 1) ? i : nd];
         }
-        wf[((size_t)v * E + e) * NFP + fp] = s;
+        wf[((size_t)v * E + e) * NFP + fp] = (double)s;
     }
 }
 
@@ -47,7 +49,10 @@ int run_traces(const kbl_ctx* c, const double* w, double* wf, cudaStream_t s)
     const size_t total = (size_t)c->E * kbl_nfp<DIM>(N);
     if (total == 0) return 0;
     const int bs = 256;
-    k_traces<DIM, N><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(w, wf, c->E, c->ops);
+    const unsigned grid = (unsigned)((total + bs - 1) / bs);
+    // FP64 in both precision modes: converting each input to FP32 costs an FP64-pipe slot
+    // on GB300, as much as the FP64 multiply-add it would replace.
+    k_traces<DIM, N, double><<<grid, bs, 0, s>>>(w, wf, c->E, c->ops);
     return 1;
 }
 
@@ -98,37 +103,37 @@ struct RhsShape {
     static constexpr int NT = EPB * NS;
 };
 
-template <int DIM, int N>
+template <int DIM, int N, typename T>
 __global__ void __launch_bounds__(RhsShape<DIM, N>::NT)
 k_rhs(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, FrOps ops,
-      double gamma, double* __restrict__ R)
+      double gamma_d, double* __restrict__ R)
 {
     using SH = RhsShape<DIM, N>;
     constexpr int NS = SH::NS, NFP = SH::NFP, NV = SH::NV, EPB = SH::EPB, NT = SH::NT;
     constexpr int NFPF = (DIM == 1) ? 1 : N;
-    __shared__ double sF[EPB][DIM][NV][NS];
-    __shared__ double sJ[EPB][NFP][NV];
-    __shared__ double sD[N][N], sgl[N], sgr[N], slm[N], slp[N];
+    __shared__ T sF[EPB][DIM][NV][NS];
+    __shared__ T sJ[EPB][NFP][NV];
+    __shared__ T sD[N][N], sgl[N], sgr[N], slm[N], slp[N];
 
     const int tid = threadIdx.x;
-    for (int i = tid; i < N * N; i += NT) sD[i / N][i % N] = ops.D[i / N][i % N];
+    for (int i = tid; i < N * N; i += NT) sD[i / N][i % N] = (T)ops.D[i / N][i % N];
     if (tid < N) {
-        sgl[tid] = ops.gl[tid];
-        sgr[tid] = ops.gr[tid];
-        slm[tid] = ops.lm[tid];
-        slp[tid] = ops.lp[tid];
+        sgl[tid] = (T)ops.gl[tid];
+        sgr[tid] = (T)ops.gr[tid];
+        slm[tid] = (T)ops.lm[tid];
+        slp[tid] = (T)ops.lp[tid];
     }
     const int el = tid / NS, nd = tid % NS;
     const int e = blockIdx.x * EPB + el;
-    const double gm1 = gamma - 1.0;
+    const T gamma = (T)gamma_d, gm1 = (T)(gamma_d - 1.0);
     if (e < m.E) {
-        double q[NV];
+        T q[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) q[v] = w[((size_t)v * m.E + e) * NS + nd];
+        for (int v = 0; v < NV; v++) q[v] = (T)w[((size_t)v * m.E + e) * NS + nd];
 #pragma unroll
         for (int dir = 0; dir < DIM; dir++) {
-            double F[NV];
-            kbl_flux<DIM>(q, dir, gm1, F);
+            T F[NV];
+            kbl_flux<DIM, T>(q, dir, gm1, F);
 #pragma unroll
             for (int v = 0; v < NV; v++) sF[el][dir][v][nd] = F[v];
         }
@@ -139,18 +144,18 @@ k_rhs(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Fr
         const int ee = blockIdx.x * EPB + ell;
         if (ee >= m.E) continue;
         const int f = fp / NFPF, k = fp % NFPF, dir = f >> 1, side = f & 1;
-        double qi[NV], qe[NV], Fc[NV];
+        T qi[NV], qe[NV], Fc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            qi[v] = wf[((size_t)v * m.E + ee) * NFP + fp];
-            qe[v] = kbl_exterior<DIM, N>(wf, m, ee, fp, v);
+            qi[v] = (T)wf[((size_t)v * m.E + ee) * NFP + fp];
+            qe[v] = (T)kbl_exterior<DIM, N>(wf, m, ee, fp, v);
         }
-        if (side == 0) kbl_rusanov<DIM>(qe, qi, dir, gamma, Fc);
-        else kbl_rusanov<DIM>(qi, qe, dir, gamma, Fc);
-        const double* l = side ? slp : slm;
+        if (side == 0) kbl_rusanov<DIM, T>(qe, qi, dir, gamma, Fc);
+        else kbl_rusanov<DIM, T>(qi, qe, dir, gamma, Fc);
+        const T* l = side ? slp : slm;
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            double FD = 0.0;
+            T FD = T(0);
 #pragma unroll
             for (int i = 0; i < N; i++) {
                 const int node = (DIM == 1) ? i : (dir == 0 ? k * N + i : i * N + k);
@@ -163,23 +168,23 @@ k_rhs(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Fr
     if (e >= m.E) return;
     const int i = (DIM == 1) ? nd : nd % N;
     const int j = (DIM == 1) ? 0 : nd / N;
-    const double sx = 2.0 / m.h[e * DIM + 0];
-    const double sy = (DIM == 2) ? 2.0 / m.h[e * DIM + 1] : 0.0;
+    const T sx = (T)(2.0 / m.h[e * DIM + 0]);
+    const T sy = (DIM == 2) ? (T)(2.0 / m.h[e * DIM + 1]) : T(0);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-        double dx = 0.0;
+        T dx = T(0);
 #pragma unroll
         for (int mm = 0; mm < N; mm++) dx += sD[i][mm] * sF[el][0][v][(DIM == 1) ? mm : j * N + mm];
         dx += sgl[i] * sJ[el][0 * NFPF + j][v] + sgr[i] * sJ[el][1 * NFPF + j][v];
-        double r = -sx * dx;
+        T r = -sx * dx;
         if (DIM == 2) {
-            double dy = 0.0;
+            T dy = T(0);
 #pragma unroll
             for (int mm = 0; mm < N; mm++) dy += sD[j][mm] * sF[el][DIM - 1][v][mm * N + i];
             dy += sgl[j] * sJ[el][2 * NFPF + i][v] + sgr[j] * sJ[el][3 * NFPF + i][v];
             r -= sy * dy;
         }
-        R[((size_t)v * m.E + e) * NS + nd] = r;
+        R[((size_t)v * m.E + e) * NS + nd] = (double)r;
     }
 }
 
@@ -189,7 +194,10 @@ int run_rhs(const kbl_ctx* c, const double* w, const double* wf, double* R, cuda
     using SH = RhsShape<DIM, N>;
     if (c->E == 0) return 0;
     const unsigned grid = (unsigned)((c->E + SH::EPB - 1) / SH::EPB);
-    k_rhs<DIM, N><<<grid, SH::NT, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, R);
+    if (c->cfg.precision == KBL_FP32_MIXED)
+        k_rhs<DIM, N, float><<<grid, SH::NT, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, R);
+    else
+        k_rhs<DIM, N, double><<<grid, SH::NT, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, R);
     return 1;
 }
 
@@ -198,8 +206,8 @@ int run_rhs(const kbl_ctx* c, const double* w, const double* wf, double* R, cuda
 // bit pattern of a positive double (integer order = value order), then the
 // finalize kernel clips to the end time.
 // ---------------------------------------------------------------------------
-template <int DIM, int N>
-__global__ void __launch_bounds__(256) k_dt(const double* __restrict__ w, MeshDev m, double gamma,
+template <int DIM, int N, typename T>
+__global__ void __launch_bounds__(256) k_dt(const double* __restrict__ w, MeshDev m, double gamma_d,
                                             double cfl, unsigned long long* dtbits)
 {
     constexpr int NS = kbl_ns<DIM>(N), NV = DIM + 2;
@@ -207,24 +215,28 @@ __global__ void __launch_bounds__(256) k_dt(const double* __restrict__ w, MeshDe
     double best = DBL_MAX;
     if (t < (size_t)m.E * NS) {
         const int e = (int)(t / NS), nd = (int)(t % NS);
-        double q[NV];
+        const T gamma = (T)gamma_d;
+        T q[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) q[v] = w[((size_t)v * m.E + e) * NS + nd];
-        const double P = kbl_pressure<DIM>(q, gamma - 1.0);
-        const double a = sqrt(gamma * P / q[0]);
+        for (int v = 0; v < NV; v++) q[v] = (T)w[((size_t)v * m.E + e) * NS + nd];
+        const T P = kbl_pressure<DIM, T>(q, gamma - T(1));
+        const T a = sqrt(gamma * P / q[0]);
+        T b = (T)DBL_MAX;
+        if (sizeof(T) == sizeof(float)) b = (T)FLT_MAX;
 #pragma unroll
         for (int k = 0; k < DIM; k++) {
-            const double cand = cfl * (m.h[e * DIM + k] / (fabs(q[1 + k] / q[0]) + a));
-            best = fmin(best, cand);
+            const T cand = (T)cfl * ((T)m.h[e * DIM + k] / (fabs(q[1 + k] / q[0]) + a));
+            b = fmin(b, cand);
         }
+        best = (double)b;
     }
-    unsigned long long b = __double_as_longlong(best);
+    unsigned long long bits = __double_as_longlong(best);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
-        b = ob < b ? ob : b;
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = ob < bits ? ob : bits;
     }
-    if ((threadIdx.x & 31) == 0) atomicMin(dtbits, b);
+    if ((threadIdx.x & 31) == 0) atomicMin(dtbits, bits);
 }
 
 __global__ void k_dt_finalize(const unsigned long long* dtbits, const double* scal, double* dt_out,
@@ -246,8 +258,11 @@ int run_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int cl
     int n = 0;
     const size_t total = (size_t)c->E * kbl_ns<DIM>(N);
     if (total > 0) {
-        k_dt<DIM, N><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(w, mesh_of(c), c->phys.gamma, cfl,
-                                                                    c->d_dtbits);
+        const unsigned grid = (unsigned)((total + 255) / 256);
+        if (c->cfg.precision == KBL_FP32_MIXED)
+            k_dt<DIM, N, float><<<grid, 256, 0, s>>>(w, mesh_of(c), c->phys.gamma, cfl, c->d_dtbits);
+        else
+            k_dt<DIM, N, double><<<grid, 256, 0, s>>>(w, mesh_of(c), c->phys.gamma, cfl, c->d_dtbits);
         n++;
     }
     k_dt_finalize<<<1, 1, 0, s>>>(c->d_dtbits, c->d_scal, dt_out, clip);

@@ -101,42 +101,41 @@ int launch_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const 
 // ---- device helpers ----------------------------------------------------------
 #define KBL_PI 3.14159265358979323846
 
-template <int DIM>
-__device__ __forceinline__ double kbl_pressure(const double* q, double gm1)
+template <int DIM, typename T = double>
+__device__ __forceinline__ T kbl_pressure(const T* q, T gm1)
 {
-    double mm = q[1] * q[1];
+    T mm = q[1] * q[1];
     if (DIM == 2) mm += q[2] * q[2];
-    return gm1 * (q[DIM + 1] - 0.5 * mm / q[0]);
+    return gm1 * (q[DIM + 1] - T(0.5) * mm / q[0]);
 }
 
 // Flux along axis `dir` (Eq. 2).
-template <int DIM>
-__device__ __forceinline__ void kbl_flux(const double* q, int dir, double gm1, double* F)
+template <int DIM, typename T = double>
+__device__ __forceinline__ void kbl_flux(const T* q, int dir, T gm1, T* F)
 {
-    const double P = kbl_pressure<DIM>(q, gm1);
-    const double u = q[1 + dir] / q[0];
+    const T P = kbl_pressure<DIM, T>(q, gm1);
+    const T u = q[1 + dir] / q[0];
     F[0] = q[1 + dir];
-    F[1] = q[1] * u + (dir == 0 ? P : 0.0);
-    if (DIM == 2) F[2] = q[2] * u + (dir == 1 ? P : 0.0);
+    F[1] = q[1] * u + (dir == 0 ? P : T(0));
+    if (DIM == 2) F[2] = q[2] * u + (dir == 1 ? P : T(0));
     F[DIM + 1] = (q[DIM + 1] + P) * u;
 }
 
 // Rusanov flux with the Davis wavespeed; ql on the minus side of the axis.
-template <int DIM>
-__device__ __forceinline__ void kbl_rusanov(const double* ql, const double* qr, int dir,
-                                            double gamma, double* F)
+template <int DIM, typename T = double>
+__device__ __forceinline__ void kbl_rusanov(const T* ql, const T* qr, int dir, T gamma, T* F)
 {
     constexpr int NV = DIM + 2;
-    const double gm1 = gamma - 1.0;
-    double Fl[NV], Fr[NV];
-    kbl_flux<DIM>(ql, dir, gm1, Fl);
-    kbl_flux<DIM>(qr, dir, gm1, Fr);
-    const double Pl = kbl_pressure<DIM>(ql, gm1), Pr = kbl_pressure<DIM>(qr, gm1);
-    const double sl = fabs(ql[1 + dir] / ql[0]) + sqrt(gamma * Pl / ql[0]);
-    const double sr = fabs(qr[1 + dir] / qr[0]) + sqrt(gamma * Pr / qr[0]);
-    const double lam = fmax(sl, sr);
+    const T gm1 = gamma - T(1);
+    T Fl[NV], Fr[NV];
+    kbl_flux<DIM, T>(ql, dir, gm1, Fl);
+    kbl_flux<DIM, T>(qr, dir, gm1, Fr);
+    const T Pl = kbl_pressure<DIM, T>(ql, gm1), Pr = kbl_pressure<DIM, T>(qr, gm1);
+    const T sl = fabs(ql[1 + dir] / ql[0]) + sqrt(gamma * Pl / ql[0]);
+    const T sr = fabs(qr[1 + dir] / qr[0]) + sqrt(gamma * Pr / qr[0]);
+    const T lam = fmax(sl, sr);
 #pragma unroll
-    for (int v = 0; v < NV; v++) F[v] = 0.5 * (Fl[v] + Fr[v]) - 0.5 * lam * (qr[v] - ql[v]);
+    for (int v = 0; v < NV; v++) F[v] = T(0.5) * (Fl[v] + Fr[v]) - T(0.5) * lam * (qr[v] - ql[v]);
 }
 
 // Exterior value of component v at face point fp of element e.

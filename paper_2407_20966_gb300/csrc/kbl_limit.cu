@@ -17,6 +17,18 @@
 
 namespace {
 
+// Order-preserving map of a double to a signed 64-bit key (finite values):
+// min/max then run on the integer pipe instead of the slow FP64 pipe.
+__device__ __forceinline__ long long dkey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double dunkey(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
+}
+
 template <int DIM, int N>
 struct LimShape {
     static constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
@@ -41,13 +53,19 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
     __shared__ double sP[EPB][NS + NFP];
     __shared__ double saP[EPB];
     __shared__ int sPtaken[EPB];
-    __shared__ double slm[N], slp[N], swq[N];
+    __shared__ double slm[N], slp[N], sW[NS];
+    __shared__ double sWsum;
 
     const int tid = threadIdx.x;
     if (tid < N) {
         slm[tid] = ops.lm[tid];
         slp[tid] = ops.lp[tid];
-        swq[tid] = ops.wq[tid];
+    }
+    if (tid < NS) sW[tid] = (DIM == 1) ? ops.wq[tid] : ops.wq[tid % N] * ops.wq[tid / N];
+    if (tid == 0) {
+        double sws = 0.0;
+        for (int n2 = 0; n2 < NS; n2++) sws += (DIM == 1) ? ops.wq[n2] : ops.wq[n2 % N] * ops.wq[n2 / N];
+        sWsum = sws;
     }
     const int el = tid / NS, nd = tid % NS;
     const int e = blockIdx.x * EPB + el;
@@ -92,22 +110,21 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
         const int ell = t / NV, v = t % NV;
         const int ee = blockIdx.x * EPB + ell;
         if (ee < E) {
-            double s = 0.0, sws = 0.0;
-            for (int n2 = 0; n2 < NS; n2++) {
-                const double W = (DIM == 1) ? swq[n2] : swq[n2 % N] * swq[n2 / N];
-                s += W * sw[ell][v][n2];
-                sws += W;
-            }
-            const double mean = s / sws;
-            double mx = sw[ell][v][0], mn = mx;
+            double s = 0.0;
+            for (int n2 = 0; n2 < NS; n2++) s += sW[n2] * sw[ell][v][n2];
+            const double mean = s / sWsum;
+            long long kmx = dkey(sw[ell][v][0]), kmn = kmx;
             for (int n2 = 1; n2 < NS; n2++) {
-                mx = fmax(mx, sw[ell][v][n2]);
-                mn = fmin(mn, sw[ell][v][n2]);
+                const long long kk = dkey(sw[ell][v][n2]);
+                kmx = kk > kmx ? kk : kmx;
+                kmn = kk < kmn ? kk : kmn;
             }
             for (int fp = 0; fp < NFP; fp++) {
-                mx = fmax(mx, sf[ell][v][fp]);
-                mn = fmin(mn, sf[ell][v][fp]);
+                const long long kk = dkey(sf[ell][v][fp]);
+                kmx = kk > kmx ? kk : kmx;
+                kmn = kk < kmn ? kk : kmn;
             }
+            const double mx = dunkey(kmx), mn = dunkey(kmn);
             const double lo = bnd[(size_t)v * E + ee];
             const double hi = bnd[((size_t)NV + v) * E + ee];
             const double dmax = mx - mean, dmin = mn - mean;
@@ -137,7 +154,11 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
         salpha[tid] = a;
     }
     __syncthreads();
-    // 4. limited state at V and its pressure
+    // 4. limited state at V.  Pressure floor test without a division first:
+    //    P < p_floor  <=>  (gamma-1) (rho E - |m|^2/2) < p_floor rho  (rho > 0);
+    //    the margin bounds the rounding of rho E - |m|^2/2 (it can cancel), so the
+    //    screen never passes a point the exact test would fail; any element it
+    //    flags gets the exact P_min of Eq. 47 below.
     const double gm1 = ph.gamma - 1.0;
     if (live) {
         const double a = salpha[el];
@@ -148,7 +169,11 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
             q[v] = m + a * (sw[el][v][nd] - m);
             sw[el][v][nd] = q[v];
         }
-        sP[el][nd] = kbl_pressure<DIM>(q, gm1);
+        double mm = q[1] * q[1];
+        if (DIM == 2) mm += q[2] * q[2];
+        const double X = fma(q[DIM + 1], q[0], -0.5 * mm);
+        const double tol = 4e-15 * (fabs(q[DIM + 1] * q[0]) + 0.5 * mm);
+        sP[el][nd] = (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) ? -1.0 : 1.0;
     }
     for (int t = tid; t < EPB * NFP; t += NT) {
         const int ell = t / NFP, fp = t % NFP;
@@ -159,23 +184,39 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
         for (int v = 0; v < NV; v++) {
             const double m = smean[ell][v];
             q[v] = m + a * (sf[ell][v][fp] - m);
+            sf[ell][v][fp] = q[v];
         }
-        sP[ell][NS + fp] = kbl_pressure<DIM>(q, gm1);
+        double mm = q[1] * q[1];
+        if (DIM == 2) mm += q[2] * q[2];
+        const double X = fma(q[DIM + 1], q[0], -0.5 * mm);
+        const double tol = 4e-15 * (fabs(q[DIM + 1] * q[0]) + 0.5 * mm);
+        sP[ell][NS + fp] = (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) ? -1.0 : 1.0;
     }
     __syncthreads();
     if (tid < EPB && blockIdx.x * EPB + tid < E) {
-        double pmin = sP[tid][0];
-        for (int n2 = 1; n2 < NS + NFP; n2++) pmin = fmin(pmin, sP[tid][n2]);
+        bool low = false;
+        for (int n2 = 0; n2 < NS + NFP; n2++) low |= sP[tid][n2] < 0.0;
         double aP = 1.0;
-        sPtaken[tid] = pmin < ph.p_floor;
-        if (pmin < ph.p_floor) {
-            double q[NV];
+        int taken = 0;
+        if (low) {
+            // exact P_min over V of the limited state (Eq. 47)
+            double pmin = INFINITY, q[NV];
+            for (int n2 = 0; n2 < NS + NFP; n2++) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) q[v] = smean[tid][v];
-            const double Pbar = kbl_pressure<DIM>(q, gm1);
-            aP = (Pbar > ph.p_floor) ? fabs((ph.p_floor - Pbar) / (pmin - Pbar)) : 0.0;
-            atomicAdd(&flags->prelimit, 1ull);
+                for (int v = 0; v < NV; v++) q[v] = n2 < NS ? sw[tid][v][n2] : sf[tid][v][n2 - NS];
+                const double P = kbl_pressure<DIM>(q, gm1);
+                if (P < pmin) pmin = P;
+            }
+            if (pmin < ph.p_floor) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) q[v] = smean[tid][v];
+                const double Pbar = kbl_pressure<DIM>(q, gm1);
+                aP = (Pbar > ph.p_floor) ? fabs((ph.p_floor - Pbar) / (pmin - Pbar)) : 0.0;
+                taken = 1;
+                atomicAdd(&flags->prelimit, 1ull);
+            }
         }
+        sPtaken[tid] = taken;
         saP[tid] = aP;
         const int ee = blockIdx.x * EPB + tid;
         if (salpha[tid] < 1.0) atomicAdd(&flags->limited, 1ull);

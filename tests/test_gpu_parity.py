@@ -18,6 +18,9 @@ CASES_2D = [  # (p, nu, elements per side)
     (2, 32, (9, 7)),
     (1, 16, (5, 17)),
     (4, 8, (6, 5)),
+    (3, 64, (3, 4)),
+    (4, 32, (4, 3)),
+    (5, 16, (3, 3)),
 ]
 
 
@@ -121,6 +124,26 @@ def test_rhs(orc, dim, p, n):
 
 
 @pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7)), (2, 2, (4, 13))])
+def test_fp32_mixed_traces_rhs_dt(orc, dim, p, n):
+    """FP32-mixed contexts run the residual and the time step in FP32 arithmetic (FP64 storage)."""
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16), precision=1)
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=55 + p)
+    om = upload(ctx, orc, mesh)
+    wf_ref = orc.traces(ocfg, om, w)
+    wd = to_dev(w)
+    wf = zeros_dev(*wf_ref.shape)
+    ctx.traces(wd, wf)
+    np.testing.assert_allclose(wf.cpu().numpy(), wf_ref, rtol=1e-14, atol=1e-14)   # FP64 in both modes
+    R_ref = orc.rhs(ocfg, om, w, wf_ref)
+    R = zeros_dev(*w.shape)
+    ctx.rhs(wd, to_dev(wf_ref), R)
+    assert (np.abs(R.cpu().numpy() - R_ref) / np.abs(R_ref).max()).max() < 5e-6
+    d = zeros_dev(1)
+    ctx.dt(wd, 0.3, d)
+    assert d.item() == pytest.approx(orc.dt(ocfg, om, w, 0.3), rel=1e-6)
+
+
+@pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7)), (2, 2, (4, 13))])
 def test_limit(orc, dim, p, n):
     ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16))
     mesh, w = mesh_and_field(orc, dim, p, n, seed=60 + p, kind="smooth")
@@ -199,7 +222,8 @@ def test_full_step(orc, dim, p, n, nu, precision):
     wd = to_dev(w)
     ctx.set_time(0.0)
     ctx.step(wd, 0.1)
-    assert ctx.time() == pytest.approx(dt, rel=1e-14)
+    # FP32-mixed contexts compute the time step in FP32
+    assert ctx.time() == pytest.approx(dt, rel=1e-14 if precision == 0 else 1e-6)
     tol = TOL_FP64 if precision == 0 else TOL_FP32
     assert state_error(wd.cpu().numpy(), ref).max() < tol
     ctx.check()
