@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2)")
     return ap.parse_args()
 
 
@@ -159,6 +160,8 @@ def run_ours(args, rank, world):
         return ctx
 
     ctx = make_ctx(precision)
+    if args.bounds_tile >= 0:
+        ctx.set_tuning(kbl.TUNE_BOUNDS_TILE, args.bounds_tile)
     xi = ctx.operator(kbl.OP_NODES)
     w0 = inputs.nodal_field(mesh, xi, wl["ic"])
     w_dev = torch.from_numpy(w0).to(dev)

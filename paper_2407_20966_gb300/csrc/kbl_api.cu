@@ -510,6 +510,24 @@ kbl_status kbl_read_counters(kbl_ctx* c, kbl_counters* out)
     return KBL_OK;
 }
 
+kbl_status kbl_set_tuning(kbl_ctx* c, int key, int value)
+{
+    if (!c) return KBL_EINVAL;
+    if (key != KBL_TUNE_BOUNDS_TILE || value < 0 || value > 1) return fail(c, KBL_EINVAL, "unknown tuning knob or value");
+    c->bounds_tile = value;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_w = nullptr;
+    return KBL_OK;
+}
+
+kbl_status kbl_get_tuning(const kbl_ctx* c, int key, int* value)
+{
+    if (!c || !value || key != KBL_TUNE_BOUNDS_TILE) return KBL_EINVAL;
+    *value = c->bounds_tile;
+    return KBL_OK;
+}
+
 kbl_status kbl_check(kbl_ctx* c)
 {
     kbl_counters k;

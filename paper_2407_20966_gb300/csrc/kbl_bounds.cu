@@ -365,18 +365,24 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
 // the bounds.  Everything else per state (U, theta, A, C, the box) is FP32,
 // because the GB300 FP64 pipe runs at ~1/76 of the FP32 rate.
 // ---------------------------------------------------------------------------
-template <int NX>
+template <int NX, int TYSEL = 0>
 struct B2f32 {
-    static constexpr int TX = (NX >= 32) ? 4 : (NX >= 16 ? 2 : 1);
-    static constexpr int TPA = NX / TX;
-    static constexpr int NT = TPA * TPA;
-    static constexpr int MINB = NT == 64 ? KBL_BOUNDS_MINB : 1;   // resident blocks per SM to aim for
+    static constexpr int TX = (NX >= 32) ? 4 : (NX >= 16 ? 2 : 1);     // x nodes per thread
+    static constexpr int TY = (TYSEL > 0 && TYSEL <= TX) ? TYSEL : TX; // y nodes per thread
+    static constexpr int TPX = NX / TX, TPY = NX / TY;
+    static constexpr int NT = TPX * TPY;
+    static constexpr int MINB = (NT == 64) ? KBL_BOUNDS_MINB : (NT == 128 ? 8 : 1);
     // table position of grid index j: with 4 nodes per thread the two float2
     // halves of a thread's tile are stored NX/2 apart, so the 16-byte loads of
     // the threads of a warp are contiguous (no shared-memory bank conflicts)
     __host__ __device__ static constexpr int pos(int j)
     {
         return TX == 4 ? ((j & 3) >> 1) * (NX / 2) + (j >> 2) * 2 + (j & 1) : j;
+    }
+    // y tables: same layout when the y tile is 4 wide, natural order otherwise
+    __host__ __device__ static constexpr int posy(int j)
+    {
+        return TY == 4 ? ((j & 3) >> 1) * (NX / 2) + (j >> 2) * 2 + (j & 1) : j;
     }
 };
 
@@ -422,16 +428,16 @@ __device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], float& out
     out_lo = lo[0] + ol + e2;
 }
 
-template <int N, int NX>
-__global__ void __launch_bounds__(B2f32<NX>::NT, B2f32<NX>::MINB)
+template <int N, int NX, int TYSEL>
+__global__ void __launch_bounds__(B2f32<NX, TYSEL>::NT, B2f32<NX, TYSEL>::MINB)
 k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
                double* __restrict__ bnd, DevFlags* flags)
 {
-    using SH = B2f32<NX>;
+    using SH = B2f32<NX, TYSEL>;
     constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP, NV = 4;
     constexpr int NSTP = (NST + 1) & ~1;         // padded to pairs (the last state repeated)
     constexpr int NPAIR = NSTP / 2;
-    constexpr int TX = SH::TX, TPA = SH::TPA, NT = SH::NT;
+    constexpr int TX = SH::TX, TY = SH::TY, TPX = SH::TPX, NT = SH::NT;
     constexpr int NW = (NT + 31) / 32;
     constexpr int K = 12;
     __shared__ double sS[NST][NV];
@@ -530,7 +536,7 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
     {
         constexpr int ROWS = NT / NX > 0 ? NT / NX : 1;
         const int j = tid % NX;
-        const int pj = SH::pos(j);
+        const int pj = SH::pos(j), pjy = SH::posy(j);
         const float2 rx = make_float2(srx[j], srx[j]);
         const float2 ry = make_float2(sry[j], sry[j]);
         for (int pr = tid / NX; pr < NPAIR; pr += ROWS) {
@@ -546,34 +552,35 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
             const float2 ex = __fmul2_rn(make_float2(fast_exp2(ax.x), fast_exp2(ax.y)), A);
             sEx[pr][pj] = ex;
             sExc[pr][pj] = __fmul2_rn(ex, C);
-            sEy[pr][pj] = make_float2(fast_exp2(ay.x), fast_exp2(ay.y));
+            sEy[pr][pjy] = make_float2(fast_exp2(ay.x), fast_exp2(ay.y));
         }
     }
     __syncthreads();
-    // 4. envelopes on this thread's TX x TX tile: packed products of a pair of states,
-    //    three-input min/max
-    const int tx = tid % TPA, ty = tid / TPA;
-    float tlo[TX][TX], thi[TX][TX], ilo[TX][TX], ihi[TX][TX];
+    // 4. envelopes on this thread's TX x TY tile: packed products of a pair of
+    //    states, three-input min/max
+    const int tx = tid % TPX, ty = tid / TPX;
+    float tlo[TX][TY], thi[TX][TY], ilo[TX][TY], ihi[TX][TY];
 #pragma unroll
     for (int a = 0; a < TX; a++)
 #pragma unroll
-        for (int b = 0; b < TX; b++) {
+        for (int b = 0; b < TY; b++) {
             tlo[a][b] = FLT_MAX; ilo[a][b] = FLT_MAX;
             thi[a][b] = 0.0f; ihi[a][b] = 0.0f;
         }
 #pragma unroll 2
     for (int pi = 0; pi < NPAIR; pi++) {
-        float2 ex[TX], exc[TX], ey[TX];
+        float2 ex[TX], exc[TX], ey[TY];
 #pragma unroll
         for (int a = 0; a < TX; a++) {
             ex[a] = sEx[pi][SH::pos(tx * TX + a)];
             exc[a] = sExc[pi][SH::pos(tx * TX + a)];
-            ey[a] = sEy[pi][SH::pos(ty * TX + a)];
         }
+#pragma unroll
+        for (int b = 0; b < TY; b++) ey[b] = sEy[pi][SH::posy(ty * TY + b)];
 #pragma unroll
         for (int a = 0; a < TX; a++)
 #pragma unroll
-            for (int b = 0; b < TX; b++) {
+            for (int b = 0; b < TY; b++) {
                 const float2 g = __fmul2_rn(ex[a], ey[b]);
                 const float2 cg = __fmul2_rn(exc[a], ey[b]);
                 tlo[a][b] = fmin3(tlo[a][b], g.x, g.y);
@@ -594,8 +601,8 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
         float cTl = 0.f, cTh = 0.f, cIl = 0.f, cIh = 0.f, cKl = 0.f, cKh = 0.f;
         float cNh = 0.f, cNl = 0.f, cPl = 0.f, cPh = 0.f;
 #pragma unroll
-        for (int b = 0; b < TX; b++) {
-            const int jy = ty * TX + b;
+        for (int b = 0; b < TY; b++) {
+            const int jy = ty * TY + b;
             const float qy = sqy[jy], qk = sqky[jy], qn = squyn[jy], qp = squyp[jy];
             const float Tl = tlo[a][b], Th = thi[a][b];
             cTl = fmaf(qy, Tl, cTl);
@@ -778,9 +785,12 @@ k_bounds1d(const double* __restrict__ w, const double* __restrict__ wf, MeshDev 
 template <int N, int NX>
 int run2d(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cudaStream_t s)
 {
-    if (c->cfg.precision == KBL_FP32_MIXED)
-        k_bounds2d_f32<N, NX><<<c->E, B2f32<NX>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
-    else
+    if (c->cfg.precision == KBL_FP32_MIXED) {
+        if (NX >= 32 && c->bounds_tile == 1)
+            k_bounds2d_f32<N, NX, 2><<<c->E, B2f32<NX, 2>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+        else
+            k_bounds2d_f32<N, NX, 0><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+    } else
         k_bounds2d_f64<N, NX><<<c->E, B2f64<NX>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
     return 1;
 }

@@ -69,6 +69,7 @@ struct kbl_ctx {
     DevFlags* d_flags = nullptr;
     std::string err;
     int64_t launches = 0;
+    int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes
     // graph of kbl_step, keyed by (w, cfl)
     cudaGraphExec_t graph = nullptr;
     double* graph_w = nullptr;

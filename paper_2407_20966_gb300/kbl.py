@@ -74,7 +74,11 @@ _SIGS = {
     "kbl_read_counters": (C.c_int, [_P, C.POINTER(KblCounters)]),
     "kbl_launch_count": (C.c_int64, [_P]),
     "kbl_bounds_noalloc": (C.c_int, [C.POINTER(KblConfig), C.c_int, _P, C.c_int, _P, _P, _P, _P]),
+    "kbl_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
+    "kbl_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
 }
+
+TUNE_BOUNDS_TILE = 0
 
 
 def exported_symbols():
@@ -242,6 +246,14 @@ class Context:
 
     def launch_count(self):
         return int(self._lib.kbl_launch_count(self._h))
+
+    def set_tuning(self, key, value):
+        self._check(self._lib.kbl_set_tuning(self._h, int(key), int(value)), "set_tuning")
+
+    def get_tuning(self, key):
+        v = C.c_int()
+        self._check(self._lib.kbl_get_tuning(self._h, int(key), C.byref(v)), "get_tuning")
+        return v.value
 
 
 def _dev_any(t, dtype_name, name):

@@ -97,6 +97,21 @@ def test_bounds_fp32_2d(orc, p, nu, n):
     assert err.max() < TOL_FP32, err.max()
 
 
+@pytest.mark.parametrize("p,nu,n", [(3, 32, (13, 11)), (4, 32, (4, 3)), (2, 64, (3, 3))])
+def test_bounds_fp32_2d_tile_4x2(orc, p, nu, n):
+    """The 4 x 2 thread tile (a launch-shape knob) gives the same bounds."""
+    from paper_2407_20966_gb300 import kbl
+    ctx, ocfg = both(orc, 2, p, (nu, nu), precision=1)
+    ctx.set_tuning(kbl.TUNE_BOUNDS_TILE, 1)
+    mesh, w = mesh_and_field(orc, 2, p, n, seed=25 + p, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    wf = orc.traces(ocfg, om, w)
+    ref = orc.bounds(ocfg, om, w, wf)
+    bnd = zeros_dev(2, ocfg.nv, mesh.n_elem)
+    ctx.bounds(to_dev(w), to_dev(wf), bnd)
+    assert bounds_error(bnd.cpu().numpy(), ref).max() < TOL_FP32
+
+
 @pytest.mark.parametrize("p,nu,n", [(3, 64, 41), (2, 200, 9), (1, 2048, 3)])
 def test_bounds_fp32_1d(orc, p, nu, n):
     err, _ = _bounds_case(orc, 1, p, (nu,), n, 1, seed=30 + p)
