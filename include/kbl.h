@@ -185,6 +185,45 @@ typedef enum { KBL_TUNE_BOUNDS_TILE = 0 } kbl_tune_key;
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 
+/* ---- Batched form -----------------------------------------------------------
+ * Many independent 2D problems (axis-aligned quad meshes) with uneven element
+ * counts and orders p = 1..4, advanced together: every phase of a stage runs as
+ * ONE persistent launch over all problems (blocks pull cost-sorted work items
+ * from a device counter), and a whole step is one captured CUDA graph.  Each
+ * problem keeps its own time step.  Precision is KBL_FP32_MIXED.
+ * Problem i's data are concatenated in problem order: nbr (E_i x 4, element
+ * indices local to the problem, negative = local boundary id), h (E_i x 2),
+ * bc (n_bc_i x 4).  Its state lives at state_offsets[i] (in doubles) of one
+ * buffer, with the single-mesh layout w_i[4][E_i][(p_i+1)^2]. */
+typedef struct kbl_batch kbl_batch;
+
+/* cfg supplies dim (must be 2), nu, gamma, k, r_fac, eps, floors and the eps
+ * reading; cfg->p is ignored and cfg->precision must be KBL_FP32_MIXED.  HOST
+ * arrays, copied.  Synchronous; allocates the batch's device memory. */
+kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int n_problems,
+                            const int32_t* p, const int32_t* n_elem, const int32_t* nbr,
+                            const double* h, const int32_t* n_bc, const double* bc,
+                            void* cuda_stream);
+kbl_status kbl_batch_destroy(kbl_batch* b);
+const char* kbl_batch_last_error(const kbl_batch* b);
+/* state_offsets[n_problems+1] (doubles) and elem_offsets[n_problems+1] (HOST). */
+kbl_status kbl_batch_layout(const kbl_batch* b, int64_t* state_offsets, int64_t* elem_offsets);
+/* FR nodes of order p (HOST, p+1 values), for building initial states. */
+kbl_status kbl_batch_nodes(const kbl_batch* b, int p, double* host_out, int n);
+/* One SSP-RK3 step of every problem, each with dt = cfl * its own CFL limit. */
+kbl_status kbl_batch_step(kbl_batch* b, double* w, double cfl);
+/* Per-problem time step of the last step (HOST, n_problems values; synchronous). */
+kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host);
+/* Time the bounds phase on state w for every combination of thread tile
+ * (4x4 / 4x2 velocity nodes per thread), elements per work item and resident
+ * blocks per SM, on a fixed sample of the work items, and keep the fastest.
+ * Synchronous.  out_ms (may be NULL) receives the best time of the sample. */
+kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms);
+/* Current launch shape: [tile, elements per item, blocks per SM, items]. */
+kbl_status kbl_batch_tuning(const kbl_batch* b, int32_t* out4);
+kbl_status kbl_batch_check(kbl_batch* b);
+int64_t kbl_batch_launch_count(const kbl_batch* b);
+
 /* Element bounds without any device allocation.  The paper has no
  * counterpart to this call; it exists for callers that cannot call
  * cudaMalloc: applications that hand all device memory to their own pool at

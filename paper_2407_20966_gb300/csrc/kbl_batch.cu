@@ -1,0 +1,780 @@
+// kbl_batch.cu -- the batched form: many independent 2D problems with uneven
+// element counts and orders, advanced together.
+//
+// Every phase of a stage (time step, traces, bounds, residual, stage + limiter)
+// is ONE persistent launch over all problems.  Each block pulls work items
+// (problem, first element, element count) from a device counter; items are
+// sorted by cost (order p, descending) so that the expensive ones start first
+// and the tail is made of cheap ones.  The element code is the same device
+// code the single-mesh kernels run (kbl_*_body.cuh), switched on the item's
+// order.  A whole SSP-RK3 step is captured once as a CUDA graph (the counters
+// are reset by a memset node).  The launch shape of the dominant bounds phase
+// (thread tile, elements per item, resident blocks per SM) is chosen by
+// kbl_batch_autotune, which times the candidates on a sample of the items.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kbl_bounds_body.cuh"
+#include "kbl_fr_body.cuh"
+#include "kbl_limit_body.cuh"
+
+namespace {
+
+using namespace kbl_dev;
+
+constexpr int PMAX_B = 4;        // orders 1..4
+constexpr int NX_B = 32;         // velocity points per axis supported by the batch
+constexpr int NTB = 256;         // threads per block of the FR / limiter phases
+constexpr int FR_CHUNK = 256;    // elements per work item of the FR / limiter phases
+constexpr int NCOUNTERS = 16;    // one work counter per persistent launch of a step
+
+struct ProbDesc {
+    long long woff;     // state offset (doubles)
+    long long wfoff;    // traces offset (doubles)
+    long long bndoff;   // bounds offset (doubles)
+    int E, p;
+    int eoff;           // first element of the problem in the concatenated mesh
+    int bcoff;          // first boundary state of the problem
+    int n_bc;
+};
+
+struct WorkItem {
+    int prob, e0, n;
+};
+
+struct BatchOps {
+    FrOps o[PMAX_B + 1];     // index p
+};
+
+struct BatchDev {
+    const ProbDesc* probs;
+    const int* nbr;          // concatenated, local indices
+    const double* h;
+    const double* bc;
+    int n_probs;
+};
+
+__device__ __forceinline__ MeshDev mesh_of_prob(const BatchDev& bd, const ProbDesc& pd)
+{
+    MeshDev m;
+    m.E = pd.E;
+    m.nbr = bd.nbr + (size_t)pd.eoff * 4;
+    m.h = bd.h + (size_t)pd.eoff * 2;
+    m.bc = bd.bc + (size_t)pd.bcoff * 4;
+    m.n_bc = pd.n_bc;
+    return m;
+}
+
+// Next work item of this block (block-uniform), or -1.
+__device__ __forceinline__ int next_item(unsigned* counter, int n_items, int* s_item)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned it = atomicAdd(counter, 1u);
+        *s_item = it < (unsigned)n_items ? (int)it : -1;
+    }
+    __syncthreads();
+    return *s_item;
+}
+
+// ---------------------------------------------------------------------------
+// persistent phase kernels
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void traces_item(const ProbDesc& pd, const WorkItem& wi, const FrOps& ops,
+                                            const double* __restrict__ w, double* __restrict__ wf)
+{
+    constexpr int NS = N * N, NFP = 4 * N;
+    const double* wp = w + pd.woff;
+    double* wfp = wf + pd.wfoff;
+    for (int t = threadIdx.x; t < wi.n * NFP; t += blockDim.x) {
+        const int e = wi.e0 + t / NFP, fp = t % NFP;
+        const int f = fp / N, k = fp % N;
+        const bool plus = f & 1, along_x = f < 2;
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            const double* we = wp + ((size_t)v * pd.E + e) * NS;
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < N; i++) s += (plus ? ops.lp[i] : ops.lm[i]) * we[along_x ? k * N + i : i * N + k];
+            wfp[((size_t)v * pd.E + e) * NFP + fp] = s;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NTB) k_batch_traces(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
+                                                      unsigned* counter, BatchOps ops, const double* w, double* wf)
+{
+    __shared__ int s_item;
+    for (;;) {
+        const int it = next_item(counter, n_items, &s_item);
+        if (it < 0) break;
+        const WorkItem wi = items[it];
+        const ProbDesc pd = bd.probs[wi.prob];
+        switch (pd.p) {
+            case 1: traces_item<2>(pd, wi, ops.o[1], w, wf); break;
+            case 2: traces_item<3>(pd, wi, ops.o[2], w, wf); break;
+            case 3: traces_item<4>(pd, wi, ops.o[3], w, wf); break;
+            case 4: traces_item<5>(pd, wi, ops.o[4], w, wf); break;
+        }
+    }
+}
+
+template <int TYSEL>
+struct BoundsUnion {
+    union {
+        Bounds2dF32Smem<2, NX_B, TYSEL> s2;
+        Bounds2dF32Smem<3, NX_B, TYSEL> s3;
+        Bounds2dF32Smem<4, NX_B, TYSEL> s4;
+        Bounds2dF32Smem<5, NX_B, TYSEL> s5;
+    };
+};
+
+template <int N, int TYSEL>
+__device__ __forceinline__ void bounds_item(void* smraw, const BatchDev& bd, const ProbDesc& pd, const WorkItem& wi,
+                                            const Phys& ph, const double* w, const double* wf, double* bnd,
+                                            DevFlags* flags)
+{
+    auto& sm = *reinterpret_cast<Bounds2dF32Smem<N, NX_B, TYSEL>*>(smraw);
+    const MeshDev m = mesh_of_prob(bd, pd);
+    for (int e = wi.e0; e < wi.e0 + wi.n; e++)
+        bounds2d_f32_element<N, NX_B, TYSEL>(sm, w + pd.woff, wf + pd.wfoff, m, e, ph, bnd + pd.bndoff, flags);
+}
+
+template <int TYSEL>
+__global__ void __launch_bounds__(B2f32<NX_B, TYSEL>::NT)
+k_batch_bounds(BatchDev bd, const WorkItem* __restrict__ items, int n_items, unsigned* counter, Phys ph,
+               const double* w, const double* wf, double* bnd, DevFlags* flags)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_item;
+    for (;;) {
+        const int it = next_item(counter, n_items, &s_item);
+        if (it < 0) break;
+        const WorkItem wi = items[it];
+        const ProbDesc pd = bd.probs[wi.prob];
+        switch (pd.p) {
+            case 1: bounds_item<2, TYSEL>(smraw, bd, pd, wi, ph, w, wf, bnd, flags); break;
+            case 2: bounds_item<3, TYSEL>(smraw, bd, pd, wi, ph, w, wf, bnd, flags); break;
+            case 3: bounds_item<4, TYSEL>(smraw, bd, pd, wi, ph, w, wf, bnd, flags); break;
+            case 4: bounds_item<5, TYSEL>(smraw, bd, pd, wi, ph, w, wf, bnd, flags); break;
+        }
+    }
+}
+
+template <int N>
+struct FrEpb {
+    static constexpr int EPB = NTB / (N * N);
+};
+
+struct RhsUnion {
+    union {
+        RhsSmem<2, 2, float, FrEpb<2>::EPB> s2;
+        RhsSmem<2, 3, float, FrEpb<3>::EPB> s3;
+        RhsSmem<2, 4, float, FrEpb<4>::EPB> s4;
+        RhsSmem<2, 5, float, FrEpb<5>::EPB> s5;
+    };
+};
+
+template <int N>
+__device__ __forceinline__ void rhs_item(void* smraw, const BatchDev& bd, const ProbDesc& pd, const WorkItem& wi,
+                                         const FrOps& ops, double gamma, const double* w, const double* wf, double* R)
+{
+    constexpr int EPB = FrEpb<N>::EPB;
+    auto& sm = *reinterpret_cast<RhsSmem<2, N, float, EPB>*>(smraw);
+    const MeshDev m = mesh_of_prob(bd, pd);
+    const int e_end = wi.e0 + wi.n;
+    for (int eb = wi.e0; eb < e_end; eb += EPB)
+        rhs_block<2, N, float, EPB>(sm, NTB, w + pd.woff, wf + pd.wfoff, m, ops, gamma, R + pd.woff, eb,
+                                    min(EPB, e_end - eb));
+}
+
+__global__ void __launch_bounds__(NTB) k_batch_rhs(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
+                                                   unsigned* counter, BatchOps ops, double gamma, const double* w,
+                                                   const double* wf, double* R)
+{
+    __shared__ __align__(16) RhsUnion sm;
+    __shared__ int s_item;
+    for (;;) {
+        const int it = next_item(counter, n_items, &s_item);
+        if (it < 0) break;
+        const WorkItem wi = items[it];
+        const ProbDesc pd = bd.probs[wi.prob];
+        switch (pd.p) {
+            case 1: rhs_item<2>(&sm, bd, pd, wi, ops.o[1], gamma, w, wf, R); break;
+            case 2: rhs_item<3>(&sm, bd, pd, wi, ops.o[2], gamma, w, wf, R); break;
+            case 3: rhs_item<4>(&sm, bd, pd, wi, ops.o[3], gamma, w, wf, R); break;
+            case 4: rhs_item<5>(&sm, bd, pd, wi, ops.o[4], gamma, w, wf, R); break;
+        }
+    }
+}
+
+struct LimUnion {
+    union {
+        LimSmem<2, 2, FrEpb<2>::EPB> s2;
+        LimSmem<2, 3, FrEpb<3>::EPB> s3;
+        LimSmem<2, 4, FrEpb<4>::EPB> s4;
+        LimSmem<2, 5, FrEpb<5>::EPB> s5;
+    };
+};
+
+template <int N>
+__device__ __forceinline__ void stage_item(void* smraw, const ProbDesc& pd, const WorkItem& wi, const FrOps& ops,
+                                           const Phys& ph, int stage, const double* wn, const double* ws,
+                                           const double* R, const double* bnd, double dt, double* wout,
+                                           DevFlags* flags)
+{
+    constexpr int EPB = FrEpb<N>::EPB;
+    auto& sm = *reinterpret_cast<LimSmem<2, N, EPB>*>(smraw);
+    const int e_end = wi.e0 + wi.n;
+    for (int eb = wi.e0; eb < e_end; eb += EPB)
+        stage_limit_block<2, N, EPB>(sm, NTB, 0, stage, wn + pd.woff, ws + pd.woff, R + pd.woff,
+                                            bnd + pd.bndoff, dt, wout + pd.woff, nullptr, pd.E, ops, ph, flags, eb,
+                                            min(EPB, e_end - eb));
+}
+
+__global__ void __launch_bounds__(NTB) k_batch_stage(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
+                                                     unsigned* counter, BatchOps ops, Phys ph, int stage,
+                                                     const double* wn, const double* ws, const double* R,
+                                                     const double* bnd, const double* dt, double* wout, DevFlags* flags)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_item;
+    for (;;) {
+        const int it = next_item(counter, n_items, &s_item);
+        if (it < 0) break;
+        const WorkItem wi = items[it];
+        const ProbDesc pd = bd.probs[wi.prob];
+        const double dtp = dt[wi.prob];
+        switch (pd.p) {
+            case 1: stage_item<2>(smraw, pd, wi, ops.o[1], ph, stage, wn, ws, R, bnd, dtp, wout, flags); break;
+            case 2: stage_item<3>(smraw, pd, wi, ops.o[2], ph, stage, wn, ws, R, bnd, dtp, wout, flags); break;
+            case 3: stage_item<4>(smraw, pd, wi, ops.o[3], ph, stage, wn, ws, R, bnd, dtp, wout, flags); break;
+            case 4: stage_item<5>(smraw, pd, wi, ops.o[4], ph, stage, wn, ws, R, bnd, dtp, wout, flags); break;
+        }
+    }
+}
+
+// Per-problem time step: dtbits[prob] <- min of cfl h / (|U| + c) (FP32 arithmetic,
+// as the single-mesh FP32-mixed path), then dt[prob] decoded.
+template <int N>
+__device__ __forceinline__ float dt_item(const BatchDev& bd, const ProbDesc& pd, const WorkItem& wi, float gamma,
+                                         float cfl, const double* w)
+{
+    constexpr int NS = N * N;
+    const double* wp = w + pd.woff;
+    const double* h = bd.h + (size_t)pd.eoff * 2;
+    float best = FLT_MAX;
+    for (int t = threadIdx.x; t < wi.n * NS; t += blockDim.x) {
+        const int e = wi.e0 + t / NS, nd = t % NS;
+        float q[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) q[v] = (float)wp[((size_t)v * pd.E + e) * NS + nd];
+        const float P = kbl_pressure<2, float>(q, gamma - 1.0f);
+        const float a = sqrtf(gamma * P / q[0]);
+#pragma unroll
+        for (int k = 0; k < 2; k++) best = fminf(best, cfl * ((float)h[e * 2 + k] / (fabsf(q[1 + k] / q[0]) + a)));
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(NTB) k_batch_dt(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
+                                                  unsigned* counter, double gamma, double cfl,
+                                                  const double* w, unsigned long long* dtbits)
+{
+    __shared__ int s_item;
+    for (;;) {
+        const int it = next_item(counter, n_items, &s_item);
+        if (it < 0) break;
+        const WorkItem wi = items[it];
+        const ProbDesc pd = bd.probs[wi.prob];
+        float b = FLT_MAX;
+        switch (pd.p) {
+            case 1: b = dt_item<2>(bd, pd, wi, (float)gamma, (float)cfl, w); break;
+            case 2: b = dt_item<3>(bd, pd, wi, (float)gamma, (float)cfl, w); break;
+            case 3: b = dt_item<4>(bd, pd, wi, (float)gamma, (float)cfl, w); break;
+            case 4: b = dt_item<5>(bd, pd, wi, (float)gamma, (float)cfl, w); break;
+        }
+        unsigned long long bits = __double_as_longlong((double)b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+            bits = ob < bits ? ob : bits;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMin(dtbits + wi.prob, bits);
+    }
+}
+
+__global__ void k_batch_dt_finalize(const unsigned long long* dtbits, double* dt, double* t, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = __longlong_as_double((long long)dtbits[i]);
+    if (!(v > 0.0) || !(v < DBL_MAX)) v = 0.0;
+    dt[i] = v;
+}
+
+__global__ void k_batch_time_advance(const double* dt, double* t, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t[i] += dt[i];
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct kbl_batch {
+    kbl_config cfg;
+    Phys phys;
+    BatchOps ops;
+    cudaStream_t stream = nullptr;
+    int P = 0;
+    long long E_total = 0, W_total = 0, WF_total = 0, BND_total = 0;
+    std::vector<ProbDesc> probs;
+    std::vector<WorkItem> fr_items_h;
+    ProbDesc* d_probs = nullptr;
+    int* d_nbr = nullptr;
+    double* d_h = nullptr;
+    double* d_bc = nullptr;
+    double *d_wf = nullptr, *d_R = nullptr, *d_bnd = nullptr, *d_wa = nullptr, *d_wb = nullptr;
+    double *d_dt = nullptr, *d_t = nullptr;
+    unsigned long long* d_dtbits = nullptr;
+    DevFlags* d_flags = nullptr;
+    unsigned* d_counters = nullptr;
+    WorkItem* d_fr_items = nullptr;
+    int n_fr_items = 0;
+    WorkItem* d_b_items = nullptr;       // bounds items for the current chunk size
+    int n_b_items = 0;
+    // launch shape of the bounds phase
+    int tile = 0, chunk = 16, blocks_per_sm = 0;
+    int nsm = 0;
+    // graph of kbl_batch_step
+    cudaGraphExec_t graph = nullptr;
+    double* graph_w = nullptr;
+    double graph_cfl = 0.0;
+    int graph_kernels = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+kbl_status bfail(kbl_batch* b, kbl_status st, const std::string& msg)
+{
+    if (b) b->err = msg;
+    return st;
+}
+
+size_t bounds_smem(int tile)
+{
+    return tile ? sizeof(BoundsUnion<2>) : sizeof(BoundsUnion<0>);
+}
+
+std::vector<WorkItem> make_items(const std::vector<ProbDesc>& probs, int chunk)
+{
+    std::vector<WorkItem> items;
+    for (int pi = 0; pi < (int)probs.size(); pi++)
+        for (int e0 = 0; e0 < probs[pi].E; e0 += chunk) items.push_back({pi, e0, std::min(chunk, probs[pi].E - e0)});
+    // expensive first: higher order, then fuller items
+    std::stable_sort(items.begin(), items.end(), [&](const WorkItem& a, const WorkItem& b) {
+        const int pa = probs[a.prob].p, pb = probs[b.prob].p;
+        if (pa != pb) return pa > pb;
+        return a.n > b.n;
+    });
+    return items;
+}
+
+cudaError_t upload_items(kbl_batch* b, const std::vector<WorkItem>& items, WorkItem** d, int* n)
+{
+    if (*d) cudaFree(*d);
+    *d = nullptr;
+    *n = (int)items.size();
+    cudaError_t e = cudaMalloc((void**)d, std::max<size_t>(1, items.size()) * sizeof(WorkItem));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+}
+
+BatchDev dev_of(const kbl_batch* b)
+{
+    BatchDev bd;
+    bd.probs = b->d_probs;
+    bd.nbr = b->d_nbr;
+    bd.h = b->d_h;
+    bd.bc = b->d_bc;
+    bd.n_probs = b->P;
+    return bd;
+}
+
+int grid_of(const kbl_batch* b, int per_sm) { return std::max(1, b->nsm * std::max(1, per_sm)); }
+
+// Bounds phase on (w, wf) -> bnd with the current launch shape; counter slot `slot`.
+int launch_bounds_phase(kbl_batch* b, const double* w, const double* wf, double* bnd, int slot, cudaStream_t s,
+                        const WorkItem* items, int n_items)
+{
+    const BatchDev bd = dev_of(b);
+    const size_t smem = bounds_smem(b->tile);
+    const int grid = grid_of(b, b->blocks_per_sm);
+    if (b->tile)
+        k_batch_bounds<2><<<grid, B2f32<NX_B, 2>::NT, smem, s>>>(bd, items, n_items, b->d_counters + slot, b->phys,
+                                                                  w, wf, bnd, b->d_flags);
+    else
+        k_batch_bounds<0><<<grid, B2f32<NX_B, 0>::NT, smem, s>>>(bd, items, n_items, b->d_counters + slot, b->phys,
+                                                                  w, wf, bnd, b->d_flags);
+    return 1;
+}
+
+int fr_blocks_per_sm(const void* fn, size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTB, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+// One SSP-RK3 step of every problem on stream s (also used for capture).
+int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s)
+{
+    const BatchDev bd = dev_of(b);
+    int n = 0;
+    cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
+    cudaMemsetAsync(b->d_dtbits, 0x7f, (size_t)b->P * sizeof(unsigned long long), s);
+    const int g_tr = grid_of(b, fr_blocks_per_sm((const void*)k_batch_traces, 0));
+    const int g_rhs = grid_of(b, fr_blocks_per_sm((const void*)k_batch_rhs, 0));
+    const int g_st = grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion)));
+    const int g_dt = grid_of(b, fr_blocks_per_sm((const void*)k_batch_dt, 0));
+    k_batch_dt<<<g_dt, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 0, b->phys.gamma, cfl, w,
+                                    b->d_dtbits);
+    k_batch_dt_finalize<<<(b->P + 255) / 256, 256, 0, s>>>(b->d_dtbits, b->d_dt, b->d_t, b->P);
+    n += 2;
+    const double* wn = w;
+    const double* ws = w;
+    double* outs[3] = {b->d_wa, b->d_wb, w};
+    for (int st = 0; st < 3; st++) {
+        k_batch_traces<<<g_tr, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 1 + 4 * st, b->ops, ws,
+                                            b->d_wf);
+        n += launch_bounds_phase(b, ws, b->d_wf, b->d_bnd, 2 + 4 * st, s, b->d_b_items, b->n_b_items);
+        k_batch_rhs<<<g_rhs, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 3 + 4 * st, b->ops,
+                                          b->phys.gamma, ws, b->d_wf, b->d_R);
+        k_batch_stage<<<g_st, NTB, sizeof(LimUnion), s>>>(bd, b->d_fr_items, b->n_fr_items,
+                                                          b->d_counters + 4 + 4 * st, b->ops, b->phys, st, wn, ws,
+                                                          b->d_R, b->d_bnd, b->d_dt, outs[st], b->d_flags);
+        n += 3;
+        ws = outs[st];
+    }
+    k_batch_time_advance<<<(b->P + 255) / 256, 256, 0, s>>>(b->d_dt, b->d_t, b->P);
+    return n + 1;
+}
+
+void drop_graph(kbl_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_w = nullptr;
+}
+
+cudaError_t set_bounds_shape(kbl_batch* b, int tile, int chunk, int per_sm)
+{
+    b->tile = tile;
+    b->blocks_per_sm = per_sm;
+    if (chunk != b->chunk || !b->d_b_items) {
+        b->chunk = chunk;
+        cudaError_t e = upload_items(b, make_items(b->probs, chunk), &b->d_b_items, &b->n_b_items);
+        if (e != cudaSuccess) return e;
+    }
+    drop_graph(b);
+    return cudaSuccess;
+}
+
+int max_bounds_blocks(int tile)
+{
+    int n = 0;
+    const size_t smem = bounds_smem(tile);
+    if (tile) {
+        cudaFuncSetAttribute(k_batch_bounds<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_bounds<2>, B2f32<NX_B, 2>::NT, smem);
+    } else {
+        cudaFuncSetAttribute(k_batch_bounds<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_bounds<0>, B2f32<NX_B, 0>::NT, smem);
+    }
+    return std::max(1, n);
+}
+
+}  // namespace
+
+extern "C" {
+
+kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const int32_t* p, const int32_t* n_elem,
+                            const int32_t* nbr, const double* h, const int32_t* n_bc, const double* bc,
+                            void* cuda_stream)
+{
+    if (!out) return KBL_EINVAL;
+    *out = nullptr;
+    if (!cfg || cfg->dim != 2 || cfg->precision != KBL_FP32_MIXED || cfg->nu[0] != NX_B || cfg->nu[1] != NX_B)
+        return KBL_EINVAL;
+    if (!(cfg->gamma > 1.0) || !(cfg->k > 0.0) || !(cfg->r_fac >= 0.0 && cfg->r_fac < 1.0) || !(cfg->eps >= 0.0))
+        return KBL_EINVAL;
+    if (P < 1 || !p || !n_elem || !nbr || !h || !n_bc) return KBL_EINVAL;
+    kbl_batch* b = new (std::nothrow) kbl_batch();
+    if (!b) return KBL_ENOMEM;
+    b->cfg = *cfg;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->phys.gamma = cfg->gamma;
+    b->phys.k = cfg->k;
+    b->phys.r_fac = cfg->r_fac;
+    b->phys.eps = cfg->eps;
+    b->phys.rho_floor = cfg->rho_floor;
+    b->phys.p_floor = cfg->p_floor;
+    b->phys.eps_rule = cfg->eps_rule;
+    b->phys.nu[0] = b->phys.nu[1] = NX_B;
+    for (int q = 1; q <= PMAX_B; q++) kbl_build_fr_ops(q, b->ops.o[q]);
+    b->P = P;
+    long long eoff = 0, bcoff = 0, woff = 0, wfoff = 0, bndoff = 0;
+    for (int i = 0; i < P; i++) {
+        if (p[i] < 1 || p[i] > PMAX_B || n_elem[i] < 1 || n_bc[i] < 0) {
+            delete b;
+            return KBL_EINVAL;
+        }
+        const int n = p[i] + 1, E = n_elem[i];
+        for (long long k = 0; k < (long long)E * 4; k++) {
+            const int v = nbr[eoff * 4 + k];
+            if (v >= E || (v < 0 && -(v + 1) >= n_bc[i])) {
+                delete b;
+                return KBL_EINVAL;
+            }
+        }
+        for (long long k = 0; k < (long long)E * 2; k++)
+            if (!(h[eoff * 2 + k] > 0.0)) {
+                delete b;
+                return KBL_EINVAL;
+            }
+        ProbDesc d;
+        d.woff = woff;
+        d.wfoff = wfoff;
+        d.bndoff = bndoff;
+        d.E = E;
+        d.p = p[i];
+        d.eoff = (int)eoff;
+        d.bcoff = (int)bcoff;
+        d.n_bc = n_bc[i];
+        b->probs.push_back(d);
+        woff += 4LL * E * n * n;
+        wfoff += 4LL * E * 4 * n;
+        bndoff += 8LL * E;
+        eoff += E;
+        bcoff += n_bc[i];
+    }
+    if (eoff > 0x7fffffffLL) {
+        delete b;
+        return KBL_EINVAL;
+    }
+    b->E_total = eoff;
+    b->W_total = woff;
+    b->WF_total = wfoff;
+    b->BND_total = bndoff;
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, 0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    };
+    A((void**)&b->d_probs, P * sizeof(ProbDesc));
+    A((void**)&b->d_nbr, eoff * 4 * sizeof(int));
+    A((void**)&b->d_h, eoff * 2 * sizeof(double));
+    A((void**)&b->d_bc, std::max<long long>(bcoff, 1) * 4 * sizeof(double));
+    A((void**)&b->d_wf, wfoff * sizeof(double));
+    A((void**)&b->d_R, woff * sizeof(double));
+    A((void**)&b->d_bnd, bndoff * sizeof(double));
+    A((void**)&b->d_wa, woff * sizeof(double));
+    A((void**)&b->d_wb, woff * sizeof(double));
+    A((void**)&b->d_dt, P * sizeof(double));
+    A((void**)&b->d_t, P * sizeof(double));
+    A((void**)&b->d_dtbits, P * sizeof(unsigned long long));
+    A((void**)&b->d_flags, sizeof(DevFlags));
+    A((void**)&b->d_counters, NCOUNTERS * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_probs, b->probs.data(), P * sizeof(ProbDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_nbr, nbr, eoff * 4 * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_h, h, eoff * 2 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && bcoff > 0) e = cudaMemcpy(b->d_bc, bc, bcoff * 4 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, sizeof(DevFlags));
+    if (e == cudaSuccess) e = cudaMemset(b->d_t, 0, P * sizeof(double));
+    if (e == cudaSuccess) e = upload_items(b, make_items(b->probs, FR_CHUNK), &b->d_fr_items, &b->n_fr_items);
+    if (e == cudaSuccess) {
+        cudaFuncSetAttribute(k_batch_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LimUnion));
+        e = set_bounds_shape(b, 0, 16, max_bounds_blocks(0));
+    }
+    if (e != cudaSuccess) {
+        kbl_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? KBL_ENOMEM : KBL_ECUDA;
+    }
+    *out = b;
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_destroy(kbl_batch* b)
+{
+    if (!b) return KBL_EINVAL;
+    drop_graph(b);
+    void* ptrs[] = {b->d_probs, b->d_nbr, b->d_h, b->d_bc, b->d_wf, b->d_R, b->d_bnd, b->d_wa, b->d_wb, b->d_dt,
+                    b->d_t, b->d_dtbits, b->d_flags, b->d_counters, b->d_fr_items, b->d_b_items};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete b;
+    return KBL_OK;
+}
+
+const char* kbl_batch_last_error(const kbl_batch* b) { return b ? b->err.c_str() : "null batch"; }
+int64_t kbl_batch_launch_count(const kbl_batch* b) { return b ? b->launches : -1; }
+
+kbl_status kbl_batch_layout(const kbl_batch* b, int64_t* so, int64_t* eo)
+{
+    if (!b || !so || !eo) return KBL_EINVAL;
+    for (int i = 0; i < b->P; i++) {
+        so[i] = b->probs[i].woff;
+        eo[i] = b->probs[i].eoff;
+    }
+    so[b->P] = b->W_total;
+    eo[b->P] = b->E_total;
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_nodes(const kbl_batch* b, int p, double* out, int n)
+{
+    if (!b || !out || p < 1 || p > PMAX_B || n < p + 1) return KBL_EINVAL;
+    for (int i = 0; i <= p; i++) out[i] = b->ops.o[p].x[i];
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_step(kbl_batch* b, double* w, double cfl)
+{
+    if (!b || !w || !(cfl > 0.0)) return bfail(b, KBL_EINVAL, "bad argument");
+    if (!(b->graph && b->graph_w == w && b->graph_cfl == cfl)) {
+        drop_graph(b);
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+        }
+        const int n = issue_batch_step(b, w, cfl, cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return bfail(b, KBL_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return bfail(b, KBL_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        }
+        b->graph_w = w;
+        b->graph_cfl = cfl;
+        b->graph_kernels = n;
+    }
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+    b->launches += b->graph_kernels;
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host)
+{
+    if (!b || !dt_host) return KBL_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(dt_host, b->d_dt, b->P * sizeof(double), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? KBL_OK : bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms)
+{
+    if (!b || !w) return KBL_EINVAL;
+    // traces of w once, then time the bounds phase on every eighth work item
+    cudaStream_t s = b->stream;
+    cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
+    const BatchDev bd = dev_of(b);
+    k_batch_traces<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_traces, 0)), NTB, 0, s>>>(
+        bd, b->d_fr_items, b->n_fr_items, b->d_counters + 1, b->ops, w, b->d_wf);
+    b->launches++;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_ms = 1e30;
+    int best[3] = {b->tile, b->chunk, b->blocks_per_sm};
+    const int chunks[] = {4, 16, 64};
+    for (int tile = 0; tile < 2; tile++) {
+        const int maxb = max_bounds_blocks(tile);
+        const int pers[] = {maxb, std::max(1, (3 * maxb) / 4), std::max(1, maxb / 2)};
+        for (int ci = 0; ci < 3; ci++) {
+            std::vector<WorkItem> all = make_items(b->probs, chunks[ci]), sample;
+            for (size_t i = 0; i < all.size(); i += 8) sample.push_back(all[i]);
+            WorkItem* d_sample = nullptr;
+            int n_sample = 0;
+            if (upload_items(b, sample, &d_sample, &n_sample) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return bfail(b, KBL_ECUDA, "autotune upload");
+            }
+            for (int pi = 0; pi < 3; pi++) {
+                if (pi > 0 && pers[pi] == pers[pi - 1]) continue;
+                b->tile = tile;
+                b->blocks_per_sm = pers[pi];
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; rep++) {   // first run warms up
+                    cudaMemsetAsync(b->d_counters + 2, 0, sizeof(unsigned), s);
+                    cudaEventRecord(e0, s);
+                    launch_bounds_phase(b, w, b->d_wf, b->d_bnd, 2, s, d_sample, n_sample);
+                    cudaEventRecord(e1, s);
+                    b->launches++;
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best[0] = tile;
+                    best[1] = chunks[ci];
+                    best[2] = pers[pi];
+                }
+            }
+            cudaFree(d_sample);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = set_bounds_shape(b, best[0], best[1], best[2]);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+    if (out_ms) *out_ms = best_ms;
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_tuning(const kbl_batch* b, int32_t* out4)
+{
+    if (!b || !out4) return KBL_EINVAL;
+    out4[0] = b->tile;
+    out4[1] = b->chunk;
+    out4[2] = b->blocks_per_sm;
+    out4[3] = b->n_b_items;
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_check(kbl_batch* b)
+{
+    if (!b) return KBL_EINVAL;
+    DevFlags f;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&f, b->d_flags, sizeof(f), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, sizeof(DevFlags));
+    if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+    if (f.nonphysical) return bfail(b, KBL_ENONPHYSICAL, "non-physical stencil state");
+    return KBL_OK;
+}
+
+}  // extern "C"

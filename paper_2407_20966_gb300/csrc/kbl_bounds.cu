@@ -36,35 +36,17 @@
 // partial sums are combined with error-free (TwoSum) compensation.
 #include <cfloat>
 
-#include "kbl_internal.cuh"
-
-#ifndef KBL_BOUNDS_MINB
-#define KBL_BOUNDS_MINB 10
-#endif
+#include "kbl_bounds_body.cuh"
 
 namespace {
+
+using namespace kbl_dev;
 
 constexpr int CH = 16;  // states per table chunk
 
 // ---------------------------------------------------------------------------
 // shared helpers
 // ---------------------------------------------------------------------------
-template <int DIM, int N, int NT>
-__device__ __forceinline__ void gather_states(const double* __restrict__ w, const double* __restrict__ wf,
-                                              const MeshDev& m, int e, double (*sS)[DIM + 2])
-{
-    constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
-    constexpr int NST = NS + 2 * NFP;
-    for (int idx = threadIdx.x; idx < NST * NV; idx += NT) {
-        const int v = idx / NST, r = idx % NST;
-        double val;
-        if (r < NS) val = w[((size_t)v * m.E + e) * NS + r];
-        else if (r < NS + NFP) val = wf[((size_t)v * m.E + e) * NFP + (r - NS)];
-        else val = kbl_exterior<DIM, N>(wf, m, e, r - NS - NFP, v);
-        sS[r][v] = val;
-    }
-}
-
 struct StatePrim {
     double U[2];
     double th;     // theta
@@ -87,11 +69,6 @@ __device__ __forceinline__ bool prim_of(const double* q, const Phys& ph, StatePr
     s.A = (DIM == 1) ? rho / sqrt(2.0 * KBL_PI * th) : rho / (2.0 * KBL_PI * th);
     s.C = 0.5 * (2.0 / (ph.gamma - 1.0) - DIM) * th;
     return true;
-}
-
-__device__ __forceinline__ void write_nan(double* bnd, int E, int e, int nv)
-{
-    for (int v = 0; v < 2 * nv; v++) bnd[(size_t)v * E + e] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // Block-wide sum of K doubles per thread; result valid in thread 0.
@@ -120,14 +97,6 @@ __device__ __forceinline__ void block_sum_f64(double (&a)[K], double* sred /* [N
             }
         }
     }
-}
-
-// Error-free transformation: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = __fadd_rn(a, b);
-    const float bp = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
 // Compensated block-wide sum of K floats per thread (hi + lo pairs);
@@ -208,27 +177,6 @@ __device__ __forceinline__ void finalize_bounds(const double* raw, double scale,
 
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
-
-__device__ __forceinline__ float fmin3(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-__device__ __forceinline__ float fmax3(float a, float b, float c)
-{
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-__device__ __forceinline__ float fast_exp2(float x)
-{
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-constexpr float LOG2E = 1.4426950408889634f;
 
 // ---------------------------------------------------------------------------
 // 2D, FP64
@@ -359,314 +307,15 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
 }
 
 // ---------------------------------------------------------------------------
-// 2D, FP32 envelopes and sums.  FP64 is used only where the path needs it:
-// X = rho E - |m|^2 / 2 (= rho P / (gamma - 1), the cancellation-prone,
-// positivity-deciding quantity) and its sign test, and the final assembly of
-// the bounds.  Everything else per state (U, theta, A, C, the box) is FP32,
-// because the GB300 FP64 pipe runs at ~1/76 of the FP32 rate.
+// 2D, FP32 envelopes and sums (body in kbl_bounds_body.cuh): one block per element
 // ---------------------------------------------------------------------------
-template <int NX, int TYSEL = 0>
-struct B2f32 {
-    static constexpr int TX = (NX >= 32) ? 4 : (NX >= 16 ? 2 : 1);     // x nodes per thread
-    static constexpr int TY = (TYSEL > 0 && TYSEL <= TX) ? TYSEL : TX; // y nodes per thread
-    static constexpr int TPX = NX / TX, TPY = NX / TY;
-    static constexpr int NT = TPX * TPY;
-    static constexpr int MINB = (NT == 64) ? KBL_BOUNDS_MINB : (NT == 128 ? 8 : 1);
-    // table position of grid index j: with 4 nodes per thread the two float2
-    // halves of a thread's tile are stored NX/2 apart, so the 16-byte loads of
-    // the threads of a warp are contiguous (no shared-memory bank conflicts)
-    __host__ __device__ static constexpr int pos(int j)
-    {
-        return TX == 4 ? ((j & 3) >> 1) * (NX / 2) + (j >> 2) * 2 + (j & 1) : j;
-    }
-    // y tables: same layout when the y tile is 4 wide, natural order otherwise
-    __host__ __device__ static constexpr int posy(int j)
-    {
-        return TY == 4 ? ((j & 3) >> 1) * (NX / 2) + (j >> 2) * 2 + (j & 1) : j;
-    }
-};
-
-// Compensated warp reduce-scatter of 16 values: afterwards lane L (even) holds
-// sum over the warp of value L / 2 as hi + lo.  16 exchanges instead of 16 x 5.
-__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], float& out_hi, float& out_lo)
-{
-    const int lane = threadIdx.x & 31;
-    float hi[8], lo[8];
-    {   // offset 16: keep the upper 8 values on lanes with bit 4 set
-        const bool up = lane & 16;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const float keep = up ? v[8 + k] : v[k];
-            const float send = up ? v[k] : v[8 + k];
-            const float o = __shfl_xor_sync(0xffffffffu, send, 16);
-            two_sum(keep, o, hi[k], lo[k]);
-        }
-    }
-#pragma unroll
-    for (int step = 0; step < 3; step++) {   // offsets 8, 4, 2
-        const int off = 8 >> step;
-        const int n = 4 >> step;              // values kept after this step
-        const bool up = lane & off;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (k >= n) break;
-            const float kh = up ? hi[n + k] : hi[k], sh = up ? hi[k] : hi[n + k];
-            const float kl = up ? lo[n + k] : lo[k], sl = up ? lo[k] : lo[n + k];
-            const float oh = __shfl_xor_sync(0xffffffffu, sh, off);
-            const float ol = __shfl_xor_sync(0xffffffffu, sl, off);
-            float s2, e2;
-            two_sum(kh, oh, s2, e2);
-            hi[k] = s2;
-            lo[k] = kl + ol + e2;
-        }
-    }
-    const float oh = __shfl_xor_sync(0xffffffffu, hi[0], 1);
-    const float ol = __shfl_xor_sync(0xffffffffu, lo[0], 1);
-    float s2, e2;
-    two_sum(hi[0], oh, s2, e2);
-    out_hi = s2;
-    out_lo = lo[0] + ol + e2;
-}
-
 template <int N, int NX, int TYSEL>
 __global__ void __launch_bounds__(B2f32<NX, TYSEL>::NT, B2f32<NX, TYSEL>::MINB)
 k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
                double* __restrict__ bnd, DevFlags* flags)
 {
-    using SH = B2f32<NX, TYSEL>;
-    constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP, NV = 4;
-    constexpr int NSTP = (NST + 1) & ~1;         // padded to pairs (the last state repeated)
-    constexpr int NPAIR = NSTP / 2;
-    constexpr int TX = SH::TX, TY = SH::TY, TPX = SH::TPX, NT = SH::NT;
-    constexpr int NW = (NT + 31) / 32;
-    constexpr int K = 12;
-    __shared__ double sS[NST][NV];
-    // per state (SoA, so that a pair of states is one 8-byte load): velocity, -log2(e)/(2 theta), A, C
-    __shared__ __align__(8) float sUx[NSTP], sUy[NSTP], sKx[NSTP], sA[NSTP], sC[NSTP];
-    __shared__ __align__(16) float2 sEx[NPAIR][NX], sExc[NPAIR][NX], sEy[NPAIR][NX];
-    __shared__ float srx[NX], sry[NX];          // grid relative to the box centre
-    // per-node moment coefficients: x: q, q u, 1/2 u^2 ; y: q, q 1/2 u^2, q u (u<0), q u (u>=0)
-    __shared__ float sqx[NX], squx[NX], skx[NX], sqy[NX], sqky[NX], squyn[NX], squyp[NX];
-    __shared__ float sbox[NW][4];
-    __shared__ int sbad;
-    __shared__ float sred[NW][16][2];
-    __shared__ double sfin[K];
-
-    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) sbad = 0;
-    gather_states<2, N, NT>(w, wf, m, e, sS);
-    __syncthreads();
-
-    // 1. primitive state of each stencil node, box candidates
-    const float gm1 = (float)(ph.gamma - 1.0), kk = (float)ph.k;
-    const float half_delta = 0.5f * (float)(2.0 / (ph.gamma - 1.0) - 2.0);
-    float blx = FLT_MAX, bly = FLT_MAX, bhx = -FLT_MAX, bhy = -FLT_MAX;
-    int bad = 0;
-    for (int i = tid; i < NSTP; i += NT) {
-        const double* q = sS[i < NST ? i : NST - 1];
-        const double X = fma(q[3], q[0], -0.5 * fma(q[2], q[2], q[1] * q[1]));
-        if (!(q[0] > 0.0) || !(X > 0.0)) bad = 1;
-        const float r = (float)q[0], inv = 1.0f / r;
-        const float ux = (float)q[1] * inv, uy = (float)q[2] * inv;
-        const float th = gm1 * ((float)X * inv) * inv;
-        const float sq = sqrtf(th);
-        sUx[i] = ux;
-        sUy[i] = uy;
-        sKx[i] = -(0.5f * LOG2E) / th;
-        sA[i] = r / (6.283185307179586f * th);
-        sC[i] = half_delta * th;
-        blx = fminf(blx, ux - kk * sq);
-        bhx = fmaxf(bhx, ux + kk * sq);
-        bly = fminf(bly, uy - kk * sq);
-        bhy = fmaxf(bhy, uy + kk * sq);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        blx = fminf(blx, __shfl_xor_sync(0xffffffffu, blx, o));
-        bhx = fmaxf(bhx, __shfl_xor_sync(0xffffffffu, bhx, o));
-        bly = fminf(bly, __shfl_xor_sync(0xffffffffu, bly, o));
-        bhy = fmaxf(bhy, __shfl_xor_sync(0xffffffffu, bhy, o));
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
-        sbox[wid][0] = blx; sbox[wid][1] = bhx; sbox[wid][2] = bly; sbox[wid][3] = bhy;
-        if (bad) atomicOr(&sbad, 1);
-    }
-    __syncthreads();
-    if (sbad) {
-        if (tid == 0) {
-            write_nan(bnd, m.E, e, NV);
-            atomicOr(&flags->nonphysical, 1);
-        }
-        return;
-    }
-    float lox = sbox[0][0], hix = sbox[0][1], loy = sbox[0][2], hiy = sbox[0][3];
-#pragma unroll
-    for (int q = 1; q < NW; q++) {
-        lox = fminf(lox, sbox[q][0]); hix = fmaxf(hix, sbox[q][1]);
-        loy = fminf(loy, sbox[q][2]); hiy = fmaxf(hiy, sbox[q][3]);
-    }
-    const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy);
-    const float hx = (hix - lox) / (float)(NX - 1), hy = (hiy - loy) / (float)(NX - 1);
-
-    // 2. state velocities and grid relative to the box centre (for the Maxwellians,
-    //    which keeps FP32 differences small), absolute grid for the moments
-    for (int i = tid; i < NSTP; i += NT) {
-        sUx[i] -= cx;
-        sUy[i] -= cy;
-    }
-    for (int j = tid; j < NX; j += NT) {
-        const float t = (float)j - 0.5f * (float)(NX - 1);
-        const float q = (j == 0 || j == NX - 1) ? 0.5f : 1.0f;
-        const float rx = t * hx, ry = t * hy;
-        const float ux = cx + rx, uy = cy + ry;
-        srx[j] = rx;
-        sry[j] = ry;
-        sqx[j] = q;
-        squx[j] = q * ux;
-        skx[j] = 0.5f * ux * ux;
-        sqy[j] = q;
-        sqky[j] = q * (0.5f * uy * uy);
-        squyn[j] = uy < 0.0f ? q * uy : 0.0f;
-        squyp[j] = uy < 0.0f ? 0.0f : q * uy;
-    }
-    __syncthreads();
-    // 3. row tables of every state, two states per packed instruction:
-    //    Ex = A exp2(-(ux-Ux)^2 kx), C Ex, Ey = exp2(-(uy-Uy)^2 kx)
-    {
-        constexpr int ROWS = NT / NX > 0 ? NT / NX : 1;
-        const int j = tid % NX;
-        const int pj = SH::pos(j), pjy = SH::posy(j);
-        const float2 rx = make_float2(srx[j], srx[j]);
-        const float2 ry = make_float2(sry[j], sry[j]);
-        for (int pr = tid / NX; pr < NPAIR; pr += ROWS) {
-            const float2 ux = reinterpret_cast<const float2*>(sUx)[pr];
-            const float2 uy = reinterpret_cast<const float2*>(sUy)[pr];
-            const float2 kx = reinterpret_cast<const float2*>(sKx)[pr];
-            const float2 A = reinterpret_cast<const float2*>(sA)[pr];
-            const float2 C = reinterpret_cast<const float2*>(sC)[pr];
-            const float2 dx = __fadd2_rn(rx, make_float2(-ux.x, -ux.y));
-            const float2 dy = __fadd2_rn(ry, make_float2(-uy.x, -uy.y));
-            const float2 ax = __fmul2_rn(__fmul2_rn(dx, dx), kx);
-            const float2 ay = __fmul2_rn(__fmul2_rn(dy, dy), kx);
-            const float2 ex = __fmul2_rn(make_float2(fast_exp2(ax.x), fast_exp2(ax.y)), A);
-            sEx[pr][pj] = ex;
-            sExc[pr][pj] = __fmul2_rn(ex, C);
-            sEy[pr][pjy] = make_float2(fast_exp2(ay.x), fast_exp2(ay.y));
-        }
-    }
-    __syncthreads();
-    // 4. envelopes on this thread's TX x TY tile: packed products of a pair of
-    //    states, three-input min/max
-    const int tx = tid % TPX, ty = tid / TPX;
-    float tlo[TX][TY], thi[TX][TY], ilo[TX][TY], ihi[TX][TY];
-#pragma unroll
-    for (int a = 0; a < TX; a++)
-#pragma unroll
-        for (int b = 0; b < TY; b++) {
-            tlo[a][b] = FLT_MAX; ilo[a][b] = FLT_MAX;
-            thi[a][b] = 0.0f; ihi[a][b] = 0.0f;
-        }
-#pragma unroll 2
-    for (int pi = 0; pi < NPAIR; pi++) {
-        float2 ex[TX], exc[TX], ey[TY];
-#pragma unroll
-        for (int a = 0; a < TX; a++) {
-            ex[a] = sEx[pi][SH::pos(tx * TX + a)];
-            exc[a] = sExc[pi][SH::pos(tx * TX + a)];
-        }
-#pragma unroll
-        for (int b = 0; b < TY; b++) ey[b] = sEy[pi][SH::posy(ty * TY + b)];
-#pragma unroll
-        for (int a = 0; a < TX; a++)
-#pragma unroll
-            for (int b = 0; b < TY; b++) {
-                const float2 g = __fmul2_rn(ex[a], ey[b]);
-                const float2 cg = __fmul2_rn(exc[a], ey[b]);
-                tlo[a][b] = fmin3(tlo[a][b], g.x, g.y);
-                thi[a][b] = fmax3(thi[a][b], g.x, g.y);
-                ilo[a][b] = fmin3(ilo[a][b], cg.x, cg.y);
-                ihi[a][b] = fmax3(ihi[a][b], cg.x, cg.y);
-            }
-    }
-    // 5. moments: column sums over this thread's y nodes, then the x weights.
-    //    raw = [Tlo, Thi, nx_hi, nx_lo, px_lo, px_hi, ny_hi, ny_lo, py_lo, py_hi, E_lo, E_hi]
-    //    (n/p: u < 0 / u >= 0 part of the momentum sums; hx hy and the
-    //    relaxation are applied in FP64 at the end)
-    float acc[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) acc[k] = 0.0f;
-#pragma unroll
-    for (int a = 0; a < TX; a++) {
-        float cTl = 0.f, cTh = 0.f, cIl = 0.f, cIh = 0.f, cKl = 0.f, cKh = 0.f;
-        float cNh = 0.f, cNl = 0.f, cPl = 0.f, cPh = 0.f;
-#pragma unroll
-        for (int b = 0; b < TY; b++) {
-            const int jy = ty * TY + b;
-            const float qy = sqy[jy], qk = sqky[jy], qn = squyn[jy], qp = squyp[jy];
-            const float Tl = tlo[a][b], Th = thi[a][b];
-            cTl = fmaf(qy, Tl, cTl);
-            cTh = fmaf(qy, Th, cTh);
-            cIl = fmaf(qy, ilo[a][b], cIl);
-            cIh = fmaf(qy, ihi[a][b], cIh);
-            cKl = fmaf(qk, Tl, cKl);
-            cKh = fmaf(qk, Th, cKh);
-            cNh = fmaf(qn, Th, cNh);
-            cNl = fmaf(qn, Tl, cNl);
-            cPl = fmaf(qp, Tl, cPl);
-            cPh = fmaf(qp, Th, cPh);
-        }
-        const int jx = tx * TX + a;
-        const float qx = sqx[jx], qux = squx[jx], kx = skx[jx];
-        const float qn = squx[jx] < 0.0f ? qux : 0.0f, qp = squx[jx] < 0.0f ? 0.0f : qux;
-        acc[0] = fmaf(qx, cTl, acc[0]);
-        acc[1] = fmaf(qx, cTh, acc[1]);
-        acc[2] = fmaf(qn, cTh, acc[2]);
-        acc[3] = fmaf(qn, cTl, acc[3]);
-        acc[4] = fmaf(qp, cTl, acc[4]);
-        acc[5] = fmaf(qp, cTh, acc[5]);
-        acc[6] = fmaf(qx, cNh, acc[6]);
-        acc[7] = fmaf(qx, cNl, acc[7]);
-        acc[8] = fmaf(qx, cPl, acc[8]);
-        acc[9] = fmaf(qx, cPh, acc[9]);
-        acc[10] = fmaf(qx, fmaf(kx, cTl, cKl + cIl), acc[10]);
-        acc[11] = fmaf(qx, fmaf(kx, cTh, cKh + cIh), acc[11]);
-    }
-    float rh, rl;
-    warp_reduce_scatter16(acc, rh, rl);
-    if ((lane & 1) == 0 && (lane >> 1) < K) {
-        sred[wid][lane >> 1][0] = rh;
-        sred[wid][lane >> 1][1] = rl;
-    }
-    __syncthreads();
-    // 6. assemble the bounds in FP64, one raw sum per lane
-    if (tid < K) {
-        float hi = sred[0][tid][0], lo = sred[0][tid][1];
-#pragma unroll
-        for (int q = 1; q < NW; q++) {
-            float s2, e2;
-            two_sum(hi, sred[q][tid][0], s2, e2);
-            hi = s2;
-            lo = lo + sred[q][tid][1] + e2;
-        }
-        // lower-bound terms take (1 - r), upper-bound terms (1 + r)
-        const bool upper_env = (tid == 1) || (tid == 2) || (tid == 5) || (tid == 6) || (tid == 9) || (tid == 11);
-        const double rel = upper_env ? 1.0 + ph.r_fac : 1.0 - ph.r_fac;
-        sfin[tid] = rel * (((double)hx * (double)hy) * ((double)hi + (double)lo));
-    }
-    __syncthreads();
-    if (tid < 2 * NV) {
-        const int v = tid % NV, up = tid / NV;
-        double val;
-        if (v == 0) val = up ? sfin[1] : sfin[0];
-        else if (v == NV - 1) val = up ? sfin[11] : sfin[10];
-        else {
-            const int b0 = 2 + 4 * (v - 1);
-            val = up ? sfin[b0 + 1] + sfin[b0 + 3] : sfin[b0 + 0] + sfin[b0 + 2];
-        }
-        if (v == 0 && !up && val < ph.rho_floor) val = ph.rho_floor;
-        bnd[((size_t)up * NV + v) * m.E + e] = val;
-    }
+    __shared__ Bounds2dF32Smem<N, NX, TYSEL> sm;
+    bounds2d_f32_element<N, NX, TYSEL>(sm, w, wf, m, blockIdx.x, ph, bnd, flags);
 }
 
 // ---------------------------------------------------------------------------

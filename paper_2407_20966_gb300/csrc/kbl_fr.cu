@@ -6,7 +6,7 @@
 // (which recovers nodal DG), Rusanov common fluxes (assumption (iv), Sec. 4).
 #include <cfloat>
 
-#include "kbl_internal.cuh"
+#include "kbl_fr_body.cuh"
 
 namespace {
 
@@ -98,7 +98,7 @@ int run_gather(const kbl_ctx* c, const double* w, const double* wf, int e0, int 
 // ---------------------------------------------------------------------------
 template <int DIM, int N>
 struct RhsShape {
-    static constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
+    static constexpr int NS = kbl_ns<DIM>(N);
     static constexpr int EPB = (DIM == 1) ? 32 : 8;
     static constexpr int NT = EPB * NS;
 };
@@ -109,83 +109,8 @@ k_rhs(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Fr
       double gamma_d, double* __restrict__ R)
 {
     using SH = RhsShape<DIM, N>;
-    constexpr int NS = SH::NS, NFP = SH::NFP, NV = SH::NV, EPB = SH::EPB, NT = SH::NT;
-    constexpr int NFPF = (DIM == 1) ? 1 : N;
-    __shared__ T sF[EPB][DIM][NV][NS];
-    __shared__ T sJ[EPB][NFP][NV];
-    __shared__ T sD[N][N], sgl[N], sgr[N], slm[N], slp[N];
-
-    const int tid = threadIdx.x;
-    for (int i = tid; i < N * N; i += NT) sD[i / N][i % N] = (T)ops.D[i / N][i % N];
-    if (tid < N) {
-        sgl[tid] = (T)ops.gl[tid];
-        sgr[tid] = (T)ops.gr[tid];
-        slm[tid] = (T)ops.lm[tid];
-        slp[tid] = (T)ops.lp[tid];
-    }
-    const int el = tid / NS, nd = tid % NS;
-    const int e = blockIdx.x * EPB + el;
-    const T gamma = (T)gamma_d, gm1 = (T)(gamma_d - 1.0);
-    if (e < m.E) {
-        T q[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) q[v] = (T)w[((size_t)v * m.E + e) * NS + nd];
-#pragma unroll
-        for (int dir = 0; dir < DIM; dir++) {
-            T F[NV];
-            kbl_flux<DIM, T>(q, dir, gm1, F);
-#pragma unroll
-            for (int v = 0; v < NV; v++) sF[el][dir][v][nd] = F[v];
-        }
-    }
-    __syncthreads();
-    for (int t = tid; t < EPB * NFP; t += NT) {
-        const int ell = t / NFP, fp = t % NFP;
-        const int ee = blockIdx.x * EPB + ell;
-        if (ee >= m.E) continue;
-        const int f = fp / NFPF, k = fp % NFPF, dir = f >> 1, side = f & 1;
-        T qi[NV], qe[NV], Fc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            qi[v] = (T)wf[((size_t)v * m.E + ee) * NFP + fp];
-            qe[v] = (T)kbl_exterior<DIM, N>(wf, m, ee, fp, v);
-        }
-        if (side == 0) kbl_rusanov<DIM, T>(qe, qi, dir, gamma, Fc);
-        else kbl_rusanov<DIM, T>(qi, qe, dir, gamma, Fc);
-        const T* l = side ? slp : slm;
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            T FD = T(0);
-#pragma unroll
-            for (int i = 0; i < N; i++) {
-                const int node = (DIM == 1) ? i : (dir == 0 ? k * N + i : i * N + k);
-                FD += l[i] * sF[ell][dir][v][node];
-            }
-            sJ[ell][fp][v] = Fc[v] - FD;
-        }
-    }
-    __syncthreads();
-    if (e >= m.E) return;
-    const int i = (DIM == 1) ? nd : nd % N;
-    const int j = (DIM == 1) ? 0 : nd / N;
-    const T sx = (T)(2.0 / m.h[e * DIM + 0]);
-    const T sy = (DIM == 2) ? (T)(2.0 / m.h[e * DIM + 1]) : T(0);
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        T dx = T(0);
-#pragma unroll
-        for (int mm = 0; mm < N; mm++) dx += sD[i][mm] * sF[el][0][v][(DIM == 1) ? mm : j * N + mm];
-        dx += sgl[i] * sJ[el][0 * NFPF + j][v] + sgr[i] * sJ[el][1 * NFPF + j][v];
-        T r = -sx * dx;
-        if (DIM == 2) {
-            T dy = T(0);
-#pragma unroll
-            for (int mm = 0; mm < N; mm++) dy += sD[j][mm] * sF[el][DIM - 1][v][mm * N + i];
-            dy += sgl[j] * sJ[el][2 * NFPF + i][v] + sgr[j] * sJ[el][3 * NFPF + i][v];
-            r -= sy * dy;
-        }
-        R[((size_t)v * m.E + e) * NS + nd] = (double)r;
-    }
+    __shared__ kbl_dev::RhsSmem<DIM, N, T, SH::EPB> sm;
+    kbl_dev::rhs_block<DIM, N, T, SH::EPB>(sm, SH::NT, w, wf, m, ops, gamma_d, R, blockIdx.x * SH::EPB, SH::EPB);
 }
 
 template <int DIM, int N>

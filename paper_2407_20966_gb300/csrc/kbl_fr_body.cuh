@@ -1,0 +1,115 @@
+// kbl_fr_body.cuh -- device code of the FR residual, shared by the single-mesh
+// kernel (kbl_fr.cu) and the batched persistent kernel (kbl_batch.cu).
+#pragma once
+
+#include "kbl_internal.cuh"
+
+namespace kbl_dev {
+
+template <int DIM, int N, typename T, int EPB>
+struct RhsSmem {
+    static constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
+    T sF[EPB][DIM][NV][NS];
+    T sJ[EPB][NFP][NV];
+    T sD[N][N], sgl[N], sgr[N], slm[N], slp[N];
+};
+
+// FR residual of elements e0 .. e0+min(EPB, nmax)-1 of one mesh, by a block of NT >= EPB*Ns threads
+// (one per solution point; the others only help with the face loop).
+//   1. states and physical fluxes at the solution points -> shared memory
+//   2. per face point: Rusanov flux of (interior trace, exterior value) minus
+//      the interpolated discontinuous flux -> jump J
+//   3. per solution point and axis: D F + g_L' J_minus + g_R' J_plus,
+//      R = -sum_axes (2 / h_axis) dF/dxi
+// T is the arithmetic type; storage is FP64.  Starts with a barrier so that a
+// block can call it repeatedly.
+template <int DIM, int N, typename T, int EPB>
+__device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, const double* __restrict__ w,
+                                          const double* __restrict__ wf, const MeshDev& m, const FrOps& ops,
+                                          double gamma_d, double* __restrict__ R, int e0, int nmax)
+{
+    constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
+    constexpr int NFPF = (DIM == 1) ? 1 : N;
+    auto& sF = sm.sF;
+    auto& sJ = sm.sJ;
+    auto& sD = sm.sD;
+    auto& sgl = sm.sgl;
+    auto& sgr = sm.sgr;
+    auto& slm = sm.slm;
+    auto& slp = sm.slp;
+    const int tid = threadIdx.x;
+    __syncthreads();
+    for (int i = tid; i < N * N; i += NT) sD[i / N][i % N] = (T)ops.D[i / N][i % N];
+    if (tid < N) {
+        sgl[tid] = (T)ops.gl[tid];
+        sgr[tid] = (T)ops.gr[tid];
+        slm[tid] = (T)ops.lm[tid];
+        slp[tid] = (T)ops.lp[tid];
+    }
+    const int el = tid / NS, nd = tid % NS;
+    const int e = e0 + el;
+    const bool node_thread = el < EPB && el < nmax && e < m.E;
+    const T gamma = (T)gamma_d, gm1 = (T)(gamma_d - 1.0);
+    if (node_thread) {
+        T q[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) q[v] = (T)w[((size_t)v * m.E + e) * NS + nd];
+#pragma unroll
+        for (int dir = 0; dir < DIM; dir++) {
+            T F[NV];
+            kbl_flux<DIM, T>(q, dir, gm1, F);
+#pragma unroll
+            for (int v = 0; v < NV; v++) sF[el][dir][v][nd] = F[v];
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < EPB * NFP; t += NT) {
+        const int ell = t / NFP, fp = t % NFP;
+        const int ee = e0 + ell;
+        if (ee >= m.E || ell >= nmax) continue;
+        const int f = fp / NFPF, k = fp % NFPF, dir = f >> 1, side = f & 1;
+        T qi[NV], qe[NV], Fc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            qi[v] = (T)wf[((size_t)v * m.E + ee) * NFP + fp];
+            qe[v] = (T)kbl_exterior<DIM, N>(wf, m, ee, fp, v);
+        }
+        if (side == 0) kbl_rusanov<DIM, T>(qe, qi, dir, gamma, Fc);
+        else kbl_rusanov<DIM, T>(qi, qe, dir, gamma, Fc);
+        const T* l = side ? slp : slm;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            T FD = T(0);
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const int node = (DIM == 1) ? i : (dir == 0 ? k * N + i : i * N + k);
+                FD += l[i] * sF[ell][dir][v][node];
+            }
+            sJ[ell][fp][v] = Fc[v] - FD;
+        }
+    }
+    __syncthreads();
+    if (!node_thread) return;
+    const int i = (DIM == 1) ? nd : nd % N;
+    const int j = (DIM == 1) ? 0 : nd / N;
+    const T sx = (T)(2.0 / m.h[e * DIM + 0]);
+    const T sy = (DIM == 2) ? (T)(2.0 / m.h[e * DIM + 1]) : T(0);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        T dx = T(0);
+#pragma unroll
+        for (int mm = 0; mm < N; mm++) dx += sD[i][mm] * sF[el][0][v][(DIM == 1) ? mm : j * N + mm];
+        dx += sgl[i] * sJ[el][0 * NFPF + j][v] + sgr[i] * sJ[el][1 * NFPF + j][v];
+        T r = -sx * dx;
+        if (DIM == 2) {
+            T dy = T(0);
+#pragma unroll
+            for (int mm = 0; mm < N; mm++) dy += sD[j][mm] * sF[el][DIM - 1][v][mm * N + i];
+            dy += sgl[j] * sJ[el][2 * NFPF + i][v] + sgr[j] * sJ[el][3 * NFPF + i][v];
+            r -= sy * dy;
+        }
+        R[((size_t)v * m.E + e) * NS + nd] = (double)r;
+    }
+}
+
+}  // namespace kbl_dev

@@ -61,7 +61,8 @@ def mesh_1d(n, x0, x1, periodic=False, bc_left=0, bc_right=1):
 def mesh_2d(nx, ny, x0, x1, y0, y1, periodic=(False, False), bc_of_face=None):
     """Uniform quad mesh, element e = iy * nx + ix.
 
-    ``bc_of_face(ix, iy, f)`` gives the boundary id of a boundary face (default 0).
+    ``bc_of_face(ix, iy, f)`` gives the boundary ids of face f for arrays of element
+    positions (default 0).
     """
     ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
     ix, iy = ix.ravel(), iy.ravel()
@@ -77,8 +78,8 @@ def mesh_2d(nx, ny, x0, x1, y0, y1, periodic=(False, False), bc_of_face=None):
         nb = np.where(inside, jy * nx + jx, 0)
         if bc_of_face is None:
             ids = np.zeros(E, dtype=np.int64)
-        else:
-            ids = np.array([bc_of_face(a, b, f) for a, b in zip(ix, iy)], dtype=np.int64)
+        else:   # vectorised over elements
+            ids = np.broadcast_to(np.asarray(bc_of_face(ix, iy, f), dtype=np.int64), (E,))
         nbr[:, f] = np.where(inside, nb, -(ids + 1))
     hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
     h = np.tile([hx, hy], (E, 1)).astype(np.float64)
@@ -181,9 +182,9 @@ def four_quadrant_states(rng, gamma=GAMMA):
 def four_quadrant(n, states):
     """One four-quadrant Riemann problem on [0, 1]^2 with n x n elements; each boundary face
     takes the state of the quadrant it lies in (Dirichlet)."""
-    def q(ix, iy):
-        return int(ix >= n // 2) + 2 * int(iy >= n // 2)
-    mesh = mesh_2d(n, n, 0.0, 1.0, 0.0, 1.0, bc_of_face=lambda ix, iy, f: q(ix, iy))
+    def q(ix, iy, f=None):
+        return (ix >= n // 2).astype(int) + 2 * (iy >= n // 2).astype(int)
+    mesh = mesh_2d(n, n, 0.0, 1.0, 0.0, 1.0, bc_of_face=q)
     mesh.bc = np.asarray(states, dtype=np.float64)
 
     def ic(x, y):
@@ -238,3 +239,29 @@ def random_discontinuous_field(rng, mesh: CartMesh, xi, gamma=GAMMA, jump=0.5):
     P = (gamma - 1) * (w[-1] - ke_old) * (1 + jump * rng.uniform(-0.5, 0.5, (E, 1)))
     P = P * (1 + 0.2 * rng.uniform(-1, 1, (E, ns)))
     return np.ascontiguousarray(conservative(rho, vel, P, gamma))
+
+
+def four_quadrant_batch(seed, n_problems, n_range=(16, 128), p_range=(1, 4)):
+    """Independent four-quadrant Riemann problems: per problem n ~ U{n_range} (n x n elements,
+    rounded to even), p ~ U{p_range}, quadrant states from four_quadrant_states.  Returns a list
+    of (p, mesh, ic) with Dirichlet boundary states per quadrant."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_problems):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        n += n % 2
+        p = int(rng.integers(p_range[0], p_range[1] + 1))
+        states = four_quadrant_states(rng)
+        mesh, ic = four_quadrant(n, states)
+        out.append((p, mesh, ic))
+    return out
+
+
+def batch_state(problems, nodes_of_p, state_offsets):
+    """Concatenated initial state of a batch: problem i at state_offsets[i], layout [4][E_i][Ns_i];
+    nodes_of_p(p) gives the reference nodes of order p."""
+    w = np.zeros(int(state_offsets[-1]))
+    for i, (p, mesh, ic) in enumerate(problems):
+        a, b = int(state_offsets[i]), int(state_offsets[i + 1])
+        w[a:b] = nodal_field(mesh, nodes_of_p(p), ic).ravel()
+    return w

@@ -74,6 +74,17 @@ _SIGS = {
     "kbl_read_counters": (C.c_int, [_P, C.POINTER(KblCounters)]),
     "kbl_launch_count": (C.c_int64, [_P]),
     "kbl_bounds_noalloc": (C.c_int, [C.POINTER(KblConfig), C.c_int, _P, C.c_int, _P, _P, _P, _P]),
+    "kbl_batch_create": (C.c_int, [C.POINTER(_P), C.POINTER(KblConfig), C.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "kbl_batch_destroy": (C.c_int, [_P]),
+    "kbl_batch_last_error": (C.c_char_p, [_P]),
+    "kbl_batch_layout": (C.c_int, [_P, _P, _P]),
+    "kbl_batch_nodes": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "kbl_batch_step": (C.c_int, [_P, _P, C.c_double]),
+    "kbl_batch_dt": (C.c_int, [_P, _P]),
+    "kbl_batch_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "kbl_batch_tuning": (C.c_int, [_P, _P]),
+    "kbl_batch_check": (C.c_int, [_P]),
+    "kbl_batch_launch_count": (C.c_int64, [_P]),
     "kbl_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "kbl_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
 }
@@ -277,3 +288,90 @@ def bounds_noalloc(cfg: KblConfig, nbr, bc, w, bnd, stream=None):
                                 stream if stream is not None else _current_stream())
     if st != OK:
         raise KblError(st, "bounds_noalloc")
+
+
+class Batch:
+    """Many independent 2D problems advanced together (kbl_batch_*): FP32-mixed, orders 1..4,
+    32 x 32 velocity grid.  meshes: list of (p, nbr[E][4], h[E][2], bc[n_bc][4])."""
+
+    def __init__(self, meshes, stream=None, **overrides):
+        lib = load()
+        cfg = KblConfig()
+        if lib.kbl_config_default(C.byref(cfg), 2, 1) != OK:
+            raise KblError(EINVAL, "config_default")
+        cfg.precision = FP32_MIXED
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.p = np.ascontiguousarray([m[0] for m in meshes], dtype=np.int32)
+        self.n_elem = np.ascontiguousarray([len(m[1]) for m in meshes], dtype=np.int32)
+        nbr = np.ascontiguousarray(np.concatenate([np.asarray(m[1], np.int32).reshape(-1, 4) for m in meshes]))
+        h = np.ascontiguousarray(np.concatenate([np.asarray(m[2], np.float64).reshape(-1, 2) for m in meshes]))
+        nbc = np.ascontiguousarray([len(m[3]) for m in meshes], dtype=np.int32)
+        bcs = [np.asarray(m[3], np.float64).reshape(-1, 4) for m in meshes]
+        bc = np.ascontiguousarray(np.concatenate(bcs) if sum(len(b) for b in bcs) else np.zeros((1, 4)))
+        hnd = C.c_void_p()
+        s = stream if stream is not None else _current_stream()
+        st = lib.kbl_batch_create(C.byref(hnd), C.byref(cfg), len(meshes), self.p.ctypes.data_as(C.c_void_p),
+                                  self.n_elem.ctypes.data_as(C.c_void_p), nbr.ctypes.data_as(C.c_void_p),
+                                  h.ctypes.data_as(C.c_void_p), nbc.ctypes.data_as(C.c_void_p),
+                                  bc.ctypes.data_as(C.c_void_p), s)
+        if st != OK:
+            raise KblError(st, "batch_create")
+        self._h, self._lib, self.P = hnd, lib, len(meshes)
+        so = np.zeros(self.P + 1, np.int64)
+        eo = np.zeros(self.P + 1, np.int64)
+        self._check(lib.kbl_batch_layout(hnd, so.ctypes.data_as(C.c_void_p), eo.ctypes.data_as(C.c_void_p)),
+                    "layout")
+        self.state_offsets, self.elem_offsets = so, eo
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self._lib.kbl_batch_last_error(self._h)
+            raise KblError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kbl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nodes(self, p):
+        out = np.zeros(p + 1)
+        self._check(self._lib.kbl_batch_nodes(self._h, p, out.ctypes.data_as(C.c_void_p), p + 1), "nodes")
+        return out
+
+    def state_view(self, w, i):
+        """Problem i's block of the concatenated state as [4][E_i][(p_i+1)^2] (a view)."""
+        a, b = int(self.state_offsets[i]), int(self.state_offsets[i + 1])
+        return w[a:b].reshape(4, int(self.n_elem[i]), (int(self.p[i]) + 1) ** 2)
+
+    def step(self, w, cfl):
+        self._check(self._lib.kbl_batch_step(self._h, _dev(w, "w"), float(cfl)), "batch_step")
+
+    def dt(self):
+        out = np.zeros(self.P)
+        self._check(self._lib.kbl_batch_dt(self._h, out.ctypes.data_as(C.c_void_p)), "batch_dt")
+        return out
+
+    def autotune(self, w):
+        ms = C.c_double()
+        self._check(self._lib.kbl_batch_autotune(self._h, _dev(w, "w"), C.byref(ms)), "batch_autotune")
+        return ms.value
+
+    def tuning(self):
+        out = np.zeros(4, np.int32)
+        self._check(self._lib.kbl_batch_tuning(self._h, out.ctypes.data_as(C.c_void_p)), "batch_tuning")
+        return {"tile": int(out[0]), "elements_per_item": int(out[1]), "blocks_per_sm": int(out[2]),
+                "items": int(out[3])}
+
+    def check(self):
+        self._check(self._lib.kbl_batch_check(self._h), "batch_check")
+
+    def launch_count(self):
+        return int(self._lib.kbl_batch_launch_count(self._h))
