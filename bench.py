@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod"])
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod", "batched"])
+    ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -304,15 +305,117 @@ def oracle_sample(wl, budget_s=12.0):
             "sample": f"{n} SSP-RK3 steps on a {desc} ({om.n_elem} elements), {el:.1f} s"}
 
 
+def oracle_batch_sample(probs, budget_s=12.0):
+    """The FP64 CPU checker on the first problems of the batch (whole problems, one core)."""
+    import oracle as orc
+    from paper_2407_20966_gb300 import inputs
+    orc.build()
+    n_el, steps, t0 = 0, 0, time.perf_counter()
+    done = []
+    for p, m, ic in probs:
+        cfg = orc.Config(dim=2, p=p, nu=(32, 32))
+        om = orc.Mesh(m.nbr, m.h, m.bc)
+        xi, _ = orc.gauss_legendre(p + 1)
+        w = inputs.nodal_field(m, xi, ic)
+        w, _ = orc.ssprk3_step(cfg, om, w, orc.dt(cfg, om, w, 0.05))
+        n_el += m.n_elem
+        steps += 1
+        done.append(f"{m.n[0]}x{m.n[1]} P{p}")
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n_el * 3 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one SSP-RK3 step of the first {steps} batch problems ({', '.join(done)}), {el:.1f} s"}
+
+
 def run_reference(args, rank):
-    wl = workload(args.workload)
     budget = max(5.0, min(60.0, 4.0 * (args.steps + args.warmup)))
-    cb = oracle_sample(wl, budget_s=budget)
+    if args.workload == "batched":
+        from paper_2407_20966_gb300 import inputs
+        probs = inputs.four_quadrant_batch(0x5EED, args.batch_problems)
+        cb = oracle_batch_sample(probs, budget_s=budget)
+        wl = {"name": f"batched: {args.batch_problems} four-quadrant Riemann problems (CPU sample)"}
+    else:
+        wl = workload(args.workload)
+        cb = oracle_sample(wl, budget_s=budget)
     return {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl["name"]}, "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_batched(args, rank, world):
+    """The batched form: 4096 independent four-quadrant problems (seed 0x5EED), n x n elements with
+    n ~ U{16..128}, orders P1..P4, 32 x 32 velocity grid, FP32-mixed, one persistent launch per
+    phase, one graph per step, launch shape from the autotuner."""
+    import torch
+    from paper_2407_20966_gb300 import build, inputs, kbl
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    probs = inputs.four_quadrant_batch(0x5EED, args.batch_problems)
+    b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs])
+    E = int(b.elem_offsets[-1])
+    w0 = inputs.batch_state(probs, b.nodes, b.state_offsets)
+    wd = torch.from_numpy(w0).to(dev)
+    tune_ms, tune_cmp = b.autotune(wd, with_cmp=True)
+    cfl = 0.05   # below the DG / SSP-RK3 limit of about 1 / (2p + 1) for every order in the batch
+    for _ in range(max(1, args.warmup)):
+        b.step(wd, cfl)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    l0 = b.launch_count()
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(dev.index) as clk:
+        for k in range(K):
+            evs[k][0].record(stream)
+            b.step(wd, cfl)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    b.check()
+    launches = b.launch_count() - l0
+    ms = sum(a.elapsed_time(c) for a, c in evs)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = E * 3 * K * world / (ms * 1e-3)
+    # end to end: per step, H2D of the state from pinned memory, one step, D2H
+    w_pin = torch.from_numpy(w0).pin_memory()
+    out_pin = torch.empty_like(w_pin).pin_memory()
+    ke = max(2, min(K, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        wd.copy_(w_pin, non_blocking=True)
+        b.step(wd, cfl)
+        out_pin.copy_(wd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    peak = CMP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = tune_cmp / (tune_ms * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched: {b.P} four-quadrant Riemann problems, n x n elements n~U[16,128], "
+                                   f"P1..P4, 32x32 velocity grid, FP32-mixed, persistent launches + graph",
+                       "elements": E, "problems": b.P, "stages_per_step": 3, "tuning": b.tuning(),
+                       "l2": "state (%.1f GB) larger than L2" % (w0.nbytes / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": E * 3 * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": w0.nbytes,
+                    "d2h_bytes_per_step": w0.nbytes},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcmp/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_batch_bounds",
+                         "measured_on": "autotune sample (every 8th work item), best launch shape",
+                         "peak_source": "152 SMs x 2070 MHz x 64 three-input FMNMX/clk/SM x 2 comparisons"},
+            "clocks": clk.summary()}
+    return line, probs, b
 
 
 def main():
@@ -327,11 +430,18 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    line, w0, wl = run_ours(args, rank, world)
-    if rank == 0:
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = oracle_sample(wl, budget_s=12.0)
-        print(json.dumps(line), flush=True)
+    if args.workload == "batched":
+        line, probs, _ = run_batched(args, rank, world)
+        if rank == 0:
+            if not args.no_cpu_baseline:
+                line["cpu_baseline"] = oracle_batch_sample(probs, budget_s=12.0)
+            print(json.dumps(line), flush=True)
+    else:
+        line, w0, wl = run_ours(args, rank, world)
+        if rank == 0:
+            if not args.no_cpu_baseline:
+                line["cpu_baseline"] = oracle_sample(wl, budget_s=12.0)
+            print(json.dumps(line), flush=True)
     if world > 1:
         import torch
         torch.distributed.barrier()

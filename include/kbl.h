@@ -216,9 +216,11 @@ kbl_status kbl_batch_step(kbl_batch* b, double* w, double cfl);
 kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host);
 /* Time the bounds phase on state w for every combination of thread tile
  * (4x4 / 4x2 velocity nodes per thread), elements per work item and resident
- * blocks per SM, on a fixed sample of the work items, and keep the fastest.
- * Synchronous.  out_ms (may be NULL) receives the best time of the sample. */
-kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms);
+ * blocks per SM, on a fixed sample of the work items (every eighth), and keep
+ * the fastest.  Synchronous.  out_ms (may be NULL) receives the best time of
+ * the sample, out_cmp (may be NULL) the envelope comparisons the sample needs
+ * (4 |S| N_u per element). */
+kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, double* out_cmp);
 /* Current launch shape: [tile, elements per item, blocks per SM, items]. */
 kbl_status kbl_batch_tuning(const kbl_batch* b, int32_t* out4);
 kbl_status kbl_batch_check(kbl_batch* b);

@@ -693,7 +693,7 @@ kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host)
     return e == cudaSuccess ? KBL_OK : bfail(b, KBL_ECUDA, cudaGetErrorString(e));
 }
 
-kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms)
+kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, double* out_cmp)
 {
     if (!b || !w) return KBL_EINVAL;
     // traces of w once, then time the bounds phase on every eighth work item
@@ -706,7 +706,7 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    double best_ms = 1e30;
+    double best_ms = 1e30, best_cmp = 0.0;
     int best[3] = {b->tile, b->chunk, b->blocks_per_sm};
     const int chunks[] = {4, 16, 64};
     for (int tile = 0; tile < 2; tile++) {
@@ -714,7 +714,12 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms)
         const int pers[] = {maxb, std::max(1, (3 * maxb) / 4), std::max(1, maxb / 2)};
         for (int ci = 0; ci < 3; ci++) {
             std::vector<WorkItem> all = make_items(b->probs, chunks[ci]), sample;
-            for (size_t i = 0; i < all.size(); i += 8) sample.push_back(all[i]);
+            double cmp = 0.0;
+            for (size_t i = 0; i < all.size(); i += 8) {
+                sample.push_back(all[i]);
+                const int n = b->probs[all[i].prob].p + 1;
+                cmp += 4.0 * (n * n + 8 * n) * (double)(NX_B * NX_B) * all[i].n;
+            }
             WorkItem* d_sample = nullptr;
             int n_sample = 0;
             if (upload_items(b, sample, &d_sample, &n_sample) != cudaSuccess) {
@@ -738,6 +743,7 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms)
                 }
                 if (ms < best_ms) {
                     best_ms = ms;
+                    best_cmp = cmp;
                     best[0] = tile;
                     best[1] = chunks[ci];
                     best[2] = pers[pi];
@@ -752,6 +758,7 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms)
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
     if (out_ms) *out_ms = best_ms;
+    if (out_cmp) *out_cmp = best_cmp;
     return KBL_OK;
 }
 

@@ -81,7 +81,7 @@ _SIGS = {
     "kbl_batch_nodes": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "kbl_batch_step": (C.c_int, [_P, _P, C.c_double]),
     "kbl_batch_dt": (C.c_int, [_P, _P]),
-    "kbl_batch_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "kbl_batch_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "kbl_batch_tuning": (C.c_int, [_P, _P]),
     "kbl_batch_check": (C.c_int, [_P]),
     "kbl_batch_launch_count": (C.c_int64, [_P]),
@@ -359,10 +359,11 @@ class Batch:
         self._check(self._lib.kbl_batch_dt(self._h, out.ctypes.data_as(C.c_void_p)), "batch_dt")
         return out
 
-    def autotune(self, w):
-        ms = C.c_double()
-        self._check(self._lib.kbl_batch_autotune(self._h, _dev(w, "w"), C.byref(ms)), "batch_autotune")
-        return ms.value
+    def autotune(self, w, with_cmp=False):
+        ms, cmp = C.c_double(), C.c_double()
+        self._check(self._lib.kbl_batch_autotune(self._h, _dev(w, "w"), C.byref(ms), C.byref(cmp)),
+                    "batch_autotune")
+        return (ms.value, cmp.value) if with_cmp else ms.value
 
     def tuning(self):
         out = np.zeros(4, np.int32)

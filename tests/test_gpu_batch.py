@@ -100,7 +100,8 @@ def test_batch_autotune_keeps_results():
     wd = torch.from_numpy(w0).cuda()
     b.step(wd, 0.2)
     first = wd.cpu().numpy()
-    ms = b.autotune(torch.from_numpy(w0).cuda())
+    ms, cmp = b.autotune(torch.from_numpy(w0).cuda(), with_cmp=True)
+    assert cmp > 0
     t = b.tuning()
     assert ms > 0 and t["tile"] in (0, 1) and t["elements_per_item"] in (4, 16, 64) and t["blocks_per_sm"] >= 1
     wd2 = torch.from_numpy(w0).cuda()
