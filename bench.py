@@ -141,6 +141,25 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# replicas: the slowest rank's time defines the job's time
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms, device=None):
+    """Max of a per-rank time over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ms_max, world):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world):
@@ -195,12 +214,8 @@ def run_ours(args, rank, world):
     with ClockSampler(dev.index) as clk:
         ms, launches = timed_steps(ctx, w_dev, args.steps, args.warmup)
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    units = E * 3 * args.steps * world
-    value = units / (ms * 1e-3)
+    ms = max_over_ranks(ms, dev)
+    value = job_throughput(E * 3 * args.steps, ms, world)
 
     # dominant kernel: the bounds kernel, timed per launch with events on the launching
     # stream, same workload and launch configuration as inside the step
@@ -379,12 +394,8 @@ def run_batched(args, rank, world):
         torch.cuda.synchronize()
     b.check()
     launches = b.launch_count() - l0
-    ms = sum(a.elapsed_time(c) for a, c in evs)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = E * 3 * K * world / (ms * 1e-3)
+    ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in evs), dev)
+    value = job_throughput(E * 3 * K, ms, world)
     # end to end: per step, H2D of the state from pinned memory, one step, D2H
     w_pin = torch.from_numpy(w0).pin_memory()
     out_pin = torch.empty_like(w_pin).pin_memory()

@@ -164,7 +164,7 @@ def sedov(n=512, gamma=GAMMA, rho0=1.0, p_amb=1e-6, e_total=1.0, L=1.2):
     def ic(x, y):
         w = np.broadcast_to(amb[:, None, None], (4,) + x.shape).copy()
         hot = conservative(rho0, [0.0, 0.0], p_c, gamma)
-        w[:, centre, :] = hot[:, None]
+        w[:, centre, :] = hot[:, None, None]
         return w
     return mesh, ic
 

@@ -1,0 +1,166 @@
+"""GPU checks at the benchmark workloads' full sizes, in the launch configuration bench.py times.
+
+The checker computes sampled elements one by one (gathering each stencil from its own traces).
+* vortex, 128^2 P3, 32^2 grid: FP32 bound error per moment; no clipping of the smooth flow
+* Sedov-type blast, 512^2 P2: sampled FP64 / FP32 bounds; positivity and conservation under
+  many limited steps (the extreme-ratio stress)
+* Sod, 200 P3, 64 points: the full run to t = 0.2 (Sec. 6.1) against the checker and the exact
+  Riemann solution
+"""
+import numpy as np
+import pytest
+
+from paper_2407_20966_gb300 import inputs
+from tests.gpu_helpers import TOL_FP32, TOL_FP64, bounds_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_20966_gb300 import build
+    build.build()
+
+
+def _sampled_bounds(orc, ctx, cfg, mesh, w, n_sample=160, seed=0):
+    import torch
+    om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+    wf = orc.traces(cfg, om, w)
+    bnd = torch.zeros((2, cfg.nv, mesh.n_elem), dtype=torch.float64, device="cuda")
+    ctx.bounds(torch.from_numpy(w).cuda(), torch.from_numpy(wf).cuda(), bnd)
+    ctx.check()
+    got = bnd.cpu().numpy()
+    idx = np.random.default_rng(seed).choice(mesh.n_elem, n_sample, replace=False)
+    ref = np.zeros((2, cfg.nv, n_sample))
+    for k, e in enumerate(idx):
+        lo, hi = orc.bounds_stencil(cfg, orc.gather_stencil(cfg, om, w, wf, int(e)))
+        ref[0, :, k], ref[1, :, k] = lo, hi
+    return bounds_error(got[:, :, idx], ref)
+
+
+def test_vortex_fp32_bound_error_per_moment(orc):
+    from paper_2407_20966_gb300 import kbl
+    mesh, ic = inputs.isentropic_vortex(128)
+    ctx = kbl.Context(dim=2, p=3, nu=(32, 32), precision=kbl.FP32_MIXED)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    w = inputs.nodal_field(mesh, ctx.operator(kbl.OP_NODES), ic)
+    cfg = orc.Config(dim=2, p=3, nu=(32, 32))
+    err = _sampled_bounds(orc, ctx, cfg, mesh, w)
+    per_moment = {name: float(err[:, k].max()) for k, name in enumerate(("rho", "m_x", "m_y", "E"))}
+    print("vortex FP32 bound error per moment (max over lower/upper, 160 sampled elements):", per_moment)
+    assert max(per_moment.values()) < TOL_FP32
+
+
+def test_vortex_smooth_flow_is_not_clipped(orc):
+    """Sec. 6.2's claim in 2D: in a smooth flow the kinetic bounds leave the solution alone."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    mesh, ic = inputs.isentropic_vortex(128)
+    ctx = kbl.Context(dim=2, p=3, nu=(32, 32), precision=kbl.FP32_MIXED)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    wd = torch.from_numpy(inputs.nodal_field(mesh, ctx.operator(kbl.OP_NODES), ic)).cuda()
+    ctx.set_time(0.0)
+    ctx.counters()
+    for _ in range(5):
+        ctx.step(wd, 0.05)
+    st, c = ctx.counters()
+    print("vortex, 5 steps at CFL 0.05: limited element-stages", c["limited_elements"], "of", 15 * mesh.n_elem)
+    assert st == kbl.OK
+    assert c["limited_elements"] == 0
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_FP32)])
+def test_sedov_sampled_bounds(orc, precision, tol):
+    from paper_2407_20966_gb300 import kbl
+    mesh, ic = inputs.sedov(512)
+    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=precision)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    xi = ctx.operator(kbl.OP_NODES)
+    w = inputs.nodal_field(mesh, xi, ic)
+    # sample around the blast as well as in the ambient gas
+    cfg = orc.Config(dim=2, p=2, nu=(32, 32))
+    err = _sampled_bounds(orc, ctx, cfg, mesh, w, n_sample=96, seed=precision)
+    assert err.max() < tol
+    centre = [255 * 512 + 255, 256 * 512 + 256, 255 * 512 + 257, 254 * 512 + 256]
+    import torch
+    om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+    wf = orc.traces(cfg, om, w)
+    bnd = torch.zeros((2, 4, mesh.n_elem), dtype=torch.float64, device="cuda")
+    ctx.bounds(torch.from_numpy(w).cuda(), torch.from_numpy(wf).cuda(), bnd)
+    got = bnd.cpu().numpy()[:, :, centre]
+    ref = np.zeros_like(got)
+    for k, e in enumerate(centre):
+        ref[0, :, k], ref[1, :, k] = orc.bounds_stencil(cfg, orc.gather_stencil(cfg, om, w, wf, e))
+    assert bounds_error(got, ref).max() < tol
+
+
+@pytest.mark.parametrize("precision,cons_tol", [(1, 1e-7), (0, 1e-12)])
+def test_sedov_positivity_and_conservation_under_limiting(precision, cons_tol):
+    """Extreme pressure ratio (4.5e3 / 1e-6): 40 steps stay physical, the pressure stays above the
+    floor at every solution point, and mass and energy are conserved (the blast has not reached
+    the boundary).  The limiter keeps element means exactly; the FP32-mixed residual conserves to
+    FP32 rounding of its volume terms, the FP64 path to FP64 rounding."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    mesh, ic = inputs.sedov(512)
+    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=precision)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    xi = ctx.operator(kbl.OP_NODES)
+    wq = ctx.operator(kbl.OP_WEIGHTS)
+    w = inputs.nodal_field(mesh, xi, ic)
+    W = np.outer(wq, wq).ravel() * (mesh.h[0, 0] * mesh.h[0, 1] / 4)
+    mass0, energy0 = (w[0] * W).sum(), (w[3] * W).sum()
+    wd = torch.from_numpy(w).cuda()
+    ctx.set_time(0.0)
+    ctx.counters()
+    for _ in range(40):
+        ctx.step(wd, 0.05)
+    st, c = ctx.counters()
+    assert st == kbl.OK and c["nonphysical"] == 0
+    assert c["limited_elements"] > 0
+    w1 = wd.cpu().numpy()
+    P = 0.4 * (w1[3] - 0.5 * (w1[1] ** 2 + w1[2] ** 2) / w1[0])
+    assert w1[0].min() > 0 and P.min() >= 1e-12 * (1 - 1e-9)
+    assert (w1[0] * W).sum() == pytest.approx(mass0, rel=cons_tol)
+    assert (w1[3] * W).sum() == pytest.approx(energy0, rel=cons_tol)
+    print(f"Sedov 512^2 P2, 40 steps, precision {precision}: limited element-stages", c["limited_elements"],
+          "pressure re-limits", c["pressure_relimits"], "min P", P.min(),
+          "mass drift", (w1[0] * W).sum() / mass0 - 1, "energy drift", (w1[3] * W).sum() / energy0 - 1)
+
+
+def test_sod_full_run_matches_checker(orc):
+    """The whole Sod run (Sec. 6.1 set-up, t = 0.2) on the device against the checker: the same
+    number of steps, the same end state to 1e-9, and the same L1 error against the exact
+    solution."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    from tests import riemann_exact
+    mesh, ic = inputs.sod(200)
+    ctx = kbl.Context(dim=1, p=3, nu=(64,), precision=kbl.FP64)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    cfg = orc.Config(dim=1, p=3, nu=(64,))
+    om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+    xi, _ = orc.gauss_legendre(4)
+    w = inputs.nodal_field(mesh, xi, ic)
+    ref, t, n = w.copy(), 0.0, 0
+    while t < 0.2 - 1e-14:
+        dt = min(orc.dt(cfg, om, ref, 0.1), 0.2 - t)
+        ref, _ = orc.ssprk3_step(cfg, om, ref, dt)
+        t += dt
+        n += 1
+    wd = torch.from_numpy(w).cuda()
+    ctx.set_time(0.0, 0.2)
+    for _ in range(n):
+        ctx.step(wd, 0.1)
+    assert ctx.time() == pytest.approx(0.2, rel=1e-12)
+    got = wd.cpu().numpy()
+    x = inputs.node_coords(mesh, xi)[0].ravel()
+    exact = riemann_exact.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), x, 0.2)
+    l1_gpu = np.abs(got[0].ravel() - exact[0]).mean()
+    l1_ref = np.abs(ref[0].ravel() - exact[0]).mean()
+    print(f"Sod, {n} steps: L1(rho) device {l1_gpu:.6e}, checker {l1_ref:.6e}, paper 1.181e-3 (HLLC, 2048 pts)")
+    assert l1_gpu == pytest.approx(l1_ref, rel=1e-8)
+    assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
