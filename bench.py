@@ -36,6 +36,10 @@ SM_MAX_MHZ = 2070.0
 # FP32 min/max: 64 three-input FMNMX instructions per clock per SM (measured), each
 # two comparisons -> 128 comparisons per clock per SM.
 CMP_PER_CLK_SM = 128.0
+# DRAM bytes (read + write) of one launch of the FP32 2D bounds kernel on the vortex workload,
+# from the ncu capture summarised in profiles/bounds_f32_vortex128_p3.md.  Must be reset to
+# None whenever that kernel changes, until it is captured again.
+BOUNDS_F32_VORTEX_TRAFFIC = 17068800 + 0
 
 
 def parse():
@@ -238,8 +242,10 @@ def run_ours(args, rank, world):
     cmp_per_launch = 4.0 * nS * NU * E           # min and max of g and of C g per (state, node)
     achieved = cmp_per_launch / (bounds_ms * 1e-3) / 1e12
     peak = CMP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = BOUNDS_F32_VORTEX_TRAFFIC if (args.workload == "vortex" and precision == kbl.FP32_MIXED
+                                             and args.bounds_tile <= 0) else None
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcmp/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_bounds2d_f32" if (
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": "k_bounds2d_f32" if (
                     wl["dim"] == 2 and precision == kbl.FP32_MIXED) else "bounds",
                 "bounds_ms_per_launch": round(bounds_ms, 4),
                 "peak_source": "152 SMs x 2070 MHz x 64 three-input FMNMX/clk/SM x 2 comparisons"}
