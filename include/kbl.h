@@ -226,6 +226,78 @@ kbl_status kbl_batch_tuning(const kbl_batch* b, int32_t* out4);
 kbl_status kbl_batch_check(kbl_batch* b);
 int64_t kbl_batch_launch_count(const kbl_batch* b);
 
+/* ---- Reverse mode (adjoint) --------------------------------------------------
+ * Hand-written vector-Jacobian products of the 2D path (FP64, any precision of
+ * the context for the *_vjp calls; the step adjoints need a KBL_FP64 context).
+ * Each *_vjp call takes the forward inputs and the cotangent of the forward
+ * output and ADDS the cotangents of the inputs into caller-owned device arrays
+ * (exceptions are stated).  Where the method takes a min or a max (the envelopes
+ * of Eq. 32, the box of Eq. 45, the extrema over V and P_min of Eq. 47, the
+ * Davis wavespeed of the Rusanov flux) the first element of the set in its
+ * natural order wins ties and receives the whole cotangent (stencil order of
+ * this header; V order = solution points then face points; components in
+ * order).  In Eq. 37 the 1 wins ties over the upper ratio, which wins over the
+ * lower one; in Eq. 39 the lowest component wins.  The epsilon rule under
+ * Eq. 37, the density floor of Sec. 3.8 (ties included), alpha_P = 0 and the
+ * sign split of the momentum sums (Eq. 35-36) contribute no derivative.
+ *
+ * Trace cotangents come in two arrays of the traces' layout: wfb[v][e][fp]
+ * for the use of e's own trace, wfb_ext[v][e][fp] for its use as the exterior
+ * value of the neighbour across that face.  The cotangent of wf is their sum;
+ * boundary states get none. */
+
+/* wb += cotangent of w through wf = traces(w): transposed interpolation of
+ * wfb (+ wfb_ext, which may be NULL). */
+kbl_status kbl_traces_vjp(kbl_ctx* ctx, const double* wfb, const double* wfb_ext, double* wb);
+
+/* Residual R = rhs(w, wf) of kbl_rhs: given Rb, wb += (dR/dw)^T Rb,
+ * wfb / wfb_ext += (dR/dwf)^T Rb.  Ties of the Rusanov wavespeed (s_L = s_R)
+ * take the minus-side state; |u| at u = 0 takes the + branch. */
+kbl_status kbl_rhs_vjp(kbl_ctx* ctx, const double* w, const double* wf, const double* Rb,
+                       double* wb, double* wfb, double* wfb_ext);
+
+/* Bounds bnd = bounds(w, wf) of kbl_bounds (FP64 arithmetic whatever the
+ * context's precision): given bndb[2][nv][E], adds the cotangents of the
+ * stencil states.  bnd must hold the forward result (it decides the density
+ * floor).  Elements with a non-physical stencil raise the flag and add
+ * nothing. */
+kbl_status kbl_bounds_vjp(kbl_ctx* ctx, const double* w, const double* wf, const double* bnd,
+                          const double* bndb, double* wb, double* wfb, double* wfb_ext);
+
+/* Stage s of kbl_stage with dt given on the host: out = limit(a_s wn + b_s (ws
+ * + dt R), bnd).  Given ob (cotangent of out): wnb = a_s g (or wnb += a_s g when
+ * accumulate_wn != 0), wsb = b_s g, Rb = b_s dt g, where g is the cotangent of
+ * the combined state; bndb[2][nv][E] = cotangent of bnd.  wsb, Rb, bndb are
+ * overwritten; ob must not alias any output.  dt itself is held fixed. */
+kbl_status kbl_stage_vjp(kbl_ctx* ctx, int s, double dt, const double* wn, const double* ws,
+                         const double* R, const double* bnd, const double* ob, int accumulate_wn,
+                         double* wnb, double* wsb, double* Rb, double* bndb);
+
+/* Integrated physical entropy (s = P rho^-gamma, Sec. 6) of w:
+ * J = sum_e |J_e| sum_n W_n P rho^-gamma with the Gauss-Legendre weights, written
+ * to the device scalar J_dev (fixed summation order: deterministic).
+ * kbl_entropy_vjp: wb = Jb dJ/dw (overwritten). */
+kbl_status kbl_entropy(kbl_ctx* ctx, const double* w, double* J_dev);
+kbl_status kbl_entropy_vjp(kbl_ctx* ctx, const double* w, double Jb, double* wb);
+
+/* One time step with a given dt (no CFL rule, no end-time clip; the context's
+ * time is not advanced): the three stages of kbl_step. */
+kbl_status kbl_step_fixed(kbl_ctx* ctx, double* w, double dt);
+
+/* Reverse of kbl_step_fixed(w, dt): on entry wbar is the cotangent of the
+ * step's output, on exit the cotangent of w (w itself is not changed).  The
+ * stage inputs, traces, bounds and residuals are recomputed from w and kept in
+ * the context's adjoint scratch (about 9 states; allocated on first use). */
+kbl_status kbl_adjoint_step(kbl_ctx* ctx, const double* w, double dt, double* wbar);
+
+/* Reverse of n fixed-dt steps from w0 (dts: host array of n): recomputes and
+ * keeps the n-1 intermediate states (n-1 more states of scratch), then runs
+ * kbl_adjoint_step backwards.  wbar: cotangent of the final state in, of w0
+ * out.  The unit of checkpointed reverse mode: a caller that keeps every K-th
+ * state of a long run calls this once per segment of K steps. */
+kbl_status kbl_adjoint_segment(kbl_ctx* ctx, const double* w0, const double* dts, int n,
+                               double* wbar);
+
 /* Element bounds without any device allocation.  The paper has no
  * counterpart to this call; it exists for callers that cannot call
  * cudaMalloc: applications that hand all device memory to their own pool at

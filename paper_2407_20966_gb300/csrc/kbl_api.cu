@@ -150,6 +150,7 @@ void free_mesh(kbl_ctx* c)
     }
     if (c->d_nbr) cudaFree(c->d_nbr);
     c->d_nbr = nullptr;
+    kbl_adjoint_release(c);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
     c->graph_w = nullptr;

@@ -75,7 +75,15 @@ struct kbl_ctx {
     double* graph_w = nullptr;
     double graph_cfl = 0.0;
     int graph_kernels = 0;
+    // adjoint scratch (kbl_adjoint.cu), grown on demand
+    double* d_adj = nullptr;
+    size_t adj_cap = 0;
+    double* d_ent = nullptr;
+    size_t ent_cap = 0;
 };
+
+// Frees the adjoint scratch of a context (kbl_adjoint.cu).
+void kbl_adjoint_release(kbl_ctx* c);
 
 MeshDev mesh_of(const kbl_ctx* c);
 

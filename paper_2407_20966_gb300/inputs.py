@@ -193,6 +193,46 @@ def four_quadrant(n, states):
     return mesh, ic
 
 
+def shock_vortex(n, gamma=GAMMA, mach=1.1, beta=0.5, radius=0.05, centre=(0.35, 0.5), shock_x=0.5):
+    """Shock-vortex interaction on [0, 1]^2 with n x n elements (n even): a stationary normal
+    shock at x = shock_x (an element boundary) between the upstream state (rho, u, v, P) =
+    (1, mach sqrt(gamma), 0, 1) and its Rankine-Hugoniot post-shock state, and an isentropic
+    vortex of strength beta and radius `radius` centred upstream at `centre`, convected
+    into the shock by the mean flow.  x faces take the upstream (left) and post-shock
+    (right) states; y is periodic.
+
+    Vortex, with r = |x - centre| / radius: velocity perturbation
+    beta/(2 pi) exp((1 - r^2)/2) (-(y-yc), x-xc) / radius; temperature
+    T = 1 - (gamma-1) beta^2 / (8 gamma pi^2) exp(1 - r^2); rho = T^(1/(gamma-1)), P = rho^gamma.
+    """
+    assert n % 2 == 0
+    m2 = mach * mach
+    c1 = math.sqrt(gamma)
+    u1 = mach * c1
+    rho2 = (gamma + 1) * m2 / ((gamma - 1) * m2 + 2)
+    p2 = 1 + 2 * gamma / (gamma + 1) * (m2 - 1)
+    u2 = u1 / rho2
+    up = conservative(1.0, [u1, 0.0], 1.0, gamma)
+    down = conservative(rho2, [u2, 0.0], p2, gamma)
+
+    def bc_of_face(ix, iy, f):
+        return np.full(np.shape(ix), 0 if f == 0 else 1)
+    mesh = mesh_2d(n, n, 0.0, 1.0, 0.0, 1.0, periodic=(False, True), bc_of_face=bc_of_face)
+    mesh.bc = np.stack([up, down]).astype(np.float64)
+
+    def ic(x, y):
+        xc = (x - centre[0]) / radius
+        yc = (y - centre[1]) / radius
+        r2 = xc * xc + yc * yc
+        a = beta / (2 * math.pi) * np.exp(0.5 * (1 - r2))
+        T = 1 - (gamma - 1) * beta * beta / (8 * gamma * math.pi ** 2) * np.exp(1 - r2)
+        rho = T ** (1 / (gamma - 1))
+        vort = conservative(rho, [u1 - a * yc, a * xc], rho ** gamma, gamma)
+        post = np.broadcast_to(down.reshape((4,) + (1,) * x.ndim), vort.shape)
+        return np.where(x[None] < shock_x, vort, post)
+    return mesh, ic
+
+
 def nodal_field(mesh: CartMesh, xi, ic):
     """w[nv][E][Ns] = ic evaluated at the solution nodes built from reference nodes xi."""
     return np.ascontiguousarray(ic(*node_coords(mesh, xi)), dtype=np.float64)

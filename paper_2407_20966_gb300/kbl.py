@@ -87,6 +87,15 @@ _SIGS = {
     "kbl_batch_launch_count": (C.c_int64, [_P]),
     "kbl_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "kbl_get_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "kbl_traces_vjp": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_rhs_vjp": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "kbl_bounds_vjp": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "kbl_stage_vjp": (C.c_int, [_P, C.c_int, C.c_double, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P, _P]),
+    "kbl_entropy": (C.c_int, [_P, _P, _P]),
+    "kbl_entropy_vjp": (C.c_int, [_P, _P, C.c_double, _P]),
+    "kbl_step_fixed": (C.c_int, [_P, _P, C.c_double]),
+    "kbl_adjoint_step": (C.c_int, [_P, _P, C.c_double, _P]),
+    "kbl_adjoint_segment": (C.c_int, [_P, _P, _P, C.c_int, _P]),
 }
 
 TUNE_BOUNDS_TILE = 0
@@ -265,6 +274,44 @@ class Context:
         v = C.c_int()
         self._check(self._lib.kbl_get_tuning(self._h, int(key), C.byref(v)), "get_tuning")
         return v.value
+
+    # ---- reverse mode (device tensors; *_vjp add into their outputs) -----
+    def traces_vjp(self, wfb, wfb_ext, wb):
+        self._check(self._lib.kbl_traces_vjp(self._h, _dev(wfb, "wfb"), _dev(wfb_ext), _dev(wb, "wb")),
+                    "traces_vjp")
+
+    def rhs_vjp(self, w, wf, Rb, wb, wfb, wfb_ext):
+        self._check(self._lib.kbl_rhs_vjp(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(Rb, "Rb"), _dev(wb, "wb"),
+                                          _dev(wfb, "wfb"), _dev(wfb_ext, "wfb_ext")), "rhs_vjp")
+
+    def bounds_vjp(self, w, wf, bnd, bndb, wb, wfb, wfb_ext):
+        self._check(self._lib.kbl_bounds_vjp(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(bnd, "bnd"),
+                                             _dev(bndb, "bndb"), _dev(wb, "wb"), _dev(wfb, "wfb"),
+                                             _dev(wfb_ext, "wfb_ext")), "bounds_vjp")
+
+    def stage_vjp(self, s, dt, wn, ws, R, bnd, ob, wnb, wsb, Rb, bndb, accumulate_wn=False):
+        self._check(self._lib.kbl_stage_vjp(self._h, int(s), float(dt), _dev(wn, "wn"), _dev(ws, "ws"), _dev(R, "R"),
+                                            _dev(bnd, "bnd"), _dev(ob, "ob"), int(bool(accumulate_wn)),
+                                            _dev(wnb, "wnb"), _dev(wsb, "wsb"), _dev(Rb, "Rb"), _dev(bndb, "bndb")),
+                    "stage_vjp")
+
+    def entropy(self, w, J_dev):
+        self._check(self._lib.kbl_entropy(self._h, _dev(w, "w"), _dev(J_dev, "J")), "entropy")
+
+    def entropy_vjp(self, w, Jb, wb):
+        self._check(self._lib.kbl_entropy_vjp(self._h, _dev(w, "w"), float(Jb), _dev(wb, "wb")), "entropy_vjp")
+
+    def step_fixed(self, w, dt):
+        self._check(self._lib.kbl_step_fixed(self._h, _dev(w, "w"), float(dt)), "step_fixed")
+
+    def adjoint_step(self, w, dt, wbar):
+        self._check(self._lib.kbl_adjoint_step(self._h, _dev(w, "w"), float(dt), _dev(wbar, "wbar")),
+                    "adjoint_step")
+
+    def adjoint_segment(self, w0, dts, wbar):
+        d, dp = _host(dts, np.float64, "dts")
+        self._check(self._lib.kbl_adjoint_segment(self._h, _dev(w0, "w0"), dp, len(d), _dev(wbar, "wbar")),
+                    "adjoint_segment")
 
 
 def _dev_any(t, dtype_name, name):
