@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod", "batched"])
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod", "batched", "adjoint"])
+    ap.add_argument("--adj-n", type=int, default=256, help="adjoint workload: elements per axis")
+    ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: time steps per gradient")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
@@ -353,6 +355,8 @@ def oracle_batch_sample(probs, budget_s=12.0):
 
 def run_reference(args, rank):
     budget = max(5.0, min(60.0, 4.0 * (args.steps + args.warmup)))
+    if args.workload == "adjoint":
+        return {"impl": "reference", "unavailable": "the FP64 CPU oracle has no reverse mode (forward only)"}
     if args.workload == "batched":
         from paper_2407_20966_gb300 import inputs
         probs = inputs.four_quadrant_batch(0x5EED, args.batch_problems)
@@ -437,6 +441,82 @@ def run_batched(args, rank, world):
     return line, probs, b
 
 
+def run_adjoint(args, rank, world):
+    """Reverse mode: the gradient of the integrated entropy at t_end with respect to the initial
+    state of the shock-vortex problem (n x n P3, 32 x 32 velocity grid, FP64, CFL 0.07) through
+    `adj_steps` limited SSP-RK3 steps, checkpoints every 10 steps.  One timed unit is one whole
+    gradient: the checkpointed forward pass plus the backward pass (segment recomputation and
+    the adjoint kernels).  Warm-up: gradients of 2-step trajectories.  `value` counts the forward
+    element-stages differentiated per second of that whole computation."""
+    import torch
+    from paper_2407_20966_gb300 import adjoint, build, inputs, kbl
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    n, n_steps, every, cfl = args.adj_n, args.adj_steps, 10, 0.07
+    mesh, ic = inputs.shock_vortex(n)
+    ctx = kbl.Context(dim=2, p=3, nu=(32, 32), precision=kbl.FP64, eps_rule=1)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    w0 = inputs.nodal_field(mesh, ctx.operator(kbl.OP_NODES), ic)
+    E = mesh.n_elem
+    wd0 = torch.from_numpy(w0).to(dev)
+    dts = adjoint.cfl_time_steps(ctx, wd0, n_steps, cfl)
+    ctx.counters()
+    w = wd0.clone()
+    for dt in dts:
+        ctx.step_fixed(w, dt)
+    st, cnt = ctx.counters()
+
+    def gradient(steps):
+        x = wd0.clone().requires_grad_(True)
+        J = adjoint.entropy(adjoint.trajectory(x, ctx, steps, checkpoint_every=every), ctx)
+        J.backward()
+        return J.detach(), x.grad
+
+    for _ in range(max(1, args.warmup)):
+        gradient(dts[:2])
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    K = max(1, args.steps)
+    l0 = ctx.launch_count()
+    times = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(K):
+            a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            x = wd0.clone().requires_grad_(True)
+            y = adjoint.trajectory(x, ctx, dts, checkpoint_every=every)
+            J = adjoint.entropy(y, ctx)
+            m.record(stream)
+            J.backward()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append((a.elapsed_time(m), m.elapsed_time(b)))
+    ctx.check()
+    launches = ctx.launch_count() - l0
+    g = x.grad
+    ms = max_over_ranks(sum(f + r for f, r in times), dev)
+    value = job_throughput(E * 3 * n_steps * K, ms, world)
+    fwd = sum(f for f, _ in times) / K
+    bwd = sum(r for _, r in times) / K
+    line = {"metric": METRIC, "value": value, "unit": "differentiated element-stages/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"adjoint: shock-vortex {n}x{n} P3 (Mach 1.1 stationary shock, isentropic "
+                                   f"vortex), 32x32 velocity grid, FP64, CFL {cfl}, gradient of the integrated "
+                                   f"entropy through {n_steps} limited SSP-RK3 steps, checkpoints every {every}",
+                       "elements": E, "time_steps": n_steps, "t_end": float(sum(dts)),
+                       "limited_element_stages": int(cnt["limited_elements"]),
+                       "forward_ms": fwd, "backward_ms": bwd, "J": float(J.item()),
+                       "grad_max_abs": float(g.abs().max().item()),
+                       "l2": "state (%.1f MB) x checkpoints; steps stream through more than L2" % (w0.nbytes / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches,
+            "clocks": clk.summary()}
+    return line, w0, workload("vortex")
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -449,7 +529,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    if args.workload == "batched":
+    if args.workload == "adjoint":
+        line, _, _ = run_adjoint(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+    elif args.workload == "batched":
         line, probs, _ = run_batched(args, rank, world)
         if rank == 0:
             if not args.no_cpu_baseline:

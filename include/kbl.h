@@ -284,19 +284,30 @@ kbl_status kbl_entropy_vjp(kbl_ctx* ctx, const double* w, double Jb, double* wb)
  * time is not advanced): the three stages of kbl_step. */
 kbl_status kbl_step_fixed(kbl_ctx* ctx, double* w, double dt);
 
+/* n steps of kbl_step_fixed in place (dts: host array of n).  With bnd_out
+ * (device, [n][3][2][nv][E]) the bounds of every stage are kept there, for
+ * kbl_adjoint_segment to reuse; may be NULL. */
+kbl_status kbl_forward_segment(kbl_ctx* ctx, double* w, const double* dts, int n, double* bnd_out);
+
 /* Reverse of kbl_step_fixed(w, dt): on entry wbar is the cotangent of the
- * step's output, on exit the cotangent of w (w itself is not changed).  The
- * stage inputs, traces, bounds and residuals are recomputed from w and kept in
- * the context's adjoint scratch (about 9 states; allocated on first use). */
+ * step's output, on exit the cotangent of w (w itself is not changed).  Same as
+ * kbl_adjoint_segment with n = 1. */
 kbl_status kbl_adjoint_step(kbl_ctx* ctx, const double* w, double dt, double* wbar);
 
-/* Reverse of n fixed-dt steps from w0 (dts: host array of n): recomputes and
- * keeps the n-1 intermediate states (n-1 more states of scratch), then runs
- * kbl_adjoint_step backwards.  wbar: cotangent of the final state in, of w0
- * out.  The unit of checkpointed reverse mode: a caller that keeps every K-th
- * state of a long run calls this once per segment of K steps. */
+/* Reverse of n fixed-dt steps from w0 (dts: host array of n).  A forward pass
+ * over the segment keeps, for every step, its input, its stage inputs and each
+ * stage's traces, bounds and residual; the reverse pass then runs the stage,
+ * residual, bounds and trace VJPs backwards through all 3n stages without
+ * recomputing anything.  bnd_in: the stage bounds kept by kbl_forward_segment
+ * over the same steps from the same w0 ([n][3][2][nv][E], device), which the
+ * forward pass then takes instead of recomputing them (the bounds are the
+ * costly part of a stage); NULL to recompute.  wbar: cotangent of the final
+ * state in, of w0 out.  Scratch (context-owned, grown on first use): (6 n + 4)
+ * solution-sized arrays, (3 n + 2) trace-sized and (3 n + 1) bound-sized ones.
+ * The unit of checkpointed reverse mode: a caller that keeps every K-th state of
+ * a long run calls this once per segment of K steps. */
 kbl_status kbl_adjoint_segment(kbl_ctx* ctx, const double* w0, const double* dts, int n,
-                               double* wbar);
+                               const double* bnd_in, double* wbar);
 
 /* Element bounds without any device allocation.  The paper has no
  * counterpart to this call; it exists for callers that cannot call

@@ -6,8 +6,9 @@ only sequences the calls and keeps the checkpoints.
 
 * :func:`trajectory` -- w(t_end) from w0 through fixed time steps ``dts`` (take them
   from :func:`cfl_time_steps`).  Checkpointing: the forward pass keeps every
-  ``checkpoint_every``-th state; the backward pass runs kbl_adjoint_segment once per
-  segment, which recomputes the segment's states and walks them backwards.
+  ``checkpoint_every``-th state (and, by default, every stage's bounds); the backward
+  pass runs kbl_adjoint_segment once per segment, which recomputes the segment's states
+  and walks them backwards.
 * :func:`entropy` -- the integrated physical entropy sum |J_e| W_n P rho^-gamma.
 
 The time steps are held fixed in the derivative (the CFL rule is not differentiated).
@@ -37,31 +38,39 @@ def cfl_time_steps(kctx: "kbl.Context", w0: torch.Tensor, n_steps: int, cfl: flo
 
 class _Trajectory(torch.autograd.Function):
     @staticmethod
-    def forward(fctx, w0, kctx, dts, every):
+    def forward(fctx, w0, kctx, dts, every, keep_bounds):
         w = w0.detach().clone()
-        ckpts = []
-        for k, dt in enumerate(dts):
-            if k % every == 0:
-                ckpts.append(w.clone())
-            kctx.step_fixed(w, dt)
-        fctx.kctx, fctx.dts, fctx.every, fctx.ckpts = kctx, list(dts), every, ckpts
+        n = len(dts)
+        segs = []
+        for a in range(0, n, every):
+            seg = dts[a:a + every]
+            bnd = None
+            if keep_bounds:
+                bnd = torch.empty((len(seg), 3, 2, kctx.nv, kctx.E), dtype=torch.float64, device=w.device)
+            segs.append((w.clone(), seg, bnd))
+            kctx.forward_segment(w, seg, bnd)
+        fctx.kctx, fctx.segs = kctx, segs
         return w
 
     @staticmethod
     def backward(fctx, wbar):
         g = wbar.detach().contiguous().clone()
-        n, K = len(fctx.dts), fctx.every
-        for s in reversed(range(len(fctx.ckpts))):
-            fctx.kctx.adjoint_segment(fctx.ckpts[s], fctx.dts[s * K:min(n, (s + 1) * K)], g)
-        fctx.ckpts = None
-        return g, None, None, None
+        for ckpt, seg, bnd in reversed(fctx.segs):
+            fctx.kctx.adjoint_segment(ckpt, seg, g, bnd)
+        fctx.segs = None
+        return g, None, None, None, None
 
 
-def trajectory(w0: torch.Tensor, kctx: "kbl.Context", dts, checkpoint_every: int = 10) -> torch.Tensor:
-    """The state after len(dts) fixed-dt steps from w0, differentiable in w0."""
+def trajectory(w0: torch.Tensor, kctx: "kbl.Context", dts, checkpoint_every: int = 10,
+               keep_bounds: bool = True) -> torch.Tensor:
+    """The state after len(dts) fixed-dt steps from w0, differentiable in w0.
+
+    Every ``checkpoint_every``-th state is kept; with ``keep_bounds`` the stage bounds of every
+    step are kept too (8 values per element and stage, an eighth of a P3 state), so that the
+    backward pass does not recompute them."""
     if checkpoint_every < 1:
         raise ValueError("checkpoint_every must be >= 1")
-    return _Trajectory.apply(w0, kctx, list(dts), int(checkpoint_every))
+    return _Trajectory.apply(w0, kctx, list(dts), int(checkpoint_every), bool(keep_bounds))
 
 
 class _Entropy(torch.autograd.Function):

@@ -193,6 +193,16 @@ k_bounds2d_vjp(const double* __restrict__ w, const double* __restrict__ wf, cons
     __shared__ int sbad;
 
     const int e = blockIdx.x, tid = threadIdx.x;
+    // an element whose bounds were not used by the limiter (zero cotangent) adds nothing
+    double b0 = 0.0;
+    if (tid < 8) {
+        const int v = tid & 3, up = tid >> 2;
+        b0 = bndb[((size_t)up * NV + v) * m.E + e];
+        // rho_min = max(raw, rho_floor): the floor branch (ties included) has no derivative
+        if (tid == 0 && bnd[e] <= ph.rho_floor) b0 = 0.0;
+        sB[tid] = b0;
+    }
+    if (!__syncthreads_or(b0 != 0.0)) return;
     if (tid == 0) sbad = 0;
     gather_states<2, N, NT>(w, wf, m, e, sS);
     __syncthreads();
@@ -214,13 +224,6 @@ k_bounds2d_vjp(const double* __restrict__ w, const double* __restrict__ wf, cons
         s.C = 0.5 * delta * s.th;
         sP[i] = s;
         snode[i][0] = snode[i][1] = snode[i][2] = snode[i][3] = 0.0;
-    }
-    if (tid < 8) {
-        const int v = tid & 3, up = tid >> 2;
-        double b = bndb[((size_t)up * NV + v) * m.E + e];
-        // rho_min = max(raw, rho_floor): the floor branch (ties included) has no derivative
-        if (tid == 0 && bnd[e] <= ph.rho_floor) b = 0.0;
-        sB[tid] = b;
     }
     __syncthreads();
     if (sbad) {
@@ -844,10 +847,15 @@ int run_entropy_vjp(const kbl_ctx* c, const double* w, double Jb, double* wb, cu
 
 bool adj_ok(const kbl_ctx* c) { return c && c->mesh_ready && c->cfg.dim == 2; }
 
-// Scratch of the adjoint (grown on demand): see adj_layout.
+// Scratch of the adjoint (grown on demand).  Fixed part: the cotangent buffers of one
+// step.  Per step of a segment: its input state, the inputs of stages 1 and 2, and the
+// traces, bounds and residual of all three stages, kept by the forward pass of the
+// segment so that the reverse pass recomputes nothing.
 struct AdjLayout {
     size_t S, F, B;
-    size_t total(int n_states) const { return 9 * S + 5 * F + 4 * B + 8 + (size_t)n_states * S; }
+    size_t fixed() const { return 4 * S + 2 * F + B; }
+    size_t per_step() const { return 6 * S + 3 * F + 3 * B + 1; }
+    size_t total(int n_steps) const { return fixed() + (size_t)n_steps * per_step(); }
 };
 
 AdjLayout adj_layout(const kbl_ctx* c)
@@ -859,9 +867,9 @@ AdjLayout adj_layout(const kbl_ctx* c)
     return l;
 }
 
-kbl_status adj_reserve(kbl_ctx* c, int n_states)
+kbl_status adj_reserve(kbl_ctx* c, int n_steps)
 {
-    const size_t need = adj_layout(c).total(n_states);
+    const size_t need = adj_layout(c).total(n_steps);
     if (c->adj_cap >= need) return KBL_OK;
     cudaStreamSynchronize(c->stream);
     if (c->d_adj) cudaFree(c->d_adj);
@@ -878,116 +886,161 @@ kbl_status adj_reserve(kbl_ctx* c, int n_states)
 }
 
 // One SSP-RK3 step with a fixed dt (read from the device scalar dtp), as kbl_step issues it.
-int issue_fixed(kbl_ctx* c, double* w, const double* dtp, cudaStream_t s)
+// With bnd_keep ([3][2][nv][E]) each stage's bounds are written there instead of the
+// context's scratch.
+int issue_fixed(kbl_ctx* c, double* w, const double* dtp, double* bnd_keep, cudaStream_t s)
 {
     int n = 0, r;
     const double* ws = w;
     double* outs[3] = {c->d_wa, c->d_wb, w};
+    const size_t B = (size_t)2 * c->nv * c->E;
     for (int st = 0; st < 3; st++) {
+        double* bnd = bnd_keep ? bnd_keep + st * B : c->d_bnd;
         if ((r = launch_traces(c, ws, c->d_wf, s)) < 0) return -1;
         n += r;
-        if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
+        if ((r = launch_bounds(c, ws, c->d_wf, bnd, s)) < 0) return -1;
         n += r;
         if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
         n += r;
-        if ((r = launch_stage(c, 0, st, w, ws, c->d_R, c->d_bnd, dtp, outs[st], nullptr, s)) < 0) return -1;
+        if ((r = launch_stage(c, 0, st, w, ws, c->d_R, bnd, dtp, outs[st], nullptr, s)) < 0) return -1;
         n += r;
         ws = outs[st];
     }
     return n;
 }
 
-// Reverse of one fixed-dt step from w: wbar (cotangent of the step's output) is
-// replaced by the cotangent of w.  Recomputes and keeps the stage inputs, traces,
-// bounds and residuals, then runs the stage, residual, bounds and trace VJPs
-// backwards through the three stages.
-int issue_adjoint_step(kbl_ctx* c, const double* w, double dt, double* wbar, cudaStream_t s)
+// The stored forward data of one step.
+struct StepStore {
+    const double* st[3];   // stage inputs (st[0] = the step's input)
+    double* R[3];
+    double* wf[3];
+    double* bn[3];
+    double* dtp;           // device copy of the step's dt
+};
+
+StepStore step_store(const kbl_ctx* c, int k, const double* input)
 {
     const AdjLayout L = adj_layout(c);
-    double* p = c->d_adj;
-    double* st[3] = {nullptr, p, p + L.S};
-    p += 2 * L.S;
-    double* R[3] = {p, p + L.S, p + 2 * L.S};
+    double* p = c->d_adj + L.fixed() + (size_t)k * L.per_step();
+    StepStore S;
+    S.st[0] = input;
+    S.st[1] = p + L.S;
+    S.st[2] = p + 2 * L.S;
     p += 3 * L.S;
-    double* wfs[3] = {p, p + L.F, p + 2 * L.F};
+    for (int i = 0; i < 3; i++) S.R[i] = p + i * L.S;
+    p += 3 * L.S;
+    for (int i = 0; i < 3; i++) S.wf[i] = p + i * L.F;
     p += 3 * L.F;
-    double* bn[3] = {p, p + L.B, p + 2 * L.B};
+    for (int i = 0; i < 3; i++) S.bn[i] = p + i * L.B;
     p += 3 * L.B;
-    double* wnb = p;
-    p += L.S;
-    double* wsb[2] = {p, p + L.S};
-    p += 2 * L.S;
-    double* Rb = p;
-    p += L.S;
-    double* wfb = p;
-    double* wfbx = p + L.F;
-    p += 2 * L.F;
-    double* bndb = p;
-    p += L.B;
-    double* dtp = p;
-    int n = 0, r;
-    k_set_scalar<<<1, 1, 0, s>>>(dtp, dt);
-    n++;
-    st[0] = const_cast<double*>(w);
+    S.dtp = p;
+    return S;
+}
+
+// Input-state slot of step k of a segment (k >= 1).
+double* step_input_slot(const kbl_ctx* c, int k)
+{
+    const AdjLayout L = adj_layout(c);
+    return c->d_adj + L.fixed() + (size_t)k * L.per_step();
+}
+
+// Forward of one step keeping every stage's traces, bounds and residual; the step's
+// output goes to `out` (skipped when out is null).
+int issue_step_store(kbl_ctx* c, const StepStore& S, double dt, double* out, bool have_bounds, cudaStream_t s)
+{
+    int n = 1, r;
+    k_set_scalar<<<1, 1, 0, s>>>(S.dtp, dt);
     for (int k = 0; k < 3; k++) {
-        if ((r = launch_traces(c, st[k], wfs[k], s)) < 0) return -1;
+        if ((r = launch_traces(c, S.st[k], S.wf[k], s)) < 0) return -1;
         n += r;
-        if ((r = launch_bounds(c, st[k], wfs[k], bn[k], s)) < 0) return -1;
+        if (!have_bounds) {
+            if ((r = launch_bounds(c, S.st[k], S.wf[k], S.bn[k], s)) < 0) return -1;
+            n += r;
+        }
+        if ((r = launch_rhs(c, S.st[k], S.wf[k], S.R[k], s)) < 0) return -1;
         n += r;
-        if ((r = launch_rhs(c, st[k], wfs[k], R[k], s)) < 0) return -1;
-        n += r;
-        if (k < 2) {
-            if ((r = launch_stage(c, 0, k, w, st[k], R[k], bn[k], dtp, st[k + 1], nullptr, s)) < 0) return -1;
+        double* o = k < 2 ? const_cast<double*>(S.st[k + 1]) : out;
+        if (o) {
+            if ((r = launch_stage(c, 0, k, S.st[0], S.st[k], S.R[k], S.bn[k], S.dtp, o, nullptr, s)) < 0) return -1;
             n += r;
         }
     }
+    return n;
+}
+
+template <int N>
+int reverse_stages(kbl_ctx* c, const StepStore& S, double dt, double* wbar, cudaStream_t s)
+{
+    const AdjLayout L = adj_layout(c);
+    double* p = c->d_adj;
+    double* wnb = p;
+    double* wsb[2] = {p + L.S, p + 2 * L.S};
+    double* Rb = p + 3 * L.S;
+    double* wfb = p + 4 * L.S;
+    double* wfbx = wfb + L.F;
+    double* bndb = wfb + 2 * L.F;
+    int n = 0;
     const double* ob = wbar;
     for (int k = 2; k >= 0; k--) {
         double* sb = wsb[k & 1];
-        switch (c->ops.n) {
-            case 2: r = run_stage_vjp<2>(c, k, dt, w, st[k], R[k], bn[k], ob, k != 2, wnb, sb, Rb, bndb, s); break;
-            case 3: r = run_stage_vjp<3>(c, k, dt, w, st[k], R[k], bn[k], ob, k != 2, wnb, sb, Rb, bndb, s); break;
-            case 4: r = run_stage_vjp<4>(c, k, dt, w, st[k], R[k], bn[k], ob, k != 2, wnb, sb, Rb, bndb, s); break;
-            case 5: r = run_stage_vjp<5>(c, k, dt, w, st[k], R[k], bn[k], ob, k != 2, wnb, sb, Rb, bndb, s); break;
-            case 6: r = run_stage_vjp<6>(c, k, dt, w, st[k], R[k], bn[k], ob, k != 2, wnb, sb, Rb, bndb, s); break;
-            default: return -1;
-        }
-        n += r;
+        n += run_stage_vjp<N>(c, k, dt, S.st[0], S.st[k], S.R[k], S.bn[k], ob, k != 2, wnb, sb, Rb, bndb, s);
         cudaMemsetAsync(wfb, 0, 2 * L.F * sizeof(double), s);
-        switch (c->ops.n) {
-            case 2: r = run_rhs_vjp<2>(c, st[k], wfs[k], Rb, sb, wfb, wfbx, s); break;
-            case 3: r = run_rhs_vjp<3>(c, st[k], wfs[k], Rb, sb, wfb, wfbx, s); break;
-            case 4: r = run_rhs_vjp<4>(c, st[k], wfs[k], Rb, sb, wfb, wfbx, s); break;
-            case 5: r = run_rhs_vjp<5>(c, st[k], wfs[k], Rb, sb, wfb, wfbx, s); break;
-            case 6: r = run_rhs_vjp<6>(c, st[k], wfs[k], Rb, sb, wfb, wfbx, s); break;
-        }
-        n += r;
-        switch (c->ops.n) {
-            case 2: r = run_bounds_vjp<2>(c, st[k], wfs[k], bn[k], bndb, sb, wfb, wfbx, s); break;
-            case 3: r = run_bounds_vjp<3>(c, st[k], wfs[k], bn[k], bndb, sb, wfb, wfbx, s); break;
-            case 4: r = run_bounds_vjp<4>(c, st[k], wfs[k], bn[k], bndb, sb, wfb, wfbx, s); break;
-            case 5: r = run_bounds_vjp<5>(c, st[k], wfs[k], bn[k], bndb, sb, wfb, wfbx, s); break;
-            case 6: r = run_bounds_vjp<6>(c, st[k], wfs[k], bn[k], bndb, sb, wfb, wfbx, s); break;
-        }
+        n += run_rhs_vjp<N>(c, S.st[k], S.wf[k], Rb, sb, wfb, wfbx, s);
+        const int r = run_bounds_vjp<N>(c, S.st[k], S.wf[k], S.bn[k], bndb, sb, wfb, wfbx, s);
         if (r < 0) return -1;
         n += r;
-        switch (c->ops.n) {
-            case 2: r = run_traces_vjp<2>(c, wfb, wfbx, sb, s); break;
-            case 3: r = run_traces_vjp<3>(c, wfb, wfbx, sb, s); break;
-            case 4: r = run_traces_vjp<4>(c, wfb, wfbx, sb, s); break;
-            case 5: r = run_traces_vjp<5>(c, wfb, wfbx, sb, s); break;
-            case 6: r = run_traces_vjp<6>(c, wfb, wfbx, sb, s); break;
-        }
-        n += r;
+        n += run_traces_vjp<N>(c, wfb, wfbx, sb, s);
         ob = sb;
     }
-    // stage 0's input is w itself: its cotangent adds to the wn part
-    const size_t tot = L.S;
-    if (tot > 0) {
-        k_add<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(wnb, ob, wbar, tot);
-        n++;
+    // stage 0's input is the step's input itself: its cotangent adds to the wn part
+    k_add<<<(unsigned)((L.S + 255) / 256), 256, 0, s>>>(wnb, ob, wbar, L.S);
+    return n + 1;
+}
+
+// Reverse of one step from its stored forward data: wbar (cotangent of the step's
+// output) is replaced by the cotangent of its input.
+int issue_step_reverse(kbl_ctx* c, const StepStore& S, double dt, double* wbar, cudaStream_t s)
+{
+    switch (c->ops.n) {
+        case 2: return reverse_stages<2>(c, S, dt, wbar, s);
+        case 3: return reverse_stages<3>(c, S, dt, wbar, s);
+        case 4: return reverse_stages<4>(c, S, dt, wbar, s);
+        case 5: return reverse_stages<5>(c, S, dt, wbar, s);
+        case 6: return reverse_stages<6>(c, S, dt, wbar, s);
     }
-    return n;
+    return -1;
+}
+
+// Stage bounds of step k from a caller's array [n][3][2][nv][E] when given.
+StepStore with_bounds(const kbl_ctx* c, StepStore S, const double* bnd_in, int k)
+{
+    if (bnd_in) {
+        const size_t B = adj_layout(c).B;
+        for (int i = 0; i < 3; i++) S.bn[i] = const_cast<double*>(bnd_in) + ((size_t)k * 3 + i) * B;
+    }
+    return S;
+}
+
+// n fixed-dt steps from w0 backwards: forward keeping everything (the stage bounds come
+// from bnd_in when given), then the reverse.
+int issue_segment(kbl_ctx* c, const double* w0, const double* dts, int n, const double* bnd_in, double* wbar,
+                  cudaStream_t s)
+{
+    int launches = 0;
+    for (int k = 0; k < n; k++) {
+        const StepStore S = with_bounds(c, step_store(c, k, k == 0 ? w0 : step_input_slot(c, k)), bnd_in, k);
+        const int r = issue_step_store(c, S, dts[k], k + 1 < n ? step_input_slot(c, k + 1) : nullptr,
+                                       bnd_in != nullptr, s);
+        if (r < 0) return -1;
+        launches += r;
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        const StepStore S = with_bounds(c, step_store(c, k, k == 0 ? w0 : step_input_slot(c, k)), bnd_in, k);
+        const int r = issue_step_reverse(c, S, dts[k], wbar, s);
+        if (r < 0) return -1;
+        launches += r;
+    }
+    return launches;
 }
 
 }  // namespace
@@ -1113,26 +1166,34 @@ kbl_status kbl_entropy_vjp(kbl_ctx* c, const double* w, double Jb, double* wb)
 
 kbl_status kbl_step_fixed(kbl_ctx* c, double* w, double dt)
 {
+    return kbl_forward_segment(c, w, &dt, 1, nullptr);
+}
+
+kbl_status kbl_forward_segment(kbl_ctx* c, double* w, const double* dts, int n, double* bnd_out)
+{
     if (!c || !c->mesh_ready) return afail(c, KBL_ESTATE, "no mesh");
-    if ((c->E > 0 && !w) || !(dt >= 0.0)) return afail(c, KBL_EINVAL, "bad argument");
-    if (c->E == 0) return KBL_OK;
-    k_set_scalar<<<1, 1, 0, c->stream>>>(c->d_scal, dt);
-    const int n = issue_fixed(c, w, c->d_scal, c->stream);
-    return acheck(c, n < 0 ? -1 : n + 1, "step_fixed");
+    if (n < 0 || (n > 0 && !dts) || (c->E > 0 && !w)) return afail(c, KBL_EINVAL, "bad argument");
+    for (int k = 0; k < n; k++)
+        if (!(dts[k] >= 0.0)) return afail(c, KBL_EINVAL, "negative or NaN dt");
+    if (c->E == 0 || n == 0) return KBL_OK;
+    const size_t B = (size_t)2 * c->nv * c->E;
+    int launches = 0;
+    for (int k = 0; k < n; k++) {
+        k_set_scalar<<<1, 1, 0, c->stream>>>(c->d_scal, dts[k]);
+        const int r = issue_fixed(c, w, c->d_scal, bnd_out ? bnd_out + (size_t)k * 3 * B : nullptr, c->stream);
+        if (r < 0) return afail(c, KBL_EINVAL, "order/dimension not compiled in");
+        launches += r + 1;
+    }
+    return acheck(c, launches, "forward_segment");
 }
 
 kbl_status kbl_adjoint_step(kbl_ctx* c, const double* w, double dt, double* wbar)
 {
-    if (!adj_ok(c)) return afail(c, KBL_ESTATE, "no 2D mesh");
-    if (c->cfg.precision != KBL_FP64) return afail(c, KBL_EINVAL, "the adjoint runs in FP64");
-    if ((c->E > 0 && (!w || !wbar)) || !(dt >= 0.0)) return afail(c, KBL_EINVAL, "bad argument");
-    if (c->E == 0) return KBL_OK;
-    kbl_status st = adj_reserve(c, 0);
-    if (st != KBL_OK) return st;
-    return acheck(c, issue_adjoint_step(c, w, dt, wbar, c->stream), "adjoint_step");
+    return kbl_adjoint_segment(c, w, &dt, 1, nullptr, wbar);
 }
 
-kbl_status kbl_adjoint_segment(kbl_ctx* c, const double* w0, const double* dts, int n, double* wbar)
+kbl_status kbl_adjoint_segment(kbl_ctx* c, const double* w0, const double* dts, int n, const double* bnd_in,
+                               double* wbar)
 {
     if (!adj_ok(c)) return afail(c, KBL_ESTATE, "no 2D mesh");
     if (c->cfg.precision != KBL_FP64) return afail(c, KBL_EINVAL, "the adjoint runs in FP64");
@@ -1140,30 +1201,11 @@ kbl_status kbl_adjoint_segment(kbl_ctx* c, const double* w0, const double* dts, 
     for (int k = 0; k < n; k++)
         if (!(dts[k] >= 0.0)) return afail(c, KBL_EINVAL, "negative or NaN dt");
     if (c->E == 0 || n == 0) return KBL_OK;
-    kbl_status st = adj_reserve(c, n - 1);
+    kbl_status st = adj_reserve(c, n);
     if (st != KBL_OK) return st;
-    const AdjLayout L = adj_layout(c);
-    double* states = c->d_adj + L.total(0);
-    cudaStream_t s = c->stream;
-    int launches = 0;
-    // forward: the inputs of steps 1 .. n-1
-    for (int k = 1; k < n; k++) {
-        double* dst = states + (size_t)(k - 1) * L.S;
-        const double* src = k == 1 ? w0 : states + (size_t)(k - 2) * L.S;
-        cudaMemcpyAsync(dst, src, L.S * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        k_set_scalar<<<1, 1, 0, s>>>(c->d_scal, dts[k - 1]);
-        const int r = issue_fixed(c, dst, c->d_scal, s);
-        if (r < 0) return afail(c, KBL_EINVAL, "order not compiled in");
-        launches += r + 1;
-    }
-    // reverse
-    for (int k = n - 1; k >= 0; k--) {
-        const double* wk = k == 0 ? w0 : states + (size_t)(k - 1) * L.S;
-        const int r = issue_adjoint_step(c, wk, dts[k], wbar, s);
-        if (r < 0) return afail(c, KBL_EINVAL, "order / velocity grid not compiled in");
-        launches += r;
-    }
-    return acheck(c, launches, "adjoint_segment");
+    const int r = issue_segment(c, w0, dts, n, bnd_in, wbar, c->stream);
+    if (r < 0) return afail(c, KBL_EINVAL, "order / velocity grid not compiled in");
+    return acheck(c, r, "adjoint_segment");
 }
 
 }  // extern "C"

@@ -95,7 +95,8 @@ _SIGS = {
     "kbl_entropy_vjp": (C.c_int, [_P, _P, C.c_double, _P]),
     "kbl_step_fixed": (C.c_int, [_P, _P, C.c_double]),
     "kbl_adjoint_step": (C.c_int, [_P, _P, C.c_double, _P]),
-    "kbl_adjoint_segment": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "kbl_adjoint_segment": (C.c_int, [_P, _P, _P, C.c_int, _P, _P]),
+    "kbl_forward_segment": (C.c_int, [_P, _P, _P, C.c_int, _P]),
 }
 
 TUNE_BOUNDS_TILE = 0
@@ -308,10 +309,15 @@ class Context:
         self._check(self._lib.kbl_adjoint_step(self._h, _dev(w, "w"), float(dt), _dev(wbar, "wbar")),
                     "adjoint_step")
 
-    def adjoint_segment(self, w0, dts, wbar):
+    def forward_segment(self, w, dts, bnd_out=None):
         d, dp = _host(dts, np.float64, "dts")
-        self._check(self._lib.kbl_adjoint_segment(self._h, _dev(w0, "w0"), dp, len(d), _dev(wbar, "wbar")),
-                    "adjoint_segment")
+        self._check(self._lib.kbl_forward_segment(self._h, _dev(w, "w"), dp, len(d), _dev(bnd_out)),
+                    "forward_segment")
+
+    def adjoint_segment(self, w0, dts, wbar, bnd_in=None):
+        d, dp = _host(dts, np.float64, "dts")
+        self._check(self._lib.kbl_adjoint_segment(self._h, _dev(w0, "w0"), dp, len(d), _dev(bnd_in),
+                                                  _dev(wbar, "wbar")), "adjoint_segment")
 
 
 def _dev_any(t, dtype_name, name):

@@ -260,10 +260,10 @@ def _J_device(ctx, w0, dts):
     return float(J.item())
 
 
-def _grad_device(ctx, w0, dts, every):
+def _grad_device(ctx, w0, dts, every, keep_bounds=True):
     from paper_2407_20966_gb300 import adjoint
     x = to_dev(w0).requires_grad_(True)
-    J = adjoint.entropy(adjoint.trajectory(x, ctx, dts, checkpoint_every=every), ctx)
+    J = adjoint.entropy(adjoint.trajectory(x, ctx, dts, checkpoint_every=every, keep_bounds=keep_bounds), ctx)
     J.backward()
     ctx.check()
     return float(J.detach().item()), x.grad.cpu().numpy()
@@ -293,14 +293,17 @@ def test_adjoint_step_matches_fd_shock_vortex(orc):
 
 def test_trajectory_gradient_checkpointing_and_fd(orc):
     """20 limited steps: checkpoints every 5 steps give bit for bit the gradient of one
-    20-step segment, and central differences of the device forward pass agree."""
+    20-step segment, and so does recomputing the stage bounds instead of keeping them;
+    central differences of the device forward pass agree."""
     from paper_2407_20966_gb300 import adjoint
     ctx, mesh, w0 = _shock_vortex()
     dts = adjoint.cfl_time_steps(ctx, to_dev(w0), 20, CFL_2D)
     ctx.counters()
     J, g5 = _grad_device(ctx, w0, dts, 5)
     _, g20 = _grad_device(ctx, w0, dts, 20)
+    _, g5r = _grad_device(ctx, w0, dts, 5, keep_bounds=False)
     np.testing.assert_array_equal(g5, g20)
+    np.testing.assert_array_equal(g5, g5r)
     assert J == _J_device(ctx, w0, dts)
     for k in range(2):
         _fd_check(ctx, w0, dts, g5, 10 + k, 1e-8, FD_TOL, f"20 steps, direction {k}")
