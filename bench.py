@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod", "batched", "adjoint"])
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint workload: elements per axis")
     ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: time steps per gradient")
+    ap.add_argument("--adj-cfl", type=float, default=0.05, help="adjoint workload: CFL number")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
@@ -443,7 +444,7 @@ def run_batched(args, rank, world):
 
 def run_adjoint(args, rank, world):
     """Reverse mode: the gradient of the integrated entropy at t_end with respect to the initial
-    state of the shock-vortex problem (n x n P3, 32 x 32 velocity grid, FP64, CFL 0.07) through
+    state of the shock-vortex problem (n x n P3, 32 x 32 velocity grid, FP64, CFL 0.05) through
     `adj_steps` limited SSP-RK3 steps, checkpoints every 10 steps.  One timed unit is one whole
     gradient: the checkpointed forward pass plus the backward pass (segment recomputation and
     the adjoint kernels).  Warm-up: gradients of 2-step trajectories.  `value` counts the forward
@@ -454,7 +455,7 @@ def run_adjoint(args, rank, world):
     build.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    n, n_steps, every, cfl = args.adj_n, args.adj_steps, 10, 0.07
+    n, n_steps, every, cfl = args.adj_n, args.adj_steps, 10, args.adj_cfl
     mesh, ic = inputs.shock_vortex(n)
     ctx = kbl.Context(dim=2, p=3, nu=(32, 32), precision=kbl.FP64, eps_rule=1)
     ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
@@ -503,7 +504,7 @@ def run_adjoint(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "differentiated element-stages/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"adjoint: shock-vortex {n}x{n} P3 (Mach 1.1 stationary shock, isentropic "
+            "config": {"workload": f"adjoint: shock-vortex on [0,2]x[0,1], {n}x{n} P3 (Mach 1.1 stationary shock, isentropic "
                                    f"vortex), 32x32 velocity grid, FP64, CFL {cfl}, gradient of the integrated "
                                    f"entropy through {n_steps} limited SSP-RK3 steps, checkpoints every {every}",
                        "elements": E, "time_steps": n_steps, "t_end": float(sum(dts)),

@@ -273,10 +273,10 @@ kbl_status kbl_stage_vjp(kbl_ctx* ctx, int s, double dt, const double* wn, const
                          const double* R, const double* bnd, const double* ob, int accumulate_wn,
                          double* wnb, double* wsb, double* Rb, double* bndb);
 
-/* Integrated physical entropy (s = P rho^-gamma, Sec. 6) of w:
- * J = sum_e |J_e| sum_n W_n P rho^-gamma with the Gauss-Legendre weights, written
- * to the device scalar J_dev (fixed summation order: deterministic).
- * kbl_entropy_vjp: wb = Jb dJ/dw (overwritten). */
+/* Integrated entropy of w: J = sum_e |J_e| sum_n W_n rho ln(P rho^-gamma), the
+ * density-weighted log of the physical entropy s = P rho^-gamma of Sec. 6, with the
+ * Gauss-Legendre weights; written to the device scalar J_dev (fixed summation
+ * order: deterministic).  kbl_entropy_vjp: wb = Jb dJ/dw (overwritten). */
 kbl_status kbl_entropy(kbl_ctx* ctx, const double* w, double* J_dev);
 kbl_status kbl_entropy_vjp(kbl_ctx* ctx, const double* w, double Jb, double* wb);
 

@@ -9,7 +9,7 @@ only sequences the calls and keeps the checkpoints.
   ``checkpoint_every``-th state (and, by default, every stage's bounds); the backward
   pass runs kbl_adjoint_segment once per segment, which recomputes the segment's states
   and walks them backwards.
-* :func:`entropy` -- the integrated physical entropy sum |J_e| W_n P rho^-gamma.
+* :func:`entropy` -- the integrated entropy sum |J_e| W_n rho ln(P rho^-gamma).
 
 The time steps are held fixed in the derivative (the CFL rule is not differentiated).
 Subgradients at ties of the method's min / max operations follow the rule stated in
@@ -91,5 +91,5 @@ class _Entropy(torch.autograd.Function):
 
 
 def entropy(w: torch.Tensor, kctx: "kbl.Context") -> torch.Tensor:
-    """Integrated physical entropy of w (a 0-dim tensor), differentiable in w."""
+    """Integrated entropy sum |J_e| W_n rho ln(P rho^-gamma) of w (a 0-dim tensor), differentiable in w."""
     return _Entropy.apply(w, kctx)

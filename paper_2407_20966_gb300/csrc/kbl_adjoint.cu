@@ -670,8 +670,9 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// integrated entropy  J = sum_e |J_e| sum_n W_n P rho^-gamma  (the physical entropy
-// s = P rho^-gamma of Sec. 6, integrated with the Gauss-Legendre rule), and its gradient
+// integrated entropy  J = sum_e |J_e| sum_n W_n rho ln(P rho^-gamma), the density-weighted log
+// of the physical entropy s = P rho^-gamma of Sec. 6, integrated with the Gauss-Legendre rule,
+// and its gradient
 // ---------------------------------------------------------------------------
 constexpr int NT_ENT = 256;
 
@@ -689,7 +690,7 @@ k_entropy_partial(const double* __restrict__ w, MeshDev m, FrOps ops, double gam
         for (int v = 0; v < 4; v++) q[v] = w[((size_t)v * m.E + e) * NS + nd];
         const double P = kbl_pressure<2>(q, gamma - 1.0);
         const double J = 0.25 * m.h[e * 2] * m.h[e * 2 + 1];
-        val = J * ops.wq[nd % N] * ops.wq[nd / N] * P * pow(q[0], -gamma);
+        val = J * ops.wq[nd % N] * ops.wq[nd / N] * q[0] * (log(P) - gamma * log(q[0]));
     }
     for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = val;
@@ -720,6 +721,7 @@ template <int N>
 __global__ void __launch_bounds__(NT_ENT)
 k_entropy_vjp(const double* __restrict__ w, MeshDev m, FrOps ops, double gamma, double Jb, double* __restrict__ wb)
 {
+    // d/dq [rho ln P - gamma rho ln rho] = (rho / P) dP/dq + (ln(P rho^-gamma) - gamma) e_rho
     constexpr int NS = N * N;
     const size_t t = (size_t)blockIdx.x * NT_ENT + threadIdx.x;
     if (t >= (size_t)m.E * NS) return;
@@ -728,10 +730,9 @@ k_entropy_vjp(const double* __restrict__ w, MeshDev m, FrOps ops, double gamma, 
     for (int v = 0; v < 4; v++) q[v] = w[((size_t)v * m.E + e) * NS + nd];
     const double P = kbl_pressure<2>(q, gamma - 1.0);
     const double c = Jb * 0.25 * m.h[e * 2] * m.h[e * 2 + 1] * ops.wq[nd % N] * ops.wq[nd / N];
-    const double rg = pow(q[0], -gamma);
     double qb[4] = {0, 0, 0, 0};
-    pressure_vjp<2>(q, gamma, c * rg, qb);
-    qb[0] += c * P * (-gamma) * rg / q[0];
+    pressure_vjp<2>(q, gamma, c * q[0] / P, qb);
+    qb[0] += c * (log(P) - gamma * log(q[0]) - gamma);
     for (int v = 0; v < 4; v++) wb[((size_t)v * m.E + e) * NS + nd] = qb[v];
 }
 

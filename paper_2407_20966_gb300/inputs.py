@@ -193,19 +193,21 @@ def four_quadrant(n, states):
     return mesh, ic
 
 
-def shock_vortex(n, gamma=GAMMA, mach=1.1, beta=0.5, radius=0.05, centre=(0.35, 0.5), shock_x=0.5):
-    """Shock-vortex interaction on [0, 1]^2 with n x n elements (n even): a stationary normal
-    shock at x = shock_x (an element boundary) between the upstream state (rho, u, v, P) =
-    (1, mach sqrt(gamma), 0, 1) and its Rankine-Hugoniot post-shock state, and an isentropic
-    vortex of strength beta and radius `radius` centred upstream at `centre`, convected
-    into the shock by the mean flow.  x faces take the upstream (left) and post-shock
-    (right) states; y is periodic.
+def shock_vortex(n, gamma=GAMMA, mach=1.1, beta=1.0, radius=0.1, centre=(0.25, 0.5), shock_x=0.5):
+    """Shock-vortex interaction on [0, 2] x [0, 1] with n x n elements (n a multiple of 4, so that
+    x = shock_x = 0.5 is an element boundary): a stationary normal shock between the upstream
+    state (rho, u, v, P) = (1, mach sqrt(gamma), 0, 1) and its Rankine-Hugoniot post-shock state,
+    and an isentropic vortex of strength beta and core radius `radius` centred upstream at
+    `centre`, carried into the shock by the mean flow.  x faces take the upstream (left) and
+    post-shock (right) states; y is periodic.
 
-    Vortex, with r = |x - centre| / radius: velocity perturbation
-    beta/(2 pi) exp((1 - r^2)/2) (-(y-yc), x-xc) / radius; temperature
-    T = 1 - (gamma-1) beta^2 / (8 gamma pi^2) exp(1 - r^2); rho = T^(1/(gamma-1)), P = rho^gamma.
+    Vortex (the form of the isentropic-vortex set-up, lengths in units of `radius`), with
+    r = |x - centre| / radius: velocity perturbation beta/(2 pi) exp((1 - r^2)/2) (-(y-yc), x-xc)
+    / radius; temperature T = 1 - (gamma-1) beta^2 / (8 gamma pi^2) exp(1 - r^2);
+    rho = T^(1/(gamma-1)), P = rho^gamma.  With beta = 1 the peak swirl speed is 0.26, a vortex
+    Mach number of about 0.22.
     """
-    assert n % 2 == 0
+    assert n % 4 == 0
     m2 = mach * mach
     c1 = math.sqrt(gamma)
     u1 = mach * c1
@@ -217,7 +219,7 @@ def shock_vortex(n, gamma=GAMMA, mach=1.1, beta=0.5, radius=0.05, centre=(0.35, 
 
     def bc_of_face(ix, iy, f):
         return np.full(np.shape(ix), 0 if f == 0 else 1)
-    mesh = mesh_2d(n, n, 0.0, 1.0, 0.0, 1.0, periodic=(False, True), bc_of_face=bc_of_face)
+    mesh = mesh_2d(n, n, 0.0, 2.0, 0.0, 1.0, periodic=(False, True), bc_of_face=bc_of_face)
     mesh.bc = np.stack([up, down]).astype(np.float64)
 
     def ic(x, y):

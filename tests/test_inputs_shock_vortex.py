@@ -39,8 +39,9 @@ def test_vortex_is_isentropic_and_mesh_layout():
     np.testing.assert_allclose((P / rho ** 1.4)[up], 1.0, rtol=1e-13)
     assert np.all(w[:, ~up] == mesh.bc[1][:, None])
     # the vortex is present: velocity deviates from the mean flow near its centre
-    near = up & ((x - 0.35) ** 2 + (y - 0.5) ** 2 < 0.05 ** 2)
+    near = up & ((x - 0.25) ** 2 + (y - 0.5) ** 2 < 0.1 ** 2)
     assert near.any() and np.abs(w[2][near]).max() > 1e-2
-    # x faces are Dirichlet (ids 0 upstream, 1 downstream), y is periodic
+    # domain [0, 2] x [0, 1]; x faces are Dirichlet (ids 0 upstream, 1 downstream), y is periodic
+    assert np.allclose(mesh.h[0], [2 / 16, 1 / 16])
     assert (mesh.nbr[::16, 0] == -1).all() and (mesh.nbr[15::16, 1] == -2).all()
     assert (mesh.nbr >= 0)[:, 2:].all()
