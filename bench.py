@@ -33,9 +33,16 @@ METRIC = "limited element-stages/sec (bounds+limit+RHS) on 1 GB300, FP32 vs FP64
 UNIT = "element-stages/s"
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# FP32 min/max: 64 three-input FMNMX instructions per clock per SM (measured), each
-# two comparisons -> 128 comparisons per clock per SM.
-CMP_PER_CLK_SM = 128.0
+# The envelope loop of the FP32 bounds kernel needs, per (stencil state, velocity node),
+# 2 products (g = Ex Ey and C g) and 4 comparisons (min and max of both): 6 FP32 lane-ops.
+# Its roofline is the measured rate of exactly that instruction mix in a register-only loop
+# (csrc/peaks/kbl_fp32_peaks.cu, `bench.py --peaks`; profiles/fp32_pipe_peaks.md): 155.5
+# lane-ops per clock per SM (packed multiplies and three-input min/max issue to two pipes
+# that overlap only in part), times 152 SMs and the 2070 MHz maximum clock.
+OPS_PER_STATE_NODE = 6.0
+LANE_OPS_PER_CLK_SM = 155.5
+PEAK_SOURCE = ("measured envelope-pattern rate 155.5 FP32 lane-ops/clk/SM (bench.py --peaks) "
+               "x 152 SMs x 2070 MHz")
 # DRAM bytes (read + write) of one launch of the FP32 2D bounds kernel on the vortex workload,
 # from the ncu capture summarised in profiles/bounds_f32_vortex128_p3.md.  Must be reset to
 # None whenever that kernel changes, until it is captured again.
@@ -52,6 +59,8 @@ def parse():
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint workload: elements per axis")
     ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: time steps per gradient")
     ap.add_argument("--adj-cfl", type=float, default=0.05, help="adjoint workload: CFL number")
+    ap.add_argument("--peaks", action="store_true",
+                    help="build and run the FP32 instruction-rate microbenchmark behind the roofline peak")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
@@ -244,16 +253,16 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     bounds_ms = sum(a.elapsed_time(b) for a, b in evs) / kb
     nS, NU = stencil_size(wl), nu_total(wl)
-    cmp_per_launch = 4.0 * nS * NU * E           # min and max of g and of C g per (state, node)
-    achieved = cmp_per_launch / (bounds_ms * 1e-3) / 1e12
-    peak = CMP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    ops_per_launch = OPS_PER_STATE_NODE * nS * NU * E   # 2 products + 4 comparisons per (state, node)
+    achieved = ops_per_launch / (bounds_ms * 1e-3) / 1e12
+    peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
     traffic = BOUNDS_F32_VORTEX_TRAFFIC if (args.workload == "vortex" and precision == kbl.FP32_MIXED
                                              and args.bounds_tile <= 0) else None
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcmp/s",
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "T FP32 lane-ops/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": "k_bounds2d_f32" if (
                     wl["dim"] == 2 and precision == kbl.FP32_MIXED) else "bounds",
-                "bounds_ms_per_launch": round(bounds_ms, 4),
-                "peak_source": "152 SMs x 2070 MHz x 64 three-input FMNMX/clk/SM x 2 comparisons"}
+                "bounds_ms_per_launch": round(bounds_ms, 4), "work": "6 lane-ops per (stencil state, velocity node)",
+                "peak_source": PEAK_SOURCE}
 
     # FP64 leg (same workload, FP64 bounds)
     fp64 = None
@@ -421,8 +430,9 @@ def run_batched(args, rank, world):
         out_pin.copy_(wd, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ke
-    peak = CMP_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = tune_cmp / (tune_ms * 1e-3) / 1e12
+    peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    # the autotuner counts 4 comparisons per (state, node); the roofline counts 6 lane-ops
+    achieved = tune_cmp * (OPS_PER_STATE_NODE / 4.0) / (tune_ms * 1e-3) / 1e12
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
@@ -434,10 +444,11 @@ def run_batched(args, rank, world):
             "e2e": {"value": E * 3 * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": w0.nbytes,
                     "d2h_bytes_per_step": w0.nbytes},
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tcmp/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_batch_bounds",
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                         "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_batch_bounds", "work": "6 lane-ops per (stencil state, velocity node)",
                          "measured_on": "autotune sample (every 8th work item), best launch shape",
-                         "peak_source": "152 SMs x 2070 MHz x 64 three-input FMNMX/clk/SM x 2 comparisons"},
+                         "peak_source": PEAK_SOURCE},
             "clocks": clk.summary()}
     return line, probs, b
 
@@ -518,8 +529,26 @@ def run_adjoint(args, rank, world):
     return line, w0, workload("vortex")
 
 
+def run_peaks():
+    """Compile and run csrc/peaks/kbl_fp32_peaks.cu: FP32 multiply and min/max rates, alone and
+    in the envelope pattern, per SM clock (clock64 inside each block); clocks sampled beside."""
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "paper_2407_20966_gb300", "csrc", "peaks", "kbl_fp32_peaks.cu")
+    exe = os.path.join(here, "paper_2407_20966_gb300", "_build", "kbl_fp32_peaks")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
+                   check=True)
+    with ClockSampler(0) as clk:
+        subprocess.run([exe], check=True)
+    print(json.dumps({"peaks_clocks": clk.summary()}))
+
+
 def main():
     args = parse()
+    if args.peaks:
+        run_peaks()
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -437,6 +437,8 @@ int run2d(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cuda
     if (c->cfg.precision == KBL_FP32_MIXED) {
         if (NX >= 32 && c->bounds_tile == 1)
             k_bounds2d_f32<N, NX, 2><<<c->E, B2f32<NX, 2>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+        else if (NX >= 32 && c->bounds_tile == 2)
+            k_bounds2d_f32<N, NX, 3><<<c->E, B2f32<NX, 3>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
         else
             k_bounds2d_f32<N, NX, 0><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
     } else

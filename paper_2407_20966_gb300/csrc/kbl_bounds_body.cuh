@@ -73,10 +73,14 @@ __device__ __forceinline__ float fast_exp2(float x)
 // the bounds.  Everything else per state (U, theta, A, C, the box) is FP32,
 // because the GB300 FP64 pipe runs at ~1/76 of the FP32 rate.
 // ---------------------------------------------------------------------------
+// Thread tile of the envelope loop: TYSEL 0 = TX x TX with TX = 4 (grids of 32 or more
+// points per axis), 2 = 4 x 2, 3 = 2 x 4 (x nodes x y nodes per thread).
 template <int NX, int TYSEL = 0>
 struct B2f32 {
-    static constexpr int TX = (NX >= 32) ? 4 : (NX >= 16 ? 2 : 1);     // x nodes per thread
-    static constexpr int TY = (TYSEL > 0 && TYSEL <= TX) ? TYSEL : TX; // y nodes per thread
+    static constexpr int TXD = (NX >= 32) ? 4 : (NX >= 16 ? 2 : 1);
+    static constexpr bool T24 = TYSEL == 3 && NX >= 32;
+    static constexpr int TX = T24 ? 2 : TXD;                                        // x nodes per thread
+    static constexpr int TY = T24 ? 4 : ((TYSEL > 0 && TYSEL <= TX) ? TYSEL : TX); // y nodes per thread
     static constexpr int TPX = NX / TX, TPY = NX / TY;
     static constexpr int NT = TPX * TPY;
     static constexpr int MINB = (NT == 64) ? KBL_BOUNDS_MINB : (NT == 128 ? 8 : 1);
