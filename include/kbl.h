@@ -180,7 +180,10 @@ int64_t kbl_launch_count(const kbl_ctx* ctx);
 /* Launch-shape knobs (not part of the method; results do not depend on them
  * beyond FP32 rounding order).  KBL_TUNE_BOUNDS_TILE selects the FP32 2D
  * bounds thread tile for grids of 32 or 64 points per axis: 0 = 4 x 4 velocity
- * nodes per thread, 1 = 4 x 2.  Setting a knob drops the captured step graph. */
+ * nodes per thread, 1 = 4 x 2, 2 = 2 x 4; 3 (32-point grids) = a persistent,
+ * warp-specialized kernel (one warp builds the next element's tables while four
+ * run the 4 x 2 envelope loop; results equal to 1 bit for bit).  Setting a knob
+ * drops the captured step graph. */
 typedef enum { KBL_TUNE_BOUNDS_TILE = 0 } kbl_tune_key;
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
