@@ -20,6 +20,18 @@ __device__ __forceinline__ double dunkey(long long k)
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
+// FP32 approximation of a double by truncating its significand, with integer operations only
+// (a conversion instruction would cost an FP64-pipe slot): |result - x| <= 2^-23 |x| for
+// 2^-126 <= |x| < 2^128, 0 below that range (|error| < 2^-126), infinity above it.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e32 = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e32 <= 0) return 0.0f;
+    if (e32 >= 255) return __uint_as_float((hi & 0x80000000u) | 0x7f800000u);
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e32 << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
 template <int DIM, int N, int EPB>
 struct LimSmem {
     static constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
@@ -32,7 +44,13 @@ struct LimSmem {
     double saP[EPB];
     int sPtaken[EPB];
     double slm[N], slp[N], sW[NS];
-    double sWsum;
+    double sWsum, sLam;
+    // exact fast path: per-component box around the mean that holds every value of V
+    double sbl[EPB][NV], sbh[EPB][NV];
+    double sdmx[EPB][NV], sdmn[EPB][NV];   // node extremes minus the mean
+    float sdev[EPB][NV][NS];               // node deviations from the mean (FP32)
+    float sfdev[EPB][NV][NFP];             // face-value deviations from the mean (FP32)
+    int sfv[EPB][NV], sfast[EPB];
 
 };
 
@@ -61,6 +79,15 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     auto& slp = sm.slp;
     auto& sW = sm.sW;
     auto& sWsum = sm.sWsum;
+    auto& sLam = sm.sLam;
+    auto& sbl = sm.sbl;
+    auto& sbh = sm.sbh;
+    auto& sfv = sm.sfv;
+    auto& sfast = sm.sfast;
+    auto& sdmx = sm.sdmx;
+    auto& sdmn = sm.sdmn;
+    auto& sdev = sm.sdev;
+    auto& sfdev = sm.sfdev;
     const int tid = threadIdx.x;
     __syncthreads();   // the block may call this for consecutive element blocks
     if (tid < N) {
@@ -72,6 +99,14 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         double sws = 0.0;
         for (int n2 = 0; n2 < NS; n2++) sws += (DIM == 1) ? ops.wq[n2] : ops.wq[n2 % N] * ops.wq[n2 / N];
         sWsum = sws;
+        // Lambda = max over the two ends of sum |l_i(+-1)|: since the weights sum to one, a face
+        // value differs from the mean by at most Lambda * max_i |w_i - mean| along its line
+        double am = 0.0, ap = 0.0;
+        for (int i = 0; i < N; i++) {
+            am += fabs(ops.lm[i]);
+            ap += fabs(ops.lp[i]);
+        }
+        sLam = fmax(am, ap);
     }
     const int el = tid / NS, nd = tid % NS;
     const int e = e0 + el;
@@ -94,10 +129,107 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         }
     }
     __syncthreads();
-    // 2. face values (interpolation along the line normal to each face)
+    // 1b. mean and node extrema (FP64), node deviations from the mean (FP64 difference, kept in
+    //     FP32), face-value deviations from them in FP32 with a rounding allowance: an exact screen
+    //     for alpha = 1.  Every face value lies within its FP32 deviation +- 1e-6 Lambda M of the
+    //     mean (M = largest node deviation; Lambda = max sum |l_i(+-1)|), up to the FP64 rounding
+    //     of the face interpolation itself, covered by delta.  If both bounds lie beyond all of V
+    //     by that margin and the node extremes already clear the epsilon rule, Eq. 37 gives
+    //     alpha_i = 1 whatever the exact face values are, so they need not be formed in FP64.
+    for (int t = tid; t < EPB * NV; t += NT) {
+        const int ell = t / NV, v = t % NV;
+        if (e0 + ell >= E || ell >= nmax) continue;
+        double sum = 0.0;
+        for (int n2 = 0; n2 < NS; n2++) sum += sW[n2] * sw[ell][v][n2];
+        const double mean = sum / sWsum;
+        long long kmx = dkey(sw[ell][v][0]), kmn = kmx;
+        for (int n2 = 1; n2 < NS; n2++) {
+            const long long kk = dkey(sw[ell][v][n2]);
+            kmx = kk > kmx ? kk : kmx;
+            kmn = kk < kmn ? kk : kmn;
+        }
+        smean[ell][v] = mean;
+        sdmx[ell][v] = dunkey(kmx) - mean;
+        sdmn[ell][v] = dunkey(kmn) - mean;
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) sdev[el][v][nd] = f32_trunc(sw[el][v][nd] - smean[el][v]);
+    }
+    __syncthreads();
     for (int t = tid; t < EPB * NFP; t += NT) {
         const int ell = t / NFP, fp = t % NFP;
         if (e0 + ell >= E || ell >= nmax) continue;
+        const int f = fp / NFPF, k = fp % NFPF;
+        const bool along_x = (DIM == 1) || f < 2;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const float l = (float)((f & 1) ? slp[i] : slm[i]);
+                acc = fmaf(l, sdev[ell][v][(DIM == 1) ? i : (along_x ? k * N + i : i * N + k)], acc);
+            }
+            sfdev[ell][v][fp] = acc;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < EPB * NV; t += NT) {
+        const int ell = t / NV, v = t % NV;
+        const int ee = e0 + ell;
+        if (ee >= E || ell >= nmax) continue;
+        const double mean = smean[ell][v], dmaxn = sdmx[ell][v], dminn = sdmn[ell][v];
+        float fmx = -FLT_MAX, fmn = FLT_MAX;
+        for (int fp = 0; fp < NFP; fp++) {
+            fmx = fmaxf(fmx, sfdev[ell][v][fp]);
+            fmn = fminf(fmn, sfdev[ell][v][fp]);
+        }
+        const double M = fmax(dmaxn, -dminn);
+        const double err = 1e-6 * sLam * M + 1e-37;
+        const double delta = 1e-14 * (fabs(mean) + fmax(fabs(mean + dmaxn), fabs(mean + dminn))) * sLam;
+        const double up = fmax(dmaxn, (double)fmx + err) + delta;    // every value of V is below mean + up
+        const double dn = fmax(-dminn, -(double)fmn + err) + delta;  // and above mean - dn
+        const double lo = bnd[(size_t)v * E + ee];
+        const double hi = bnd[((size_t)NV + v) * E + ee];
+        sbl[ell][v] = mean - dn;
+        sbh[ell][v] = mean + up;
+        sfv[ell][v] = (dmaxn >= ph.eps) && (-dminn >= ph.eps) && (hi - mean >= up) && (mean - lo >= dn);
+    }
+    __syncthreads();
+    // 1c. pressure over the box: a lower bound of P on it (rho from its lower end, E from its lower
+    //     end, |m|^2 from the larger end of each component) that clears 2 p_floor plus an allowance
+    //     for the rounding of the exact pressure test below means no point of V can fail it
+    if (tid < EPB) {
+        const int ell = tid;
+        int fast = 0;
+        if (e0 + ell < E && ell < nmax) {
+            fast = 1;
+#pragma unroll
+            for (int v = 0; v < NV; v++) fast &= sfv[ell][v];
+            const double rlo = sbl[ell][0];
+            double mm = 0.0;
+#pragma unroll
+            for (int k = 1; k <= DIM; k++) {
+                const double a = fmax(fabs(sbl[ell][k]), fabs(sbh[ell][k]));
+                mm += a * a;
+            }
+            const double elo = sbl[ell][DIM + 1];
+            const double eabs = fmax(fabs(elo), fabs(sbh[ell][DIM + 1]));
+            if (!(rlo > 0.0)) {
+                fast = 0;
+            } else {
+                const double plb = (ph.gamma - 1.0) * (elo - 0.5 * mm / rlo);
+                if (!(plb >= 2.0 * ph.p_floor + 1e-13 * (eabs + mm / rlo))) fast = 0;
+            }
+        }
+        sfast[ell] = fast;
+    }
+    __syncthreads();
+    // 2. face values (interpolation along the line normal to each face)
+    for (int t = tid; t < EPB * NFP; t += NT) {
+        const int ell = t / NFP, fp = t % NFP;
+        if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
         const int f = fp / NFPF, k = fp % NFPF;
         const double* l = (f & 1) ? slp : slm;
         const bool along_x = (DIM == 1) || f < 2;
@@ -114,10 +246,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     for (int t = tid; t < EPB * NV; t += NT) {
         const int ell = t / NV, v = t % NV;
         const int ee = e0 + ell;
-        if (ee < E && ell < nmax) {
-            double s = 0.0;
-            for (int n2 = 0; n2 < NS; n2++) s += sW[n2] * sw[ell][v][n2];
-            const double mean = s / sWsum;
+        if (ee < E && ell < nmax && sfast[ell]) {
+            salpha_v[ell][v] = 1.0;
+        } else if (ee < E && ell < nmax) {
+            const double mean = smean[ell][v];
             long long kmx = dkey(sw[ell][v][0]), kmn = kmx;
             for (int n2 = 1; n2 < NS; n2++) {
                 const long long kk = dkey(sw[ell][v][n2]);
@@ -144,7 +276,6 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
                 if (t1 < a) a = t1;
                 if (t2 < a) a = t2;
             }
-            smean[ell][v] = mean;
             salpha_v[ell][v] = a;
         }
     }
@@ -165,7 +296,9 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     //    screen never passes a point the exact test would fail; any element it
     //    flags gets the exact P_min of Eq. 47 below.
     const double gm1 = ph.gamma - 1.0;
-    if (live) {
+    if (live && sfast[el]) {
+        sP[el][nd] = 1.0;   // alpha = 1 and the box test passed: w~ = w, no pressure re-limit
+    } else if (live) {
         const double a = salpha[el];
         double q[NV];
 #pragma unroll
@@ -183,6 +316,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     for (int t = tid; t < EPB * NFP; t += NT) {
         const int ell = t / NFP, fp = t % NFP;
         if (e0 + ell >= E || ell >= nmax) continue;
+        if (sfast[ell]) {
+            sP[ell][NS + fp] = 1.0;
+            continue;
+        }
         const double a = salpha[ell];
         double q[NV];
 #pragma unroll
