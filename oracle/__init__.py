@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 class _Cfg(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nu", C.c_int * 2), ("gamma", C.c_double),
                 ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
-                ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int)]
+                ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
+                ("uncoupled", C.c_int)]
 
 
 class _Mesh(C.Structure):
@@ -106,6 +107,7 @@ class Config:
     rho_floor: float = 1e-12
     p_floor: float = 1e-12
     eps_rule: int = 0
+    uncoupled: int = 0
 
     @property
     def nv(self):
@@ -126,7 +128,7 @@ class Config:
     def _c(self):
         nu = list(self.nu) + [1] * (2 - len(self.nu))
         return _Cfg(self.dim, self.p, (C.c_int * 2)(*nu[:2]), self.gamma, self.k, self.r_fac,
-                    self.eps, self.rho_floor, self.p_floor, self.eps_rule)
+                    self.eps, self.rho_floor, self.p_floor, self.eps_rule, self.uncoupled)
 
 
 class Mesh:

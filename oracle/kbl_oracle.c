@@ -510,7 +510,10 @@ void orc_rhs(const orc_cfg* c, const orc_mesh* m, const double* w, const double*
  *  alpha_i: Eq. 37 per component over V = solution points + face points,
  *           with the epsilon rule stated under it
  *  alpha  : alpha_min = min_i alpha_i (Eq. 39), w~ = mean + alpha (w - mean)
- *           (Eq. 38); at face points w~ = mean + alpha (wf - mean)
+ *           (Eq. 38); at face points w~ = mean + alpha (wf - mean).  With
+ *           c->uncoupled each component i takes its own alpha_i instead (the
+ *           independent limiting stated after Eq. 39); alpha_out[0] still
+ *           reports alpha_min
  *  P      : P_min over V of w~ (Eq. 47); if below p_floor,
  *           alpha_P = |(p_floor - P(mean)) / (P_min - P(mean))| (Eq. 49) and
  *           w~~ = mean + alpha_P (w~ - mean) (Eq. 48).  When P(mean) itself is
@@ -531,7 +534,7 @@ void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
         }
         mean[v] = s / sw;
     }
-    double alpha = 1.0;
+    double alpha = 1.0, alpha_v[4];
     for (int v = 0; v < nv; v++) {
         double mx = wel[v * ns], mn = wel[v * ns];
         for (int nd = 1; nd < ns; nd++) {
@@ -555,13 +558,15 @@ void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
             if (t1 < a) a = t1;
             if (t2 < a) a = t2;
         }
+        alpha_v[v] = a;
         if (a < alpha) alpha = a;
     }
     double* wt = malloc(sizeof(double) * nv * ns);
     double* wtf = malloc(sizeof(double) * nv * nfp);
     for (int v = 0; v < nv; v++) {
-        for (int nd = 0; nd < ns; nd++) wt[v * ns + nd] = mean[v] + alpha * (wel[v * ns + nd] - mean[v]);
-        for (int fp = 0; fp < nfp; fp++) wtf[v * nfp + fp] = mean[v] + alpha * (wfel[v * nfp + fp] - mean[v]);
+        const double av = c->uncoupled ? alpha_v[v] : alpha;
+        for (int nd = 0; nd < ns; nd++) wt[v * ns + nd] = mean[v] + av * (wel[v * ns + nd] - mean[v]);
+        for (int fp = 0; fp < nfp; fp++) wtf[v * nfp + fp] = mean[v] + av * (wfel[v * nfp + fp] - mean[v]);
     }
     double pmin = INFINITY, q[4];
     for (int nd = 0; nd < ns; nd++) {

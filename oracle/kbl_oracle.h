@@ -47,6 +47,9 @@ typedef struct {
     double p_floor;   /* pressure floor, Sec. 3.8 */
     int eps_rule;     /* 0: alpha_i = 0 when |extremum - mean| < eps (as printed);
                          1: the component is skipped (alpha_i = 1) */
+    int uncoupled;    /* 0: every component takes alpha_min = min_i alpha_i (Eq. 38-39, the
+                         paper's choice); 1: each component its own alpha_i (the independent
+                         option stated after Eq. 39) */
 } orc_cfg;
 
 typedef struct {

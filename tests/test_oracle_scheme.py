@@ -91,6 +91,59 @@ def test_limiter_epsilon_rule(orc):
     np.testing.assert_array_equal(wl, w)
 
 
+def test_uncoupled_limiting_touches_only_the_offending_component(orc):
+    """The independent option stated after Eq. 39: each component takes its own alpha_i.  With
+    only the density above its bound, the coupled limiter (Eq. 38-39) pulls every component toward
+    its mean by alpha_rho, the uncoupled one only the density, which then touches its bound exactly
+    at the worst point of V; the other components keep their values."""
+    cfg = orc.Config(dim=1, p=3)
+    xi, wq = orc.gauss_legendre(4)
+    w = np.stack([1.0 + 0.3 * xi, 0.2 + 0.05 * xi, 2.5 + 0.1 * xi])
+    L = np.array([[orc.lagrange(xi, j, t) for j in range(4)] for t in (-1.0, 1.0)])
+    wf = w @ L.T
+    mean = _mean(w, wq, 1)
+    lo = np.array([0.5, 0.0, 1.0])
+    hi = np.array([mean[0] + 0.5 * (max(w[0].max(), wf[0].max()) - mean[0]), 1.0, 9.0])
+    wc, ac = orc.limit_element(cfg, w, wf, lo, hi)
+    cfg.uncoupled = 1
+    wu, au = orc.limit_element(cfg, w, wf, lo, hi)
+    assert ac[0] == pytest.approx(0.5, rel=1e-13) and au[0] == ac[0]   # alpha_out reports alpha_min
+    # coupled: every component contracted by 1/2
+    np.testing.assert_allclose(wc, mean[:, None] + 0.5 * (w - mean[:, None]), rtol=1e-14)
+    # uncoupled: density contracted by 1/2, the others unchanged (up to rounding of mean + 1 (w - mean))
+    np.testing.assert_allclose(wu[0], mean[0] + 0.5 * (w[0] - mean[0]), rtol=1e-14)
+    np.testing.assert_allclose(wu[1:], w[1:], rtol=1e-15, atol=1e-15)
+    wuf = wu @ L.T
+    assert max(wu[0].max(), wuf[0].max()) == pytest.approx(hi[0], rel=1e-14)
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_uncoupled_limiting_conserves_means_and_enforces_each_bound(orc, d):
+    """Independent limiting keeps every component's mean and, with the means inside the bounds,
+    puts every value of V inside its own component's bounds; it never limits more than the coupled
+    limiter (|w~ - mean| componentwise at least as large)."""
+    cfg, mesh, om, w, xi, wq = _setup(orc, d, 6 if d == 2 else 16, seed=20 + d)
+    wf = orc.traces(cfg, om, w)
+    bnd = orc.bounds(cfg, om, w, wf)
+    rng = np.random.default_rng(6)
+    m0 = _mean(w, wq, d)
+    w2 = m0[..., None] + 1.5 * (w - m0[..., None]) * (1 + 0.3 * rng.uniform(-1, 1, w.shape))
+    w2 = w2 - (_mean(w2, wq, d) - m0)[..., None]
+    wc, _ = orc.limit(cfg, om, w2, bnd)
+    cfg.uncoupled = 1
+    wu, alpha = orc.limit(cfg, om, w2, bnd)
+    np.testing.assert_allclose(_mean(wu, wq, d), _mean(w2, wq, d), rtol=1e-13, atol=1e-14)
+    assert np.any(alpha[0] < 1)
+    wuf = orc.traces(cfg, om, wu)
+    scale = 1e-12 * np.abs(bnd).max()
+    for arr in (wu, wuf):
+        assert np.all(arr >= bnd[0][..., None] - scale)
+        assert np.all(arr <= bnd[1][..., None] + scale)
+    mean = _mean(w2, wq, d)[..., None]
+    assert np.all(np.abs(wu - mean) >= np.abs(wc - mean) - 1e-13 * np.abs(w2).max())
+    assert np.any(np.abs(wu - mean) > np.abs(wc - mean) + 1e-9)
+
+
 def test_pressure_relimit_restores_floor(orc):
     """Eq. 47-49: a node with negative pressure is pulled back so that P >= 1e-12 on V (the
     pressure is quasi-concave)."""
