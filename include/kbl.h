@@ -79,6 +79,10 @@ typedef struct {
     int eps_rule;     /* 0: alpha_i = 0 when |min_V - mean| or |max_V - mean| < eps
                          (as printed); 1: such a component is skipped */
     int precision;    /* kbl_precision */
+    int uncoupled;    /* 0: every component takes alpha_min = min_i alpha_i (Eq. 38-39, the
+                         paper's choice); 1: each component its own alpha_i (the independent
+                         limiting stated after Eq. 39).  The pressure step of Eq. 47-49
+                         follows in both cases; alpha[0][e] reports alpha_min. */
 } kbl_config;
 
 typedef struct kbl_ctx kbl_ctx;
@@ -92,7 +96,7 @@ typedef struct {
 
 /* Fill cfg with the paper's defaults for dimension d and order p: gamma 1.4,
  * k = 4, nu = 32 per axis in 2D and 64 in 1D, r_fac = 1e-3, eps = 1e-13,
- * floors 1e-12, eps_rule 0, FP64. */
+ * floors 1e-12, eps_rule 0, FP64, coupled limiting. */
 kbl_status kbl_config_default(kbl_config* cfg, int dim, int p);
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy

@@ -426,8 +426,9 @@ struct StageVjpSmem {
     double smean[EPB_L][NV], smb[EPB_L][NV];
     double salpha_v[EPB_L][NV];
     int sbranch[EPB_L][NV], sxarg[EPB_L][NV][2];
-    double salpha[EPB_L], saP[EPB_L], sPbar[EPB_L], spmin[EPB_L], sxb[EPB_L];
-    int staken[EPB_L], sapm[EPB_L], svstar[EPB_L], sxpt[EPB_L];
+    double salpha[EPB_L], saP[EPB_L], sPbar[EPB_L], spmin[EPB_L];
+    double sxb[EPB_L][NV];   // cotangent of the extreme point of Eq. 37 of each component
+    int staken[EPB_L], sapm[EPB_L], svstar[EPB_L], sxpt[EPB_L][NV];
     double sW[NS], sWsum;
 };
 
@@ -453,6 +454,8 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
     const int e0 = blockIdx.x * EPB_L, e = e0 + el;
     const bool live = e < E;
     const double gm1 = ph.gamma - 1.0;
+    // the factor of Eq. 38 that component v of element ell takes (per component if uncoupled)
+    auto aeff = [&](int ell, int v) { return ph.uncoupled ? sm.salpha_v[ell][v] : sm.salpha[ell]; };
     if (tid < NS) sm.sW[tid] = ops.wq[tid % N] * ops.wq[tid / N];
     if (tid == 0) {
         double s = 0.0;
@@ -536,8 +539,8 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
         int apm = 0;
         for (int n2 = 0; n2 < NVP; n2++) {
             for (int v = 0; v < NV; v++) {
-                const double mv = smean[ell][v];
-                q[v] = mv + a * ((n2 < NS ? sw[ell][v][n2] : sf[ell][v][n2 - NS]) - mv);
+                const double mv = smean[ell][v], av = ph.uncoupled ? sm.salpha_v[ell][v] : a;
+                q[v] = mv + av * ((n2 < NS ? sw[ell][v][n2] : sf[ell][v][n2 - NS]) - mv);
             }
             const double P = kbl_pressure<2>(q, gm1);
             if (P < pmin) { pmin = P; apm = n2; }
@@ -567,15 +570,15 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
     // 6. Eq. 48-49 backwards: the mean's share and aP's cotangent
     if (tid < EPB_L && e0 + tid < E && sm.staken[tid]) {
         const int ell = tid, ee = e0 + ell;
-        const double a = sm.salpha[ell], aP = sm.saP[ell];
+        const double aP = sm.saP[ell];
         double aPb = 0.0;
         for (int v = 0; v < NV; v++) {
-            const double mv = smean[ell][v];
+            const double mv = smean[ell][v], av = aeff(ell, v);
             double so = 0.0;
             for (int n2 = 0; n2 < NS; n2++) {
                 const double o = ob[((size_t)v * E + ee) * NS + n2];
                 so += o;
-                aPb += o * (a * (sw[ell][v][n2] - mv));
+                aPb += o * (av * (sw[ell][v][n2] - mv));
             }
             smb[ell][v] += (1.0 - aP) * so;
         }
@@ -593,7 +596,7 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
             double qt[NV], qtb[NV] = {0, 0, 0, 0};
             for (int v = 0; v < NV; v++) {
                 const double mv = smean[ell][v];
-                qt[v] = mv + a * ((apm < NS ? sw[ell][v][apm] : sf[ell][v][apm - NS]) - mv);
+                qt[v] = mv + aeff(ell, v) * ((apm < NS ? sw[ell][v][apm] : sf[ell][v][apm - NS]) - mv);
             }
             pressure_vjp<2>(qt, ph.gamma, pmb, qtb);
             for (int v = 0; v < NV; v++) {
@@ -603,14 +606,14 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
         }
     }
     __syncthreads();
-    // 7. Eq. 38 backwards: alpha's cotangent, then Eq. 37 through the winning ratio
+    // 7. Eq. 38 backwards: the cotangent of each component's factor (summed into alpha_min's
+    //    when coupled), then Eq. 37 through the winning ratio
     if (tid < EPB_L && e0 + tid < E) {
         const int ell = tid, ee = e0 + ell;
-        const double a = sm.salpha[ell];
-        double ab = 0.0;
+        double abv[NV];
         for (int v = 0; v < NV; v++) {
-            const double mv = smean[ell][v];
-            double st = 0.0;
+            const double mv = smean[ell][v], av = aeff(ell, v);
+            double st = 0.0, ab = 0.0;
             for (int n2 = 0; n2 < NS; n2++) {
                 st += stb[ell][v][n2];
                 ab += stb[ell][v][n2] * (sw[ell][v][n2] - mv);
@@ -619,25 +622,35 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
                 st += stfb[ell][v][fp];
                 ab += stfb[ell][v][fp] * (sf[ell][v][fp] - mv);
             }
-            smb[ell][v] += (1.0 - a) * st;
+            smb[ell][v] += (1.0 - av) * st;
+            abv[v] = ab;
+            sm.sxpt[ell][v] = -1;
+            sm.sxb[ell][v] = 0.0;
         }
         double bb[2 * NV];
         for (int k = 0; k < 2 * NV; k++) bb[k] = 0.0;
-        sm.sxpt[ell] = -1;
-        sm.sxb[ell] = 0.0;
-        const int vs = sm.svstar[ell];
-        if (vs >= 0 && sm.sbranch[ell][vs] >= 2) {
-            const int up = sm.sbranch[ell][vs] == 2;
-            const int xpt = sm.sxarg[ell][vs][up ? 0 : 1];
-            const double mv = smean[ell][vs];
-            const double x = xpt < NS ? sw[ell][vs][xpt] : sf[ell][vs][xpt - NS];
-            const double b = up ? bnd[((size_t)NV + vs) * E + ee] : bnd[(size_t)vs * E + ee];
+        // the components whose ratio of Eq. 37 carries a derivative, and the cotangent it gets
+        for (int v = 0; v < NV; v++) {
+            double ab;
+            if (ph.uncoupled) {
+                ab = abv[v];
+            } else {
+                if (v != sm.svstar[ell]) continue;
+                ab = 0.0;
+                for (int u = 0; u < NV; u++) ab += abv[u];
+            }
+            if (sm.sbranch[ell][v] < 2) continue;
+            const int up = sm.sbranch[ell][v] == 2;
+            const int xpt = sm.sxarg[ell][v][up ? 0 : 1];
+            const double mv = smean[ell][v];
+            const double x = xpt < NS ? sw[ell][v][xpt] : sf[ell][v][xpt - NS];
+            const double b = up ? bnd[((size_t)NV + v) * E + ee] : bnd[(size_t)v * E + ee];
             const double den = x - mv, rr = (b - mv) / den;
             const double sg = rr < 0.0 ? -1.0 : 1.0;
-            bb[(up ? NV : 0) + vs] = sg * ab / den;
-            sm.sxb[ell] = -sg * rr * ab / den;
-            sm.sxpt[ell] = vs * NVP + xpt;
-            smb[ell][vs] += sg * ab * (rr - 1.0) / den;
+            bb[(up ? NV : 0) + v] = sg * ab / den;
+            sm.sxb[ell][v] = -sg * rr * ab / den;
+            sm.sxpt[ell][v] = xpt;
+            smb[ell][v] += sg * ab * (rr - 1.0) / den;
         }
         for (int k = 0; k < 2 * NV; k++) bndb[(size_t)k * E + ee] = bb[k];
     }
@@ -646,18 +659,16 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
     for (int t = tid; t < EPB_L * NFP; t += NT) {
         const int ell = t / NFP, fp = t % NFP;
         if (e0 + ell >= E) continue;
-        const double a = sm.salpha[ell];
         for (int v = 0; v < NV; v++)
-            sfb[ell][v][fp] = a * stfb[ell][v][fp] + (sm.sxpt[ell] == v * NVP + NS + fp ? sm.sxb[ell] : 0.0);
+            sfb[ell][v][fp] = aeff(ell, v) * stfb[ell][v][fp] + (sm.sxpt[ell][v] == NS + fp ? sm.sxb[ell][v] : 0.0);
     }
     __syncthreads();
     // 9. nodes: alpha * w~ cotangent + extreme point + mean (weights W / sum W) + faces
     //    (transposed interpolation), then the stage combination backwards
     if (!live) return;
     const int i = nd % N, j = nd / N;
-    const double a = sm.salpha[el];
     for (int v = 0; v < NV; v++) {
-        double g = a * stb[el][v][nd] + (sm.sxpt[el] == v * NVP + nd ? sm.sxb[el] : 0.0);
+        double g = aeff(el, v) * stb[el][v][nd] + (sm.sxpt[el][v] == nd ? sm.sxb[el][v] : 0.0);
         g += smb[el][v] * sm.sW[nd] / sm.sWsum;
         g += ops.lm[i] * sfb[el][v][0 * N + j] + ops.lp[i] * sfb[el][v][1 * N + j] +
              ops.lm[j] * sfb[el][v][2 * N + i] + ops.lp[j] * sfb[el][v][3 * N + i];

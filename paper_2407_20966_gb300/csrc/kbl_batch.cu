@@ -530,6 +530,7 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
     b->phys.rho_floor = cfg->rho_floor;
     b->phys.p_floor = cfg->p_floor;
     b->phys.eps_rule = cfg->eps_rule;
+    b->phys.uncoupled = cfg->uncoupled ? 1 : 0;
     b->phys.nu[0] = b->phys.nu[1] = NX_B;
     for (int q = 1; q <= PMAX_B; q++) kbl_build_fr_ops(q, b->ops.o[q]);
     b->P = P;

@@ -28,6 +28,7 @@ struct Phys {
     double gamma, k, r_fac, eps, rho_floor, p_floor;
     int eps_rule;
     int nu[2];
+    int uncoupled;
 };
 
 struct MeshDev {

@@ -299,10 +299,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     if (live && sfast[el]) {
         sP[el][nd] = 1.0;   // alpha = 1 and the box test passed: w~ = w, no pressure re-limit
     } else if (live) {
-        const double a = salpha[el];
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
+            const double a = ph.uncoupled ? salpha_v[el][v] : salpha[el];   // Eq. 38 (or per component)
             const double m = smean[el][v];
             q[v] = m + a * (sw[el][v][nd] - m);
             sw[el][v][nd] = q[v];
@@ -320,10 +320,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             sP[ell][NS + fp] = 1.0;
             continue;
         }
-        const double a = salpha[ell];
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
+            const double a = ph.uncoupled ? salpha_v[ell][v] : salpha[ell];
             const double m = smean[ell][v];
             q[v] = m + a * (sf[ell][v][fp] - m);
             sf[ell][v][fp] = q[v];

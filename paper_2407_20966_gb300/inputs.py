@@ -116,6 +116,33 @@ def sod(n=200, gamma=GAMMA):
     return mesh, ic
 
 
+def riemann_1d(n, left, right, x0, x1, xs, gamma=GAMMA):
+    """1D Riemann problem on [x0, x1]: primitive (rho, u, P) states left / right of xs, Dirichlet
+    ends carrying the two states."""
+    mesh = mesh_1d(n, x0, x1, periodic=False, bc_left=0, bc_right=1)
+    ql = conservative(left[0], [left[1]], left[2], gamma)
+    qr = conservative(right[0], [right[1]], right[2], gamma)
+    mesh.bc = np.stack([ql, qr]).astype(np.float64)
+
+    def ic(x):
+        return np.where(x <= xs, ql[:, None, None], qr[:, None, None])
+    return mesh, ic
+
+
+def problem_123(n=100, gamma=GAMMA):
+    """Double rarefaction ("123 problem", Sec. 6): [0, 1], (1, -2, 0.4) | (1, 2, 0.4) at x = 0.5."""
+    return riemann_1d(n, (1.0, -2.0, 0.4), (1.0, 2.0, 0.4), 0.0, 1.0, 0.5, gamma)
+
+
+LEBLANC_GAMMA = 5.0 / 3.0
+
+
+def leblanc(n=100, gamma=LEBLANC_GAMMA):
+    """Leblanc shock tube (Sec. 6): [0, 9], (1, 0, (gamma-1) 1e-1) | (1e-3, 0, (gamma-1) 1e-10) at
+    x = 3.  The paper does not restate gamma here; the problem's usual value 5/3 is taken."""
+    return riemann_1d(n, (1.0, 0.0, (gamma - 1) * 1e-1), (1e-3, 0.0, (gamma - 1) * 1e-10), 0.0, 9.0, 3.0, gamma)
+
+
 def density_pulse(n, gamma=GAMMA, sigma=500.0):
     """Smooth convecting pulse on periodic [-0.5, 0.5] (Sec. 6.2): rho = 1 + exp(-sigma x^2), u = 1, P = 1."""
     mesh = mesh_1d(n, -0.5, 0.5, periodic=True)

@@ -146,16 +146,17 @@ def test_bounds_vjp_single_state_stencil(orc):
 
 
 @pytest.mark.parametrize("stage", [0, 1, 2])
-@pytest.mark.parametrize("case", ["tight", "pressure"])
+@pytest.mark.parametrize("case", ["tight", "pressure", "uncoupled"])
 def test_stage_vjp_matches_fd(orc, stage, case):
     """Stage + limiter.  'tight': the kinetic bounds narrowed by a quarter of their width on both
     sides, so that Eq. 37 limits most elements; 'pressure': the bounds as computed and a
-    pressure floor of 0.5, so that Eq. 48-49 re-limit elements."""
+    pressure floor of 0.5, so that Eq. 48-49 re-limit elements; 'uncoupled': as 'tight' with each
+    component limited by its own factor."""
     from paper_2407_20966_gb300 import kbl
     p = 3
     p_floor = 0.5 if case == "pressure" else 1e-12
     mesh, w, rng = _field(orc, p, n=(6, 5), seed=20 + stage, kind="disc")
-    ctx = _ctx(mesh, p, nu=16, eps_rule=1, p_floor=p_floor)
+    ctx = _ctx(mesh, p, nu=16, eps_rule=1, p_floor=p_floor, uncoupled=int(case == "uncoupled"))
     E, ns, nfp = mesh.n_elem, ctx.ns, ctx.nfp
     wd = to_dev(w)
     wf = zeros_dev(4, E, nfp)
@@ -165,7 +166,7 @@ def test_stage_vjp_matches_fd(orc, stage, case):
     R = zeros_dev(4, E, ns)
     ctx.rhs(wd, wf, R)
     bnd0, R0 = bnd.cpu().numpy(), R.cpu().numpy()
-    if case == "tight":
+    if case in ("tight", "uncoupled"):
         width = bnd0[1] - bnd0[0]
         bnd0 = np.stack([bnd0[0] + 0.25 * width, bnd0[1] - 0.25 * width])
     bnd = to_dev(bnd0)
@@ -177,7 +178,7 @@ def test_stage_vjp_matches_fd(orc, stage, case):
     ctx.stage(stage, to_dev(wn), wd, R, bnd, dtd, out)
     st, c = ctx.counters()
     assert st == kbl.OK
-    assert (c["limited_elements"] if case == "tight" else c["pressure_relimits"]) > 0
+    assert (c["pressure_relimits"] if case == "pressure" else c["limited_elements"]) > 0
     ob = rng.standard_normal(w.shape)
     wnb, wsb, Rb, bndb = zeros_dev(*w.shape), zeros_dev(*w.shape), zeros_dev(*w.shape), zeros_dev(2, 4, E)
     ctx.stage_vjp(stage, dt, to_dev(wn), wd, R, bnd, to_dev(ob), wnb, wsb, Rb, bndb)

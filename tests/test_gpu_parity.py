@@ -223,6 +223,50 @@ def test_limit(orc, dim, p, n):
     assert (a_ref[0] < 1).any()
 
 
+@pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7)), (2, 2, (4, 13))])
+def test_limit_uncoupled(orc, dim, p, n):
+    """The independent limiting stated after Eq. 39 (uncoupled = 1): each component by its own
+    alpha_i, on both sides; it differs from the coupled result where the factors differ."""
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16), uncoupled=1)
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=160 + p, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    bnd = orc.bounds(ocfg, om, w, orc.traces(ocfg, om, w))
+    rng = np.random.default_rng(13)
+    w2 = w * (1 + 0.3 * rng.uniform(-1, 1, w.shape))
+    ref, a_ref = orc.limit(ocfg, om, w2, bnd)
+    wd = to_dev(w2)
+    alpha = zeros_dev(2, mesh.n_elem)
+    ctx.limit(wd, to_dev(bnd), alpha)
+    got = wd.cpu().numpy()
+    assert state_error(got, ref).max() < TOL_FP64
+    np.testing.assert_allclose(alpha.cpu().numpy(), a_ref, rtol=1e-10, atol=1e-12)
+    ocfg.uncoupled = 0
+    coupled, _ = orc.limit(ocfg, om, w2, bnd)
+    assert state_error(got, coupled).max() > 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_step_uncoupled(orc, precision):
+    ctx, ocfg = both(orc, 2, 3, (16, 16), precision=precision, uncoupled=1)
+    mesh, w = mesh_and_field(orc, 2, 3, (7, 6), seed=170, kind="disc")
+    om = upload(ctx, orc, mesh)
+    dt = orc.dt(ocfg, om, w, 0.05)
+    ref, _ = orc.ssprk3_step(ocfg, om, w, dt)
+    wd = to_dev(w)
+    ctx.set_time(0.0)
+    ctx.counters()
+    ctx.step(wd, 0.05)
+    st, c = ctx.counters()
+    assert st == 0 and c["limited_elements"] > 0
+    tol = TOL_FP64 if precision == 0 else TOL_FP32
+    err = state_error(wd.cpu().numpy(), ref).max(axis=(0, 2))
+    if precision == 0:
+        assert err.max() < tol
+    else:
+        # heavily limited elements amplify the FP32 bound error (conditioning of Eq. 37)
+        assert np.median(err) < tol
+
+
 def test_pressure_relimit_path(orc):
     """Elements with negative pressure at some nodes exercise Eq. 47-49 on both sides."""
     ctx, ocfg = both(orc, 2, 2, (16, 16))
