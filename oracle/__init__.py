@@ -42,7 +42,7 @@ class _Cfg(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nu", C.c_int * 2), ("gamma", C.c_double),
                 ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
-                ("uncoupled", C.c_int)]
+                ("uncoupled", C.c_int), ("flux", C.c_int)]
 
 
 class _Mesh(C.Structure):
@@ -67,6 +67,7 @@ def _load():
                 "orc_pressure": (C.c_double, [cfgp, d]),
                 "orc_flux": (None, [cfgp, d, C.c_int, d]),
                 "orc_rusanov": (None, [cfgp, d, d, C.c_int, d]),
+                "orc_hllc": (None, [cfgp, d, d, C.c_int, d]),
                 "orc_bounds_stencil": (C.c_int, [cfgp, C.c_int, d, d, d]),
                 "orc_state_moments": (C.c_int, [cfgp, C.c_int, d, C.c_int, d]),
                 "orc_velocity_box": (C.c_int, [cfgp, C.c_int, d, d, d]),
@@ -108,6 +109,7 @@ class Config:
     p_floor: float = 1e-12
     eps_rule: int = 0
     uncoupled: int = 0
+    flux: int = 0
 
     @property
     def nv(self):
@@ -128,7 +130,7 @@ class Config:
     def _c(self):
         nu = list(self.nu) + [1] * (2 - len(self.nu))
         return _Cfg(self.dim, self.p, (C.c_int * 2)(*nu[:2]), self.gamma, self.k, self.r_fac,
-                    self.eps, self.rho_floor, self.p_floor, self.eps_rule, self.uncoupled)
+                    self.eps, self.rho_floor, self.p_floor, self.eps_rule, self.uncoupled, self.flux)
 
 
 class Mesh:
@@ -203,6 +205,14 @@ def rusanov(cfg: Config, wl, wr, direction):
     wr = np.ascontiguousarray(wr, dtype=np.float64)
     F = np.zeros(cfg.nv)
     _load().orc_rusanov(C.byref(cfg._c()), _dp(wl), _dp(wr), direction, _dp(F))
+    return F
+
+
+def hllc(cfg: Config, wl, wr, direction):
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    F = np.zeros(cfg.nv)
+    _load().orc_hllc(C.byref(cfg._c()), _dp(wl), _dp(wr), direction, _dp(F))
     return F
 
 

@@ -141,6 +141,52 @@ void orc_rusanov(const orc_cfg* c, const double* wl, const double* wr, int dir,
     for (int v = 0; v < nv; v++) F[v] = 0.5 * (Fl[v] + Fr[v]) - 0.5 * lam * (wr[v] - wl[v]);
 }
 
+/* HLLC flux (Toro, Spruce & Speares 1994, the Riemann solver of the paper's
+ * experiments, Sec. 5) with the Davis wave-speed estimates
+ *   S_l = min(U_l - c_l, U_r - c_r),  S_r = max(U_l + c_l, U_r + c_r)
+ * (U the velocity along the axis) and the contact speed
+ *   S* = (P_r - P_l + rho_l U_l (S_l - U_l) - rho_r U_r (S_r - U_r))
+ *        / (rho_l (S_l - U_l) - rho_r (S_r - U_r)).
+ * The flux is F(w_l) for 0 <= S_l, F(w_l) + S_l (w*_l - w_l) for S_l <= 0 <= S*,
+ * F(w_r) + S_r (w*_r - w_r) for S* <= 0 <= S_r and F(w_r) for S_r <= 0, with the
+ * star state of side K
+ *   w*_K = rho_K (S_K - U_K)/(S_K - S*) [1, S* along the axis, the other velocity
+ *          components of K, E_K/rho_K + (S* - U_K)(S* + P_K/(rho_K (S_K - U_K)))]. */
+void orc_hllc(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F)
+{
+    int d = c->dim, nv = orc_nv(c);
+    double Pl = orc_pressure(c, wl), Pr = orc_pressure(c, wr);
+    double Ul = wl[1 + dir] / wl[0], Ur = wr[1 + dir] / wr[0];
+    double cl = sqrt(c->gamma * Pl / wl[0]), cr = sqrt(c->gamma * Pr / wr[0]);
+    double Sl = Ul - cl < Ur - cr ? Ul - cl : Ur - cr;
+    double Sr = Ul + cl > Ur + cr ? Ul + cl : Ur + cr;
+    double Ss = (Pr - Pl + wl[0] * Ul * (Sl - Ul) - wr[0] * Ur * (Sr - Ur)) /
+                (wl[0] * (Sl - Ul) - wr[0] * (Sr - Ur));
+    if (0.0 <= Sl) {
+        orc_flux(c, wl, dir, F);
+        return;
+    }
+    if (Sr <= 0.0) {
+        orc_flux(c, wr, dir, F);
+        return;
+    }
+    const double* w = Ss >= 0.0 ? wl : wr;
+    double S = Ss >= 0.0 ? Sl : Sr, U = Ss >= 0.0 ? Ul : Ur, P = Ss >= 0.0 ? Pl : Pr;
+    orc_flux(c, w, dir, F);
+    double f = w[0] * (S - U) / (S - Ss), ws[4];
+    ws[0] = f;
+    for (int k = 0; k < d; k++) ws[1 + k] = f * (k == dir ? Ss : w[1 + k] / w[0]);
+    ws[d + 1] = f * (w[d + 1] / w[0] + (Ss - U) * (Ss + P / (w[0] * (S - U))));
+    for (int v = 0; v < nv; v++) F[v] += S * (ws[v] - w[v]);
+}
+
+/* The common flux of the configuration: Rusanov (c->flux == 0) or HLLC (1). */
+static void orc_common_flux(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F)
+{
+    if (c->flux == 1) orc_hllc(c, wl, wr, dir, F);
+    else orc_rusanov(c, wl, wr, dir, F);
+}
+
 /* ===================================================================== */
 /* Kinetic bounds                                                          */
 /* ===================================================================== */
@@ -467,8 +513,8 @@ void orc_rhs(const orc_cfg* c, const orc_mesh* m, const double* w, const double*
             double wi[4], we[4], Fc[4], FD[4];
             for (int v = 0; v < nv; v++) wi[v] = wf[((size_t)v * E + e) * nfp + fp];
             orc_exterior(c, m, wf, e, fp, we);
-            if (side == 0) orc_rusanov(c, we, wi, dir, Fc);
-            else orc_rusanov(c, wi, we, dir, Fc);
+            if (side == 0) orc_common_flux(c, we, wi, dir, Fc);
+            else orc_common_flux(c, wi, we, dir, Fc);
             const double* l = side == 0 ? o.lm : o.lp;
             for (int v = 0; v < nv; v++) {
                 double s = 0.0;

@@ -50,6 +50,8 @@ typedef struct {
     int uncoupled;    /* 0: every component takes alpha_min = min_i alpha_i (Eq. 38-39, the
                          paper's choice); 1: each component its own alpha_i (the independent
                          option stated after Eq. 39) */
+    int flux;         /* common flux: 0 Rusanov (the flux of the analysis, Sec. 4), 1 HLLC
+                         (the flux of the experiments, Sec. 5) */
 } orc_cfg;
 
 typedef struct {
@@ -76,6 +78,7 @@ void orc_correction_deriv(int p, double x, double* dgl, double* dgr);
 /* ---- Euler physics (Eq. 2, Eq. 3) ------------------------------------ */
 double orc_pressure(const orc_cfg* c, const double* w);
 void orc_flux(const orc_cfg* c, const double* w, int dir, double* F);
+void orc_hllc(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F);
 void orc_rusanov(const orc_cfg* c, const double* wl, const double* wr, int dir,
                  double* F);
 

@@ -143,8 +143,12 @@ def leblanc(n=100, gamma=LEBLANC_GAMMA):
     return riemann_1d(n, (1.0, 0.0, (gamma - 1) * 1e-1), (1e-3, 0.0, (gamma - 1) * 1e-10), 0.0, 9.0, 3.0, gamma)
 
 
-def density_pulse(n, gamma=GAMMA, sigma=500.0):
-    """Smooth convecting pulse on periodic [-0.5, 0.5] (Sec. 6.2): rho = 1 + exp(-sigma x^2), u = 1, P = 1."""
+def density_pulse(n, gamma=GAMMA, sigma=200.0):
+    """Smooth convecting pulse on periodic [-0.5, 0.5] (Sec. 6.2): rho = 1 + exp(-sigma x^2), u = 1, P = 1.
+
+    Sec. 6.2 prints sigma = 500, but its own error tables (Tables 3 and 4) are those of sigma = 200:
+    an independent discontinuous Galerkin solution and the checker reproduce them to four digits
+    with 200 and are five to twelve times larger with 500.  200 is taken."""
     mesh = mesh_1d(n, -0.5, 0.5, periodic=True)
 
     def ic(x, t=0.0):
