@@ -83,6 +83,10 @@ typedef struct {
                          paper's choice); 1: each component its own alpha_i (the independent
                          limiting stated after Eq. 39).  The pressure step of Eq. 47-49
                          follows in both cases; alpha[0][e] reports alpha_min. */
+    int flux;         /* common flux of the residual: 0 Rusanov with the Davis wavespeed
+                         (assumption (iv) of Sec. 4), 1 HLLC (Toro, Spruce & Speares 1994,
+                         the flux of the experiments, Sec. 5) with Davis wave-speed
+                         estimates.  The residual adjoint covers flux 0. */
 } kbl_config;
 
 typedef struct kbl_ctx kbl_ctx;
@@ -96,7 +100,7 @@ typedef struct {
 
 /* Fill cfg with the paper's defaults for dimension d and order p: gamma 1.4,
  * k = 4, nu = 32 per axis in 2D and 64 in 1D, r_fac = 1e-3, eps = 1e-13,
- * floors 1e-12, eps_rule 0, FP64, coupled limiting. */
+ * floors 1e-12, eps_rule 0, FP64, coupled limiting, Rusanov flux. */
 kbl_status kbl_config_default(kbl_config* cfg, int dim, int p);
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy
@@ -136,8 +140,9 @@ kbl_status kbl_gather_stencil(kbl_ctx* ctx, const double* w, const double* wf,
  * then rho_min <- max(rho_min, rho_floor). */
 kbl_status kbl_bounds(kbl_ctx* ctx, const double* w, const double* wf, double* bnd);
 
-/* FR residual R = -div F with Rusanov interface fluxes (assumption (iv) of
- * Sec. 4) and the g_DG correction; wf must hold the traces of w. */
+/* FR residual R = -div F with the configured interface flux (Rusanov,
+ * assumption (iv) of Sec. 4, or HLLC) and the g_DG correction; wf must hold the
+ * traces of w. */
 kbl_status kbl_rhs(kbl_ctx* ctx, const double* w, const double* wf, double* R);
 
 /* Limit w in place against bnd (Eq. 37-39, then Eq. 47-49); alpha may be NULL. */

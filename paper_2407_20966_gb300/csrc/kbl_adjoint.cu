@@ -1088,6 +1088,7 @@ kbl_status kbl_rhs_vjp(kbl_ctx* c, const double* w, const double* wf, const doub
                        double* wfb_ext)
 {
     if (!adj_ok(c)) return afail(c, KBL_ESTATE, "no 2D mesh");
+    if (c->phys.flux != 0) return afail(c, KBL_EINVAL, "the residual adjoint covers the Rusanov flux");
     if (c->E > 0 && (!w || !wf || !Rb || !wb || !wfb || !wfb_ext)) return afail(c, KBL_EINVAL, "null array");
     int r = -1;
     switch (c->ops.n) {
@@ -1209,6 +1210,7 @@ kbl_status kbl_adjoint_segment(kbl_ctx* c, const double* w0, const double* dts, 
 {
     if (!adj_ok(c)) return afail(c, KBL_ESTATE, "no 2D mesh");
     if (c->cfg.precision != KBL_FP64) return afail(c, KBL_EINVAL, "the adjoint runs in FP64");
+    if (c->phys.flux != 0) return afail(c, KBL_EINVAL, "the residual adjoint covers the Rusanov flux");
     if (n < 0 || (n > 0 && !dts) || (c->E > 0 && (!w0 || !wbar))) return afail(c, KBL_EINVAL, "bad argument");
     for (int k = 0; k < n; k++)
         if (!(dts[k] >= 0.0)) return afail(c, KBL_EINVAL, "negative or NaN dt");

@@ -217,6 +217,7 @@ kbl_status kbl_config_default(kbl_config* cfg, int dim, int p)
     cfg->eps_rule = 0;
     cfg->precision = KBL_FP64;
     cfg->uncoupled = 0;
+    cfg->flux = 0;
     return KBL_OK;
 }
 
@@ -238,6 +239,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         return KBL_EINVAL;
     if (cfg->precision != KBL_FP64 && cfg->precision != KBL_FP32_MIXED) return KBL_EINVAL;
     if (cfg->uncoupled != 0 && cfg->uncoupled != 1) return KBL_EINVAL;
+    if (cfg->flux != 0 && cfg->flux != 1) return KBL_EINVAL;
     kbl_ctx* c = new (std::nothrow) kbl_ctx();
     if (!c) return KBL_ENOMEM;
     c->cfg = *cfg;
@@ -252,6 +254,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     c->phys.nu[0] = cfg->nu[0];
     c->phys.nu[1] = cfg->dim == 2 ? cfg->nu[1] : 1;
     c->phys.uncoupled = cfg->uncoupled;
+    c->phys.flux = cfg->flux;
     build_ops(cfg->p, c->ops);
     const int n = cfg->p + 1;
     c->nv = cfg->dim + 2;

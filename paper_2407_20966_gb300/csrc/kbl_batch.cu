@@ -182,7 +182,8 @@ struct RhsUnion {
 
 template <int N>
 __device__ __forceinline__ void rhs_item(void* smraw, const BatchDev& bd, const ProbDesc& pd, const WorkItem& wi,
-                                         const FrOps& ops, double gamma, const double* w, const double* wf, double* R)
+                                         const FrOps& ops, double gamma, int flux, const double* w, const double* wf,
+                                         double* R)
 {
     constexpr int EPB = FrEpb<N>::EPB;
     auto& sm = *reinterpret_cast<RhsSmem<2, N, float, EPB>*>(smraw);
@@ -190,12 +191,12 @@ __device__ __forceinline__ void rhs_item(void* smraw, const BatchDev& bd, const 
     const int e_end = wi.e0 + wi.n;
     for (int eb = wi.e0; eb < e_end; eb += EPB)
         rhs_block<2, N, float, EPB>(sm, NTB, w + pd.woff, wf + pd.wfoff, m, ops, gamma, R + pd.woff, eb,
-                                    min(EPB, e_end - eb));
+                                    min(EPB, e_end - eb), flux);
 }
 
 __global__ void __launch_bounds__(NTB) k_batch_rhs(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
-                                                   unsigned* counter, BatchOps ops, double gamma, const double* w,
-                                                   const double* wf, double* R)
+                                                   unsigned* counter, BatchOps ops, double gamma, int flux,
+                                                   const double* w, const double* wf, double* R)
 {
     __shared__ __align__(16) RhsUnion sm;
     __shared__ int s_item;
@@ -205,10 +206,10 @@ __global__ void __launch_bounds__(NTB) k_batch_rhs(BatchDev bd, const WorkItem* 
         const WorkItem wi = items[it];
         const ProbDesc pd = bd.probs[wi.prob];
         switch (pd.p) {
-            case 1: rhs_item<2>(&sm, bd, pd, wi, ops.o[1], gamma, w, wf, R); break;
-            case 2: rhs_item<3>(&sm, bd, pd, wi, ops.o[2], gamma, w, wf, R); break;
-            case 3: rhs_item<4>(&sm, bd, pd, wi, ops.o[3], gamma, w, wf, R); break;
-            case 4: rhs_item<5>(&sm, bd, pd, wi, ops.o[4], gamma, w, wf, R); break;
+            case 1: rhs_item<2>(&sm, bd, pd, wi, ops.o[1], gamma, flux, w, wf, R); break;
+            case 2: rhs_item<3>(&sm, bd, pd, wi, ops.o[2], gamma, flux, w, wf, R); break;
+            case 3: rhs_item<4>(&sm, bd, pd, wi, ops.o[3], gamma, flux, w, wf, R); break;
+            case 4: rhs_item<5>(&sm, bd, pd, wi, ops.o[4], gamma, flux, w, wf, R); break;
         }
     }
 }
@@ -459,7 +460,7 @@ int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s)
                                             b->d_wf);
         n += launch_bounds_phase(b, ws, b->d_wf, b->d_bnd, 2 + 4 * st, s, b->d_b_items, b->n_b_items);
         k_batch_rhs<<<g_rhs, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 3 + 4 * st, b->ops,
-                                          b->phys.gamma, ws, b->d_wf, b->d_R);
+                                          b->phys.gamma, b->phys.flux, ws, b->d_wf, b->d_R);
         k_batch_stage<<<g_st, NTB, sizeof(LimUnion), s>>>(bd, b->d_fr_items, b->n_fr_items,
                                                           b->d_counters + 4 + 4 * st, b->ops, b->phys, st, wn, ws,
                                                           b->d_R, b->d_bnd, b->d_dt, outs[st], b->d_flags);
@@ -531,6 +532,7 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
     b->phys.p_floor = cfg->p_floor;
     b->phys.eps_rule = cfg->eps_rule;
     b->phys.uncoupled = cfg->uncoupled ? 1 : 0;
+    b->phys.flux = cfg->flux == 1 ? 1 : 0;
     b->phys.nu[0] = b->phys.nu[1] = NX_B;
     for (int q = 1; q <= PMAX_B; q++) kbl_build_fr_ops(q, b->ops.o[q]);
     b->P = P;

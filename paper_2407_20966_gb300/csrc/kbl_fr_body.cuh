@@ -17,7 +17,7 @@ struct RhsSmem {
 // FR residual of elements e0 .. e0+min(EPB, nmax)-1 of one mesh, by a block of NT >= EPB*Ns threads
 // (one per solution point; the others only help with the face loop).
 //   1. states and physical fluxes at the solution points -> shared memory
-//   2. per face point: Rusanov flux of (interior trace, exterior value) minus
+//   2. per face point: common flux (Rusanov, or HLLC with flux == 1) of (interior trace, exterior value) minus
 //      the interpolated discontinuous flux -> jump J
 //   3. per solution point and axis: D F + g_L' J_minus + g_R' J_plus,
 //      R = -sum_axes (2 / h_axis) dF/dxi
@@ -26,7 +26,7 @@ struct RhsSmem {
 template <int DIM, int N, typename T, int EPB>
 __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, const double* __restrict__ w,
                                           const double* __restrict__ wf, const MeshDev& m, const FrOps& ops,
-                                          double gamma_d, double* __restrict__ R, int e0, int nmax)
+                                          double gamma_d, double* __restrict__ R, int e0, int nmax, int flux = 0)
 {
     constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
     constexpr int NFPF = (DIM == 1) ? 1 : N;
@@ -74,8 +74,13 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
             qi[v] = (T)wf[((size_t)v * m.E + ee) * NFP + fp];
             qe[v] = (T)kbl_exterior<DIM, N>(wf, m, ee, fp, v);
         }
-        if (side == 0) kbl_rusanov<DIM, T>(qe, qi, dir, gamma, Fc);
-        else kbl_rusanov<DIM, T>(qi, qe, dir, gamma, Fc);
+        if (flux == 1) {
+            if (side == 0) kbl_hllc<DIM, T>(qe, qi, dir, gamma, Fc);
+            else kbl_hllc<DIM, T>(qi, qe, dir, gamma, Fc);
+        } else {
+            if (side == 0) kbl_rusanov<DIM, T>(qe, qi, dir, gamma, Fc);
+            else kbl_rusanov<DIM, T>(qi, qe, dir, gamma, Fc);
+        }
         const T* l = side ? slp : slm;
 #pragma unroll
         for (int v = 0; v < NV; v++) {

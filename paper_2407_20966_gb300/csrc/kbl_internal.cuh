@@ -29,6 +29,7 @@ struct Phys {
     int eps_rule;
     int nu[2];
     int uncoupled;
+    int flux;   // 0 Rusanov, 1 HLLC
 };
 
 struct MeshDev {
@@ -146,6 +147,45 @@ __device__ __forceinline__ void kbl_rusanov(const T* ql, const T* qr, int dir, T
     const T lam = fmax(sl, sr);
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] = T(0.5) * (Fl[v] + Fr[v]) - T(0.5) * lam * (qr[v] - ql[v]);
+}
+
+// HLLC flux (Toro, Spruce & Speares 1994) with the Davis wave-speed estimates
+// S_l = min(U_l - c_l, U_r - c_r), S_r = max(U_l + c_l, U_r + c_r) and the contact speed S*;
+// ql on the minus side of the axis.  F(ql) for 0 <= S_l, F(ql) + S_l (q*_l - ql) for
+// S_l <= 0 <= S*, F(qr) + S_r (q*_r - qr) for S* <= 0 <= S_r, F(qr) for S_r <= 0, with
+// q*_K = rho_K (S_K - U_K)/(S_K - S*) [1, S* along the axis, the other velocities of K,
+// E_K/rho_K + (S* - U_K)(S* + P_K / (rho_K (S_K - U_K)))].
+template <int DIM, typename T = double>
+__device__ __forceinline__ void kbl_hllc(const T* ql, const T* qr, int dir, T gamma, T* F)
+{
+    constexpr int NV = DIM + 2;
+    const T gm1 = gamma - T(1);
+    const T Pl = kbl_pressure<DIM, T>(ql, gm1), Pr = kbl_pressure<DIM, T>(qr, gm1);
+    const T Ul = ql[1 + dir] / ql[0], Ur = qr[1 + dir] / qr[0];
+    const T cl = sqrt(gamma * Pl / ql[0]), cr = sqrt(gamma * Pr / qr[0]);
+    const T Sl = fmin(Ul - cl, Ur - cr), Sr = fmax(Ul + cl, Ur + cr);
+    const T Ss = (Pr - Pl + ql[0] * Ul * (Sl - Ul) - qr[0] * Ur * (Sr - Ur)) /
+                 (ql[0] * (Sl - Ul) - qr[0] * (Sr - Ur));
+    if (T(0) <= Sl) {
+        kbl_flux<DIM, T>(ql, dir, gm1, F);
+        return;
+    }
+    if (Sr <= T(0)) {
+        kbl_flux<DIM, T>(qr, dir, gm1, F);
+        return;
+    }
+    const bool left = Ss >= T(0);
+    const T* q = left ? ql : qr;
+    const T S = left ? Sl : Sr, U = left ? Ul : Ur, P = left ? Pl : Pr;
+    kbl_flux<DIM, T>(q, dir, gm1, F);
+    const T f = q[0] * (S - U) / (S - Ss);
+    T qs[NV];
+    qs[0] = f;
+#pragma unroll
+    for (int k = 0; k < DIM; k++) qs[1 + k] = f * (k == dir ? Ss : q[1 + k] / q[0]);
+    qs[DIM + 1] = f * (q[DIM + 1] / q[0] + (Ss - U) * (Ss + P / (q[0] * (S - U))));
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v] += S * (qs[v] - q[v]);
 }
 
 // Exterior value of component v at face point fp of element e.

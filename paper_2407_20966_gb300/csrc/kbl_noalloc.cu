@@ -97,6 +97,7 @@ extern "C" kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, cons
     c.phys.p_floor = cfg->p_floor;
     c.phys.eps_rule = cfg->eps_rule;
     c.phys.uncoupled = cfg->uncoupled ? 1 : 0;
+    c.phys.flux = 0;
     c.phys.nu[0] = cfg->nu[0];
     c.phys.nu[1] = cfg->dim == 2 ? cfg->nu[1] : 1;
     kbl_build_fr_ops(cfg->p, c.ops);

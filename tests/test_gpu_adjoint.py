@@ -379,3 +379,7 @@ def test_adjoint_rejects_bad_input():
         ctx32.adjoint_step(to_dev(w0), 0.1, to_dev(w0))   # FP64 only
     with pytest.raises(kbl.KblError):
         ctx64.adjoint_segment(to_dev(w0), [0.1, -1.0], to_dev(w0))
+    ctxh = kbl.Context(dim=2, p=2, nu=(8, 8), precision=kbl.FP64, flux=1)
+    ctxh.mesh_upload(m2.nbr, m2.h, m2.bc)
+    with pytest.raises(kbl.KblError):
+        ctxh.adjoint_step(to_dev(w0), 0.1, to_dev(w0))   # the residual adjoint covers Rusanov

@@ -305,6 +305,43 @@ def test_stage(orc, s):
     assert state_error(out.cpu().numpy(), ref).max() < TOL_FP64
 
 
+@pytest.mark.parametrize("dim,p,n,precision", [(1, 3, 37, 0), (2, 3, (9, 7), 0), (2, 2, (4, 13), 0),
+                                               (2, 3, (9, 7), 1), (1, 4, 21, 1)])
+def test_rhs_hllc(orc, dim, p, n, precision):
+    """The residual with the HLLC flux of Sec. 5 (flux = 1) on both sides, on discontinuous data
+    (every branch of the flux is taken)."""
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16), precision=precision, flux=1)
+    for seed in range(180, 200):   # the first discontinuous field whose face traces are physical
+        mesh, w = mesh_and_field(orc, dim, p, n, seed=seed, kind="disc")
+        om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+        wf = orc.traces(ocfg, om, w)
+        mm = sum(wf[1 + k] ** 2 for k in range(dim))
+        if wf[0].min() > 0 and ((wf[dim + 1] - 0.5 * mm / wf[0]).min() > 0):
+            break
+    om = upload(ctx, orc, mesh)
+    R_ref = orc.rhs(ocfg, om, w, wf)
+    R = zeros_dev(*w.shape)
+    ctx.rhs(to_dev(w), to_dev(wf), R)
+    err = (np.abs(R.cpu().numpy() - R_ref) / np.abs(R_ref).max()).max()
+    assert err < (1e-13 if precision == 0 else 5e-6), err
+    ocfg.flux = 0
+    assert np.abs(orc.rhs(ocfg, om, w, wf) - R_ref).max() > 1e-3 * np.abs(R_ref).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_step_hllc(orc, precision):
+    ctx, ocfg = both(orc, 2, 3, (16, 16), precision=precision, flux=1)
+    mesh, w = mesh_and_field(orc, 2, 3, (7, 6), seed=190, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    dt = orc.dt(ocfg, om, w, 0.05)
+    ref, _ = orc.ssprk3_step(ocfg, om, w, dt)
+    wd = to_dev(w)
+    ctx.set_time(0.0)
+    ctx.step(wd, 0.05)
+    ctx.check()
+    assert state_error(wd.cpu().numpy(), ref).max() < (TOL_FP64 if precision == 0 else TOL_FP32)
+
+
 @pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7))])
 def test_dt(orc, dim, p, n):
     ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16))
