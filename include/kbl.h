@@ -69,7 +69,9 @@ typedef enum { KBL_FP64 = 0, KBL_FP32_MIXED = 1 } kbl_precision;
 typedef struct {
     int dim;          /* 1 or 2 */
     int p;            /* polynomial order, 1..5 */
-    int nu[2];        /* velocity points per axis (Sec. 3.7); 2D: 8, 16, 32 or 64; 1D: 2..4096 */
+    int nu[2];        /* velocity points per axis (Sec. 3.7); 2D: nu[0] == nu[1], 2..64 (8, 16,
+                         32 and 64 fill the kernels' tiles; other counts run on the next
+                         tile up with zero-weight padding); 1D: 2..4096 */
     double gamma;     /* ratio of specific heats */
     double k;         /* box half-width in thermal units, Eq. 45 (4 in Sec. 5) */
     double r_fac;     /* relaxation of the envelopes, Eq. 40 (1e-3; 0 = strict) */
@@ -85,8 +87,16 @@ typedef struct {
                          follows in both cases; alpha[0][e] reports alpha_min. */
     int flux;         /* common flux of the residual: 0 Rusanov with the Davis wavespeed
                          (assumption (iv) of Sec. 4), 1 HLLC (Toro, Spruce & Speares 1994,
-                         the flux of the experiments, Sec. 5) with Davis wave-speed
-                         estimates.  The residual adjoint covers flux 0. */
+                         the flux of the experiments, Sec. 5), 2 HLL (Harten, Lax & van
+                         Leer 1983, the flux of the Sedov run, Sec. 6.6), both with Davis
+                         wave-speed estimates.  Other values: KBL_EINVAL.  The residual
+                         adjoint covers flux 0. */
+    int quadrature;   /* velocity quadrature on the equispaced grid: 0 the trapezoidal rule
+                         (Sec. 3.7, Sec. 5), 1 Romberg (the alternative Sec. 5 names): with
+                         nu - 1 = 2^L m, m odd, Richardson extrapolation of the L + 1 nested
+                         trapezoidal sums of steps 2^L h .. h; needs nu - 1 even (KBL_EINVAL
+                         otherwise).  Its weights are positive, so every envelope argument
+                         of Sec. 4 holds unchanged.  The bounds adjoint covers 0. */
 } kbl_config;
 
 typedef struct kbl_ctx kbl_ctx;
@@ -209,9 +219,11 @@ kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
  * buffer, with the single-mesh layout w_i[4][E_i][(p_i+1)^2]. */
 typedef struct kbl_batch kbl_batch;
 
-/* cfg supplies dim (must be 2), nu, gamma, k, r_fac, eps, floors and the eps
- * reading; cfg->p is ignored and cfg->precision must be KBL_FP32_MIXED.  HOST
- * arrays, copied.  Synchronous; allocates the batch's device memory. */
+/* cfg supplies dim (must be 2), nu (must be 32 x 32), gamma, k, r_fac, eps,
+ * floors, the eps reading, the limiting form and the flux; cfg->p is ignored,
+ * cfg->precision must be KBL_FP32_MIXED and cfg->quadrature 0 (KBL_EINVAL
+ * otherwise).  HOST arrays, copied.  Synchronous; allocates the batch's device
+ * memory. */
 kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int n_problems,
                             const int32_t* p, const int32_t* n_elem, const int32_t* nbr,
                             const double* h, const int32_t* n_bc, const double* bc,
@@ -337,7 +349,9 @@ kbl_status kbl_adjoint_segment(kbl_ctx* ctx, const double* w0, const double* dts
  * device array of 2^20 doubles (8 MiB) that every GPU loading the library
  * keeps until the process exits, so n_elem * (d+2) * Nfp must not exceed
  * 1048576 (16384 two-dimensional P3 elements); larger meshes, like bad
- * configurations, return KBL_EINVAL before anything is launched.  No
+ * configurations, return KBL_EINVAL before anything is launched.  The
+ * trapezoidal rule only (quadrature 0): a weight table would need an
+ * allocation.  No
  * cudaMalloc, cudaFree or other allocating routine is called.  Asynchronous;
  * a non-physical stencil state gives NaN bounds for its element.  The first
  * call on each device looks up the device address of the scratch array

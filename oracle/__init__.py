@@ -42,7 +42,7 @@ class _Cfg(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nu", C.c_int * 2), ("gamma", C.c_double),
                 ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
-                ("uncoupled", C.c_int), ("flux", C.c_int)]
+                ("uncoupled", C.c_int), ("flux", C.c_int), ("quadrature", C.c_int)]
 
 
 class _Mesh(C.Structure):
@@ -68,6 +68,8 @@ def _load():
                 "orc_flux": (None, [cfgp, d, C.c_int, d]),
                 "orc_rusanov": (None, [cfgp, d, d, C.c_int, d]),
                 "orc_hllc": (None, [cfgp, d, d, C.c_int, d]),
+                "orc_hll": (None, [cfgp, d, d, C.c_int, d]),
+                "orc_romberg_weight": (C.c_double, [C.c_int, C.c_int]),
                 "orc_bounds_stencil": (C.c_int, [cfgp, C.c_int, d, d, d]),
                 "orc_state_moments": (C.c_int, [cfgp, C.c_int, d, C.c_int, d]),
                 "orc_velocity_box": (C.c_int, [cfgp, C.c_int, d, d, d]),
@@ -110,6 +112,7 @@ class Config:
     eps_rule: int = 0
     uncoupled: int = 0
     flux: int = 0
+    quadrature: int = 0
 
     @property
     def nv(self):
@@ -130,7 +133,8 @@ class Config:
     def _c(self):
         nu = list(self.nu) + [1] * (2 - len(self.nu))
         return _Cfg(self.dim, self.p, (C.c_int * 2)(*nu[:2]), self.gamma, self.k, self.r_fac,
-                    self.eps, self.rho_floor, self.p_floor, self.eps_rule, self.uncoupled, self.flux)
+                    self.eps, self.rho_floor, self.p_floor, self.eps_rule, self.uncoupled, self.flux,
+                    self.quadrature)
 
 
 class Mesh:
@@ -213,6 +217,19 @@ def hllc(cfg: Config, wl, wr, direction):
     wr = np.ascontiguousarray(wr, dtype=np.float64)
     F = np.zeros(cfg.nv)
     _load().orc_hllc(C.byref(cfg._c()), _dp(wl), _dp(wr), direction, _dp(F))
+    return F
+
+
+def romberg_weights(n):
+    """Romberg weights, in units of the grid spacing, of an axis of n equispaced nodes."""
+    return np.array([_load().orc_romberg_weight(n, j) for j in range(n)])
+
+
+def hll(cfg: Config, wl, wr, direction):
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    F = np.zeros(cfg.nv)
+    _load().orc_hll(C.byref(cfg._c()), _dp(wl), _dp(wr), direction, _dp(F))
     return F
 
 

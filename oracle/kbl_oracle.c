@@ -180,10 +180,37 @@ void orc_hllc(const orc_cfg* c, const double* wl, const double* wr, int dir, dou
     for (int v = 0; v < nv; v++) F[v] += S * (ws[v] - w[v]);
 }
 
-/* The common flux of the configuration: Rusanov (c->flux == 0) or HLLC (1). */
+/* HLL flux (Harten, Lax & van Leer 1983; the Riemann solver of the Sedov run,
+ * Sec. 6.6) with the same Davis estimates S_l, S_r as above:
+ *   F(w_l) for 0 <= S_l,  F(w_r) for S_r <= 0, and otherwise the flux of the single
+ *   intermediate state,  (S_r F(w_l) - S_l F(w_r) + S_l S_r (w_r - w_l)) / (S_r - S_l). */
+void orc_hll(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F)
+{
+    int nv = orc_nv(c);
+    double Pl = orc_pressure(c, wl), Pr = orc_pressure(c, wr);
+    double Ul = wl[1 + dir] / wl[0], Ur = wr[1 + dir] / wr[0];
+    double cl = sqrt(c->gamma * Pl / wl[0]), cr = sqrt(c->gamma * Pr / wr[0]);
+    double Sl = Ul - cl < Ur - cr ? Ul - cl : Ur - cr;
+    double Sr = Ul + cl > Ur + cr ? Ul + cl : Ur + cr;
+    if (0.0 <= Sl) {
+        orc_flux(c, wl, dir, F);
+        return;
+    }
+    if (Sr <= 0.0) {
+        orc_flux(c, wr, dir, F);
+        return;
+    }
+    double Fl[4], Fr[4];
+    orc_flux(c, wl, dir, Fl);
+    orc_flux(c, wr, dir, Fr);
+    for (int v = 0; v < nv; v++) F[v] = (Sr * Fl[v] - Sl * Fr[v] + Sl * Sr * (wr[v] - wl[v])) / (Sr - Sl);
+}
+
+/* The common flux of the configuration: Rusanov (c->flux == 0), HLLC (1) or HLL (2). */
 static void orc_common_flux(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F)
 {
     if (c->flux == 1) orc_hllc(c, wl, wr, dir, F);
+    else if (c->flux == 2) orc_hll(c, wl, wr, dir, F);
     else orc_rusanov(c, wl, wr, dir, F);
 }
 
@@ -238,14 +265,38 @@ static void orc_box(int d, double kk, int nS, const orc_maxw* g, double* lo, dou
     }
 }
 
-/* Equispaced velocity grid over [lo, hi] with trapezoidal weights (Sec. 3.7):
- * u_j = lo + j h, h = (hi - lo)/(N - 1), weight h (h/2 at both ends). */
-static void orc_grid(int N, double lo, double hi, double* u, double* wq)
+/* Romberg weight of node j, in units of h, on an axis of N equispaced nodes (the
+ * quadrature Sec. 5 names beside the trapezoidal rule).  Romberg's method is linear in the
+ * node values, so node j's weight is what the method returns for values 1 at node j and 0
+ * elsewhere.  With N - 1 = 2^L m (m odd): R(k, 0) is the trapezoidal sum of step
+ * 2^(L-k) h (k = 0 the coarsest), R(k, i) = R(k, i-1) + (R(k, i-1) - R(k-1, i-1)) / (4^i - 1)
+ * for 1 <= i <= k, and the weight is R(L, L). */
+double orc_romberg_weight(int N, int j)
+{
+    int L = 0;
+    while ((N - 1) % (2 << L) == 0) L++;
+    double R[24][24];
+    for (int k = 0; k <= L; k++) {
+        int step = 1 << (L - k);
+        R[k][0] = (j % step != 0) ? 0.0 : (j == 0 || j == N - 1) ? 0.5 * step : (double)step;
+    }
+    double four_i = 1.0;
+    for (int i = 1; i <= L; i++) {
+        four_i *= 4.0;
+        for (int k = i; k <= L; k++) R[k][i] = R[k][i - 1] + (R[k][i - 1] - R[k - 1][i - 1]) / (four_i - 1.0);
+    }
+    return R[L][L];
+}
+
+/* Equispaced velocity grid over [lo, hi] (Sec. 3.7): u_j = lo + j h, h = (hi - lo)/(N - 1),
+ * with trapezoidal weights (h, h/2 at both ends; rule 0) or Romberg weights (rule 1). */
+static void orc_grid(int N, int rule, double lo, double hi, double* u, double* wq)
 {
     double h = (hi - lo) / (N - 1);
     for (int j = 0; j < N; j++) {
         u[j] = lo + j * h;
-        wq[j] = (j == 0 || j == N - 1) ? 0.5 * h : h;
+        if (rule == 1) wq[j] = orc_romberg_weight(N, j) * h;
+        else wq[j] = (j == 0 || j == N - 1) ? 0.5 * h : h;
     }
 }
 
@@ -303,6 +354,7 @@ static int orc_walk(const orc_cfg* c, int nS, const double* S, int which,
     if (nS < 1 || nS > ORC_MAX_S) return -2;
     int Nx = c->nu[0], Ny = d == 2 ? c->nu[1] : 1;
     if (Nx < 2 || Nx > ORC_MAX_NU || (d == 2 && (Ny < 2 || Ny > ORC_MAX_NU))) return -2;
+    if (c->quadrature == 1 && ((Nx - 1) % 2 != 0 || (d == 2 && (Ny - 1) % 2 != 0))) return -2;
     orc_maxw g[ORC_MAX_S];
     for (int i = 0; i < nS; i++)
         if (orc_maxwellian_of(c, S + i * nv, &g[i])) return -1;
@@ -312,8 +364,8 @@ static int orc_walk(const orc_cfg* c, int nS, const double* S, int which,
     double* wx = malloc(sizeof(double) * Nx);
     double* uy = malloc(sizeof(double) * Ny);
     double* wy = malloc(sizeof(double) * Ny);
-    orc_grid(Nx, blo[0], bhi[0], ux, wx);
-    if (d == 2) orc_grid(Ny, blo[1], bhi[1], uy, wy);
+    orc_grid(Nx, c->quadrature, blo[0], bhi[0], ux, wx);
+    if (d == 2) orc_grid(Ny, c->quadrature, blo[1], bhi[1], uy, wy);
     else { uy[0] = 0.0; wy[0] = 1.0; }
     for (int v = 0; v < nv; v++) lo[v] = hi[v] = 0.0;
     double r = c->r_fac;

@@ -51,7 +51,9 @@ typedef struct {
                          paper's choice); 1: each component its own alpha_i (the independent
                          option stated after Eq. 39) */
     int flux;         /* common flux: 0 Rusanov (the flux of the analysis, Sec. 4), 1 HLLC
-                         (the flux of the experiments, Sec. 5) */
+                         (the flux of the experiments, Sec. 5), 2 HLL (the Sedov run, Sec. 6.6) */
+    int quadrature;   /* velocity quadrature: 0 trapezoidal (Sec. 3.7), 1 Romberg (named in
+                         Sec. 5; needs nu - 1 even on every axis) */
 } orc_cfg;
 
 typedef struct {
@@ -79,6 +81,8 @@ void orc_correction_deriv(int p, double x, double* dgl, double* dgr);
 double orc_pressure(const orc_cfg* c, const double* w);
 void orc_flux(const orc_cfg* c, const double* w, int dir, double* F);
 void orc_hllc(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F);
+void orc_hll(const orc_cfg* c, const double* wl, const double* wr, int dir, double* F);
+double orc_romberg_weight(int N, int j);
 void orc_rusanov(const orc_cfg* c, const double* wl, const double* wr, int dir,
                  double* F);
 

@@ -859,6 +859,12 @@ int run_entropy_vjp(const kbl_ctx* c, const double* w, double Jb, double* wb, cu
 
 bool adj_ok(const kbl_ctx* c) { return c && c->mesh_ready && c->cfg.dim == 2; }
 
+// The bounds adjoint differentiates the trapezoidal rule on a full kernel tile.
+bool adj_grid_ok(const kbl_ctx* c)
+{
+    return c->cfg.quadrature == 0 && kbl_tile_nx(c->cfg.nu[0]) == c->cfg.nu[0];
+}
+
 // Scratch of the adjoint (grown on demand).  Fixed part: the cotangent buffers of one
 // step.  Per step of a segment: its input state, the inputs of stages 1 and 2, and the
 // traces, bounds and residual of all three stages, kept by the forward pass of the
@@ -1105,6 +1111,7 @@ kbl_status kbl_bounds_vjp(kbl_ctx* c, const double* w, const double* wf, const d
                           double* wb, double* wfb, double* wfb_ext)
 {
     if (!adj_ok(c)) return afail(c, KBL_ESTATE, "no 2D mesh");
+    if (!adj_grid_ok(c)) return afail(c, KBL_EINVAL, "the bounds adjoint covers the trapezoidal rule on 8, 16, 32 or 64 nodes per axis");
     if (c->E > 0 && (!w || !wf || !bnd || !bndb || !wb || !wfb || !wfb_ext))
         return afail(c, KBL_EINVAL, "null array");
     int r = -1;
@@ -1209,6 +1216,7 @@ kbl_status kbl_adjoint_segment(kbl_ctx* c, const double* w0, const double* dts, 
                                double* wbar)
 {
     if (!adj_ok(c)) return afail(c, KBL_ESTATE, "no 2D mesh");
+    if (!adj_grid_ok(c)) return afail(c, KBL_EINVAL, "the bounds adjoint covers the trapezoidal rule on 8, 16, 32 or 64 nodes per axis");
     if (c->cfg.precision != KBL_FP64) return afail(c, KBL_EINVAL, "the adjoint runs in FP64");
     if (c->phys.flux != 0) return afail(c, KBL_EINVAL, "the residual adjoint covers the Rusanov flux");
     if (n < 0 || (n > 0 && !dts) || (c->E > 0 && (!w0 || !wbar))) return afail(c, KBL_EINVAL, "bad argument");

@@ -16,6 +16,30 @@
 
 namespace {
 
+// ---- velocity quadrature ---------------------------------------------------
+// Romberg weights (units of the grid spacing h) on nu equispaced nodes, the quadrature
+// Sec. 5 names beside the trapezoidal rule.  With nu - 1 = 2^L m (m odd) the rule
+// extrapolates the L + 1 nested trapezoidal sums of steps 2^L h, ..., 2h, h (Richardson,
+// T_k^j = T_k^(j-1) + (T_k^(j-1) - T_(k-1)^(j-1)) / (4^j - 1)).  Every sum is linear in the
+// node values, so the tableau is run on weight vectors.
+void romberg_weights(int nu, std::vector<double>& q)
+{
+    int L = 0;
+    for (int m = nu - 1; m > 0 && m % 2 == 0; m /= 2) L++;
+    std::vector<std::vector<double>> T(L + 1, std::vector<double>(nu, 0.0));
+    for (int k = 0; k <= L; k++) {   // T[k]: trapezoidal sum of step 2^(L-k) h
+        const int st = 1 << (L - k);
+        for (int j = 0; j < nu; j += st) T[k][j] = (j == 0 || j == nu - 1) ? 0.5 * st : (double)st;
+    }
+    double f = 1.0;
+    for (int lev = 1; lev <= L; lev++) {
+        f *= 4.0;
+        for (int k = L; k >= lev; k--)
+            for (int j = 0; j < nu; j++) T[k][j] += (T[k][j] - T[k - 1][j]) / (f - 1.0);
+    }
+    q = T[L];
+}
+
 // ---- FR operators --------------------------------------------------------
 void jacobi_eigen(int n, double* A /* n*n, symmetric, destroyed */, double* V /* n*n, columns */)
 {
@@ -218,6 +242,7 @@ kbl_status kbl_config_default(kbl_config* cfg, int dim, int p)
     cfg->precision = KBL_FP64;
     cfg->uncoupled = 0;
     cfg->flux = 0;
+    cfg->quadrature = 0;
     return KBL_OK;
 }
 
@@ -230,7 +255,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     if (cfg->p < 1 || cfg->p > KBL_PMAX) return KBL_EINVAL;
     if (cfg->dim == 2) {
         const int nx = cfg->nu[0];
-        if (cfg->nu[1] != nx || (nx != 8 && nx != 16 && nx != 32 && nx != 64)) return KBL_EINVAL;
+        if (cfg->nu[1] != nx || nx < 2 || nx > 64) return KBL_EINVAL;
     } else if (cfg->nu[0] < 2 || cfg->nu[0] > 4096) {
         return KBL_EINVAL;
     }
@@ -239,7 +264,9 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         return KBL_EINVAL;
     if (cfg->precision != KBL_FP64 && cfg->precision != KBL_FP32_MIXED) return KBL_EINVAL;
     if (cfg->uncoupled != 0 && cfg->uncoupled != 1) return KBL_EINVAL;
-    if (cfg->flux != 0 && cfg->flux != 1) return KBL_EINVAL;
+    if (cfg->flux < 0 || cfg->flux > 2) return KBL_EINVAL;
+    if (cfg->quadrature != 0 && cfg->quadrature != 1) return KBL_EINVAL;
+    if (cfg->quadrature == 1 && (cfg->nu[0] < 3 || (cfg->nu[0] - 1) % 2 != 0)) return KBL_EINVAL;
     kbl_ctx* c = new (std::nothrow) kbl_ctx();
     if (!c) return KBL_ENOMEM;
     c->cfg = *cfg;
@@ -255,6 +282,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     c->phys.nu[1] = cfg->dim == 2 ? cfg->nu[1] : 1;
     c->phys.uncoupled = cfg->uncoupled;
     c->phys.flux = cfg->flux;
+    c->phys.qw = nullptr;
     build_ops(cfg->p, c->ops);
     const int n = cfg->p + 1;
     c->nv = cfg->dim + 2;
@@ -266,6 +294,16 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         (e = dalloc(&c->d_flags, 1)) != cudaSuccess) {
         kbl_destroy(c);
         return KBL_ECUDA;
+    }
+    if (cfg->quadrature == 1) {
+        std::vector<double> q;
+        romberg_weights(cfg->nu[0], q);
+        if ((e = dalloc(&c->d_qw, q.size())) != cudaSuccess ||
+            (e = cudaMemcpy(c->d_qw, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            kbl_destroy(c);
+            return KBL_ECUDA;
+        }
+        c->phys.qw = c->d_qw;
     }
     const double scal[3] = {0.0, 0.0, INFINITY};
     if ((e = cudaMemcpy(c->d_scal, scal, sizeof(scal), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -284,6 +322,7 @@ kbl_status kbl_destroy(kbl_ctx* c)
     if (c->d_scal) cudaFree(c->d_scal);
     if (c->d_dtbits) cudaFree(c->d_dtbits);
     if (c->d_flags) cudaFree(c->d_flags);
+    if (c->d_qw) cudaFree(c->d_qw);
     delete c;
     return KBL_OK;
 }

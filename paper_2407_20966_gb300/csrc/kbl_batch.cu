@@ -519,6 +519,7 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
         return KBL_EINVAL;
     if (!(cfg->gamma > 1.0) || !(cfg->k > 0.0) || !(cfg->r_fac >= 0.0 && cfg->r_fac < 1.0) || !(cfg->eps >= 0.0))
         return KBL_EINVAL;
+    if (cfg->flux < 0 || cfg->flux > 2 || cfg->quadrature != 0) return KBL_EINVAL;
     if (P < 1 || !p || !n_elem || !nbr || !h || !n_bc) return KBL_EINVAL;
     kbl_batch* b = new (std::nothrow) kbl_batch();
     if (!b) return KBL_ENOMEM;
@@ -532,7 +533,8 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
     b->phys.p_floor = cfg->p_floor;
     b->phys.eps_rule = cfg->eps_rule;
     b->phys.uncoupled = cfg->uncoupled ? 1 : 0;
-    b->phys.flux = cfg->flux == 1 ? 1 : 0;
+    b->phys.flux = cfg->flux;
+    b->phys.qw = nullptr;
     b->phys.nu[0] = b->phys.nu[1] = NX_B;
     for (int q = 1; q <= PMAX_B; q++) kbl_build_fr_ops(q, b->ops.o[q]);
     b->P = P;

@@ -229,12 +229,13 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
         sbox[tid] = b;
     }
     __syncthreads();
+    const int nu = ph.nu[0];   // nodes per axis; tile nodes j >= nu sit on the box end with weight 0
     for (int j = tid; j < 2 * NX; j += NT) {
         const int d = j / NX, jj = j % NX;
         const double lo = sbox[2 * d], hi = sbox[2 * d + 1];
-        const double h = (hi - lo) / (NX - 1);
-        const double u = lo + jj * h;
-        const double wq = (jj == 0 || jj == NX - 1) ? 0.5 * h : h;
+        const double h = (hi - lo) / (nu - 1);
+        const double u = lo + min(jj, nu - 1) * h;
+        const double wq = kbl_qweight(ph, jj, nu) * h;
         if (d == 0) { sux[jj] = u; swx[jj] = wq; }
         else { suy[jj] = u; swy[jj] = wq; }
     }
@@ -453,7 +454,7 @@ k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, Me
             {
                 const int j = lane;
                 const float t = (float)j - 0.5f * (float)(NX - 1);
-                const float q = (j == 0 || j == NX - 1) ? 0.5f : 1.0f;
+                const float q = (float)kbl_qweight(ph, j, NX);
                 const float rxs = t * hx, rys = t * hy;
                 const float ux = cx + rxs, uy = cy + rys;
                 sm.coef[b][0][j] = q;
@@ -685,7 +686,7 @@ k_bounds1d(const double* __restrict__ w, const double* __restrict__ wf, MeshDev 
         for (int k = 0; k < 8; k++) acc[k] = 0.0;
         for (int j = tid; j < NU; j += NT1) {
             const double u = lo + j * h;
-            const double M = (j == 0 || j == NU - 1) ? 0.5 * h : h;
+            const double M = kbl_qweight(ph, j, NU) * h;
             double Tl = DBL_MAX, Th = 0.0, Il = DBL_MAX, Ih = 0.0;
 #pragma unroll
             for (int i = 0; i < NST; i++) {
@@ -721,7 +722,7 @@ k_bounds1d(const double* __restrict__ w, const double* __restrict__ wf, MeshDev 
         for (int j = tid; j < NU; j += NT1) {
             const double ud = lo + j * h;
             const float u = (float)ud, ur = (float)(ud - c);
-            const float q = (j == 0 || j == NU - 1) ? 0.5f : 1.0f;
+            const float q = (float)kbl_qweight(ph, j, NU);
             float Tl = FLT_MAX, Th = 0.0f, Il = FLT_MAX, Ih = 0.0f;
 #pragma unroll
             for (int i = 0; i < NST; i++) {
@@ -757,7 +758,7 @@ int run2d(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cuda
             k_bounds2d_f32<N, NX, 2><<<c->E, B2f32<NX, 2>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
         else if (NX >= 32 && c->bounds_tile == 2)
             k_bounds2d_f32<N, NX, 3><<<c->E, B2f32<NX, 3>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
-        else if (NX == 32 && c->bounds_tile == 3)
+        else if (NX == 32 && c->cfg.nu[0] == 32 && c->bounds_tile == 3)
             return run2d_ws<N>(c, w, wf, bnd, s);
         else
             k_bounds2d_f32<N, NX, 0><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
@@ -777,7 +778,7 @@ int run_bounds(const kbl_ctx* c, const double* w, const double* wf, double* bnd,
             k_bounds1d<N, false><<<c->E, NT1, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
         return 1;
     }
-    switch (c->cfg.nu[0]) {
+    switch (kbl_tile_nx(c->cfg.nu[0])) {
         case 8: return run2d<N, 8>(c, w, wf, bnd, s);
         case 16: return run2d<N, 16>(c, w, wf, bnd, s);
         case 32: return run2d<N, 32>(c, w, wf, bnd, s);

@@ -236,7 +236,8 @@ __device__ __forceinline__ void bounds2d_f32_element(
         loy = fminf(loy, sbox[q][2]); hiy = fmaxf(hiy, sbox[q][3]);
     }
     const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy);
-    const float hx = (hix - lox) / (float)(NX - 1), hy = (hiy - loy) / (float)(NX - 1);
+    const int nu = ph.nu[0];   // nodes per axis; tile nodes j >= nu sit on the box end with weight 0
+    const float hx = (hix - lox) / (float)(nu - 1), hy = (hiy - loy) / (float)(nu - 1);
 
     // 2. state velocities and grid relative to the box centre (for the Maxwellians,
     //    which keeps FP32 differences small), absolute grid for the moments
@@ -245,8 +246,8 @@ __device__ __forceinline__ void bounds2d_f32_element(
         sUy[i] -= cy;
     }
     for (int j = tid; j < NX; j += NT) {
-        const float t = (float)j - 0.5f * (float)(NX - 1);
-        const float q = (j == 0 || j == NX - 1) ? 0.5f : 1.0f;
+        const float t = (float)min(j, nu - 1) - 0.5f * (float)(nu - 1);
+        const float q = (float)kbl_qweight(ph, j, nu);
         const float rx = t * hx, ry = t * hy;
         const float ux = cx + rx, uy = cy + ry;
         srx[j] = rx;

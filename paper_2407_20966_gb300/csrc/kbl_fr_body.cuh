@@ -17,7 +17,8 @@ struct RhsSmem {
 // FR residual of elements e0 .. e0+min(EPB, nmax)-1 of one mesh, by a block of NT >= EPB*Ns threads
 // (one per solution point; the others only help with the face loop).
 //   1. states and physical fluxes at the solution points -> shared memory
-//   2. per face point: common flux (Rusanov, or HLLC with flux == 1) of (interior trace, exterior value) minus
+//   2. per face point: common flux (Rusanov; HLLC with flux == 1, HLL with flux == 2) of (interior trace,
+//      exterior value) minus
 //      the interpolated discontinuous flux -> jump J
 //   3. per solution point and axis: D F + g_L' J_minus + g_R' J_plus,
 //      R = -sum_axes (2 / h_axis) dF/dxi
@@ -77,6 +78,9 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
         if (flux == 1) {
             if (side == 0) kbl_hllc<DIM, T>(qe, qi, dir, gamma, Fc);
             else kbl_hllc<DIM, T>(qi, qe, dir, gamma, Fc);
+        } else if (flux == 2) {
+            if (side == 0) kbl_hll<DIM, T>(qe, qi, dir, gamma, Fc);
+            else kbl_hll<DIM, T>(qi, qe, dir, gamma, Fc);
         } else {
             if (side == 0) kbl_rusanov<DIM, T>(qe, qi, dir, gamma, Fc);
             else kbl_rusanov<DIM, T>(qi, qe, dir, gamma, Fc);

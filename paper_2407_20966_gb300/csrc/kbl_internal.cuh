@@ -29,8 +29,24 @@ struct Phys {
     int eps_rule;
     int nu[2];
     int uncoupled;
-    int flux;   // 0 Rusanov, 1 HLLC
+    int flux;   // 0 Rusanov, 1 HLLC, 2 HLL
+    // velocity quadrature: per-node weights in units of the grid spacing (nu[0] values,
+    // the same rule on every axis), or nullptr for the trapezoidal rule
+    const double* qw;
 };
+
+// Weight, in units of the grid spacing, of velocity node j of an axis of nu nodes: the
+// uploaded rule when there is one, else the trapezoidal rule of Sec. 3.7 (1/2 at both
+// ends).  Nodes j >= nu pad a kernel's tile and carry no weight.
+__device__ __forceinline__ double kbl_qweight(const Phys& ph, int j, int nu)
+{
+    if (j >= nu) return 0.0;
+    if (ph.qw) return ph.qw[j];
+    return (j == 0 || j == nu - 1) ? 0.5 : 1.0;
+}
+
+// Tile size (velocity nodes per axis) of the 2D bounds kernels that holds an axis of nu nodes.
+__host__ __device__ constexpr int kbl_tile_nx(int nu) { return nu <= 8 ? 8 : nu <= 16 ? 16 : nu <= 32 ? 32 : 64; }
 
 struct MeshDev {
     int E;
@@ -69,6 +85,7 @@ struct kbl_ctx {
     double* d_scal = nullptr;   // [0] dt, [1] t, [2] t_end
     unsigned long long* d_dtbits = nullptr;
     DevFlags* d_flags = nullptr;
+    double* d_qw = nullptr;     // velocity quadrature weights (Romberg), or nullptr
     std::string err;
     int64_t launches = 0;
     int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes
@@ -186,6 +203,34 @@ __device__ __forceinline__ void kbl_hllc(const T* ql, const T* qr, int dir, T ga
     qs[DIM + 1] = f * (q[DIM + 1] / q[0] + (Ss - U) * (Ss + P / (q[0] * (S - U))));
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] += S * (qs[v] - q[v]);
+}
+
+// HLL flux (Harten, Lax & van Leer 1983; the Riemann solver of the Sedov run, Sec. 6.6)
+// with the Davis estimates of kbl_hllc: F(ql) for 0 <= S_l, F(qr) for S_r <= 0, else
+// (S_r F(ql) - S_l F(qr) + S_l S_r (qr - ql)) / (S_r - S_l).
+template <int DIM, typename T>
+__device__ __forceinline__ void kbl_hll(const T* ql, const T* qr, int dir, T gamma, T* F)
+{
+    constexpr int NV = DIM + 2;
+    const T gm1 = gamma - T(1);
+    const T Pl = kbl_pressure<DIM, T>(ql, gm1), Pr = kbl_pressure<DIM, T>(qr, gm1);
+    const T Ul = ql[1 + dir] / ql[0], Ur = qr[1 + dir] / qr[0];
+    const T cl = sqrt(gamma * Pl / ql[0]), cr = sqrt(gamma * Pr / qr[0]);
+    const T Sl = fmin(Ul - cl, Ur - cr), Sr = fmax(Ul + cl, Ur + cr);
+    if (T(0) <= Sl) {
+        kbl_flux<DIM, T>(ql, dir, gm1, F);
+        return;
+    }
+    if (Sr <= T(0)) {
+        kbl_flux<DIM, T>(qr, dir, gm1, F);
+        return;
+    }
+    T Fr[NV];
+    kbl_flux<DIM, T>(ql, dir, gm1, F);
+    kbl_flux<DIM, T>(qr, dir, gm1, Fr);
+    const T inv = T(1) / (Sr - Sl);
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v] = (Sr * F[v] - Sl * Fr[v] + Sl * Sr * (qr[v] - ql[v])) * inv;
 }
 
 // Exterior value of component v at face point fp of element e.

@@ -58,13 +58,13 @@ bool config_ok(const kbl_config* cfg)
     if (!cfg || (cfg->dim != 1 && cfg->dim != 2) || cfg->p < 1 || cfg->p > KBL_PMAX) return false;
     if (cfg->dim == 2) {
         const int nx = cfg->nu[0];
-        if (cfg->nu[1] != nx || (nx != 8 && nx != 16 && nx != 32 && nx != 64)) return false;
+        if (cfg->nu[1] != nx || nx < 2 || nx > 64) return false;
     } else if (cfg->nu[0] < 2 || cfg->nu[0] > 4096) {
         return false;
     }
     return cfg->gamma > 1.0 && cfg->k > 0.0 && cfg->r_fac >= 0.0 && cfg->r_fac < 1.0 && cfg->eps >= 0.0 &&
            cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0 &&
-           (cfg->precision == KBL_FP64 || cfg->precision == KBL_FP32_MIXED);
+           (cfg->precision == KBL_FP64 || cfg->precision == KBL_FP32_MIXED) && cfg->quadrature == 0;
 }
 
 }  // namespace
@@ -98,6 +98,7 @@ extern "C" kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, cons
     c.phys.eps_rule = cfg->eps_rule;
     c.phys.uncoupled = cfg->uncoupled ? 1 : 0;
     c.phys.flux = 0;
+    c.phys.qw = nullptr;   // trapezoidal rule: a weight table would need an allocation
     c.phys.nu[0] = cfg->nu[0];
     c.phys.nu[1] = cfg->dim == 2 ? cfg->nu[1] : 1;
     kbl_build_fr_ops(cfg->p, c.ops);

@@ -130,7 +130,7 @@ def riemann_1d(n, left, right, x0, x1, xs, gamma=GAMMA):
 
 
 def problem_123(n=100, gamma=GAMMA):
-    """Double rarefaction ("123 problem", Sec. 6): [0, 1], (1, -2, 0.4) | (1, 2, 0.4) at x = 0.5."""
+    """Double rarefaction ("123 problem", Sec. 6.3): [0, 1], (1, -2, 0.4) | (1, 2, 0.4) at x = 0.5."""
     return riemann_1d(n, (1.0, -2.0, 0.4), (1.0, 2.0, 0.4), 0.0, 1.0, 0.5, gamma)
 
 
@@ -138,7 +138,7 @@ LEBLANC_GAMMA = 5.0 / 3.0
 
 
 def leblanc(n=100, gamma=LEBLANC_GAMMA):
-    """Leblanc shock tube (Sec. 6): [0, 9], (1, 0, (gamma-1) 1e-1) | (1e-3, 0, (gamma-1) 1e-10) at
+    """Leblanc shock tube (Sec. 6.5): [0, 9], (1, 0, (gamma-1) 1e-1) | (1e-3, 0, (gamma-1) 1e-10) at
     x = 3.  The paper does not restate gamma here; the problem's usual value 5/3 is taken."""
     return riemann_1d(n, (1.0, 0.0, (gamma - 1) * 1e-1), (1e-3, 0.0, (gamma - 1) * 1e-10), 0.0, 9.0, 3.0, gamma)
 

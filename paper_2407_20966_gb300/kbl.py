@@ -34,7 +34,8 @@ class KblConfig(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nu", C.c_int * 2), ("gamma", C.c_double),
                 ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
-                ("precision", C.c_int), ("uncoupled", C.c_int), ("flux", C.c_int)]
+                ("precision", C.c_int), ("uncoupled", C.c_int), ("flux", C.c_int),
+                ("quadrature", C.c_int)]
 
 
 class KblCounters(C.Structure):

@@ -51,7 +51,9 @@ def test_invalid_configs_rejected_before_any_device_call(lib):
     lib.kbl_config_default(C.byref(cfg), 2, 3)
     h = C.c_void_p()
     bad = []
-    for field, val in (("nu", (24, 24)), ("gamma", 1.0), ("r_fac", 1.0), ("k", 0.0), ("precision", 7)):
+    for field, val in (("nu", (65, 65)), ("nu", (17, 33)), ("gamma", 1.0), ("r_fac", 1.0), ("k", 0.0),
+                       ("precision", 7), ("flux", 3), ("quadrature", 2),
+                       ("quadrature", 1)):   # 31 intervals: no coarser grid for Romberg
         c2 = kbl.KblConfig()
         C.pointer(c2)[0] = cfg
         if field == "nu":

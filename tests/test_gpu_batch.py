@@ -124,19 +124,21 @@ def test_batch_rejects_bad_input():
         kbl.Batch([(2, bad, m.h, np.zeros((0, 4)))])             # neighbour out of range
 
 
-def test_batch_hllc_equals_single_mesh_path():
-    """With the HLLC flux (flux = 1) each problem's batched step equals the single-mesh step."""
+@pytest.mark.parametrize("flux", [1, 2])
+def test_batch_hllc_equals_single_mesh_path(flux):
+    """With the HLLC (flux = 1) or HLL (flux = 2) flux each problem's batched step equals the
+    single-mesh step."""
     import torch
     from paper_2407_20966_gb300 import kbl
     probs = inputs.four_quadrant_batch(9, 5, n_range=(2, 6))
-    b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs], flux=1)
+    b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs], flux=flux)
     w0 = inputs.batch_state(probs, b.nodes, b.state_offsets)
     wd = torch.from_numpy(w0).cuda()
     b.step(wd, 0.05)
     b.check()
     got = wd.cpu().numpy()
     for i, (p, m, ic) in enumerate(probs):
-        ctx = kbl.Context(dim=2, p=p, nu=(32, 32), precision=kbl.FP32_MIXED, flux=1)
+        ctx = kbl.Context(dim=2, p=p, nu=(32, 32), precision=kbl.FP32_MIXED, flux=flux)
         ctx.mesh_upload(m.nbr, m.h, m.bc)
         wi = torch.from_numpy(np.ascontiguousarray(b.state_view(w0, i))).cuda()
         ctx.set_time(0.0)

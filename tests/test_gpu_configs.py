@@ -97,16 +97,18 @@ def test_sedov_sampled_bounds(orc, precision, tol):
     assert bounds_error(got, ref).max() < tol
 
 
+@pytest.mark.parametrize("flux", [0, 2])
 @pytest.mark.parametrize("precision,cons_tol", [(1, 1e-7), (0, 1e-12)])
-def test_sedov_positivity_and_conservation_under_limiting(precision, cons_tol):
+def test_sedov_positivity_and_conservation_under_limiting(precision, cons_tol, flux):
     """Extreme pressure ratio (4.5e3 / 1e-6): 40 steps stay physical, the pressure stays above the
     floor at every solution point, and mass and energy are conserved (the blast has not reached
     the boundary).  The limiter keeps element means exactly; the FP32-mixed residual conserves to
-    FP32 rounding of its volume terms, the FP64 path to FP64 rounding."""
+    FP32 rounding of its volume terms, the FP64 path to FP64 rounding.  Rusanov, and HLL, the
+    flux of the paper's own Sedov run (Sec. 6.6)."""
     import torch
     from paper_2407_20966_gb300 import kbl
     mesh, ic = inputs.sedov(512)
-    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=precision)
+    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=precision, flux=flux)
     ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
     xi = ctx.operator(kbl.OP_NODES)
     wq = ctx.operator(kbl.OP_WEIGHTS)
@@ -126,7 +128,8 @@ def test_sedov_positivity_and_conservation_under_limiting(precision, cons_tol):
     assert w1[0].min() > 0 and P.min() >= 1e-12 * (1 - 1e-9)
     assert (w1[0] * W).sum() == pytest.approx(mass0, rel=cons_tol)
     assert (w1[3] * W).sum() == pytest.approx(energy0, rel=cons_tol)
-    print(f"Sedov 512^2 P2, 40 steps, precision {precision}: limited element-stages", c["limited_elements"],
+    print(f"Sedov 512^2 P2, 40 steps, precision {precision}, flux {flux}: limited element-stages",
+          c["limited_elements"],
           "pressure re-limits", c["pressure_relimits"], "min P", P.min(),
           "mass drift", (w1[0] * W).sum() / mass0 - 1, "energy drift", (w1[3] * W).sum() / energy0 - 1)
 

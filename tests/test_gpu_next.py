@@ -2,16 +2,17 @@
 
 * strict bounds at the paper's 1D resolution: Sod with k = 8 and 2048 velocity points, relaxed
   (r = 1e-3) against strict (r = 0) bounds (the comparison of Sec. 6.1);
-* the near-vacuum 123 problem and the Leblanc shock tube (Sec. 6), run to the paper's end
+* the near-vacuum 123 problem and the Leblanc shock tube (Sec. 6.3, 6.5), run to the paper's end
   times: the device run equals the checker's (123 problem: whole run; Leblanc: first steps),
-  stays physical, and converges toward the exact Riemann solution.
+  stays physical, and converges toward the exact Riemann solution;
+* the smooth pulse tables of Sec. 6.2 with HLLC, and the Sedov blast with HLL (Sec. 6.6).
 """
 import numpy as np
 import pytest
 
 from paper_2407_20966_gb300 import inputs
 from tests import riemann_exact
-from tests.gpu_helpers import to_dev
+from tests.gpu_helpers import state_error, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -87,7 +88,7 @@ def test_sod_relaxed_vs_strict_bounds_high_resolution(orc):
 
 
 def test_123_problem_whole_run_against_checker(orc):
-    """Two outrunning rarefactions leave a near-vacuum centre (Sec. 6): 100 P2 elements to t = 0.15.
+    """Two outrunning rarefactions leave a near-vacuum centre (Sec. 6.3): 100 P2 elements to t = 0.15.
     The device run equals the checker's run, density and pressure stay positive, and the density
     error against the exact solution is that of a converging first-order-at-the-kinks run."""
     from paper_2407_20966_gb300 import kbl
@@ -117,7 +118,7 @@ def test_123_problem_whole_run_against_checker(orc):
 
 
 def test_leblanc_shock_tube(orc):
-    """Pressure ratio 1e9, density ratio 1e3 (Sec. 6): 100 P3 elements to t = 6.  The first steps
+    """Pressure ratio 1e9, density ratio 1e3 (Sec. 6.5): 100 P3 elements to t = 6.  The first steps
     equal the checker's; the run stays physical throughout; the density error against the exact
     solution is bounded (the contact is smeared at this resolution, as the paper's figures show)."""
     from paper_2407_20966_gb300 import kbl
@@ -186,3 +187,23 @@ def test_pulse_convergence_rate_on_device():
     print(f"pulse P3 rates: relaxed {rates[1e-3]}, strict {rates[0.0]}")
     for r in rates:
         assert abs(np.mean(rates[r]) - 4.696) < 1.0
+
+
+def test_sedov_hll_matches_checker(orc):
+    """The Sedov blast with the HLL flux of the paper's run (Sec. 6.6), 32^2 P2: five steps on the
+    device equal the checker's five steps (the limiter and the pressure re-limit both act)."""
+    from paper_2407_20966_gb300 import kbl
+    mesh, ic = inputs.sedov(32)
+    ctx = kbl.Context(dim=2, p=2, nu=(16, 16), precision=kbl.FP64, flux=2)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    xi = ctx.operator(kbl.OP_NODES)
+    w0 = inputs.nodal_field(mesh, xi, ic)
+    w, n, st, c = _run_device(ctx, w0, 1e9, 0.05, max_steps=5)
+    assert st == kbl.OK and n == 5
+    assert c["limited_elements"] > 0
+    cfg = orc.Config(dim=2, p=2, nu=(16, 16), flux=2)
+    om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+    ref = w0.copy()
+    for _ in range(5):
+        ref, _ = orc.ssprk3_step(cfg, om, ref, orc.dt(cfg, om, ref, 0.05))
+    assert state_error(w, ref).max() < 1e-10

@@ -305,12 +305,13 @@ def test_stage(orc, s):
     assert state_error(out.cpu().numpy(), ref).max() < TOL_FP64
 
 
+@pytest.mark.parametrize("flux", [1, 2])
 @pytest.mark.parametrize("dim,p,n,precision", [(1, 3, 37, 0), (2, 3, (9, 7), 0), (2, 2, (4, 13), 0),
                                                (2, 3, (9, 7), 1), (1, 4, 21, 1)])
-def test_rhs_hllc(orc, dim, p, n, precision):
-    """The residual with the HLLC flux of Sec. 5 (flux = 1) on both sides, on discontinuous data
-    (every branch of the flux is taken)."""
-    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16), precision=precision, flux=1)
+def test_rhs_hllc(orc, dim, p, n, precision, flux):
+    """The residual with the HLLC flux of Sec. 5 (flux = 1) or the HLL flux of Sec. 6.6 (flux = 2)
+    on both sides, on discontinuous data (every branch of the flux is taken)."""
+    ctx, ocfg = both(orc, dim, p, (64,) if dim == 1 else (16, 16), precision=precision, flux=flux)
     for seed in range(180, 200):   # the first discontinuous field whose face traces are physical
         mesh, w = mesh_and_field(orc, dim, p, n, seed=seed, kind="disc")
         om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
@@ -328,9 +329,10 @@ def test_rhs_hllc(orc, dim, p, n, precision):
     assert np.abs(orc.rhs(ocfg, om, w, wf) - R_ref).max() > 1e-3 * np.abs(R_ref).max()
 
 
+@pytest.mark.parametrize("flux", [1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_full_step_hllc(orc, precision):
-    ctx, ocfg = both(orc, 2, 3, (16, 16), precision=precision, flux=1)
+def test_full_step_hllc(orc, precision, flux):
+    ctx, ocfg = both(orc, 2, 3, (16, 16), precision=precision, flux=flux)
     mesh, w = mesh_and_field(orc, 2, 3, (7, 6), seed=190, kind="smooth")
     om = upload(ctx, orc, mesh)
     dt = orc.dt(ocfg, om, w, 0.05)

@@ -341,6 +341,60 @@ def test_hllc_flux_properties(orc):
         np.testing.assert_allclose(orc.hllc(cfg, sup_l, sup_r, 0), orc.flux(cfg, sup_l, 0), rtol=1e-14)
 
 
+def test_hll_flux_properties(orc):
+    """HLL (the flux of the Sedov run, Sec. 6.6): consistent; supersonic states give the upwind
+    physical flux; with both states at rest and one sound speed the Davis estimates are -c, +c and
+    HLL is the Rusanov flux with lambda = c; the single intermediate state obeys the
+    Rankine-Hugoniot condition across both outer waves; a contact at rest is smeared (unlike
+    HLLC); mirroring the states mirrors the flux."""
+    for d in (1, 2):
+        cfg = orc.Config(dim=d, p=2, flux=2)
+        rng = np.random.default_rng(10 + d)
+        for _ in range(5):
+            q = inputs.random_states(rng, 1, d)[0]
+            for ax in range(d):
+                np.testing.assert_allclose(orc.hll(cfg, q, q, ax), orc.flux(cfg, q, ax), rtol=1e-14, atol=1e-14)
+        sup_l = inputs.conservative(1.0, [3.0] + [0.1] * (d - 1), 0.5)
+        sup_r = inputs.conservative(0.5, [2.5] + [0.0] * (d - 1), 0.3)
+        np.testing.assert_allclose(orc.hll(cfg, sup_l, sup_r, 0), orc.flux(cfg, sup_l, 0), rtol=1e-14)
+        np.testing.assert_allclose(orc.hll(cfg, _mirror(sup_r, 0), _mirror(sup_l, 0), 0),
+                                   orc.flux(cfg, _mirror(sup_l, 0), 0), rtol=1e-14)
+        rest = [0.0] * d
+        # same P / rho on both sides: the same sound speed
+        ql, qr = inputs.conservative(1.0, rest, 0.7), inputs.conservative(0.4, rest, 0.28)
+        np.testing.assert_allclose(orc.hll(cfg, ql, qr, 0), orc.rusanov(cfg, ql, qr, 0), rtol=1e-14, atol=1e-15)
+        # a contact at rest: HLL diffuses it (nonzero mass flux), HLLC does not
+        ql, qr = inputs.conservative(1.0, rest, 0.7), inputs.conservative(0.2, rest, 0.7)
+        assert abs(orc.hll(cfg, ql, qr, 0)[0]) > 1e-2
+        for _ in range(5):
+            ql, qr = inputs.random_states(rng, 2, d)
+            for ax in range(d):
+                F = orc.hll(cfg, ql, qr, ax)
+                # Davis estimates, written from the primitive states
+                gm = cfg.gamma
+                def prim(q):
+                    u = q[1 + ax] / q[0]
+                    P = (gm - 1) * (q[-1] - 0.5 * sum(q[1 + k] ** 2 for k in range(d)) / q[0])
+                    return u, np.sqrt(gm * P / q[0])
+                (ul, cl), (ur, cr) = prim(ql), prim(qr)
+                Sl, Sr = min(ul - cl, ur - cr), max(ul + cl, ur + cr)
+                Fl, Fr = orc.flux(cfg, ql, ax), orc.flux(cfg, qr, ax)
+                if Sl < 0 < Sr:
+                    q_star = (Sr * qr - Sl * ql - (Fr - Fl)) / (Sr - Sl)
+                    np.testing.assert_allclose(F, Fl + Sl * (q_star - ql), rtol=1e-12, atol=1e-12)
+                    np.testing.assert_allclose(F, Fr + Sr * (q_star - qr), rtol=1e-12, atol=1e-12)
+                # mirror symmetry along the axis: F(M qr, M ql) = -M F(ql, qr)
+                Fm = orc.hll(cfg, _mirror(qr, ax), _mirror(ql, ax), ax)
+                np.testing.assert_allclose(Fm, -_mirror(F, ax), rtol=1e-12, atol=1e-12)
+
+
+def _mirror(q, ax):
+    """Reflect a state (or a flux) along axis ax: the momentum component of that axis changes sign."""
+    m = np.array(q, dtype=np.float64).copy()
+    m[1 + ax] = -m[1 + ax]
+    return m
+
+
 def test_density_pulse_limiter_does_not_clip(orc):
     """Sec. 6.2: at a smooth extremum the kinetic bounds leave the high-order solution alone
     (the paper's strict and relaxed errors coincide with the unlimited scheme's behaviour)."""
