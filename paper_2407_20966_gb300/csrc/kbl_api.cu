@@ -6,6 +6,7 @@
 // barycentric Lagrange formulas, and the g_DG correction derivatives from the
 // nodal-DG lifting identity g_L'(x_i) = -l_i(-1) / w_i, g_R'(x_i) = l_i(1) / w_i
 // that holds for Gauss-Legendre solution points.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -283,6 +284,8 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     c->phys.uncoupled = cfg->uncoupled;
     c->phys.flux = cfg->flux;
     c->phys.qw = nullptr;
+    c->phys.qwf = nullptr;
+    kbl_phys_derive(c->phys);
     build_ops(cfg->p, c->ops);
     const int n = cfg->p + 1;
     c->nv = cfg->dim + 2;
@@ -296,14 +299,21 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         return KBL_ECUDA;
     }
     if (cfg->quadrature == 1) {
+        // the table in FP64, then its FP32 copy, in one allocation
+        const int nq = cfg->nu[0];
         std::vector<double> q;
-        romberg_weights(cfg->nu[0], q);
-        if ((e = dalloc(&c->d_qw, q.size())) != cudaSuccess ||
-            (e = cudaMemcpy(c->d_qw, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        romberg_weights(nq, q);
+        std::vector<double> buf(nq + (nq + 1) / 2, 0.0);
+        std::copy(q.begin(), q.end(), buf.begin());
+        float* qf = reinterpret_cast<float*>(buf.data() + nq);
+        for (int j = 0; j < nq; j++) qf[j] = (float)q[j];
+        if ((e = dalloc(&c->d_qw, buf.size())) != cudaSuccess ||
+            (e = cudaMemcpy(c->d_qw, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
             kbl_destroy(c);
             return KBL_ECUDA;
         }
         c->phys.qw = c->d_qw;
+        c->phys.qwf = reinterpret_cast<const float*>(c->d_qw + nq);
     }
     const double scal[3] = {0.0, 0.0, INFINITY};
     if ((e = cudaMemcpy(c->d_scal, scal, sizeof(scal), cudaMemcpyHostToDevice)) != cudaSuccess ||

@@ -535,7 +535,9 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
     b->phys.uncoupled = cfg->uncoupled ? 1 : 0;
     b->phys.flux = cfg->flux;
     b->phys.qw = nullptr;
+    b->phys.qwf = nullptr;
     b->phys.nu[0] = b->phys.nu[1] = NX_B;
+    kbl_phys_derive(b->phys);
     for (int q = 1; q <= PMAX_B; q++) kbl_build_fr_ops(q, b->ops.o[q]);
     b->P = P;
     long long eoff = 0, bcoff = 0, woff = 0, wfoff = 0, bndoff = 0;

@@ -311,13 +311,13 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
 // ---------------------------------------------------------------------------
 // 2D, FP32 envelopes and sums (body in kbl_bounds_body.cuh): one block per element
 // ---------------------------------------------------------------------------
-template <int N, int NX, int TYSEL>
+template <int N, int NX, int TYSEL, bool PAD = false>
 __global__ void __launch_bounds__(B2f32<NX, TYSEL>::NT, B2f32<NX, TYSEL>::MINB)
 k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
                double* __restrict__ bnd, DevFlags* flags)
 {
     __shared__ Bounds2dF32Smem<N, NX, TYSEL> sm;
-    bounds2d_f32_element<N, NX, TYSEL>(sm, w, wf, m, blockIdx.x, ph, bnd, flags);
+    bounds2d_f32_element<N, NX, TYSEL, PAD>(sm, w, wf, m, blockIdx.x, ph, bnd, flags);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,8 +401,7 @@ k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, Me
 
     if (wid == 0) {
         // ------------------------------ producer ------------------------------
-        const float gm1 = (float)(ph.gamma - 1.0), kk = (float)ph.k;
-        const float half_delta = 0.5f * (float)(2.0 / (ph.gamma - 1.0) - 2.0);
+        const float gm1 = ph.gm1f, kk = ph.kf, half_delta = ph.half_delta2f;
         for (int it = 0; it < n_iter; it++) {
             const int e = (int)blockIdx.x + it * G, b = it & 1;
             for (int idx = lane; idx < NST * NV; idx += 32) {
@@ -419,10 +418,10 @@ k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, Me
             for (int i = lane; i < NSTP; i += 32) {
                 const double* q = sm.sS[i < NST ? i : NST - 1];
                 const double X = fma(q[3], q[0], -0.5 * fma(q[2], q[2], q[1] * q[1]));
-                if (!(q[0] > 0.0) || !(X > 0.0)) bad = 1;
-                const float r = (float)q[0], inv = 1.0f / r;
-                const float ux = (float)q[1] * inv, uy = (float)q[2] * inv;
-                const float th = gm1 * ((float)X * inv) * inv;
+                if (!kbl_positive(q[0]) || !kbl_positive(X)) bad = 1;
+                const float r = f32_trunc(q[0]), inv = 1.0f / r;
+                const float ux = f32_trunc(q[1]) * inv, uy = f32_trunc(q[2]) * inv;
+                const float th = gm1 * (f32_trunc(X) * inv) * inv;
                 const float sq = sqrtf(th);
                 sm.sUx[i] = ux;
                 sm.sUy[i] = uy;
@@ -454,7 +453,7 @@ k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, Me
             {
                 const int j = lane;
                 const float t = (float)j - 0.5f * (float)(NX - 1);
-                const float q = (float)kbl_qweight(ph, j, NX);
+                const float q = kbl_qweight_f(ph, j, NX);
                 const float rxs = t * hx, rys = t * hy;
                 const float ux = cx + rxs, uy = cy + rys;
                 sm.coef[b][0][j] = q;
@@ -591,8 +590,8 @@ k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, Me
                 lo = lo + sm.sred[q][ctid][1] + e2;
             }
             const bool upper_env = (ctid == 1) || (ctid == 2) || (ctid == 5) || (ctid == 6) || (ctid == 9) || (ctid == 11);
-            const double rel = upper_env ? 1.0 + ph.r_fac : 1.0 - ph.r_fac;
-            sm.sfin[ctid] = rel * (((double)hx * (double)hy) * ((double)hi + (double)lo));
+            const double rel = upper_env ? ph.rel_hi : ph.rel_lo;
+            sm.sfin[ctid] = rel * ((f64_widen(hx) * f64_widen(hy)) * (f64_widen(hi) + f64_widen(lo)));
         }
         ws::consumers_sync();
         if (bad) {
@@ -609,7 +608,7 @@ k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, Me
                 const int b0 = 2 + 4 * (v - 1);
                 val = up ? sm.sfin[b0 + 1] + sm.sfin[b0 + 3] : sm.sfin[b0 + 0] + sm.sfin[b0 + 2];
             }
-            if (v == 0 && !up && val < ph.rho_floor) val = ph.rho_floor;
+            if (v == 0 && !up && __double_as_longlong(val) < __double_as_longlong(ph.rho_floor)) val = ph.rho_floor;
             bnd[((size_t)up * NV + v) * m.E + e] = val;
         }
     }
@@ -754,11 +753,14 @@ template <int N, int NX>
 int run2d(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cudaStream_t s)
 {
     if (c->cfg.precision == KBL_FP32_MIXED) {
-        if (NX >= 32 && c->bounds_tile == 1)
+        if (c->cfg.nu[0] != NX || c->phys.qwf)   // padded tile or weight table: the 4x4 (or narrower) tile
+            k_bounds2d_f32<N, NX, 0, true><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd,
+                                                                            c->d_flags);
+        else if (NX >= 32 && c->bounds_tile == 1)
             k_bounds2d_f32<N, NX, 2><<<c->E, B2f32<NX, 2>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
         else if (NX >= 32 && c->bounds_tile == 2)
             k_bounds2d_f32<N, NX, 3><<<c->E, B2f32<NX, 3>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
-        else if (NX == 32 && c->cfg.nu[0] == 32 && c->bounds_tile == 3)
+        else if (NX == 32 && c->bounds_tile == 3)
             return run2d_ws<N>(c, w, wf, bnd, s);
         else
             k_bounds2d_f32<N, NX, 0><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);

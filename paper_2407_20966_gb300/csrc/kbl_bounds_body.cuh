@@ -164,8 +164,10 @@ struct Bounds2dF32Smem {
 };
 
 // Bounds of element e of one mesh (one block of SM::NT threads).  The block may
-// call it for several elements in a row: it starts with a barrier.
-template <int N, int NX, int TYSEL>
+// call it for several elements in a row: it starts with a barrier.  PAD: the grid has
+// ph.nu[0] <= NX nodes per axis or a weight table (else exactly NX nodes, trapezoidal
+// rule, with the node count and the weights folded into the code).
+template <int N, int NX, int TYSEL, bool PAD = false>
 __device__ __forceinline__ void bounds2d_f32_element(
     Bounds2dF32Smem<N, NX, TYSEL>& sm, const double* __restrict__ w, const double* __restrict__ wf,
     const MeshDev& m, int e, const Phys& ph, double* __restrict__ bnd, DevFlags* flags)
@@ -187,17 +189,18 @@ __device__ __forceinline__ void bounds2d_f32_element(
     __syncthreads();
 
     // 1. primitive state of each stencil node, box candidates
-    const float gm1 = (float)(ph.gamma - 1.0), kk = (float)ph.k;
-    const float half_delta = 0.5f * (float)(2.0 / (ph.gamma - 1.0) - 2.0);
+    const float gm1 = ph.gm1f, kk = ph.kf, half_delta = ph.half_delta2f;
     float blx = FLT_MAX, bly = FLT_MAX, bhx = -FLT_MAX, bhy = -FLT_MAX;
     int bad = 0;
     for (int i = tid; i < NSTP; i += NT) {
         const double* q = sS[i < NST ? i : NST - 1];
+        // rho e rho = rho E - |m|^2 / 2 and the positivity tests in FP64; the FP32 copies by
+        // truncation on the integer pipe
         const double X = fma(q[3], q[0], -0.5 * fma(q[2], q[2], q[1] * q[1]));
-        if (!(q[0] > 0.0) || !(X > 0.0)) bad = 1;
-        const float r = (float)q[0], inv = 1.0f / r;
-        const float ux = (float)q[1] * inv, uy = (float)q[2] * inv;
-        const float th = gm1 * ((float)X * inv) * inv;
+        if (!kbl_positive(q[0]) || !kbl_positive(X)) bad = 1;
+        const float r = f32_trunc(q[0]), inv = 1.0f / r;
+        const float ux = f32_trunc(q[1]) * inv, uy = f32_trunc(q[2]) * inv;
+        const float th = gm1 * (f32_trunc(X) * inv) * inv;
         const float sq = sqrtf(th);
         sUx[i] = ux;
         sUy[i] = uy;
@@ -236,7 +239,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
         loy = fminf(loy, sbox[q][2]); hiy = fmaxf(hiy, sbox[q][3]);
     }
     const float cx = 0.5f * (lox + hix), cy = 0.5f * (loy + hiy);
-    const int nu = ph.nu[0];   // nodes per axis; tile nodes j >= nu sit on the box end with weight 0
+    const int nu = PAD ? ph.nu[0] : NX;   // nodes per axis; tile nodes j >= nu sit on the box end, weight 0
     const float hx = (hix - lox) / (float)(nu - 1), hy = (hiy - loy) / (float)(nu - 1);
 
     // 2. state velocities and grid relative to the box centre (for the Maxwellians,
@@ -246,8 +249,8 @@ __device__ __forceinline__ void bounds2d_f32_element(
         sUy[i] -= cy;
     }
     for (int j = tid; j < NX; j += NT) {
-        const float t = (float)min(j, nu - 1) - 0.5f * (float)(nu - 1);
-        const float q = (float)kbl_qweight(ph, j, nu);
+        const float t = (float)(PAD ? min(j, nu - 1) : j) - 0.5f * (float)(nu - 1);
+        const float q = PAD ? kbl_qweight_f(ph, j, nu) : ((j == 0 || j == NX - 1) ? 0.5f : 1.0f);
         const float rx = t * hx, ry = t * hy;
         const float ux = cx + rx, uy = cy + ry;
         srx[j] = rx;
@@ -381,8 +384,8 @@ __device__ __forceinline__ void bounds2d_f32_element(
         }
         // lower-bound terms take (1 - r), upper-bound terms (1 + r)
         const bool upper_env = (tid == 1) || (tid == 2) || (tid == 5) || (tid == 6) || (tid == 9) || (tid == 11);
-        const double rel = upper_env ? 1.0 + ph.r_fac : 1.0 - ph.r_fac;
-        sfin[tid] = rel * (((double)hx * (double)hy) * ((double)hi + (double)lo));
+        const double rel = upper_env ? ph.rel_hi : ph.rel_lo;
+        sfin[tid] = rel * ((f64_widen(hx) * f64_widen(hy)) * (f64_widen(hi) + f64_widen(lo)));
     }
     __syncthreads();
     if (tid < 2 * NV) {
@@ -394,7 +397,8 @@ __device__ __forceinline__ void bounds2d_f32_element(
             const int b0 = 2 + 4 * (v - 1);
             val = up ? sfin[b0 + 1] + sfin[b0 + 3] : sfin[b0 + 0] + sfin[b0 + 2];
         }
-        if (v == 0 && !up && val < ph.rho_floor) val = ph.rho_floor;
+        // val >= 0 (a sum of non-negative terms) or NaN: the order of the bit patterns decides
+        if (v == 0 && !up && __double_as_longlong(val) < __double_as_longlong(ph.rho_floor)) val = ph.rho_floor;
         bnd[((size_t)up * NV + v) * m.E + e] = val;
     }
 }

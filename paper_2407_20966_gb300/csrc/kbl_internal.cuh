@@ -31,9 +31,62 @@ struct Phys {
     int uncoupled;
     int flux;   // 0 Rusanov, 1 HLLC, 2 HLL
     // velocity quadrature: per-node weights in units of the grid spacing (nu[0] values,
-    // the same rule on every axis), or nullptr for the trapezoidal rule
+    // the same rule on every axis; qwf its FP32 copy), or nullptr for the trapezoidal rule
     const double* qw;
+    const float* qwf;
+    // derived on the host (kbl_phys_derive), so that FP32 kernels spend no FP64 division or
+    // conversion on them: gamma - 1, k, delta / 2 = 1/(gamma - 1) - d/2 for d = 2, 1 -+ r
+    float gm1f, kf, half_delta2f;
+    double rel_lo, rel_hi;
 };
+
+inline void kbl_phys_derive(Phys& p)
+{
+    p.gm1f = (float)(p.gamma - 1.0);
+    p.kf = (float)p.k;
+    p.half_delta2f = 0.5f * (float)(2.0 / (p.gamma - 1.0) - 2.0);
+    p.rel_lo = 1.0 - p.r_fac;
+    p.rel_hi = 1.0 + p.r_fac;
+}
+
+// FP32 approximation of a double by truncating its significand, with integer operations only
+// (a conversion instruction would cost an FP64-pipe slot): |result - x| <= 2^-23 |x| for
+// 2^-126 <= |x| < 2^128, 0 below that range (|error| < 2^-126), infinity above it.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e32 = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e32 <= 0) return 0.0f;
+    if (e32 >= 255) return __uint_as_float((hi & 0x80000000u) | 0x7f800000u);
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e32 << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// x > 0.0 decided on the bit pattern with integer operations (true for +inf, false for
+// zeros, negatives and NaN), which keeps the test off the FP64 pipe.
+__device__ __forceinline__ bool kbl_positive(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000ll;
+}
+
+// Exact FP64 value of a float, with integer operations for the finite ones of magnitude 0 or
+// at least 2^-126 (subnormal floats give 0; infinities and NaN take the conversion).
+__device__ __forceinline__ double f64_widen(float x)
+{
+    const unsigned b = __float_as_uint(x), ex = (b >> 23) & 0xffu;
+    if (ex == 0u) return 0.0;
+    if (ex == 255u) return (double)x;
+    const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// FP32 weight of velocity node j (see kbl_qweight), for the FP32 kernels.
+__device__ __forceinline__ float kbl_qweight_f(const Phys& ph, int j, int nu)
+{
+    if (j >= nu) return 0.0f;
+    if (ph.qwf) return ph.qwf[j];
+    return (j == 0 || j == nu - 1) ? 0.5f : 1.0f;
+}
 
 // Weight, in units of the grid spacing, of velocity node j of an axis of nu nodes: the
 // uploaded rule when there is one, else the trapezoidal rule of Sec. 3.7 (1/2 at both

@@ -20,18 +20,6 @@ __device__ __forceinline__ double dunkey(long long k)
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
 }
 
-// FP32 approximation of a double by truncating its significand, with integer operations only
-// (a conversion instruction would cost an FP64-pipe slot): |result - x| <= 2^-23 |x| for
-// 2^-126 <= |x| < 2^128, 0 below that range (|error| < 2^-126), infinity above it.
-__device__ __forceinline__ float f32_trunc(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int e32 = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-    if (e32 <= 0) return 0.0f;
-    if (e32 >= 255) return __uint_as_float((hi & 0x80000000u) | 0x7f800000u);
-    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e32 << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
-}
-
 template <int DIM, int N, int EPB>
 struct LimSmem {
     static constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;

@@ -99,8 +99,10 @@ extern "C" kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, cons
     c.phys.uncoupled = cfg->uncoupled ? 1 : 0;
     c.phys.flux = 0;
     c.phys.qw = nullptr;   // trapezoidal rule: a weight table would need an allocation
+    c.phys.qwf = nullptr;
     c.phys.nu[0] = cfg->nu[0];
     c.phys.nu[1] = cfg->dim == 2 ? cfg->nu[1] : 1;
+    kbl_phys_derive(c.phys);
     kbl_build_fr_ops(cfg->p, c.ops);
     c.stream = (cudaStream_t)cuda_stream;
     c.nv = nv;

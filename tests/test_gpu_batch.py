@@ -94,7 +94,10 @@ def test_batch_matches_fp64_checker(orc):
         assert np.all(err <= np.maximum(TOL_FP32, 10 * sens)), (i, err.max(), sens[np.argmax(err)])
 
 
-def test_batch_autotune_keeps_results():
+def test_batch_autotune_keeps_results(orc):
+    """The autotuner changes the launch shape only: the state after a step differs by the FP32
+    summation order of the bounds, which the limiter amplifies where it cuts deep (Eq. 37), so
+    the criterion per element is that of test_batch_matches_fp64_checker."""
     import torch
     b, probs, w0 = _batch(seed=7, n_problems=9, n_range=(4, 12))
     wd = torch.from_numpy(w0).cuda()
@@ -108,7 +111,16 @@ def test_batch_autotune_keeps_results():
     b.step(wd2, 0.2)
     b.check()
     # a different thread tile only changes the FP32 summation order of the bounds
-    assert state_error(wd2.cpu().numpy().reshape(-1)[None, None, :], first.reshape(-1)[None, None, :]).max() < 1e-5
+    got = wd2.cpu().numpy()
+    dts = b.dt()
+    for i, (p, m, ic) in enumerate(probs):
+        cfg = orc.Config(dim=2, p=p, nu=(32, 32))
+        om = orc.Mesh(m.nbr, m.h, m.bc)
+        wi = np.ascontiguousarray(b.state_view(w0, i))
+        ref = _oracle_step(orc, cfg, om, wi, dts[i])
+        sens = state_error(_oracle_step(orc, cfg, om, wi, dts[i], pert=1e-6, seed=i), ref).max(axis=(0, 2))
+        err = state_error(b.state_view(got, i), b.state_view(first, i)).max(axis=(0, 2))
+        assert np.all(err <= np.maximum(TOL_FP32, 10 * sens)), (i, err.max(), sens[np.argmax(err)])
     launches = b.launch_count()
     assert launches > 0
 
