@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2)")
+    ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2, 2: 2x4, 3: warp-specialized)")
     return ap.parse_args()
 
 

@@ -40,9 +40,17 @@ __device__ __forceinline__ float mn2(float a, float b)
     asm volatile("min.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
     return r;
 }
+__device__ __forceinline__ float mx2(float a, float b)
+{
+    float r;
+    asm volatile("max.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-// KIND: 0 FMUL, 1 FMUL2, 2 FMNMX, 3 FMNMX3, 4 envelope pattern (2 FMUL2 + 4 FMNMX3)
+// KIND: 0 FMUL, 1 FMUL2, 2 FMNMX, 3 FMNMX3, 4 envelope pattern (2 FMUL2 + 4 FMNMX3),
+// 5 the same work with scalar products (4 FMUL + 4 FMNMX3), 6 with two-input min/max
+// (2 FMUL2 + 8 FMNMX), 7 half packed, half scalar products (1 FMUL2 + 2 FMUL + 4 FMNMX3)
 template <int KIND>
 __global__ void __launch_bounds__(THREADS) k_rate(float* out, long long* stamps, float seed)
 {
@@ -73,6 +81,30 @@ __global__ void __launch_bounds__(THREADS) k_rate(float* out, long long* stamps,
             } else if (KIND == 3) {
                 a[i] = mn3(a[i], b[i], c[i]);
                 d[i] = mx3(d[i], b[i], c[i]);
+            } else if (KIND == 5) {
+                const float gx = p[i].x * 1.0000001f, gy = p[i].y * 0.9999999f;
+                const float hx = b[i] * 1.0000001f, hy = c[i] * 0.9999999f;
+                a[i] = mn3(a[i], gx, gy);
+                d[i] = mx3(d[i], gx, gy);
+                b[i] = mn3(b[i], hx, hy);
+                c[i] = mx3(c[i], hx, hy);
+                p[i] = make_float2(gy, gx);
+            } else if (KIND == 6) {
+                const float2 g = mul2(p[i], k);
+                const float2 h = mul2(make_float2(b[i], c[i]), k);
+                a[i] = mn2(mn2(a[i], g.x), g.y);
+                d[i] = mx2(mx2(d[i], g.x), g.y);
+                b[i] = mn2(mn2(b[i], h.x), h.y);
+                c[i] = mx2(mx2(c[i], h.x), h.y);
+                p[i] = make_float2(g.y, g.x);
+            } else if (KIND == 7) {
+                const float2 g = mul2(p[i], k);
+                const float hx = b[i] * 1.0000001f, hy = c[i] * 0.9999999f;
+                a[i] = mn3(a[i], g.x, g.y);
+                d[i] = mx3(d[i], g.x, g.y);
+                b[i] = mn3(b[i], hx, hy);
+                c[i] = mx3(c[i], hx, hy);
+                p[i] = make_float2(g.y, g.x);
             } else {
                 const float2 g = mul2(p[i], k);
                 const float2 h = mul2(make_float2(b[i], c[i]), k);
@@ -99,9 +131,12 @@ __global__ void __launch_bounds__(THREADS) k_rate(float* out, long long* stamps,
 }
 
 // lane-operations per thread per iteration of each kind
-constexpr double OPS[5] = {2.0 * CHAINS, 2.0 * CHAINS, 2.0 * CHAINS, 4.0 * CHAINS, 12.0 * CHAINS};
-const char* NAMES[5] = {"FMUL (1 product)", "FMUL2 (2 products)", "FMNMX (1 comparison)",
-                        "FMNMX3 (2 comparisons)", "envelope pattern (4 products + 8 comparisons)"};
+constexpr double OPS[8] = {2.0 * CHAINS, 2.0 * CHAINS, 2.0 * CHAINS, 4.0 * CHAINS,
+                          12.0 * CHAINS, 12.0 * CHAINS, 12.0 * CHAINS, 12.0 * CHAINS};
+const char* NAMES[8] = {"FMUL (1 product)", "FMUL2 (2 products)", "FMNMX (1 comparison)",
+                        "FMNMX3 (2 comparisons)", "envelope pattern (4 products + 8 comparisons)",
+                        "  same, scalar FMUL products", "  same, two-input FMNMX",
+                        "  same, half FMUL2 half FMUL"};
 
 template <int KIND>
 double rate(float* out, long long* cyc, int sms)
@@ -167,6 +202,9 @@ int main()
     rate<2>(out, cyc, sms);
     const double r3 = rate<3>(out, cyc, sms);
     const double r4 = rate<4>(out, cyc, sms);
+    rate<5>(out, cyc, sms);
+    rate<6>(out, cyc, sms);
+    rate<7>(out, cyc, sms);
     // separate budgets: the envelope pattern would run at the slower of its two parts alone;
     // one shared budget: its time would be the sum of both
     const double t_sep = std::max(4.0 / r1, 8.0 / r3), t_sum = 4.0 / r1 + 8.0 / r3;
