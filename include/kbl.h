@@ -103,7 +103,8 @@ typedef struct kbl_ctx kbl_ctx;
 
 typedef struct {
     int32_t nonphysical;      /* a stencil state with rho <= 0 or P <= 0 was met */
-    int32_t timeout;          /* a bounded device wait gave up */
+    int32_t timeout;          /* a bounded device wait gave up (no kernel of this
+                                 version waits on another; kept for the ABI) */
     int64_t limited_elements; /* elements with alpha_min < 1 in the last stage run */
     int64_t pressure_relimits;/* elements where the step of Eq. 48 was taken */
 } kbl_counters;
@@ -199,10 +200,8 @@ int64_t kbl_launch_count(const kbl_ctx* ctx);
 /* Launch-shape knobs (not part of the method; results do not depend on them
  * beyond FP32 rounding order).  KBL_TUNE_BOUNDS_TILE selects the FP32 2D
  * bounds thread tile for grids of 32 or 64 points per axis: 0 = 4 x 4 velocity
- * nodes per thread, 1 = 4 x 2, 2 = 2 x 4; 3 (32-point grids) = a persistent,
- * warp-specialized kernel (one warp builds the next element's tables while four
- * run the 4 x 2 envelope loop; results equal to 1 bit for bit).  Setting a knob
- * drops the captured step graph. */
+ * nodes per thread, 1 = 4 x 2, 2 = 2 x 4.  Setting a knob drops the captured
+ * step graph. */
 typedef enum { KBL_TUNE_BOUNDS_TILE = 0 } kbl_tune_key;
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);

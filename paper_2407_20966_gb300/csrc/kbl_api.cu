@@ -569,7 +569,7 @@ kbl_status kbl_read_counters(kbl_ctx* c, kbl_counters* out)
 kbl_status kbl_set_tuning(kbl_ctx* c, int key, int value)
 {
     if (!c) return KBL_EINVAL;
-    if (key != KBL_TUNE_BOUNDS_TILE || value < 0 || value > 3) return fail(c, KBL_EINVAL, "unknown tuning knob or value");
+    if (key != KBL_TUNE_BOUNDS_TILE || value < 0 || value > 2) return fail(c, KBL_EINVAL, "unknown tuning knob or value");
     c->bounds_tile = value;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;

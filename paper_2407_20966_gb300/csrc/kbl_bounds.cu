@@ -321,322 +321,6 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
 }
 
 // ---------------------------------------------------------------------------
-// 2D, FP32, warp-specialized and persistent.  Each block walks the elements
-// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 (the producer) gathers the next
-// element's stencil, computes its primitive states and box and writes its row tables
-// and moment coefficients into one of two buffers, while warps 1..4 (the consumers,
-// 4 x 2 velocity nodes per thread) run the envelope loop, the moments and the
-// compensated reduction of the current element from the other buffer.  Hand-over
-// through named barriers: FULL[b] (the producer arrives, the consumers wait) and
-// EMPTY[b] (the consumers arrive once they no longer read buffer b, the producer waits
-// before refilling it).  Both sides walk the same element sequence, so every barrier
-// generation is matched.  The arithmetic is that of the 4 x 2 tile of k_bounds2d_f32.
-// ---------------------------------------------------------------------------
-namespace ws {
-constexpr int CW = 4;                    // consumer warps
-constexpr int NTH = 32 * (1 + CW);       // threads per block
-constexpr int NTC = 32 * CW;             // consumer threads
-// named barrier ids (0 is __syncthreads): FULL b = 1 + b, EMPTY b = 3 + b, consumers only = 5
-template <int ID, int COUNT>
-__device__ __forceinline__ void bar_sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory"); }
-template <int ID, int COUNT>
-__device__ __forceinline__ void bar_arrive() { asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(COUNT) : "memory"); }
-__device__ __forceinline__ void full_arrive(int b)
-{
-    __threadfence_block();   // the buffer's contents before the hand-over
-    if (b) bar_arrive<2, NTH>();
-    else bar_arrive<1, NTH>();
-}
-__device__ __forceinline__ void full_wait(int b)
-{
-    if (b) bar_sync<2, NTH>();
-    else bar_sync<1, NTH>();
-}
-__device__ __forceinline__ void empty_arrive(int b)
-{
-    if (b) bar_arrive<4, NTH>();
-    else bar_arrive<3, NTH>();
-}
-__device__ __forceinline__ void empty_wait(int b)
-{
-    if (b) bar_sync<4, NTH>();
-    else bar_sync<3, NTH>();
-}
-__device__ __forceinline__ void consumers_sync() { bar_sync<5, NTC>(); }
-}  // namespace ws
-
-template <int N, int NX>
-struct WsSmem {
-    static constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP, NV = 4;
-    static constexpr int NSTP = (NST + 1) & ~1, NPAIR = NSTP / 2;
-    // producer scratch
-    double sS[NST][NV];
-    __align__(8) float sUx[NSTP], sUy[NSTP], sKx[NSTP], sA[NSTP], sC[NSTP];
-    // two element buffers
-    __align__(16) float2 sEx[2][NPAIR][NX], sExc[2][NPAIR][NX], sEy[2][NPAIR][NX];
-    float coef[2][7][NX];   // x: q, q u, u^2/2; y: q, q u^2/2, q u (u < 0), q u (u >= 0)
-    float scal[2][2];       // hx, hy
-    int bad[2];
-    // consumers
-    float sred[ws::CW][16][2];
-    double sfin[12];
-};
-
-template <int N, int NX>
-__global__ void __launch_bounds__(ws::NTH, (N <= 4 ? 5 : 3))
-k_bounds2d_f32ws(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
-                 double* __restrict__ bnd, DevFlags* flags)
-{
-    static_assert(NX == 32, "one table column per producer lane");
-    using SMT = WsSmem<N, NX>;
-    using SH = B2f32<NX, 2>;   // 4 x 2 tile: x tables in the permuted layout, y tables in natural order
-    static_assert(SH::NT == ws::NTC, "consumer tile");
-    constexpr int NST = SMT::NST, NV = 4, NSTP = SMT::NSTP, NPAIR = SMT::NPAIR;
-    constexpr int TX = SH::TX, TY = SH::TY, TPX = SH::TPX;
-    extern __shared__ __align__(16) unsigned char ws_raw[];
-    SMT& sm = *reinterpret_cast<SMT*>(ws_raw);
-    const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if ((int)blockIdx.x >= m.E) return;   // block-uniform
-    const int n_iter = (m.E - (int)blockIdx.x + G - 1) / G;
-
-    if (wid == 0) {
-        // ------------------------------ producer ------------------------------
-        const float gm1 = ph.gm1f, kk = ph.kf, half_delta = ph.half_delta2f;
-        for (int it = 0; it < n_iter; it++) {
-            const int e = (int)blockIdx.x + it * G, b = it & 1;
-            for (int idx = lane; idx < NST * NV; idx += 32) {
-                const int v = idx / NST, r = idx % NST;
-                double val;
-                if (r < SMT::NS) val = w[((size_t)v * m.E + e) * SMT::NS + r];
-                else if (r < SMT::NS + SMT::NFP) val = wf[((size_t)v * m.E + e) * SMT::NFP + (r - SMT::NS)];
-                else val = kbl_exterior<2, N>(wf, m, e, r - SMT::NS - SMT::NFP, v);
-                sm.sS[r][v] = val;
-            }
-            __syncwarp();
-            float blx = FLT_MAX, bly = FLT_MAX, bhx = -FLT_MAX, bhy = -FLT_MAX;
-            int bad = 0;
-            for (int i = lane; i < NSTP; i += 32) {
-                const double* q = sm.sS[i < NST ? i : NST - 1];
-                const double X = fma(q[3], q[0], -0.5 * fma(q[2], q[2], q[1] * q[1]));
-                if (!kbl_positive(q[0]) || !kbl_positive(X)) bad = 1;
-                const float r = f32_trunc(q[0]), inv = 1.0f / r;
-                const float ux = f32_trunc(q[1]) * inv, uy = f32_trunc(q[2]) * inv;
-                const float th = gm1 * (f32_trunc(X) * inv) * inv;
-                const float sq = sqrtf(th);
-                sm.sUx[i] = ux;
-                sm.sUy[i] = uy;
-                sm.sKx[i] = -(0.5f * LOG2E) / th;
-                sm.sA[i] = r / (6.283185307179586f * th);
-                sm.sC[i] = half_delta * th;
-                blx = fminf(blx, ux - kk * sq);
-                bhx = fmaxf(bhx, ux + kk * sq);
-                bly = fminf(bly, uy - kk * sq);
-                bhy = fmaxf(bhy, uy + kk * sq);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                blx = fminf(blx, __shfl_xor_sync(0xffffffffu, blx, o));
-                bhx = fmaxf(bhx, __shfl_xor_sync(0xffffffffu, bhx, o));
-                bly = fminf(bly, __shfl_xor_sync(0xffffffffu, bly, o));
-                bhy = fmaxf(bhy, __shfl_xor_sync(0xffffffffu, bhy, o));
-            }
-            bad = __any_sync(0xffffffffu, bad);
-            const float cx = 0.5f * (blx + bhx), cy = 0.5f * (bly + bhy);
-            const float hx = (bhx - blx) / (float)(NX - 1), hy = (bhy - bly) / (float)(NX - 1);
-            __syncwarp();
-            for (int i = lane; i < NSTP; i += 32) {
-                sm.sUx[i] -= cx;
-                sm.sUy[i] -= cy;
-            }
-            __syncwarp();
-            if (it >= 2) ws::empty_wait(b);   // the consumers are done with buffer b
-            {
-                const int j = lane;
-                const float t = (float)j - 0.5f * (float)(NX - 1);
-                const float q = kbl_qweight_f(ph, j, NX);
-                const float rxs = t * hx, rys = t * hy;
-                const float ux = cx + rxs, uy = cy + rys;
-                sm.coef[b][0][j] = q;
-                sm.coef[b][1][j] = q * ux;
-                sm.coef[b][2][j] = 0.5f * ux * ux;
-                sm.coef[b][3][j] = q;
-                sm.coef[b][4][j] = q * (0.5f * uy * uy);
-                sm.coef[b][5][j] = uy < 0.0f ? q * uy : 0.0f;
-                sm.coef[b][6][j] = uy < 0.0f ? 0.0f : q * uy;
-                const int pj = SH::pos(j), pjy = SH::posy(j);
-                const float2 rx = make_float2(rxs, rxs), ry = make_float2(rys, rys);
-                for (int pr = 0; pr < NPAIR; pr++) {
-                    const float2 ux2 = reinterpret_cast<const float2*>(sm.sUx)[pr];
-                    const float2 uy2 = reinterpret_cast<const float2*>(sm.sUy)[pr];
-                    const float2 kx = reinterpret_cast<const float2*>(sm.sKx)[pr];
-                    const float2 A = reinterpret_cast<const float2*>(sm.sA)[pr];
-                    const float2 C = reinterpret_cast<const float2*>(sm.sC)[pr];
-                    const float2 dx = __fadd2_rn(rx, make_float2(-ux2.x, -ux2.y));
-                    const float2 dy = __fadd2_rn(ry, make_float2(-uy2.x, -uy2.y));
-                    const float2 ax = __fmul2_rn(__fmul2_rn(dx, dx), kx);
-                    const float2 ay = __fmul2_rn(__fmul2_rn(dy, dy), kx);
-                    const float2 ex = __fmul2_rn(make_float2(fast_exp2(ax.x), fast_exp2(ax.y)), A);
-                    sm.sEx[b][pr][pj] = ex;
-                    sm.sExc[b][pr][pj] = __fmul2_rn(ex, C);
-                    sm.sEy[b][pr][pjy] = make_float2(fast_exp2(ay.x), fast_exp2(ay.y));
-                }
-            }
-            if (lane == 0) {
-                sm.scal[b][0] = hx;
-                sm.scal[b][1] = hy;
-                sm.bad[b] = bad;
-            }
-            ws::full_arrive(b);   // buffer b holds element e
-        }
-        return;
-    }
-
-    // ------------------------------ consumers ------------------------------
-    const int ctid = threadIdx.x - 32, cw = wid - 1;
-    const int tx = ctid % TPX, ty = ctid / TPX;
-    for (int it = 0; it < n_iter; it++) {
-        const int e = (int)blockIdx.x + it * G, b = it & 1;
-        ws::full_wait(b);
-        const bool bad = sm.bad[b] != 0;
-        float acc[16];
-#pragma unroll
-        for (int k = 0; k < 16; k++) acc[k] = 0.0f;
-        if (!bad) {
-            float tlo[TX][TY], thi[TX][TY], ilo[TX][TY], ihi[TX][TY];
-#pragma unroll
-            for (int a = 0; a < TX; a++)
-#pragma unroll
-                for (int c = 0; c < TY; c++) {
-                    tlo[a][c] = FLT_MAX; ilo[a][c] = FLT_MAX;
-                    thi[a][c] = 0.0f; ihi[a][c] = 0.0f;
-                }
-#pragma unroll 2
-            for (int pi = 0; pi < NPAIR; pi++) {
-                float2 ex[TX], exc[TX], ey[TY];
-#pragma unroll
-                for (int a = 0; a < TX; a++) {
-                    ex[a] = sm.sEx[b][pi][SH::pos(tx * TX + a)];
-                    exc[a] = sm.sExc[b][pi][SH::pos(tx * TX + a)];
-                }
-#pragma unroll
-                for (int c = 0; c < TY; c++) ey[c] = sm.sEy[b][pi][SH::posy(ty * TY + c)];
-#pragma unroll
-                for (int a = 0; a < TX; a++)
-#pragma unroll
-                    for (int c = 0; c < TY; c++) {
-                        const float2 g = __fmul2_rn(ex[a], ey[c]);
-                        const float2 cg = __fmul2_rn(exc[a], ey[c]);
-                        tlo[a][c] = fmin3(tlo[a][c], g.x, g.y);
-                        thi[a][c] = fmax3(thi[a][c], g.x, g.y);
-                        ilo[a][c] = fmin3(ilo[a][c], cg.x, cg.y);
-                        ihi[a][c] = fmax3(ihi[a][c], cg.x, cg.y);
-                    }
-            }
-            // moments (the same sums as bounds2d_f32_stencil)
-#pragma unroll
-            for (int a = 0; a < TX; a++) {
-                float cTl = 0.f, cTh = 0.f, cIl = 0.f, cIh = 0.f, cKl = 0.f, cKh = 0.f;
-                float cNh = 0.f, cNl = 0.f, cPl = 0.f, cPh = 0.f;
-#pragma unroll
-                for (int c = 0; c < TY; c++) {
-                    const int jy = ty * TY + c;
-                    const float qy = sm.coef[b][3][jy], qk = sm.coef[b][4][jy];
-                    const float qn = sm.coef[b][5][jy], qp = sm.coef[b][6][jy];
-                    const float Tl = tlo[a][c], Th = thi[a][c];
-                    cTl = fmaf(qy, Tl, cTl);
-                    cTh = fmaf(qy, Th, cTh);
-                    cIl = fmaf(qy, ilo[a][c], cIl);
-                    cIh = fmaf(qy, ihi[a][c], cIh);
-                    cKl = fmaf(qk, Tl, cKl);
-                    cKh = fmaf(qk, Th, cKh);
-                    cNh = fmaf(qn, Th, cNh);
-                    cNl = fmaf(qn, Tl, cNl);
-                    cPl = fmaf(qp, Tl, cPl);
-                    cPh = fmaf(qp, Th, cPh);
-                }
-                const int jx = tx * TX + a;
-                const float qx = sm.coef[b][0][jx], qux = sm.coef[b][1][jx], kx = sm.coef[b][2][jx];
-                const float qn = qux < 0.0f ? qux : 0.0f, qp = qux < 0.0f ? 0.0f : qux;
-                acc[0] = fmaf(qx, cTl, acc[0]);
-                acc[1] = fmaf(qx, cTh, acc[1]);
-                acc[2] = fmaf(qn, cTh, acc[2]);
-                acc[3] = fmaf(qn, cTl, acc[3]);
-                acc[4] = fmaf(qp, cTl, acc[4]);
-                acc[5] = fmaf(qp, cTh, acc[5]);
-                acc[6] = fmaf(qx, cNh, acc[6]);
-                acc[7] = fmaf(qx, cNl, acc[7]);
-                acc[8] = fmaf(qx, cPl, acc[8]);
-                acc[9] = fmaf(qx, cPh, acc[9]);
-                acc[10] = fmaf(qx, fmaf(kx, cTl, cKl + cIl), acc[10]);
-                acc[11] = fmaf(qx, fmaf(kx, cTh, cKh + cIh), acc[11]);
-            }
-        }
-        const float hx = sm.scal[b][0], hy = sm.scal[b][1];
-        if (it + 2 < n_iter) ws::empty_arrive(b);   // buffer b no longer read
-        float rh, rl;
-        warp_reduce_scatter16(acc, rh, rl);
-        if ((lane & 1) == 0 && (lane >> 1) < 12) {
-            sm.sred[cw][lane >> 1][0] = rh;
-            sm.sred[cw][lane >> 1][1] = rl;
-        }
-        ws::consumers_sync();
-        if (ctid < 12) {
-            float hi = sm.sred[0][ctid][0], lo = sm.sred[0][ctid][1];
-#pragma unroll
-            for (int q = 1; q < ws::CW; q++) {
-                float s2, e2;
-                two_sum(hi, sm.sred[q][ctid][0], s2, e2);
-                hi = s2;
-                lo = lo + sm.sred[q][ctid][1] + e2;
-            }
-            const bool upper_env = (ctid == 1) || (ctid == 2) || (ctid == 5) || (ctid == 6) || (ctid == 9) || (ctid == 11);
-            const double rel = upper_env ? ph.rel_hi : ph.rel_lo;
-            sm.sfin[ctid] = rel * ((f64_widen(hx) * f64_widen(hy)) * (f64_widen(hi) + f64_widen(lo)));
-        }
-        ws::consumers_sync();
-        if (bad) {
-            if (ctid == 0) {
-                write_nan(bnd, m.E, e, NV);
-                atomicOr(&flags->nonphysical, 1);
-            }
-        } else if (ctid < 2 * NV) {
-            const int v = ctid % NV, up = ctid / NV;
-            double val;
-            if (v == 0) val = up ? sm.sfin[1] : sm.sfin[0];
-            else if (v == NV - 1) val = up ? sm.sfin[11] : sm.sfin[10];
-            else {
-                const int b0 = 2 + 4 * (v - 1);
-                val = up ? sm.sfin[b0 + 1] + sm.sfin[b0 + 3] : sm.sfin[b0 + 0] + sm.sfin[b0 + 2];
-            }
-            if (v == 0 && !up && __double_as_longlong(val) < __double_as_longlong(ph.rho_floor)) val = ph.rho_floor;
-            bnd[((size_t)up * NV + v) * m.E + e] = val;
-        }
-    }
-}
-
-template <int N>
-int run2d_ws(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cudaStream_t s)
-{
-    const size_t smem = sizeof(WsSmem<N, 32>);
-    static int grid_per_sm = 0, sms = 0;
-    if (grid_per_sm == 0) {
-        if (cudaFuncSetAttribute(k_bounds2d_f32ws<N, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return -1;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid_per_sm, k_bounds2d_f32ws<N, 32>, ws::NTH, smem) !=
-                cudaSuccess ||
-            grid_per_sm < 1)
-            grid_per_sm = 1;
-    }
-    const int g = std::min(c->E, grid_per_sm * sms);
-    k_bounds2d_f32ws<N, 32><<<g, ws::NTH, smem, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
-    return 1;
-}
-
-// ---------------------------------------------------------------------------
 // 1D (FP64 and FP32): one block per element, one thread per velocity node
 // (strided), direct evaluation of every Maxwellian.
 // ---------------------------------------------------------------------------
@@ -760,8 +444,6 @@ int run2d(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cuda
             k_bounds2d_f32<N, NX, 2><<<c->E, B2f32<NX, 2>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
         else if (NX >= 32 && c->bounds_tile == 2)
             k_bounds2d_f32<N, NX, 3><<<c->E, B2f32<NX, 3>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
-        else if (NX == 32 && c->bounds_tile == 3)
-            return run2d_ws<N>(c, w, wf, bnd, s);
         else
             k_bounds2d_f32<N, NX, 0><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
     } else
