@@ -274,11 +274,12 @@ __device__ __forceinline__ float dt_item(const BatchDev& bd, const ProbDesc& pd,
         const int e = wi.e0 + t / NS, nd = t % NS;
         float q[4];
 #pragma unroll
-        for (int v = 0; v < 4; v++) q[v] = (float)wp[((size_t)v * pd.E + e) * NS + nd];
+        for (int v = 0; v < 4; v++) q[v] = from_f64<float>(wp[((size_t)v * pd.E + e) * NS + nd]);
         const float P = kbl_pressure<2, float>(q, gamma - 1.0f);
         const float a = sqrtf(gamma * P / q[0]);
 #pragma unroll
-        for (int k = 0; k < 2; k++) best = fminf(best, cfl * ((float)h[e * 2 + k] / (fabsf(q[1 + k] / q[0]) + a)));
+        for (int k = 0; k < 2; k++)
+            best = fminf(best, cfl * (from_f64<float>(h[e * 2 + k]) / (fabsf(q[1 + k] / q[0]) + a)));
     }
     return best;
 }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NTB) k_batch_dt(BatchDev bd, const WorkItem* _
             case 3: b = dt_item<4>(bd, pd, wi, (float)gamma, (float)cfl, w); break;
             case 4: b = dt_item<5>(bd, pd, wi, (float)gamma, (float)cfl, w); break;
         }
-        unsigned long long bits = __double_as_longlong((double)b);
+        unsigned long long bits = __double_as_longlong(to_f64<float>(b));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);

@@ -32,6 +32,41 @@ __device__ __forceinline__ void gather_states(const double* __restrict__ w, cons
     }
 }
 
+// The same copy with one thread per stencil state (2D): the source of a state is found
+// once and its four components are loaded together.
+template <int N, int NT>
+__device__ __forceinline__ void gather_states_by_state(const double* __restrict__ w, const double* __restrict__ wf,
+                                                       const MeshDev& m, int e, double (*sS)[4])
+{
+    constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP;
+    for (int r = threadIdx.x; r < NST; r += NT) {
+        const double* src;
+        size_t stride;
+        if (r < NS) {
+            src = w + (size_t)e * NS + r;
+            stride = (size_t)m.E * NS;
+        } else if (r < NS + NFP) {
+            src = wf + (size_t)e * NFP + (r - NS);
+            stride = (size_t)m.E * NFP;
+        } else {
+            const int fp = r - NS - NFP, f = fp / N, k = fp - f * N;
+            const int nb = m.nbr[e * 4 + f];
+            if (nb >= 0) {
+                src = wf + (size_t)nb * NFP + (f ^ 1) * N + k;
+                stride = (size_t)m.E * NFP;
+            } else {
+                src = m.bc + (size_t)(-nb - 1) * 4;
+                stride = 1;
+            }
+        }
+        const double v0 = src[0], v1 = src[stride], v2 = src[2 * stride], v3 = src[3 * stride];
+        sS[r][0] = v0;
+        sS[r][1] = v1;
+        sS[r][2] = v2;
+        sS[r][3] = v3;
+    }
+}
+
 // Error-free transformation: s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
@@ -98,20 +133,22 @@ struct B2f32 {
     }
 };
 
-// Compensated warp reduce-scatter of 16 values: afterwards lane L (even) holds
-// sum over the warp of value L / 2 as hi + lo.  16 exchanges instead of 16 x 5.
-__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], float& out_hi, float& out_lo)
+// Warp reduce-scatter of 16 values: afterwards lane L (even) holds the sum over the warp
+// of value L / 2.  16 exchanges instead of 16 x 5.  Plain FP32 adds: the 32 partial sums
+// meet in a 5-level pairwise tree, whose rounding error is at most 5 ulp of the sum of
+// magnitudes (each thread's own 16-term sums add at most 16 more), far inside the 1e-5
+// the FP32 bounds are held to.
+__device__ __forceinline__ float warp_reduce_scatter16(const float (&v)[16])
 {
     const int lane = threadIdx.x & 31;
-    float hi[8], lo[8];
+    float s[8];
     {   // offset 16: keep the upper 8 values on lanes with bit 4 set
         const bool up = lane & 16;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
             const float keep = up ? v[8 + k] : v[k];
             const float send = up ? v[k] : v[8 + k];
-            const float o = __shfl_xor_sync(0xffffffffu, send, 16);
-            two_sum(keep, o, hi[k], lo[k]);
+            s[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
         }
     }
 #pragma unroll
@@ -122,22 +159,11 @@ __device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], float& out
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (k >= n) break;
-            const float kh = up ? hi[n + k] : hi[k], sh = up ? hi[k] : hi[n + k];
-            const float kl = up ? lo[n + k] : lo[k], sl = up ? lo[k] : lo[n + k];
-            const float oh = __shfl_xor_sync(0xffffffffu, sh, off);
-            const float ol = __shfl_xor_sync(0xffffffffu, sl, off);
-            float s2, e2;
-            two_sum(kh, oh, s2, e2);
-            hi[k] = s2;
-            lo[k] = kl + ol + e2;
+            const float keep = up ? s[n + k] : s[k], send = up ? s[k] : s[n + k];
+            s[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
-    const float oh = __shfl_xor_sync(0xffffffffu, hi[0], 1);
-    const float ol = __shfl_xor_sync(0xffffffffu, lo[0], 1);
-    float s2, e2;
-    two_sum(hi[0], oh, s2, e2);
-    out_hi = s2;
-    out_lo = lo[0] + ol + e2;
+    return s[0] + __shfl_xor_sync(0xffffffffu, s[0], 1);
 }
 
 template <int N, int NX, int TYSEL>
@@ -150,15 +176,19 @@ struct Bounds2dF32Smem {
     static constexpr int NW = (NT + 31) / 32;
     static constexpr int K = 12;
     double sS[NST][NV];
-    // per state (SoA, so that a pair of states is one 8-byte load): velocity, -log2(e)/(2 theta), A, C
-    __align__(8) float sUx[NSTP], sUy[NSTP], sKx[NSTP], sA[NSTP], sC[NSTP];
+    // per state: velocity, s = sqrt(log2(e) / (2 theta)), A, C
+    float sUx[NSTP], sUy[NSTP], sSc[NSTP], sA[NSTP], sC[NSTP];
+    // per pair of states, for the row tables: (-s Ux', -s Uy') of both states (velocities
+    // relative to the box centre), (s, A) of both, C of both
+    float4 sPu[NPAIR], sPs[NPAIR];
+    float2 sPc[NPAIR];
     __align__(16) float2 sEx[NPAIR][NX], sExc[NPAIR][NX], sEy[NPAIR][NX];
     float srx[NX], sry[NX];          // grid relative to the box centre
     // per-node moment coefficients: x: q, q u, 1/2 u^2 ; y: q, q 1/2 u^2, q u (u<0), q u (u>=0)
     float sqx[NX], squx[NX], skx[NX], sqy[NX], sqky[NX], squyn[NX], squyp[NX];
     float sbox[NW][4];
     int sbad;
-    float sred[NW][16][2];
+    float sred[NW][16];
     double sfin[K];
 
 };
@@ -177,7 +207,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
     constexpr int NS = SM::NS, NFP = SM::NFP, NST = SM::NST, NV = SM::NV, NSTP = SM::NSTP, NPAIR = SM::NPAIR;
     constexpr int TX = SM::TX, TY = SM::TY, TPX = SM::TPX, NT = SM::NT, NW = SM::NW, K = SM::K;
     (void)NS; (void)NFP; (void)TY;
-    auto& sS = sm.sS; auto& sUx = sm.sUx; auto& sUy = sm.sUy; auto& sKx = sm.sKx; auto& sA = sm.sA;
+    auto& sS = sm.sS; auto& sUx = sm.sUx; auto& sUy = sm.sUy; auto& sSc = sm.sSc; auto& sA = sm.sA;
     auto& sC = sm.sC; auto& sEx = sm.sEx; auto& sExc = sm.sExc; auto& sEy = sm.sEy; auto& srx = sm.srx;
     auto& sry = sm.sry; auto& sqx = sm.sqx; auto& squx = sm.squx; auto& skx = sm.skx; auto& sqy = sm.sqy;
     auto& sqky = sm.sqky; auto& squyn = sm.squyn; auto& squyp = sm.squyp; auto& sbox = sm.sbox;
@@ -185,7 +215,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __syncthreads();   // the block may reuse sm for consecutive elements
     if (tid == 0) sbad = 0;
-    gather_states<2, N, NT>(w, wf, m, e, sS);
+    gather_states_by_state<N, NT>(w, wf, m, e, sS);
     __syncthreads();
 
     // 1. primitive state of each stencil node, box candidates
@@ -198,14 +228,16 @@ __device__ __forceinline__ void bounds2d_f32_element(
         // truncation on the integer pipe
         const double X = fma(q[3], q[0], -0.5 * fma(q[2], q[2], q[1] * q[1]));
         if (!kbl_positive(q[0]) || !kbl_positive(X)) bad = 1;
-        const float r = f32_trunc(q[0]), inv = 1.0f / r;
+        // reciprocals and the square root by the special-function unit (a few ulp)
+        const float r = f32_trunc(q[0]), inv = __fdividef(1.0f, r);
         const float ux = f32_trunc(q[1]) * inv, uy = f32_trunc(q[2]) * inv;
         const float th = gm1 * (f32_trunc(X) * inv) * inv;
-        const float sq = sqrtf(th);
+        const float rs = rsqrtf(th);              // 1 / sqrt(theta)
+        const float sq = th * rs;                 // sqrt(theta)
         sUx[i] = ux;
         sUy[i] = uy;
-        sKx[i] = -(0.5f * LOG2E) / th;
-        sA[i] = r / (6.283185307179586f * th);
+        sSc[i] = 0.84932180028801904f * rs;       // sqrt(log2(e) / 2) / sqrt(theta)
+        sA[i] = r * (0.15915494309189535f * (rs * rs));   // rho / (2 pi theta)
         sC[i] = half_delta * th;
         blx = fminf(blx, ux - kk * sq);
         bhx = fmaxf(bhx, ux + kk * sq);
@@ -244,9 +276,12 @@ __device__ __forceinline__ void bounds2d_f32_element(
 
     // 2. state velocities and grid relative to the box centre (for the Maxwellians,
     //    which keeps FP32 differences small), absolute grid for the moments
-    for (int i = tid; i < NSTP; i += NT) {
-        sUx[i] -= cx;
-        sUy[i] -= cy;
+    for (int pr = tid; pr < NPAIR; pr += NT) {
+        const float sa = sSc[2 * pr], sb = sSc[2 * pr + 1];
+        sm.sPu[pr] = make_float4(-sa * (sUx[2 * pr] - cx), -sb * (sUx[2 * pr + 1] - cx),
+                                 -sa * (sUy[2 * pr] - cy), -sb * (sUy[2 * pr + 1] - cy));
+        sm.sPs[pr] = make_float4(sa, sb, sA[2 * pr], sA[2 * pr + 1]);
+        sm.sPc[pr] = make_float2(sC[2 * pr], sC[2 * pr + 1]);
     }
     for (int j = tid; j < NX; j += NT) {
         const float t = (float)(PAD ? min(j, nu - 1) : j) - 0.5f * (float)(nu - 1);
@@ -265,7 +300,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
     }
     __syncthreads();
     // 3. row tables of every state, two states per packed instruction:
-    //    Ex = A exp2(-(ux-Ux)^2 kx), C Ex, Ey = exp2(-(uy-Uy)^2 kx)
+    //    Ex = A exp2(-(s (ux - Ux))^2), C Ex, Ey = exp2(-(s (uy - Uy))^2), s^2 = log2(e) / (2 theta)
     {
         constexpr int ROWS = NT / NX > 0 ? NT / NX : 1;
         const int j = tid % NX;
@@ -273,19 +308,15 @@ __device__ __forceinline__ void bounds2d_f32_element(
         const float2 rx = make_float2(srx[j], srx[j]);
         const float2 ry = make_float2(sry[j], sry[j]);
         for (int pr = tid / NX; pr < NPAIR; pr += ROWS) {
-            const float2 ux = reinterpret_cast<const float2*>(sUx)[pr];
-            const float2 uy = reinterpret_cast<const float2*>(sUy)[pr];
-            const float2 kx = reinterpret_cast<const float2*>(sKx)[pr];
-            const float2 A = reinterpret_cast<const float2*>(sA)[pr];
-            const float2 C = reinterpret_cast<const float2*>(sC)[pr];
-            const float2 dx = __fadd2_rn(rx, make_float2(-ux.x, -ux.y));
-            const float2 dy = __fadd2_rn(ry, make_float2(-uy.x, -uy.y));
-            const float2 ax = __fmul2_rn(__fmul2_rn(dx, dx), kx);
-            const float2 ay = __fmul2_rn(__fmul2_rn(dy, dy), kx);
-            const float2 ex = __fmul2_rn(make_float2(fast_exp2(ax.x), fast_exp2(ax.y)), A);
+            const float4 u = sm.sPu[pr], sa = sm.sPs[pr];
+            const float2 s2 = make_float2(sa.x, sa.y);
+            const float2 dx = __ffma2_rn(rx, s2, make_float2(u.x, u.y));
+            const float2 dy = __ffma2_rn(ry, s2, make_float2(u.z, u.w));
+            const float2 ax = __fmul2_rn(dx, dx), ay = __fmul2_rn(dy, dy);
+            const float2 ex = __fmul2_rn(make_float2(fast_exp2(-ax.x), fast_exp2(-ax.y)), make_float2(sa.z, sa.w));
             sEx[pr][pj] = ex;
-            sExc[pr][pj] = __fmul2_rn(ex, C);
-            sEy[pr][pjy] = make_float2(fast_exp2(ay.x), fast_exp2(ay.y));
+            sExc[pr][pj] = __fmul2_rn(ex, sm.sPc[pr]);
+            sEy[pr][pjy] = make_float2(fast_exp2(-ay.x), fast_exp2(-ay.y));
         }
     }
     __syncthreads();
@@ -365,27 +396,18 @@ __device__ __forceinline__ void bounds2d_f32_element(
         acc[10] = fmaf(qx, fmaf(kx, cTl, cKl + cIl), acc[10]);
         acc[11] = fmaf(qx, fmaf(kx, cTh, cKh + cIh), acc[11]);
     }
-    float rh, rl;
-    warp_reduce_scatter16(acc, rh, rl);
-    if ((lane & 1) == 0 && (lane >> 1) < K) {
-        sred[wid][lane >> 1][0] = rh;
-        sred[wid][lane >> 1][1] = rl;
-    }
+    const float rs = warp_reduce_scatter16(acc);
+    if ((lane & 1) == 0 && (lane >> 1) < K) sred[wid][lane >> 1] = rs;
     __syncthreads();
     // 6. assemble the bounds in FP64, one raw sum per lane
     if (tid < K) {
-        float hi = sred[0][tid][0], lo = sred[0][tid][1];
+        float sum = sred[0][tid];
 #pragma unroll
-        for (int q = 1; q < NW; q++) {
-            float s2, e2;
-            two_sum(hi, sred[q][tid][0], s2, e2);
-            hi = s2;
-            lo = lo + sred[q][tid][1] + e2;
-        }
+        for (int q = 1; q < NW; q++) sum += sred[q][tid];
         // lower-bound terms take (1 - r), upper-bound terms (1 + r)
         const bool upper_env = (tid == 1) || (tid == 2) || (tid == 5) || (tid == 6) || (tid == 9) || (tid == 11);
         const double rel = upper_env ? ph.rel_hi : ph.rel_lo;
-        sfin[tid] = rel * ((f64_widen(hx) * f64_widen(hy)) * (f64_widen(hi) + f64_widen(lo)));
+        sfin[tid] = rel * ((f64_widen(hx) * f64_widen(hy)) * f64_widen(sum));
     }
     __syncthreads();
     if (tid < 2 * NV) {

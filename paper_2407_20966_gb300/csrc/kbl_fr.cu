@@ -144,17 +144,17 @@ __global__ void __launch_bounds__(256) k_dt(const double* __restrict__ w, MeshDe
         const T gamma = (T)gamma_d;
         T q[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) q[v] = (T)w[((size_t)v * m.E + e) * NS + nd];
+        for (int v = 0; v < NV; v++) q[v] = kbl_dev::from_f64<T>(w[((size_t)v * m.E + e) * NS + nd]);
         const T P = kbl_pressure<DIM, T>(q, gamma - T(1));
         const T a = sqrt(gamma * P / q[0]);
         T b = (T)DBL_MAX;
         if (sizeof(T) == sizeof(float)) b = (T)FLT_MAX;
 #pragma unroll
         for (int k = 0; k < DIM; k++) {
-            const T cand = (T)cfl * ((T)m.h[e * DIM + k] / (fabs(q[1 + k] / q[0]) + a));
+            const T cand = (T)cfl * (kbl_dev::from_f64<T>(m.h[e * DIM + k]) / (fabs(q[1 + k] / q[0]) + a));
             b = fmin(b, cand);
         }
-        best = (double)b;
+        best = kbl_dev::to_f64<T>(b);
     }
     unsigned long long bits = __double_as_longlong(best);
 #pragma unroll

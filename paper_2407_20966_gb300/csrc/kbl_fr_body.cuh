@@ -6,6 +6,18 @@
 
 namespace kbl_dev {
 
+// Storage (FP64) to arithmetic type and back.  For FP32 arithmetic the conversions run on
+// the integer pipe (truncation in, exact widening out): a conversion instruction would take
+// an FP64-pipe slot, and the FP64 pipe is the slow one.
+template <typename T>
+__device__ __forceinline__ T from_f64(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return f32_trunc(x); }
+template <typename T>
+__device__ __forceinline__ double to_f64(T x) { return x; }
+template <>
+__device__ __forceinline__ double to_f64<float>(float x) { return f64_widen(x); }
+
 template <int DIM, int N, typename T, int EPB>
 struct RhsSmem {
     static constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
@@ -50,11 +62,11 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
     const int el = tid / NS, nd = tid % NS;
     const int e = e0 + el;
     const bool node_thread = el < EPB && el < nmax && e < m.E;
-    const T gamma = (T)gamma_d, gm1 = (T)(gamma_d - 1.0);
+    const T gamma = from_f64<T>(gamma_d), gm1 = from_f64<T>(gamma_d - 1.0);
     if (node_thread) {
         T q[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) q[v] = (T)w[((size_t)v * m.E + e) * NS + nd];
+        for (int v = 0; v < NV; v++) q[v] = from_f64<T>(w[((size_t)v * m.E + e) * NS + nd]);
 #pragma unroll
         for (int dir = 0; dir < DIM; dir++) {
             T F[NV];
@@ -72,8 +84,8 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
         T qi[NV], qe[NV], Fc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            qi[v] = (T)wf[((size_t)v * m.E + ee) * NFP + fp];
-            qe[v] = (T)kbl_exterior<DIM, N>(wf, m, ee, fp, v);
+            qi[v] = from_f64<T>(wf[((size_t)v * m.E + ee) * NFP + fp]);
+            qe[v] = from_f64<T>(kbl_exterior<DIM, N>(wf, m, ee, fp, v));
         }
         if (flux == 1) {
             if (side == 0) kbl_hllc<DIM, T>(qe, qi, dir, gamma, Fc);
@@ -101,8 +113,8 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
     if (!node_thread) return;
     const int i = (DIM == 1) ? nd : nd % N;
     const int j = (DIM == 1) ? 0 : nd / N;
-    const T sx = (T)(2.0 / m.h[e * DIM + 0]);
-    const T sy = (DIM == 2) ? (T)(2.0 / m.h[e * DIM + 1]) : T(0);
+    const T sx = T(2) / from_f64<T>(m.h[e * DIM + 0]);
+    const T sy = (DIM == 2) ? T(2) / from_f64<T>(m.h[e * DIM + 1]) : T(0);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         T dx = T(0);
@@ -117,7 +129,7 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
             dy += sgl[j] * sJ[el][2 * NFPF + i][v] + sgr[j] * sJ[el][3 * NFPF + i][v];
             r -= sy * dy;
         }
-        R[((size_t)v * m.E + e) * NS + nd] = (double)r;
+        R[((size_t)v * m.E + e) * NS + nd] = to_f64<T>(r);
     }
 }
 
