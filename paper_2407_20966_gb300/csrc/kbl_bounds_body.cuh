@@ -175,14 +175,22 @@ struct Bounds2dF32Smem {
     static constexpr int TX = SH::TX, TY = SH::TY, TPX = SH::TPX, NT = SH::NT;
     static constexpr int NW = (NT + 31) / 32;
     static constexpr int K = 12;
-    double sS[NST][NV];
-    // per state: velocity, s = sqrt(log2(e) / (2 theta)), A, C
-    float sUx[NSTP], sUy[NSTP], sSc[NSTP], sA[NSTP], sC[NSTP];
+    // The stencil copy and the per-state constants are dead once the row tables are
+    // written (a barrier lies between), so they share storage with the tables.
+    union __align__(16) {
+        struct {
+            double sS[NST][NV];
+            // per state: velocity, s = sqrt(log2(e) / (2 theta)), A, C
+            float sUx[NSTP], sUy[NSTP], sSc[NSTP], sA[NSTP], sC[NSTP];
+        } pre;
+        struct {
+            float2 sEx[NPAIR][NX], sExc[NPAIR][NX], sEy[NPAIR][NX];
+        } tab;
+    } u;
     // per pair of states, for the row tables: (-s Ux', -s Uy') of both states (velocities
     // relative to the box centre), (s, A) of both, C of both
     float4 sPu[NPAIR], sPs[NPAIR];
     float2 sPc[NPAIR];
-    __align__(16) float2 sEx[NPAIR][NX], sExc[NPAIR][NX], sEy[NPAIR][NX];
     float srx[NX], sry[NX];          // grid relative to the box centre
     // per-node moment coefficients: x: q, q u, 1/2 u^2 ; y: q, q 1/2 u^2, q u (u<0), q u (u>=0)
     float sqx[NX], squx[NX], skx[NX], sqy[NX], sqky[NX], squyn[NX], squyp[NX];
@@ -207,8 +215,9 @@ __device__ __forceinline__ void bounds2d_f32_element(
     constexpr int NS = SM::NS, NFP = SM::NFP, NST = SM::NST, NV = SM::NV, NSTP = SM::NSTP, NPAIR = SM::NPAIR;
     constexpr int TX = SM::TX, TY = SM::TY, TPX = SM::TPX, NT = SM::NT, NW = SM::NW, K = SM::K;
     (void)NS; (void)NFP; (void)TY;
-    auto& sS = sm.sS; auto& sUx = sm.sUx; auto& sUy = sm.sUy; auto& sSc = sm.sSc; auto& sA = sm.sA;
-    auto& sC = sm.sC; auto& sEx = sm.sEx; auto& sExc = sm.sExc; auto& sEy = sm.sEy; auto& srx = sm.srx;
+    auto& sS = sm.u.pre.sS; auto& sUx = sm.u.pre.sUx; auto& sUy = sm.u.pre.sUy; auto& sSc = sm.u.pre.sSc;
+    auto& sA = sm.u.pre.sA; auto& sC = sm.u.pre.sC; auto& sEx = sm.u.tab.sEx; auto& sExc = sm.u.tab.sExc;
+    auto& sEy = sm.u.tab.sEy; auto& srx = sm.srx;
     auto& sry = sm.sry; auto& sqx = sm.sqx; auto& squx = sm.squx; auto& skx = sm.skx; auto& sqy = sm.sqy;
     auto& sqky = sm.sqky; auto& squyn = sm.squyn; auto& squyp = sm.squyp; auto& sbox = sm.sbox;
     auto& sbad = sm.sbad; auto& sred = sm.sred; auto& sfin = sm.sfin;
