@@ -44,9 +44,9 @@ LANE_OPS_PER_CLK_SM = 155.5
 PEAK_SOURCE = ("measured envelope-pattern rate 155.5 FP32 lane-ops/clk/SM (bench.py --peaks) "
                "x 152 SMs x 2070 MHz")
 # DRAM bytes (read + write) of one launch of the FP32 2D bounds kernel on the vortex workload,
-# from the ncu capture summarised in profiles/bounds_f32_vortex128_p3.md.  Must be reset to
-# None whenever that kernel changes, until it is captured again.
-BOUNDS_F32_VORTEX_TRAFFIC = 17068800 + 0
+# from an ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum).  Must be
+# reset to None whenever that kernel changes, until it is captured again.
+BOUNDS_F32_VORTEX_TRAFFIC = 17078016 + 0
 
 
 def parse():
