@@ -429,7 +429,7 @@ struct StageVjpSmem {
     double salpha[EPB_L], saP[EPB_L], sPbar[EPB_L], spmin[EPB_L];
     double sxb[EPB_L][NV];   // cotangent of the extreme point of Eq. 37 of each component
     int staken[EPB_L], sapm[EPB_L], svstar[EPB_L], sxpt[EPB_L][NV];
-    double sW[NS], sWsum;
+    double sW[NS];
 };
 
 template <int N>
@@ -456,12 +456,7 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
     const double gm1 = ph.gamma - 1.0;
     // the factor of Eq. 38 that component v of element ell takes (per component if uncoupled)
     auto aeff = [&](int ell, int v) { return ph.uncoupled ? sm.salpha_v[ell][v] : sm.salpha[ell]; };
-    if (tid < NS) sm.sW[tid] = ops.wq[tid % N] * ops.wq[tid / N];
-    if (tid == 0) {
-        double s = 0.0;
-        for (int n2 = 0; n2 < NS; n2++) s += ops.wq[n2 % N] * ops.wq[n2 / N];
-        sm.sWsum = s;
-    }
+    if (tid < NS) sm.sW[tid] = ops.wm2[tid];   // the forward kernel's mean: sum W w times 1 / sum W
     // 1. stage combination (the forward kernel's expression)
     if (live)
         for (int v = 0; v < NV; v++) {
@@ -496,7 +491,7 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
         if (ee >= E) continue;
         double s = 0.0;
         for (int n2 = 0; n2 < NS; n2++) s += sm.sW[n2] * sw[ell][v][n2];
-        const double mean = s / sm.sWsum;
+        const double mean = s * ops.winv2;
         double mx = sw[ell][v][0], mn = mx;
         int amx = 0, amn = 0;
         for (int n2 = 1; n2 < NVP; n2++) {
@@ -669,7 +664,7 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
     const int i = nd % N, j = nd / N;
     for (int v = 0; v < NV; v++) {
         double g = aeff(el, v) * stb[el][v][nd] + (sm.sxpt[el][v] == nd ? sm.sxb[el][v] : 0.0);
-        g += smb[el][v] * sm.sW[nd] / sm.sWsum;
+        g += smb[el][v] * (sm.sW[nd] * ops.winv2);
         g += ops.lm[i] * sfb[el][v][0 * N + j] + ops.lp[i] * sfb[el][v][1 * N + j] +
              ops.lm[j] * sfb[el][v][2 * N + i] + ops.lp[j] * sfb[el][v][3 * N + i];
         const size_t gi = ((size_t)v * E + e) * NS + nd;

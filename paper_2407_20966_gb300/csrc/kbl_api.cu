@@ -140,6 +140,19 @@ void build_ops(int p, FrOps& o)
         o.gl[i] = -o.lm[i] / o.wq[i];
         o.gr[i] = o.lp[i] / o.wq[i];
     }
+    double s1 = 0.0, s2 = 0.0, am = 0.0, ap = 0.0;
+    for (int i = 0; i < n; i++) {
+        s1 += o.wq[i];
+        am += std::fabs(o.lm[i]);
+        ap += std::fabs(o.lp[i]);
+    }
+    for (int k = 0; k < n * n; k++) {
+        o.wm2[k] = o.wq[k % n] * o.wq[k / n];
+        s2 += o.wm2[k];
+    }
+    o.winv1 = 1.0 / s1;
+    o.winv2 = 1.0 / s2;
+    o.lam = std::max(am, ap);
 }
 
 kbl_status fail(kbl_ctx* c, kbl_status st, const char* msg)

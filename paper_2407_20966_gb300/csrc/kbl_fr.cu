@@ -162,7 +162,14 @@ __global__ void __launch_bounds__(256) k_dt(const double* __restrict__ w, MeshDe
         const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
         bits = ob < bits ? ob : bits;
     }
-    if ((threadIdx.x & 31) == 0) atomicMin(dtbits, bits);
+    // one atomic per block: thousands of warps on one address would serialise in L2
+    __shared__ unsigned long long swarp[8];
+    if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) bits = swarp[k] < bits ? swarp[k] : bits;
+        atomicMin(dtbits, bits);
+    }
 }
 
 __global__ void k_dt_finalize(const unsigned long long* dtbits, const double* scal, double* dt_out,

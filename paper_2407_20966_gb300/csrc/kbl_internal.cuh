@@ -21,6 +21,11 @@ struct FrOps {
     double lm[KBL_NMAX], lp[KBL_NMAX];      // l_i(-1), l_i(+1)
     double D[KBL_NMAX][KBL_NMAX];           // D[i][m] = l_m'(x_i)
     double gl[KBL_NMAX], gr[KBL_NMAX];      // g_L'(x_i), g_R'(x_i)
+    // limiter constants, computed on the host once per order: the 2D mean weights
+    // wq[n % N] wq[n / N], 1 / sum of the weights in 1D and 2D, and Lambda = max over the two
+    // ends of sum_i |l_i(+-1)| (a face value lies within Lambda max_i |w_i - mean| of the mean)
+    double wm2[KBL_NMAX * KBL_NMAX];
+    double winv1, winv2, lam;
 };
 
 // Physical and method constants, passed by value.

@@ -32,7 +32,6 @@ struct LimSmem {
     double saP[EPB];
     int sPtaken[EPB];
     double slm[N], slp[N], sW[NS];
-    double sWsum, sLam;
     // exact fast path: per-component box around the mean that holds every value of V
     double sbl[EPB][NV], sbh[EPB][NV];
     double sdmx[EPB][NV], sdmn[EPB][NV];   // node extremes minus the mean
@@ -66,8 +65,6 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     auto& slm = sm.slm;
     auto& slp = sm.slp;
     auto& sW = sm.sW;
-    auto& sWsum = sm.sWsum;
-    auto& sLam = sm.sLam;
     auto& sbl = sm.sbl;
     auto& sbh = sm.sbh;
     auto& sfv = sm.sfv;
@@ -82,20 +79,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         slm[tid] = ops.lm[tid];
         slp[tid] = ops.lp[tid];
     }
-    if (tid < NS) sW[tid] = (DIM == 1) ? ops.wq[tid] : ops.wq[tid % N] * ops.wq[tid / N];
-    if (tid == 0) {
-        double sws = 0.0;
-        for (int n2 = 0; n2 < NS; n2++) sws += (DIM == 1) ? ops.wq[n2] : ops.wq[n2 % N] * ops.wq[n2 / N];
-        sWsum = sws;
-        // Lambda = max over the two ends of sum |l_i(+-1)|: since the weights sum to one, a face
-        // value differs from the mean by at most Lambda * max_i |w_i - mean| along its line
-        double am = 0.0, ap = 0.0;
-        for (int i = 0; i < N; i++) {
-            am += fabs(ops.lm[i]);
-            ap += fabs(ops.lp[i]);
-        }
-        sLam = fmax(am, ap);
-    }
+    // mean weights, 1 / their sum and Lambda come precomputed with the operators (no FP64
+    // arithmetic here: every FP64 instruction holds the slow FP64 pipe however few lanes run)
+    if (tid < NS) sW[tid] = (DIM == 1) ? ops.wq[tid] : ops.wm2[tid];
+    const double winv = (DIM == 1) ? ops.winv1 : ops.winv2, sLam = ops.lam;
     const int el = tid / NS, nd = tid % NS;
     const int e = e0 + el;
     const bool live = el < EPB && el < nmax && e < E;
@@ -129,7 +116,7 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         if (e0 + ell >= E || ell >= nmax) continue;
         double sum = 0.0;
         for (int n2 = 0; n2 < NS; n2++) sum += sW[n2] * sw[ell][v][n2];
-        const double mean = sum / sWsum;
+        const double mean = sum * winv;
         long long kmx = dkey(sw[ell][v][0]), kmn = kmx;
         for (int n2 = 1; n2 < NS; n2++) {
             const long long kk = dkey(sw[ell][v][n2]);
