@@ -192,8 +192,10 @@ struct Bounds2dF32Smem {
     float4 sPu[NPAIR], sPs[NPAIR];
     float2 sPc[NPAIR];
     float srx[NX], sry[NX];          // grid relative to the box centre
-    // per-node moment coefficients: x: q, q u, 1/2 u^2 ; y: q, q 1/2 u^2, q u (u<0), q u (u>=0)
-    float sqx[NX], squx[NX], skx[NX], sqy[NX], sqky[NX], squyn[NX], squyp[NX];
+    // per-node moment coefficients, each duplicated into a pair so that one packed FMA updates
+    // a (lower, upper) pair of sums: x: q, q u (u<0), q u (u>=0), 1/2 u^2; y: q, q 1/2 u^2,
+    // q u (u<0), q u (u>=0)
+    float2 sqx[NX], squxn[NX], squxp[NX], skx[NX], sqy[NX], sqky[NX], squyn[NX], squyp[NX];
     float sbox[NW][4];
     int sbad;
     float sred[NW][16];
@@ -218,7 +220,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
     auto& sS = sm.u.pre.sS; auto& sUx = sm.u.pre.sUx; auto& sUy = sm.u.pre.sUy; auto& sSc = sm.u.pre.sSc;
     auto& sA = sm.u.pre.sA; auto& sC = sm.u.pre.sC; auto& sEx = sm.u.tab.sEx; auto& sExc = sm.u.tab.sExc;
     auto& sEy = sm.u.tab.sEy; auto& srx = sm.srx;
-    auto& sry = sm.sry; auto& sqx = sm.sqx; auto& squx = sm.squx; auto& skx = sm.skx; auto& sqy = sm.sqy;
+    auto& sry = sm.sry; auto& sqx = sm.sqx; auto& squxn = sm.squxn; auto& squxp = sm.squxp; auto& skx = sm.skx; auto& sqy = sm.sqy;
     auto& sqky = sm.sqky; auto& squyn = sm.squyn; auto& squyp = sm.squyp; auto& sbox = sm.sbox;
     auto& sbad = sm.sbad; auto& sred = sm.sred; auto& sfin = sm.sfin;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -299,13 +301,17 @@ __device__ __forceinline__ void bounds2d_f32_element(
         const float ux = cx + rx, uy = cy + ry;
         srx[j] = rx;
         sry[j] = ry;
-        sqx[j] = q;
-        squx[j] = q * ux;
-        skx[j] = 0.5f * ux * ux;
-        sqy[j] = q;
-        sqky[j] = q * (0.5f * uy * uy);
-        squyn[j] = uy < 0.0f ? q * uy : 0.0f;
-        squyp[j] = uy < 0.0f ? 0.0f : q * uy;
+        const float qux = q * ux, kx = 0.5f * ux * ux, qky = q * (0.5f * uy * uy);
+        const float qxn = qux < 0.0f ? qux : 0.0f, qxp = qux < 0.0f ? 0.0f : qux;
+        const float qyn = uy < 0.0f ? q * uy : 0.0f, qyp = uy < 0.0f ? 0.0f : q * uy;
+        sqx[j] = make_float2(q, q);
+        squxn[j] = make_float2(qxn, qxn);
+        squxp[j] = make_float2(qxp, qxp);
+        skx[j] = make_float2(kx, kx);
+        sqy[j] = make_float2(q, q);
+        sqky[j] = make_float2(qky, qky);
+        squyn[j] = make_float2(qyn, qyn);
+        squyp[j] = make_float2(qyp, qyp);
     }
     __syncthreads();
     // 3. row tables of every state, two states per packed instruction:
@@ -368,45 +374,40 @@ __device__ __forceinline__ void bounds2d_f32_element(
     //    raw = [Tlo, Thi, nx_hi, nx_lo, px_lo, px_hi, ny_hi, ny_lo, py_lo, py_hi, E_lo, E_hi]
     //    (n/p: u < 0 / u >= 0 part of the momentum sums; hx hy and the
     //    relaxation are applied in FP64 at the end)
-    float acc[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) acc[k] = 0.0f;
+    //    Every sum pairs with its counterpart of the other envelope, so one packed FMA
+    //    updates both; lane by lane the arithmetic and its order are those of scalar FMAs.
+    float2 a01 = make_float2(0.f, 0.f), a32 = a01, a45 = a01, a76 = a01, a89 = a01, aE = a01;
 #pragma unroll
     for (int a = 0; a < TX; a++) {
-        float cTl = 0.f, cTh = 0.f, cIl = 0.f, cIh = 0.f, cKl = 0.f, cKh = 0.f;
-        float cNh = 0.f, cNl = 0.f, cPl = 0.f, cPh = 0.f;
+        float2 cT = make_float2(0.f, 0.f), cI = cT, cK = cT, cN = cT, cP = cT;
 #pragma unroll
         for (int b = 0; b < TY; b++) {
             const int jy = ty * TY + b;
-            const float qy = sqy[jy], qk = sqky[jy], qn = squyn[jy], qp = squyp[jy];
-            const float Tl = tlo[a][b], Th = thi[a][b];
-            cTl = fmaf(qy, Tl, cTl);
-            cTh = fmaf(qy, Th, cTh);
-            cIl = fmaf(qy, ilo[a][b], cIl);
-            cIh = fmaf(qy, ihi[a][b], cIh);
-            cKl = fmaf(qk, Tl, cKl);
-            cKh = fmaf(qk, Th, cKh);
-            cNh = fmaf(qn, Th, cNh);
-            cNl = fmaf(qn, Tl, cNl);
-            cPl = fmaf(qp, Tl, cPl);
-            cPh = fmaf(qp, Th, cPh);
+            const float2 T = make_float2(tlo[a][b], thi[a][b]);
+            cT = __ffma2_rn(sqy[jy], T, cT);
+            cI = __ffma2_rn(sqy[jy], make_float2(ilo[a][b], ihi[a][b]), cI);
+            cK = __ffma2_rn(sqky[jy], T, cK);
+            cN = __ffma2_rn(squyn[jy], T, cN);
+            cP = __ffma2_rn(squyp[jy], T, cP);
         }
         const int jx = tx * TX + a;
-        const float qx = sqx[jx], qux = squx[jx], kx = skx[jx];
-        const float qn = squx[jx] < 0.0f ? qux : 0.0f, qp = squx[jx] < 0.0f ? 0.0f : qux;
-        acc[0] = fmaf(qx, cTl, acc[0]);
-        acc[1] = fmaf(qx, cTh, acc[1]);
-        acc[2] = fmaf(qn, cTh, acc[2]);
-        acc[3] = fmaf(qn, cTl, acc[3]);
-        acc[4] = fmaf(qp, cTl, acc[4]);
-        acc[5] = fmaf(qp, cTh, acc[5]);
-        acc[6] = fmaf(qx, cNh, acc[6]);
-        acc[7] = fmaf(qx, cNl, acc[7]);
-        acc[8] = fmaf(qx, cPl, acc[8]);
-        acc[9] = fmaf(qx, cPh, acc[9]);
-        acc[10] = fmaf(qx, fmaf(kx, cTl, cKl + cIl), acc[10]);
-        acc[11] = fmaf(qx, fmaf(kx, cTh, cKh + cIh), acc[11]);
+        const float2 qx = sqx[jx];
+        a01 = __ffma2_rn(qx, cT, a01);
+        a32 = __ffma2_rn(squxn[jx], cT, a32);
+        a45 = __ffma2_rn(squxp[jx], cT, a45);
+        a76 = __ffma2_rn(qx, cN, a76);
+        a89 = __ffma2_rn(qx, cP, a89);
+        aE = __ffma2_rn(qx, __ffma2_rn(skx[jx], cT, __fadd2_rn(cK, cI)), aE);
     }
+    float acc[16];
+    acc[0] = a01.x; acc[1] = a01.y;
+    acc[2] = a32.y; acc[3] = a32.x;
+    acc[4] = a45.x; acc[5] = a45.y;
+    acc[6] = a76.y; acc[7] = a76.x;
+    acc[8] = a89.x; acc[9] = a89.y;
+    acc[10] = aE.x; acc[11] = aE.y;
+#pragma unroll
+    for (int k = 12; k < 16; k++) acc[k] = 0.0f;
     const float rs = warp_reduce_scatter16(acc);
     if ((lane & 1) == 0 && (lane >> 1) < K) sred[wid][lane >> 1] = rs;
     __syncthreads();
