@@ -253,14 +253,21 @@ k_bounds2d_vjp(const double* __restrict__ w, const double* __restrict__ wf, cons
     __syncthreads();
     // the same separable tables (and arithmetic) as the forward FP64 kernel, so the
     // winners of every min / max are those of the forward pass
-    for (int idx = tid; idx < NST * NX; idx += NT) {
-        const int i = idx / NX, j = idx % NX;
-        const AdjPrim& s = sP[i];
-        const double dx = sux[j] - s.U[0], dy = suy[j] - s.U[1];
-        const double ex = s.A * exp(-(dx * dx) / (2.0 * s.th));
-        sEx[i][j] = ex;
-        sExc[i][j] = s.C * ex;
-        sEy[i][j] = exp(-(dy * dy) / (2.0 * s.th));
+    {
+        constexpr int SEG = NX < 16 ? NX : 16, NSG = NX / SEG;
+        const double hx = (sbox[1] - sbox[0]) / (NX - 1), hy = (sbox[3] - sbox[2]) / (NX - 1);
+        for (int task = tid; task < NST * 2 * NSG; task += NT) {
+            const int i = task / (2 * NSG), axis = (task / NSG) & 1, jb = (task % NSG) * SEG;
+            const AdjPrim& s = sP[i];
+            if (axis == 0)
+                kbl_gauss_segment(s.A, s.U[0], s.th, sbox[0], hx, NX, jb, jb + SEG, [&](int j, double v) {
+                    sEx[i][j] = v;
+                    sExc[i][j] = s.C * v;
+                });
+            else
+                kbl_gauss_segment(1.0, s.U[1], s.th, sbox[2], hy, NX, jb, jb + SEG,
+                                  [&](int j, double v) { sEy[i][j] = v; });
+        }
     }
     const double rm = 1.0 - ph.r_fac, rp = 1.0 + ph.r_fac;
     const double Lx = sbox[1] - sbox[0], Ly = sbox[3] - sbox[2];

@@ -201,7 +201,7 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
     __shared__ StatePrim sP[NST];
     __shared__ double sEx[CH][NX], sExc[CH][NX], sEy[CH][NX];
     __shared__ double sux[NX], suy[NX], swx[NX], swy[NX];
-    __shared__ double sbox[4];
+    __shared__ double sbox[4], sgh[2];
     __shared__ int sbad;
     __shared__ double sred[NW * 12];
 
@@ -230,10 +230,11 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
     }
     __syncthreads();
     const int nu = ph.nu[0];   // nodes per axis; tile nodes j >= nu sit on the box end with weight 0
+    if (tid < 2) sgh[tid] = (sbox[2 * tid + 1] - sbox[2 * tid]) / (nu - 1);
+    __syncthreads();
     for (int j = tid; j < 2 * NX; j += NT) {
         const int d = j / NX, jj = j % NX;
-        const double lo = sbox[2 * d], hi = sbox[2 * d + 1];
-        const double h = (hi - lo) / (nu - 1);
+        const double lo = sbox[2 * d], h = sgh[d];
         const double u = lo + min(jj, nu - 1) * h;
         const double wq = kbl_qweight(ph, jj, nu) * h;
         if (d == 0) { sux[jj] = u; swx[jj] = wq; }
@@ -251,14 +252,19 @@ k_bounds2d_f64(const double* __restrict__ w, const double* __restrict__ wf, Mesh
     for (int c0 = 0; c0 < NST; c0 += CH) {
         const int nc = min(CH, NST - c0);
         __syncthreads();
-        for (int idx = tid; idx < nc * NX; idx += NT) {
-            const int i = idx / NX, j = idx % NX;
+        // row tables by segments of SEG nodes (product recurrence, a few exponentials per segment)
+        constexpr int SEG = NX < 16 ? NX : 16, NSG = NX / SEG;
+        for (int task = tid; task < nc * 2 * NSG; task += NT) {
+            const int i = task / (2 * NSG), axis = (task / NSG) & 1, jb = (task % NSG) * SEG;
             const StatePrim& s = sP[c0 + i];
-            const double dx = sux[j] - s.U[0], dy = suy[j] - s.U[1];
-            const double ex = s.A * exp(-(dx * dx) / (2.0 * s.th));
-            sEx[i][j] = ex;
-            sExc[i][j] = s.C * ex;
-            sEy[i][j] = exp(-(dy * dy) / (2.0 * s.th));
+            if (axis == 0)
+                kbl_gauss_segment(s.A, s.U[0], s.th, sbox[0], sgh[0], nu, jb, jb + SEG, [&](int j, double v) {
+                    sEx[i][j] = v;
+                    sExc[i][j] = s.C * v;
+                });
+            else
+                kbl_gauss_segment(1.0, s.U[1], s.th, sbox[2], sgh[1], nu, jb, jb + SEG,
+                                  [&](int j, double v) { sEy[i][j] = v; });
         }
         __syncthreads();
         for (int i = 0; i < nc; i++) {

@@ -103,6 +103,51 @@ __device__ __forceinline__ double kbl_qweight(const Phys& ph, int j, int nu)
     return (j == 0 || j == nu - 1) ? 0.5 : 1.0;
 }
 
+// One segment [jb, je) of a Maxwellian factor on an equispaced velocity axis, FP64:
+//   emit(j, scale exp(-(u_j - U)^2 / (2 theta))),  u_j = lo + j h for j < nu (the nodes j >= nu
+//   of a padded tile repeat the last node),
+// by a product recurrence instead of one exponential per node: with d_j = u_j - U,
+//   E(j + 1) = E(j) R(j),  R(j + 1) = R(j) Q,  R(j) = exp(-h (2 d_j + h) / (2 theta)),
+//   Q = exp(-h^2 / theta),
+// and its mirror image to the left.  It starts at the segment node nearest U, so every ratio is
+// at most 1 (up to rounding): values only shrink, an underflow to 0 is harmless and nothing
+// overflows.  Each step adds a few ulp; over a 16-node segment the relative error stays
+// below 1e-13.  Callers that must agree bit for bit (the forward bounds and their adjoint)
+// call it with the same arguments.
+template <typename Emit>
+__device__ __forceinline__ void kbl_gauss_segment(double scale, double U, double th, double lo, double h, int nu,
+                                                  int jb, int je, Emit emit)
+{
+    const double i2t = 0.5 / th;
+    const int jr = min(je, nu);   // real nodes of the segment: [jb, jr)
+    if (jr > jb) {
+        int j0 = (int)rint((U - lo) / h);
+        j0 = max(jb, min(jr - 1, j0));
+        const double d0 = fma((double)j0, h, lo) - U;
+        const double e0 = scale * exp(-(d0 * d0) * i2t);
+        const double q = exp(-2.0 * (h * h) * i2t);
+        emit(j0, e0);
+        double e = e0, r = exp(-h * (2.0 * d0 + h) * i2t);
+        for (int j = j0 + 1; j < jr; j++) {
+            e *= r;
+            r *= q;
+            emit(j, e);
+        }
+        e = e0;
+        r = exp(-h * (h - 2.0 * d0) * i2t);
+        for (int j = j0 - 1; j >= jb; j--) {
+            e *= r;
+            r *= q;
+            emit(j, e);
+        }
+    }
+    if (je > jr) {   // padding: the last real node
+        const double d = fma((double)(nu - 1), h, lo) - U;
+        const double ep = scale * exp(-(d * d) * i2t);
+        for (int j = max(jb, jr); j < je; j++) emit(j, ep);
+    }
+}
+
 // Tile size (velocity nodes per axis) of the 2D bounds kernels that holds an axis of nu nodes.
 __host__ __device__ constexpr int kbl_tile_nx(int nu) { return nu <= 8 ? 8 : nu <= 16 ? 16 : nu <= 32 ? 32 : 64; }
 
