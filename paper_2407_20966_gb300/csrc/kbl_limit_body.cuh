@@ -129,8 +129,11 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     }
     __syncthreads();
     if (live) {
+        // FP32 differences of the truncated values (integer-pipe truncation, one FP32 subtraction):
+        // each is within 2^-23 (|w| + |mean|) + 2^-24 |w - mean| of the exact deviation, which
+        // the face allowance below covers
 #pragma unroll
-        for (int v = 0; v < NV; v++) sdev[el][v][nd] = f32_trunc(sw[el][v][nd] - smean[el][v]);
+        for (int v = 0; v < NV; v++) sdev[el][v][nd] = f32_trunc(sw[el][v][nd]) - f32_trunc(smean[el][v]);
     }
     __syncthreads();
     for (int t = tid; t < EPB * NFP; t += NT) {
@@ -161,7 +164,9 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             fmn = fminf(fmn, sfdev[ell][v][fp]);
         }
         const double M = fmax(dmaxn, -dminn);
-        const double err = 1e-6 * sLam * M + 1e-37;
+        // FP32 face interpolation (1e-6 of Lambda M) and the truncated node deviations
+        // (at most 2^-23 (2 |mean| + M) + 2^-24 M each, below 2.4e-7 (|mean| + M); 5e-7 with margin)
+        const double err = sLam * (1e-6 * M + 5e-7 * (fabs(mean) + M)) + 1e-37;
         const double delta = 1e-14 * (fabs(mean) + fmax(fabs(mean + dmaxn), fabs(mean + dminn))) * sLam;
         const double up = fmax(dmaxn, (double)fmx + err) + delta;    // every value of V is below mean + up
         const double dn = fmax(-dminn, -(double)fmn + err) + delta;  // and above mean - dn
@@ -194,8 +199,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             if (!(rlo > 0.0)) {
                 fast = 0;
             } else {
-                const double plb = (ph.gamma - 1.0) * (elo - 0.5 * mm / rlo);
-                if (!(plb >= 2.0 * ph.p_floor + 1e-13 * (eabs + mm / rlo))) fast = 0;
+                // (gamma - 1)(elo - mm / (2 rlo)) >= 2 p_floor + 1e-13 (eabs + mm / rlo), multiplied
+                // through by rlo > 0: no FP64 division; its few ulp of rounding sit far inside 1e-13
+                const double lhs = (ph.gamma - 1.0) * fma(elo, rlo, -0.5 * mm);
+                if (!(lhs >= 2.0 * ph.p_floor * rlo + 1e-13 * fma(eabs, rlo, mm))) fast = 0;
             }
         }
         sfast[ell] = fast;
