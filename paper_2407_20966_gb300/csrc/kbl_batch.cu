@@ -145,8 +145,10 @@ __device__ __forceinline__ void bounds_item(void* smraw, const BatchDev& bd, con
         bounds2d_f32_element<N, NX_B, TYSEL>(sm, w + pd.woff, wf + pd.wfoff, m, e, ph, bnd + pd.bndoff, flags);
 }
 
+// at least 7 resident blocks: the shared memory of a P4 work item allows 7, and without the
+// hint the unrolled envelope loop takes enough registers to allow only 6
 template <int TYSEL>
-__global__ void __launch_bounds__(B2f32<NX_B, TYSEL>::NT)
+__global__ void __launch_bounds__(B2f32<NX_B, TYSEL>::NT, 7)
 k_batch_bounds(BatchDev bd, const WorkItem* __restrict__ items, int n_items, unsigned* counter, Phys ph,
                const double* w, const double* wf, double* bnd, DevFlags* flags)
 {
