@@ -196,7 +196,8 @@ __device__ __forceinline__ void rhs_item(void* smraw, const BatchDev& bd, const 
                                     min(EPB, e_end - eb), flux);
 }
 
-__global__ void __launch_bounds__(NTB) k_batch_rhs(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
+// 4 resident blocks: without the hint the switch over orders inflates the register count
+__global__ void __launch_bounds__(NTB, 4) k_batch_rhs(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
                                                    unsigned* counter, BatchOps ops, double gamma, int flux,
                                                    const double* w, const double* wf, double* R)
 {
@@ -240,7 +241,8 @@ __device__ __forceinline__ void stage_item(void* smraw, const ProbDesc& pd, cons
                                             min(EPB, e_end - eb));
 }
 
-__global__ void __launch_bounds__(NTB) k_batch_stage(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
+// 4 resident blocks: without the hint the switch over orders inflates the register count
+__global__ void __launch_bounds__(NTB, 4) k_batch_stage(BatchDev bd, const WorkItem* __restrict__ items, int n_items,
                                                      unsigned* counter, BatchOps ops, Phys ph, int stage,
                                                      const double* wn, const double* ws, const double* R,
                                                      const double* bnd, const double* dt, double* wout, DevFlags* flags)
