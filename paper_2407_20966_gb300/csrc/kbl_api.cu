@@ -153,6 +153,13 @@ void build_ops(int p, FrOps& o)
     o.winv1 = 1.0 / s1;
     o.winv2 = 1.0 / s2;
     o.lam = std::max(am, ap);
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) o.Df[i][j] = (float)o.D[i][j];
+        o.glf[i] = (float)o.gl[i];
+        o.grf[i] = (float)o.gr[i];
+        o.lmf[i] = (float)o.lm[i];
+        o.lpf[i] = (float)o.lp[i];
+    }
 }
 
 kbl_status fail(kbl_ctx* c, kbl_status st, const char* msg)

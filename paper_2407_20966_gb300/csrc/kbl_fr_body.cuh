@@ -52,17 +52,20 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
     auto& slp = sm.slp;
     const int tid = threadIdx.x;
     __syncthreads();
-    for (int i = tid; i < N * N; i += NT) sD[i / N][i % N] = (T)ops.D[i / N][i % N];
+    // FP32: the host-rounded copies (no FP64 conversion instructions here)
+    constexpr bool F32 = sizeof(T) == sizeof(float);
+    for (int i = tid; i < N * N; i += NT)
+        sD[i / N][i % N] = F32 ? (T)ops.Df[i / N][i % N] : (T)ops.D[i / N][i % N];
     if (tid < N) {
-        sgl[tid] = (T)ops.gl[tid];
-        sgr[tid] = (T)ops.gr[tid];
-        slm[tid] = (T)ops.lm[tid];
-        slp[tid] = (T)ops.lp[tid];
+        sgl[tid] = F32 ? (T)ops.glf[tid] : (T)ops.gl[tid];
+        sgr[tid] = F32 ? (T)ops.grf[tid] : (T)ops.gr[tid];
+        slm[tid] = F32 ? (T)ops.lmf[tid] : (T)ops.lm[tid];
+        slp[tid] = F32 ? (T)ops.lpf[tid] : (T)ops.lp[tid];
     }
     const int el = tid / NS, nd = tid % NS;
     const int e = e0 + el;
     const bool node_thread = el < EPB && el < nmax && e < m.E;
-    const T gamma = from_f64<T>(gamma_d), gm1 = from_f64<T>(gamma_d - 1.0);
+    const T gamma = from_f64<T>(gamma_d), gm1 = F32 ? gamma - T(1) : from_f64<T>(gamma_d - 1.0);
     if (node_thread) {
         T q[NV];
 #pragma unroll

@@ -26,6 +26,8 @@ struct FrOps {
     // ends of sum_i |l_i(+-1)| (a face value lies within Lambda max_i |w_i - mean| of the mean)
     double wm2[KBL_NMAX * KBL_NMAX];
     double winv1, winv2, lam;
+    // FP32 copies (rounded on the host) of the residual's operators, for the FP32 arithmetic
+    float Df[KBL_NMAX][KBL_NMAX], glf[KBL_NMAX], grf[KBL_NMAX], lmf[KBL_NMAX], lpf[KBL_NMAX];
 };
 
 // Physical and method constants, passed by value.
