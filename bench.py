@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2070.0
 # The envelope loop of the FP32 bounds kernel needs, per (stencil state, velocity node),
 # 2 products (g = Ex Ey and C g) and 4 comparisons (min and max of both): 6 FP32 lane-ops.
 # Its roofline is the measured rate of exactly that instruction mix in a register-only loop
-# (csrc/peaks/kbl_fp32_peaks.cu, `bench.py --peaks`; profiles/fp32_pipe_peaks.md): 155.5
+# (csrc/peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
 # lane-ops per clock per SM (packed multiplies and three-input min/max issue to two pipes
 # that overlap only in part), times 152 SMs and the 2070 MHz maximum clock.
 OPS_PER_STATE_NODE = 6.0
