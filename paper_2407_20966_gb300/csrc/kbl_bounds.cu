@@ -23,17 +23,20 @@
 //
 // 2D kernels use the separable form of the Maxwellian on the tensor grid:
 // g_i(ux, uy) = (A_i exp(-(ux-Ux_i)^2/(2 theta_i))) (exp(-(uy-Uy_i)^2/(2 theta_i))),
-// so a block builds per-state row tables Ex, C*Ex, Ey (|S| (nx + ny) exps) and
-// every (state, node) pair then costs two multiplies and four min/max.
+// so a block builds per-state row tables Ex, C*Ex, Ey and every (state, node)
+// pair then costs two multiplies and four min/max.
 //
 // FP64 kernels: the min/max run on the integer pipe as unsigned 64-bit
 // compares of the bit patterns (all values are >= +0, where integer order is
-// value order), because the GB300 FP64 pipe is ~1/76 of FP32.
+// value order), because the GB300 FP64 pipe is ~1/76 of FP32; the row tables
+// come from a product recurrence (kbl_gauss_segment), a few exponentials per
+// segment of 16 nodes.
 // FP32 kernels: FP64 only for X = rho E - |m|^2/2 (rho P / (gamma-1)) with its
 // positivity test and for assembling the final bounds; velocities are taken
 // relative to the box centre inside the exponentials; pairs of states share
-// one packed multiply (__fmul2_rn) and one three-input min/max; per-warp
-// partial sums are combined with error-free (TwoSum) compensation.
+// one packed multiply (__fmul2_rn) and one three-input min/max; the partial
+// sums of the threads meet in a pairwise tree (the 1D kernel keeps a
+// compensated block sum).
 #include <algorithm>
 #include <cfloat>
 
