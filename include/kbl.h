@@ -136,6 +136,13 @@ kbl_status kbl_mesh_upload(kbl_ctx* ctx, int n_elem, const int32_t* nbr_host,
  * 4 D[p+1][p+1] with D[i][m] = l_m'(x_i), 5 g_L'(x_i)[p+1], 6 g_R'(x_i)[p+1]. */
 kbl_status kbl_get_operator(const kbl_ctx* ctx, int which, double* host_out, int n);
 
+/* The velocity quadrature weights the kernels apply on one axis of nu points, in
+ * units of the grid spacing (Sec. 3.7, Sec. 5): quadrature 0 the trapezoidal rule,
+ * 1 Romberg (see kbl_config.quadrature).  Host only, no context, no device call:
+ * for checking.  host_out[nu]; KBL_EINVAL for nu < 2, an unknown rule or, with
+ * Romberg, nu - 1 odd. */
+kbl_status kbl_velocity_weights(int nu, int quadrature, double* host_out);
+
 /* Interior values at the face points: wf = interpolation of w (Sec. 2.3). */
 kbl_status kbl_traces(kbl_ctx* ctx, const double* w, double* wf);
 

@@ -345,6 +345,20 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     return KBL_OK;
 }
 
+kbl_status kbl_velocity_weights(int nu, int quadrature, double* host_out)
+{
+    if (!host_out || nu < 2 || (quadrature != 0 && quadrature != 1)) return KBL_EINVAL;
+    if (quadrature == 1) {
+        if ((nu - 1) % 2 != 0) return KBL_EINVAL;
+        std::vector<double> q;
+        romberg_weights(nu, q);
+        std::copy(q.begin(), q.end(), host_out);
+    } else {
+        for (int j = 0; j < nu; j++) host_out[j] = (j == 0 || j == nu - 1) ? 0.5 : 1.0;
+    }
+    return KBL_OK;
+}
+
 kbl_status kbl_destroy(kbl_ctx* c)
 {
     if (!c) return KBL_EINVAL;

@@ -60,6 +60,7 @@ _SIGS = {
     "kbl_nstencil": (C.c_int, [_P]),
     "kbl_mesh_upload": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "kbl_get_operator": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "kbl_velocity_weights": (C.c_int, [C.c_int, C.c_int, _P]),
     "kbl_traces": (C.c_int, [_P, _P, _P]),
     "kbl_gather_stencil": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P]),
     "kbl_bounds": (C.c_int, [_P, _P, _P, _P]),
@@ -328,6 +329,16 @@ def _dev_any(t, dtype_name, name):
     if str(t.dtype) != dtype_name:
         raise TypeError(f"{name} must be {dtype_name}")
     return C.c_void_p(t.data_ptr())
+
+
+def velocity_weights(nu, quadrature=0):
+    """The library's velocity quadrature weights on an axis of nu points, in units of the grid
+    spacing (kbl_velocity_weights; host only)."""
+    out = np.zeros(int(nu))
+    st = load().kbl_velocity_weights(int(nu), int(quadrature), out.ctypes.data_as(C.c_void_p))
+    if st != OK:
+        raise KblError(st, "velocity_weights")
+    return out
 
 
 def bounds_noalloc(cfg: KblConfig, nbr, bc, w, bnd, stream=None):

@@ -83,3 +83,22 @@ def test_romberg_needs_an_even_number_of_intervals(orc):
     S = inputs.random_states(np.random.default_rng(1), 3, 1)
     with pytest.raises(Exception):
         orc.bounds_stencil(cfg, S)
+
+
+@pytest.mark.parametrize("n", [3, 5, 9, 17, 33, 63, 65, 97, 2049])
+def test_library_weights_equal_the_checkers(orc, n):
+    """The weights the kernels apply (library host code, kbl_velocity_weights) against the
+    checker's independent construction: Romberg to rounding, the trapezoidal rule exactly.
+    Host only, so this runs without a GPU."""
+    from paper_2407_20966_gb300 import kbl
+    np.testing.assert_allclose(kbl.velocity_weights(n, 1), orc.romberg_weights(n), rtol=1e-13, atol=1e-15)
+    trap = np.ones(n)
+    trap[0] = trap[-1] = 0.5
+    np.testing.assert_array_equal(kbl.velocity_weights(n, 0), trap)
+
+
+def test_library_weights_reject_bad_arguments():
+    from paper_2407_20966_gb300 import kbl
+    for nu, q in ((1, 0), (64, 1), (33, 2)):
+        with pytest.raises(kbl.KblError):
+            kbl.velocity_weights(nu, q)
