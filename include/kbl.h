@@ -158,6 +158,17 @@ kbl_status kbl_gather_stencil(kbl_ctx* ctx, const double* w, const double* wf,
  * then rho_min <- max(rho_min, rho_floor). */
 kbl_status kbl_bounds(kbl_ctx* ctx, const double* w, const double* wf, double* bnd);
 
+/* The same bounds for stencils the caller assembles (Eq. 29-46 take any set of
+ * states): for element families whose traces live outside this library --
+ * triangles with their own solution and face points, unstructured meshes.
+ * S: DEVICE, conservative states S[n_elem][n_states][4] (element e's stencil is
+ * S[e][0..n_states-1]); bnd: DEVICE, bnd[2][4][n_elem] as kbl_bounds writes it.
+ * Uses the context's configuration (velocity grid, k, r_fac, floors, quadrature,
+ * precision); needs no mesh.  2D only, 1 <= n_states <= 64, else KBL_EINVAL.
+ * Asynchronous on the context's stream; a non-physical state gives NaN bounds
+ * for its element and raises the non-physical flag. */
+kbl_status kbl_bounds_stencil(kbl_ctx* ctx, int n_elem, int n_states, const double* S, double* bnd);
+
 /* FR residual R = -div F with the configured interface flux (Rusanov,
  * assumption (iv) of Sec. 4, or HLLC) and the g_DG correction; wf must hold the
  * traces of w. */

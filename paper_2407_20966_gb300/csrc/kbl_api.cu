@@ -475,6 +475,15 @@ kbl_status kbl_bounds(kbl_ctx* c, const double* w, const double* wf, double* bnd
     return after_launch(c, launch_bounds(c, w, wf, bnd, c->stream), "bounds");
 }
 
+kbl_status kbl_bounds_stencil(kbl_ctx* c, int n_elem, int n_states, const double* S, double* bnd)
+{
+    if (!c) return KBL_EINVAL;
+    if (c->cfg.dim != 2) return fail(c, KBL_EINVAL, "explicit stencils are 2D");
+    if (n_elem < 0 || n_states < 1 || n_states > 64) return fail(c, KBL_EINVAL, "n_elem >= 0, 1 <= n_states <= 64");
+    if (n_elem > 0 && (!S || !bnd)) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_bounds_stencil(c, n_elem, n_states, S, bnd, c->stream), "bounds_stencil");
+}
+
 kbl_status kbl_rhs(kbl_ctx* c, const double* w, const double* wf, double* R)
 {
     if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");

@@ -166,10 +166,11 @@ __device__ __forceinline__ float warp_reduce_scatter16(const float (&v)[16])
     return s[0] + __shfl_xor_sync(0xffffffffu, s[0], 1);
 }
 
-template <int N, int NX, int TYSEL>
-struct Bounds2dF32Smem {
+// Shared memory of one element's FP32 bounds for a stencil of NST_ states.
+template <int NST_, int NX, int TYSEL>
+struct Bounds2dF32SmemS {
     using SH = B2f32<NX, TYSEL>;
-    static constexpr int NS = N * N, NFP = 4 * N, NST = NS + 2 * NFP, NV = 4;
+    static constexpr int NST = NST_, NV = 4;
     static constexpr int NSTP = (NST + 1) & ~1;         // padded to pairs (the last state repeated)
     static constexpr int NPAIR = NSTP / 2;
     static constexpr int TX = SH::TX, TY = SH::TY, TPX = SH::TPX, NT = SH::NT;
@@ -203,20 +204,25 @@ struct Bounds2dF32Smem {
 
 };
 
-// Bounds of element e of one mesh (one block of SM::NT threads).  The block may
-// call it for several elements in a row: it starts with a barrier.  PAD: the grid has
-// ph.nu[0] <= NX nodes per axis or a weight table (else exactly NX nodes, trapezoidal
-// rule, with the node count and the weights folded into the code).
-template <int N, int NX, int TYSEL, bool PAD = false>
-__device__ __forceinline__ void bounds2d_f32_element(
-    Bounds2dF32Smem<N, NX, TYSEL>& sm, const double* __restrict__ w, const double* __restrict__ wf,
-    const MeshDev& m, int e, const Phys& ph, double* __restrict__ bnd, DevFlags* flags)
+// The FR stencil of an order-N element: N^2 solution points, 4N own and 4N exterior face points.
+template <int N, int NX, int TYSEL>
+using Bounds2dF32Smem = Bounds2dF32SmemS<N * N + 8 * N, NX, TYSEL>;
+
+// Bounds of one element from a stencil of NST states (one block of SM::NT threads):
+// gather(sS) fills sS[NST][4] with the stencil's conservative states; the bounds go to
+// column e of bnd[2][4][E].  The block may call it for several elements in a row: it
+// starts with a barrier.  PAD: the grid has ph.nu[0] <= NX nodes per axis or a weight table
+// (else exactly NX nodes, trapezoidal rule, with the node count and the weights folded
+// into the code).
+template <int NST_, int NX, int TYSEL, bool PAD, typename Gather>
+__device__ __forceinline__ void bounds2d_f32_core(Bounds2dF32SmemS<NST_, NX, TYSEL>& sm, Gather gather, int E, int e,
+                                                  const Phys& ph, double* __restrict__ bnd, DevFlags* flags)
 {
-    using SM = Bounds2dF32Smem<N, NX, TYSEL>;
+    using SM = Bounds2dF32SmemS<NST_, NX, TYSEL>;
     using SH = typename SM::SH;
-    constexpr int NS = SM::NS, NFP = SM::NFP, NST = SM::NST, NV = SM::NV, NSTP = SM::NSTP, NPAIR = SM::NPAIR;
+    constexpr int NST = SM::NST, NV = SM::NV, NSTP = SM::NSTP, NPAIR = SM::NPAIR;
     constexpr int TX = SM::TX, TY = SM::TY, TPX = SM::TPX, NT = SM::NT, NW = SM::NW, K = SM::K;
-    (void)NS; (void)NFP; (void)TY;
+    (void)TY;
     auto& sS = sm.u.pre.sS; auto& sUx = sm.u.pre.sUx; auto& sUy = sm.u.pre.sUy; auto& sSc = sm.u.pre.sSc;
     auto& sA = sm.u.pre.sA; auto& sC = sm.u.pre.sC; auto& sEx = sm.u.tab.sEx; auto& sExc = sm.u.tab.sExc;
     auto& sEy = sm.u.tab.sEy; auto& srx = sm.srx;
@@ -226,7 +232,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __syncthreads();   // the block may reuse sm for consecutive elements
     if (tid == 0) sbad = 0;
-    gather_states_by_state<N, NT>(w, wf, m, e, sS);
+    gather(sS);
     __syncthreads();
 
     // 1. primitive state of each stencil node, box candidates
@@ -270,7 +276,7 @@ __device__ __forceinline__ void bounds2d_f32_element(
     __syncthreads();
     if (sbad) {   // block-uniform
         if (tid == 0) {
-            write_nan(bnd, m.E, e, NV);
+            write_nan(bnd, E, e, NV);
             atomicOr(&flags->nonphysical, 1);
         }
         return;
@@ -433,8 +439,20 @@ __device__ __forceinline__ void bounds2d_f32_element(
         }
         // val >= 0 (a sum of non-negative terms) or NaN: the order of the bit patterns decides
         if (v == 0 && !up && __double_as_longlong(val) < __double_as_longlong(ph.rho_floor)) val = ph.rho_floor;
-        bnd[((size_t)up * NV + v) * m.E + e] = val;
+        bnd[((size_t)up * NV + v) * E + e] = val;
     }
+}
+
+// Bounds of element e of an FR mesh (the stencil of Sec. 5: own solution and face points,
+// exterior face values).
+template <int N, int NX, int TYSEL, bool PAD = false>
+__device__ __forceinline__ void bounds2d_f32_element(
+    Bounds2dF32Smem<N, NX, TYSEL>& sm, const double* __restrict__ w, const double* __restrict__ wf,
+    const MeshDev& m, int e, const Phys& ph, double* __restrict__ bnd, DevFlags* flags)
+{
+    constexpr int NT = B2f32<NX, TYSEL>::NT;
+    bounds2d_f32_core<N * N + 8 * N, NX, TYSEL, PAD>(
+        sm, [&](double (*sS)[4]) { gather_states_by_state<N, NT>(w, wf, m, e, sS); }, m.E, e, ph, bnd, flags);
 }
 
 

@@ -60,6 +60,7 @@ _SIGS = {
     "kbl_nstencil": (C.c_int, [_P]),
     "kbl_mesh_upload": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "kbl_get_operator": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "kbl_bounds_stencil": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "kbl_velocity_weights": (C.c_int, [C.c_int, C.c_int, _P]),
     "kbl_traces": (C.c_int, [_P, _P, _P]),
     "kbl_gather_stencil": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P]),
@@ -209,6 +210,12 @@ class Context:
         self._check(self._lib.kbl_mesh_upload(self._h, E, pn, ph, bc.shape[0] if bc.size else 0, pb),
                     "mesh_upload")
         self.E = E
+
+    def bounds_stencil(self, S, bnd):
+        """Bounds of explicit stencils (kbl_bounds_stencil): S float64 [E][n_states][4] and
+        bnd float64 [2][4][E], CUDA tensors."""
+        E, n = int(S.shape[0]), int(S.shape[1])
+        self._check(self._lib.kbl_bounds_stencil(self._h, E, n, _dev(S, "S"), _dev(bnd, "bnd")), "bounds_stencil")
 
     def operator(self, which):
         n = (self.p + 1) ** 2 if which == OP_D else self.p + 1
