@@ -169,6 +169,20 @@ kbl_status kbl_bounds(kbl_ctx* ctx, const double* w, const double* wf, double* b
  * for its element and raises the non-physical flag. */
 kbl_status kbl_bounds_stencil(kbl_ctx* ctx, int n_elem, int n_states, const double* S, double* bnd);
 
+/* Limiting of node sets the caller assembles (Eq. 37-39, then Eq. 47-49), for element
+ * families whose operators live outside this library.  Per element e: ns solution values
+ * U[e][ns][nv] (DEVICE, limited in place) whose mean is sum W U / sum W with the positive
+ * weights W[ns] (HOST, copied), nf face values F[e][nf][nv] (DEVICE, read only: they
+ * enter the extremes over V and the pressure minimum; recompute them from the limited U,
+ * which for an interpolation with weights summing to one equals limiting them), bounds
+ * bnd[2][nv][n_elem] (DEVICE).  alpha (DEVICE, may be NULL) receives alpha_min and
+ * alpha_P as alpha[2][n_elem].  Uses the context's eps, eps reading, coupled or uncoupled
+ * form, gamma and p_floor; FP64 whatever the precision; needs no mesh.  1 <= ns <= 64,
+ * 0 <= nf <= 64, else KBL_EINVAL.  Asynchronous; the limited and re-limited counts add to
+ * the context's counters. */
+kbl_status kbl_limit_nodes(kbl_ctx* ctx, int n_elem, int ns, int nf, const double* W, double* U,
+                           const double* F, const double* bnd, double* alpha);
+
 /* FR residual R = -div F with the configured interface flux (Rusanov,
  * assumption (iv) of Sec. 4, or HLLC) and the g_DG correction; wf must hold the
  * traces of w. */

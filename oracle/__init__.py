@@ -79,6 +79,7 @@ def _load():
                 "orc_bounds": (C.c_int, [cfgp, meshp, d, d, d]),
                 "orc_rhs": (None, [cfgp, meshp, d, d, d]),
                 "orc_limit_element": (None, [cfgp, d, d, d, d, d]),
+                "orc_limit_nodes": (None, [cfgp, C.c_int, C.c_int, d, d, d, d, d, d]),
                 "orc_limit": (None, [cfgp, meshp, d, d, d]),
                 "orc_stage_combine": (None, [cfgp, meshp, C.c_int, d, d, d, C.c_double, d]),
                 "orc_dt": (C.c_double, [cfgp, meshp, d, C.c_double]),
@@ -306,6 +307,20 @@ def limit_element(cfg: Config, wel, wfel, wmin, wmax):
     wmax = np.ascontiguousarray(wmax, dtype=np.float64)
     a = np.zeros(2)
     _load().orc_limit_element(C.byref(cfg._c()), _dp(wel), _dp(wfel), _dp(wmin), _dp(wmax), _dp(a))
+    return wel, a
+
+
+def limit_nodes(cfg: Config, Wq, wel, wfel, wmin, wmax):
+    """Limit one element's node set: solution values wel[nv][ns] with mean weights Wq[ns], face
+    values wfel[nv][nf]; returns the limited solution values and (alpha, alpha_P)."""
+    Wq = np.ascontiguousarray(Wq, dtype=np.float64)
+    wel = np.array(wel, dtype=np.float64, order="C")
+    wfel = np.ascontiguousarray(wfel, dtype=np.float64)
+    wmin = np.ascontiguousarray(wmin, dtype=np.float64)
+    wmax = np.ascontiguousarray(wmax, dtype=np.float64)
+    a = np.zeros(2)
+    _load().orc_limit_nodes(C.byref(cfg._c()), wel.shape[1], wfel.shape[1], _dp(Wq), _dp(wel), _dp(wfel),
+                            _dp(wmin), _dp(wmax), _dp(a))
     return wel, a
 
 

@@ -602,9 +602,10 @@ void orc_rhs(const orc_cfg* c, const orc_mesh* m, const double* w, const double*
     free(W); free(F); free(J);
 }
 
-/* Limiting of one element, Sec. 3.4 and Sec. 3.8.
- *  mean   : positive-quadrature mean with Gauss-Legendre weights (Eq. 13 and
- *           assumption (iii)(a) of Sec. 4)
+/* Limiting of one element's node set, Sec. 3.4 and Sec. 3.8: ns solution values
+ * wel[nv][ns] with positive mean weights Wq[ns], nfp face values wfel[nv][nfp].
+ *  mean   : positive-quadrature mean sum Wq w / sum Wq (Eq. 13 and assumption
+ *           (iii)(a) of Sec. 4)
  *  alpha_i: Eq. 37 per component over V = solution points + face points,
  *           with the epsilon rule stated under it
  *  alpha  : alpha_min = min_i alpha_i (Eq. 39), w~ = mean + alpha (w - mean)
@@ -616,19 +617,16 @@ void orc_rhs(const orc_cfg* c, const orc_mesh* m, const double* w, const double*
  *           alpha_P = |(p_floor - P(mean)) / (P_min - P(mean))| (Eq. 49) and
  *           w~~ = mean + alpha_P (w~ - mean) (Eq. 48).  When P(mean) itself is
  *           not above p_floor, alpha_P is taken as 0. */
-void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
-                       const double* wmin, const double* wmax, double* alpha_out)
+void orc_limit_nodes(const orc_cfg* c, int ns, int nfp, const double* Wq, double* wel, const double* wfel,
+                     const double* wmin, const double* wmax, double* alpha_out)
 {
-    int d = c->dim, nv = orc_nv(c), ns = orc_ns(c), nfp = orc_nfp(c), n = c->p + 1;
-    double xg[16], wg[16];
-    orc_gauss_legendre(n, xg, wg);
+    int nv = orc_nv(c);
     double mean[4];
     for (int v = 0; v < nv; v++) {
         double s = 0.0, sw = 0.0;
         for (int nd = 0; nd < ns; nd++) {
-            double W = (d == 1) ? wg[nd] : wg[nd % n] * wg[nd / n];
-            s += W * wel[v * ns + nd];
-            sw += W;
+            s += Wq[nd] * wel[v * ns + nd];
+            sw += Wq[nd];
         }
         mean[v] = s / sw;
     }
@@ -688,6 +686,17 @@ void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
     }
     free(wt); free(wtf);
     if (alpha_out) { alpha_out[0] = alpha; alpha_out[1] = aP; }
+}
+
+/* The FR element: Gauss-Legendre weights (tensor products in 2D) for the mean. */
+void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
+                       const double* wmin, const double* wmax, double* alpha_out)
+{
+    int d = c->dim, ns = orc_ns(c), n = c->p + 1;
+    double xg[16], wg[16], Wq[256];
+    orc_gauss_legendre(n, xg, wg);
+    for (int nd = 0; nd < ns; nd++) Wq[nd] = (d == 1) ? wg[nd] : wg[nd % n] * wg[nd / n];
+    orc_limit_nodes(c, ns, orc_nfp(c), Wq, wel, wfel, wmin, wmax, alpha_out);
 }
 
 void orc_limit(const orc_cfg* c, const orc_mesh* m, double* w, const double* bnd,

@@ -114,6 +114,8 @@ void orc_rhs(const orc_cfg* c, const orc_mesh* m, const double* w,
 /* Limit one element: wel[nv][Ns] in place; wfel[nv][Nfp] are its unlimited
  * face values.  alpha_out[0] = alpha_min (Eq. 39), alpha_out[1] = alpha_P
  * (Eq. 49, 1 when the pressure step is not taken). */
+void orc_limit_nodes(const orc_cfg* c, int ns, int nfp, const double* Wq, double* wel, const double* wfel,
+                     const double* wmin, const double* wmax, double* alpha_out);
 void orc_limit_element(const orc_cfg* c, double* wel, const double* wfel,
                        const double* wmin, const double* wmax, double* alpha_out);
 void orc_limit(const orc_cfg* c, const orc_mesh* m, double* w, const double* bnd,

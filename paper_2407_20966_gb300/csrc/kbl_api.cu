@@ -484,6 +484,18 @@ kbl_status kbl_bounds_stencil(kbl_ctx* c, int n_elem, int n_states, const double
     return after_launch(c, launch_bounds_stencil(c, n_elem, n_states, S, bnd, c->stream), "bounds_stencil");
 }
 
+kbl_status kbl_limit_nodes(kbl_ctx* c, int n_elem, int ns, int nf, const double* W, double* U, const double* F,
+                           const double* bnd, double* alpha)
+{
+    if (!c) return KBL_EINVAL;
+    if (n_elem < 0 || ns < 1 || ns > 64 || nf < 0 || nf > 64) return fail(c, KBL_EINVAL, "1 <= ns <= 64, 0 <= nf <= 64");
+    if (!W) return fail(c, KBL_EINVAL, "null weights");
+    for (int n = 0; n < ns; n++)
+        if (!(W[n] > 0.0) || !(W[n] < INFINITY)) return fail(c, KBL_EINVAL, "mean weights must be positive");
+    if (n_elem > 0 && (!U || !bnd || (nf > 0 && !F))) return fail(c, KBL_EINVAL, "null array");
+    return after_launch(c, launch_limit_nodes(c, n_elem, ns, nf, W, U, F, bnd, alpha, c->stream), "limit_nodes");
+}
+
 kbl_status kbl_rhs(kbl_ctx* c, const double* w, const double* wf, double* R)
 {
     if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");

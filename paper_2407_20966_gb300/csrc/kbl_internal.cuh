@@ -226,6 +226,9 @@ int launch_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int
 int launch_time_advance(const kbl_ctx* c, cudaStream_t s);
 int launch_bounds(const kbl_ctx* c, const double* w, const double* wf, double* bnd,
                   cudaStream_t s);
+// limiting of explicit node sets U[E][ns][nv] (in place) with faces F[E][nf][nv], W[ns] host
+int launch_limit_nodes(const kbl_ctx* c, int E, int ns, int nf, const double* W, double* U, const double* F,
+                       const double* bnd, double* alpha, cudaStream_t s);
 // bounds of explicit stencils S[E][nst][4] (2D, 1 <= nst <= 64); -1 for other shapes
 int launch_bounds_stencil(const kbl_ctx* c, int E, int nst, const double* S, double* bnd, cudaStream_t s);
 // mode 0: RK stage s fused with the limiter; mode 1: limiter only (ws = w in place)

@@ -50,7 +50,107 @@ int run_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const dou
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Limiting of caller-assembled node sets (Eq. 37-39, Eq. 47-49), FP64, one thread per
+// element: solution values U[E][ns][nv] (limited in place) with positive mean weights
+// W[ns], face values F[E][nf][nv] (read only: they enter the extremes over V and the
+// pressure minimum), bounds bnd[2][nv][E].  The operations and their order follow the FR
+// limiter's exact path.
+// ---------------------------------------------------------------------------
+struct NodeWeights {
+    double w[64];
+};
+
+template <int NV>
+__global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, NodeWeights W, double* __restrict__ U,
+                                                     const double* __restrict__ F, const double* __restrict__ bnd,
+                                                     double* __restrict__ alpha_out, Phys ph, DevFlags* flags)
+{
+    constexpr int DIM = NV - 2;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    double* u = U + (size_t)e * ns * NV;
+    const double* f = F + (size_t)e * nf * NV;
+    double mean[NV], av[NV], alpha = 1.0;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        double s = 0.0, sw = 0.0;
+        for (int n = 0; n < ns; n++) {
+            s += W.w[n] * u[n * NV + v];
+            sw += W.w[n];
+        }
+        mean[v] = s / sw;
+        double mx = u[v], mn = u[v];
+        for (int n = 1; n < ns; n++) {
+            mx = fmax(mx, u[n * NV + v]);
+            mn = fmin(mn, u[n * NV + v]);
+        }
+        for (int n = 0; n < nf; n++) {
+            mx = fmax(mx, f[n * NV + v]);
+            mn = fmin(mn, f[n * NV + v]);
+        }
+        const double dmax = mx - mean[v], dmin = mn - mean[v];
+        const double lo = bnd[(size_t)v * E + e], hi = bnd[((size_t)NV + v) * E + e];
+        double a;
+        if (fabs(dmin) < ph.eps || fabs(dmax) < ph.eps) {
+            a = ph.eps_rule ? 1.0 : 0.0;
+        } else {
+            a = 1.0;
+            const double t1 = fabs((hi - mean[v]) / dmax), t2 = fabs((lo - mean[v]) / dmin);
+            if (t1 < a) a = t1;
+            if (t2 < a) a = t2;
+        }
+        av[v] = a;
+        if (a < alpha) alpha = a;
+    }
+    if (!ph.uncoupled)
+#pragma unroll
+        for (int v = 0; v < NV; v++) av[v] = alpha;
+    // P_min over V of the limited values
+    const double gm1 = ph.gamma - 1.0;
+    double pmin = INFINITY;
+    for (int n = 0; n < ns + nf; n++) {
+        const double* x = n < ns ? u + n * NV : f + (n - ns) * NV;
+        double q[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) q[v] = mean[v] + av[v] * (x[v] - mean[v]);
+        pmin = fmin(pmin, kbl_pressure<DIM>(q, gm1));
+    }
+    double aP = 1.0;
+    const bool relimit = pmin < ph.p_floor;
+    if (relimit) {
+        const double Pbar = kbl_pressure<DIM>(mean, gm1);
+        aP = (Pbar > ph.p_floor) ? fabs((ph.p_floor - Pbar) / (pmin - Pbar)) : 0.0;
+    }
+    for (int n = 0; n < ns; n++)
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const double wt = mean[v] + av[v] * (u[n * NV + v] - mean[v]);
+            u[n * NV + v] = relimit ? mean[v] + aP * (wt - mean[v]) : wt;
+        }
+    if (alpha_out) {
+        alpha_out[e] = alpha;
+        alpha_out[(size_t)E + e] = aP;
+    }
+    if (alpha < 1.0) atomicAdd(&flags->limited, 1ull);
+    if (relimit) atomicAdd(&flags->prelimit, 1ull);
+}
+
 }  // namespace
+
+int launch_limit_nodes(const kbl_ctx* c, int E, int ns, int nf, const double* W, double* U, const double* F,
+                       const double* bnd, double* alpha, cudaStream_t s)
+{
+    if (E == 0) return 0;
+    NodeWeights nw;
+    for (int n = 0; n < 64; n++) nw.w[n] = n < ns ? W[n] : 0.0;
+    const unsigned grid = (unsigned)((E + 127) / 128);
+    if (c->cfg.dim == 2)
+        k_limit_nodes<4><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags);
+    else
+        k_limit_nodes<3><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags);
+    return 1;
+}
 
 int launch_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const double* ws,
                  const double* R, const double* bnd, const double* dt, double* wout, double* alpha,

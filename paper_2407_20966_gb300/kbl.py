@@ -61,6 +61,7 @@ _SIGS = {
     "kbl_mesh_upload": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "kbl_get_operator": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "kbl_bounds_stencil": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
+    "kbl_limit_nodes": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "kbl_velocity_weights": (C.c_int, [C.c_int, C.c_int, _P]),
     "kbl_traces": (C.c_int, [_P, _P, _P]),
     "kbl_gather_stencil": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P]),
@@ -216,6 +217,15 @@ class Context:
         bnd float64 [2][4][E], CUDA tensors."""
         E, n = int(S.shape[0]), int(S.shape[1])
         self._check(self._lib.kbl_bounds_stencil(self._h, E, n, _dev(S, "S"), _dev(bnd, "bnd")), "bounds_stencil")
+
+    def limit_nodes(self, W, U, F, bnd, alpha=None):
+        """Limit explicit node sets (kbl_limit_nodes): W host [ns] positive mean weights; U float64
+        [E][ns][nv] (limited in place), F float64 [E][nf][nv], bnd [2][nv][E], alpha [2][E] or
+        None: CUDA tensors."""
+        E, ns, nf = int(U.shape[0]), int(U.shape[1]), int(F.shape[1])
+        Wh, pW = _host(W, np.float64, "W")
+        self._check(self._lib.kbl_limit_nodes(self._h, E, ns, nf, pW, _dev(U, "U"), _dev(F, "F") if nf else None,
+                                              _dev(bnd, "bnd"), _dev(alpha, "alpha")), "limit_nodes")
 
     def operator(self, which):
         n = (self.p + 1) ** 2 if which == OP_D else self.p + 1

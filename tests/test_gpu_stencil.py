@@ -99,3 +99,53 @@ def test_argument_checks():
         ctx1.bounds_stencil(zeros_dev(3, 5, 4), zeros_dev(2, 4, 3))
     # no elements: nothing to do
     ctx.bounds_stencil(zeros_dev(0, 5, 4), zeros_dev(2, 4, 0))
+
+
+def _node_sets(seed, E, ns, nf, d, spread):
+    rng = np.random.default_rng(seed)
+    nv = d + 2
+    base = inputs.random_states(rng, E, d)
+    U = base[:, None, :] * (1.0 + spread * rng.uniform(-1.0, 1.0, (E, ns, nv)))
+    F = base[:, None, :] * (1.0 + spread * rng.uniform(-1.0, 1.0, (E, nf, nv)))
+    for X in (U, F):
+        ke = 0.5 * sum(X[..., 1 + k] ** 2 for k in range(d)) / X[..., 0]
+        X[..., d + 1] = np.maximum(X[..., d + 1], 1.2 * ke + 1e-2)
+    W = rng.uniform(0.2, 1.0, ns)
+    m = np.einsum("n,enk->ek", W, U) / W.sum()
+    lo = (m - 0.05 * np.abs(m) - 1e-3).T.copy()
+    hi = (m + 0.05 * np.abs(m) + 1e-3).T.copy()
+    return W, U, F, np.stack([lo, hi])
+
+
+@pytest.mark.parametrize("d,ns,nf,p_floor", [(2, 6, 9, 1e-12), (2, 6, 9, 0.05), (2, 10, 12, 1e-12), (1, 5, 2, 0.05),
+                                             (2, 1, 0, 1e-12)])
+@pytest.mark.parametrize("uncoupled", [0, 1])
+def test_limit_node_sets_against_checker(orc, d, ns, nf, p_floor, uncoupled):
+    """Caller-assembled node sets (6 + 9: a P2 triangle's solution and face points) with any
+    positive mean weights, limited on the device and by the checker's node-set limiter."""
+    from paper_2407_20966_gb300 import kbl
+    E = 53
+    W, U, F, bnd = _node_sets(500 + ns + nf, E, ns, nf, d, 0.4)
+    ctx = kbl.Context(dim=d, p=2, nu=(32,) * d if d == 2 else (64,), p_floor=p_floor, uncoupled=uncoupled)
+    Ud = to_dev(U)
+    alpha = zeros_dev(2, E)
+    ctx.limit_nodes(W, Ud, to_dev(F) if nf else zeros_dev(E, 0, d + 2), to_dev(bnd), alpha)
+    st, c = ctx.counters()
+    assert st == kbl.OK and c["limited_elements"] > 0
+    cfg = orc.Config(dim=d, p=2, nu=(16,) * d, p_floor=p_floor, uncoupled=uncoupled)
+    got, ga = Ud.cpu().numpy(), alpha.cpu().numpy()
+    for e in range(E):
+        ref, a = orc.limit_nodes(cfg, W, U[e].T, F[e].T if nf else np.zeros((d + 2, 0)), bnd[0, :, e], bnd[1, :, e])
+        scale = np.abs(U[e]).max()
+        np.testing.assert_allclose(got[e], ref.T, rtol=1e-12, atol=1e-13 * scale)
+        np.testing.assert_allclose(ga[:, e], a, rtol=1e-12, atol=1e-14)
+
+
+def test_limit_node_sets_argument_checks():
+    from paper_2407_20966_gb300 import kbl
+    ctx = kbl.Context(dim=2, p=3, nu=(32, 32))
+    U, F, bnd = zeros_dev(3, 6, 4), zeros_dev(3, 9, 4), zeros_dev(2, 4, 3)
+    for W, UU, FF in ((np.ones(6) * -1.0, U, F), (np.ones(65), zeros_dev(3, 65, 4), F),
+                      (np.ones(6), U, zeros_dev(3, 65, 4))):
+        with pytest.raises(kbl.KblError):
+            ctx.limit_nodes(W, UU, FF, bnd)

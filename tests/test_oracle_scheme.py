@@ -410,3 +410,58 @@ def test_density_pulse_high_order_convergence(orc):
     paper = {r[0]: float(r[1]) for r in rows}
     rate = math.log2(_pulse_error(orc, 20, True) / _pulse_error(orc, 40, True))
     assert abs(rate - paper["relaxed"]) < 1.0, rate
+
+
+def _node_set(rng, ns, nf, d, spread):
+    base = inputs.random_states(rng, 1, d)[0]
+    nv = d + 2
+    U = base[:, None] * (1.0 + spread * rng.uniform(-1.0, 1.0, (nv, ns)))
+    F = base[:, None] * (1.0 + spread * rng.uniform(-1.0, 1.0, (nv, nf)))
+    for X in (U, F):
+        ke = 0.5 * sum(X[1 + k] ** 2 for k in range(d)) / X[0]
+        X[d + 1] = np.maximum(X[d + 1], 1.2 * ke + 1e-2)
+    return U, F
+
+
+def test_node_set_limiter_is_the_element_limiter_with_gauss_weights(orc):
+    """orc_limit_nodes with the tensor Gauss-Legendre weights is orc_limit_element exactly."""
+    rng = np.random.default_rng(70)
+    cfg = orc.Config(dim=2, p=3, nu=(16, 16))
+    xg, wg = orc.gauss_legendre(4)
+    W = np.outer(wg, wg).ravel()          # node n = j * N + i takes wg[i] wg[j]
+    for _ in range(5):
+        U, F = _node_set(rng, 16, 16, 2, 0.4)
+        m = U @ W / W.sum()
+        lo, hi = m - 0.1 * np.abs(m) - 0.05, m + 0.1 * np.abs(m) + 0.05
+        a_el = orc.limit_element(cfg, U, F, lo, hi)
+        a_nd = orc.limit_nodes(cfg, W, U, F, lo, hi)
+        np.testing.assert_array_equal(a_el[0], a_nd[0])
+        np.testing.assert_array_equal(a_el[1], a_nd[1])
+
+
+@pytest.mark.parametrize("d,ns,nf", [(2, 6, 9), (2, 10, 12), (1, 5, 2)])
+def test_node_set_limiter_properties(orc, d, ns, nf):
+    """Any positive mean weights (a P2 triangle: 6 solution and 9 face points): the weighted
+    mean is kept (Eq. 38 moves values toward it), every limited solution value lies inside its
+    bounds when the mean does (Eq. 37), an element already inside keeps its values, and the
+    pressure floor holds after Eq. 47-49."""
+    rng = np.random.default_rng(80 + ns)
+    cfg = orc.Config(dim=d, p=2, nu=(16,) * d, p_floor=0.05)
+    for trial in range(6):
+        W = rng.uniform(0.2, 1.0, ns)
+        U, F = _node_set(rng, ns, nf, d, 0.5)
+        m = U @ W / W.sum()
+        lo, hi = m - 0.05 * np.abs(m) - 1e-3, m + 0.05 * np.abs(m) + 1e-3
+        Ul, a = orc.limit_nodes(cfg, W, U, F, lo, hi)
+        np.testing.assert_allclose(Ul @ W / W.sum(), m, rtol=1e-13, atol=1e-14)
+        if a[1] == 1.0:
+            assert np.all(Ul >= lo[:, None] - 1e-12 * np.abs(lo[:, None]) - 1e-14)
+            assert np.all(Ul <= hi[:, None] + 1e-12 * np.abs(hi[:, None]) + 1e-14)
+        P = (cfg.gamma - 1) * (Ul[d + 1] - 0.5 * sum(Ul[1 + k] ** 2 for k in range(d)) / Ul[0])
+        assert P.min() >= 0.05 * (1 - 1e-9)
+        wide_lo = np.minimum(U.min(axis=1), F.min(axis=1)) - 1.0
+        wide_hi = np.maximum(U.max(axis=1), F.max(axis=1)) + 1.0
+        cfg_free = orc.Config(dim=d, p=2, nu=(16,) * d, p_floor=1e-12)
+        Uf, af = orc.limit_nodes(cfg_free, W, U, F, wide_lo, wide_hi)
+        assert af[0] == 1.0 and af[1] == 1.0
+        np.testing.assert_allclose(Uf, U, rtol=1e-15, atol=1e-15)
