@@ -117,9 +117,17 @@ kbl_status kbl_config_default(kbl_config* cfg, int dim, int p);
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy
  * default stream).  Synchronous.  *out is NULL on failure. */
 kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream);
+/* Free the context and everything it allocated (mesh copy, scratch, adjoint
+ * storage).  KBL_EINVAL for NULL.  The caller's arrays are untouched. */
 kbl_status kbl_destroy(kbl_ctx* ctx);
+/* Bind later launches (the step graph's included) to another stream. */
 kbl_status kbl_set_stream(kbl_ctx* ctx, void* cuda_stream);
+/* Message of the context's last failure (owned by the context; valid until the
+ * next call on it); "null context" for NULL. */
 const char* kbl_last_error(const kbl_ctx* ctx);
+/* Layout sizes: conserved variables nv = d + 2, solution points Ns = (p+1)^d,
+ * face points Nfp (2 in 1D, 4 (p+1) in 2D), stencil states Ns + 2 Nfp (Sec. 5);
+ * -1 for NULL. */
 int kbl_nv(const kbl_ctx* ctx);
 int kbl_ns(const kbl_ctx* ctx);
 int kbl_nfp(const kbl_ctx* ctx);
@@ -223,6 +231,8 @@ kbl_status kbl_run_host(kbl_ctx* ctx, const double* w_host_in, double* w_host_ou
 /* Wait for the context's stream and report device-side flags (then clear
  * them): KBL_ENONPHYSICAL if a non-physical state was met. */
 kbl_status kbl_check(kbl_ctx* ctx);
+/* The same wait, with the flags and the limiting counters copied to *out (HOST)
+ * before they are cleared; returns what kbl_check would. */
 kbl_status kbl_read_counters(kbl_ctx* ctx, kbl_counters* out);
 
 /* Number of kernel launches the context has issued (graph launches count
@@ -235,7 +245,7 @@ int64_t kbl_launch_count(const kbl_ctx* ctx);
  * nodes per thread, 1 = 4 x 2, 2 = 2 x 4.  Setting a knob drops the captured
  * step graph. */
 typedef enum { KBL_TUNE_BOUNDS_TILE = 0 } kbl_tune_key;
-kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);
+kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);   /* KBL_EINVAL for an unknown key or value */
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 
 /* ---- Batched form -----------------------------------------------------------
@@ -259,7 +269,9 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int n_proble
                             const int32_t* p, const int32_t* n_elem, const int32_t* nbr,
                             const double* h, const int32_t* n_bc, const double* bc,
                             void* cuda_stream);
+/* Free the batch and its device memory; KBL_EINVAL for NULL. */
 kbl_status kbl_batch_destroy(kbl_batch* b);
+/* Message of the batch's last failure (owned by the batch). */
 const char* kbl_batch_last_error(const kbl_batch* b);
 /* state_offsets[n_problems+1] (doubles) and elem_offsets[n_problems+1] (HOST). */
 kbl_status kbl_batch_layout(const kbl_batch* b, int64_t* state_offsets, int64_t* elem_offsets);
@@ -278,7 +290,9 @@ kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host);
 kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, double* out_cmp);
 /* Current launch shape: [tile, elements per item, blocks per SM, items]. */
 kbl_status kbl_batch_tuning(const kbl_batch* b, int32_t* out4);
+/* Wait for the batch's stream and report (then clear) its device flags, as kbl_check. */
 kbl_status kbl_batch_check(kbl_batch* b);
+/* Kernel launches the batch has issued (graph launches count their kernels). */
 int64_t kbl_batch_launch_count(const kbl_batch* b);
 
 /* ---- Reverse mode (adjoint) --------------------------------------------------
