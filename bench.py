@@ -46,7 +46,7 @@ PEAK_SOURCE = ("measured envelope-pattern rate 155.5 FP32 lane-ops/clk/SM (bench
 # DRAM bytes (read + write) of one launch of the FP32 2D bounds kernel on the vortex workload,
 # from an ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum).  Must be
 # reset to None whenever that kernel changes, until it is captured again.
-BOUNDS_F32_VORTEX_TRAFFIC = 17071104 + 0
+BOUNDS_F32_VORTEX_TRAFFIC = 17071616 + 0
 
 
 def parse():
@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2, 2: 2x4, 3: warp-specialized)")
+    ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2, 2: 2x4; -1: default)")
     return ap.parse_args()
 
 
