@@ -28,7 +28,7 @@ struct LimSmem {
     double smean[EPB][NV];
     double salpha_v[EPB][NV];
     double salpha[EPB];
-    double sP[EPB][NS + NFP];
+    int slow[EPB];               // some point of V failed the division-free pressure screen
     double saP[EPB];
     int sPtaken[EPB];
     double slm[N], slp[N], sW[NS];
@@ -59,7 +59,7 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     auto& smean = sm.smean;
     auto& salpha_v = sm.salpha_v;
     auto& salpha = sm.salpha;
-    auto& sP = sm.sP;
+    auto& slow = sm.slow;
     auto& saP = sm.saP;
     auto& sPtaken = sm.sPtaken;
     auto& slm = sm.slm;
@@ -206,6 +206,7 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             }
         }
         sfast[ell] = fast;
+        slow[ell] = 0;
     }
     __syncthreads();
     // 2. face values (interpolation along the line normal to each face)
@@ -263,24 +264,25 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     }
     __syncthreads();
     if (tid < EPB) {
-        double a = 1.0;
+        // every alpha_i lies in [0, 1] (never NaN: a NaN ratio is not taken), where the order of
+        // the bit patterns is the order of the values: the minimum on the integer pipe
+        long long ka = __double_as_longlong(1.0);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            const double b = salpha_v[tid][v];
-            if (b < a) a = b;
+            const long long kb = __double_as_longlong(salpha_v[tid][v]);
+            ka = kb < ka ? kb : ka;
         }
-        salpha[tid] = a;
+        salpha[tid] = __longlong_as_double(ka);
     }
     __syncthreads();
     // 4. limited state at V.  Pressure floor test without a division first:
     //    P < p_floor  <=>  (gamma-1) (rho E - |m|^2/2) < p_floor rho  (rho > 0);
     //    the margin bounds the rounding of rho E - |m|^2/2 (it can cancel), so the
     //    screen never passes a point the exact test would fail; any element it
-    //    flags gets the exact P_min of Eq. 47 below.
+    //    flags gets the exact P_min of Eq. 47 below.  Elements that passed the exact screen
+    //    (alpha = 1 and the box test) keep w~ = w and need no pressure re-limit.
     const double gm1 = ph.gamma - 1.0;
-    if (live && sfast[el]) {
-        sP[el][nd] = 1.0;   // alpha = 1 and the box test passed: w~ = w, no pressure re-limit
-    } else if (live) {
+    if (live && !sfast[el]) {
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -293,15 +295,11 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         if (DIM == 2) mm += q[2] * q[2];
         const double X = fma(q[DIM + 1], q[0], -0.5 * mm);
         const double tol = 4e-15 * (fabs(q[DIM + 1] * q[0]) + 0.5 * mm);
-        sP[el][nd] = (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) ? -1.0 : 1.0;
+        if (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) slow[el] = 1;
     }
     for (int t = tid; t < EPB * NFP; t += NT) {
         const int ell = t / NFP, fp = t % NFP;
-        if (e0 + ell >= E || ell >= nmax) continue;
-        if (sfast[ell]) {
-            sP[ell][NS + fp] = 1.0;
-            continue;
-        }
+        if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -314,12 +312,11 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         if (DIM == 2) mm += q[2] * q[2];
         const double X = fma(q[DIM + 1], q[0], -0.5 * mm);
         const double tol = 4e-15 * (fabs(q[DIM + 1] * q[0]) + 0.5 * mm);
-        sP[ell][NS + fp] = (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) ? -1.0 : 1.0;
+        if (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) slow[ell] = 1;
     }
     __syncthreads();
     if (tid < EPB && tid < nmax && e0 + tid < E) {
-        bool low = false;
-        for (int n2 = 0; n2 < NS + NFP; n2++) low |= sP[tid][n2] < 0.0;
+        const bool low = slow[tid] != 0;
         double aP = 1.0;
         int taken = 0;
         if (low) {
@@ -343,7 +340,8 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         sPtaken[tid] = taken;
         saP[tid] = aP;
         const int ee = e0 + tid;
-        if (salpha[tid] < 1.0) atomicAdd(&flags->limited, 1ull);
+        // alpha in [0, 1]: alpha < 1 on the bit patterns
+        if (__double_as_longlong(salpha[tid]) < __double_as_longlong(1.0)) atomicAdd(&flags->limited, 1ull);
         if (alpha_out) {
             alpha_out[ee] = salpha[tid];
             alpha_out[E + ee] = aP;
