@@ -159,7 +159,12 @@ void build_ops(int p, FrOps& o)
         o.grf[i] = (float)o.gr[i];
         o.lmf[i] = (float)o.lm[i];
         o.lpf[i] = (float)o.lp[i];
+        o.wqf[i] = (float)o.wq[i];
     }
+    for (int k = 0; k < n * n; k++) o.wm2f[k] = (float)o.wm2[k];
+    o.winv1f = (float)o.winv1;
+    o.winv2f = (float)o.winv2;
+    o.lamf = kbl_f32_up(o.lam);
 }
 
 kbl_status fail(kbl_ctx* c, kbl_status st, const char* msg)

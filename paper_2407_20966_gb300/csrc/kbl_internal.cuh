@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 
@@ -28,7 +29,25 @@ struct FrOps {
     double winv1, winv2, lam;
     // FP32 copies (rounded on the host) of the residual's operators, for the FP32 arithmetic
     float Df[KBL_NMAX][KBL_NMAX], glf[KBL_NMAX], grf[KBL_NMAX], lmf[KBL_NMAX], lpf[KBL_NMAX];
+    // for the FP32 screen of the limiter: the mean weights and 1 / their sum rounded to
+    // nearest, and Lambda rounded up
+    float wm2f[KBL_NMAX * KBL_NMAX], wqf[KBL_NMAX], winv1f, winv2f, lamf;
 };
+
+// FP32 value nearest x, moved one step up (down) when it lies below (above) x: a float
+// bound of a double, for the conservative FP32 screens.
+inline float kbl_f32_up(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+inline float kbl_f32_down(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafter(f, -INFINITY);
+    return f;
+}
 
 // Physical and method constants, passed by value.
 struct Phys {
@@ -45,6 +64,8 @@ struct Phys {
     // conversion on them: gamma - 1, k, delta / 2 = 1/(gamma - 1) - d/2 for d = 2, 1 -+ r
     float gm1f, kf, half_delta2f;
     double rel_lo, rel_hi;
+    // float bounds for the limiter's FP32 screen: eps and p_floor rounded up, gamma - 1 down
+    float epsf_up, pfloorf_up, gm1f_down;
 };
 
 inline void kbl_phys_derive(Phys& p)
@@ -52,6 +73,9 @@ inline void kbl_phys_derive(Phys& p)
     p.gm1f = (float)(p.gamma - 1.0);
     p.kf = (float)p.k;
     p.half_delta2f = 0.5f * (float)(2.0 / (p.gamma - 1.0) - 2.0);
+    p.epsf_up = kbl_f32_up(p.eps);
+    p.pfloorf_up = kbl_f32_up(p.p_floor);
+    p.gm1f_down = kbl_f32_down(p.gamma - 1.0);
     p.rel_lo = 1.0 - p.r_fac;
     p.rel_hi = 1.0 + p.r_fac;
 }

@@ -32,11 +32,15 @@ struct LimSmem {
     double saP[EPB];
     int sPtaken[EPB];
     double slm[N], slp[N], sW[NS];
-    // exact fast path: per-component box around the mean that holds every value of V
-    double sbl[EPB][NV], sbh[EPB][NV];
-    double sdmx[EPB][NV], sdmn[EPB][NV];   // node extremes minus the mean
-    float sdev[EPB][NV][NS];               // node deviations from the mean (FP32)
-    float sfdev[EPB][NV][NFP];             // face-value deviations from the mean (FP32)
+    // FP32 screen (exact for alpha = 1 and the pressure test, see stage_limit_block)
+    double sc[EPB][NV];                    // reference value c of each component
+    float saf[EPB][NV][NS];                // fl32 of the node values minus c
+    float smf[EPB][NV], sem[EPB][NV];      // FP32 mean m' and a bound of |c + m' - mean|
+    float sdx[EPB][NV], sdn[EPB][NV];      // largest and smallest node deviation from m'
+    float samax[EPB][NV], ssum[EPB][NV];   // max |a_n|, sum W |a_n| / sum W
+    float sdev[EPB][NV][NS];               // node deviations from m'
+    float sfdev[EPB][NV][NFP];             // face deviations from m' (FP32 interpolation)
+    float sbl[EPB][NV], sbh[EPB][NV];      // a box that holds every value of V
     int sfv[EPB][NV], sfast[EPB];
 
 };
@@ -69,8 +73,14 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     auto& sbh = sm.sbh;
     auto& sfv = sm.sfv;
     auto& sfast = sm.sfast;
-    auto& sdmx = sm.sdmx;
-    auto& sdmn = sm.sdmn;
+    auto& sc = sm.sc;
+    auto& saf = sm.saf;
+    auto& smf = sm.smf;
+    auto& sem = sm.sem;
+    auto& sdx = sm.sdx;
+    auto& sdn = sm.sdn;
+    auto& samax = sm.samax;
+    auto& ssum = sm.ssum;
     auto& sdev = sm.sdev;
     auto& sfdev = sm.sfdev;
     const int tid = threadIdx.x;
@@ -82,11 +92,12 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     // mean weights, 1 / their sum and Lambda come precomputed with the operators (no FP64
     // arithmetic here: every FP64 instruction holds the slow FP64 pipe however few lanes run)
     if (tid < NS) sW[tid] = (DIM == 1) ? ops.wq[tid] : ops.wm2[tid];
-    const double winv = (DIM == 1) ? ops.winv1 : ops.winv2, sLam = ops.lam;
+    const double winv = (DIM == 1) ? ops.winv1 : ops.winv2;
     const int el = tid / NS, nd = tid % NS;
     const int e = e0 + el;
     const bool live = el < EPB && el < nmax && e < E;
-    // 1. stage combination
+    // 1. stage combination; the FP32 screen works on the differences from a reference value c
+    //    of each component near the element's values (its node-0 value before the stage)
     if (live) {
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -101,39 +112,65 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
                 val = ws[g];
             }
             sw[el][v][nd] = val;
+            const double c = ws[((size_t)v * E + e) * NS];
+            saf[el][v][nd] = f32_trunc(val - c);
+            if (nd == 0) sc[el][v] = c;
         }
     }
     __syncthreads();
-    // 1b. mean and node extrema (FP64), node deviations from the mean (FP64 difference, kept in
-    //     FP32), face-value deviations from them in FP32 with a rounding allowance: an exact screen
-    //     for alpha = 1.  Every face value lies within its FP32 deviation +- 1e-6 Lambda M of the
-    //     mean (M = largest node deviation; Lambda = max sum |l_i(+-1)|), up to the FP64 rounding
-    //     of the face interpolation itself, covered by delta.  If both bounds lie beyond all of V
-    //     by that margin and the node extremes already clear the epsilon rule, Eq. 37 gives
-    //     alpha_i = 1 whatever the exact face values are, so they need not be formed in FP64.
+    // 1b. An exact screen for alpha = 1, in FP32 (GB300 runs FP64 at ~1/76 of the FP32 rate).
+    //     Notation per element and component: w_n the FP64 node values, mean = the FP64 mean
+    //     the exact path forms, c the reference, a_n = trunc32(fl64(w_n - c)) (|a_n - (w_n - c)|
+    //     <= (2^-23 + 2^-53) |w_n - c| + 2^-126), m' = the FP32 weighted mean of the a_n, S' =
+    //     the FP32 weighted mean of the |a_n|, A = max |a_n|, C = |c| rounded up to FP32,
+    //     d_n = fl32(a_n - m'), M = max |d_n|.  Errors scale with the deviations, except the
+    //     FP64 rounding of the exact path itself, which scales with C.
+    //   (i)   |c + m' - mean| <= e_m = (NS + 8) 2^-23 S' + (2 NS + 4) 2^-53 (C + S') + tiny: the
+    //         FP32 sum (inputs 2^-23, weights 2^-24, NS-term FMA sum NS 2^-24, 1 / sum W and the
+    //         product 2 2^-24, relative to S, with a factor 2 to spare) and the FP64 sum and
+    //         1 / sum W of the exact mean.
+    //   (ii)  each node: |(w_n - mean) - d_n| <= e_node = 2^-23 M + 2^-22 A + e_m + tiny.
+    //   (iii) each face value f (FP64 interpolation of the exact path): |(f - mean) - fd| <=
+    //         e_face = Lambda (e_node + (N + 3) 2^-24 M) + 1e-13 Lambda (C + A) + tiny, fd the
+    //         FP32 interpolation of the d_n (FP32 weights and sum: (N + 2) 2^-24 Lambda M; the
+    //         FP64 rounding and sum l_i - 1 of the exact path: below 4 N 2^-53 Lambda (C + A)).
+    //   So every value of V minus mean lies in [-dn, up], dn = max(-min d, -min fd) + e_face,
+    //   up = max(max d, max fd) + e_face.  The exact path's dmax = fl64(max_V - mean) is then
+    //   <= up (1 + 2^-52) and >= max d - e_node; likewise dmin.  Eq. 37 gives alpha_i = 1 when
+    //   both clear eps and hi - mean >= up (1 + 2^-52), mean - lo >= dn (1 + 2^-52): checked
+    //   below with hb = trunc32(fl64(hi - c)) (2^-22 |hb| + tiny) and m' for mean - c (e_m).
+    //   Every FP32 evaluation has at most a few roundings of non-negative terms (2^-24 each),
+    //   which the factors (1 + 2^-16) on the right-hand sides and (1 - 2^-20) on the left cover.
+    //   Non-finite values: trunc32 maps NaN and |x| >= 2^128 to infinities, which fail
+    //   S' <= 1e30 and C <= 1e30; below those bounds every FP32 quantity here stays finite.
+    constexpr float TINY = 1e-35f;                  // covers the absolute 2^-126 terms
+    constexpr float CM = (float)(NS + 8) * 0x1p-23f;
+    constexpr float CM64 = (float)(2 * NS + 4) * 0x1p-53f;
+    constexpr float UPF = 1.0f + 0x1p-16f, DNF = 1.0f - 0x1p-20f;
+    const float winvf = (DIM == 1) ? ops.winv1f : ops.winv2f;
     for (int t = tid; t < EPB * NV; t += NT) {
         const int ell = t / NV, v = t % NV;
         if (e0 + ell >= E || ell >= nmax) continue;
-        double sum = 0.0;
-        for (int n2 = 0; n2 < NS; n2++) sum += sW[n2] * sw[ell][v][n2];
-        const double mean = sum * winv;
-        long long kmx = dkey(sw[ell][v][0]), kmn = kmx;
-        for (int n2 = 1; n2 < NS; n2++) {
-            const long long kk = dkey(sw[ell][v][n2]);
-            kmx = kk > kmx ? kk : kmx;
-            kmn = kk < kmn ? kk : kmn;
-        }
-        smean[ell][v] = mean;
-        sdmx[ell][v] = dunkey(kmx) - mean;
-        sdmn[ell][v] = dunkey(kmn) - mean;
-    }
-    __syncthreads();
-    if (live) {
-        // FP32 differences of the truncated values (integer-pipe truncation, one FP32 subtraction):
-        // each is within 2^-23 (|w| + |mean|) + 2^-24 |w - mean| of the exact deviation, which
-        // the face allowance below covers
+        float sm_ = 0.0f, sa = 0.0f, amax = -FLT_MAX, amin = FLT_MAX;
 #pragma unroll
-        for (int v = 0; v < NV; v++) sdev[el][v][nd] = f32_trunc(sw[el][v][nd]) - f32_trunc(smean[el][v]);
+        for (int n2 = 0; n2 < NS; n2++) {
+            const float a = saf[ell][v][n2], wf = (DIM == 1) ? ops.wqf[n2] : ops.wm2f[n2];
+            sm_ = fmaf(wf, a, sm_);
+            sa = fmaf(wf, fabsf(a), sa);
+            amax = fmaxf(amax, a);
+            amin = fminf(amin, a);
+        }
+        const float m = sm_ * winvf;
+#pragma unroll
+        for (int n2 = 0; n2 < NS; n2++) sdev[ell][v][n2] = saf[ell][v][n2] - m;
+        smf[ell][v] = m;
+        const float S = sa * winvf;
+        const float C = fabsf(f32_trunc(sc[ell][v])) * (1.0f + 0x1p-22f);
+        ssum[ell][v] = fmaxf(S, C);
+        sem[ell][v] = CM * S + CM64 * (C + S) + TINY;
+        sdx[ell][v] = amax - m;   // = max_n d_n: rounding is monotone
+        sdn[ell][v] = amin - m;
+        samax[ell][v] = fmaxf(amax, -amin);
     }
     __syncthreads();
     for (int t = tid; t < EPB * NFP; t += NT) {
@@ -146,7 +183,7 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             float acc = 0.0f;
 #pragma unroll
             for (int i = 0; i < N; i++) {
-                const float l = (float)((f & 1) ? slp[i] : slm[i]);
+                const float l = (f & 1) ? ops.lpf[i] : ops.lmf[i];
                 acc = fmaf(l, sdev[ell][v][(DIM == 1) ? i : (along_x ? k * N + i : i * N + k)], acc);
             }
             sfdev[ell][v][fp] = acc;
@@ -157,29 +194,43 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         const int ell = t / NV, v = t % NV;
         const int ee = e0 + ell;
         if (ee >= E || ell >= nmax) continue;
-        const double mean = smean[ell][v], dmaxn = sdmx[ell][v], dminn = sdmn[ell][v];
+        const float m = smf[ell][v], em = sem[ell][v], dx = sdx[ell][v], dnn = sdn[ell][v], A = samax[ell][v];
         float fmx = -FLT_MAX, fmn = FLT_MAX;
         for (int fp = 0; fp < NFP; fp++) {
             fmx = fmaxf(fmx, sfdev[ell][v][fp]);
             fmn = fminf(fmn, sfdev[ell][v][fp]);
         }
-        const double M = fmax(dmaxn, -dminn);
-        // FP32 face interpolation (1e-6 of Lambda M) and the truncated node deviations
-        // (at most 2^-23 (2 |mean| + M) + 2^-24 M each, below 2.4e-7 (|mean| + M); 5e-7 with margin)
-        const double err = sLam * (1e-6 * M + 5e-7 * (fabs(mean) + M)) + 1e-37;
-        const double delta = 1e-14 * (fabs(mean) + fmax(fabs(mean + dmaxn), fabs(mean + dminn))) * sLam;
-        const double up = fmax(dmaxn, (double)fmx + err) + delta;    // every value of V is below mean + up
-        const double dn = fmax(-dminn, -(double)fmn + err) + delta;  // and above mean - dn
-        const double lo = bnd[(size_t)v * E + ee];
-        const double hi = bnd[((size_t)NV + v) * E + ee];
-        sbl[ell][v] = mean - dn;
-        sbh[ell][v] = mean + up;
-        sfv[ell][v] = (dmaxn >= ph.eps) && (-dminn >= ph.eps) && (hi - mean >= up) && (mean - lo >= dn);
+        const double c = sc[ell][v];
+        const float c32 = f32_trunc(c), C = fabsf(c32) * (1.0f + 0x1p-22f);
+        const float lam = ops.lamf;
+        const float M = fmaxf(dx, -dnn);
+        const float enode = 0x1p-23f * M + 0x1p-22f * A + em + TINY;
+        const float eface = lam * (enode + (float)(N + 3) * 0x1p-24f * M) + (1e-13f * lam) * (C + A) + TINY;
+        const float up = (fmaxf(dx, fmx) + eface) * UPF;
+        const float dn = (fmaxf(-dnn, -fmn) + eface) * UPF;
+        const float need = (ph.epsf_up + enode) * UPF;
+        const float hb = f32_trunc(bnd[((size_t)NV + v) * E + ee] - c);
+        const float lb = f32_trunc(bnd[(size_t)v * E + ee] - c);
+        const bool ok = (ssum[ell][v] <= 1e30f) && (dx >= need) && (-dnn >= need) &&
+                        ((hb - m) * DNF >= (up + 0x1p-22f * fabsf(hb) + em + TINY) * UPF) &&
+                        ((m - lb) * DNF >= (dn + 0x1p-22f * fabsf(lb) + em + TINY) * UPF);
+        sfv[ell][v] = ok;
+        // every value of V lies in [c + rl, c + rh], rl = m' - dn - e_m, rh = m' + up + e_m; in
+        // absolute FP32 terms (c32 = trunc32(c): |c - c32| <= 2^-22 |c32| + tiny, and the
+        // rounding of rl, rh and of c32 + r) the box is widened by 2^-22 (|c32 + r| + |c32|) +
+        // 2^-23 |r| + tiny
+        const float rl = m - (dn + em) * UPF, rh = m + (up + em) * UPF;
+        const float bl = c32 + rl, bh = c32 + rh;
+        sbl[ell][v] = bl - (0x1p-22f * (fabsf(bl) + fabsf(c32)) + 0x1p-23f * fabsf(rl) + TINY) * UPF;
+        sbh[ell][v] = bh + (0x1p-22f * (fabsf(bh) + fabsf(c32)) + 0x1p-23f * fabsf(rh) + TINY) * UPF;
     }
     __syncthreads();
-    // 1c. pressure over the box: a lower bound of P on it (rho from its lower end, E from its lower
-    //     end, |m|^2 from the larger end of each component) that clears 2 p_floor plus an allowance
-    //     for the rounding of the exact pressure test below means no point of V can fail it
+    // 1c. pressure over the box, FP32: with rho >= rlo > 0, E >= elo, |m|^2 <= mm at every point
+    //     of V, the exact test below (gamma-1)(X - tol) >= p_floor rho, X = rho E - |m|^2/2, holds
+    //     at every point when (gamma-1)(elo rlo - mm/2 - G) >= 2 p_floor rlo: the left side minus
+    //     the right grows with rho once it is >= 0 at rlo, and G = 1e-6 (|E|max rlo + mm) covers
+    //     the FP32 rounding of elo rlo - mm/2, the exact test's tol (4e-15) and its FP64
+    //     rounding; the factor 2 and 1e-36 cover the rounding (or underflow) of p_floor rlo.
     if (tid < EPB) {
         const int ell = tid;
         int fast = 0;
@@ -187,29 +238,33 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             fast = 1;
 #pragma unroll
             for (int v = 0; v < NV; v++) fast &= sfv[ell][v];
-            const double rlo = sbl[ell][0];
-            double mm = 0.0;
+            const float rlo = sbl[ell][0];
+            float mm = 0.0f;
 #pragma unroll
             for (int k = 1; k <= DIM; k++) {
-                const double a = fmax(fabs(sbl[ell][k]), fabs(sbh[ell][k]));
-                mm += a * a;
+                const float a = fmaxf(fabsf(sbl[ell][k]), fabsf(sbh[ell][k]));
+                mm = fmaf(a, a, mm);
             }
-            const double elo = sbl[ell][DIM + 1];
-            const double eabs = fmax(fabs(elo), fabs(sbh[ell][DIM + 1]));
-            if (!(rlo > 0.0)) {
-                fast = 0;
-            } else {
-                // (gamma - 1)(elo - mm / (2 rlo)) >= 2 p_floor + 1e-13 (eabs + mm / rlo), multiplied
-                // through by rlo > 0: no FP64 division; its few ulp of rounding sit far inside 1e-13
-                const double lhs = (ph.gamma - 1.0) * fma(elo, rlo, -0.5 * mm);
-                if (!(lhs >= 2.0 * ph.p_floor * rlo + 1e-13 * fma(eabs, rlo, mm))) fast = 0;
-            }
+            mm *= 1.0f + 0x1p-20f;
+            const float elo = sbl[ell][DIM + 1];
+            const float eabs = fmaxf(fabsf(elo), fabsf(sbh[ell][DIM + 1]));
+            const float Y = fmaf(elo, rlo, -0.5f * mm) - 1e-6f * fmaf(eabs, rlo, mm);
+            if (!(rlo > 0.0f) || !(ph.gm1f_down * Y >= 2.0f * ph.pfloorf_up * rlo + 1e-36f)) fast = 0;
         }
         sfast[ell] = fast;
         slow[ell] = 0;
     }
     __syncthreads();
-    // 2. face values (interpolation along the line normal to each face)
+    // 2. the exact path, for the elements the screen did not pass: the FP64 mean (the weights
+    //    in order, then 1 / sum W) and the face values (interpolation along the line normal to
+    //    each face)
+    for (int t = tid; t < EPB * NV; t += NT) {
+        const int ell = t / NV, v = t % NV;
+        if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
+        double sum = 0.0;
+        for (int n2 = 0; n2 < NS; n2++) sum += sW[n2] * sw[ell][v][n2];
+        smean[ell][v] = sum * winv;
+    }
     for (int t = tid; t < EPB * NFP; t += NT) {
         const int ell = t / NFP, fp = t % NFP;
         if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
