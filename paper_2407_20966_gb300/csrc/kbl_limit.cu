@@ -11,6 +11,9 @@
 //   P_min over V (Eq. 47); if < p_floor:
 //     alpha_P = |(p_floor - P(mean)) / (P_min - P(mean))| (0 if P(mean) <= p_floor)
 //     w~~ = mean + alpha_P (w~ - mean)          (Eq. 48-49)
+// An exact FP32 screen (kbl_limit_body.cuh) first certifies, where it can, that alpha = 1
+// and that no point of V fails the pressure test; those elements keep w and skip the FP64
+// steps above, whose results they would not change beyond the rounding of mean + (w - mean).
 #include <cfloat>
 
 #include "kbl_limit_body.cuh"
