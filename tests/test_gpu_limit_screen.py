@@ -106,3 +106,23 @@ def test_screen_at_the_pressure_floor(orc, dim, p, n):
     np.testing.assert_allclose(ga, a_ref, rtol=1e-10, atol=1e-12)
     np.testing.assert_array_equal(ga[1] < 1, a_ref[1] < 1)
     assert ((a_ref[1] < 1) == (gp < 0)).all()
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-8, 1e6, 1e25, 1e35, 1e100])
+def test_screen_at_extreme_magnitudes(orc, scale):
+    """States scaled into and beyond the FP32 range (eps = 0 and p_floor = 0, so that only the
+    bound tests decide): where the screen cannot resolve the values it must leave the element
+    to the exact path, and every result equals the checker's."""
+    ctx, ocfg = both(orc, 2, 3, (16, 16), eps=0.0, p_floor=0.0)
+    mesh, w = mesh_and_field(orc, 2, 3, (8, 6), seed=630, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    w = w * scale
+    mean, V = _mean_and_V(orc, ocfg, om, w, 2, 3)
+    dmax, dmin = V.max(axis=2) - mean, V.min(axis=2) - mean
+    g = np.array([[-1e-3, -1e-7, 1e-7, 1e-3, 0.5][e % 5] for e in range(mesh.n_elem)])
+    bnd = np.stack([mean + dmin * (1 + g), mean + dmax * (1 + g)])
+    got, ga, ref, a_ref = _limit_both(orc, ctx, ocfg, om, w, bnd)
+    assert state_error(got, ref).max() < TOL_FP64
+    np.testing.assert_allclose(ga, a_ref, rtol=1e-10, atol=1e-12)
+    np.testing.assert_array_equal(ga[0] < 1, a_ref[0] < 1)
+    assert ((a_ref[0] < 1) == (g < 0)).all()
