@@ -32,7 +32,8 @@
 // come from a product recurrence (kbl_gauss_segment), a few exponentials per
 // segment of 16 nodes.
 // FP32 kernels: FP64 only for X = rho E - |m|^2/2 (rho P / (gamma-1)) with its
-// positivity test and for assembling the final bounds; velocities are taken
+// positivity test (and, in 1D, for assembling the final bounds; the 2D kernels
+// assemble them in FP32 and widen them exactly); velocities are taken
 // relative to the box centre inside the exponentials; pairs of states share
 // one packed multiply (__fmul2_rn) and one three-input min/max; the partial
 // sums of the threads meet in a pairwise tree (the 1D kernel keeps a

@@ -104,9 +104,9 @@ __device__ __forceinline__ float fast_exp2(float x)
 // ---------------------------------------------------------------------------
 // 2D, FP32 envelopes and sums.  FP64 is used only where the path needs it:
 // X = rho E - |m|^2 / 2 (= rho P / (gamma - 1), the cancellation-prone,
-// positivity-deciding quantity) and its sign test, and the final assembly of
-// the bounds.  Everything else per state (U, theta, A, C, the box) is FP32,
-// because the GB300 FP64 pipe runs at ~1/76 of the FP32 rate.
+// positivity-deciding quantity) and its sign test.  Everything else per state
+// (U, theta, A, C, the box) and the assembly of the bounds is FP32, because the
+// GB300 FP64 pipe runs at ~1/76 of the FP32 rate.
 // ---------------------------------------------------------------------------
 // Thread tile of the envelope loop: TYSEL 0 = TX x TX with TX = 4 (grids of 32 or more
 // points per axis), 2 = 4 x 2, 3 = 2 x 4 (x nodes x y nodes per thread).
@@ -200,7 +200,7 @@ struct Bounds2dF32SmemS {
     float sbox[NW][4];
     int sbad;
     float sred[NW][16];
-    double sfin[K];
+    float sfin[K];
 
 };
 
@@ -417,31 +417,34 @@ __device__ __forceinline__ void bounds2d_f32_core(Bounds2dF32SmemS<NST_, NX, TYS
     const float rs = warp_reduce_scatter16(acc);
     if ((lane & 1) == 0 && (lane >> 1) < K) sred[wid][lane >> 1] = rs;
     __syncthreads();
-    // 6. assemble the bounds in FP64, one raw sum per lane
+    // 6. assemble the bounds, one raw sum per lane, in FP32 (three more roundings, ~2e-7 of
+    //    the bound, next to the ~3e-7 of the sums): an FP64 chain here held the slow FP64 pipe
+    //    on every element's critical path.  The FP64 value is the exact widening.
     if (tid < K) {
         float sum = sred[0][tid];
 #pragma unroll
         for (int q = 1; q < NW; q++) sum += sred[q][tid];
         // lower-bound terms take (1 - r), upper-bound terms (1 + r)
         const bool upper_env = (tid == 1) || (tid == 2) || (tid == 5) || (tid == 6) || (tid == 9) || (tid == 11);
-        const double rel = upper_env ? ph.rel_hi : ph.rel_lo;
-        sfin[tid] = rel * ((f64_widen(hx) * f64_widen(hy)) * f64_widen(sum));
+        sfin[tid] = (upper_env ? ph.rel_hif : ph.rel_lof) * ((hx * hy) * sum);
     }
     __syncthreads();
     if (tid < 2 * NV) {
         const int v = tid % NV, up = tid / NV;
-        double val;
-        if (v == 0) val = up ? sfin[1] : sfin[0];
-        else if (v == NV - 1) val = up ? sfin[11] : sfin[10];
+        float valf;
+        if (v == 0) valf = up ? sfin[1] : sfin[0];
+        else if (v == NV - 1) valf = up ? sfin[11] : sfin[10];
         else {
             const int b0 = 2 + 4 * (v - 1);
-            val = up ? sfin[b0 + 1] + sfin[b0 + 3] : sfin[b0 + 0] + sfin[b0 + 2];
+            valf = up ? sfin[b0 + 1] + sfin[b0 + 3] : sfin[b0 + 0] + sfin[b0 + 2];
         }
+        double val = f64_widen(valf);
         // val >= 0 (a sum of non-negative terms) or NaN: the order of the bit patterns decides
         if (v == 0 && !up && __double_as_longlong(val) < __double_as_longlong(ph.rho_floor)) val = ph.rho_floor;
         bnd[((size_t)up * NV + v) * E + e] = val;
     }
 }
+
 
 // Bounds of element e of an FR mesh (the stencil of Sec. 5: own solution and face points,
 // exterior face values).

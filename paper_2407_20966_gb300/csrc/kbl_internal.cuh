@@ -64,6 +64,7 @@ struct Phys {
     // conversion on them: gamma - 1, k, delta / 2 = 1/(gamma - 1) - d/2 for d = 2, 1 -+ r
     float gm1f, kf, half_delta2f;
     double rel_lo, rel_hi;
+    float rel_lof, rel_hif;   // FP32 copies of 1 -+ r
     // float bounds for the limiter's FP32 screen: eps and p_floor rounded up, gamma - 1 down
     float epsf_up, pfloorf_up, gm1f_down;
 };
@@ -78,6 +79,8 @@ inline void kbl_phys_derive(Phys& p)
     p.gm1f_down = kbl_f32_down(p.gamma - 1.0);
     p.rel_lo = 1.0 - p.r_fac;
     p.rel_hi = 1.0 + p.r_fac;
+    p.rel_lof = (float)p.rel_lo;
+    p.rel_hif = (float)p.rel_hi;
 }
 
 // FP32 approximation of a double by truncating its significand, with integer operations only
