@@ -2,7 +2,8 @@
 
 Closed forms: moments of one Maxwellian (whole line and truncated box, via erf),
 the truncation error the paper prints for k = 4 and k = 8, the two-state 1D
-envelope integrated exactly between its crossing points.  Theorems: constant-state
+envelope integrated exactly between its crossing points, and a separable two-state 2D
+case reduced to it.  Theorems: constant-state
 preservation (Thm 4.1), positivity (Thm 4.2), Riemann-averaged states (Thm 4.3),
 the first-order Lax-Friedrichs update (Thm 4.4), mean preservation (Thm 4.5).
 Invariant: every stencil state's own quadrature moments lie inside the bounds,
@@ -168,6 +169,43 @@ def test_two_state_1d_bounds_match_piecewise_closed_form(orc):
             sc = np.abs(exact_hi).max()
             errs.append(max(np.abs(lo - exact_lo).max(), np.abs(hi - exact_hi).max()) / sc)
         assert errs[1] < 2e-7, errs
+        assert errs[1] < errs[0]
+
+
+def test_two_state_2d_bounds_match_separable_closed_form(orc):
+    """Two 2D states with the same temperature and the same U_y: every Maxwellian is
+    a_i(u_x) Gamma(u_y) with a common Gamma, so each 2D envelope is Gamma times the 1D envelope
+    of the a_i, and every bound is a product of an exact 1D envelope integral (erf pieces
+    between the crossing points) and erf moments of Gamma (split at u_y = 0 for the y
+    momentum).  A transposed axis, a wrong sign split or a dropped energy term fails it."""
+    rng = np.random.default_rng(11)
+    delta = 2 / (G - 1) - 2
+    for trial in range(3):
+        th, Uy = rng.uniform(0.5, 1.5), rng.uniform(-0.8, 0.8)
+        ws = []
+        for _ in range(2):
+            rho, Ux = rng.uniform(0.3, 2.0), rng.uniform(-1.0, 1.0)
+            ws.append([rho, rho * Ux, rho * Uy, rho * th / (G - 1) + 0.5 * rho * (Ux * Ux + Uy * Uy)])
+        ws = np.array(ws)
+        st = [(w[0] / (2 * math.pi * th), w[1] / w[0], th) for w in ws]
+        lo_b, hi_b = orc.velocity_box(cfg_of(orc, 2, (17, 17)), ws)
+        Xlo = _envelope_exact(st, (1, 1), lo_b[0], hi_b[0], False)
+        Xhi = _envelope_exact(st, (1, 1), lo_b[0], hi_b[0], True)
+        y0, y1 = lo_b[1], hi_b[1]
+        Y0, Y1, Y2 = gauss_moments_1d(1.0, Uy, th, y0, y1)
+        Yn = gauss_moments_1d(1.0, Uy, th, y0, min(0.0, y1))[1] if y0 < 0 else 0.0
+        Yp = Y1 - Yn
+        c = 0.5 * delta * th          # the internal-energy weight of both states
+        exact_lo = np.array([Xlo[0] * Y0, (Xhi[1] + Xlo[2]) * Y0, Xhi[0] * Yn + Xlo[0] * Yp,
+                             Xlo[3] * Y0 + Xlo[0] * 0.5 * Y2 + c * Xlo[0] * Y0])
+        exact_hi = np.array([Xhi[0] * Y0, (Xlo[1] + Xhi[2]) * Y0, Xlo[0] * Yn + Xhi[0] * Yp,
+                             Xhi[3] * Y0 + Xhi[0] * 0.5 * Y2 + c * Xhi[0] * Y0])
+        errs = []
+        for n in (513, 2049):
+            lo, hi = orc.bounds_stencil(cfg_of(orc, 2, (n, n)), ws)
+            sc = np.abs(exact_hi).max()
+            errs.append(max(np.abs(lo - exact_lo).max(), np.abs(hi - exact_hi).max()) / sc)
+        assert errs[1] < 5e-7, errs
         assert errs[1] < errs[0]
 
 
