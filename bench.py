@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2070.0
 # The envelope loop of the FP32 bounds kernel needs, per (stencil state, velocity node),
 # 2 products (g = Ex Ey and C g) and 4 comparisons (min and max of both): 6 FP32 lane-ops.
 # Its roofline is the measured rate of exactly that instruction mix in a register-only loop
-# (csrc/peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
+# (peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
 # lane-ops per clock per SM (packed multiplies and three-input min/max issue to two pipes
 # that overlap only in part), times 152 SMs and the 2070 MHz maximum clock.
 OPS_PER_STATE_NODE = 6.0
@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subworkloads", action="store_true",
+                    help="vortex only: skip the Sedov and batched sub-objects of the default line")
     ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2, 2: 2x4; -1: default)")
     return ap.parse_args()
 
@@ -275,21 +277,28 @@ def run_ours(args, rank, world):
         fp64 = {"value": E * 3 * k64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / k64}
         c64.close()
 
-    # end to end through the C-ABI with host buffers (pinned), per step: H2D, step, D2H
-    w_pin = torch.from_numpy(w0).pin_memory()
+    # end to end through the C-ABI with host buffers (pinned): an ensemble of independent states
+    # of the workload (the initial state with a seeded 1e-6 perturbation per member), one step
+    # each; every member pays its H2D copy and the D2H copy of its result, which
+    # kbl_run_host_ensemble overlaps with the neighbouring members' steps
+    M = 16
+    rng = np.random.default_rng(1)
+    ens = np.ascontiguousarray(np.stack([w0 * (1 + 1e-6 * rng.uniform(-1, 1, w0.shape)) for _ in range(M)]))
+    w_pin = torch.from_numpy(ens).pin_memory()
     out_pin = torch.empty_like(w_pin).pin_memory()
     win, wout = w_pin.numpy(), out_pin.numpy()
     ctx.set_time(0.0)
-    ctx.run_host(win, wout, 1, wl["cfl"])
-    ke = max(5, min(args.steps, 20))
+    ctx.run_host_ensemble(win, wout, 1, wl["cfl"])
+    ke = max(3, min(args.steps // 4, 8))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
-        ctx.run_host(win, wout, 1, wl["cfl"])
-    e2e_s = (time.perf_counter() - t0) / ke
+        ctx.run_host_ensemble(win, wout, 1, wl["cfl"])
+    e2e_s = (time.perf_counter() - t0) / (ke * M)
     nbytes = w0.nbytes
     e2e = {"value": E * 3 / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes}
+           "d2h_bytes_per_step": nbytes, "call": f"kbl_run_host_ensemble, {M} members x 1 step, pinned host buffers"}
+    ctx.set_time(0.0)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -305,12 +314,11 @@ def run_ours(args, rank, world):
 # ---------------------------------------------------------------------------
 # CPU checker timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, budget_s=12.0):
-    """Time the FP64 CPU checker on a bounded sample of the workload: a 16 x 16 block of
-    elements of the 2D mesh (periodic within the block), or the whole 1D mesh; single thread."""
+def _oracle_block(wl):
+    """The bounded CPU sample of a workload: a 16 x 16 block of elements of the 2D mesh
+    (periodic within the block), or the whole 1D mesh."""
     import oracle as orc
     from paper_2407_20966_gb300 import inputs
-    orc.build()
     cfg = orc.Config(dim=wl["dim"], p=wl["p"], nu=tuple(wl["nu"]), flux=wl.get("flux", 0))
     xi, _ = orc.gauss_legendre(wl["p"] + 1)
     mesh = wl["mesh"]
@@ -327,18 +335,57 @@ def oracle_sample(wl, budget_s=12.0):
         w = inputs.nodal_field(mesh, xi, wl["ic"])
         om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
         desc = "whole mesh"
-    w = np.ascontiguousarray(w)
+    return cfg, om, np.ascontiguousarray(w), desc
+
+
+def _oracle_steps(wl_name, budget_s, max_steps=200):
+    """Run the checker's SSP-RK3 steps on the bounded sample until the budget is spent; returns
+    (element-stages, seconds, steps, description).  Also the body of each parallel worker."""
+    import oracle as orc
+    wl = workload(wl_name)
+    cfg, om, w, desc = _oracle_block(wl)
     dt = orc.dt(cfg, om, w, wl["cfl"])
     n, t0 = 0, time.perf_counter()
     while True:
         w, _ = orc.ssprk3_step(cfg, om, w, dt)
         n += 1
         el = time.perf_counter() - t0
-        if el > budget_s or n >= 200:
+        if el > budget_s or n >= max_steps:
             break
-    value = om.n_elem * 3 * n / el
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} SSP-RK3 steps on a {desc} ({om.n_elem} elements), {el:.1f} s"}
+    return om.n_elem * 3 * n, el, n, f"{desc} ({om.n_elem} elements)"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(wl_name, budget_s=12.0, workers=None):
+    """Time the FP64 CPU checker, as it stands, on a bounded sample of the workload: one process
+    on one core, then (workers > 1) one independent replica of the same sample per host core in a
+    spawn-started process pool, the total over the wall time of the slowest."""
+    import oracle as orc
+    orc.build()
+    units, el, n, desc = _oracle_steps(wl_name, budget_s)
+    single = {"value": units / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{n} SSP-RK3 steps on a {desc}, {el:.1f} s"}
+    workers = host_cores() if workers is None else workers
+    if workers <= 1:
+        return single
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.starmap(_oracle_steps, [(wl_name, budget_s, 10 ** 9)] * workers)
+    wall = time.perf_counter() - t0
+    total = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return {"value": total / slowest, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{workers} independent replicas (one per host core, spawn pool), each "
+                      f"{res[0][2]}+ SSP-RK3 steps on a {desc} for {budget_s:.0f} s; {wall:.1f} s wall",
+            "single_core": single}
 
 
 def oracle_batch_sample(probs, budget_s=12.0):
@@ -375,7 +422,7 @@ def run_reference(args, rank):
         wl = {"name": f"batched: {args.batch_problems} four-quadrant Riemann problems (CPU sample)"}
     else:
         wl = workload(args.workload)
-        cb = oracle_sample(wl, budget_s=budget)
+        cb = oracle_sample(args.workload, budget_s=0.5 * budget)
     return {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -383,31 +430,41 @@ def run_reference(args, rank):
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_batched(args, rank, world):
+def batch_stencil_nodes(b):
+    """Sum over the batch's elements of |S| N_u: the (stencil state, velocity node) pairs of one
+    bounds launch, |S| = (p+1)^2 + 8 (p+1), N_u = 32 x 32."""
+    n = b.p.astype(np.int64) + 1
+    return int(((n * n + 8 * n) * b.n_elem.astype(np.int64)).sum() * 32 * 32)
+
+
+def run_batched(args, rank, world, steps=None, warmup=None):
     """The batched form: 4096 independent four-quadrant problems (seed 0x5EED), n x n elements with
     n ~ U{16..128}, orders P1..P4, 32 x 32 velocity grid, FP32-mixed, one persistent launch per
-    phase, one graph per step, launch shape from the autotuner."""
+    phase, one graph per step, launch shape from the autotuner.  The roofline is taken on a
+    bounds launch over the whole batch in the tuned shape (CUDA events on the batch's stream);
+    the e2e figure goes through kbl_batch_run_host (groups of problems whose copies overlap)."""
     import torch
     from paper_2407_20966_gb300 import build, inputs, kbl
 
     build.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    K = args.steps if steps is None else steps
+    W = args.warmup if warmup is None else warmup
     probs = inputs.four_quadrant_batch(0x5EED, args.batch_problems)
     b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs])
     E = int(b.elem_offsets[-1])
     w0 = inputs.batch_state(probs, b.nodes, b.state_offsets)
     wd = torch.from_numpy(w0).to(dev)
-    tune_ms, tune_cmp = b.autotune(wd, with_cmp=True)
+    b.autotune(wd)
     cfl = 0.05   # below the DG / SSP-RK3 limit of about 1 / (2p + 1) for every order in the batch
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, W)):
         b.step(wd, cfl)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     stream = torch.cuda.current_stream()
     l0 = b.launch_count()
-    K = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     with ClockSampler(dev.index) as clk:
         for k in range(K):
@@ -419,22 +476,28 @@ def run_batched(args, rank, world):
     launches = b.launch_count() - l0
     ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in evs), dev)
     value = job_throughput(E * 3 * K, ms, world)
-    # end to end: per step, H2D of the state from pinned memory, one step, D2H
+    # dominant kernel: the bounds phase over the whole batch, tuned shape, timed alone
+    bnd = torch.zeros(8 * E, dtype=torch.float64, device=dev)
+    b.bounds(wd, bnd)
+    bms = []
+    for _ in range(3):
+        b.bounds(wd, bnd)
+        bms.append(b.bounds_ms())
+    bounds_ms = float(np.mean(bms))
+    peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = OPS_PER_STATE_NODE * batch_stencil_nodes(b) / (bounds_ms * 1e-3) / 1e12
+    del bnd
+    # end to end: the whole batch from pinned host memory, one step, back to pinned host memory
     w_pin = torch.from_numpy(w0).pin_memory()
     out_pin = torch.empty_like(w_pin).pin_memory()
-    ke = max(2, min(K, 3))
+    b.run_host(w_pin.numpy(), out_pin.numpy(), 1, cfl)
+    ke = 2
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
-        wd.copy_(w_pin, non_blocking=True)
-        b.step(wd, cfl)
-        out_pin.copy_(wd, non_blocking=True)
-        torch.cuda.synchronize()
+        b.run_host(w_pin.numpy(), out_pin.numpy(), 1, cfl)
     e2e_s = (time.perf_counter() - t0) / ke
-    peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
-    # the autotuner counts 4 comparisons per (state, node); the roofline counts 6 lane-ops
-    achieved = tune_cmp * (OPS_PER_STATE_NODE / 4.0) / (tune_ms * 1e-3) / 1e12
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"batched: {b.P} four-quadrant Riemann problems, n x n elements n~U[16,128], "
@@ -443,15 +506,88 @@ def run_batched(args, rank, world):
                        "l2": "state (%.1f GB) larger than L2" % (w0.nbytes / 1e9),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": E * 3 * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": w0.nbytes,
-                    "d2h_bytes_per_step": w0.nbytes},
+                    "d2h_bytes_per_step": w0.nbytes,
+                    "call": "kbl_batch_run_host, 1 step, pinned host buffers, copies overlapped by problem groups"},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                          "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "kernel": "k_batch_bounds", "work": "6 lane-ops per (stencil state, velocity node)",
-                         "measured_on": "autotune sample (every 8th work item), best launch shape",
+                         "kernel": "k_batch_bounds", "bounds_ms_per_launch": round(bounds_ms, 3),
+                         "work": "6 lane-ops per (stencil state, velocity node)",
+                         "measured_on": "one bounds launch over the whole batch in the tuned launch shape",
                          "peak_source": PEAK_SOURCE},
             "clocks": clk.summary()}
+    b.close()
+    del wd, w_pin, out_pin
+    torch.cuda.empty_cache()
     return line, probs, b
+
+
+def run_sub_mesh(args, name, steps, warmup, dev):
+    """A second single-mesh workload timed like the headline (L2 flushed between steps, CUDA
+    events on the launching stream), with its own clock record and bounds roofline; FP64 beside."""
+    import torch
+    from paper_2407_20966_gb300 import inputs, kbl
+    wl = workload(name)
+    mesh = wl["mesh"]
+    E = mesh.n_elem
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def make_ctx(prec):
+        c = kbl.Context(dim=wl["dim"], p=wl["p"], nu=wl["nu"], precision=prec, flux=wl.get("flux", 0))
+        c.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+        return c
+
+    def timed(c, w, K, W):
+        c.set_time(0.0)
+        for _ in range(W):
+            c.step(w, wl["cfl"])
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            c.step(w, wl["cfl"])
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        c.check()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    ctx = make_ctx(kbl.FP32_MIXED)
+    w0 = inputs.nodal_field(mesh, ctx.operator(kbl.OP_NODES), wl["ic"])
+    wd = torch.from_numpy(w0).to(dev)
+    with ClockSampler(dev.index) as clk:
+        ms = timed(ctx, wd, steps, warmup)
+    wd.copy_(torch.from_numpy(w0))
+    wf = torch.zeros((ctx.nv, E, ctx.nfp), dtype=torch.float64, device=dev)
+    bnd = torch.zeros((2, ctx.nv, E), dtype=torch.float64, device=dev)
+    ctx.traces(wd, wf)
+    for _ in range(2):
+        ctx.bounds(wd, wf, bnd)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, z in evs:
+        flush.zero_()
+        a.record(stream)
+        ctx.bounds(wd, wf, bnd)
+        z.record(stream)
+    torch.cuda.synchronize()
+    bounds_ms = sum(a.elapsed_time(z) for a, z in evs) / len(evs)
+    achieved = OPS_PER_STATE_NODE * stencil_size(wl) * nu_total(wl) * E / (bounds_ms * 1e-3) / 1e12
+    peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    ctx.close()
+    c64 = make_ctx(kbl.FP64)
+    k64 = 2
+    ms64 = timed(c64, torch.from_numpy(w0).to(dev), k64, 1)
+    c64.close()
+    return {"workload": wl["name"], "elements": E, "value": E * 3 * steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "precision": "fp32",
+            "l2": "flushed between timed steps (256 MB write)",
+            "fp64": {"value": E * 3 * k64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / k64},
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                         "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_bounds2d_f32", "bounds_ms_per_launch": round(bounds_ms, 4),
+                         "work": "6 lane-ops per (stencil state, velocity node)", "peak_source": PEAK_SOURCE},
+            "clocks": clk.summary()}
 
 
 def run_adjoint(args, rank, world):
@@ -531,18 +667,22 @@ def run_adjoint(args, rank, world):
 
 
 def run_peaks():
-    """Compile and run csrc/peaks/kbl_fp32_peaks.cu: FP32 multiply and min/max rates, alone and
-    in the envelope pattern, per SM clock (clock64 inside each block); clocks sampled beside."""
+    """Compile and run the register-only rate probes under peaks/: FP32 multiply and min/max
+    rates, alone and in the envelope pattern (kbl_fp32_peaks.cu), then the integer and FP64
+    operations the other kernels spend (kbl_int_fp64_rates.cu), per SM clock (clock64 inside
+    each block); clocks sampled beside."""
     import subprocess
     here = os.path.dirname(os.path.abspath(__file__))
-    src = os.path.join(here, "paper_2407_20966_gb300", "csrc", "peaks", "kbl_fp32_peaks.cu")
-    exe = os.path.join(here, "paper_2407_20966_gb300", "_build", "kbl_fp32_peaks")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
-                   check=True)
-    with ClockSampler(0) as clk:
-        subprocess.run([exe], check=True)
-    print(json.dumps({"peaks_clocks": clk.summary()}))
+    out_dir = os.path.join(here, "paper_2407_20966_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    for name in ("kbl_fp32_peaks", "kbl_int_fp64_rates"):
+        src = os.path.join(here, "peaks", name + ".cu")
+        exe = os.path.join(out_dir, name)
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
+                       check=True)
+        with ClockSampler(0) as clk:
+            subprocess.run([exe], check=True)
+        print(json.dumps({"peaks": name, "clocks": clk.summary()}), flush=True)
 
 
 def main():
@@ -572,9 +712,20 @@ def main():
             print(json.dumps(line), flush=True)
     else:
         line, w0, wl = run_ours(args, rank, world)
+        if args.workload == "vortex" and not args.no_subworkloads:
+            # the larger configurations under the same clock: Sedov 512^2 P2 and the 4096-problem batch
+            import torch
+            dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+            line["sedov"] = run_sub_mesh(args, "sedov", steps=min(args.steps, 10), warmup=3, dev=dev)
+            bl, _, _ = run_batched(args, rank, world, steps=3, warmup=1)
+            line["batched"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "e2e",
+                                                  "gpu_launches", "roofline", "clocks")}
+            line["batched"]["workload"] = bl["config"]["workload"]
+            line["batched"]["elements"] = bl["config"]["elements"]
+            line["batched"]["tuning"] = bl["config"]["tuning"]
         if rank == 0:
             if not args.no_cpu_baseline:
-                line["cpu_baseline"] = oracle_sample(wl, budget_s=12.0)
+                line["cpu_baseline"] = oracle_sample(args.workload, budget_s=12.0)
             print(json.dumps(line), flush=True)
     if world > 1:
         import torch

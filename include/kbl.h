@@ -101,12 +101,20 @@ typedef struct {
 
 typedef struct kbl_ctx kbl_ctx;
 
+/* Counters of the limiter since the last read (kbl_read_counters clears them). */
 typedef struct {
     int32_t nonphysical;      /* a stencil state with rho <= 0 or P <= 0 was met */
     int32_t timeout;          /* a bounded device wait gave up (no kernel of this
                                  version waits on another; kept for the ABI) */
-    int64_t limited_elements; /* elements with alpha_min < 1 in the last stage run */
-    int64_t pressure_relimits;/* elements where the step of Eq. 48 was taken */
+    int64_t limited_elements; /* element-stages with alpha_min < 1 (Eq. 39) */
+    int64_t pressure_relimits;/* element-stages where the step of Eq. 48 was taken */
+    int64_t eps_rule_activations; /* (element, component) pairs where the epsilon rule stated
+                                 under Eq. 37 decided alpha_i (|min_V - mean| or
+                                 |max_V - mean| below eps) */
+    int64_t mean_outside_bounds;  /* (element, component) pairs whose element mean lay outside
+                                 [w_min, w_max] (the case the absolute values of Eq. 37 cover) */
+    int64_t alpha_hist[10];   /* limited element-stages by alpha_min: bin k counts
+                                 k/10 <= alpha_min < (k+1)/10 (their sum is limited_elements) */
 } kbl_counters;
 
 /* Fill cfg with the paper's defaults for dimension d and order p: gamma 1.4,
@@ -228,6 +236,17 @@ kbl_status kbl_time_sync(kbl_ctx* ctx, double* t_host);
 kbl_status kbl_run_host(kbl_ctx* ctx, const double* w_host_in, double* w_host_out,
                         int n_steps, double cfl);
 
+/* End-to-end runs of an ensemble of independent states on the context's mesh, from HOST
+ * buffers (pinned for the copies to overlap): member k's state w_host_in + k * nv * E * Ns
+ * takes n_steps steps of kbl_step, each member from the context's time at the call (with the
+ * end-time clip of kbl_step), and lands in w_host_out + k * nv * E * Ns (the output may alias the
+ * input).  Two device copies of the state alternate: member k+1's host-to-device copy and member
+ * k-1's device-to-host copy run while member k steps (one cudaMemcpyAsync per member and
+ * direction, on two copy streams of the context).  The first call allocates the second device
+ * copy.  Afterwards the context's time is the last member's end time.  Synchronous. */
+kbl_status kbl_run_host_ensemble(kbl_ctx* ctx, int n_members, const double* w_host_in, double* w_host_out,
+                                 int n_steps, double cfl);
+
 /* Wait for the context's stream and report device-side flags (then clear
  * them): KBL_ENONPHYSICAL if a non-physical state was met. */
 kbl_status kbl_check(kbl_ctx* ctx);
@@ -279,6 +298,34 @@ kbl_status kbl_batch_layout(const kbl_batch* b, int64_t* state_offsets, int64_t*
 kbl_status kbl_batch_nodes(const kbl_batch* b, int p, double* host_out, int n);
 /* One SSP-RK3 step of every problem, each with dt = cfl * its own CFL limit. */
 kbl_status kbl_batch_step(kbl_batch* b, double* w, double cfl);
+/* The phases of one batched stage as separate calls, running the persistent kernels of
+ * kbl_batch_step: for checking a stage of every problem against kbl_traces + kbl_bounds,
+ * kbl_rhs and kbl_stage on identical inputs.  All arrays DEVICE, in the concatenated
+ * layout: w, ws, wn, R, wout like the state (problem i at state_offsets[i]); bnd with
+ * problem i's bounds [2][4][E_i] at 8 * elem_offsets[i]; dt_dev[n_problems].
+ * kbl_batch_bounds: face traces (batch scratch) then the kinetic bounds of Sec. 3.3-3.8.
+ * kbl_batch_rhs: face traces then the FR residual of Sec. 2.3 with the configured flux.
+ * kbl_batch_stage: wout = limit(a_s wn + b_s (ws + dt R), bnd) (Sec. 5 SSP-RK3, Eq. 37-39,
+ * Eq. 47-49) for stage st in {0,1,2}; wout may alias wn.  Asynchronous on the batch's
+ * stream; KBL_EINVAL for a null array or a bad stage. */
+kbl_status kbl_batch_bounds(kbl_batch* b, const double* w, double* bnd);
+kbl_status kbl_batch_rhs(kbl_batch* b, const double* w, double* R);
+kbl_status kbl_batch_stage(kbl_batch* b, int st, const double* wn, const double* ws, const double* R,
+                           const double* bnd, const double* dt_dev, double* wout);
+/* End-to-end run on HOST buffers (pinned for the copies to overlap): the batch state
+ * w_host_in (concatenated layout) is copied to the batch's own device copy, every problem takes
+ * n_steps steps of kbl_batch_step, and the result is copied to w_host_out (may alias
+ * w_host_in).  The problems are cut into up to 8 groups of consecutive problems of similar state
+ * size, each with its own work items and step graph: group g's host-to-device copy, group
+ * g-1's steps and group g-2's device-to-host copy run at the same time on three streams (one
+ * cudaMemcpyAsync per group and direction).  The first call allocates the device copy (one state)
+ * and the groups.  Synchronous; the batch's scratch, per-problem time steps and clocks are those
+ * of kbl_batch_step. */
+kbl_status kbl_batch_run_host(kbl_batch* b, const double* w_host_in, double* w_host_out, int n_steps, double cfl);
+/* Device time of the bounds launch of the last kbl_batch_bounds call (CUDA events on the batch's
+ * stream around that launch alone; synchronous): for measuring the dominant phase in the
+ * launch shape the step graph uses.  KBL_ESTATE before any kbl_batch_bounds call. */
+kbl_status kbl_batch_bounds_ms(kbl_batch* b, double* ms);
 /* Per-problem time step of the last step (HOST, n_problems values; synchronous). */
 kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host);
 /* Time the bounds phase on state w for every combination of thread tile

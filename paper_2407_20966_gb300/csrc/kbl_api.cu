@@ -191,9 +191,17 @@ kbl_status after_launch(kbl_ctx* c, int n, const char* where)
     return KBL_OK;
 }
 
+void drop_graphs(kbl_ctx* c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph2) cudaGraphExecDestroy(c->graph2);
+    c->graph = c->graph2 = nullptr;
+    c->graph_w = c->graph2_w = nullptr;
+}
+
 void free_mesh(kbl_ctx* c)
 {
-    double** bufs[] = {&c->d_h, &c->d_bc, &c->d_wf, &c->d_R, &c->d_bnd, &c->d_wa, &c->d_wb, &c->d_whost};
+    double** bufs[] = {&c->d_h, &c->d_bc, &c->d_wf, &c->d_R, &c->d_bnd, &c->d_wa, &c->d_wb, &c->d_whost, &c->d_whost2};
     for (double** b : bufs) {
         if (*b) cudaFree(*b);
         *b = nullptr;
@@ -201,9 +209,7 @@ void free_mesh(kbl_ctx* c)
     if (c->d_nbr) cudaFree(c->d_nbr);
     c->d_nbr = nullptr;
     kbl_adjoint_release(c);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-    c->graph_w = nullptr;
+    drop_graphs(c);
     c->mesh_ready = false;
 }
 
@@ -246,6 +252,29 @@ int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s)
 
 void kbl_build_fr_ops(int p, FrOps& o) { build_ops(p, o); }
 
+bool kbl_config_valid(const kbl_config* cfg)
+{
+    if (!cfg) return false;
+    if (cfg->dim != 1 && cfg->dim != 2) return false;
+    if (cfg->p < 1 || cfg->p > KBL_PMAX) return false;
+    if (cfg->dim == 2) {
+        const int nx = cfg->nu[0];
+        if (cfg->nu[1] != nx || nx < 2 || nx > 64) return false;
+    } else if (cfg->nu[0] < 2 || cfg->nu[0] > 4096) {
+        return false;
+    }
+    if (!(cfg->gamma > 1.0) || !(cfg->k > 0.0) || !(cfg->r_fac >= 0.0 && cfg->r_fac < 1.0) ||
+        !(cfg->eps >= 0.0) || !(cfg->rho_floor >= 0.0) || !(cfg->p_floor >= 0.0))
+        return false;
+    if (cfg->eps_rule != 0 && cfg->eps_rule != 1) return false;
+    if (cfg->precision != KBL_FP64 && cfg->precision != KBL_FP32_MIXED) return false;
+    if (cfg->uncoupled != 0 && cfg->uncoupled != 1) return false;
+    if (cfg->flux < 0 || cfg->flux > 2) return false;
+    if (cfg->quadrature != 0 && cfg->quadrature != 1) return false;
+    if (cfg->quadrature == 1 && (cfg->nu[0] < 3 || (cfg->nu[0] - 1) % 2 != 0)) return false;
+    return true;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -276,23 +305,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
 {
     if (!out) return KBL_EINVAL;
     *out = nullptr;
-    if (!cfg) return KBL_EINVAL;
-    if (cfg->dim != 1 && cfg->dim != 2) return KBL_EINVAL;
-    if (cfg->p < 1 || cfg->p > KBL_PMAX) return KBL_EINVAL;
-    if (cfg->dim == 2) {
-        const int nx = cfg->nu[0];
-        if (cfg->nu[1] != nx || nx < 2 || nx > 64) return KBL_EINVAL;
-    } else if (cfg->nu[0] < 2 || cfg->nu[0] > 4096) {
-        return KBL_EINVAL;
-    }
-    if (!(cfg->gamma > 1.0) || !(cfg->k > 0.0) || !(cfg->r_fac >= 0.0 && cfg->r_fac < 1.0) ||
-        !(cfg->eps >= 0.0) || !(cfg->rho_floor >= 0.0) || !(cfg->p_floor >= 0.0))
-        return KBL_EINVAL;
-    if (cfg->precision != KBL_FP64 && cfg->precision != KBL_FP32_MIXED) return KBL_EINVAL;
-    if (cfg->uncoupled != 0 && cfg->uncoupled != 1) return KBL_EINVAL;
-    if (cfg->flux < 0 || cfg->flux > 2) return KBL_EINVAL;
-    if (cfg->quadrature != 0 && cfg->quadrature != 1) return KBL_EINVAL;
-    if (cfg->quadrature == 1 && (cfg->nu[0] < 3 || (cfg->nu[0] - 1) % 2 != 0)) return KBL_EINVAL;
+    if (!kbl_config_valid(cfg)) return KBL_EINVAL;
     kbl_ctx* c = new (std::nothrow) kbl_ctx();
     if (!c) return KBL_ENOMEM;
     c->cfg = *cfg;
@@ -318,7 +331,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     c->nfp = cfg->dim == 1 ? 2 : 4 * n;
     c->nsten = c->ns + 2 * c->nfp;
     cudaError_t e;
-    if ((e = dalloc(&c->d_scal, 3)) != cudaSuccess || (e = dalloc(&c->d_dtbits, 1)) != cudaSuccess ||
+    if ((e = dalloc(&c->d_scal, 4)) != cudaSuccess || (e = dalloc(&c->d_dtbits, 1)) != cudaSuccess ||
         (e = dalloc(&c->d_flags, 1)) != cudaSuccess) {
         kbl_destroy(c);
         return KBL_ECUDA;
@@ -340,7 +353,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         c->phys.qw = c->d_qw;
         c->phys.qwf = reinterpret_cast<const float*>(c->d_qw + nq);
     }
-    const double scal[3] = {0.0, 0.0, INFINITY};
+    const double scal[4] = {0.0, 0.0, INFINITY, 0.0};
     if ((e = cudaMemcpy(c->d_scal, scal, sizeof(scal), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(c->d_flags, 0, sizeof(DevFlags))) != cudaSuccess) {
         kbl_destroy(c);
@@ -372,6 +385,13 @@ kbl_status kbl_destroy(kbl_ctx* c)
     if (c->d_dtbits) cudaFree(c->d_dtbits);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->d_qw) cudaFree(c->d_qw);
+    if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+    if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+    for (int k = 0; k < 2; k++) {
+        if (c->ev_h2d[k]) cudaEventDestroy(c->ev_h2d[k]);
+        if (c->ev_step[k]) cudaEventDestroy(c->ev_step[k]);
+        if (c->ev_d2h[k]) cudaEventDestroy(c->ev_d2h[k]);
+    }
     delete c;
     return KBL_OK;
 }
@@ -556,9 +576,21 @@ kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
     if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
     if ((c->E > 0 && !w) || !(cfl > 0.0)) return fail(c, KBL_EINVAL, "bad argument");
     if (c->E == 0) return KBL_OK;
+    if (c->graph2 && c->graph2_w == w && c->graph2_cfl == cfl) {   // most recently used slot first
+        std::swap(c->graph, c->graph2);
+        std::swap(c->graph_w, c->graph2_w);
+        std::swap(c->graph_cfl, c->graph2_cfl);
+        std::swap(c->graph_kernels, c->graph2_kernels);
+    }
     if (!(c->graph && c->graph_w == w && c->graph_cfl == cfl)) {
-        if (c->graph) cudaGraphExecDestroy(c->graph);
+        // the new graph takes the first slot; the previous one moves to the second
+        if (c->graph2) cudaGraphExecDestroy(c->graph2);
+        c->graph2 = c->graph;
+        c->graph2_w = c->graph_w;
+        c->graph2_cfl = c->graph_cfl;
+        c->graph2_kernels = c->graph_kernels;
         c->graph = nullptr;
+        c->graph_w = nullptr;
         cudaStream_t cap;
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
@@ -609,6 +641,61 @@ kbl_status kbl_run_host(kbl_ctx* c, const double* win, double* wout, int n_steps
     return KBL_OK;
 }
 
+kbl_status kbl_run_host_ensemble(kbl_ctx* c, int n_members, const double* win, double* wout, int n_steps,
+                                 double cfl)
+{
+    if (!ready(c)) return fail(c, KBL_ESTATE, "no mesh");
+    if (n_members < 0 || n_steps < 0 || !(cfl > 0.0) || (c->E > 0 && n_members > 0 && (!win || !wout)))
+        return fail(c, KBL_EINVAL, "bad argument");
+    if (c->E == 0 || n_members == 0) return KBL_OK;
+    const size_t count = (size_t)c->E * c->nv * c->ns;
+    cudaError_t e = cudaSuccess;
+    if (!c->d_whost2) e = dalloc(&c->d_whost2, count);
+    if (e == cudaSuccess && !c->s_h2d) e = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->s_d2h) e = cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+        if (!c->ev_h2d[k]) e = cudaEventCreateWithFlags(&c->ev_h2d[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !c->ev_step[k]) e = cudaEventCreateWithFlags(&c->ev_step[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !c->ev_d2h[k]) e = cudaEventCreateWithFlags(&c->ev_d2h[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "ensemble set-up");
+    double* buf[2] = {c->d_whost, c->d_whost2};
+    // every member starts from the context's current time: keep it in scal[3]; the copies wait
+    // for the work queued on the context's stream before this call
+    e = cudaMemcpyAsync(c->d_scal + 3, c->d_scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_step[1], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_h2d, c->ev_step[1], 0);
+    for (int k = 0; k < n_members && e == cudaSuccess; k++) {
+        const int b = k & 1;
+        const double* in = win + (size_t)k * count;
+        double* out = wout + (size_t)k * count;
+        if (k >= 2) e = cudaStreamWaitEvent(c->s_h2d, c->ev_d2h[b], 0);   // member k-2 has left buf[b]
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf[b], in, count * sizeof(double), cudaMemcpyHostToDevice, c->s_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_h2d[b], c->s_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_h2d[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_scal + 1, c->d_scal + 3, sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) break;
+        for (int i = 0; i < n_steps; i++) {
+            const kbl_status st = kbl_step(c, buf[b], cfl);
+            if (st != KBL_OK) {
+                cudaStreamSynchronize(c->s_h2d);
+                cudaStreamSynchronize(c->s_d2h);
+                return st;
+            }
+        }
+        e = cudaEventRecord(c->ev_step[b], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_d2h, c->ev_step[b], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf[b], count * sizeof(double), cudaMemcpyDeviceToHost, c->s_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_d2h[b], c->s_d2h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_d2h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_h2d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ensemble run");
+    return KBL_OK;
+}
+
 kbl_status kbl_read_counters(kbl_ctx* c, kbl_counters* out)
 {
     if (!c || !out) return KBL_EINVAL;
@@ -621,6 +708,9 @@ kbl_status kbl_read_counters(kbl_ctx* c, kbl_counters* out)
     out->timeout = f.timeout;
     out->limited_elements = (int64_t)f.limited;
     out->pressure_relimits = (int64_t)f.prelimit;
+    out->eps_rule_activations = (int64_t)f.eps_rule;
+    out->mean_outside_bounds = (int64_t)f.mean_outside;
+    for (int k = 0; k < KBL_ALPHA_BINS; k++) out->alpha_hist[k] = (int64_t)f.alpha_hist[k];
     if (f.timeout) return fail(c, KBL_ETIMEOUT, "a bounded device wait gave up");
     if (f.nonphysical) return fail(c, KBL_ENONPHYSICAL, "non-physical stencil state (rho <= 0 or P <= 0)");
     return KBL_OK;
@@ -631,9 +721,7 @@ kbl_status kbl_set_tuning(kbl_ctx* c, int key, int value)
     if (!c) return KBL_EINVAL;
     if (key != KBL_TUNE_BOUNDS_TILE || value < 0 || value > 2) return fail(c, KBL_EINVAL, "unknown tuning knob or value");
     c->bounds_tile = value;
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-    c->graph_w = nullptr;
+    drop_graphs(c);
     return KBL_OK;
 }
 

@@ -31,6 +31,7 @@ constexpr int NX_B = 32;         // velocity points per axis supported by the ba
 constexpr int NTB = 256;         // threads per block of the FR / limiter phases
 constexpr int FR_CHUNK = 256;    // elements per work item of the FR / limiter phases
 constexpr int NCOUNTERS = 16;    // one work counter per persistent launch of a step
+#define KBL_BATCH_HOST_GROUPS 8  // problem groups of kbl_batch_run_host (copies overlap steps)
 
 struct ProbDesc {
     long long woff;     // state offset (doubles)
@@ -367,6 +368,27 @@ struct kbl_batch {
     int graph_kernels = 0;
     int64_t launches = 0;
     std::string err;
+    // kbl_batch_run_host: the library's device copy of the state and the problems cut into
+    // groups of consecutive problems, each with its own work items, counters and step graph, so
+    // that the copies of one group overlap the step of another
+    struct Group {
+        int p0 = 0, p1 = 0;
+        WorkItem* fr = nullptr;
+        int n_fr = 0;
+        WorkItem* bi = nullptr;
+        int n_bi = 0, chunk = 0;
+        cudaGraphExec_t graph = nullptr;
+        double cfl = 0.0;
+        int kernels = 0;
+        cudaEvent_t h2d = nullptr, done = nullptr;
+    };
+    std::vector<Group> groups;
+    double* d_whost = nullptr;
+    unsigned* d_gcounters = nullptr;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    // timing of the bounds launch of kbl_batch_bounds (kbl_batch_bounds_ms)
+    cudaEvent_t tb0 = nullptr, tb1 = nullptr;
+    bool tb_valid = false;
 };
 
 namespace {
@@ -382,10 +404,11 @@ size_t bounds_smem(int tile)
     return tile ? sizeof(BoundsUnion<2>) : sizeof(BoundsUnion<0>);
 }
 
-std::vector<WorkItem> make_items(const std::vector<ProbDesc>& probs, int chunk)
+std::vector<WorkItem> make_items(const std::vector<ProbDesc>& probs, int chunk, int p0 = 0, int p1 = -1)
 {
     std::vector<WorkItem> items;
-    for (int pi = 0; pi < (int)probs.size(); pi++)
+    if (p1 < 0) p1 = (int)probs.size();
+    for (int pi = p0; pi < p1; pi++)
         for (int e0 = 0; e0 < probs[pi].E; e0 += chunk) items.push_back({pi, e0, std::min(chunk, probs[pi].E - e0)});
     // expensive first: higher order, then fuller items
     std::stable_sort(items.begin(), items.end(), [&](const WorkItem& a, const WorkItem& b) {
@@ -419,19 +442,19 @@ BatchDev dev_of(const kbl_batch* b)
 
 int grid_of(const kbl_batch* b, int per_sm) { return std::max(1, b->nsm * std::max(1, per_sm)); }
 
-// Bounds phase on (w, wf) -> bnd with the current launch shape; counter slot `slot`.
-int launch_bounds_phase(kbl_batch* b, const double* w, const double* wf, double* bnd, int slot, cudaStream_t s,
-                        const WorkItem* items, int n_items)
+// Bounds phase on (w, wf) -> bnd with the current launch shape; work counter `counter`.
+int launch_bounds_phase(kbl_batch* b, const double* w, const double* wf, double* bnd, unsigned* counter,
+                        cudaStream_t s, const WorkItem* items, int n_items)
 {
     const BatchDev bd = dev_of(b);
     const size_t smem = bounds_smem(b->tile);
     const int grid = grid_of(b, b->blocks_per_sm);
     if (b->tile)
-        k_batch_bounds<2><<<grid, B2f32<NX_B, 2>::NT, smem, s>>>(bd, items, n_items, b->d_counters + slot, b->phys,
-                                                                  w, wf, bnd, b->d_flags);
+        k_batch_bounds<2><<<grid, B2f32<NX_B, 2>::NT, smem, s>>>(bd, items, n_items, counter, b->phys, w, wf, bnd,
+                                                                  b->d_flags);
     else
-        k_batch_bounds<0><<<grid, B2f32<NX_B, 0>::NT, smem, s>>>(bd, items, n_items, b->d_counters + slot, b->phys,
-                                                                  w, wf, bnd, b->d_flags);
+        k_batch_bounds<0><<<grid, B2f32<NX_B, 0>::NT, smem, s>>>(bd, items, n_items, counter, b->phys, w, wf, bnd,
+                                                                  b->d_flags);
     return 1;
 }
 
@@ -442,38 +465,88 @@ int fr_blocks_per_sm(const void* fn, size_t smem)
     return n;
 }
 
-// One SSP-RK3 step of every problem on stream s (also used for capture).
-int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s)
+// The work of one step: FR and bounds work items of problems [p0, p1) and the counter slots of
+// its persistent launches.
+struct ItemSet {
+    const WorkItem* fr;
+    int n_fr;
+    const WorkItem* bi;
+    int n_bi;
+    unsigned* counters;
+    int p0, p1;
+};
+
+ItemSet all_items(const kbl_batch* b)
+{
+    return {b->d_fr_items, b->n_fr_items, b->d_b_items, b->n_b_items, b->d_counters, 0, b->P};
+}
+
+// One SSP-RK3 step of the problems of `is` on stream s (also used for capture).
+int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const ItemSet& is)
 {
     const BatchDev bd = dev_of(b);
+    const int np = is.p1 - is.p0;
     int n = 0;
-    cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
-    cudaMemsetAsync(b->d_dtbits, 0x7f, (size_t)b->P * sizeof(unsigned long long), s);
+    cudaMemsetAsync(is.counters, 0, NCOUNTERS * sizeof(unsigned), s);
+    cudaMemsetAsync(b->d_dtbits + is.p0, 0x7f, (size_t)np * sizeof(unsigned long long), s);
     const int g_tr = grid_of(b, fr_blocks_per_sm((const void*)k_batch_traces, 0));
     const int g_rhs = grid_of(b, fr_blocks_per_sm((const void*)k_batch_rhs, 0));
     const int g_st = grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion)));
     const int g_dt = grid_of(b, fr_blocks_per_sm((const void*)k_batch_dt, 0));
-    k_batch_dt<<<g_dt, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 0, b->phys.gamma, cfl, w,
-                                    b->d_dtbits);
-    k_batch_dt_finalize<<<(b->P + 255) / 256, 256, 0, s>>>(b->d_dtbits, b->d_dt, b->d_t, b->P);
+    k_batch_dt<<<g_dt, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 0, b->phys.gamma, cfl, w, b->d_dtbits);
+    k_batch_dt_finalize<<<(np + 255) / 256, 256, 0, s>>>(b->d_dtbits + is.p0, b->d_dt + is.p0, b->d_t + is.p0, np);
     n += 2;
     const double* wn = w;
     const double* ws = w;
     double* outs[3] = {b->d_wa, b->d_wb, w};
     for (int st = 0; st < 3; st++) {
-        k_batch_traces<<<g_tr, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 1 + 4 * st, b->ops, ws,
-                                            b->d_wf);
-        n += launch_bounds_phase(b, ws, b->d_wf, b->d_bnd, 2 + 4 * st, s, b->d_b_items, b->n_b_items);
-        k_batch_rhs<<<g_rhs, NTB, 0, s>>>(bd, b->d_fr_items, b->n_fr_items, b->d_counters + 3 + 4 * st, b->ops,
-                                          b->phys.gamma, b->phys.flux, ws, b->d_wf, b->d_R);
-        k_batch_stage<<<g_st, NTB, sizeof(LimUnion), s>>>(bd, b->d_fr_items, b->n_fr_items,
-                                                          b->d_counters + 4 + 4 * st, b->ops, b->phys, st, wn, ws,
-                                                          b->d_R, b->d_bnd, b->d_dt, outs[st], b->d_flags);
+        k_batch_traces<<<g_tr, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 1 + 4 * st, b->ops, ws, b->d_wf);
+        n += launch_bounds_phase(b, ws, b->d_wf, b->d_bnd, is.counters + 2 + 4 * st, s, is.bi, is.n_bi);
+        k_batch_rhs<<<g_rhs, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 3 + 4 * st, b->ops, b->phys.gamma,
+                                          b->phys.flux, ws, b->d_wf, b->d_R);
+        k_batch_stage<<<g_st, NTB, sizeof(LimUnion), s>>>(bd, is.fr, is.n_fr, is.counters + 4 + 4 * st, b->ops,
+                                                          b->phys, st, wn, ws, b->d_R, b->d_bnd, b->d_dt, outs[st],
+                                                          b->d_flags);
         n += 3;
         ws = outs[st];
     }
-    k_batch_time_advance<<<(b->P + 255) / 256, 256, 0, s>>>(b->d_dt, b->d_t, b->P);
+    k_batch_time_advance<<<(np + 255) / 256, 256, 0, s>>>(b->d_dt + is.p0, b->d_t + is.p0, np);
     return n + 1;
+}
+
+// Capture one step of `is` on state w as a graph.
+cudaError_t capture_step(kbl_batch* b, double* w, double cfl, const ItemSet& is, cudaGraphExec_t* out, int* kernels)
+{
+    *out = nullptr;
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return e;
+    }
+    *kernels = issue_batch_step(b, w, cfl, cap, is);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) *out = nullptr;
+    return e;
+}
+
+void drop_groups(kbl_batch* b)
+{
+    for (auto& g : b->groups) {
+        if (g.graph) cudaGraphExecDestroy(g.graph);
+        if (g.fr) cudaFree(g.fr);
+        if (g.bi) cudaFree(g.bi);
+        if (g.h2d) cudaEventDestroy(g.h2d);
+        if (g.done) cudaEventDestroy(g.done);
+    }
+    b->groups.clear();
 }
 
 void drop_graph(kbl_batch* b)
@@ -493,6 +566,7 @@ cudaError_t set_bounds_shape(kbl_batch* b, int tile, int chunk, int per_sm)
         if (e != cudaSuccess) return e;
     }
     drop_graph(b);
+    drop_groups(b);
     return cudaSuccess;
 }
 
@@ -633,6 +707,13 @@ kbl_status kbl_batch_destroy(kbl_batch* b)
 {
     if (!b) return KBL_EINVAL;
     drop_graph(b);
+    drop_groups(b);
+    if (b->d_whost) cudaFree(b->d_whost);
+    if (b->d_gcounters) cudaFree(b->d_gcounters);
+    if (b->s_h2d) cudaStreamDestroy(b->s_h2d);
+    if (b->s_d2h) cudaStreamDestroy(b->s_d2h);
+    if (b->tb0) cudaEventDestroy(b->tb0);
+    if (b->tb1) cudaEventDestroy(b->tb1);
     void* ptrs[] = {b->d_probs, b->d_nbr, b->d_h, b->d_bc, b->d_wf, b->d_R, b->d_bnd, b->d_wa, b->d_wb, b->d_dt,
                     b->d_t, b->d_dtbits, b->d_flags, b->d_counters, b->d_fr_items, b->d_b_items};
     for (void* q : ptrs)
@@ -668,25 +749,9 @@ kbl_status kbl_batch_step(kbl_batch* b, double* w, double cfl)
     if (!b || !w || !(cfl > 0.0)) return bfail(b, KBL_EINVAL, "bad argument");
     if (!(b->graph && b->graph_w == w && b->graph_cfl == cfl)) {
         drop_graph(b);
-        cudaStream_t cap;
-        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
-        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) {
-            cudaStreamDestroy(cap);
-            return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
-        }
-        const int n = issue_batch_step(b, w, cfl, cap);
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(cap, &g);
-        cudaStreamDestroy(cap);
+        int n = 0;
+        const cudaError_t e = capture_step(b, w, cfl, all_items(b), &b->graph, &n);
         if (e != cudaSuccess) return bfail(b, KBL_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&b->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            b->graph = nullptr;
-            return bfail(b, KBL_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-        }
         b->graph_w = w;
         b->graph_cfl = cfl;
         b->graph_kernels = n;
@@ -695,6 +760,163 @@ kbl_status kbl_batch_step(kbl_batch* b, double* w, double cfl)
     if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
     b->launches += b->graph_kernels;
     return KBL_OK;
+}
+
+// Groups of consecutive problems of roughly equal state size for kbl_batch_run_host, with their
+// own work items (bounds items at the current chunk size) and events.
+cudaError_t build_groups(kbl_batch* b)
+{
+    if (!b->groups.empty() && b->groups[0].chunk == b->chunk) return cudaSuccess;
+    drop_groups(b);
+    const int G = std::min(b->P, KBL_BATCH_HOST_GROUPS);
+    int p0 = 0;
+    for (int g = 0; g < G; g++) {
+        // end of group g: the first problem whose state ends at or past (g + 1) / G of the total
+        int p1 = p0 + 1;
+        const double target = (double)b->W_total * (g + 1) / G;
+        while (p1 < b->P && (double)(b->probs[p1 - 1].woff + 4LL * b->probs[p1 - 1].E * (b->probs[p1 - 1].p + 1) *
+                                               (b->probs[p1 - 1].p + 1)) < target)
+            p1++;
+        if (g == G - 1) p1 = b->P;
+        p1 = std::min(p1, b->P - (G - 1 - g));   // leave a problem for every later group
+        kbl_batch::Group gr;
+        gr.p0 = p0;
+        gr.p1 = p1;
+        gr.chunk = b->chunk;
+        cudaError_t e = upload_items(b, make_items(b->probs, FR_CHUNK, p0, p1), &gr.fr, &gr.n_fr);
+        if (e == cudaSuccess) e = upload_items(b, make_items(b->probs, b->chunk, p0, p1), &gr.bi, &gr.n_bi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gr.h2d, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&gr.done, cudaEventDisableTiming);
+        b->groups.push_back(gr);
+        if (e != cudaSuccess) {
+            drop_groups(b);
+            return e;
+        }
+        p0 = p1;
+    }
+    return cudaSuccess;
+}
+
+kbl_status kbl_batch_run_host(kbl_batch* b, const double* win, double* wout, int n_steps, double cfl)
+{
+    if (!b) return KBL_EINVAL;
+    if (!win || !wout || n_steps < 0 || !(cfl > 0.0)) return bfail(b, KBL_EINVAL, "bad argument");
+    cudaError_t e = cudaSuccess;
+    if (!b->d_whost) e = cudaMalloc((void**)&b->d_whost, std::max<long long>(b->W_total, 2) * sizeof(double));
+    if (e == cudaSuccess && !b->d_gcounters)
+        e = cudaMalloc((void**)&b->d_gcounters, (size_t)NCOUNTERS * KBL_BATCH_HOST_GROUPS * sizeof(unsigned));
+    if (e == cudaSuccess && !b->s_h2d) e = cudaStreamCreateWithFlags(&b->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !b->s_d2h) e = cudaStreamCreateWithFlags(&b->s_d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = build_groups(b);
+    if (e != cudaSuccess) return bfail(b, e == cudaErrorMemoryAllocation ? KBL_ENOMEM : KBL_ECUDA, cudaGetErrorString(e));
+    // the copies wait for whatever the caller queued on the batch's stream before this call
+    cudaEvent_t start = nullptr;
+    if ((e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(start, b->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(b->s_h2d, start, 0)) != cudaSuccess) {
+        if (start) cudaEventDestroy(start);
+        return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+    }
+    cudaEventDestroy(start);
+    const int G = (int)b->groups.size();
+    for (int g = 0; g < G && e == cudaSuccess; g++) {
+        auto& gr = b->groups[g];
+        const long long a = b->probs[gr.p0].woff;
+        const long long z = gr.p1 < b->P ? b->probs[gr.p1].woff : b->W_total;
+        e = cudaMemcpyAsync(b->d_whost + a, win + a, (size_t)(z - a) * sizeof(double), cudaMemcpyHostToDevice, b->s_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(gr.h2d, b->s_h2d);
+    }
+    for (int g = 0; g < G && e == cudaSuccess; g++) {
+        auto& gr = b->groups[g];
+        if (!(gr.graph && gr.cfl == cfl)) {
+            if (gr.graph) cudaGraphExecDestroy(gr.graph);
+            unsigned* cnt = b->d_gcounters + (size_t)NCOUNTERS * g;
+            e = capture_step(b, b->d_whost, cfl, {gr.fr, gr.n_fr, gr.bi, gr.n_bi, cnt, gr.p0, gr.p1}, &gr.graph,
+                             &gr.kernels);
+            gr.cfl = cfl;
+            if (e != cudaSuccess) break;
+        }
+        e = cudaStreamWaitEvent(b->stream, gr.h2d, 0);
+        for (int k = 0; k < n_steps && e == cudaSuccess; k++) {
+            e = cudaGraphLaunch(gr.graph, b->stream);
+            b->launches += gr.kernels;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(gr.done, b->stream);
+    }
+    for (int g = 0; g < G && e == cudaSuccess; g++) {
+        auto& gr = b->groups[g];
+        const long long a = b->probs[gr.p0].woff;
+        const long long z = gr.p1 < b->P ? b->probs[gr.p1].woff : b->W_total;
+        e = cudaStreamWaitEvent(b->s_d2h, gr.done, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(wout + a, b->d_whost + a, (size_t)(z - a) * sizeof(double), cudaMemcpyDeviceToHost,
+                                b->s_d2h);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s_d2h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? KBL_OK : bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_batch_bounds_ms(kbl_batch* b, double* ms)
+{
+    if (!b || !ms) return KBL_EINVAL;
+    if (!b->tb_valid) return bfail(b, KBL_ESTATE, "no kbl_batch_bounds call yet");
+    float f = 0.0f;
+    cudaError_t e = cudaEventSynchronize(b->tb1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&f, b->tb0, b->tb1);
+    if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+    *ms = f;
+    return KBL_OK;
+}
+
+// The phases of one batched stage as separate calls (the same persistent kernels the step
+// graph runs), for checking a stage against the single-problem calls on identical inputs.
+kbl_status kbl_batch_bounds(kbl_batch* b, const double* w, double* bnd)
+{
+    if (!b || !w || !bnd) return bfail(b, KBL_EINVAL, "null array");
+    cudaStream_t s = b->stream;
+    cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
+    k_batch_traces<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_traces, 0)), NTB, 0, s>>>(
+        dev_of(b), b->d_fr_items, b->n_fr_items, b->d_counters + 1, b->ops, w, b->d_wf);
+    if (!b->tb0) cudaEventCreate(&b->tb0);
+    if (!b->tb1) cudaEventCreate(&b->tb1);
+    cudaEventRecord(b->tb0, s);
+    launch_bounds_phase(b, w, b->d_wf, bnd, b->d_counters + 2, s, b->d_b_items, b->n_b_items);
+    cudaEventRecord(b->tb1, s);
+    b->tb_valid = true;
+    b->launches += 2;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_batch_rhs(kbl_batch* b, const double* w, double* R)
+{
+    if (!b || !w || !R) return bfail(b, KBL_EINVAL, "null array");
+    cudaStream_t s = b->stream;
+    const BatchDev bd = dev_of(b);
+    cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
+    k_batch_traces<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_traces, 0)), NTB, 0, s>>>(
+        bd, b->d_fr_items, b->n_fr_items, b->d_counters + 1, b->ops, w, b->d_wf);
+    k_batch_rhs<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_rhs, 0)), NTB, 0, s>>>(
+        bd, b->d_fr_items, b->n_fr_items, b->d_counters + 3, b->ops, b->phys.gamma, b->phys.flux, w, b->d_wf, R);
+    b->launches += 2;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_batch_stage(kbl_batch* b, int st, const double* wn, const double* ws, const double* R,
+                           const double* bnd, const double* dt_dev, double* wout)
+{
+    if (!b) return KBL_EINVAL;
+    if (st < 0 || st > 2) return bfail(b, KBL_EINVAL, "stage must be 0, 1 or 2");
+    if (!wn || !ws || !R || !bnd || !dt_dev || !wout) return bfail(b, KBL_EINVAL, "null array");
+    cudaStream_t s = b->stream;
+    cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
+    k_batch_stage<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion))), NTB, sizeof(LimUnion),
+                    s>>>(dev_of(b), b->d_fr_items, b->n_fr_items, b->d_counters + 4, b->ops, b->phys, st, wn, ws, R,
+                         bnd, dt_dev, wout, b->d_flags);
+    b->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : bfail(b, KBL_ECUDA, cudaGetErrorString(e));
 }
 
 kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host)
@@ -719,7 +941,8 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, dou
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double best_ms = 1e30, best_cmp = 0.0;
-    int best[3] = {b->tile, b->chunk, b->blocks_per_sm};
+    const int entry[3] = {b->tile, b->chunk, b->blocks_per_sm};
+    int best[3] = {entry[0], entry[1], entry[2]};
     const int chunks[] = {4, 16, 64};
     for (int tile = 0; tile < 2; tile++) {
         const int maxb = max_bounds_blocks(tile);
@@ -737,6 +960,9 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, dou
             if (upload_items(b, sample, &d_sample, &n_sample) != cudaSuccess) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
+                if (d_sample) cudaFree(d_sample);
+                // back to the launch shape the batch had on entry
+                set_bounds_shape(b, entry[0], entry[1], entry[2]);
                 return bfail(b, KBL_ECUDA, "autotune upload");
             }
             for (int pi = 0; pi < 3; pi++) {
@@ -747,7 +973,7 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, dou
                 for (int rep = 0; rep < 2; rep++) {   // first run warms up
                     cudaMemsetAsync(b->d_counters + 2, 0, sizeof(unsigned), s);
                     cudaEventRecord(e0, s);
-                    launch_bounds_phase(b, w, b->d_wf, b->d_bnd, 2, s, d_sample, n_sample);
+                    launch_bounds_phase(b, w, b->d_wf, b->d_bnd, b->d_counters + 2, s, d_sample, n_sample);
                     cudaEventRecord(e1, s);
                     b->launches++;
                     cudaEventSynchronize(e1);

@@ -188,12 +188,24 @@ struct MeshDev {
     int n_bc;
 };
 
+#define KBL_ALPHA_BINS 10
+
 struct DevFlags {
     int nonphysical;
     int timeout;
     unsigned long long limited;
     unsigned long long prelimit;
+    unsigned long long eps_rule;                    // components where the epsilon rule of Eq. 37 fired
+    unsigned long long mean_outside;                // components whose mean lies outside [lo, hi]
+    unsigned long long alpha_hist[KBL_ALPHA_BINS];  // limited elements by alpha_min, bins of width 1/10
 };
+
+// Histogram bin of a limiting factor alpha in [0, 1): floor(10 alpha), at most 9.
+__device__ __forceinline__ int kbl_alpha_bin(double a)
+{
+    const int b = (int)(a * (double)KBL_ALPHA_BINS);
+    return b < 0 ? 0 : (b >= KBL_ALPHA_BINS ? KBL_ALPHA_BINS - 1 : b);
+}
 
 struct kbl_ctx {
     kbl_config cfg;
@@ -214,18 +226,26 @@ struct kbl_ctx {
     double* d_wa = nullptr;     // stage buffers [nv][E][Ns]
     double* d_wb = nullptr;
     double* d_whost = nullptr;  // device copy used by kbl_run_host
-    double* d_scal = nullptr;   // [0] dt, [1] t, [2] t_end
+    double* d_whost2 = nullptr; // second device copy of kbl_run_host_ensemble (first call allocates it)
+    double* d_scal = nullptr;   // [0] dt, [1] t, [2] t_end, [3] start time of kbl_run_host_ensemble
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;   // copy streams of kbl_run_host_ensemble
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_step[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
     unsigned long long* d_dtbits = nullptr;
     DevFlags* d_flags = nullptr;
     double* d_qw = nullptr;     // velocity quadrature weights (Romberg), or nullptr
     std::string err;
     int64_t launches = 0;
     int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes
-    // graph of kbl_step, keyed by (w, cfl)
+    // graph of kbl_step, keyed by (w, cfl); a second slot for the other state buffer of
+    // kbl_run_host_ensemble (the least recently used slot is replaced)
     cudaGraphExec_t graph = nullptr;
     double* graph_w = nullptr;
     double graph_cfl = 0.0;
     int graph_kernels = 0;
+    cudaGraphExec_t graph2 = nullptr;
+    double* graph2_w = nullptr;
+    double graph2_cfl = 0.0;
+    int graph2_kernels = 0;
     // adjoint scratch (kbl_adjoint.cu), grown on demand
     double* d_adj = nullptr;
     size_t adj_cap = 0;
@@ -240,6 +260,8 @@ MeshDev mesh_of(const kbl_ctx* c);
 
 // FR operators of order p (host, FP64); defined in kbl_api.cu.
 void kbl_build_fr_ops(int p, FrOps& o);
+// The configuration checks of kbl_create (every entry point that takes a kbl_config applies them).
+bool kbl_config_valid(const kbl_config* cfg);
 
 // ---- launchers (kbl_fr.cu, kbl_bounds.cu, kbl_limit.cu) ------------------
 // Each returns the number of kernels it launched, or -1 if the (dim, p)

@@ -94,8 +94,10 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
         }
         const double dmax = mx - mean[v], dmin = mn - mean[v];
         const double lo = bnd[(size_t)v * E + e], hi = bnd[((size_t)NV + v) * E + e];
+        if (mean[v] < lo || mean[v] > hi) atomicAdd(&flags->mean_outside, 1ull);
         double a;
         if (fabs(dmin) < ph.eps || fabs(dmax) < ph.eps) {
+            atomicAdd(&flags->eps_rule, 1ull);
             a = ph.eps_rule ? 1.0 : 0.0;
         } else {
             a = 1.0;
@@ -135,7 +137,10 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
         alpha_out[e] = alpha;
         alpha_out[(size_t)E + e] = aP;
     }
-    if (alpha < 1.0) atomicAdd(&flags->limited, 1ull);
+    if (alpha < 1.0) {
+        atomicAdd(&flags->limited, 1ull);
+        atomicAdd(&flags->alpha_hist[kbl_alpha_bin(alpha)], 1ull);
+    }
     if (relimit) atomicAdd(&flags->prelimit, 1ull);
 }
 

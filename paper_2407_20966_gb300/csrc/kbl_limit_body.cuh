@@ -303,8 +303,12 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             const double lo = bnd[(size_t)v * E + ee];
             const double hi = bnd[((size_t)NV + v) * E + ee];
             const double dmax = mx - mean, dmin = mn - mean;
+            // counters of the limiter's rarely taken branches (elements the screen passed meet
+            // neither: it certifies both deviations above eps and the mean strictly inside)
+            if (mean < lo || mean > hi) atomicAdd(&flags->mean_outside, 1ull);
             double a;
             if (fabs(dmin) < ph.eps || fabs(dmax) < ph.eps) {
+                atomicAdd(&flags->eps_rule, 1ull);
                 a = ph.eps_rule ? 1.0 : 0.0;
             } else {
                 // comparisons written so that a NaN ratio is ignored
@@ -396,7 +400,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         saP[tid] = aP;
         const int ee = e0 + tid;
         // alpha in [0, 1]: alpha < 1 on the bit patterns
-        if (__double_as_longlong(salpha[tid]) < __double_as_longlong(1.0)) atomicAdd(&flags->limited, 1ull);
+        if (__double_as_longlong(salpha[tid]) < __double_as_longlong(1.0)) {
+            atomicAdd(&flags->limited, 1ull);
+            atomicAdd(&flags->alpha_hist[kbl_alpha_bin(salpha[tid])], 1ull);
+        }
         if (alpha_out) {
             alpha_out[ee] = salpha[tid];
             alpha_out[E + ee] = aP;

@@ -53,27 +53,14 @@ cudaError_t symbol_addrs(SymbolAddrs& out)
     return cudaSuccess;
 }
 
-bool config_ok(const kbl_config* cfg)
-{
-    if (!cfg || (cfg->dim != 1 && cfg->dim != 2) || cfg->p < 1 || cfg->p > KBL_PMAX) return false;
-    if (cfg->dim == 2) {
-        const int nx = cfg->nu[0];
-        if (cfg->nu[1] != nx || nx < 2 || nx > 64) return false;
-    } else if (cfg->nu[0] < 2 || cfg->nu[0] > 4096) {
-        return false;
-    }
-    return cfg->gamma > 1.0 && cfg->k > 0.0 && cfg->r_fac >= 0.0 && cfg->r_fac < 1.0 && cfg->eps >= 0.0 &&
-           cfg->rho_floor >= 0.0 && cfg->p_floor >= 0.0 &&
-           (cfg->precision == KBL_FP64 || cfg->precision == KBL_FP32_MIXED) && cfg->quadrature == 0;
-}
-
 }  // namespace
 
 extern "C" kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, const int32_t* nbr_dev,
                                          int n_bc, const double* bc_dev, const double* w_dev,
                                          double* bnd_dev, void* cuda_stream)
 {
-    if (!config_ok(cfg) || n_elem < 0 || n_bc < 0) return KBL_EINVAL;
+    // the configurations kbl_create accepts, with the trapezoidal rule only
+    if (!kbl_config_valid(cfg) || cfg->quadrature != 0 || n_elem < 0 || n_bc < 0) return KBL_EINVAL;
     const int n = cfg->p + 1;
     const int nv = cfg->dim + 2;
     const int ns = cfg->dim == 1 ? n : n * n;
@@ -96,8 +83,8 @@ extern "C" kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, cons
     c.phys.rho_floor = cfg->rho_floor;
     c.phys.p_floor = cfg->p_floor;
     c.phys.eps_rule = cfg->eps_rule;
-    c.phys.uncoupled = cfg->uncoupled ? 1 : 0;
-    c.phys.flux = 0;
+    c.phys.uncoupled = cfg->uncoupled;
+    c.phys.flux = cfg->flux;
     c.phys.qw = nullptr;   // trapezoidal rule: a weight table would need an allocation
     c.phys.qwf = nullptr;
     c.phys.nu[0] = cfg->nu[0];
@@ -117,7 +104,8 @@ extern "C" kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, cons
     c.d_flags = a.flags;
 
     // the traces are fully rewritten before they are read; the flag word must
-    // start at zero on every call
+    // start at zero on every call (the kernels set it; this call reports non-physical
+    // stencils through NaN bounds only, so the word is write-only scratch here)
     if ((e = cudaMemsetAsync(a.flags, 0, sizeof(DevFlags), c.stream)) != cudaSuccess) return KBL_ECUDA;
     if (launch_traces(&c, w_dev, a.traces, c.stream) < 0) return KBL_EINVAL;
     if (launch_bounds(&c, w_dev, a.traces, bnd_dev, c.stream) < 0) return KBL_EINVAL;

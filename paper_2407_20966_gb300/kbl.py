@@ -40,7 +40,9 @@ class KblConfig(C.Structure):
 
 class KblCounters(C.Structure):
     _fields_ = [("nonphysical", C.c_int32), ("timeout", C.c_int32),
-                ("limited_elements", C.c_int64), ("pressure_relimits", C.c_int64)]
+                ("limited_elements", C.c_int64), ("pressure_relimits", C.c_int64),
+                ("eps_rule_activations", C.c_int64), ("mean_outside_bounds", C.c_int64),
+                ("alpha_hist", C.c_int64 * 10)]
 
 
 _lib = None
@@ -74,6 +76,7 @@ _SIGS = {
     "kbl_set_time": (C.c_int, [_P, C.c_double, C.c_double]),
     "kbl_time_sync": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "kbl_run_host": (C.c_int, [_P, _P, _P, C.c_int, C.c_double]),
+    "kbl_run_host_ensemble": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_double]),
     "kbl_check": (C.c_int, [_P]),
     "kbl_read_counters": (C.c_int, [_P, C.POINTER(KblCounters)]),
     "kbl_launch_count": (C.c_int64, [_P]),
@@ -85,6 +88,11 @@ _SIGS = {
     "kbl_batch_nodes": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "kbl_batch_step": (C.c_int, [_P, _P, C.c_double]),
     "kbl_batch_dt": (C.c_int, [_P, _P]),
+    "kbl_batch_bounds": (C.c_int, [_P, _P, _P]),
+    "kbl_batch_bounds_ms": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "kbl_batch_run_host": (C.c_int, [_P, _P, _P, C.c_int, C.c_double]),
+    "kbl_batch_rhs": (C.c_int, [_P, _P, _P]),
+    "kbl_batch_stage": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "kbl_batch_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "kbl_batch_tuning": (C.c_int, [_P, _P]),
     "kbl_batch_check": (C.c_int, [_P]),
@@ -276,13 +284,27 @@ class Context:
                                            w_out.ctypes.data_as(C.c_void_p), int(n_steps), float(cfl)),
                     "run_host")
 
+    def run_host_ensemble(self, w_in: np.ndarray, w_out: np.ndarray, n_steps, cfl):
+        """Independent states w_in[k] ([members][nv][E][Ns], host) stepped n_steps each, into
+        w_out[k]; copies overlap the steps of neighbouring members (kbl_run_host_ensemble)."""
+        for a in (w_in, w_out):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("host arrays must be contiguous float64")
+        if w_in.shape != w_out.shape:
+            raise TypeError("input and output shapes differ")
+        self._check(self._lib.kbl_run_host_ensemble(self._h, int(w_in.shape[0]), w_in.ctypes.data_as(C.c_void_p),
+                                                    w_out.ctypes.data_as(C.c_void_p), int(n_steps), float(cfl)),
+                    "run_host_ensemble")
+
     def check(self):
         self._check(self._lib.kbl_check(self._h), "check")
 
     def counters(self):
         k = KblCounters()
         st = self._lib.kbl_read_counters(self._h, C.byref(k))
-        return st, {f: getattr(k, f) for f, _ in KblCounters._fields_}
+        out = {f: getattr(k, f) for f, _ in KblCounters._fields_}
+        out["alpha_hist"] = list(k.alpha_hist)
+        return st, out
 
     def launch_count(self):
         return int(self._lib.kbl_launch_count(self._h))
@@ -440,6 +462,37 @@ class Batch:
         out = np.zeros(self.P)
         self._check(self._lib.kbl_batch_dt(self._h, out.ctypes.data_as(C.c_void_p)), "batch_dt")
         return out
+
+    def bounds_view(self, bnd, i):
+        """Problem i's bounds [2][4][E_i] in a concatenated bounds array (a view)."""
+        a, n = 8 * int(self.elem_offsets[i]), int(self.n_elem[i])
+        return bnd[a:a + 8 * n].reshape(2, 4, n)
+
+    def bounds(self, w, bnd):
+        self._check(self._lib.kbl_batch_bounds(self._h, _dev(w, "w"), _dev(bnd, "bnd")), "batch_bounds")
+
+    def bounds_ms(self):
+        """Device time of the bounds launch of the last bounds() call (ms)."""
+        ms = C.c_double()
+        self._check(self._lib.kbl_batch_bounds_ms(self._h, C.byref(ms)), "batch_bounds_ms")
+        return ms.value
+
+    def run_host(self, w_in: np.ndarray, w_out: np.ndarray, n_steps, cfl):
+        """End to end on host buffers (kbl_batch_run_host): copies overlap the steps by groups."""
+        for a in (w_in, w_out):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != int(self.state_offsets[-1]):
+                raise TypeError("host arrays must be contiguous float64 of the batch state's size")
+        self._check(self._lib.kbl_batch_run_host(self._h, w_in.ctypes.data_as(C.c_void_p),
+                                                 w_out.ctypes.data_as(C.c_void_p), int(n_steps), float(cfl)),
+                    "batch_run_host")
+
+    def rhs(self, w, R):
+        self._check(self._lib.kbl_batch_rhs(self._h, _dev(w, "w"), _dev(R, "R")), "batch_rhs")
+
+    def stage(self, s, wn, ws, R, bnd, dt_dev, wout):
+        self._check(self._lib.kbl_batch_stage(self._h, int(s), _dev(wn, "wn"), _dev(ws, "ws"), _dev(R, "R"),
+                                              _dev(bnd, "bnd"), _dev(dt_dev, "dt"), _dev(wout, "wout")),
+                    "batch_stage")
 
     def autotune(self, w, with_cmp=False):
         ms, cmp = C.c_double(), C.c_double()

@@ -167,3 +167,92 @@ def test_sod_full_run_matches_checker(orc):
     print(f"Sod, {n} steps: L1(rho) device {l1_gpu:.6e}, checker {l1_ref:.6e}, paper 1.181e-3 (HLLC, 2048 pts)")
     assert l1_gpu == pytest.approx(l1_ref, rel=1e-8)
     assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def _fullsize_sample(E, n_side, n_sample, seed, extra=()):
+    """>= n_sample distinct elements: random ones, the first and last thread blocks of the
+    FR and stage kernels (8 elements each), and the given extra elements."""
+    rng = np.random.default_rng(seed)
+    idx = set(rng.choice(E, n_sample, replace=False).tolist())
+    idx.update(range(0, 8))
+    idx.update(range(E - 8, E))
+    idx.update(int(e) for e in extra)
+    return np.array(sorted(idx))
+
+
+@pytest.mark.parametrize("workload", ["vortex", "sedov"])
+def test_fullsize_stage_parity_identical_inputs(orc, workload):
+    """The benchmark workloads at full size, in bench.py's launch configuration (FP32-mixed, one
+    launch over the whole mesh per call): the three stages of a step, each on identical inputs.
+    Device traces, bounds, residual and stage + limiter of the whole mesh; the checker computes
+    2000+ sampled elements one by one (the first and last blocks and, for Sedov, the blast cells
+    and their neighbours among them): bounds to 1e-5, residual to 1e-5 per element and component,
+    the limited state to 1e-12 when both sides limit against the same bounds, and the composed
+    FP32 stage (the device's own residual and bounds) to 1e-5."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    from tests.gpu_helpers import rhs_error, state_error
+    if workload == "vortex":
+        mesh, ic = inputs.isentropic_vortex(128)
+        p, flux, nside = 3, 0, 128
+        extra = ()
+    else:
+        mesh, ic = inputs.sedov(512)
+        p, flux, nside = 2, 2, 512
+        c = 256
+        extra = [(c + dy) * nside + c + dx for dy in range(-4, 4) for dx in range(-4, 4)]
+    ctx = kbl.Context(dim=2, p=p, nu=(32, 32), precision=kbl.FP32_MIXED, flux=flux)
+    ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
+    cfg = orc.Config(dim=2, p=p, nu=(32, 32), flux=flux)
+    om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+    w = inputs.nodal_field(mesh, ctx.operator(kbl.OP_NODES), ic)
+    E = mesh.n_elem
+    idx = _fullsize_sample(E, nside, 2000, seed=17, extra=extra)
+    dt = orc.dt(cfg, om, w, 0.05)
+    dtd = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    wn, ws = w, w
+    limited = 0
+    for s in range(3):
+        wsd = torch.from_numpy(ws).cuda()
+        wf_ref = orc.traces(cfg, om, ws)
+        wf = torch.zeros(wf_ref.shape, dtype=torch.float64, device="cuda")
+        ctx.traces(wsd, wf)
+        np.testing.assert_allclose(wf.cpu().numpy(), wf_ref, rtol=1e-14, atol=1e-14 * np.abs(wf_ref).max())
+        wfd = torch.from_numpy(wf_ref).cuda()
+        bnd = torch.zeros((2, 4, E), dtype=torch.float64, device="cuda")
+        ctx.bounds(wsd, wfd, bnd)
+        R = torch.zeros(w.shape, dtype=torch.float64, device="cuda")
+        ctx.rhs(wsd, wfd, R)
+        ctx.check()
+        bg, Rg = bnd.cpu().numpy(), R.cpu().numpy()
+        bref = np.zeros((2, 4, len(idx)))
+        for k, e in enumerate(idx):
+            bref[0, :, k], bref[1, :, k] = orc.bounds_stencil(cfg, orc.gather_stencil(cfg, om, ws, wf_ref, int(e)))
+        eb = bounds_error(bg[:, :, idx], bref)
+        assert eb.max() < TOL_FP32, ("bounds", s, eb.max())
+        R_ref = orc.rhs(cfg, om, ws, wf_ref)
+        er = rhs_error(Rg, R_ref, ws, wf_ref, mesh)
+        assert er.max() < TOL_FP32, ("residual", s, er.max())
+        # stage + limiter: both sides limit against the device's bounds (identical inputs)
+        out = torch.zeros(w.shape, dtype=torch.float64, device="cuda")
+        ctx.stage(s, torch.from_numpy(wn).cuda(), wsd, torch.from_numpy(R_ref).cuda(), bnd, dtd, out)
+        # the composed FP32 stage: the device's own residual and bounds
+        out2 = torch.zeros(w.shape, dtype=torch.float64, device="cuda")
+        ctx.stage(s, torch.from_numpy(wn).cuda(), wsd, R, bnd, dtd, out2)
+        got, got2 = out.cpu().numpy(), out2.cpu().numpy()
+        comb = orc.stage_combine(cfg, om, s, wn, ws, R_ref, dt)
+        wfc = orc.traces(cfg, om, comb)
+        ref = np.zeros((4, len(idx), w.shape[2]))
+        ref2 = np.zeros_like(ref)
+        for k, e in enumerate(idx):
+            ref[:, k], a = orc.limit_element(cfg, comb[:, e], wfc[:, e], bg[0, :, e], bg[1, :, e])
+            ref2[:, k], _ = orc.limit_element(cfg, comb[:, e], wfc[:, e], bref[0, :, k], bref[1, :, k])
+            limited += int(a[0] < 1)
+        es = state_error(got[:, idx], ref).max(axis=(0, 2))
+        assert es.max() < TOL_FP64, ("stage", s, es.max())
+        ec = state_error(got2[:, idx], ref2).max(axis=(0, 2))
+        assert ec.max() < TOL_FP32, ("composed", s, ec.max())
+        print(f"{workload} stage {s}: bounds {eb.max():.2e} residual {er.max():.2e} stage {es.max():.2e} "
+              f"composed {ec.max():.2e} on {len(idx)} elements")
+        ws = got
+    print(f"{workload}: limited element-stages in the sample", limited)

@@ -8,8 +8,8 @@ a non-physical state.
 import numpy as np
 import pytest
 
-from tests.gpu_helpers import (TOL_FP32, TOL_FP64, both, bounds_error, mesh_and_field,
-                               state_error, to_dev, upload, zeros_dev)
+from tests.gpu_helpers import (TOL_FP32, TOL_FP64, both, bounds_error, mesh_and_field, rhs_error,
+                               state_error, step_sensitivity, to_dev, upload, zeros_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -155,7 +155,7 @@ def test_rhs(orc, dim, p, n):
     ref = orc.rhs(ocfg, om, w, wf)
     R = zeros_dev(*w.shape)
     ctx.rhs(to_dev(w), to_dev(wf), R)
-    err = np.abs(R.cpu().numpy() - ref) / np.abs(ref).max()
+    err = rhs_error(R.cpu().numpy(), ref, w, wf, mesh)   # per element and component
     assert err.max() < TOL_FP64, err.max()
 
 
@@ -173,7 +173,8 @@ def test_fp32_mixed_traces_rhs_dt(orc, dim, p, n):
     R_ref = orc.rhs(ocfg, om, w, wf_ref)
     R = zeros_dev(*w.shape)
     ctx.rhs(wd, to_dev(wf_ref), R)
-    assert (np.abs(R.cpu().numpy() - R_ref) / np.abs(R_ref).max()).max() < 5e-6
+    err = rhs_error(R.cpu().numpy(), R_ref, w, wf_ref, mesh)   # per element and component
+    assert err.max() < TOL_FP32, err.max()
     d = zeros_dev(1)
     ctx.dt(wd, 0.3, d)
     assert d.item() == pytest.approx(orc.dt(ocfg, om, w, 0.3), rel=1e-6)
@@ -220,24 +221,29 @@ def test_limit_uncoupled(orc, dim, p, n):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_step_uncoupled(orc, precision):
+    """A whole SSP-RK3 step with uncoupled limiting against the checker, element by element: 1e-12
+    FP64; FP32-mixed against max(1e-5, 10 x the checker's own sensitivity to 1e-6 bound and
+    residual errors) (gpu_helpers.step_sensitivity).  The checker takes the device's time step
+    (FP32 arithmetic in the mixed mode)."""
     ctx, ocfg = both(orc, 2, 3, (16, 16), precision=precision, uncoupled=1)
     mesh, w = mesh_and_field(orc, 2, 3, (7, 6), seed=170, kind="disc")
     om = upload(ctx, orc, mesh)
-    dt = orc.dt(ocfg, om, w, 0.05)
-    ref, _ = orc.ssprk3_step(ocfg, om, w, dt)
     wd = to_dev(w)
     ctx.set_time(0.0)
     ctx.counters()
     ctx.step(wd, 0.05)
     st, c = ctx.counters()
     assert st == 0 and c["limited_elements"] > 0
-    tol = TOL_FP64 if precision == 0 else TOL_FP32
+    dt = ctx.time()
+    assert dt == pytest.approx(orc.dt(ocfg, om, w, 0.05), rel=1e-14 if precision == 0 else 1e-6)
+    ref, _ = orc.ssprk3_step(ocfg, om, w, dt)
     err = state_error(wd.cpu().numpy(), ref).max(axis=(0, 2))
+    print("uncoupled step, precision", precision, ": max error", err.max())
     if precision == 0:
-        assert err.max() < tol
+        assert err.max() < TOL_FP64, (int(np.argmax(err)), err.max())
     else:
-        # heavily limited elements amplify the FP32 bound error (conditioning of Eq. 37)
-        assert np.median(err) < tol
+        allowed = np.maximum(TOL_FP32, 10 * step_sensitivity(orc, ocfg, om, w, dt, ref))
+        assert np.all(err <= allowed), (int(np.argmax(err / allowed)), err.max())
 
 
 def test_pressure_relimit_path(orc):
@@ -296,8 +302,8 @@ def test_rhs_hllc(orc, dim, p, n, precision, flux):
     R_ref = orc.rhs(ocfg, om, w, wf)
     R = zeros_dev(*w.shape)
     ctx.rhs(to_dev(w), to_dev(wf), R)
-    err = (np.abs(R.cpu().numpy() - R_ref) / np.abs(R_ref).max()).max()
-    assert err < (1e-13 if precision == 0 else 5e-6), err
+    err = rhs_error(R.cpu().numpy(), R_ref, w, wf, mesh).max()   # per element and component
+    assert err < (TOL_FP64 if precision == 0 else TOL_FP32), err
     ocfg.flux = 0
     assert np.abs(orc.rhs(ocfg, om, w, wf) - R_ref).max() > 1e-3 * np.abs(R_ref).max()
 
@@ -436,3 +442,73 @@ def test_bad_arguments_rejected(orc):
         ctx.mesh_upload(np.array([[5, 0, 0, 0]]), np.ones((1, 2)), None)   # neighbour out of range
     with pytest.raises(kbl.KblError):
         ctx.mesh_upload(np.array([[-3, 0, 0, 0]]), np.ones((1, 2)), np.ones((1, 4)))  # bad bc id
+
+
+def test_limiter_counters(orc):
+    """The limiter's counters: the alpha histogram matches the factors the checker computes, the
+    epsilon rule of Eq. 37 fires on exactly the (element, component) pairs whose extreme over V
+    lies within eps of the mean, and the mean-outside-bounds count matches the pairs whose mean
+    lies outside [w_min, w_max]."""
+    ctx, ocfg = both(orc, 2, 2, (16, 16))
+    mesh, w = mesh_and_field(orc, 2, 2, (9, 8), seed=77, kind="smooth")
+    om = upload(ctx, orc, mesh)
+    E = mesh.n_elem
+    bnd = orc.bounds(ocfg, om, w, orc.traces(ocfg, om, w))
+    rng = np.random.default_rng(8)
+    w2 = w * (1 + 0.3 * rng.uniform(-1, 1, w.shape))
+    w2[2, 3:9] = w2[2, 3:9, :1]          # m_y constant in six elements: the epsilon rule fires
+    x, wq = orc.gauss_legendre(3)
+    W = np.outer(wq, wq).ravel()
+    mean = (w2 * W).sum(axis=2) / W.sum()
+    bnd[0, 0, 20:25] = mean[0, 20:25] + 0.05   # the density mean below its lower bound
+    bnd[1, 3, 30:33] = mean[3, 30:33] - 0.05   # the energy mean above its upper bound
+    ref, a_ref = orc.limit(ocfg, om, w2, bnd)
+    wf = orc.traces(ocfg, om, w2)
+    vmax = np.maximum(w2.max(axis=2), wf.max(axis=2))
+    vmin = np.minimum(w2.min(axis=2), wf.min(axis=2))
+    n_eps = int(((np.abs(vmin - mean) < ocfg.eps) | (np.abs(vmax - mean) < ocfg.eps)).sum())
+    n_out = int(((mean < bnd[0]) | (mean > bnd[1])).sum())
+    a = a_ref[0][a_ref[0] < 1]
+    hist = np.bincount(np.minimum((a * 10).astype(int), 9), minlength=10)
+    ctx.counters()
+    wd = to_dev(w2)
+    ctx.limit(wd, to_dev(bnd))
+    st, c = ctx.counters()
+    assert state_error(wd.cpu().numpy(), ref).max() < TOL_FP64
+    print("counters:", c)
+    assert n_eps == 6 and n_out >= 8
+    assert c["eps_rule_activations"] == n_eps
+    assert c["mean_outside_bounds"] == n_out
+    assert c["alpha_hist"] == hist.tolist()
+    assert sum(c["alpha_hist"]) == c["limited_elements"] == int((a_ref[0] < 1).sum())
+
+
+def test_run_host_ensemble_matches_device_steps(orc):
+    """kbl_run_host_ensemble: independent states on one mesh, two alternating device copies with
+    the copies of neighbouring members overlapping each member's steps; every member's result
+    equals kbl_step on device data from the same start time, bit for bit, and aliasing the
+    output with the input gives the same."""
+    import torch
+    ctx, ocfg = both(orc, 2, 3, (16, 16), precision=1)
+    mesh, w = mesh_and_field(orc, 2, 3, (6, 5), seed=31, kind="smooth")
+    upload(ctx, orc, mesh)
+    rng = np.random.default_rng(4)
+    members = np.ascontiguousarray(np.stack([w * (1 + 0.01 * rng.uniform(-1, 1, w.shape)) for _ in range(5)]))
+    ref = []
+    for k in range(5):
+        wd = to_dev(members[k])
+        ctx.set_time(0.25)
+        for _ in range(2):
+            ctx.step(wd, 0.1)
+        ref.append(wd.cpu().numpy())
+    ref = np.stack(ref)
+    w_in = torch.from_numpy(members).pin_memory()
+    w_out = torch.zeros_like(w_in).pin_memory()
+    ctx.set_time(0.25)
+    ctx.run_host_ensemble(w_in.numpy(), w_out.numpy(), 2, 0.1)
+    np.testing.assert_array_equal(w_out.numpy(), ref)
+    inout = members.copy()
+    ctx.set_time(0.25)
+    ctx.run_host_ensemble(inout, inout, 2, 0.1)
+    np.testing.assert_array_equal(inout, ref)
+    ctx.check()

@@ -44,7 +44,23 @@ def trunc32(xv):
 
 
 def fmaf(a, b, c):
-    return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(f32)
+    """fmaf with one rounding: the float32 product is exact in float64, the sum p + c is carried
+    exactly as s + err (Knuth's two-sum), and s is rounded to float32 with the tie that err
+    decides when s falls on a float32 midpoint (the one case where rounding s alone would round
+    twice)."""
+    p = np.asarray(a, np.float64) * np.asarray(b, np.float64)
+    c64 = np.asarray(c, np.float64)
+    with np.errstate(invalid="ignore", over="ignore"):
+        s = p + c64
+        bb = s - p
+        err = (p - (s - bb)) + (c64 - bb)
+        r = s.astype(f32)
+        r64 = r.astype(np.float64)
+        other = np.where(s > r64, np.nextafter(r, f32(np.inf)), np.nextafter(r, f32(-np.inf)))
+        o64 = other.astype(np.float64)
+        mid = (s != r64) & ((r64 + o64) * 0.5 == s)
+        take_other = mid & (err != 0) & (np.sign(err) == np.sign(o64 - s))
+    return np.where(take_other, other, r).astype(f32)
 
 
 @pytest.fixture(scope="module")
