@@ -152,6 +152,17 @@ kbl_status kbl_mesh_upload(kbl_ctx* ctx, int n_elem, const int32_t* nbr_host,
  * 4 D[p+1][p+1] with D[i][m] = l_m'(x_i), 5 g_L'(x_i)[p+1], 6 g_R'(x_i)[p+1]. */
 kbl_status kbl_get_operator(const kbl_ctx* ctx, int which, double* host_out, int n);
 
+/* The 2D FR residual of Sec. 2.3 (g_DG correction, Sec. 5) as one matrix per order p: with
+ * Ns = (p+1)^2 and K = 2 Ns + 4 (p+1), the residual of an element is R[v][n] = sum_k X[v][k]
+ * B[k][n], X[v] = [(2/h_x) Fx_v at the Ns solution points, (2/h_y) Fy_v at them, (2/h_x) F*_v at
+ * the 2(p+1) face points of faces 0 and 1, (2/h_y) F*_v at those of faces 2 and 3] (F* the common
+ * flux, face-point order of this header).  The interpolated discontinuous flux is folded into the
+ * derivative: B holds -(D[i][m] - g_L'(x_i) l_m(-1) - g_R'(x_i) l_m(+1)) along each axis and the
+ * lifting -g_L', -g_R'.  The tensor-core residual (KBL_TUNE_RHS_TC) multiplies by it.  Host only,
+ * no context, no device call: for checking.  host_out[K][Ns] row-major, n >= K Ns; KBL_EINVAL
+ * for p outside 1..5 or a short buffer. */
+kbl_status kbl_residual_operator(int p, double* host_out, int n);
+
 /* The velocity quadrature weights the kernels apply on one axis of nu points, in
  * units of the grid spacing (Sec. 3.7, Sec. 5): quadrature 0 the trapezoidal rule,
  * 1 Romberg (see kbl_config.quadrature).  Host only, no context, no device call:
@@ -263,7 +274,11 @@ int64_t kbl_launch_count(const kbl_ctx* ctx);
  * bounds thread tile for grids of 32 or 64 points per axis: 0 = 4 x 4 velocity
  * nodes per thread, 1 = 4 x 2, 2 = 2 x 4.  Setting a knob drops the captured
  * step graph. */
-typedef enum { KBL_TUNE_BOUNDS_TILE = 0 } kbl_tune_key;
+typedef enum { KBL_TUNE_BOUNDS_TILE = 0, KBL_TUNE_RHS_TC = 1 } kbl_tune_key;
+/* KBL_TUNE_RHS_TC: 1 (default) runs the FP32-mixed 2D residual of orders 2 and 3 with its operator
+ * product (operator 7 of kbl_get_operator) on the tensor cores (tcgen05, TF32 split into
+ * hi + lo pairs, FP32 accumulation; element tiles staged by TMA), 0 on the CUDA cores.  Other
+ * orders, 1D and FP64 always use the CUDA cores.  Setting it drops the captured step graph. */
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);   /* KBL_EINVAL for an unknown key or value */
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 

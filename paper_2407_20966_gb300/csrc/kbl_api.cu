@@ -353,6 +353,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         c->phys.qw = c->d_qw;
         c->phys.qwf = reinterpret_cast<const float*>(c->d_qw + nq);
     }
+    if (cfg->dim == 2 && cfg->precision == KBL_FP32_MIXED) c->d_tcop = kbl_rhs_tc_upload(c->ops, cfg->p);
     const double scal[4] = {0.0, 0.0, INFINITY, 0.0};
     if ((e = cudaMemcpy(c->d_scal, scal, sizeof(scal), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(c->d_flags, 0, sizeof(DevFlags))) != cudaSuccess) {
@@ -360,6 +361,19 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
         return KBL_ECUDA;
     }
     *out = c;
+    return KBL_OK;
+}
+
+kbl_status kbl_residual_operator(int p, double* host_out, int n)
+{
+    if (!host_out || p < 1 || p > KBL_PMAX) return KBL_EINVAL;
+    FrOps o;
+    build_ops(p, o);
+    std::vector<double> B;
+    int K = 0, NS = 0;
+    kbl_rhs_operator(o, p, B, K, NS);
+    if (n < K * NS) return KBL_EINVAL;
+    std::copy(B.begin(), B.end(), host_out);
     return KBL_OK;
 }
 
@@ -385,6 +399,7 @@ kbl_status kbl_destroy(kbl_ctx* c)
     if (c->d_dtbits) cudaFree(c->d_dtbits);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->d_qw) cudaFree(c->d_qw);
+    if (c->d_tcop) cudaFree(c->d_tcop);
     if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
     if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
     for (int k = 0; k < 2; k++) {
@@ -719,6 +734,11 @@ kbl_status kbl_read_counters(kbl_ctx* c, kbl_counters* out)
 kbl_status kbl_set_tuning(kbl_ctx* c, int key, int value)
 {
     if (!c) return KBL_EINVAL;
+    if (key == KBL_TUNE_RHS_TC && (value == 0 || value == 1)) {
+        c->rhs_tc = value;
+        drop_graphs(c);
+        return KBL_OK;
+    }
     if (key != KBL_TUNE_BOUNDS_TILE || value < 0 || value > 2) return fail(c, KBL_EINVAL, "unknown tuning knob or value");
     c->bounds_tile = value;
     drop_graphs(c);
@@ -727,8 +747,10 @@ kbl_status kbl_set_tuning(kbl_ctx* c, int key, int value)
 
 kbl_status kbl_get_tuning(const kbl_ctx* c, int key, int* value)
 {
-    if (!c || !value || key != KBL_TUNE_BOUNDS_TILE) return KBL_EINVAL;
-    *value = c->bounds_tile;
+    if (!c || !value) return KBL_EINVAL;
+    if (key == KBL_TUNE_BOUNDS_TILE) *value = c->bounds_tile;
+    else if (key == KBL_TUNE_RHS_TC) *value = c->rhs_tc;
+    else return KBL_EINVAL;
     return KBL_OK;
 }
 

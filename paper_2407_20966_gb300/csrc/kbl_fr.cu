@@ -228,6 +228,8 @@ int launch_gather(const kbl_ctx* c, const double* w, const double* wf, int e0, i
 
 int launch_rhs(const kbl_ctx* c, const double* w, const double* wf, double* R, cudaStream_t s)
 {
+    const int r = launch_rhs_tc(c, w, wf, R, s);
+    if (r >= 0) return r;
     KBL_DISPATCH(c->cfg.dim, c->cfg.p + 1, run_rhs, c, w, wf, R, s);
 }
 

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "kbl.h"
 
@@ -233,6 +234,8 @@ struct kbl_ctx {
     unsigned long long* d_dtbits = nullptr;
     DevFlags* d_flags = nullptr;
     double* d_qw = nullptr;     // velocity quadrature weights (Romberg), or nullptr
+    float* d_tcop = nullptr;    // split residual operator of the tensor-core residual, or nullptr
+    int rhs_tc = 1;             // knob: 1 residual products on the tensor cores where covered, 0 CUDA cores
     std::string err;
     int64_t launches = 0;
     int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes
@@ -270,6 +273,12 @@ int launch_traces(const kbl_ctx* c, const double* w, double* wf, cudaStream_t s)
 int launch_gather(const kbl_ctx* c, const double* w, const double* wf, int e0, int n,
                   double* S, cudaStream_t s);
 int launch_rhs(const kbl_ctx* c, const double* w, const double* wf, double* R, cudaStream_t s);
+// the FP32-mixed 2D residual with its operator products on the tensor cores (kbl_fr_tc.cu): -1 when
+// not covered (order, dimension, precision, knob), -2 when these arrays cannot be TMA-mapped
+int launch_rhs_tc(const kbl_ctx* c, const double* w, const double* wf, double* R, cudaStream_t s);
+// folded residual operator B[K][Ns] of order p (FP64) and its split device copy (kbl_fr_tc.cu)
+void kbl_rhs_operator(const FrOps& o, int p, std::vector<double>& B, int& K, int& NS);
+float* kbl_rhs_tc_upload(const FrOps& o, int p);
 // dt_out <- cfl * min(h / (|U| + c)); with clip, also <= t_end - t of the context
 int launch_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int clip, cudaStream_t s);
 int launch_time_advance(const kbl_ctx* c, cudaStream_t s);

@@ -65,6 +65,7 @@ _SIGS = {
     "kbl_bounds_stencil": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "kbl_limit_nodes": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P]),
     "kbl_velocity_weights": (C.c_int, [C.c_int, C.c_int, _P]),
+    "kbl_residual_operator": (C.c_int, [C.c_int, _P, C.c_int]),
     "kbl_traces": (C.c_int, [_P, _P, _P]),
     "kbl_gather_stencil": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, _P]),
     "kbl_bounds": (C.c_int, [_P, _P, _P, _P]),
@@ -112,6 +113,7 @@ _SIGS = {
 }
 
 TUNE_BOUNDS_TILE = 0
+TUNE_RHS_TC = 1
 
 
 def exported_symbols():
@@ -368,6 +370,17 @@ def _dev_any(t, dtype_name, name):
     if str(t.dtype) != dtype_name:
         raise TypeError(f"{name} must be {dtype_name}")
     return C.c_void_p(t.data_ptr())
+
+
+def residual_operator(p):
+    """The 2D FR residual as one matrix B[K][Ns] of order p (kbl_residual_operator; host only)."""
+    N = int(p) + 1
+    K, NS = 2 * N * N + 4 * N, N * N
+    out = np.zeros(K * NS)
+    st = load().kbl_residual_operator(int(p), out.ctypes.data_as(C.c_void_p), K * NS)
+    if st != OK:
+        raise KblError(st, "residual_operator")
+    return out.reshape(K, NS)
 
 
 def velocity_weights(nu, quadrature=0):
