@@ -46,7 +46,7 @@ PEAK_SOURCE = ("measured envelope-pattern rate 155.5 FP32 lane-ops/clk/SM (bench
 # DRAM bytes (read + write) of one launch of the FP32 2D bounds kernel on the vortex workload,
 # from an ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum).  Must be
 # reset to None whenever that kernel changes, until it is captured again.
-BOUNDS_F32_VORTEX_TRAFFIC = 17070592 + 0
+BOUNDS_F32_VORTEX_TRAFFIC = None
 
 
 def parse():
@@ -476,6 +476,19 @@ def run_batched(args, rank, world, steps=None, warmup=None):
     launches = b.launch_count() - l0
     ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in evs), dev)
     value = job_throughput(E * 3 * K, ms, world)
+    # the same steps as one persistent launch per phase (the other form), for comparison
+    b.set_form(0)
+    b.step(wd, cfl)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kp = 2
+    e0.record(stream)
+    for _ in range(kp):
+        b.step(wd, cfl)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.check()
+    per_phase_ms = e0.elapsed_time(e1) / kp
+    b.set_form(1)
     # dominant kernel: the bounds phase over the whole batch, tuned shape, timed alone
     bnd = torch.zeros(8 * E, dtype=torch.float64, device=dev)
     b.bounds(wd, bnd)
@@ -509,6 +522,8 @@ def run_batched(args, rank, world, steps=None, warmup=None):
                     "d2h_bytes_per_step": w0.nbytes,
                     "call": "kbl_batch_run_host, 1 step, pinned host buffers, copies overlapped by problem groups"},
             "gpu_launches": launches,
+            "form": {"timed": "one persistent launch per step (per-problem dataflow between phases)",
+                     "per_phase_launches_ms_per_step": per_phase_ms},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                          "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "kernel": "k_batch_bounds", "bounds_ms_per_launch": round(bounds_ms, 3),
@@ -719,7 +734,7 @@ def main():
             line["sedov"] = run_sub_mesh(args, "sedov", steps=min(args.steps, 10), warmup=3, dev=dev)
             bl, _, _ = run_batched(args, rank, world, steps=3, warmup=1)
             line["batched"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "e2e",
-                                                  "gpu_launches", "roofline", "clocks")}
+                                                  "gpu_launches", "form", "roofline", "clocks")}
             line["batched"]["workload"] = bl["config"]["workload"]
             line["batched"]["elements"] = bl["config"]["elements"]
             line["batched"]["tuning"] = bl["config"]["tuning"]

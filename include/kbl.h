@@ -59,11 +59,14 @@ typedef enum {
     KBL_ESTATE = 6
 } kbl_status;
 
-/* Arithmetic of the bounds kernel (the rest of the path is FP64 in both).
- * KBL_FP64: Maxwellians, envelopes and velocity sums in FP64.
- * KBL_FP32_MIXED: Maxwellians, envelopes and velocity sums in FP32 with
- *   compensated sums across threads; primitive states (pressure), the box,
- *   the density floor, the limiting factors and the pressure checks in FP64. */
+/* Arithmetic of the path.
+ * KBL_FP64: everything in FP64.
+ * KBL_FP32_MIXED: Maxwellians, envelopes and velocity sums in FP32 (2D: each thread sums its
+ *   16 velocity nodes, the threads' sums meet in a pairwise tree, at most 25 roundings of the sum
+ *   of magnitudes, which for these single-signed sums is the sum itself: <= 1.5e-6 relative;
+ *   1D: compensated block sums); the residual and the time step in FP32 arithmetic on FP64
+ *   storage; FP64 for rho E - |m|^2/2 and its positivity test in the bounds, the state, the
+ *   face traces and the limiter (whose FP32 screen only certifies alpha = 1 exactly). */
 typedef enum { KBL_FP64 = 0, KBL_FP32_MIXED = 1 } kbl_precision;
 
 typedef struct {
@@ -278,15 +281,16 @@ typedef enum { KBL_TUNE_BOUNDS_TILE = 0, KBL_TUNE_RHS_TC = 1 } kbl_tune_key;
 /* KBL_TUNE_RHS_TC: 1 (default) runs the FP32-mixed 2D residual of orders 2 and 3 with its operator
  * product (operator 7 of kbl_get_operator) on the tensor cores (tcgen05, TF32 split into
  * hi + lo pairs, FP32 accumulation; element tiles staged by TMA), 0 on the CUDA cores.  Other
- * orders, 1D and FP64 always use the CUDA cores.  Setting it drops the captured step graph. */
+ * orders, 1D and FP64 always use the CUDA cores.  Default 0 (CUDA cores: measured faster on the
+ * benchmark workloads).  Setting it drops the captured step graph. */
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);   /* KBL_EINVAL for an unknown key or value */
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 
 /* ---- Batched form -----------------------------------------------------------
  * Many independent 2D problems (axis-aligned quad meshes) with uneven element
- * counts and orders p = 1..4, advanced together: every phase of a stage runs as
- * ONE persistent launch over all problems (blocks pull cost-sorted work items
- * from a device counter), and a whole step is one captured CUDA graph.  Each
+ * counts and orders p = 1..4, advanced together: a whole step is ONE persistent
+ * launch over all problems and phases (blocks pull cost-sorted work items from a
+ * device counter; see kbl_batch_set_form), captured once as a CUDA graph.  Each
  * problem keeps its own time step.  Precision is KBL_FP32_MIXED.
  * Problem i's data are concatenated in problem order: nbr (E_i x 4, element
  * indices local to the problem, negative = local boundary id), h (E_i x 2),
@@ -341,12 +345,26 @@ kbl_status kbl_batch_run_host(kbl_batch* b, const double* w_host_in, double* w_h
  * stream around that launch alone; synchronous): for measuring the dominant phase in the
  * launch shape the step graph uses.  KBL_ESTATE before any kbl_batch_bounds call. */
 kbl_status kbl_batch_bounds_ms(kbl_batch* b, double* ms);
+/* Form of kbl_batch_step: 1 (default) ONE persistent launch for the whole step, whose blocks pull
+ * the work items of all 13 phases (time step; per stage traces, bounds, residual, stage +
+ * limiter) in phase order and wait, per problem, only for the earlier phases that problem's item
+ * depends on (bounded waits: a wait that runs out raises the timeout flag, which
+ * kbl_batch_check reports as KBL_ETIMEOUT, and ends the launch); 0 one persistent launch per
+ * phase (14 launches).  Both run the same device code per element: results are identical.
+ * Drops the captured graphs.  KBL_EINVAL for other values. */
+kbl_status kbl_batch_set_form(kbl_batch* b, int fused);
+/* For testing the timeout path of the fused form without a fault: with on != 0 the first bounds
+ * item of the next steps waits for a completion count that no item reaches, so that wait runs
+ * out after wait_polls polls of about a microsecond (a second by default) and the step ends
+ * with KBL_ETIMEOUT (its state is then undefined); on = 0 restores normal steps.  wait_polls
+ * also bounds every other wait of the fused form.  Drops the captured graphs. */
+kbl_status kbl_batch_stall_test(kbl_batch* b, int on, int wait_polls);
 /* Per-problem time step of the last step (HOST, n_problems values; synchronous). */
 kbl_status kbl_batch_dt(kbl_batch* b, double* dt_host);
 /* Time the bounds phase on state w for every combination of thread tile
- * (4x4 / 4x2 velocity nodes per thread), elements per work item and resident
- * blocks per SM, on a fixed sample of the work items (every eighth), and keep
- * the fastest.  Synchronous.  out_ms (may be NULL) receives the best time of
+ * (velocity nodes per thread: 4x4, 4x2, 2x4; the fused form takes the 128-thread 4x2 and 2x4),
+ * elements per work item and resident blocks per SM, on a fixed sample of the work items
+ * (every eighth), and keep the fastest.  Synchronous.  out_ms (may be NULL) receives the best time of
  * the sample, out_cmp (may be NULL) the envelope comparisons the sample needs
  * (4 |S| N_u per element). */
 kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, double* out_cmp);

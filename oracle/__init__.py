@@ -50,6 +50,11 @@ class _Mesh(C.Structure):
                 ("n_bc", C.c_int), ("bc", C.POINTER(C.c_double))]
 
 
+class _TriMesh(C.Structure):
+    _fields_ = [("n_elem", C.c_int), ("xy", C.POINTER(C.c_double)), ("nbr", C.POINTER(C.c_int)),
+                ("nbr_edge", C.POINTER(C.c_int)), ("n_bc", C.c_int), ("bc", C.POINTER(C.c_double))]
+
+
 def _load():
     global _lib
     with _lock:
@@ -58,6 +63,7 @@ def _load():
             d = C.POINTER(C.c_double)
             cfgp = C.POINTER(_Cfg)
             meshp = C.POINTER(_Mesh)
+            trip = C.POINTER(_TriMesh)
             sig = {
                 "orc_legendre": (None, [C.c_int, C.c_double, d, d]),
                 "orc_gauss_legendre": (C.c_int, [C.c_int, d, d]),
@@ -84,6 +90,12 @@ def _load():
                 "orc_stage_combine": (None, [cfgp, meshp, C.c_int, d, d, d, C.c_double, d]),
                 "orc_dt": (C.c_double, [cfgp, meshp, d, C.c_double]),
                 "orc_ssprk3_step": (C.c_int, [cfgp, meshp, d, C.c_double, d]),
+                "orc_tri_points": (C.c_int, [C.c_int, d, d]),
+                "orc_tri_traces": (None, [cfgp, trip, d, d]),
+                "orc_tri_gather_stencil": (None, [cfgp, trip, d, d, C.c_int, d]),
+                "orc_tri_rhs": (None, [cfgp, trip, d, d, d]),
+                "orc_tri_dt": (C.c_double, [cfgp, trip, d, C.c_double]),
+                "orc_tri_ssprk3_step": (C.c_int, [cfgp, trip, d, C.c_double, d]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -350,4 +362,69 @@ def ssprk3_step(cfg: Config, mesh: Mesh, w, dt_):
     alpha = np.zeros((2, mesh.n_elem))
     _check(_load().orc_ssprk3_step(C.byref(cfg._c()), C.byref(mesh._c()), _dp(w), float(dt_),
                                    _dp(alpha)), "ssprk3_step")
+    return w, alpha
+
+
+# ---- triangles (Sec. 5) ----------------------------------------------------
+class TriMesh:
+    """Affine triangles: xy[E][3][2] (counterclockwise), nbr[E][3] (element across edge f from vertex f
+    to vertex f+1, < 0 boundary id -(nbr+1)), nbr_edge[E][3] (the neighbour's matched edge), bc."""
+
+    def __init__(self, xy, nbr, nbr_edge, bc=None):
+        self.xy = np.ascontiguousarray(xy, dtype=np.float64)
+        self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        self.nbr_edge = np.ascontiguousarray(nbr_edge, dtype=np.int32)
+        self.n_elem = self.nbr.shape[0]
+        self.bc = np.ascontiguousarray(bc if bc is not None else np.zeros((1, 4)), dtype=np.float64)
+
+    def _c(self):
+        return _TriMesh(self.n_elem, _dp(self.xy), self.nbr.ctypes.data_as(C.POINTER(C.c_int)),
+                        self.nbr_edge.ctypes.data_as(C.POINTER(C.c_int)), self.bc.shape[0], _dp(self.bc))
+
+
+def tri_ns(p):
+    return (p + 1) * (p + 2) // 2
+
+
+def tri_points(p):
+    """Williams-Shunn solution points rs[ns][2] and weights w[ns] on (0,0), (1,0), (0,1)."""
+    ns = tri_ns(p)
+    rs, w = np.zeros((ns, 2)), np.zeros(ns)
+    _check(_load().orc_tri_points(int(p), _dp(rs), _dp(w)), "tri_points")
+    return rs, w
+
+
+def tri_traces(cfg: Config, m: TriMesh, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    wf = np.zeros((m.n_elem, 3 * (cfg.p + 1), 4))
+    _load().orc_tri_traces(C.byref(cfg._c()), C.byref(m._c()), _dp(w), _dp(wf))
+    return wf
+
+
+def tri_gather_stencil(cfg: Config, m: TriMesh, w, wf, e):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    wf = np.ascontiguousarray(wf, dtype=np.float64)
+    S = np.zeros((tri_ns(cfg.p) + 6 * (cfg.p + 1), 4))
+    _load().orc_tri_gather_stencil(C.byref(cfg._c()), C.byref(m._c()), _dp(w), _dp(wf), int(e), _dp(S))
+    return S
+
+
+def tri_rhs(cfg: Config, m: TriMesh, w, wf):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    wf = np.ascontiguousarray(wf, dtype=np.float64)
+    R = np.zeros_like(w)
+    _load().orc_tri_rhs(C.byref(cfg._c()), C.byref(m._c()), _dp(w), _dp(wf), _dp(R))
+    return R
+
+
+def tri_dt(cfg: Config, m: TriMesh, w, cfl):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    return _load().orc_tri_dt(C.byref(cfg._c()), C.byref(m._c()), _dp(w), float(cfl))
+
+
+def tri_ssprk3_step(cfg: Config, m: TriMesh, w, dt_):
+    w = np.array(w, dtype=np.float64, order="C")
+    alpha = np.zeros((2, m.n_elem))
+    _check(_load().orc_tri_ssprk3_step(C.byref(cfg._c()), C.byref(m._c()), _dp(w), float(dt_), _dp(alpha)),
+           "tri_ssprk3_step")
     return w, alpha

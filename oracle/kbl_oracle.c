@@ -790,3 +790,396 @@ int orc_ssprk3_step(const orc_cfg* c, const orc_mesh* m, double* w, double dt,
     free(wn); free(ws); free(wo); free(R); free(wf); free(bnd);
     return rc;
 }
+
+/* ===================================================================== */
+/* Triangles (Sec. 5: Williams-Shunn solution points, Gauss-Legendre flux */
+/* points), affine elements, flux reconstruction with the DG correction.  */
+/* ===================================================================== */
+/* Reference triangle: vertices (0,0), (1,0), (0,1); (r, s) coordinates; barycentrics
+ * (1 - r - s, r, s).  Edge f runs from vertex f to vertex (f + 1) % 3.  Arrays of
+ * the triangle path are element-major: w[E][ns][4], wf[E][nfp][4]. */
+
+int orc_tri_ns(int p) { return (p + 1) * (p + 2) / 2; }
+int orc_tri_nfp(int p) { return 3 * (p + 1); }
+
+/* Exact integral over the reference triangle of r^i s^j: i! j! / (i + j + 2)!. */
+static double orc_tri_monomial_integral(int i, int j)
+{
+    double num = 1.0, den = 1.0;
+    for (int k = 2; k <= i; k++) num *= k;
+    for (int k = 2; k <= j; k++) num *= k;
+    for (int k = 2; k <= i + j + 2; k++) den *= k;
+    return num / den;
+}
+
+/* The six points of two symmetric orbits (a, a), (1 - 2a, a), (a, 1 - 2a) with weights W. */
+static void orc_tri_orbits6(double a1, double a2, double* rs)
+{
+    const double a[2] = {a1, a2};
+    for (int o = 0; o < 2; o++) {
+        rs[(3 * o + 0) * 2 + 0] = a[o];            rs[(3 * o + 0) * 2 + 1] = a[o];
+        rs[(3 * o + 1) * 2 + 0] = 1.0 - 2 * a[o];  rs[(3 * o + 1) * 2 + 1] = a[o];
+        rs[(3 * o + 2) * 2 + 0] = a[o];            rs[(3 * o + 2) * 2 + 1] = 1.0 - 2 * a[o];
+    }
+}
+
+/* Residuals of the moment equations of the 6-point rule on r^k, k = 0..4. */
+static void orc_tri_res6(const double* x, double* F)
+{
+    double rs[12];
+    orc_tri_orbits6(x[0], x[1], rs);
+    for (int k = 0; k < 4; k++) {
+        const int deg = k == 0 ? 0 : k + 1;   /* 1, r^2, r^3, r^4 */
+        double q = 0.0;
+        for (int i = 0; i < 6; i++) q += (i < 3 ? x[2] : x[3]) * pow(rs[2 * i], deg);
+        F[k] = q - orc_tri_monomial_integral(deg, 0);
+    }
+}
+
+/* Williams-Shunn solution points and their quadrature weights on the reference triangle.
+ * p = 1: the 3-point interior symmetric rule, barycentric (2/3, 1/6, 1/6), weights 1/6,
+ * exact to degree 2.  p = 2: the 6-point rule of two symmetric orbits exact to degree 4 (its
+ * four moment equations on 1, r^2, r^3, r^4 fix the two orbit parameters and the two weights),
+ * solved by Newton's method with a finite-difference Jacobian from (0.1, 0.45, 0.05, 0.11).
+ * rs[ns][2], w[ns]; returns 0, or -2 for another order. */
+int orc_tri_points(int p, double* rs, double* w)
+{
+    if (p == 1) {
+        const double a = 1.0 / 6.0;
+        rs[0] = a;           rs[1] = a;
+        rs[2] = 1.0 - 2 * a; rs[3] = a;
+        rs[4] = a;           rs[5] = 1.0 - 2 * a;
+        w[0] = w[1] = w[2] = 1.0 / 6.0;
+        return 0;
+    }
+    if (p != 2) return -2;
+    double x[4] = {0.1, 0.45, 0.05, 0.11};
+    for (int it = 0; it < 60; it++) {
+        double F[4], J[4][5];
+        orc_tri_res6(x, F);
+        double nrm = 0.0;
+        for (int k = 0; k < 4; k++) nrm += fabs(F[k]);
+        if (nrm < 1e-16) break;
+        for (int c = 0; c < 4; c++) {
+            double xp[4], Fp[4];
+            memcpy(xp, x, sizeof(xp));
+            const double hstep = 1e-7 * (fabs(x[c]) + 1e-3);
+            xp[c] += hstep;
+            orc_tri_res6(xp, Fp);
+            for (int k = 0; k < 4; k++) J[k][c] = (Fp[k] - F[k]) / hstep;
+        }
+        for (int k = 0; k < 4; k++) J[k][4] = -F[k];
+        /* Gaussian elimination with partial pivoting */
+        for (int c = 0; c < 4; c++) {
+            int piv = c;
+            for (int r = c + 1; r < 4; r++)
+                if (fabs(J[r][c]) > fabs(J[piv][c])) piv = r;
+            for (int k = 0; k < 5; k++) { double t = J[c][k]; J[c][k] = J[piv][k]; J[piv][k] = t; }
+            for (int r = c + 1; r < 4; r++) {
+                const double f = J[r][c] / J[c][c];
+                for (int k = c; k < 5; k++) J[r][k] -= f * J[c][k];
+            }
+        }
+        double dx[4];
+        for (int c = 3; c >= 0; c--) {
+            double t = J[c][4];
+            for (int k = c + 1; k < 4; k++) t -= J[c][k] * dx[k];
+            dx[c] = t / J[c][c];
+        }
+        for (int c = 0; c < 4; c++) x[c] += dx[c];
+    }
+    orc_tri_orbits6(x[0], x[1], rs);
+    for (int i = 0; i < 6; i++) w[i] = i < 3 ? x[2] : x[3];
+    return 0;
+}
+
+/* Monomials r^a s^b with a + b <= p, in the order a + b = 0, 1, ..., p and a descending. */
+static int orc_tri_monomials(int p, int* ea, int* eb)
+{
+    int n = 0;
+    for (int d = 0; d <= p; d++)
+        for (int a = d; a >= 0; a--) { ea[n] = a; eb[n] = d - a; n++; }
+    return n;
+}
+
+typedef struct {
+    int p, ns, nfp;
+    double rs[6][2], wq[6];          /* solution points, weights (sum 1/2) */
+    double C[6][6];                  /* phi_j = sum_m C[m][j] r^a_m s^b_m */
+    double fr[9][2];                 /* flux points (reference) */
+    double gw[9];                    /* Gauss-Legendre weight of each flux point (sum 2 per edge) */
+    double phi_f[9][6];              /* phi_j at the flux points */
+    double dr[6][6], ds[6][6];       /* d phi_j / dr, / ds at the solution points [i][j] */
+} orc_triops;
+
+static double orc_tri_phi(const orc_triops* o, int j, double r, double s, int dr, int ds)
+{
+    int ea[6], eb[6];
+    const int n = orc_tri_monomials(o->p, ea, eb);
+    double v = 0.0;
+    for (int m = 0; m < n; m++) {
+        int a = ea[m], b = eb[m];
+        double coef = o->C[m][j];
+        if (dr) { if (a == 0) continue; coef *= a; a -= 1; }
+        if (ds) { if (b == 0) continue; coef *= b; b -= 1; }
+        v += coef * pow(r, a) * pow(s, b);
+    }
+    return v;
+}
+
+/* The Lagrange basis of the solution points (inverse of the monomial Vandermonde matrix by
+ * Gauss-Jordan elimination), its derivatives at the solution points, its values at the flux
+ * points (p + 1 Gauss-Legendre points on each edge, in the edge's direction). */
+static int orc_tri_build_ops(int p, orc_triops* o)
+{
+    if (p < 1 || p > 2) return -2;
+    o->p = p;
+    o->ns = orc_tri_ns(p);
+    o->nfp = orc_tri_nfp(p);
+    double rs[12], wq[6];
+    orc_tri_points(p, rs, wq);
+    int ea[6], eb[6];
+    const int n = orc_tri_monomials(p, ea, eb);
+    double A[6][12];
+    for (int i = 0; i < n; i++) {
+        o->rs[i][0] = rs[2 * i];
+        o->rs[i][1] = rs[2 * i + 1];
+        o->wq[i] = wq[i];
+        for (int m = 0; m < n; m++) A[i][m] = pow(rs[2 * i], ea[m]) * pow(rs[2 * i + 1], eb[m]);
+        for (int m = 0; m < n; m++) A[i][n + m] = (i == m) ? 1.0 : 0.0;
+    }
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        for (int k = 0; k < 2 * n; k++) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+        const double d = A[c][c];
+        for (int k = 0; k < 2 * n; k++) A[c][k] /= d;
+        for (int r = 0; r < n; r++) {
+            if (r == c) continue;
+            const double f = A[r][c];
+            for (int k = 0; k < 2 * n; k++) A[r][k] -= f * A[c][k];
+        }
+    }
+    /* V C = I with V[i][m] = mono_m(x_i): C = V^-1 is the right half */
+    for (int m = 0; m < n; m++)
+        for (int j = 0; j < n; j++) o->C[m][j] = A[m][n + j];
+    double xg[8], wg[8];
+    orc_gauss_legendre(p + 1, xg, wg);
+    const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+    for (int f = 0; f < 3; f++)
+        for (int k = 0; k <= p; k++) {
+            const double t = 0.5 * (1.0 + xg[k]);
+            const int q = f * (p + 1) + k;
+            o->fr[q][0] = V[f][0] + t * (V[(f + 1) % 3][0] - V[f][0]);
+            o->fr[q][1] = V[f][1] + t * (V[(f + 1) % 3][1] - V[f][1]);
+            o->gw[q] = wg[k];
+        }
+    for (int q = 0; q < o->nfp; q++)
+        for (int j = 0; j < n; j++) o->phi_f[q][j] = orc_tri_phi(o, j, o->fr[q][0], o->fr[q][1], 0, 0);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            o->dr[i][j] = orc_tri_phi(o, j, o->rs[i][0], o->rs[i][1], 1, 0);
+            o->ds[i][j] = orc_tri_phi(o, j, o->rs[i][0], o->rs[i][1], 0, 1);
+        }
+    return 0;
+}
+
+/* Affine geometry of element e: x = X0 + J (r, s), J = [X1 - X0 | X2 - X0]; the inverse
+ * Jacobian rows (dr/dx, dr/dy), (ds/dx, ds/dy); det J; edge lengths; outward unit normals
+ * (the vertices run counterclockwise: the outward normal of edge (dx, dy) is (dy, -dx) / L). */
+typedef struct { double rx, ry, sx, sy, det, len[3], nx[3], ny[3]; } orc_trigeo;
+
+static void orc_tri_geometry(const orc_trimesh* m, int e, orc_trigeo* g)
+{
+    const double* X = m->xy + (size_t)e * 6;
+    const double J00 = X[2] - X[0], J10 = X[3] - X[1], J01 = X[4] - X[0], J11 = X[5] - X[1];
+    g->det = J00 * J11 - J01 * J10;
+    g->rx = J11 / g->det;  g->ry = -J01 / g->det;
+    g->sx = -J10 / g->det; g->sy = J00 / g->det;
+    for (int f = 0; f < 3; f++) {
+        const double dx = X[2 * ((f + 1) % 3)] - X[2 * f], dy = X[2 * ((f + 1) % 3) + 1] - X[2 * f + 1];
+        g->len[f] = sqrt(dx * dx + dy * dy);
+        g->nx[f] = dy / g->len[f];
+        g->ny[f] = -dx / g->len[f];
+    }
+}
+
+/* Interior values at the flux points: interpolation of the solution polynomial. */
+void orc_tri_traces(const orc_cfg* c, const orc_trimesh* m, const double* w, double* wf)
+{
+    orc_triops o;
+    if (orc_tri_build_ops(c->p, &o)) return;
+    for (int e = 0; e < m->n_elem; e++)
+        for (int q = 0; q < o.nfp; q++)
+            for (int v = 0; v < 4; v++) {
+                double s = 0.0;
+                for (int j = 0; j < o.ns; j++) s += o.phi_f[q][j] * w[((size_t)e * o.ns + j) * 4 + v];
+                wf[((size_t)e * o.nfp + q) * 4 + v] = s;
+            }
+}
+
+/* Exterior value at flux point k of edge f of element e: the neighbour's interior value at the
+ * same point (its matched edge runs the other way: its point p - k), or the boundary state. */
+static void orc_tri_exterior(const orc_trimesh* m, int p, const double* wf, int e, int f, int k, double* q)
+{
+    const int nb = m->nbr[e * 3 + f];
+    if (nb >= 0) {
+        const int g = m->nbr_edge[e * 3 + f];
+        const double* src = wf + ((size_t)nb * 3 * (p + 1) + g * (p + 1) + (p - k)) * 4;
+        for (int v = 0; v < 4; v++) q[v] = src[v];
+    } else {
+        for (int v = 0; v < 4; v++) q[v] = m->bc[(-nb - 1) * 4 + v];
+    }
+}
+
+/* The stencil of Sec. 5 for a triangle: its solution points, its flux points, the exterior
+ * values at the flux points; S[ns + 2 nfp][4]. */
+void orc_tri_gather_stencil(const orc_cfg* c, const orc_trimesh* m, const double* w, const double* wf, int e,
+                            double* S)
+{
+    const int p = c->p, ns = orc_tri_ns(p), nfp = orc_tri_nfp(p);
+    for (int i = 0; i < ns; i++)
+        for (int v = 0; v < 4; v++) S[i * 4 + v] = w[((size_t)e * ns + i) * 4 + v];
+    for (int q = 0; q < nfp; q++)
+        for (int v = 0; v < 4; v++) S[(ns + q) * 4 + v] = wf[((size_t)e * nfp + q) * 4 + v];
+    for (int f = 0; f < 3; f++)
+        for (int k = 0; k <= p; k++) orc_tri_exterior(m, p, wf, e, f, k, S + (ns + nfp + f * (p + 1) + k) * 4);
+}
+
+/* Common flux along the outward normal n of an edge, qi inside, qe outside: the configured 1D
+ * flux (Rusanov, HLLC or HLL) of the states rotated into the (n, t) frame, t = (-n_y, n_x),
+ * with the interior state on the minus side, and its momentum part rotated back. */
+static void orc_tri_common_flux(const orc_cfg* c, const double* qi, const double* qe, double nx, double ny,
+                                double* F)
+{
+    const double li[4] = {qi[0], qi[1] * nx + qi[2] * ny, -qi[1] * ny + qi[2] * nx, qi[3]};
+    const double le[4] = {qe[0], qe[1] * nx + qe[2] * ny, -qe[1] * ny + qe[2] * nx, qe[3]};
+    double Fl[4];
+    orc_common_flux(c, li, le, 0, Fl);
+    F[0] = Fl[0];
+    F[1] = Fl[1] * nx - Fl[2] * ny;
+    F[2] = Fl[1] * ny + Fl[2] * nx;
+    F[3] = Fl[3];
+}
+
+/* Strong-form nodal DG residual (FR with the DG correction) of an affine triangle:
+ *   R_i = -div F_h(x_i) - sum_q phi_i(x_q) (|e_q| gw_q / 2) / (det J w_i) (F*_n - F_h . n)(x_q)
+ * with F_h the interpolation of the solution-point fluxes (Eq. 2), x_q the flux points and
+ * F*_n the common normal flux.  The Williams-Shunn rule integrates the degree-2p products
+ * phi_i phi_j exactly, so the mass matrix is diag(det J w_i) and the lifting above is exact. */
+void orc_tri_rhs(const orc_cfg* c, const orc_trimesh* m, const double* w, const double* wf, double* R)
+{
+    orc_triops o;
+    if (orc_tri_build_ops(c->p, &o)) return;
+    const int ns = o.ns, nfp = o.nfp, p = c->p;
+    for (int e = 0; e < m->n_elem; e++) {
+        orc_trigeo g;
+        orc_tri_geometry(m, e, &g);
+        double Fx[6][4], Fy[6][4];
+        for (int j = 0; j < ns; j++) {
+            orc_flux(c, w + ((size_t)e * ns + j) * 4, 0, Fx[j]);
+            orc_flux(c, w + ((size_t)e * ns + j) * 4, 1, Fy[j]);
+        }
+        for (int i = 0; i < ns; i++)
+            for (int v = 0; v < 4; v++) {
+                double div = 0.0;
+                for (int j = 0; j < ns; j++) {
+                    const double dx = o.dr[i][j] * g.rx + o.ds[i][j] * g.sx;
+                    const double dy = o.dr[i][j] * g.ry + o.ds[i][j] * g.sy;
+                    div += dx * Fx[j][v] + dy * Fy[j][v];
+                }
+                R[((size_t)e * ns + i) * 4 + v] = -div;
+            }
+        for (int f = 0; f < 3; f++)
+            for (int k = 0; k <= p; k++) {
+                const int q = f * (p + 1) + k;
+                double qe[4], Fs[4];
+                orc_tri_exterior(m, p, wf, e, f, k, qe);
+                orc_tri_common_flux(c, wf + ((size_t)e * nfp + q) * 4, qe, g.nx[f], g.ny[f], Fs);
+                for (int v = 0; v < 4; v++) {
+                    double Fn = 0.0;
+                    for (int j = 0; j < ns; j++) Fn += o.phi_f[q][j] * (Fx[j][v] * g.nx[f] + Fy[j][v] * g.ny[f]);
+                    const double jump = Fs[v] - Fn;
+                    for (int i = 0; i < ns; i++)
+                        R[((size_t)e * ns + i) * 4 + v] -= o.phi_f[q][i] * (0.5 * g.len[f] * o.gw[q]) /
+                                                           (g.det * o.wq[i]) * jump;
+                }
+            }
+    }
+}
+
+/* Time step on triangles (the paper states no rule): cfl * min over elements and solution
+ * points of h_e / (|U| + c), h_e = 2 area / longest edge (the shortest altitude). */
+double orc_tri_dt(const orc_cfg* c, const orc_trimesh* m, const double* w, double cfl)
+{
+    const int ns = orc_tri_ns(c->p);
+    double best = INFINITY;
+    for (int e = 0; e < m->n_elem; e++) {
+        orc_trigeo g;
+        orc_tri_geometry(m, e, &g);
+        double lmax = g.len[0];
+        if (g.len[1] > lmax) lmax = g.len[1];
+        if (g.len[2] > lmax) lmax = g.len[2];
+        const double h = g.det / lmax;   /* 2 (det / 2) / longest edge */
+        for (int i = 0; i < ns; i++) {
+            const double* q = w + ((size_t)e * ns + i) * 4;
+            const double P = orc_pressure(c, q);
+            const double u = sqrt(q[1] * q[1] + q[2] * q[2]) / q[0];
+            const double t = h / (u + sqrt(c->gamma * P / q[0]));
+            if (t < best) best = t;
+        }
+    }
+    return cfl * best;
+}
+
+/* One SSP-RK3 step on triangles, limited after every stage as on quads (Sec. 3.9, Sec. 5):
+ * bounds of each element's stencil (orc_bounds_stencil), the residual, the Shu-Osher
+ * combination, then the limiter of the node set (orc_limit_nodes) with the Williams-Shunn
+ * weights for the mean and the flux-point values of the combined state. */
+int orc_tri_ssprk3_step(const orc_cfg* c, const orc_trimesh* m, double* w, double dt, double* alpha)
+{
+    const int p = c->p, ns = orc_tri_ns(p), nfp = orc_tri_nfp(p), E = m->n_elem, nst = ns + 2 * nfp;
+    if (p < 1 || p > 2) return -2;
+    orc_triops o;
+    orc_tri_build_ops(p, &o);
+    const size_t N = (size_t)E * ns * 4;
+    double* wn = malloc(sizeof(double) * N);
+    double* ws = malloc(sizeof(double) * N);
+    double* R = malloc(sizeof(double) * N);
+    double* wf = malloc(sizeof(double) * (size_t)E * nfp * 4);
+    double* lo = malloc(sizeof(double) * (size_t)E * 4);
+    double* hi = malloc(sizeof(double) * (size_t)E * 4);
+    double S[64 * 4], wel[4 * 6], wfel[4 * 9];
+    memcpy(wn, w, sizeof(double) * N);
+    memcpy(ws, w, sizeof(double) * N);
+    int rc = 0;
+    for (int s = 0; s < 3; s++) {
+        orc_tri_traces(c, m, ws, wf);
+        for (int e = 0; e < E; e++) {
+            orc_tri_gather_stencil(c, m, ws, wf, e, S);
+            const int r = orc_bounds_stencil(c, nst, S, lo + 4 * e, hi + 4 * e);
+            if (r) rc = r;
+        }
+        orc_tri_rhs(c, m, ws, wf, R);
+        for (size_t i = 0; i < N; i++) {
+            const double t = ws[i] + dt * R[i];
+            ws[i] = s == 0 ? t : (s == 1 ? 0.75 * wn[i] + 0.25 * t : (1.0 / 3.0) * wn[i] + (2.0 / 3.0) * t);
+        }
+        orc_tri_traces(c, m, ws, wf);
+        for (int e = 0; e < E; e++) {
+            double a[2];
+            for (int v = 0; v < 4; v++) {
+                for (int i = 0; i < ns; i++) wel[v * ns + i] = ws[((size_t)e * ns + i) * 4 + v];
+                for (int q = 0; q < nfp; q++) wfel[v * nfp + q] = wf[((size_t)e * nfp + q) * 4 + v];
+            }
+            orc_limit_nodes(c, ns, nfp, o.wq, wel, wfel, lo + 4 * e, hi + 4 * e, a);
+            for (int v = 0; v < 4; v++)
+                for (int i = 0; i < ns; i++) ws[((size_t)e * ns + i) * 4 + v] = wel[v * ns + i];
+            if (alpha && s == 2) { alpha[e] = a[0]; alpha[E + e] = a[1]; }
+        }
+    }
+    memcpy(w, ws, sizeof(double) * N);
+    free(wn); free(ws); free(R); free(wf); free(lo); free(hi);
+    return rc;
+}

@@ -128,6 +128,26 @@ double orc_dt(const orc_cfg* c, const orc_mesh* m, const double* w, double cfl);
 int orc_ssprk3_step(const orc_cfg* c, const orc_mesh* m, double* w, double dt,
                     double* alpha /* [2][E] of the last stage, or NULL */);
 
+/* ---- triangles (Sec. 5), affine elements, element-major arrays ------- */
+typedef struct {
+    int n_elem;
+    const double* xy;     /* [E][3][2] vertices, counterclockwise */
+    const int* nbr;       /* [E][3] element across edge f (vertex f to (f+1)%3), < 0 boundary id -(nbr+1) */
+    const int* nbr_edge;  /* [E][3] the neighbour's edge matched to edge f */
+    int n_bc;
+    const double* bc;     /* [n_bc][4] */
+} orc_trimesh;
+
+int orc_tri_ns(int p);    /* (p+1)(p+2)/2 solution points */
+int orc_tri_nfp(int p);   /* 3 (p+1) flux points */
+int orc_tri_points(int p, double* rs, double* w);
+void orc_tri_traces(const orc_cfg* c, const orc_trimesh* m, const double* w, double* wf);
+void orc_tri_gather_stencil(const orc_cfg* c, const orc_trimesh* m, const double* w, const double* wf, int e,
+                            double* S);
+void orc_tri_rhs(const orc_cfg* c, const orc_trimesh* m, const double* w, const double* wf, double* R);
+double orc_tri_dt(const orc_cfg* c, const orc_trimesh* m, const double* w, double cfl);
+int orc_tri_ssprk3_step(const orc_cfg* c, const orc_trimesh* m, double* w, double dt, double* alpha);
+
 #ifdef __cplusplus
 }
 #endif

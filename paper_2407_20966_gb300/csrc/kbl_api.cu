@@ -223,28 +223,28 @@ cudaError_t dalloc(T** p, size_t count)
     return cudaMalloc((void**)p, count * sizeof(T));
 }
 
-// Issue one full SSP-RK3 step on stream s (used directly and for capture).
+// Issue one full SSP-RK3 step on stream s (for capture): the traces and the clipped time step of w
+// in one kernel, then per stage the bounds, the residual and the stage + limiter kernel, which also
+// writes the next stage's traces (stages 0 and 1) or advances the clock (stage 2): 10 kernels.
 int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s)
 {
     int n = 0, r;
-    if ((r = launch_dt(c, w, cfl, c->d_scal, 1, s)) < 0) return -1;
+    if ((r = launch_traces_dt(c, w, c->d_wf, cfl, s)) < 0) return -1;
     n += r;
     const double* wn = w;
     const double* ws = w;
     double* outs[3] = {c->d_wa, c->d_wb, w};
     for (int st = 0; st < 3; st++) {
-        if ((r = launch_traces(c, ws, c->d_wf, s)) < 0) return -1;
-        n += r;
         if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
         n += r;
         if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
         n += r;
-        if ((r = launch_stage(c, 0, st, wn, ws, c->d_R, c->d_bnd, c->d_scal, outs[st], nullptr, s)) < 0)
+        if ((r = launch_stage_step(c, st, wn, ws, c->d_R, c->d_bnd, outs[st], st < 2 ? c->d_wf : nullptr, st == 2, s)) <
+            0)
             return -1;
         n += r;
         ws = outs[st];
     }
-    n += launch_time_advance(c, s);
     return n;
 }
 
@@ -332,6 +332,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     c->nsten = c->ns + 2 * c->nfp;
     cudaError_t e;
     if ((e = dalloc(&c->d_scal, 4)) != cudaSuccess || (e = dalloc(&c->d_dtbits, 1)) != cudaSuccess ||
+        (e = dalloc(&c->d_blocks_done, 1)) != cudaSuccess ||
         (e = dalloc(&c->d_flags, 1)) != cudaSuccess) {
         kbl_destroy(c);
         return KBL_ECUDA;
@@ -356,6 +357,8 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     if (cfg->dim == 2 && cfg->precision == KBL_FP32_MIXED) c->d_tcop = kbl_rhs_tc_upload(c->ops, cfg->p);
     const double scal[4] = {0.0, 0.0, INFINITY, 0.0};
     if ((e = cudaMemcpy(c->d_scal, scal, sizeof(scal), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c->d_dtbits, 0x7f, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(c->d_blocks_done, 0, sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMemset(c->d_flags, 0, sizeof(DevFlags))) != cudaSuccess) {
         kbl_destroy(c);
         return KBL_ECUDA;
@@ -397,6 +400,7 @@ kbl_status kbl_destroy(kbl_ctx* c)
     free_mesh(c);
     if (c->d_scal) cudaFree(c->d_scal);
     if (c->d_dtbits) cudaFree(c->d_dtbits);
+    if (c->d_blocks_done) cudaFree(c->d_blocks_done);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->d_qw) cudaFree(c->d_qw);
     if (c->d_tcop) cudaFree(c->d_tcop);

@@ -169,31 +169,32 @@ k_batch_bounds(BatchDev bd, const WorkItem* __restrict__ items, int n_items, uns
     }
 }
 
-template <int N>
+template <int N, int NT = NTB>
 struct FrEpb {
-    static constexpr int EPB = NTB / (N * N);
+    static constexpr int EPB = NT / (N * N);
 };
 
+template <int NT = NTB>
 struct RhsUnion {
     union {
-        RhsSmem<2, 2, float, FrEpb<2>::EPB> s2;
-        RhsSmem<2, 3, float, FrEpb<3>::EPB> s3;
-        RhsSmem<2, 4, float, FrEpb<4>::EPB> s4;
-        RhsSmem<2, 5, float, FrEpb<5>::EPB> s5;
+        RhsSmem<2, 2, float, FrEpb<2, NT>::EPB> s2;
+        RhsSmem<2, 3, float, FrEpb<3, NT>::EPB> s3;
+        RhsSmem<2, 4, float, FrEpb<4, NT>::EPB> s4;
+        RhsSmem<2, 5, float, FrEpb<5, NT>::EPB> s5;
     };
 };
 
-template <int N>
+template <int N, int NT = NTB>
 __device__ __forceinline__ void rhs_item(void* smraw, const BatchDev& bd, const ProbDesc& pd, const WorkItem& wi,
                                          const FrOps& ops, double gamma, int flux, const double* w, const double* wf,
                                          double* R)
 {
-    constexpr int EPB = FrEpb<N>::EPB;
+    constexpr int EPB = FrEpb<N, NT>::EPB;
     auto& sm = *reinterpret_cast<RhsSmem<2, N, float, EPB>*>(smraw);
     const MeshDev m = mesh_of_prob(bd, pd);
     const int e_end = wi.e0 + wi.n;
     for (int eb = wi.e0; eb < e_end; eb += EPB)
-        rhs_block<2, N, float, EPB>(sm, NTB, w + pd.woff, wf + pd.wfoff, m, ops, gamma, R + pd.woff, eb,
+        rhs_block<2, N, float, EPB>(sm, NT, w + pd.woff, wf + pd.wfoff, m, ops, gamma, R + pd.woff, eb,
                                     min(EPB, e_end - eb), flux);
 }
 
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(NTB, 4) k_batch_rhs(BatchDev bd, const WorkIte
                                                    unsigned* counter, BatchOps ops, double gamma, int flux,
                                                    const double* w, const double* wf, double* R)
 {
-    __shared__ __align__(16) RhsUnion sm;
+    __shared__ __align__(16) RhsUnion<> sm;
     __shared__ int s_item;
     for (;;) {
         const int it = next_item(counter, n_items, &s_item);
@@ -218,26 +219,27 @@ __global__ void __launch_bounds__(NTB, 4) k_batch_rhs(BatchDev bd, const WorkIte
     }
 }
 
+template <int NT = NTB>
 struct LimUnion {
     union {
-        LimSmem<2, 2, FrEpb<2>::EPB> s2;
-        LimSmem<2, 3, FrEpb<3>::EPB> s3;
-        LimSmem<2, 4, FrEpb<4>::EPB> s4;
-        LimSmem<2, 5, FrEpb<5>::EPB> s5;
+        LimSmem<2, 2, FrEpb<2, NT>::EPB> s2;
+        LimSmem<2, 3, FrEpb<3, NT>::EPB> s3;
+        LimSmem<2, 4, FrEpb<4, NT>::EPB> s4;
+        LimSmem<2, 5, FrEpb<5, NT>::EPB> s5;
     };
 };
 
-template <int N>
+template <int N, int NT = NTB>
 __device__ __forceinline__ void stage_item(void* smraw, const ProbDesc& pd, const WorkItem& wi, const FrOps& ops,
                                            const Phys& ph, int stage, const double* wn, const double* ws,
                                            const double* R, const double* bnd, double dt, double* wout,
                                            DevFlags* flags)
 {
-    constexpr int EPB = FrEpb<N>::EPB;
+    constexpr int EPB = FrEpb<N, NT>::EPB;
     auto& sm = *reinterpret_cast<LimSmem<2, N, EPB>*>(smraw);
     const int e_end = wi.e0 + wi.n;
     for (int eb = wi.e0; eb < e_end; eb += EPB)
-        stage_limit_block<2, N, EPB>(sm, NTB, 0, stage, wn + pd.woff, ws + pd.woff, R + pd.woff,
+        stage_limit_block<2, N, EPB>(sm, NT, 0, stage, wn + pd.woff, ws + pd.woff, R + pd.woff,
                                             bnd + pd.bndoff, dt, wout + pd.woff, nullptr, pd.E, ops, ph, flags, eb,
                                             min(EPB, e_end - eb));
 }
@@ -331,6 +333,189 @@ __global__ void k_batch_time_advance(const double* dt, double* t, int n)
     if (i < n) t[i] += dt[i];
 }
 
+// ---------------------------------------------------------------------------
+// The whole step as ONE persistent launch (dataflow).  The step's work is 13 phases -- the time
+// step, then per stage s = 0, 1, 2: traces, bounds, residual, stage + limiter -- each cut into the
+// same work items as the per-phase launches.  Blocks pull items from one counter in phase-major
+// order; an item waits only until the earlier phases its problem depends on are complete (a
+// per-problem count of finished items per phase), never on a grid-wide barrier, so the phases of
+// different problems overlap.  Dependencies of a problem's phase: bounds and residual of stage s
+// on its traces; the stage on its bounds and residual (stage 0 also on the time step); the traces
+// of stage s + 1 on the stage s (which also releases the scratch the next stage rewrites).  An
+// item depends only on items earlier in the queue, already taken by running blocks, so the
+// launch cannot deadlock whatever the residency.  Waits poll with a bounded count; one that runs
+// out raises the timeout flag and an abort word that ends every block at its next item.
+// ---------------------------------------------------------------------------
+constexpr int NTF = 128;   // threads per block of the fused step (the 4 x 2 or 2 x 4 bounds tile)
+#ifndef KBL_FUSED_MINB
+#define KBL_FUSED_MINB 6   // resident blocks per SM the fused kernel is compiled for
+#endif
+constexpr int NPH = 13;    // phases of a step
+enum { PK_DT = 0, PK_TR = 1, PK_B = 2, PK_R = 3, PK_S = 4 };
+__host__ __device__ __forceinline__ int phase_kind(int ph) { return ph == 0 ? PK_DT : 1 + (ph - 1) % 4; }
+__host__ __device__ __forceinline__ int phase_stage(int ph) { return ph == 0 ? 0 : (ph - 1) / 4; }
+
+struct FusedDev {
+    const WorkItem* fr;    // FR / limiter / time-step items
+    int n_fr;
+    const WorkItem* bi;    // bounds items
+    int n_b;
+    const int* cnt_fr;     // [P] FR items of each problem
+    const int* cnt_b;      // [P] bounds items of each problem
+    unsigned* done;        // [NPH][P] finished items of each phase and problem (zeroed before the step)
+    unsigned* queue;       // next item (zeroed before the step)
+    int* abort;            // set when a wait ran out (zeroed before the step)
+    int stall_test;        // nonzero: the first bounds item waits for a count no item reaches
+    int wait_polls;        // bound of every wait, in polls of about 1 us
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Poll until *p >= target (bounded); false when the bound ran out or another block aborted.
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned target, int polls, const int* abort)
+{
+    for (int it = 0; it < polls; it++) {
+        if (ld_acquire(p) >= target) return true;
+        if (*(volatile const int*)abort) return false;
+        __nanosleep(it < 16 ? 64 : 1024);
+    }
+    return ld_acquire(p) >= target;
+}
+
+template <int TYSEL>
+struct FusedSmem {
+    static constexpr size_t B = sizeof(BoundsUnion<TYSEL>), R_ = sizeof(RhsUnion<NTF>), L = sizeof(LimUnion<NTF>);
+    static constexpr size_t BYTES = B > R_ ? (B > L ? B : L) : (R_ > L ? R_ : L);
+};
+
+template <int TYSEL>
+__global__ void __launch_bounds__(NTF, KBL_FUSED_MINB)
+k_batch_step_fused(BatchDev bd, FusedDev fd, BatchOps ops, Phys ph, double cfl, double* w, double* wa, double* wb,
+                   double* wf, double* R, double* bnd, unsigned long long* dtbits, double* dtv, double* tv,
+                   DevFlags* flags)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_item, s_ok;
+    const int P = bd.n_probs;
+    const int total = 10 * fd.n_fr + 3 * fd.n_b;
+    double* outs[3] = {wa, wb, w};
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned it = atomicAdd(fd.queue, 1u);
+            s_item = (it < (unsigned)total && !*(volatile int*)fd.abort) ? (int)it : -1;
+        }
+        __syncthreads();
+        int idx = s_item;
+        if (idx < 0) break;
+        int phs = 0;
+        for (; phs < NPH - 1; phs++) {
+            const int n = phase_kind(phs) == PK_B ? fd.n_b : fd.n_fr;
+            if (idx < n) break;
+            idx -= n;
+        }
+        const int kind = phase_kind(phs), st = phase_stage(phs);
+        const WorkItem wi = kind == PK_B ? fd.bi[idx] : fd.fr[idx];
+        const int prob = wi.prob;
+        // dependencies (thread 0 waits; the block follows)
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            const unsigned nfr = (unsigned)fd.cnt_fr[prob], nb = (unsigned)fd.cnt_b[prob];
+            if (kind == PK_TR && st > 0) ok = wait_count(fd.done + (size_t)(phs - 1) * P + prob, nfr, fd.wait_polls, fd.abort);
+            if (kind == PK_B) {
+                const unsigned extra = (fd.stall_test && phs == 2 && idx == 0) ? 1u : 0u;   // a count never reached
+                ok = wait_count(fd.done + (size_t)(phs - 1) * P + prob, nfr + extra, fd.wait_polls, fd.abort);
+            }
+            if (kind == PK_R) ok = wait_count(fd.done + (size_t)(phs - 2) * P + prob, nfr, fd.wait_polls, fd.abort);
+            if (kind == PK_S) {
+                ok = wait_count(fd.done + (size_t)(phs - 2) * P + prob, nb, fd.wait_polls, fd.abort) &&
+                     wait_count(fd.done + (size_t)(phs - 1) * P + prob, nfr, fd.wait_polls, fd.abort);
+                if (ok && st == 0) ok = wait_count(fd.done + prob, nfr, fd.wait_polls, fd.abort);
+            }
+            if (!ok) {
+                if (!*(volatile int*)fd.abort) atomicOr(&flags->timeout, 1);
+                atomicExch(fd.abort, 1);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        __threadfence();
+        const ProbDesc pd = bd.probs[prob];
+        const double* ws = st == 0 ? w : outs[st - 1];
+        if (kind == PK_DT) {
+            float b = FLT_MAX;
+            switch (pd.p) {
+                case 1: b = dt_item<2>(bd, pd, wi, (float)ph.gamma, (float)cfl, w); break;
+                case 2: b = dt_item<3>(bd, pd, wi, (float)ph.gamma, (float)cfl, w); break;
+                case 3: b = dt_item<4>(bd, pd, wi, (float)ph.gamma, (float)cfl, w); break;
+                case 4: b = dt_item<5>(bd, pd, wi, (float)ph.gamma, (float)cfl, w); break;
+            }
+            unsigned long long bits = __double_as_longlong(to_f64<float>(b));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+                bits = ob < bits ? ob : bits;
+            }
+            if ((threadIdx.x & 31) == 0) atomicMin(dtbits + prob, bits);
+        } else if (kind == PK_TR) {
+            switch (pd.p) {
+                case 1: traces_item<2>(pd, wi, ops.o[1], ws, wf); break;
+                case 2: traces_item<3>(pd, wi, ops.o[2], ws, wf); break;
+                case 3: traces_item<4>(pd, wi, ops.o[3], ws, wf); break;
+                case 4: traces_item<5>(pd, wi, ops.o[4], ws, wf); break;
+            }
+        } else if (kind == PK_B) {
+            switch (pd.p) {
+                case 1: bounds_item<2, TYSEL>(smraw, bd, pd, wi, ph, ws, wf, bnd, flags); break;
+                case 2: bounds_item<3, TYSEL>(smraw, bd, pd, wi, ph, ws, wf, bnd, flags); break;
+                case 3: bounds_item<4, TYSEL>(smraw, bd, pd, wi, ph, ws, wf, bnd, flags); break;
+                case 4: bounds_item<5, TYSEL>(smraw, bd, pd, wi, ph, ws, wf, bnd, flags); break;
+            }
+        } else if (kind == PK_R) {
+            switch (pd.p) {
+                case 1: rhs_item<2, NTF>(smraw, bd, pd, wi, ops.o[1], ph.gamma, ph.flux, ws, wf, R); break;
+                case 2: rhs_item<3, NTF>(smraw, bd, pd, wi, ops.o[2], ph.gamma, ph.flux, ws, wf, R); break;
+                case 3: rhs_item<4, NTF>(smraw, bd, pd, wi, ops.o[3], ph.gamma, ph.flux, ws, wf, R); break;
+                case 4: rhs_item<5, NTF>(smraw, bd, pd, wi, ops.o[4], ph.gamma, ph.flux, ws, wf, R); break;
+            }
+        } else {
+            // the problem's time step (all its time-step items are complete): k_batch_dt_finalize's decoding
+            double dtp = __longlong_as_double((long long)atomicAdd(dtbits + prob, 0ull));
+            if (!(dtp > 0.0) || !(dtp < DBL_MAX)) dtp = 0.0;
+            switch (pd.p) {
+                case 1: stage_item<2, NTF>(smraw, pd, wi, ops.o[1], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
+                case 2: stage_item<3, NTF>(smraw, pd, wi, ops.o[2], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
+                case 3: stage_item<4, NTF>(smraw, pd, wi, ops.o[3], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
+                case 4: stage_item<5, NTF>(smraw, pd, wi, ops.o[4], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
+            }
+            if (st == 2) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    // the problem's last stage-2 item: publish its time step and advance its clock
+                    if (atomicAdd(fd.done + (size_t)phs * P + prob, 1u) + 1u == (unsigned)fd.cnt_fr[prob]) {
+                        dtv[prob] = dtp;
+                        tv[prob] += dtp;
+                    }
+                }
+                continue;
+            }
+        }
+        // publish: this item's writes before its count
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(fd.done + (size_t)phs * P + prob, 1u);
+        }
+    }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -389,6 +574,13 @@ struct kbl_batch {
     // timing of the bounds launch of kbl_batch_bounds (kbl_batch_bounds_ms)
     cudaEvent_t tb0 = nullptr, tb1 = nullptr;
     bool tb_valid = false;
+    // the fused single-launch step (default) and its control words
+    int fused = 1;
+    int stall_test = 0;
+    int wait_polls = 1 << 20;          // about a second per wait
+    int* d_cnt = nullptr;              // [2][P]: FR items, bounds items of each problem
+    unsigned* d_done = nullptr;        // [13][P] finished items per phase and problem
+    unsigned* d_fctl = nullptr;        // [0] queue, [1] abort; per group g at 2 + 2 g
 };
 
 namespace {
@@ -399,9 +591,11 @@ kbl_status bfail(kbl_batch* b, kbl_status st, const std::string& msg)
     return st;
 }
 
+// launch-shape tile index -> thread tile of the bounds body: 0 = 4x4 (64 threads), 1 = 4x2, 2 = 2x4
+// (128 threads each)
 size_t bounds_smem(int tile)
 {
-    return tile ? sizeof(BoundsUnion<2>) : sizeof(BoundsUnion<0>);
+    return tile == 2 ? sizeof(BoundsUnion<3>) : tile == 1 ? sizeof(BoundsUnion<2>) : sizeof(BoundsUnion<0>);
 }
 
 std::vector<WorkItem> make_items(const std::vector<ProbDesc>& probs, int chunk, int p0 = 0, int p1 = -1)
@@ -449,7 +643,10 @@ int launch_bounds_phase(kbl_batch* b, const double* w, const double* wf, double*
     const BatchDev bd = dev_of(b);
     const size_t smem = bounds_smem(b->tile);
     const int grid = grid_of(b, b->blocks_per_sm);
-    if (b->tile)
+    if (b->tile == 2)
+        k_batch_bounds<3><<<grid, B2f32<NX_B, 3>::NT, smem, s>>>(bd, items, n_items, counter, b->phys, w, wf, bnd,
+                                                                  b->d_flags);
+    else if (b->tile)
         k_batch_bounds<2><<<grid, B2f32<NX_B, 2>::NT, smem, s>>>(bd, items, n_items, counter, b->phys, w, wf, bnd,
                                                                   b->d_flags);
     else
@@ -491,7 +688,7 @@ int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const 
     cudaMemsetAsync(b->d_dtbits + is.p0, 0x7f, (size_t)np * sizeof(unsigned long long), s);
     const int g_tr = grid_of(b, fr_blocks_per_sm((const void*)k_batch_traces, 0));
     const int g_rhs = grid_of(b, fr_blocks_per_sm((const void*)k_batch_rhs, 0));
-    const int g_st = grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion)));
+    const int g_st = grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion<>)));
     const int g_dt = grid_of(b, fr_blocks_per_sm((const void*)k_batch_dt, 0));
     k_batch_dt<<<g_dt, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 0, b->phys.gamma, cfl, w, b->d_dtbits);
     k_batch_dt_finalize<<<(np + 255) / 256, 256, 0, s>>>(b->d_dtbits + is.p0, b->d_dt + is.p0, b->d_t + is.p0, np);
@@ -504,7 +701,7 @@ int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const 
         n += launch_bounds_phase(b, ws, b->d_wf, b->d_bnd, is.counters + 2 + 4 * st, s, is.bi, is.n_bi);
         k_batch_rhs<<<g_rhs, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 3 + 4 * st, b->ops, b->phys.gamma,
                                           b->phys.flux, ws, b->d_wf, b->d_R);
-        k_batch_stage<<<g_st, NTB, sizeof(LimUnion), s>>>(bd, is.fr, is.n_fr, is.counters + 4 + 4 * st, b->ops,
+        k_batch_stage<<<g_st, NTB, sizeof(LimUnion<>), s>>>(bd, is.fr, is.n_fr, is.counters + 4 + 4 * st, b->ops,
                                                           b->phys, st, wn, ws, b->d_R, b->d_bnd, b->d_dt, outs[st],
                                                           b->d_flags);
         n += 3;
@@ -513,6 +710,8 @@ int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const 
     k_batch_time_advance<<<(np + 255) / 256, 256, 0, s>>>(b->d_dt + is.p0, b->d_t + is.p0, np);
     return n + 1;
 }
+
+int issue_batch_step_fused(kbl_batch* b, double* w, double cfl, cudaStream_t s, const ItemSet& is, unsigned* ctl);
 
 // Capture one step of `is` on state w as a graph.
 cudaError_t capture_step(kbl_batch* b, double* w, double cfl, const ItemSet& is, cudaGraphExec_t* out, int* kernels)
@@ -526,7 +725,7 @@ cudaError_t capture_step(kbl_batch* b, double* w, double cfl, const ItemSet& is,
         cudaStreamDestroy(cap);
         return e;
     }
-    *kernels = issue_batch_step(b, w, cfl, cap, is);
+    *kernels = b->fused ? issue_batch_step_fused(b, w, cfl, cap, is, is.counters) : issue_batch_step(b, w, cfl, cap, is);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
@@ -549,6 +748,65 @@ void drop_groups(kbl_batch* b)
     b->groups.clear();
 }
 
+// Items per problem (FR and bounds) for the fused step's dependency counts.
+cudaError_t upload_counts(kbl_batch* b)
+{
+    std::vector<int> cnt(2 * (size_t)b->P, 0);
+    for (int i = 0; i < b->P; i++) {
+        cnt[i] = (b->probs[i].E + FR_CHUNK - 1) / FR_CHUNK;
+        cnt[b->P + i] = (b->probs[i].E + b->chunk - 1) / b->chunk;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b->d_cnt) e = cudaMalloc((void**)&b->d_cnt, cnt.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
+    return e;
+}
+
+template <int TYSEL>
+int fused_blocks_per_sm()
+{
+    int n = 0;
+    const size_t smem = FusedSmem<TYSEL>::BYTES;
+    cudaFuncSetAttribute(k_batch_step_fused<TYSEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step_fused<TYSEL>, NTF, smem);
+    return std::max(1, n);
+}
+
+// One SSP-RK3 step of the problems of `is` as ONE kernel launch (plus the resets of its control
+// words); ctl: [queue, abort] of this launch.
+int issue_batch_step_fused(kbl_batch* b, double* w, double cfl, cudaStream_t s, const ItemSet& is, unsigned* ctl)
+{
+    const int np = is.p1 - is.p0;
+    cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+    cudaMemsetAsync(b->d_done, 0, (size_t)NPH * b->P * sizeof(unsigned), s);
+    cudaMemsetAsync(b->d_dtbits + is.p0, 0x7f, (size_t)np * sizeof(unsigned long long), s);
+    FusedDev fd;
+    fd.fr = is.fr;
+    fd.n_fr = is.n_fr;
+    fd.bi = is.bi;
+    fd.n_b = is.n_bi;
+    fd.cnt_fr = b->d_cnt;
+    fd.cnt_b = b->d_cnt + b->P;
+    fd.done = b->d_done;
+    fd.queue = ctl;
+    fd.abort = reinterpret_cast<int*>(ctl + 1);
+    fd.stall_test = b->stall_test;
+    fd.wait_polls = b->wait_polls;
+    const BatchDev bd = dev_of(b);
+    if (b->tile == 2) {
+        const int grid = b->nsm * std::min(fused_blocks_per_sm<3>(), std::max(1, b->blocks_per_sm));
+        k_batch_step_fused<3><<<grid, NTF, FusedSmem<3>::BYTES, s>>>(bd, fd, b->ops, b->phys, cfl, w, b->d_wa, b->d_wb,
+                                                                   b->d_wf, b->d_R, b->d_bnd, b->d_dtbits, b->d_dt,
+                                                                   b->d_t, b->d_flags);
+    } else {
+        const int grid = b->nsm * std::min(fused_blocks_per_sm<2>(), std::max(1, b->blocks_per_sm));
+        k_batch_step_fused<2><<<grid, NTF, FusedSmem<2>::BYTES, s>>>(bd, fd, b->ops, b->phys, cfl, w, b->d_wa, b->d_wb,
+                                                                   b->d_wf, b->d_R, b->d_bnd, b->d_dtbits, b->d_dt,
+                                                                   b->d_t, b->d_flags);
+    }
+    return 1;
+}
+
 void drop_graph(kbl_batch* b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -563,6 +821,7 @@ cudaError_t set_bounds_shape(kbl_batch* b, int tile, int chunk, int per_sm)
     if (chunk != b->chunk || !b->d_b_items) {
         b->chunk = chunk;
         cudaError_t e = upload_items(b, make_items(b->probs, chunk), &b->d_b_items, &b->n_b_items);
+        if (e == cudaSuccess) e = upload_counts(b);
         if (e != cudaSuccess) return e;
     }
     drop_graph(b);
@@ -574,7 +833,10 @@ int max_bounds_blocks(int tile)
 {
     int n = 0;
     const size_t smem = bounds_smem(tile);
-    if (tile) {
+    if (tile == 2) {
+        cudaFuncSetAttribute(k_batch_bounds<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_bounds<3>, B2f32<NX_B, 3>::NT, smem);
+    } else if (tile) {
         cudaFuncSetAttribute(k_batch_bounds<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_bounds<2>, B2f32<NX_B, 2>::NT, smem);
     } else {
@@ -684,6 +946,7 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
     A((void**)&b->d_dtbits, P * sizeof(unsigned long long));
     A((void**)&b->d_flags, sizeof(DevFlags));
     A((void**)&b->d_counters, NCOUNTERS * sizeof(unsigned));
+    A((void**)&b->d_done, (size_t)NPH * P * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_probs, b->probs.data(), P * sizeof(ProbDesc), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_nbr, nbr, eoff * 4 * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_h, h, eoff * 2 * sizeof(double), cudaMemcpyHostToDevice);
@@ -692,8 +955,8 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
     if (e == cudaSuccess) e = cudaMemset(b->d_t, 0, P * sizeof(double));
     if (e == cudaSuccess) e = upload_items(b, make_items(b->probs, FR_CHUNK), &b->d_fr_items, &b->n_fr_items);
     if (e == cudaSuccess) {
-        cudaFuncSetAttribute(k_batch_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LimUnion));
-        e = set_bounds_shape(b, 0, 16, max_bounds_blocks(0));
+        cudaFuncSetAttribute(k_batch_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LimUnion<>));
+        e = set_bounds_shape(b, 1, 16, max_bounds_blocks(1));
     }
     if (e != cudaSuccess) {
         kbl_batch_destroy(b);
@@ -714,6 +977,8 @@ kbl_status kbl_batch_destroy(kbl_batch* b)
     if (b->s_d2h) cudaStreamDestroy(b->s_d2h);
     if (b->tb0) cudaEventDestroy(b->tb0);
     if (b->tb1) cudaEventDestroy(b->tb1);
+    if (b->d_cnt) cudaFree(b->d_cnt);
+    if (b->d_done) cudaFree(b->d_done);
     void* ptrs[] = {b->d_probs, b->d_nbr, b->d_h, b->d_bc, b->d_wf, b->d_R, b->d_bnd, b->d_wa, b->d_wb, b->d_dt,
                     b->d_t, b->d_dtbits, b->d_flags, b->d_counters, b->d_fr_items, b->d_b_items};
     for (void* q : ptrs)
@@ -911,7 +1176,7 @@ kbl_status kbl_batch_stage(kbl_batch* b, int st, const double* wn, const double*
     if (!wn || !ws || !R || !bnd || !dt_dev || !wout) return bfail(b, KBL_EINVAL, "null array");
     cudaStream_t s = b->stream;
     cudaMemsetAsync(b->d_counters, 0, NCOUNTERS * sizeof(unsigned), s);
-    k_batch_stage<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion))), NTB, sizeof(LimUnion),
+    k_batch_stage<<<grid_of(b, fr_blocks_per_sm((const void*)k_batch_stage, sizeof(LimUnion<>))), NTB, sizeof(LimUnion<>),
                     s>>>(dev_of(b), b->d_fr_items, b->n_fr_items, b->d_counters + 4, b->ops, b->phys, st, wn, ws, R,
                          bnd, dt_dev, wout, b->d_flags);
     b->launches += 1;
@@ -944,7 +1209,8 @@ kbl_status kbl_batch_autotune(kbl_batch* b, const double* w, double* out_ms, dou
     const int entry[3] = {b->tile, b->chunk, b->blocks_per_sm};
     int best[3] = {entry[0], entry[1], entry[2]};
     const int chunks[] = {4, 16, 64};
-    for (int tile = 0; tile < 2; tile++) {
+    // thread tiles the step's form can run: the fused launch has 128-thread blocks (4x2, 2x4)
+    for (int tile = b->fused ? 1 : 0; tile < 3; tile++) {
         const int maxb = max_bounds_blocks(tile);
         const int pers[] = {maxb, std::max(1, (3 * maxb) / 4), std::max(1, maxb / 2)};
         for (int ci = 0; ci < 3; ci++) {
@@ -1018,7 +1284,27 @@ kbl_status kbl_batch_check(kbl_batch* b)
     if (e == cudaSuccess) e = cudaMemcpy(&f, b->d_flags, sizeof(f), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(b->d_flags, 0, sizeof(DevFlags));
     if (e != cudaSuccess) return bfail(b, KBL_ECUDA, cudaGetErrorString(e));
+    if (f.timeout) return bfail(b, KBL_ETIMEOUT, "a bounded device wait of the fused step gave up");
     if (f.nonphysical) return bfail(b, KBL_ENONPHYSICAL, "non-physical stencil state");
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_set_form(kbl_batch* b, int fused)
+{
+    if (!b || (fused != 0 && fused != 1)) return bfail(b, KBL_EINVAL, "form must be 0 (per-phase launches) or 1 (one launch)");
+    b->fused = fused;
+    drop_graph(b);
+    drop_groups(b);
+    return KBL_OK;
+}
+
+kbl_status kbl_batch_stall_test(kbl_batch* b, int on, int wait_polls)
+{
+    if (!b || wait_polls < 1) return KBL_EINVAL;
+    b->stall_test = on ? 1 : 0;
+    b->wait_polls = wait_polls;
+    drop_graph(b);
+    drop_groups(b);
     return KBL_OK;
 }
 

@@ -23,8 +23,8 @@
 //
 // 2D kernels use the separable form of the Maxwellian on the tensor grid:
 // g_i(ux, uy) = (A_i exp(-(ux-Ux_i)^2/(2 theta_i))) (exp(-(uy-Uy_i)^2/(2 theta_i))),
-// so a block builds per-state row tables Ex, C*Ex, Ey and every (state, node)
-// pair then costs two multiplies and four min/max.
+// so a block builds per-state row tables (Ex, Ey; FP64 kernels also C*Ex) and every
+// (state, node) pair then costs two multiplies (g = Ex Ey and C g) and four min/max.
 //
 // FP64 kernels: the min/max run on the integer pipe as unsigned 64-bit
 // compares of the bit patterns (all values are >= +0, where integer order is

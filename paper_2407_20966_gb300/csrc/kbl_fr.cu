@@ -172,17 +172,101 @@ __global__ void __launch_bounds__(256) k_dt(const double* __restrict__ w, MeshDe
     }
 }
 
-__global__ void k_dt_finalize(const unsigned long long* dtbits, const double* scal, double* dt_out,
+__global__ void k_dt_finalize(unsigned long long* dtbits, const double* scal, double* dt_out,
                               int clip)
 {
-    // scal: [0] dt, [1] t, [2] t_end.  With clip the step stops at t_end.
+    // scal: [0] dt, [1] t, [2] t_end.  With clip the step stops at t_end.  The reduction word is
+    // left at its start value, which the fused traces + time step kernel of kbl_step relies on.
     double dt = __longlong_as_double((long long)*dtbits);
+    *dtbits = 0x7f7f7f7f7f7f7f7full;
     if (!(dt > 0.0) || !(dt < DBL_MAX)) dt = 0.0;
     if (clip) dt = fmin(dt, scal[2] - scal[1]);
     *dt_out = dt;
 }
 
 __global__ void k_time_advance(double* scal) { scal[1] += scal[0]; }
+
+// ---------------------------------------------------------------------------
+// The first work of a step in one pass over w: the face traces (as k_traces, FP64) and the time
+// step (as k_dt with its arithmetic type T), whose block minima meet in dtbits; the last block to
+// finish (a counter of finished blocks) decodes the step, clips it to the end time and resets the
+// reduction word and the counter for the next step, so that neither a memset nor a finalizing
+// kernel is needed.
+// ---------------------------------------------------------------------------
+template <int DIM, int N, typename T>
+__global__ void __launch_bounds__(256) k_traces_dt(const double* __restrict__ w, double* __restrict__ wf, MeshDev m,
+                                                   FrOps ops, double gamma_d, double cfl,
+                                                   unsigned long long* dtbits, unsigned* blocks_done, double* scal)
+{
+    constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
+    constexpr int NK = NS > NFP ? NS : NFP;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = t < (size_t)m.E * NK;
+    const int e = in ? (int)(t / NK) : 0, k = (int)(t % NK);
+    if (in && k < NFP) {   // traces: the operations and order of k_traces
+        const int fp = k;
+        const int f = (DIM == 1) ? fp : fp / N;
+        const int kk = (DIM == 1) ? 0 : fp % N;
+        const bool plus = f & 1;
+        const bool along_x = (DIM == 1) || f < 2;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const double* we = w + ((size_t)v * m.E + e) * NS;
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const double l = plus ? ops.lp[i] : ops.lm[i];
+                const int nd = along_x ? kk * N + i : i * N + kk;
+                s += l * we[(DIM == 1) ? i : nd];
+            }
+            wf[((size_t)v * m.E + e) * NFP + fp] = s;
+        }
+    }
+    double best = DBL_MAX;
+    if (in && k < NS) {    // time step: the operations of k_dt
+        const int nd = k;
+        const T gamma = (T)gamma_d;
+        T q[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) q[v] = kbl_dev::from_f64<T>(w[((size_t)v * m.E + e) * NS + nd]);
+        const T P = kbl_pressure<DIM, T>(q, gamma - T(1));
+        const T a = sqrt(gamma * P / q[0]);
+        T b = (T)DBL_MAX;
+        if (sizeof(T) == sizeof(float)) b = (T)FLT_MAX;
+#pragma unroll
+        for (int kd = 0; kd < DIM; kd++) {
+            const T cand = (T)cfl * (kbl_dev::from_f64<T>(m.h[e * DIM + kd]) / (fabs(q[1 + kd] / q[0]) + a));
+            b = fmin(b, cand);
+        }
+        best = kbl_dev::to_f64<T>(b);
+    }
+    unsigned long long bits = __double_as_longlong(best);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = ob < bits ? ob : bits;
+    }
+    __shared__ unsigned long long swarp[8];
+    __shared__ int s_last;
+    if ((threadIdx.x & 31) == 0) swarp[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) bits = swarp[q] < bits ? swarp[q] : bits;
+        atomicMin(dtbits, bits);
+        __threadfence();
+        s_last = atomicAdd(blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long fb = atomicAdd(dtbits, 0ull);
+        double dt = __longlong_as_double((long long)fb);
+        if (!(dt > 0.0) || !(dt < DBL_MAX)) dt = 0.0;
+        scal[0] = fmin(dt, scal[2] - scal[1]);   // clipped to the end time
+        *dtbits = 0x7f7f7f7f7f7f7f7full;         // the value the reduction starts from
+        *blocks_done = 0u;
+    }
+}
 
 template <int DIM, int N>
 int run_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int clip, cudaStream_t s)
@@ -202,7 +286,28 @@ int run_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int cl
     return n + 1;
 }
 
+template <int DIM, int N>
+int run_traces_dt(const kbl_ctx* c, const double* w, double* wf, double cfl, cudaStream_t s)
+{
+    constexpr int NK = kbl_ns<DIM>(N) > kbl_nfp<DIM>(N) ? kbl_ns<DIM>(N) : kbl_nfp<DIM>(N);
+    const size_t total = (size_t)c->E * NK;
+    if (total == 0) return 0;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    if (c->cfg.precision == KBL_FP32_MIXED)
+        k_traces_dt<DIM, N, float><<<grid, 256, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, cfl, c->d_dtbits,
+                                                        c->d_blocks_done, c->d_scal);
+    else
+        k_traces_dt<DIM, N, double><<<grid, 256, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, cfl, c->d_dtbits,
+                                                         c->d_blocks_done, c->d_scal);
+    return 1;
+}
+
 }  // namespace
+
+int launch_traces_dt(const kbl_ctx* c, const double* w, double* wf, double cfl, cudaStream_t s)
+{
+    KBL_DISPATCH(c->cfg.dim, c->cfg.p + 1, run_traces_dt, c, w, wf, cfl, s);
+}
 
 MeshDev mesh_of(const kbl_ctx* c)
 {

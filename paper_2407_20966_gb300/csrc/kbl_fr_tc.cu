@@ -21,13 +21,15 @@
 // kind::tf32 per k-step accumulating in FP32 in tensor memory: the dropped lo*lo term and the
 // TF32 rounding of lo are 2^-22 of each product, the FP32 level.
 //
-// Per tile: thread 0 arms an mbarrier and issues TMA loads of the state and trace tiles (2D maps
-// [component][element * points], boxes of 16 elements; elements past the mesh read as zeros);
-// the threads load the exterior face values (neighbour traces, scattered) and the widths, then
-// form X in shared memory in the K-major no-swizzle layout (8-row x 16-byte core matrices);
-// thread 0 issues the MMAs and a tcgen05.commit to a second mbarrier; each warp reads its 32
-// rows of the accumulator with tcgen05.ld and writes R (FP64, exact widening).  The next tile's
-// TMA is issued as soon as the current one's shared tiles are consumed.  Every wait on an
+// Per tile (persistent blocks of 8 warps, 3 per SM): thread 0 arms an mbarrier and issues the TMA
+// loads of the state tile (2D map [component][element * points], boxes of 16 elements; elements
+// past the mesh read as zeros); meanwhile the threads form the face-point columns of X from the
+// traces (own and exterior, read from global memory), then, once the tile has landed, the
+// solution-point columns, in shared memory in the K-major no-swizzle layout (8-row x 16-byte core
+// matrices; each warp writes whole core matrices, 32 banks); thread 0 issues the MMAs and a
+// tcgen05.commit to a second mbarrier; warps w and w + 4 read rows 32 (w % 4) .. of the
+// accumulator (columns 0-7 and 8-15) with tcgen05.ld and write R (FP64, exact widening).  The
+// next tile's TMA is issued as soon as the current state tile is consumed.  Every wait on an
 // mbarrier is bounded: on expiry the block raises the timeout flag, stops taking tiles, waits
 // (bounded) for its MMA in flight, frees its tensor memory and returns.
 #include <cuda.h>
@@ -43,9 +45,10 @@ namespace {
 using namespace kbl_dev;
 
 constexpr int TC_EL = 32;         // elements per tile (x 4 components = 128 rows)
-constexpr int TC_NT = 128;        // threads per block (4 warps: one per component of the tile)
+constexpr int TC_NT = 256;        // threads per block (8 warps)
 constexpr int TC_HALF = 16;       // elements per TMA box
 constexpr int TC_TMEM_COLS = 32;  // tensor-memory columns per block (accumulator needs 16)
+constexpr int TC_MINB = 3;        // resident blocks per SM (shared memory ~71 KB each)
 
 template <int N>
 struct TcShape {
@@ -57,20 +60,20 @@ struct TcShape {
     static constexpr int SBO = KC * 128;              // bytes between 8-row groups
     static constexpr int A_BYTES = (128 / 8) * SBO;
     static constexpr int B_BYTES = (NG / 8) * SBO;
-    static constexpr int W_BYTES = 4 * TC_EL * NS * 8;     // state tile, FP64
-    static constexpr int WF_BYTES = 4 * TC_EL * NFP * 8;   // trace tile, FP64
+    static constexpr int W_BYTES = 4 * TC_EL * NS * 8;     // state tile, FP64 (TMA)
     // dynamic shared memory layout (offsets from a 1024-byte aligned base)
     static constexpr int OFF_W = 0;
-    static constexpr int OFF_WF = OFF_W + W_BYTES;
-    static constexpr int OFF_AH = (OFF_WF + WF_BYTES + 1023) / 1024 * 1024;
+    static constexpr int OFF_AH = (OFF_W + W_BYTES + 1023) / 1024 * 1024;
     static constexpr int OFF_AL = OFF_AH + A_BYTES;
     static constexpr int OFF_BH = OFF_AL + A_BYTES;
     static constexpr int OFF_BL = OFF_BH + B_BYTES;
-    static constexpr int OFF_EXT = OFF_BL + B_BYTES;                     // float [32][NFP][4]
-    static constexpr int OFF_H = OFF_EXT + TC_EL * NFP * 4 * 4;          // float2 [32]
+    static constexpr int OFF_H = OFF_BL + B_BYTES;                       // float2 [32]
     static constexpr int OFF_BAR = OFF_H + TC_EL * 8;                    // 2 mbarriers
     static constexpr int OFF_MISC = OFF_BAR + 16;                        // tmem address, status
     static constexpr int BYTES = OFF_MISC + 16 + 1024;                   // + alignment slack
+    // work decomposition: a warp covers 8 elements x 4 points (one 8 x 4 core-matrix block of X
+    // per component, so its shared-memory writes hit 32 different banks)
+    static constexpr int NODE_GROUPS = (NS + 3) / 4, FACE_GROUPS = (NFP + 3) / 4;
 };
 
 // Byte offset of element (row, k) of a TF32 operand in the K-major no-swizzle canonical layout:
@@ -156,17 +159,15 @@ __device__ __forceinline__ void tc_commit(unsigned bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16])
+__device__ __forceinline__ void tc_ld8(unsigned taddr, float (&v)[8])
 {
-    unsigned r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 // TF32 split of an FP32 value: hi = x rounded to TF32, lo = (x - hi) rounded to TF32.
 __device__ __forceinline__ void tf32_split(float x, unsigned& hi, unsigned& lo)
@@ -187,25 +188,24 @@ struct TcArgs {
 };
 
 template <int N>
-__global__ void __launch_bounds__(TC_NT, 1)
-k_rhs_tc(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUtensorMap map_wf, TcArgs a)
+__global__ void __launch_bounds__(TC_NT, TC_MINB)
+k_rhs_tc(const __grid_constant__ CUtensorMap map_w, TcArgs a)
 {
     using SH = TcShape<N>;
     constexpr int NS = SH::NS, NFP = SH::NFP, KP = SH::KP, KC = SH::KC, NG = SH::NG;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* sm = (unsigned char*)(((size_t)smraw + 1023) & ~(size_t)1023);
     const double* sW = (const double*)(sm + SH::OFF_W);
-    const double* sWF = (const double*)(sm + SH::OFF_WF);
     unsigned* sAh = (unsigned*)(sm + SH::OFF_AH);
     unsigned* sAl = (unsigned*)(sm + SH::OFF_AL);
-    float* sExt = (float*)(sm + SH::OFF_EXT);
     float2* sH = (float2*)(sm + SH::OFF_H);
     const unsigned bar_tma = smem_u32(sm + SH::OFF_BAR), bar_mma = bar_tma + 8;
     unsigned* s_misc = (unsigned*)(sm + SH::OFF_MISC);   // [0] tmem address, [1] status
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int E = a.m.E;
     const int ntiles = (E + TC_EL - 1) / TC_EL;
-    constexpr unsigned TX_BYTES = (unsigned)(SH::W_BYTES + SH::WF_BYTES);
+    constexpr unsigned TX_BYTES = (unsigned)SH::W_BYTES;
+    constexpr int NW = TC_NT / 32;
 
     // set-up: operator B into shared memory, barriers, tensor memory
     {
@@ -235,11 +235,8 @@ k_rhs_tc(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUte
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles) {
         mbar_expect_tx(bar_tma, TX_BYTES);
-        for (int hf = 0; hf < 2; hf++) {
-            const int e0 = tile * TC_EL + hf * TC_HALF;
-            tma_load_2d(smem_u32(sW) + hf * (SH::W_BYTES / 2), &map_w, e0 * NS, 0, bar_tma);
-            tma_load_2d(smem_u32(sWF) + hf * (SH::WF_BYTES / 2), &map_wf, e0 * NFP, 0, bar_tma);
-        }
+        for (int hf = 0; hf < 2; hf++)
+            tma_load_2d(smem_u32(sW) + hf * (SH::W_BYTES / 2), &map_w, (tile * TC_EL + hf * TC_HALF) * NS, 0, bar_tma);
     }
     // what a failed wait may leave in flight: the MMA of tile `it` (parity it & 1), the TMA of
     // the following tile (parity (it + 1) & 1)
@@ -248,20 +245,7 @@ k_rhs_tc(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUte
     for (; tile < ntiles; it++, tile += gridDim.x) {
         const int e0 = tile * TC_EL;
         const int nel = min(TC_EL, E - e0);
-        // exterior values (scattered neighbour traces or boundary states) and the 2/h factors
-        for (int idx = tid; idx < TC_EL * NFP; idx += TC_NT) {
-            const int el = idx / NFP, fp = idx % NFP;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (el < nel) {
-                const int e = e0 + el;
-                q.x = from_f64<float>(kbl_exterior<2, N>(a.wf, a.m, e, fp, 0));
-                q.y = from_f64<float>(kbl_exterior<2, N>(a.wf, a.m, e, fp, 1));
-                q.z = from_f64<float>(kbl_exterior<2, N>(a.wf, a.m, e, fp, 2));
-                q.w = from_f64<float>(kbl_exterior<2, N>(a.wf, a.m, e, fp, 3));
-            }
-            reinterpret_cast<float4*>(sExt)[idx] = q;
-        }
-        if (tid < TC_EL) {
+        if (tid < TC_EL) {   // the 2/h factors
             float2 s = make_float2(0.f, 0.f);
             if (tid < nel) {
                 s.x = 2.0f / from_f64<float>(a.m.h[(size_t)(e0 + tid) * 2 + 0]);
@@ -269,13 +253,55 @@ k_rhs_tc(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUte
             }
             sH[tid] = s;
         }
-        // the tile's state and traces
+        // X, face points first (their traces come from global memory, as the state tile lands):
+        // common fluxes scaled by 2/h of their axis
+        for (int wq = warp; wq < 4 * SH::FACE_GROUPS; wq += NW) {
+            const int el = ((wq & 3) << 3) | (lane >> 2), fp = ((wq >> 2) << 2) | (lane & 3);
+            if (fp >= NFP) continue;
+            float Fc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (el < nel) {
+                const int e = e0 + el;
+                const int f = fp / N, dir = f >> 1, side = f & 1;
+                float qi[4], qe[4];
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    qi[v] = from_f64<float>(a.wf[((size_t)v * E + e) * NFP + fp]);
+                    qe[v] = from_f64<float>(kbl_exterior<2, N>(a.wf, a.m, e, fp, v));
+                }
+                const float* ql = side ? qi : qe;
+                const float* qr = side ? qe : qi;
+                if (a.flux == 1) kbl_hllc<2, float>(ql, qr, dir, gamma, Fc);
+                else if (a.flux == 2) kbl_hll<2, float>(ql, qr, dir, gamma, Fc);
+                else kbl_rusanov<2, float>(ql, qr, dir, gamma, Fc);
+                const float s = dir ? 2.0f / from_f64<float>(a.m.h[(size_t)e * 2 + 1])
+                                    : 2.0f / from_f64<float>(a.m.h[(size_t)e * 2 + 0]);
+#pragma unroll
+                for (int v = 0; v < 4; v++) Fc[v] *= s;
+            }
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const int row = v * TC_EL + el;
+                unsigned hi, lo;
+                tf32_split(Fc[v], hi, lo);
+                sAh[tc_off(row, 2 * NS + fp, KC) / 4] = hi;
+                sAl[tc_off(row, 2 * NS + fp, KC) / 4] = lo;
+            }
+        }
+        if (SH::K < KP) {   // zero padding columns of K
+            for (int idx = tid; idx < 128 * (KP - SH::K); idx += TC_NT) {
+                const int row = idx / (KP - SH::K), k = SH::K + idx % (KP - SH::K);
+                sAh[tc_off(row, k, KC) / 4] = 0u;
+                sAl[tc_off(row, k, KC) / 4] = 0u;
+            }
+        }
+        // the tile's state
         if (tid == 0 && !mbar_wait_bounded(bar_tma, it & 1)) s_misc[1] = 1;
         __syncthreads();
         if (s_misc[1]) break;
         // X: fluxes at the solution points, scaled by 2/h
-        for (int idx = tid; idx < TC_EL * NS; idx += TC_NT) {
-            const int el = idx / NS, nd = idx % NS;
+        for (int wq = warp; wq < 4 * SH::NODE_GROUPS; wq += NW) {
+            const int el = ((wq & 3) << 3) | (lane >> 2), nd = ((wq >> 2) << 2) | (lane & 3);
+            if (nd >= NS) continue;
             float Fx[4] = {0.f, 0.f, 0.f, 0.f}, Fy[4] = {0.f, 0.f, 0.f, 0.f};
             if (el < nel) {
                 const double* src = sW + (el / TC_HALF) * (4 * TC_HALF * NS) + (el % TC_HALF) * NS + nd;
@@ -303,61 +329,19 @@ k_rhs_tc(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUte
                 sAl[tc_off(row, NS + nd, KC) / 4] = lo;
             }
         }
-        // X: common fluxes at the face points, scaled by 2/h of their axis
-        for (int idx = tid; idx < TC_EL * NFP; idx += TC_NT) {
-            const int el = idx / NFP, fp = idx % NFP;
-            float Fc[4] = {0.f, 0.f, 0.f, 0.f};
-            if (el < nel) {
-                const int f = fp / N, dir = f >> 1, side = f & 1;
-                const double* src = sWF + (el / TC_HALF) * (4 * TC_HALF * NFP) + (el % TC_HALF) * NFP + fp;
-                float qi[4], qe[4];
-#pragma unroll
-                for (int v = 0; v < 4; v++) qi[v] = from_f64<float>(src[v * TC_HALF * NFP]);
-                const float4 x = reinterpret_cast<const float4*>(sExt)[idx];
-                qe[0] = x.x;
-                qe[1] = x.y;
-                qe[2] = x.z;
-                qe[3] = x.w;
-                const float* ql = side ? qi : qe;
-                const float* qr = side ? qe : qi;
-                if (a.flux == 1) kbl_hllc<2, float>(ql, qr, dir, gamma, Fc);
-                else if (a.flux == 2) kbl_hll<2, float>(ql, qr, dir, gamma, Fc);
-                else kbl_rusanov<2, float>(ql, qr, dir, gamma, Fc);
-                const float s = dir ? sH[el].y : sH[el].x;
-#pragma unroll
-                for (int v = 0; v < 4; v++) Fc[v] *= s;
-            }
-#pragma unroll
-            for (int v = 0; v < 4; v++) {
-                const int row = v * TC_EL + el;
-                unsigned hi, lo;
-                tf32_split(Fc[v], hi, lo);
-                sAh[tc_off(row, 2 * NS + fp, KC) / 4] = hi;
-                sAl[tc_off(row, 2 * NS + fp, KC) / 4] = lo;
-            }
-        }
-        if (SH::K < KP) {   // zero padding columns of K
-            for (int idx = tid; idx < 128 * (KP - SH::K); idx += TC_NT) {
-                const int row = idx / (KP - SH::K), k = SH::K + idx % (KP - SH::K);
-                sAh[tc_off(row, k, KC) / 4] = 0u;
-                sAl[tc_off(row, k, KC) / 4] = 0u;
-            }
-        }
         fence_proxy_async();   // X (generic writes) visible to the tensor core (async proxy)
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (tid == 0) {
-            // the next tile's TMA may overwrite the state and trace tiles now
+            // the next tile's TMA may overwrite the state tile now
             const int nt = tile + gridDim.x;
             tma_next = nt < ntiles;
             if (nt < ntiles) {
                 mbar_expect_tx(bar_tma, TX_BYTES);
-                for (int hf = 0; hf < 2; hf++) {
-                    const int n0 = nt * TC_EL + hf * TC_HALF;
-                    tma_load_2d(smem_u32(sW) + hf * (SH::W_BYTES / 2), &map_w, n0 * NS, 0, bar_tma);
-                    tma_load_2d(smem_u32(sWF) + hf * (SH::WF_BYTES / 2), &map_wf, n0 * NFP, 0, bar_tma);
-                }
+                for (int hf = 0; hf < 2; hf++)
+                    tma_load_2d(smem_u32(sW) + hf * (SH::W_BYTES / 2), &map_w, (nt * TC_EL + hf * TC_HALF) * NS, 0,
+                                bar_tma);
             }
             const unsigned idesc = tc_idesc(128, NG);
             const unsigned ah = smem_u32(sAh), al = smem_u32(sAl);
@@ -377,13 +361,16 @@ k_rhs_tc(const __grid_constant__ CUtensorMap map_w, const __grid_constant__ CUte
         if (s_misc[1]) break;
         mma_in_flight = false;
         tc_fence_after();
-        // epilogue: warp w holds rows 32w .. 32w+31 = component w of the tile's 32 elements
-        float acc[16];
-        tc_ld16(tmem + ((unsigned)(warp * 32) << 16), acc);
+        // epilogue: warp w holds rows 32 (w % 4) .. + 31 = component w % 4 of the tile's 32
+        // elements, columns 8 (w / 4) .. + 7
+        float acc[8];
+        const int cq = warp >> 2;
+        tc_ld8(tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(cq * 8), acc);
         if (lane < nel) {
-            double* dst = a.R + ((size_t)warp * E + e0 + lane) * NS;
+            double* dst = a.R + ((size_t)(warp & 3) * E + e0 + lane) * NS;
 #pragma unroll
-            for (int n = 0; n < NS && n < 16; n++) dst[n] = to_f64<float>(acc[n]);
+            for (int n = 0; n < 8; n++)
+                if (cq * 8 + n < NS) dst[cq * 8 + n] = to_f64<float>(acc[n]);
         }
         tc_fence_before();
         __syncthreads();   // accumulator and X free for the next tile
@@ -457,12 +444,13 @@ int run_rhs_tc(const kbl_ctx* c, const double* w, const double* wf, double* R, c
 {
     using SH = TcShape<N>;
     if (c->E == 0) return 0;
-    // TMA: 16-byte aligned bases and strides (E * pts * 8 a multiple of 16)
-    if (((size_t)w & 15) || ((size_t)wf & 15) || ((size_t)c->E * SH::NS * 8) % 16 || ((size_t)c->E * SH::NFP * 8) % 16)
-        return -2;
-    CUtensorMap mw, mwf;
-    if (!make_map(&mw, w, c->E, SH::NS) || !make_map(&mwf, wf, c->E, SH::NFP)) return -2;
-    if (cudaFuncSetAttribute(k_rhs_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::BYTES) != cudaSuccess)
+    // TMA of the state: 16-byte aligned base and row stride (E * Ns * 8 a multiple of 16)
+    if (((size_t)w & 15) || ((size_t)c->E * SH::NS * 8) % 16) return -2;
+    CUtensorMap mw;
+    if (!make_map(&mw, w, c->E, SH::NS)) return -2;
+    if (cudaFuncSetAttribute(k_rhs_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rhs_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess)
         return -2;
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
@@ -479,7 +467,7 @@ int run_rhs_tc(const kbl_ctx* c, const double* w, const double* wf, double* R, c
     a.flux = c->phys.flux;
     a.R = R;
     a.flags = c->d_flags;
-    k_rhs_tc<N><<<grid, TC_NT, SH::BYTES, s>>>(mw, mwf, a);
+    k_rhs_tc<N><<<grid, TC_NT, SH::BYTES, s>>>(mw, a);
     return 1;
 }
 

@@ -232,10 +232,11 @@ struct kbl_ctx {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;   // copy streams of kbl_run_host_ensemble
     cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_step[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
     unsigned long long* d_dtbits = nullptr;
+    unsigned* d_blocks_done = nullptr;   // finished-block counter of the fused traces + time step
     DevFlags* d_flags = nullptr;
     double* d_qw = nullptr;     // velocity quadrature weights (Romberg), or nullptr
     float* d_tcop = nullptr;    // split residual operator of the tensor-core residual, or nullptr
-    int rhs_tc = 1;             // knob: 1 residual products on the tensor cores where covered, 0 CUDA cores
+    int rhs_tc = 0;             // knob: 1 residual products on the tensor cores where covered, 0 CUDA cores
     std::string err;
     int64_t launches = 0;
     int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes
@@ -282,6 +283,12 @@ float* kbl_rhs_tc_upload(const FrOps& o, int p);
 // dt_out <- cfl * min(h / (|U| + c)); with clip, also <= t_end - t of the context
 int launch_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int clip, cudaStream_t s);
 int launch_time_advance(const kbl_ctx* c, cudaStream_t s);
+// the first kernel of kbl_step: face traces of w and the clipped time step into scal[0] in one pass
+int launch_traces_dt(const kbl_ctx* c, const double* w, double* wf, double cfl, cudaStream_t s);
+// the stage kernel of kbl_step (dt from scal[0]): stage + limiter, then the next stage's traces
+// (wf_next, may be nullptr) or the clock update (advance)
+int launch_stage_step(const kbl_ctx* c, int stage, const double* wn, const double* ws, const double* R,
+                      const double* bnd, double* wout, double* wf_next, int advance, cudaStream_t s);
 int launch_bounds(const kbl_ctx* c, const double* w, const double* wf, double* bnd,
                   cudaStream_t s);
 // limiting of explicit node sets U[E][ns][nv] (in place) with faces F[E][nf][nv], W[ns] host

@@ -40,6 +40,37 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
                                                 ops, ph, flags, blockIdx.x * SH::EPB, SH::EPB);
 }
 
+// The stage kernel of kbl_step: the stage and limiter, then (wf_next) the next stage's face traces
+// from the limited state still in shared memory, or (advance) the clock of the step.
+template <int DIM, int N>
+__global__ void __launch_bounds__(LimShape<DIM, N>::NT)
+k_stage_limit_step(int stage, const double* wn, const double* ws, const double* __restrict__ R,
+                   const double* __restrict__ bnd, double* scal, double* wout, double* __restrict__ wf_next,
+                   int advance, int E, FrOps ops, Phys ph, DevFlags* flags)
+{
+    using SH = LimShape<DIM, N>;
+    __shared__ kbl_dev::LimSmem<DIM, N, SH::EPB> sm;
+    const double dt = scal[0];
+    const int e0 = blockIdx.x * SH::EPB;
+    kbl_dev::stage_limit_block<DIM, N, SH::EPB, true>(sm, SH::NT, 0, stage, wn, ws, R, bnd, dt, wout, nullptr, E,
+                                                      ops, ph, flags, e0, SH::EPB);
+    if (wf_next) kbl_dev::traces_of_block<DIM, N, SH::EPB>(sm, SH::NT, E, e0, SH::EPB, wf_next);
+    // the clock: t += dt, once (no block of this launch reads t)
+    if (advance && blockIdx.x == 0 && threadIdx.x == 0) scal[1] += dt;
+}
+
+template <int DIM, int N>
+int run_stage_step(const kbl_ctx* c, int stage, const double* wn, const double* ws, const double* R, const double* bnd,
+                   double* wout, double* wf_next, int advance, cudaStream_t s)
+{
+    using SH = LimShape<DIM, N>;
+    if (c->E == 0) return 0;
+    const unsigned grid = (unsigned)((c->E + SH::EPB - 1) / SH::EPB);
+    k_stage_limit_step<DIM, N><<<grid, SH::NT, 0, s>>>(stage, wn, ws, R, bnd, c->d_scal, wout, wf_next, advance, c->E,
+                                                     c->ops, c->phys, c->d_flags);
+    return 1;
+}
+
 template <int DIM, int N>
 int run_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const double* ws,
               const double* R, const double* bnd, const double* dt, double* wout, double* alpha,
@@ -165,4 +196,10 @@ int launch_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const 
                  cudaStream_t s)
 {
     KBL_DISPATCH(c->cfg.dim, c->cfg.p + 1, run_stage, c, mode, stage, wn, ws, R, bnd, dt, wout, alpha, s);
+}
+
+int launch_stage_step(const kbl_ctx* c, int stage, const double* wn, const double* ws, const double* R,
+                      const double* bnd, double* wout, double* wf_next, int advance, cudaStream_t s)
+{
+    KBL_DISPATCH(c->cfg.dim, c->cfg.p + 1, run_stage_step, c, stage, wn, ws, R, bnd, wout, wf_next, advance, s);
 }

@@ -48,7 +48,7 @@ struct LimSmem {
 // SSP-RK3 stage (mode 0) or limiter only (mode 1, ws = w in place) for elements
 // e0 .. e0+min(EPB, nmax)-1 of one mesh, by a block of NT >= EPB*Ns threads.  Starts with a
 // barrier so that a block can call it repeatedly.
-template <int DIM, int N, int EPB>
+template <int DIM, int N, int EPB, bool KEEP = false>
 __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int NT, int mode, int stage,
                                                   const double* wn, const double* ws,
                                                   const double* __restrict__ R,
@@ -410,7 +410,7 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         }
     }
     __syncthreads();
-    // 5. write
+    // 5. write (with KEEP the written state also stays in sw, for a caller that continues with it)
     if (live) {
         const double aP = saP[el];
 #pragma unroll
@@ -421,6 +421,37 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
                 val = m + aP * (val - m);
             }
             wout[((size_t)v * E + e) * NS + nd] = val;
+            if (KEEP) sw[el][v][nd] = val;
+        }
+    }
+}
+
+// Face traces of the state stage_limit_block<..., KEEP = true> just wrote (it is in sw): the
+// operations and order of k_traces, so the values equal kbl_traces of that state bit for bit.
+template <int DIM, int N, int EPB>
+__device__ __forceinline__ void traces_of_block(LimSmem<DIM, N, EPB>& sm, int NT, int E, int e0, int nmax,
+                                                double* __restrict__ wf)
+{
+    constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
+    constexpr int NFPF = (DIM == 1) ? 1 : N;
+    __syncthreads();
+    for (int t = threadIdx.x; t < EPB * NFP; t += NT) {
+        const int ell = t / NFP, fp = t % NFP;
+        const int e = e0 + ell;
+        if (e >= E || ell >= nmax) continue;
+        const int f = fp / NFPF, k = fp % NFPF;
+        const bool plus = f & 1;
+        const bool along_x = (DIM == 1) || f < 2;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                const double l = plus ? sm.slp[i] : sm.slm[i];
+                const int nd = along_x ? k * N + i : i * N + k;
+                s += l * sm.sw[ell][v][(DIM == 1) ? i : nd];
+            }
+            wf[((size_t)v * E + e) * NFP + fp] = s;
         }
     }
 }

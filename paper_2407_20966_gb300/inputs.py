@@ -338,3 +338,84 @@ def batch_state(problems, nodes_of_p, state_offsets):
         a, b = int(state_offsets[i]), int(state_offsets[i + 1])
         w[a:b] = nodal_field(mesh, nodes_of_p(p), ic).ravel()
     return w
+
+
+class TriMeshData:
+    """An affine triangle mesh: xy[E][3][2] vertices (counterclockwise), nbr[E][3] (element across
+    edge f, from vertex f to vertex f+1; negative = boundary id -(nbr+1)), nbr_edge[E][3] (the
+    neighbour's matched edge), bc[n_bc][4]."""
+
+    def __init__(self, xy, nbr, nbr_edge, bc):
+        self.xy, self.nbr, self.nbr_edge, self.bc = xy, nbr, nbr_edge, bc
+        self.n_elem = nbr.shape[0]
+
+
+def tri_mesh_2d(nx, ny, x0, x1, y0, y1, jitter=0.0, seed=0, periodic=(True, True)):
+    """Unstructured-looking triangles on [x0,x1] x [y0,y1]: an nx x ny grid whose vertices are moved
+    by up to jitter cell widths (seeded; the same move for periodic images), each cell cut into a
+    lower-left (v00, v10, v01) and an upper-right (v10, v11, v01) triangle.  Element coordinates
+    are unwrapped across periodic boundaries.  Non-periodic sides get boundary ids 0 (x) and 1 (y)."""
+    rng = np.random.default_rng(seed)
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    mx, my = nx + 1, ny + 1
+    jit = rng.uniform(-jitter, jitter, (mx, my, 2))
+    if periodic[0]:
+        jit[nx, :, :] = jit[0, :, :]
+    else:
+        jit[0, :, 0] = 0.0
+        jit[nx, :, 0] = 0.0
+    if periodic[1]:
+        jit[:, ny, :] = jit[:, 0, :]
+    else:
+        jit[:, 0, 1] = 0.0
+        jit[:, ny, 1] = 0.0
+
+    def vert(i, j):
+        return np.array([x0 + (i + jit[i, j, 0]) * hx, y0 + (j + jit[i, j, 1]) * hy])
+
+    E = 2 * nx * ny
+    xy = np.zeros((E, 3, 2))
+    nbr = np.zeros((E, 3), np.int32)
+    nbr_edge = np.zeros((E, 3), np.int32)
+
+    def tid(i, j, t):
+        return 2 * (j * nx + i) + t
+
+    for j in range(ny):
+        for i in range(nx):
+            a, b = tid(i, j, 0), tid(i, j, 1)
+            xy[a] = [vert(i, j), vert(i + 1, j), vert(i, j + 1)]
+            xy[b] = [vert(i + 1, j), vert(i + 1, j + 1), vert(i, j + 1)]
+            # lower-left: edge 0 bottom, 1 diagonal, 2 left; upper-right: 0 right, 1 top, 2 diagonal
+            nbr[a, 1], nbr_edge[a, 1] = b, 2
+            nbr[b, 2], nbr_edge[b, 2] = a, 1
+            if j > 0 or periodic[1]:
+                nbr[a, 0], nbr_edge[a, 0] = tid(i, (j - 1) % ny, 1), 1
+            else:
+                nbr[a, 0], nbr_edge[a, 0] = -2, 0
+            if i > 0 or periodic[0]:
+                nbr[a, 2], nbr_edge[a, 2] = tid((i - 1) % nx, j, 1), 0
+            else:
+                nbr[a, 2], nbr_edge[a, 2] = -1, 0
+            if i < nx - 1 or periodic[0]:
+                nbr[b, 0], nbr_edge[b, 0] = tid((i + 1) % nx, j, 0), 2
+            else:
+                nbr[b, 0], nbr_edge[b, 0] = -1, 0
+            if j < ny - 1 or periodic[1]:
+                nbr[b, 1], nbr_edge[b, 1] = tid(i, (j + 1) % ny, 0), 0
+            else:
+                nbr[b, 1], nbr_edge[b, 1] = -2, 0
+    bc = np.array([[1.0, 0.0, 0.0, 2.5], [1.0, 0.0, 0.0, 2.5]])
+    return TriMeshData(xy, nbr, nbr_edge, bc)
+
+
+def tri_nodal_field(mesh, rs, ic):
+    """Initial state at the solution points of every triangle, w[E][ns][4]; rs[ns][2] reference
+    points on (0,0), (1,0), (0,1), ic(x, y) -> (4, ...) conservative state."""
+    X0 = mesh.xy[:, 0, :]
+    J1 = mesh.xy[:, 1, :] - X0
+    J2 = mesh.xy[:, 2, :] - X0
+    x = X0[:, None, 0] + rs[None, :, 0] * J1[:, None, 0] + rs[None, :, 1] * J2[:, None, 0]
+    y = X0[:, None, 1] + rs[None, :, 0] * J1[:, None, 1] + rs[None, :, 1] * J2[:, None, 1]
+    q = np.asarray(ic(x, y), dtype=np.float64)          # [4][E][ns]
+    return np.ascontiguousarray(np.moveaxis(q, 0, -1))  # [E][ns][4]

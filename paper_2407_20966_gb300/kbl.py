@@ -90,6 +90,8 @@ _SIGS = {
     "kbl_batch_step": (C.c_int, [_P, _P, C.c_double]),
     "kbl_batch_dt": (C.c_int, [_P, _P]),
     "kbl_batch_bounds": (C.c_int, [_P, _P, _P]),
+    "kbl_batch_set_form": (C.c_int, [_P, C.c_int]),
+    "kbl_batch_stall_test": (C.c_int, [_P, C.c_int, C.c_int]),
     "kbl_batch_bounds_ms": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "kbl_batch_run_host": (C.c_int, [_P, _P, _P, C.c_int, C.c_double]),
     "kbl_batch_rhs": (C.c_int, [_P, _P, _P]),
@@ -476,6 +478,13 @@ class Batch:
         self._check(self._lib.kbl_batch_dt(self._h, out.ctypes.data_as(C.c_void_p)), "batch_dt")
         return out
 
+    def set_form(self, fused):
+        """1: one persistent launch per step (default); 0: one launch per phase."""
+        self._check(self._lib.kbl_batch_set_form(self._h, int(fused)), "batch_set_form")
+
+    def stall_test(self, on, wait_polls=1 << 20):
+        self._check(self._lib.kbl_batch_stall_test(self._h, int(on), int(wait_polls)), "batch_stall_test")
+
     def bounds_view(self, bnd, i):
         """Problem i's bounds [2][4][E_i] in a concatenated bounds array (a view)."""
         a, n = 8 * int(self.elem_offsets[i]), int(self.n_elem[i])
@@ -517,7 +526,7 @@ class Batch:
         out = np.zeros(4, np.int32)
         self._check(self._lib.kbl_batch_tuning(self._h, out.ctypes.data_as(C.c_void_p)), "batch_tuning")
         return {"tile": int(out[0]), "elements_per_item": int(out[1]), "blocks_per_sm": int(out[2]),
-                "items": int(out[3])}
+                "items": int(out[3])}   # tile: 0 = 4x4, 1 = 4x2, 2 = 2x4 velocity nodes per thread
 
     def check(self):
         self._check(self._lib.kbl_batch_check(self._h), "batch_check")

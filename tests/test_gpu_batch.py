@@ -47,6 +47,8 @@ def test_batch_step_equals_single_mesh_path(orc):
     dts = b.dt()
     for i, (p, m, ic) in enumerate(probs):
         ctx = kbl.Context(dim=2, p=p, nu=(32, 32), precision=kbl.FP32_MIXED)
+        ctx.set_tuning(kbl.TUNE_RHS_TC, 0)   # the batch runs the CUDA-core residual
+        ctx.set_tuning(kbl.TUNE_BOUNDS_TILE, b.tuning()["tile"])   # and its bounds thread tile
         ctx.mesh_upload(m.nbr, m.h, m.bc)
         wi = torch.from_numpy(np.ascontiguousarray(b.state_view(w0, i))).cuda()
         ctx.set_time(0.0)
@@ -214,6 +216,8 @@ def test_batch_hllc_equals_single_mesh_path(flux):
     got = wd.cpu().numpy()
     for i, (p, m, ic) in enumerate(probs):
         ctx = kbl.Context(dim=2, p=p, nu=(32, 32), precision=kbl.FP32_MIXED, flux=flux)
+        ctx.set_tuning(kbl.TUNE_RHS_TC, 0)   # the batch runs the CUDA-core residual
+        ctx.set_tuning(kbl.TUNE_BOUNDS_TILE, b.tuning()["tile"])   # and its bounds thread tile
         ctx.mesh_upload(m.nbr, m.h, m.bc)
         wi = torch.from_numpy(np.ascontiguousarray(b.state_view(w0, i))).cuda()
         ctx.set_time(0.0)
@@ -240,3 +244,54 @@ def test_batch_run_host_matches_device_steps():
     w_inout = w0.copy()   # the output may alias the input
     b.run_host(w_inout, w_inout, 2, 0.1)
     np.testing.assert_array_equal(w_inout, ref)
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+def test_batch_one_launch_equals_per_phase_launches(flux):
+    """The fused form (the whole step as one persistent launch, per-problem dataflow between the
+    13 phases) gives bit for bit the state and time steps of one persistent launch per phase:
+    every element runs the same device code whichever block takes its work item."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    probs = inputs.four_quadrant_batch(31 + flux, 23, n_range=(2, 14))
+    b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs], flux=flux)
+    w0 = inputs.batch_state(probs, b.nodes, b.state_offsets)
+    out = []
+    for form in (1, 0):
+        b.set_form(form)
+        wd = torch.from_numpy(w0).cuda()
+        for _ in range(2):
+            b.step(wd, 0.1)
+        b.check()
+        out.append((wd.cpu().numpy(), b.dt()))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert b.launch_count() > 0
+
+
+def test_batch_one_launch_wait_timeout_is_reported():
+    """Failure detection without a fault: a wait of the fused step is made to run out (it waits
+    for a completion count no item reaches); the step ends with KBL_ETIMEOUT instead of hanging,
+    and the batch then steps correctly again."""
+    import time
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    probs = inputs.four_quadrant_batch(41, 9, n_range=(2, 8))
+    b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs])
+    w0 = inputs.batch_state(probs, b.nodes, b.state_offsets)
+    wref = torch.from_numpy(w0).cuda()
+    b.step(wref, 0.1)
+    b.check()
+    b.stall_test(1, wait_polls=200000)      # about 0.2 s
+    wd = torch.from_numpy(w0).cuda()
+    t0 = time.perf_counter()
+    b.step(wd, 0.1)
+    with pytest.raises(kbl.KblError) as ei:
+        b.check()
+    assert ei.value.status == kbl.ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    b.stall_test(0)
+    wd = torch.from_numpy(w0).cuda()
+    b.step(wd, 0.1)
+    b.check()
+    np.testing.assert_array_equal(wd.cpu().numpy(), wref.cpu().numpy())

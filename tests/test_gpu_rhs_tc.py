@@ -28,6 +28,7 @@ def _cuda():
 def test_rhs_tensor_cores_match_checker(orc, p, n, flux, kind):
     from paper_2407_20966_gb300 import kbl
     ctx, ocfg = both(orc, 2, p, (16, 16), precision=1, flux=flux)
+    ctx.set_tuning(kbl.TUNE_RHS_TC, 1)
     assert ctx.get_tuning(kbl.TUNE_RHS_TC) == 1
     for seed in range(500, 540):   # a field whose face traces are physical (HLLC, HLL need it)
         mesh, w = mesh_and_field(orc, 2, p, n, seed=seed, kind=kind)
@@ -58,7 +59,9 @@ def test_rhs_tensor_cores_match_checker(orc, p, n, flux, kind):
 def test_full_step_with_tensor_core_residual(orc, p):
     """A step with the tensor-core residual inside the step graph, against the checker with the
     device's time step (criterion of test_full_step_uncoupled)."""
+    from paper_2407_20966_gb300 import kbl
     ctx, ocfg = both(orc, 2, p, (32, 32), precision=1)
+    ctx.set_tuning(kbl.TUNE_RHS_TC, 1)
     mesh, w = mesh_and_field(orc, 2, p, (11, 9), seed=77 + p, kind="disc")
     om = upload(ctx, orc, mesh)
     wd = to_dev(w)
