@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2070.0
 # The envelope loop of the FP32 bounds kernel needs, per (stencil state, velocity node),
 # 2 products (g = Ex Ey and C g) and 4 comparisons (min and max of both): 6 FP32 lane-ops.
 # Its roofline is the measured rate of exactly that instruction mix in a register-only loop
-# (peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
+# (csrc/peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
 # lane-ops per clock per SM (packed multiplies and three-input min/max issue to two pipes
 # that overlap only in part), times 152 SMs and the 2070 MHz maximum clock.
 OPS_PER_STATE_NODE = 6.0
@@ -476,8 +476,8 @@ def run_batched(args, rank, world, steps=None, warmup=None):
     launches = b.launch_count() - l0
     ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in evs), dev)
     value = job_throughput(E * 3 * K, ms, world)
-    # the same steps as one persistent launch per phase (the other form), for comparison
-    b.set_form(0)
+    # the same steps as ONE persistent launch per step (the other form), for comparison
+    b.set_form(1)
     b.step(wd, cfl)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kp = 2
@@ -487,8 +487,8 @@ def run_batched(args, rank, world, steps=None, warmup=None):
     e1.record(stream)
     torch.cuda.synchronize()
     b.check()
-    per_phase_ms = e0.elapsed_time(e1) / kp
-    b.set_form(1)
+    one_launch_ms = e0.elapsed_time(e1) / kp
+    b.set_form(0)
     # dominant kernel: the bounds phase over the whole batch, tuned shape, timed alone
     bnd = torch.zeros(8 * E, dtype=torch.float64, device=dev)
     b.bounds(wd, bnd)
@@ -522,8 +522,9 @@ def run_batched(args, rank, world, steps=None, warmup=None):
                     "d2h_bytes_per_step": w0.nbytes,
                     "call": "kbl_batch_run_host, 1 step, pinned host buffers, copies overlapped by problem groups"},
             "gpu_launches": launches,
-            "form": {"timed": "one persistent launch per step (per-problem dataflow between phases)",
-                     "per_phase_launches_ms_per_step": per_phase_ms},
+            "form": {"timed": "one persistent launch per phase, 14 per step, in one graph",
+                     "one_launch_ms_per_step": one_launch_ms,
+                     "one_launch": "the whole step as one persistent launch with per-problem dataflow"},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                          "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "kernel": "k_batch_bounds", "bounds_ms_per_launch": round(bounds_ms, 3),
@@ -682,16 +683,16 @@ def run_adjoint(args, rank, world):
 
 
 def run_peaks():
-    """Compile and run the register-only rate probes under peaks/: FP32 multiply and min/max
-    rates, alone and in the envelope pattern (kbl_fp32_peaks.cu), then the integer and FP64
-    operations the other kernels spend (kbl_int_fp64_rates.cu), per SM clock (clock64 inside
-    each block); clocks sampled beside."""
+    """Compile and run the register-only rate probes under paper_2407_20966_gb300/csrc/peaks/:
+    FP32 multiply and min/max rates, alone and in the envelope pattern (kbl_fp32_peaks.cu),
+    then the integer and FP64 operations the other kernels spend (kbl_int_fp64_rates.cu), per
+    SM clock (clock64 inside each block); clocks sampled beside."""
     import subprocess
     here = os.path.dirname(os.path.abspath(__file__))
     out_dir = os.path.join(here, "paper_2407_20966_gb300", "_build")
     os.makedirs(out_dir, exist_ok=True)
     for name in ("kbl_fp32_peaks", "kbl_int_fp64_rates"):
-        src = os.path.join(here, "peaks", name + ".cu")
+        src = os.path.join(here, "paper_2407_20966_gb300", "csrc", "peaks", name + ".cu")
         exe = os.path.join(out_dir, name)
         subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
                        check=True)

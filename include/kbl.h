@@ -278,7 +278,7 @@ int64_t kbl_launch_count(const kbl_ctx* ctx);
  * nodes per thread, 1 = 4 x 2, 2 = 2 x 4.  Setting a knob drops the captured
  * step graph. */
 typedef enum { KBL_TUNE_BOUNDS_TILE = 0, KBL_TUNE_RHS_TC = 1 } kbl_tune_key;
-/* KBL_TUNE_RHS_TC: 1 (default) runs the FP32-mixed 2D residual of orders 2 and 3 with its operator
+/* KBL_TUNE_RHS_TC: 1 runs the FP32-mixed 2D residual of orders 2 and 3 with its operator
  * product (operator 7 of kbl_get_operator) on the tensor cores (tcgen05, TF32 split into
  * hi + lo pairs, FP32 accumulation; element tiles staged by TMA), 0 on the CUDA cores.  Other
  * orders, 1D and FP64 always use the CUDA cores.  Default 0 (CUDA cores: measured faster on the
@@ -288,9 +288,10 @@ kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 
 /* ---- Batched form -----------------------------------------------------------
  * Many independent 2D problems (axis-aligned quad meshes) with uneven element
- * counts and orders p = 1..4, advanced together: a whole step is ONE persistent
- * launch over all problems and phases (blocks pull cost-sorted work items from a
- * device counter; see kbl_batch_set_form), captured once as a CUDA graph.  Each
+ * counts and orders p = 1..4, advanced together: each phase of a step is ONE
+ * persistent launch over all problems (blocks pull cost-sorted work items from a
+ * device counter), or the whole step one launch (kbl_batch_set_form), captured
+ * once as a CUDA graph.  Each
  * problem keeps its own time step.  Precision is KBL_FP32_MIXED.
  * Problem i's data are concatenated in problem order: nbr (E_i x 4, element
  * indices local to the problem, negative = local boundary id), h (E_i x 2),
@@ -345,13 +346,15 @@ kbl_status kbl_batch_run_host(kbl_batch* b, const double* w_host_in, double* w_h
  * stream around that launch alone; synchronous): for measuring the dominant phase in the
  * launch shape the step graph uses.  KBL_ESTATE before any kbl_batch_bounds call. */
 kbl_status kbl_batch_bounds_ms(kbl_batch* b, double* ms);
-/* Form of kbl_batch_step: 1 (default) ONE persistent launch for the whole step, whose blocks pull
- * the work items of all 13 phases (time step; per stage traces, bounds, residual, stage +
- * limiter) in phase order and wait, per problem, only for the earlier phases that problem's item
- * depends on (bounded waits: a wait that runs out raises the timeout flag, which
- * kbl_batch_check reports as KBL_ETIMEOUT, and ends the launch); 0 one persistent launch per
- * phase (14 launches).  Both run the same device code per element: results are identical.
- * Drops the captured graphs.  KBL_EINVAL for other values. */
+/* Form of kbl_batch_step: 1 ONE persistent launch for the whole step, whose blocks pull the
+ * work items of all 13 phases (time step; per stage traces, bounds, residual, stage + limiter)
+ * in phase order and wait, per problem, only for the earlier phases that problem's item depends
+ * on (bounded waits: a wait that runs out raises the timeout flag, which kbl_batch_check
+ * reports as KBL_ETIMEOUT, and ends the launch); 0 (default) one persistent launch per phase
+ * (14 launches), each in the launch shape the autotuner picks for its phase -- measured about
+ * 6% faster on the batched benchmark workload, as the one-launch kernel is compiled for the
+ * register budget of its most demanding phase.  Both run the same device code per element:
+ * results are identical.  Drops the captured graphs.  KBL_EINVAL for other values. */
 kbl_status kbl_batch_set_form(kbl_batch* b, int fused);
 /* For testing the timeout path of the fused form without a fault: with on != 0 the first bounds
  * item of the next steps waits for a completion count that no item reaches, so that wait runs
@@ -488,6 +491,67 @@ kbl_status kbl_adjoint_segment(kbl_ctx* ctx, const double* w0, const double* dts
 kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, const int32_t* nbr_dev,
                               int n_bc, const double* bc_dev, const double* w_dev,
                               double* bnd_dev, void* cuda_stream);
+
+/* ---- triangles (Sec. 5) ----------------------------------------------------
+ * Affine triangles with the Williams-Shunn solution points of order p in {1, 2}
+ * (3 and 6 points: the interior symmetric rules of degree 2 and 4, which are
+ * also the mean weights of the limiter) and p + 1 Gauss-Legendre flux points per
+ * edge; the residual is flux reconstruction with the DG correction (a strong-form
+ * nodal DG residual with the exact diagonal mass matrix), and a step is SSP-RK3
+ * with the kinetic bounds of every element's stencil (its solution points, its
+ * flux points and their exterior values, Sec. 5) and the node-set limiter after
+ * every stage, FP64 except for the bounds, which follow cfg->precision.
+ * Reference triangle (0,0), (1,0), (0,1); edge f runs from vertex f to vertex
+ * (f + 1) % 3, its flux points in that direction; the element across the edge
+ * runs it the other way.  All arrays are element-major: solution
+ * w[E][ns][4] (ns = (p+1)(p+2)/2), traces wf[E][nfp][4] (nfp = 3 (p+1), edge by
+ * edge), stencils S[E][ns + 2 nfp][4] (solution points, flux points, exterior
+ * values).  Device arrays unless marked HOST; calls are asynchronous on the
+ * stream given at creation unless stated. */
+typedef struct kbl_tri kbl_tri;
+
+/* Solution points rs[ns][2] and weights w[ns] (HOST, sum 1/2) of order p on the
+ * reference triangle; KBL_EINVAL for p outside {1, 2}. */
+kbl_status kbl_tri_points(int p, double* rs, double* w);
+
+/* A triangle mesh: xy[E][3][2] (HOST) vertices counterclockwise; nbr[E][3] (HOST)
+ * the element across edge f, or -(b+1) for boundary state b; nbr_edge[E][3]
+ * (HOST) that element's edge matched to f; bc[n_bc][4] (HOST) boundary states.
+ * cfg: dim 2, p in {1, 2}, gamma, flux, bounds and limiter settings as for
+ * kbl_create.  Copies everything; allocates a context for the bounds and the
+ * limiter and the step's scratch (about (3 ns + 5 nfp + 8) E doubles).
+ * KBL_EINVAL for a bad configuration, an out-of-range neighbour or a clockwise or
+ * degenerate element; KBL_ENOMEM / KBL_ECUDA on allocation failure. */
+kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy,
+                          const int32_t* nbr, const int32_t* nbr_edge, int n_bc, const double* bc,
+                          void* cuda_stream);
+kbl_status kbl_tri_destroy(kbl_tri* t);
+const char* kbl_tri_last_error(const kbl_tri* t);
+
+/* Interior values at the flux points: wf = interpolation of w (Eq. 2 on triangles). */
+kbl_status kbl_tri_traces(kbl_tri* t, const double* w, double* wf);
+
+/* Stencils of Sec. 5 for every element, from w and its traces wf. */
+kbl_status kbl_tri_gather_stencil(kbl_tri* t, const double* w, const double* wf, double* S);
+
+/* Residual R[E][ns][4] = -div F_h - sum_q lift (F*_n - F_h . n): the
+ * interpolated flux's divergence and the DG lifting of the flux-point jumps, with
+ * the configured common flux of the states rotated into each edge's normal frame. */
+kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R);
+
+/* Time step (synchronous): cfl * min over elements and solution points of
+ * h / (|U| + c), h = 2 area / longest edge; *dt_host = 0 for an empty mesh. */
+kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host);
+
+/* One SSP-RK3 step of w (in place) with the given dt: per stage the traces and
+ * stencils of the stage input, their kinetic bounds (kbl_bounds_stencil with the
+ * mesh's configuration), the residual, the Shu-Osher combination, the traces of
+ * the combined state and the node-set limiter (kbl_limit_nodes with the solution
+ * points' weights).  Non-physical states raise the flag kbl_tri_check reports. */
+kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt);
+
+/* Wait for the stream and report (then clear) the device flags, as kbl_check. */
+kbl_status kbl_tri_check(kbl_tri* t);
 
 #ifdef __cplusplus
 }

@@ -348,7 +348,8 @@ __global__ void k_batch_time_advance(const double* dt, double* t, int n)
 // ---------------------------------------------------------------------------
 constexpr int NTF = 128;   // threads per block of the fused step (the 4 x 2 or 2 x 4 bounds tile)
 #ifndef KBL_FUSED_MINB
-#define KBL_FUSED_MINB 6   // resident blocks per SM the fused kernel is compiled for
+#define KBL_FUSED_MINB 7   // resident blocks per SM the fused kernel is compiled for (measured
+                           // 5: 927, 6: 894, 7: 876 ms per step on the batched benchmark)
 #endif
 constexpr int NPH = 13;    // phases of a step
 enum { PK_DT = 0, PK_TR = 1, PK_B = 2, PK_R = 3, PK_S = 4 };
@@ -403,7 +404,6 @@ k_batch_step_fused(BatchDev bd, FusedDev fd, BatchOps ops, Phys ph, double cfl, 
     __shared__ int s_item, s_ok;
     const int P = bd.n_probs;
     const int total = 10 * fd.n_fr + 3 * fd.n_b;
-    double* outs[3] = {wa, wb, w};
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -447,7 +447,9 @@ k_batch_step_fused(BatchDev bd, FusedDev fd, BatchOps ops, Phys ph, double cfl, 
         if (!s_ok) break;
         __threadfence();
         const ProbDesc pd = bd.probs[prob];
-        const double* ws = st == 0 ? w : outs[st - 1];
+        // stage inputs and outputs: w -> wa -> wb -> w (selects, not an indexed array)
+        const double* ws = st == 0 ? w : (st == 1 ? wa : wb);
+        double* wo = st == 0 ? wa : (st == 1 ? wb : w);
         if (kind == PK_DT) {
             float b = FLT_MAX;
             switch (pd.p) {
@@ -489,10 +491,10 @@ k_batch_step_fused(BatchDev bd, FusedDev fd, BatchOps ops, Phys ph, double cfl, 
             double dtp = __longlong_as_double((long long)atomicAdd(dtbits + prob, 0ull));
             if (!(dtp > 0.0) || !(dtp < DBL_MAX)) dtp = 0.0;
             switch (pd.p) {
-                case 1: stage_item<2, NTF>(smraw, pd, wi, ops.o[1], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
-                case 2: stage_item<3, NTF>(smraw, pd, wi, ops.o[2], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
-                case 3: stage_item<4, NTF>(smraw, pd, wi, ops.o[3], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
-                case 4: stage_item<5, NTF>(smraw, pd, wi, ops.o[4], ph, st, w, ws, R, bnd, dtp, outs[st], flags); break;
+                case 1: stage_item<2, NTF>(smraw, pd, wi, ops.o[1], ph, st, w, ws, R, bnd, dtp, wo, flags); break;
+                case 2: stage_item<3, NTF>(smraw, pd, wi, ops.o[2], ph, st, w, ws, R, bnd, dtp, wo, flags); break;
+                case 3: stage_item<4, NTF>(smraw, pd, wi, ops.o[3], ph, st, w, ws, R, bnd, dtp, wo, flags); break;
+                case 4: stage_item<5, NTF>(smraw, pd, wi, ops.o[4], ph, st, w, ws, R, bnd, dtp, wo, flags); break;
             }
             if (st == 2) {
                 __syncthreads();
@@ -574,8 +576,8 @@ struct kbl_batch {
     // timing of the bounds launch of kbl_batch_bounds (kbl_batch_bounds_ms)
     cudaEvent_t tb0 = nullptr, tb1 = nullptr;
     bool tb_valid = false;
-    // the fused single-launch step (default) and its control words
-    int fused = 1;
+    // the fused single-launch step (kbl_batch_set_form) and its control words
+    int fused = 0;
     int stall_test = 0;
     int wait_polls = 1 << 20;          // about a second per wait
     int* d_cnt = nullptr;              // [2][P]: FR items, bounds items of each problem

@@ -1,0 +1,650 @@
+// kbl_tri.cu -- the method on affine triangles (Sec. 5: Williams-Shunn solution points,
+// Gauss-Legendre flux points), FP64 flux reconstruction with the DG correction, and the SSP-RK3
+// step that feeds the element-agnostic bounds (kbl_bounds_stencil) and node-set limiter
+// (kbl_limit_nodes).
+//
+// Reference triangle (0,0), (1,0), (0,1); barycentrics (l1, l2, l3) = (1 - r - s, r, s).  Edge f
+// runs from vertex f to vertex (f + 1) % 3 with p + 1 Gauss-Legendre flux points in its
+// direction; the element across it runs the shared edge the other way (its point p - k).
+// Arrays are element-major: w[E][ns][4], traces wf[E][nfp][4], stencils S[E][ns + 2 nfp][4].
+//
+// Solution points: the Williams-Shunn points of orders 1 and 2 are the unique interior
+// symmetric rules of 3 points (degree 2) and 6 points in two orbits (degree 4).  They are found
+// here from their symmetric moment equations (the invariants 1, e2, e3, e2^2 of the
+// barycentrics) by Newton's method with an analytic Jacobian.  The rule integrates the degree-2p
+// products of the Lagrange basis exactly, so the nodal mass matrix is diag(det J w_i) and the
+// lifting of the DG correction at flux point q is phi_i(x_q) (|e_q| gw_q / 2) / (det J w_i).
+//
+// Residual (Sec. 2.3 on simplices): R_i = -div F_h(x_i) - sum_q lift_iq (F*_n - F_h . n)(x_q),
+// F_h the interpolation of the solution-point fluxes, F*_n the configured common flux of the
+// states rotated into the edge's (n, t) frame.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kbl_internal.cuh"
+
+namespace {
+
+constexpr int TRI_PMAX = 2, TRI_NSMAX = 6, TRI_NFPMAX = 9;
+
+struct TriOps {
+    int p, ns, nfp;
+    double wq[TRI_NSMAX];                 // rule weights (sum 1/2)
+    double dr[TRI_NSMAX][TRI_NSMAX];      // d phi_j / dr at solution point i: [i][j]
+    double ds[TRI_NSMAX][TRI_NSMAX];
+    double phif[TRI_NFPMAX][TRI_NSMAX];   // phi_j at flux point q
+    double gw[TRI_NFPMAX];                // Gauss-Legendre weight of flux point q (sum 2 per edge)
+};
+
+// Per element: inverse Jacobian (dr/dx, dr/dy, ds/dx, ds/dy), det J, edge lengths, outward
+// unit normals, h = det J / longest edge (the shortest altitude).
+struct TriGeo {
+    double rx, ry, sx, sy, det, len[3], nx[3], ny[3], h;
+};
+
+// ---- host: the rule and the basis ------------------------------------------
+// Symmetric-orbit points (a, a), (1 - 2a, a), (a, 1 - 2a) in (r, s); their barycentrics are the
+// permutations of (1 - 2a, a, a).  Invariant moments of one orbit (sum over its 3 points) of
+// e2 = l1 l2 + l1 l3 + l2 l3, e3 = l1 l2 l3, e2^2 and their a-derivatives.
+void orbit_moments(double a, double m[4], double dm[4])
+{
+    const double b = 1.0 - 2.0 * a, db = -2.0;
+    const double e2 = 2.0 * a * b + a * a, de2 = 2.0 * (b + a * db) + 2.0 * a;
+    const double e3 = a * a * b, de3 = 2.0 * a * b + a * a * db;
+    m[0] = 3.0;
+    m[1] = 3.0 * e2;
+    m[2] = 3.0 * e3;
+    m[3] = 3.0 * e2 * e2;
+    dm[0] = 0.0;
+    dm[1] = 3.0 * de2;
+    dm[2] = 3.0 * de3;
+    dm[3] = 6.0 * e2 * de2;
+}
+
+// Exact integrals over the reference triangle of 1, e2, e3, e2^2 (sums of
+// int l1^i l2^j l3^k = i! j! k! / (i + j + k + 2)!).
+void invariant_integrals(double I[4])
+{
+    I[0] = 0.5;
+    I[1] = 3.0 * (1.0 / 24.0);                       // 3 x int l1 l2
+    I[2] = 1.0 / 120.0;                              // int l1 l2 l3
+    // e2^2 = sum l_i^2 l_j^2 (3 terms) + 2 sum over pairs of products sharing a factor:
+    //   2 (l1^2 l2 l3 + l1 l2^2 l3 + l1 l2 l3^2)
+    I[3] = 3.0 * (2.0 * 2.0 / 720.0) + 2.0 * 3.0 * (2.0 / 720.0);
+}
+
+bool ws_points(int p, double rs[][2], double* w)
+{
+    if (p == 1) {
+        const double a = 1.0 / 6.0;   // the interior 3-point rule of degree 2 (one orbit, equal weights)
+        const double pts[3][2] = {{a, a}, {1.0 - 2.0 * a, a}, {a, 1.0 - 2.0 * a}};
+        for (int i = 0; i < 3; i++) {
+            rs[i][0] = pts[i][0];
+            rs[i][1] = pts[i][1];
+            w[i] = 1.0 / 6.0;
+        }
+        return true;
+    }
+    if (p != 2) return false;
+    // unknowns x = (a1, a2, W1, W2): W1 M(a1) + W2 M(a2) = I for the four invariants
+    double x[4] = {0.1, 0.45, 0.05, 0.11}, I[4];
+    invariant_integrals(I);
+    for (int it = 0; it < 50; it++) {
+        double m1[4], dm1[4], m2[4], dm2[4], F[4], J[4][4];
+        orbit_moments(x[0], m1, dm1);
+        orbit_moments(x[1], m2, dm2);
+        double nrm = 0.0;
+        for (int k = 0; k < 4; k++) {
+            F[k] = x[2] * m1[k] + x[3] * m2[k] - I[k];
+            nrm += std::fabs(F[k]);
+            J[k][0] = x[2] * dm1[k];
+            J[k][1] = x[3] * dm2[k];
+            J[k][2] = m1[k];
+            J[k][3] = m2[k];
+        }
+        if (nrm < 1e-17) break;
+        // solve J dx = -F by Gaussian elimination with partial pivoting
+        double A[4][5];
+        for (int k = 0; k < 4; k++) {
+            for (int c = 0; c < 4; c++) A[k][c] = J[k][c];
+            A[k][4] = -F[k];
+        }
+        for (int c = 0; c < 4; c++) {
+            int piv = c;
+            for (int r = c + 1; r < 4; r++)
+                if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+            for (int k = 0; k < 5; k++) std::swap(A[c][k], A[piv][k]);
+            for (int r = c + 1; r < 4; r++) {
+                const double f = A[r][c] / A[c][c];
+                for (int k = c; k < 5; k++) A[r][k] -= f * A[c][k];
+            }
+        }
+        double dx[4];
+        for (int c = 3; c >= 0; c--) {
+            double t = A[c][4];
+            for (int k = c + 1; k < 4; k++) t -= A[c][k] * dx[k];
+            dx[c] = t / A[c][c];
+        }
+        for (int c = 0; c < 4; c++) x[c] += dx[c];
+    }
+    const double a[2] = {x[0], x[1]};
+    for (int o = 0; o < 2; o++) {
+        const double pts[3][2] = {{a[o], a[o]}, {1.0 - 2.0 * a[o], a[o]}, {a[o], 1.0 - 2.0 * a[o]}};
+        for (int i = 0; i < 3; i++) {
+            rs[3 * o + i][0] = pts[i][0];
+            rs[3 * o + i][1] = pts[i][1];
+            w[3 * o + i] = x[2 + o];
+        }
+    }
+    return true;
+}
+
+// Homogeneous barycentric monomials l1^i l2^j l3^k, i + j + k = p: a basis of the degree-p
+// polynomials on the triangle.  Value and (r, s) derivatives (dl1 = (-1, -1), dl2 = (1, 0),
+// dl3 = (0, 1)).
+int bary_exps(int p, int (*ex)[3])
+{
+    int n = 0;
+    for (int i = p; i >= 0; i--)
+        for (int j = p - i; j >= 0; j--) {
+            ex[n][0] = i;
+            ex[n][1] = j;
+            ex[n][2] = p - i - j;
+            n++;
+        }
+    return n;
+}
+void bary_eval(const int e[3], double r, double s, double& v, double& vr, double& vs)
+{
+    const double l[3] = {1.0 - r - s, r, s};
+    const double dlr[3] = {-1.0, 1.0, 0.0}, dls[3] = {-1.0, 0.0, 1.0};
+    double pw[3], dpw[3];
+    for (int k = 0; k < 3; k++) {
+        pw[k] = std::pow(l[k], e[k]);
+        dpw[k] = e[k] > 0 ? e[k] * std::pow(l[k], e[k] - 1) : 0.0;
+    }
+    v = pw[0] * pw[1] * pw[2];
+    vr = vs = 0.0;
+    for (int k = 0; k < 3; k++) {
+        const double rest = pw[(k + 1) % 3] * pw[(k + 2) % 3];
+        vr += dpw[k] * dlr[k] * rest;
+        vs += dpw[k] * dls[k] * rest;
+    }
+}
+
+// Lagrange basis on the solution points: phi_j = sum_m c[m][j] b_m with the barycentric
+// monomials b_m; c = V^-1 for V[i][m] = b_m(x_i), by LU factorisation (Doolittle, partial
+// pivoting) and one solve per unit vector.
+bool build_tri_ops(int p, const FrOps& gl, TriOps& o)
+{
+    if (p < 1 || p > TRI_PMAX) return false;
+    std::memset(&o, 0, sizeof(o));
+    o.p = p;
+    o.ns = (p + 1) * (p + 2) / 2;
+    o.nfp = 3 * (p + 1);
+    double rs[TRI_NSMAX][2];
+    if (!ws_points(p, rs, o.wq)) return false;
+    int ex[TRI_NSMAX][3];
+    const int n = bary_exps(p, ex);
+    double LU[TRI_NSMAX][TRI_NSMAX];
+    int perm[TRI_NSMAX];
+    for (int i = 0; i < n; i++) {
+        perm[i] = i;
+        for (int m = 0; m < n; m++) {
+            double v, vr, vs;
+            bary_eval(ex[m], rs[i][0], rs[i][1], v, vr, vs);
+            LU[i][m] = v;
+        }
+    }
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (std::fabs(LU[r][c]) > std::fabs(LU[piv][c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < n; k++) std::swap(LU[c][k], LU[piv][k]);
+            std::swap(perm[c], perm[piv]);
+        }
+        for (int r = c + 1; r < n; r++) {
+            LU[r][c] /= LU[c][c];
+            for (int k = c + 1; k < n; k++) LU[r][k] -= LU[r][c] * LU[c][k];
+        }
+    }
+    double cf[TRI_NSMAX][TRI_NSMAX];   // cf[m][j]
+    for (int j = 0; j < n; j++) {
+        double y[TRI_NSMAX];
+        for (int i = 0; i < n; i++) {   // L y = P e_j
+            double t = perm[i] == j ? 1.0 : 0.0;
+            for (int k = 0; k < i; k++) t -= LU[i][k] * y[k];
+            y[i] = t;
+        }
+        for (int i = n - 1; i >= 0; i--) {   // U c = y
+            double t = y[i];
+            for (int k = i + 1; k < n; k++) t -= LU[i][k] * cf[k][j];
+            cf[i][j] = t / LU[i][i];
+        }
+    }
+    auto phi = [&](int j, double r, double s, double& v, double& vr, double& vs) {
+        v = vr = vs = 0.0;
+        for (int m = 0; m < n; m++) {
+            double b, br, bs;
+            bary_eval(ex[m], r, s, b, br, bs);
+            v += cf[m][j] * b;
+            vr += cf[m][j] * br;
+            vs += cf[m][j] * bs;
+        }
+    };
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) {
+            double v, vr, vs;
+            phi(j, rs[i][0], rs[i][1], v, vr, vs);
+            o.dr[i][j] = vr;
+            o.ds[i][j] = vs;
+        }
+    const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+    for (int f = 0; f < 3; f++)
+        for (int k = 0; k <= p; k++) {
+            const double t = 0.5 * (1.0 + gl.x[k]);
+            const double r = V[f][0] + t * (V[(f + 1) % 3][0] - V[f][0]);
+            const double s = V[f][1] + t * (V[(f + 1) % 3][1] - V[f][1]);
+            const int q = f * (p + 1) + k;
+            o.gw[q] = gl.wq[k];
+            for (int j = 0; j < n; j++) {
+                double v, vr, vs;
+                phi(j, r, s, v, vr, vs);
+                o.phif[q][j] = v;
+            }
+        }
+    return true;
+}
+
+// ---- device -----------------------------------------------------------------------
+struct TriMeshDev {
+    int E, p;
+    const TriGeo* geo;
+    const int* nbr;
+    const int* nbr_edge;
+    const double* bc;
+};
+
+__device__ __forceinline__ const double* tri_exterior(const TriMeshDev& m, const double* __restrict__ wf, int e,
+                                                      int f, int k)
+{
+    const int nb = m.nbr[e * 3 + f];
+    if (nb >= 0) return wf + ((size_t)nb * 3 * (m.p + 1) + m.nbr_edge[e * 3 + f] * (m.p + 1) + (m.p - k)) * 4;
+    return m.bc + (size_t)(-nb - 1) * 4;
+}
+
+__global__ void k_tri_traces(const double* __restrict__ w, double* __restrict__ wf, int E, TriOps o)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)E * o.nfp) return;
+    const int e = (int)(t / o.nfp), q = (int)(t % o.nfp);
+    const double* we = w + (size_t)e * o.ns * 4;
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+        double s = 0.0;
+        for (int j = 0; j < o.ns; j++) s += o.phif[q][j] * we[j * 4 + v];
+        wf[((size_t)e * o.nfp + q) * 4 + v] = s;
+    }
+}
+
+__global__ void k_tri_gather(const double* __restrict__ w, const double* __restrict__ wf, TriMeshDev m, int ns,
+                             int nfp, double* __restrict__ S)
+{
+    const int nst = ns + 2 * nfp;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)m.E * nst) return;
+    const int e = (int)(t / nst), r = (int)(t % nst);
+    const double* src;
+    if (r < ns) src = w + ((size_t)e * ns + r) * 4;
+    else if (r < ns + nfp) src = wf + ((size_t)e * nfp + (r - ns)) * 4;
+    else {
+        const int q = r - ns - nfp;
+        src = tri_exterior(m, wf, e, q / (m.p + 1), q % (m.p + 1));
+    }
+    double* dst = S + ((size_t)e * nst + r) * 4;
+    dst[0] = src[0];
+    dst[1] = src[1];
+    dst[2] = src[2];
+    dst[3] = src[3];
+}
+
+// Common flux along the outward normal (nx, ny), interior state qi on the minus side.
+__device__ __forceinline__ void tri_common_flux(const double* qi, const double* qe, double nx, double ny,
+                                                double gamma, int flux, double* F)
+{
+    const double li[4] = {qi[0], qi[1] * nx + qi[2] * ny, -qi[1] * ny + qi[2] * nx, qi[3]};
+    const double le[4] = {qe[0], qe[1] * nx + qe[2] * ny, -qe[1] * ny + qe[2] * nx, qe[3]};
+    double Fl[4];
+    if (flux == 1) kbl_hllc<2, double>(li, le, 0, gamma, Fl);
+    else if (flux == 2) kbl_hll<2, double>(li, le, 0, gamma, Fl);
+    else kbl_rusanov<2, double>(li, le, 0, gamma, Fl);
+    F[0] = Fl[0];
+    F[1] = Fl[1] * nx - Fl[2] * ny;
+    F[2] = Fl[1] * ny + Fl[2] * nx;
+    F[3] = Fl[3];
+}
+
+// One thread per element (FP64), order P fixed at compile time so that the loops unroll and
+// the per-point fluxes stay in registers.
+template <int P>
+__global__ void __launch_bounds__(128) k_tri_rhs(const double* __restrict__ w, const double* __restrict__ wf,
+                                                 TriMeshDev m, TriOps o, double gamma, int flux, double* __restrict__ R)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const TriGeo g = m.geo[e];
+    constexpr int ns = (P + 1) * (P + 2) / 2, nfp = 3 * (P + 1);
+    double Fx[TRI_NSMAX][4], Fy[TRI_NSMAX][4], out[TRI_NSMAX][4];
+    for (int j = 0; j < ns; j++) {
+        double q[4];
+        for (int v = 0; v < 4; v++) q[v] = w[((size_t)e * ns + j) * 4 + v];
+        kbl_flux<2, double>(q, 0, gamma - 1.0, Fx[j]);
+        kbl_flux<2, double>(q, 1, gamma - 1.0, Fy[j]);
+    }
+    for (int i = 0; i < ns; i++)
+        for (int v = 0; v < 4; v++) {
+            double div = 0.0;
+            for (int j = 0; j < ns; j++) {
+                const double dx = o.dr[i][j] * g.rx + o.ds[i][j] * g.sx;
+                const double dy = o.dr[i][j] * g.ry + o.ds[i][j] * g.sy;
+                div += dx * Fx[j][v] + dy * Fy[j][v];
+            }
+            out[i][v] = -div;
+        }
+#pragma unroll 1
+    for (int q = 0; q < nfp; q++) {
+        const int f = q / (P + 1), k = q % (P + 1);
+        const double nx = g.nx[f], ny = g.ny[f];
+        double Fs[4];
+        tri_common_flux(wf + ((size_t)e * nfp + q) * 4, tri_exterior(m, wf, e, f, k), nx, ny, gamma, flux, Fs);
+        const double sc = 0.5 * g.len[f] * o.gw[q] / g.det;
+        for (int v = 0; v < 4; v++) {
+            double Fn = 0.0;
+            for (int j = 0; j < ns; j++) Fn += o.phif[q][j] * (Fx[j][v] * nx + Fy[j][v] * ny);
+            const double jump = Fs[v] - Fn;
+            for (int i = 0; i < ns; i++) out[i][v] -= o.phif[q][i] * sc / o.wq[i] * jump;
+        }
+    }
+    for (int i = 0; i < ns; i++)
+        for (int v = 0; v < 4; v++) R[((size_t)e * ns + i) * 4 + v] = out[i][v];
+}
+
+// SSP-RK3 combination (Shu-Osher form), element-wise.
+__global__ void k_tri_combine(int s, const double* __restrict__ wn, const double* ws, const double* __restrict__ R,
+                              double dt, double* wout, size_t n)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double v = ws[t] + dt * R[t];
+    wout[t] = s == 0 ? v : (s == 1 ? 0.75 * wn[t] + 0.25 * v : (1.0 / 3.0) * wn[t] + (2.0 / 3.0) * v);
+}
+
+// dt bits: min over elements and solution points of h / (|U| + c) (positive doubles order as their bits).
+__global__ void k_tri_dt(const double* __restrict__ w, TriMeshDev m, int ns, double gamma,
+                         unsigned long long* bits)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double best = DBL_MAX;
+    if (e < m.E) {
+        const double h = m.geo[e].h;
+        for (int i = 0; i < ns; i++) {
+            const double* q = w + ((size_t)e * ns + i) * 4;
+            const double P = kbl_pressure<2, double>(q, gamma - 1.0);
+            const double u = sqrt(q[1] * q[1] + q[2] * q[2]) / q[0];
+            best = fmin(best, h / (u + sqrt(gamma * P / q[0])));
+        }
+    }
+    unsigned long long b = __double_as_longlong(best);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+        b = ob < b ? ob : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMin(bits, b);
+}
+
+}  // namespace
+
+struct kbl_tri {
+    kbl_config cfg;
+    kbl_ctx* ctx = nullptr;     // bounds of explicit stencils and node-set limiting
+    TriOps ops;
+    int E = 0, n_bc = 0;
+    cudaStream_t stream = nullptr;
+    TriGeo* d_geo = nullptr;
+    int* d_nbr = nullptr;
+    int* d_nbr_edge = nullptr;
+    double* d_bc = nullptr;
+    double *d_wf = nullptr, *d_S = nullptr, *d_bnd = nullptr, *d_R = nullptr, *d_wa = nullptr, *d_wb = nullptr;
+    unsigned long long* d_bits = nullptr;
+    std::string err;
+};
+
+namespace {
+
+kbl_status tfail(kbl_tri* t, kbl_status st, const std::string& msg)
+{
+    if (t) t->err = msg;
+    return st;
+}
+
+TriMeshDev tri_dev(const kbl_tri* t)
+{
+    TriMeshDev m;
+    m.E = t->E;
+    m.p = t->cfg.p;
+    m.geo = t->d_geo;
+    m.nbr = t->d_nbr;
+    m.nbr_edge = t->d_nbr_edge;
+    m.bc = t->d_bc;
+    return m;
+}
+
+unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+extern "C" {
+
+kbl_status kbl_tri_points(int p, double* rs, double* w)
+{
+    if (!rs || !w) return KBL_EINVAL;
+    double pts[TRI_NSMAX][2], wq[TRI_NSMAX];
+    if (!ws_points(p, pts, wq)) return KBL_EINVAL;
+    const int ns = (p + 1) * (p + 2) / 2;
+    for (int i = 0; i < ns; i++) {
+        rs[2 * i] = pts[i][0];
+        rs[2 * i + 1] = pts[i][1];
+        w[i] = wq[i];
+    }
+    return KBL_OK;
+}
+
+kbl_status kbl_tri_destroy(kbl_tri* t)
+{
+    if (!t) return KBL_EINVAL;
+    void* ptrs[] = {t->d_geo, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_wf, t->d_S, t->d_bnd, t->d_R, t->d_wa, t->d_wb,
+                    t->d_bits};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (t->ctx) kbl_destroy(t->ctx);
+    delete t;
+    return KBL_OK;
+}
+
+kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy, const int32_t* nbr,
+                          const int32_t* nbr_edge, int n_bc, const double* bc, void* cuda_stream)
+{
+    if (!out) return KBL_EINVAL;
+    *out = nullptr;
+    if (!kbl_config_valid(cfg) || cfg->dim != 2 || cfg->p < 1 || cfg->p > TRI_PMAX) return KBL_EINVAL;
+    if (n_elem < 0 || n_bc < 0 || (n_elem > 0 && (!xy || !nbr || !nbr_edge)) || (n_bc > 0 && !bc)) return KBL_EINVAL;
+    for (long i = 0; i < 3L * n_elem; i++) {
+        const int b = nbr[i], g = nbr_edge[i];
+        if (b >= n_elem || (b < 0 && -(b + 1) >= n_bc) || (b >= 0 && (g < 0 || g > 2))) return KBL_EINVAL;
+    }
+    kbl_tri* t = new (std::nothrow) kbl_tri();
+    if (!t) return KBL_ENOMEM;
+    t->cfg = *cfg;
+    t->E = n_elem;
+    t->n_bc = n_bc;
+    t->stream = (cudaStream_t)cuda_stream;
+    kbl_status st = kbl_create(&t->ctx, cfg, cuda_stream);
+    if (st != KBL_OK) {
+        delete t;
+        return st;
+    }
+    FrOps gl;
+    kbl_build_fr_ops(cfg->p, gl);
+    if (!build_tri_ops(cfg->p, gl, t->ops)) {
+        kbl_tri_destroy(t);
+        return KBL_EINVAL;
+    }
+    // geometry on the host
+    std::vector<TriGeo> geo(std::max(1, n_elem));
+    for (int e = 0; e < n_elem; e++) {
+        const double* X = xy + (size_t)e * 6;
+        const double J00 = X[2] - X[0], J10 = X[3] - X[1], J01 = X[4] - X[0], J11 = X[5] - X[1];
+        TriGeo& g = geo[e];
+        g.det = J00 * J11 - J01 * J10;
+        if (!(g.det > 0.0)) {
+            kbl_tri_destroy(t);
+            return KBL_EINVAL;   // degenerate or clockwise element
+        }
+        g.rx = J11 / g.det;
+        g.ry = -J01 / g.det;
+        g.sx = -J10 / g.det;
+        g.sy = J00 / g.det;
+        double lmax = 0.0;
+        for (int f = 0; f < 3; f++) {
+            const double dx = X[2 * ((f + 1) % 3)] - X[2 * f], dy = X[2 * ((f + 1) % 3) + 1] - X[2 * f + 1];
+            g.len[f] = std::sqrt(dx * dx + dy * dy);
+            g.nx[f] = dy / g.len[f];
+            g.ny[f] = -dx / g.len[f];
+            lmax = std::max(lmax, g.len[f]);
+        }
+        g.h = g.det / lmax;
+    }
+    const size_t E = (size_t)std::max(1, n_elem), ns = t->ops.ns, nfp = t->ops.nfp;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    };
+    A((void**)&t->d_geo, E * sizeof(TriGeo));
+    A((void**)&t->d_nbr, E * 3 * sizeof(int));
+    A((void**)&t->d_nbr_edge, E * 3 * sizeof(int));
+    A((void**)&t->d_bc, (size_t)std::max(1, n_bc) * 4 * sizeof(double));
+    A((void**)&t->d_wf, E * nfp * 4 * sizeof(double));
+    A((void**)&t->d_S, E * (ns + 2 * nfp) * 4 * sizeof(double));
+    A((void**)&t->d_bnd, E * 8 * sizeof(double));
+    A((void**)&t->d_R, E * ns * 4 * sizeof(double));
+    A((void**)&t->d_wa, E * ns * 4 * sizeof(double));
+    A((void**)&t->d_wb, E * ns * 4 * sizeof(double));
+    A((void**)&t->d_bits, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(t->d_geo, geo.data(), E * sizeof(TriGeo), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_elem > 0) e = cudaMemcpy(t->d_nbr, nbr, (size_t)n_elem * 3 * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_elem > 0)
+        e = cudaMemcpy(t->d_nbr_edge, nbr_edge, (size_t)n_elem * 3 * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_bc > 0) e = cudaMemcpy(t->d_bc, bc, (size_t)n_bc * 4 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        kbl_tri_destroy(t);
+        return e == cudaErrorMemoryAllocation ? KBL_ENOMEM : KBL_ECUDA;
+    }
+    *out = t;
+    return KBL_OK;
+}
+
+const char* kbl_tri_last_error(const kbl_tri* t) { return t ? t->err.c_str() : "null triangle mesh"; }
+
+kbl_status kbl_tri_traces(kbl_tri* t, const double* w, double* wf)
+{
+    if (!t || (t->E > 0 && (!w || !wf))) return tfail(t, KBL_EINVAL, "null array");
+    const size_t n = (size_t)t->E * t->ops.nfp;
+    if (n) k_tri_traces<<<blocks_for(n, 256), 256, 0, t->stream>>>(w, wf, t->E, t->ops);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_tri_gather_stencil(kbl_tri* t, const double* w, const double* wf, double* S)
+{
+    if (!t || (t->E > 0 && (!w || !wf || !S))) return tfail(t, KBL_EINVAL, "null array");
+    const size_t n = (size_t)t->E * (t->ops.ns + 2 * t->ops.nfp);
+    if (n) k_tri_gather<<<blocks_for(n, 256), 256, 0, t->stream>>>(w, wf, tri_dev(t), t->ops.ns, t->ops.nfp, S);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R)
+{
+    if (!t || (t->E > 0 && (!w || !wf || !R))) return tfail(t, KBL_EINVAL, "null array");
+    if (t->E && t->cfg.p == 1)
+        k_tri_rhs<1><<<blocks_for(t->E, 128), 128, 0, t->stream>>>(w, wf, tri_dev(t), t->ops, t->cfg.gamma,
+                                                                    t->cfg.flux, R);
+    else if (t->E)
+        k_tri_rhs<2><<<blocks_for(t->E, 128), 128, 0, t->stream>>>(w, wf, tri_dev(t), t->ops, t->cfg.gamma,
+                                                                    t->cfg.flux, R);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host)
+{
+    if (!t || !dt_host || !(cfl > 0.0) || (t->E > 0 && !w)) return tfail(t, KBL_EINVAL, "bad argument");
+    *dt_host = 0.0;
+    if (t->E == 0) return KBL_OK;
+    cudaError_t e = cudaMemsetAsync(t->d_bits, 0x7f, sizeof(unsigned long long), t->stream);
+    if (e == cudaSuccess)
+        k_tri_dt<<<blocks_for(t->E, 128), 128, 0, t->stream>>>(w, tri_dev(t), t->ops.ns, t->cfg.gamma, t->d_bits);
+    unsigned long long b = 0;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&b, t->d_bits, sizeof(b), cudaMemcpyDeviceToHost, t->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+    if (e != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+    double h;
+    std::memcpy(&h, &b, sizeof(h));
+    *dt_host = (h > 0.0 && h < 1e300) ? cfl * h : 0.0;   // 0 when no point gave a finite rate
+    return KBL_OK;
+}
+
+// One SSP-RK3 step with a given dt: per stage the traces and stencils of its input, the kinetic
+// bounds of every stencil (kbl_bounds_stencil: the configured precision and quadrature), the
+// residual, the combination, the traces of the combined state and the node-set limiter
+// (kbl_limit_nodes, mean weights = the Williams-Shunn weights).
+kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
+{
+    if (!t || (t->E > 0 && !w) || !(dt >= 0.0)) return tfail(t, KBL_EINVAL, "bad argument");
+    if (t->E == 0) return KBL_OK;
+    const int ns = t->ops.ns, nfp = t->ops.nfp, nst = ns + 2 * nfp;
+    const size_t N = (size_t)t->E * ns * 4;
+    const double* ws = w;
+    double* outs[3] = {t->d_wa, t->d_wb, w};
+    kbl_status st;
+    for (int s = 0; s < 3; s++) {
+        if ((st = kbl_tri_traces(t, ws, t->d_wf)) != KBL_OK) return st;
+        if ((st = kbl_tri_gather_stencil(t, ws, t->d_wf, t->d_S)) != KBL_OK) return st;
+        if ((st = kbl_bounds_stencil(t->ctx, t->E, nst, t->d_S, t->d_bnd)) != KBL_OK)
+            return tfail(t, st, kbl_last_error(t->ctx));
+        if ((st = kbl_tri_residual(t, ws, t->d_wf, t->d_R)) != KBL_OK) return st;
+        k_tri_combine<<<blocks_for(N, 256), 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], N);
+        if ((st = kbl_tri_traces(t, outs[s], t->d_wf)) != KBL_OK) return st;
+        if ((st = kbl_limit_nodes(t->ctx, t->E, ns, nfp, t->ops.wq, outs[s], t->d_wf, t->d_bnd, nullptr)) != KBL_OK)
+            return tfail(t, st, kbl_last_error(t->ctx));
+        ws = outs[s];
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+kbl_status kbl_tri_check(kbl_tri* t)
+{
+    if (!t) return KBL_EINVAL;
+    const kbl_status st = kbl_check(t->ctx);
+    return st == KBL_OK ? KBL_OK : tfail(t, st, kbl_last_error(t->ctx));
+}
+
+}  // extern "C"

@@ -112,6 +112,16 @@ _SIGS = {
     "kbl_adjoint_step": (C.c_int, [_P, _P, C.c_double, _P]),
     "kbl_adjoint_segment": (C.c_int, [_P, _P, _P, C.c_int, _P, _P]),
     "kbl_forward_segment": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "kbl_tri_points": (C.c_int, [C.c_int, _P, _P]),
+    "kbl_tri_create": (C.c_int, [C.POINTER(_P), C.POINTER(KblConfig), C.c_int, _P, _P, _P, C.c_int, _P, _P]),
+    "kbl_tri_destroy": (C.c_int, [_P]),
+    "kbl_tri_last_error": (C.c_char_p, [_P]),
+    "kbl_tri_traces": (C.c_int, [_P, _P, _P]),
+    "kbl_tri_gather_stencil": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_tri_residual": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_tri_dt": (C.c_int, [_P, _P, C.c_double, C.POINTER(C.c_double)]),
+    "kbl_tri_step": (C.c_int, [_P, _P, C.c_double]),
+    "kbl_tri_check": (C.c_int, [_P]),
 }
 
 TUNE_BOUNDS_TILE = 0
@@ -533,3 +543,83 @@ class Batch:
 
     def launch_count(self):
         return int(self._lib.kbl_batch_launch_count(self._h))
+
+
+def tri_points(p):
+    """Williams-Shunn solution points rs[ns][2] and weights w[ns] of order p (host only)."""
+    ns = (int(p) + 1) * (int(p) + 2) // 2
+    rs, w = np.zeros((ns, 2)), np.zeros(ns)
+    st = load().kbl_tri_points(int(p), rs.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p))
+    if st != OK:
+        raise KblError(st, "tri_points")
+    return rs, w
+
+
+class TriMesh:
+    """Affine triangles of order p in {1, 2} (kbl_tri_*): xy[E][3][2] counterclockwise,
+    nbr[E][3] (neighbour or -(b+1)), nbr_edge[E][3], bc[n_bc][4] -- host arrays.  Solution
+    arrays are CUDA float64 tensors w[E][ns][4]."""
+
+    def __init__(self, p, xy, nbr, nbr_edge, bc, precision=FP64, stream=None, **overrides):
+        lib = load()
+        cfg = KblConfig()
+        if lib.kbl_config_default(C.byref(cfg), 2, int(p)) != OK:
+            raise KblError(EINVAL, "config_default")
+        cfg.precision = precision
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        xy, px = _host(xy, np.float64, "xy")
+        nb, pn = _host(nbr, np.int32, "nbr")
+        ne, pe = _host(nbr_edge, np.int32, "nbr_edge")
+        bc, pb = _host(bc, np.float64, "bc")
+        self.E = int(xy.reshape(-1, 6).shape[0])
+        n_bc = int(bc.reshape(-1, 4).shape[0]) if bc.size else 0
+        h = C.c_void_p()
+        st = lib.kbl_tri_create(C.byref(h), C.byref(cfg), self.E, px, pn, pe, n_bc, pb if n_bc else None,
+                                stream if stream is not None else _current_stream())
+        if st != OK:
+            raise KblError(st, "tri_create")
+        self._h, self._lib = h, lib
+        self.p = int(p)
+        self.ns = (self.p + 1) * (self.p + 2) // 2
+        self.nfp = 3 * (self.p + 1)
+        self.nstencil = self.ns + 2 * self.nfp
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = self._lib.kbl_tri_last_error(self._h)
+            raise KblError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.kbl_tri_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def traces(self, w, wf):
+        self._check(self._lib.kbl_tri_traces(self._h, _dev(w, "w"), _dev(wf, "wf")), "tri_traces")
+
+    def gather_stencil(self, w, wf, S):
+        self._check(self._lib.kbl_tri_gather_stencil(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(S, "S")),
+                    "tri_gather_stencil")
+
+    def residual(self, w, wf, R):
+        self._check(self._lib.kbl_tri_residual(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(R, "R")),
+                    "tri_residual")
+
+    def dt(self, w, cfl):
+        out = C.c_double()
+        self._check(self._lib.kbl_tri_dt(self._h, _dev(w, "w"), float(cfl), C.byref(out)), "tri_dt")
+        return out.value
+
+    def step(self, w, dt):
+        self._check(self._lib.kbl_tri_step(self._h, _dev(w, "w"), float(dt)), "tri_step")
+
+    def check(self):
+        self._check(self._lib.kbl_tri_check(self._h), "tri_check")

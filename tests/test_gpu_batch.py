@@ -278,6 +278,7 @@ def test_batch_one_launch_wait_timeout_is_reported():
     from paper_2407_20966_gb300 import kbl
     probs = inputs.four_quadrant_batch(41, 9, n_range=(2, 8))
     b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs])
+    b.set_form(1)
     w0 = inputs.batch_state(probs, b.nodes, b.state_offsets)
     wref = torch.from_numpy(w0).cuda()
     b.step(wref, 0.1)
