@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2070.0
 # The envelope loop of the FP32 bounds kernel needs, per (stencil state, velocity node),
 # 2 products (g = Ex Ey and C g) and 4 comparisons (min and max of both): 6 FP32 lane-ops.
 # Its roofline is the measured rate of exactly that instruction mix in a register-only loop
-# (csrc/peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
+# (peaks/kbl_fp32_peaks.cu, `bench.py --peaks`): 155.5
 # lane-ops per clock per SM (packed multiplies and three-input min/max issue to two pipes
 # that overlap only in part), times 152 SMs and the 2070 MHz maximum clock.
 OPS_PER_STATE_NODE = 6.0
@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "sedov", "sod", "batched", "adjoint"])
+    ap.add_argument("--workload", default="vortex",
+                    choices=["vortex", "sedov", "sod", "batched", "adjoint", "triangles"])
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint workload: elements per axis")
     ap.add_argument("--adj-steps", type=int, default=100, help="adjoint workload: time steps per gradient")
     ap.add_argument("--adj-cfl", type=float, default=0.05, help="adjoint workload: CFL number")
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--no-subworkloads", action="store_true",
                     help="vortex only: skip the Sedov and batched sub-objects of the default line")
     ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2, 2: 2x4; -1: default)")
+    ap.add_argument("--rhs-tc", action="store_true",
+                    help="FP32-mixed residual of P2/P3 on the tensor cores (off by default: slower, see the header)")
     return ap.parse_args()
 
 
@@ -203,6 +206,8 @@ def run_ours(args, rank, world):
     ctx = make_ctx(precision)
     if args.bounds_tile >= 0:
         ctx.set_tuning(kbl.TUNE_BOUNDS_TILE, args.bounds_tile)
+    if args.rhs_tc:
+        ctx.set_tuning(kbl.TUNE_RHS_TC, 1)
     xi = ctx.operator(kbl.OP_NODES)
     w0 = inputs.nodal_field(mesh, xi, wl["ic"])
     w_dev = torch.from_numpy(w0).to(dev)
@@ -606,6 +611,97 @@ def run_sub_mesh(args, name, steps, warmup, dev):
             "clocks": clk.summary()}
 
 
+def _tri_blast(x, y, gamma=1.4):
+    """Smoothed circular blast (tanh front about 2.5 cells wide at 256^2) with a weak shear, on [0,1]^2."""
+    import numpy as np
+    s = 0.5 * (1 - np.tanh((np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2) - 0.25) / 0.01))
+    rho = 0.125 + 0.875 * s
+    P = 0.1 + 0.9 * s
+    u = 0.2 * np.sin(2 * np.pi * y)
+    v = -0.2 * np.sin(2 * np.pi * x)
+    return np.stack([rho, rho * u, rho * v, P / (gamma - 1) + 0.5 * rho * (u * u + v * v)])
+
+
+def run_triangles(args, steps, warmup, dev):
+    """Affine triangles (Sec. 5: Williams-Shunn P2 solution points, 3 Gauss-Legendre points per
+    edge): 2 x 256 x 256 jittered periodic triangles on [0,1]^2, 32 x 32 velocity grid, FP32-mixed
+    bounds, FP64 residual and limiter, HLLC, fixed dt at CFL 0.05.  One step is kbl_tri_step:
+    per stage traces, stencils, bounds of the 24-state stencils, residual, combination, traces,
+    node-set limiter.  Timed like the headline (L2 flushed between steps); the roofline is the
+    explicit-stencil bounds launch over the whole mesh, timed alone with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_2407_20966_gb300 import inputs, kbl
+    m = inputs.tri_mesh_2d(256, 256, 0.0, 1.0, 0.0, 1.0, jitter=0.2, seed=17)
+    E = m.n_elem
+    tm = kbl.TriMesh(2, m.xy, m.nbr, m.nbr_edge, m.bc, precision=kbl.FP32_MIXED, flux=1, nu=(32, 32))
+    rs, _ = kbl.tri_points(2)
+    w0 = inputs.tri_nodal_field(m, rs, _tri_blast)
+    wd = torch.from_numpy(w0).to(dev)
+    dt = tm.dt(wd, 0.05)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        tm.step(wd, dt)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(dev.index) as clk:
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            tm.step(wd, dt)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    tm.check()
+    ms = sum(a.elapsed_time(z) for a, z in evs)
+    # dominant kernel: bounds of the gathered stencils over the whole mesh
+    wf = torch.zeros(E, tm.nfp, 4, dtype=torch.float64, device=dev)
+    S = torch.zeros(E, tm.nstencil, 4, dtype=torch.float64, device=dev)
+    bnd = torch.zeros(2, 4, E, dtype=torch.float64, device=dev)
+    tm.traces(wd, wf)
+    tm.gather_stencil(wd, wf, S)
+    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=kbl.FP32_MIXED)
+    ctx.bounds_stencil(S, bnd)
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, z in bev:
+        flush.zero_()
+        a.record(stream)
+        ctx.bounds_stencil(S, bnd)
+        z.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    bounds_ms = sum(a.elapsed_time(z) for a, z in bev) / len(bev)
+    achieved = OPS_PER_STATE_NODE * tm.nstencil * 32 * 32 * E / (bounds_ms * 1e-3) / 1e12
+    peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    ctx.close()
+    # end to end: pinned host state in, one step, pinned host state out
+    w_pin = torch.from_numpy(w0).pin_memory()
+    out_pin = torch.empty_like(w_pin).pin_memory()
+    ke = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        wd.copy_(w_pin, non_blocking=True)
+        tm.step(wd, dt)
+        out_pin.copy_(wd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    tm.close()
+    return {"workload": f"triangles: {E} periodic jittered P2 triangles (Williams-Shunn points), 32x32 velocity "
+                        f"grid, FP32-mixed bounds, HLLC, smoothed blast", "elements": E,
+            "value": E * 3 * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "warmup": warmup, "l2": "flushed between timed steps (256 MB write)",
+            "e2e": {"value": E * 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w0.nbytes),
+                    "d2h_bytes_per_step": int(w0.nbytes),
+                    "call": "pinned host copy in, kbl_tri_step, pinned host copy out"},
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                         "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_bounds_stencil_f32", "bounds_ms_per_launch": round(bounds_ms, 4),
+                         "work": "6 lane-ops per (stencil state, velocity node), 24 states per element",
+                         "peak_source": PEAK_SOURCE},
+            "clocks": clk.summary()}
+
+
 def run_adjoint(args, rank, world):
     """Reverse mode: the gradient of the integrated entropy at t_end with respect to the initial
     state of the shock-vortex problem (n x n P3, 32 x 32 velocity grid, FP64, CFL 0.05) through
@@ -683,7 +779,8 @@ def run_adjoint(args, rank, world):
 
 
 def run_peaks():
-    """Compile and run the register-only rate probes under paper_2407_20966_gb300/csrc/peaks/:
+    """Compile and run the register-only rate probes under peaks/ (measurement code beside this
+    file, not part of the library):
     FP32 multiply and min/max rates, alone and in the envelope pattern (kbl_fp32_peaks.cu),
     then the integer and FP64 operations the other kernels spend (kbl_int_fp64_rates.cu), per
     SM clock (clock64 inside each block); clocks sampled beside."""
@@ -692,7 +789,7 @@ def run_peaks():
     out_dir = os.path.join(here, "paper_2407_20966_gb300", "_build")
     os.makedirs(out_dir, exist_ok=True)
     for name in ("kbl_fp32_peaks", "kbl_int_fp64_rates"):
-        src = os.path.join(here, "paper_2407_20966_gb300", "csrc", "peaks", name + ".cu")
+        src = os.path.join(here, "peaks", name + ".cu")
         exe = os.path.join(out_dir, name)
         subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-o", exe, src],
                        check=True)
@@ -720,6 +817,21 @@ def main():
         line, _, _ = run_adjoint(args, rank, world)
         if rank == 0:
             print(json.dumps(line), flush=True)
+    elif args.workload == "triangles":
+        import torch
+        from paper_2407_20966_gb300 import build
+        build.build()
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+        torch.cuda.set_device(dev)
+        sub = run_triangles(args, steps=args.steps, warmup=args.warmup, dev=dev)
+        if rank == 0:
+            line = {"metric": METRIC, "value": sub["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": sub["ms_per_step"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                    "config": {"workload": sub["workload"], "elements": sub["elements"], "l2": sub["l2"],
+                               "parallelism": f"replicas x{world}"},
+                    "e2e": sub["e2e"], "roofline": sub["roofline"], "clocks": sub["clocks"]}
+            print(json.dumps(line), flush=True)
     elif args.workload == "batched":
         line, probs, _ = run_batched(args, rank, world)
         if rank == 0:
@@ -739,6 +851,7 @@ def main():
             line["batched"]["workload"] = bl["config"]["workload"]
             line["batched"]["elements"] = bl["config"]["elements"]
             line["batched"]["tuning"] = bl["config"]["tuning"]
+            line["triangles"] = run_triangles(args, steps=min(args.steps, 10), warmup=3, dev=dev)
         if rank == 0:
             if not args.no_cpu_baseline:
                 line["cpu_baseline"] = oracle_sample(args.workload, budget_s=12.0)
