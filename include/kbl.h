@@ -500,7 +500,9 @@ kbl_status kbl_bounds_noalloc(const kbl_config* cfg, int n_elem, const int32_t* 
  * nodal DG residual with the exact diagonal mass matrix), and a step is SSP-RK3
  * with the kinetic bounds of every element's stencil (its solution points, its
  * flux points and their exterior values, Sec. 5) and the node-set limiter after
- * every stage, FP64 except for the bounds, which follow cfg->precision.
+ * every stage.  KBL_FP64: everything in FP64; KBL_FP32_MIXED: the bounds and the
+ * residual as in that mode for quads (FP32 arithmetic on FP64 storage), the
+ * traces, the state and the limiter FP64.
  * Reference triangle (0,0), (1,0), (0,1); edge f runs from vertex f to vertex
  * (f + 1) % 3, its flux points in that direction; the element across the edge
  * runs it the other way.  All arrays are element-major: solution
@@ -519,7 +521,7 @@ kbl_status kbl_tri_points(int p, double* rs, double* w);
  * (HOST) that element's edge matched to f; bc[n_bc][4] (HOST) boundary states.
  * cfg: dim 2, p in {1, 2}, gamma, flux, bounds and limiter settings as for
  * kbl_create.  Copies everything; allocates a context for the bounds and the
- * limiter and the step's scratch (about (3 ns + 5 nfp + 8) E doubles).
+ * limiter and the step's scratch ((12 ns + 4 nfp + 8) E doubles).
  * KBL_EINVAL for a bad configuration, an out-of-range neighbour or a clockwise or
  * degenerate element; KBL_ENOMEM / KBL_ECUDA on allocation failure. */
 kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy,
@@ -536,18 +538,21 @@ kbl_status kbl_tri_gather_stencil(kbl_tri* t, const double* w, const double* wf,
 
 /* Residual R[E][ns][4] = -div F_h - sum_q lift (F*_n - F_h . n): the
  * interpolated flux's divergence and the DG lifting of the flux-point jumps, with
- * the configured common flux of the states rotated into each edge's normal frame. */
+ * the configured common flux of the states rotated into each edge's normal frame.
+ * FP64, or FP32 arithmetic on FP64 storage in KBL_FP32_MIXED. */
 kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R);
 
 /* Time step (synchronous): cfl * min over elements and solution points of
  * h / (|U| + c), h = 2 area / longest edge; *dt_host = 0 for an empty mesh. */
 kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host);
 
-/* One SSP-RK3 step of w (in place) with the given dt: per stage the traces and
- * stencils of the stage input, their kinetic bounds (kbl_bounds_stencil with the
+/* One SSP-RK3 step of w (in place) with the given dt: per stage the kinetic
+ * bounds of the stencils of the stage input (the stencils of kbl_tri_gather_stencil,
+ * gathered inside the bounds kernel; the bounds of kbl_bounds_stencil with the
  * mesh's configuration), the residual, the Shu-Osher combination, the traces of
  * the combined state and the node-set limiter (kbl_limit_nodes with the solution
- * points' weights).  Non-physical states raise the flag kbl_tri_check reports. */
+ * points' weights), whose limited face values are the next stage's traces.
+ * Non-physical states raise the flag kbl_tri_check reports. */
 kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt);
 
 /* Wait for the stream and report (then clear) the device flags, as kbl_check. */

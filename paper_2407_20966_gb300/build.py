@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkbl.so")
-SOURCES = ["kbl_api.cu", "kbl_fr.cu", "kbl_fr_tc.cu", "kbl_bounds.cu", "kbl_stencil.cu", "kbl_limit.cu", "kbl_noalloc.cu", "kbl_batch.cu", "kbl_tri.cu",
-           "kbl_adjoint.cu"]
+SOURCES = ["kbl_api.cu", "kbl_fr.cu", "kbl_fr_tc.cu", "kbl_bounds.cu", "kbl_stencil.cu", "kbl_limit.cu",
+           "kbl_noalloc.cu", "kbl_batch.cu", "kbl_tri.cu", "kbl_tri_bounds.cu", "kbl_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -293,7 +293,11 @@ int launch_bounds(const kbl_ctx* c, const double* w, const double* wf, double* b
                   cudaStream_t s);
 // limiting of explicit node sets U[E][ns][nv] (in place) with faces F[E][nf][nv], W[ns] host
 int launch_limit_nodes(const kbl_ctx* c, int E, int ns, int nf, const double* W, double* U, const double* F,
-                       const double* bnd, double* alpha, cudaStream_t s);
+                       const double* bnd, double* alpha, cudaStream_t s, double* F_out = nullptr);
+// Bounds of the Sec. 5 stencils of affine triangles of order p (1 or 2), gathered in the kernel
+// from w[E][ns][4], wf[E][nfp][4] and the connectivity of kbl_tri (kbl_tri.cu); -1 if not covered.
+int launch_bounds_tri(const kbl_ctx* c, int E, int p, const double* w, const double* wf, const int* nbr,
+                      const int* nbr_edge, const double* bc, double* bnd, cudaStream_t s);
 // bounds of explicit stencils S[E][nst][4] (2D, 1 <= nst <= 64); -1 for other shapes
 int launch_bounds_stencil(const kbl_ctx* c, int E, int nst, const double* S, double* bnd, cudaStream_t s);
 // mode 0: RK stage s fused with the limiter; mode 1: limiter only (ws = w in place)

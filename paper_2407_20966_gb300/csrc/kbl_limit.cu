@@ -95,10 +95,23 @@ struct NodeWeights {
     double w[64];
 };
 
+// The node-set limiter, one thread per element, FP64 and the checker's arithmetic; three
+// shortcuts leave every result as it is:
+// - extrema of V through order-preserving integer keys (the integer pipe, not FP64 min/max);
+// - Eq. 37 without its divisions when lo <= mn < mean < mx <= hi for the extremes mn, mx of V
+//   (then both ratios are >= 1 after rounding: hi - mean >= mx - mean > 0 and
+//   lo - mean <= mn - mean < 0 round monotonically), so alpha_i = 1;
+// - the pressure test of Eq. 47 without divisions: gm1 (E rho - |m|^2 / 2) >= p_floor rho plus a
+//   margin of 16 ulp of the terms proves P >= p_floor as the exact formula rounds it; only an
+//   element that fails this test forms P_min with the divisions.
+// F_out (may be NULL; may alias F): the limited face values mean + alpha (f - mean), then the
+// pressure step, as for the solution values: the traces of the limited state, whose
+// interpolation weights sum to one.
 template <int NV>
 __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, NodeWeights W, double* __restrict__ U,
-                                                     const double* __restrict__ F, const double* __restrict__ bnd,
-                                                     double* __restrict__ alpha_out, Phys ph, DevFlags* flags)
+                                                     const double* F, const double* __restrict__ bnd,
+                                                     double* __restrict__ alpha_out, Phys ph, DevFlags* flags,
+                                                     double* F_out)
 {
     constexpr int DIM = NV - 2;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,15 +127,18 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
             sw += W.w[n];
         }
         mean[v] = s / sw;
-        double mx = u[v], mn = u[v];
+        long long kmx = kbl_dev::dkey(u[v]), kmn = kmx;
         for (int n = 1; n < ns; n++) {
-            mx = fmax(mx, u[n * NV + v]);
-            mn = fmin(mn, u[n * NV + v]);
+            const long long k = kbl_dev::dkey(u[n * NV + v]);
+            kmx = k > kmx ? k : kmx;
+            kmn = k < kmn ? k : kmn;
         }
         for (int n = 0; n < nf; n++) {
-            mx = fmax(mx, f[n * NV + v]);
-            mn = fmin(mn, f[n * NV + v]);
+            const long long k = kbl_dev::dkey(f[n * NV + v]);
+            kmx = k > kmx ? k : kmx;
+            kmn = k < kmn ? k : kmn;
         }
+        const double mx = kbl_dev::dunkey(kmx), mn = kbl_dev::dunkey(kmn);
         const double dmax = mx - mean[v], dmin = mn - mean[v];
         const double lo = bnd[(size_t)v * E + e], hi = bnd[((size_t)NV + v) * E + e];
         if (mean[v] < lo || mean[v] > hi) atomicAdd(&flags->mean_outside, 1ull);
@@ -130,6 +146,8 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
         if (fabs(dmin) < ph.eps || fabs(dmax) < ph.eps) {
             atomicAdd(&flags->eps_rule, 1ull);
             a = ph.eps_rule ? 1.0 : 0.0;
+        } else if (mx <= hi && mn >= lo && dmax > 0.0 && dmin < 0.0) {
+            a = 1.0;
         } else {
             a = 1.0;
             const double t1 = fabs((hi - mean[v]) / dmax), t2 = fabs((lo - mean[v]) / dmin);
@@ -142,21 +160,45 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
     if (!ph.uncoupled)
 #pragma unroll
         for (int v = 0; v < NV; v++) av[v] = alpha;
-    // P_min over V of the limited values
+    // Eq. 47 over V of the limited values: first without divisions
     const double gm1 = ph.gamma - 1.0;
-    double pmin = INFINITY;
-    for (int n = 0; n < ns + nf; n++) {
+    bool sure = true;
+    for (int n = 0; n < ns + nf && sure; n++) {
         const double* x = n < ns ? u + n * NV : f + (n - ns) * NV;
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) q[v] = mean[v] + av[v] * (x[v] - mean[v]);
-        pmin = fmin(pmin, kbl_pressure<DIM>(q, gm1));
+        double mm = q[1] * q[1];
+        if (DIM == 2) mm += q[2] * q[2];
+        const double er = q[DIM + 1] * q[0], hm = 0.5 * mm;
+        const double margin = 16.0 * DBL_EPSILON * gm1 * (fabs(er) + hm) + 16.0 * DBL_EPSILON * ph.p_floor * q[0];
+        sure = q[0] > 0.0 && gm1 * (er - hm) >= ph.p_floor * q[0] + margin;
     }
     double aP = 1.0;
-    const bool relimit = pmin < ph.p_floor;
-    if (relimit) {
-        const double Pbar = kbl_pressure<DIM>(mean, gm1);
-        aP = (Pbar > ph.p_floor) ? fabs((ph.p_floor - Pbar) / (pmin - Pbar)) : 0.0;
+    bool relimit = false;
+    if (!sure) {
+        double pmin = INFINITY;
+        for (int n = 0; n < ns + nf; n++) {
+            const double* x = n < ns ? u + n * NV : f + (n - ns) * NV;
+            double q[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) q[v] = mean[v] + av[v] * (x[v] - mean[v]);
+            pmin = fmin(pmin, kbl_pressure<DIM>(q, gm1));
+        }
+        relimit = pmin < ph.p_floor;
+        if (relimit) {
+            const double Pbar = kbl_pressure<DIM>(mean, gm1);
+            aP = (Pbar > ph.p_floor) ? fabs((ph.p_floor - Pbar) / (pmin - Pbar)) : 0.0;
+        }
+    }
+    if (F_out) {
+        double* fo = F_out + (size_t)e * nf * NV;
+        for (int n = 0; n < nf; n++)
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const double ft = mean[v] + av[v] * (f[n * NV + v] - mean[v]);
+                fo[n * NV + v] = relimit ? mean[v] + aP * (ft - mean[v]) : ft;
+            }
     }
     for (int n = 0; n < ns; n++)
 #pragma unroll
@@ -178,16 +220,16 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
 }  // namespace
 
 int launch_limit_nodes(const kbl_ctx* c, int E, int ns, int nf, const double* W, double* U, const double* F,
-                       const double* bnd, double* alpha, cudaStream_t s)
+                       const double* bnd, double* alpha, cudaStream_t s, double* F_out)
 {
     if (E == 0) return 0;
     NodeWeights nw;
     for (int n = 0; n < 64; n++) nw.w[n] = n < ns ? W[n] : 0.0;
     const unsigned grid = (unsigned)((E + 127) / 128);
     if (c->cfg.dim == 2)
-        k_limit_nodes<4><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags);
+        k_limit_nodes<4><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags, F_out);
     else
-        k_limit_nodes<3><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags);
+        k_limit_nodes<3><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags, F_out);
     return 1;
 }
 

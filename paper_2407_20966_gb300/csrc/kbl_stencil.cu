@@ -5,7 +5,7 @@
 // bounds code (bounds2d_f32_core, bounds2d_f64_core) on stencils the caller assembles --
 // for triangles with their own solution and face points, or any unstructured mesh whose
 // traces live outside this library -- read from S[E][n_states][4].  A stencil shorter than
-// the compiled capacity (16, 32, 48 or 64 states) repeats its last state, which changes
+// the compiled capacity (16, 24, 32, 48 or 64 states) repeats its last state, which changes
 // neither the envelopes (a min or max over a repeated value) nor the velocity box.
 #include "kbl_bounds64_body.cuh"
 
@@ -83,6 +83,7 @@ int launch_bounds_stencil(const kbl_ctx* c, int E, int nst, const double* S, dou
     if (E == 0) return 0;
     if (c->cfg.dim != 2 || nst < 1 || nst > 64) return -1;
     if (nst <= 16) return run_stencil_nx<16>(c, E, nst, S, bnd, s);
+    if (nst <= 24) return run_stencil_nx<24>(c, E, nst, S, bnd, s);   // a P2 triangle's stencil
     if (nst <= 32) return run_stencil_nx<32>(c, E, nst, S, bnd, s);
     if (nst <= 48) return run_stencil_nx<48>(c, E, nst, S, bnd, s);
     return run_stencil_nx<64>(c, E, nst, S, bnd, s);

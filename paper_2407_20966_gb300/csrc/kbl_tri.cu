@@ -26,7 +26,7 @@
 #include <string>
 #include <vector>
 
-#include "kbl_internal.cuh"
+#include "kbl_fr_body.cuh"
 
 namespace {
 
@@ -39,6 +39,10 @@ struct TriOps {
     double ds[TRI_NSMAX][TRI_NSMAX];
     double phif[TRI_NFPMAX][TRI_NSMAX];   // phi_j at flux point q
     double gw[TRI_NFPMAX];                // Gauss-Legendre weight of flux point q (sum 2 per edge)
+    double lift[TRI_NFPMAX][TRI_NSMAX];   // phi_i(x_q) gw_q / (2 w_i): the lifting without |e| / det J
+    // FP32 copies (rounded on the host) for the FP32 arithmetic of the mixed precision
+    float drf[TRI_NSMAX][TRI_NSMAX], dsf[TRI_NSMAX][TRI_NSMAX], phiff[TRI_NFPMAX][TRI_NSMAX],
+        liftf[TRI_NFPMAX][TRI_NSMAX];
 };
 
 // Per element: inverse Jacobian (dr/dx, dr/dy, ds/dx, ds/dy), det J, edge lengths, outward
@@ -259,6 +263,18 @@ bool build_tri_ops(int p, const FrOps& gl, TriOps& o)
                 o.phif[q][j] = v;
             }
         }
+    for (int q = 0; q < o.nfp; q++)
+        for (int i = 0; i < n; i++) o.lift[q][i] = o.phif[q][i] * o.gw[q] / (2.0 * o.wq[i]);
+    for (int i = 0; i < TRI_NSMAX; i++)
+        for (int j = 0; j < TRI_NSMAX; j++) {
+            o.drf[i][j] = (float)o.dr[i][j];
+            o.dsf[i][j] = (float)o.ds[i][j];
+        }
+    for (int q = 0; q < TRI_NFPMAX; q++)
+        for (int j = 0; j < TRI_NSMAX; j++) {
+            o.phiff[q][j] = (float)o.phif[q][j];
+            o.liftf[q][j] = (float)o.lift[q][j];
+        }
     return true;
 }
 
@@ -314,65 +330,109 @@ __global__ void k_tri_gather(const double* __restrict__ w, const double* __restr
     dst[3] = src[3];
 }
 
-// Common flux along the outward normal (nx, ny), interior state qi on the minus side.
-__device__ __forceinline__ void tri_common_flux(const double* qi, const double* qe, double nx, double ny,
-                                                double gamma, int flux, double* F)
+// Common flux along the outward unit normal (nx, ny), interior state qi on the minus side: the
+// configured 1D flux of the states rotated into the edge's (n, t) frame, rotated back.
+template <typename T>
+__device__ __forceinline__ void tri_common_flux(const T* qi, const T* qe, T nx, T ny, T gamma, int flux, T* F)
 {
-    const double li[4] = {qi[0], qi[1] * nx + qi[2] * ny, -qi[1] * ny + qi[2] * nx, qi[3]};
-    const double le[4] = {qe[0], qe[1] * nx + qe[2] * ny, -qe[1] * ny + qe[2] * nx, qe[3]};
-    double Fl[4];
-    if (flux == 1) kbl_hllc<2, double>(li, le, 0, gamma, Fl);
-    else if (flux == 2) kbl_hll<2, double>(li, le, 0, gamma, Fl);
-    else kbl_rusanov<2, double>(li, le, 0, gamma, Fl);
+    const T li[4] = {qi[0], qi[1] * nx + qi[2] * ny, -qi[1] * ny + qi[2] * nx, qi[3]};
+    const T le[4] = {qe[0], qe[1] * nx + qe[2] * ny, -qe[1] * ny + qe[2] * nx, qe[3]};
+    T Fl[4];
+    if (flux == 1) kbl_hllc<2, T>(li, le, 0, gamma, Fl);
+    else if (flux == 2) kbl_hll<2, T>(li, le, 0, gamma, Fl);
+    else kbl_rusanov<2, T>(li, le, 0, gamma, Fl);
     F[0] = Fl[0];
     F[1] = Fl[1] * nx - Fl[2] * ny;
     F[2] = Fl[1] * ny + Fl[2] * nx;
     F[3] = Fl[3];
 }
 
-// One thread per element (FP64), order P fixed at compile time so that the loops unroll and
-// the per-point fluxes stay in registers.
-template <int P>
+template <typename T>
+__device__ __forceinline__ T tri_in(double x) { return kbl_dev::from_f64<T>(x); }
+
+// One thread per element, order P fixed at compile time (the loops unroll, the fluxes stay in
+// registers), arithmetic T (FP64, or FP32 on FP64 storage for the mixed precision).  The
+// physical fluxes enter as contravariant fluxes Fr = (dr/dx) Fx + (dr/dy) Fy, Fs = (ds/dx) Fx +
+// (ds/dy) Fy, so that -div F_h(x_i) = -sum_j (dr_ij Fr_j + ds_ij Fs_j); the normal flux at a flux
+// point is a_f Fr_h + b_f Fs_h with (a_f, b_f) = J^T n_f of its edge; the jump of the common flux
+// is lifted with lift_qi |e_f| / det J.
+template <int P, typename T>
 __global__ void __launch_bounds__(128) k_tri_rhs(const double* __restrict__ w, const double* __restrict__ wf,
-                                                 TriMeshDev m, TriOps o, double gamma, int flux, double* __restrict__ R)
+                                                 TriMeshDev m, TriOps o, double gamma_d, int flux,
+                                                 double* __restrict__ R)
 {
+    constexpr bool F32 = sizeof(T) == sizeof(float);
+    constexpr int ns = (P + 1) * (P + 2) / 2, nfp = 3 * (P + 1);
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m.E) return;
-    const TriGeo g = m.geo[e];
-    constexpr int ns = (P + 1) * (P + 2) / 2, nfp = 3 * (P + 1);
-    double Fx[TRI_NSMAX][4], Fy[TRI_NSMAX][4], out[TRI_NSMAX][4];
+    const TriGeo& g = m.geo[e];
+    const T rx = tri_in<T>(g.rx), ry = tri_in<T>(g.ry), sx = tri_in<T>(g.sx), sy = tri_in<T>(g.sy);
+    const T gamma = tri_in<T>(gamma_d), gm1 = F32 ? gamma - T(1) : tri_in<T>(gamma_d - 1.0);
+    T Fr[ns][4], Fs[ns][4], out[ns][4];
+#pragma unroll
     for (int j = 0; j < ns; j++) {
-        double q[4];
-        for (int v = 0; v < 4; v++) q[v] = w[((size_t)e * ns + j) * 4 + v];
-        kbl_flux<2, double>(q, 0, gamma - 1.0, Fx[j]);
-        kbl_flux<2, double>(q, 1, gamma - 1.0, Fy[j]);
-    }
-    for (int i = 0; i < ns; i++)
+        T q[4], Fx[4], Fy[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) q[v] = tri_in<T>(w[((size_t)e * ns + j) * 4 + v]);
+        kbl_flux<2, T>(q, 0, gm1, Fx);
+        kbl_flux<2, T>(q, 1, gm1, Fy);
+#pragma unroll
         for (int v = 0; v < 4; v++) {
-            double div = 0.0;
+            Fr[j][v] = rx * Fx[v] + ry * Fy[v];
+            Fs[j][v] = sx * Fx[v] + sy * Fy[v];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < ns; i++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            T div = T(0);
+#pragma unroll
             for (int j = 0; j < ns; j++) {
-                const double dx = o.dr[i][j] * g.rx + o.ds[i][j] * g.sx;
-                const double dy = o.dr[i][j] * g.ry + o.ds[i][j] * g.sy;
-                div += dx * Fx[j][v] + dy * Fy[j][v];
+                const T dr = F32 ? (T)o.drf[i][j] : (T)o.dr[i][j];
+                const T ds = F32 ? (T)o.dsf[i][j] : (T)o.ds[i][j];
+                div += dr * Fr[j][v] + ds * Fs[j][v];
             }
             out[i][v] = -div;
         }
+    // J = inverse of ((rx, ry), (sx, sy)): J00 = x_r = sy det, J01 = x_s = -ry det, J10 = y_r = -sx det,
+    // J11 = y_s = rx det
+    const T det = tri_in<T>(g.det);
 #pragma unroll 1
-    for (int q = 0; q < nfp; q++) {
-        const int f = q / (P + 1), k = q % (P + 1);
-        const double nx = g.nx[f], ny = g.ny[f];
-        double Fs[4];
-        tri_common_flux(wf + ((size_t)e * nfp + q) * 4, tri_exterior(m, wf, e, f, k), nx, ny, gamma, flux, Fs);
-        const double sc = 0.5 * g.len[f] * o.gw[q] / g.det;
-        for (int v = 0; v < 4; v++) {
-            double Fn = 0.0;
-            for (int j = 0; j < ns; j++) Fn += o.phif[q][j] * (Fx[j][v] * nx + Fy[j][v] * ny);
-            const double jump = Fs[v] - Fn;
-            for (int i = 0; i < ns; i++) out[i][v] -= o.phif[q][i] * sc / o.wq[i] * jump;
+    for (int f = 0; f < 3; f++) {
+        const T nx = tri_in<T>(g.nx[f]), ny = tri_in<T>(g.ny[f]);
+        const T a = det * (sy * nx - sx * ny), b = det * (rx * ny - ry * nx);
+        const T sc = tri_in<T>(g.len[f]) / det;
+#pragma unroll
+        for (int k = 0; k <= P; k++) {
+            const int q = f * (P + 1) + k;
+            T qi[4], qe[4], Fc[4];
+            const double* ext = tri_exterior(m, wf, e, f, k);
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                qi[v] = tri_in<T>(wf[((size_t)e * nfp + q) * 4 + v]);
+                qe[v] = tri_in<T>(ext[v]);
+            }
+            tri_common_flux<T>(qi, qe, nx, ny, gamma, flux, Fc);
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                T fr = T(0), fs = T(0);
+#pragma unroll
+                for (int j = 0; j < ns; j++) {
+                    const T ph = F32 ? (T)o.phiff[q][j] : (T)o.phif[q][j];
+                    fr += ph * Fr[j][v];
+                    fs += ph * Fs[j][v];
+                }
+                const T jump = sc * (Fc[v] - (a * fr + b * fs));
+#pragma unroll
+                for (int i = 0; i < ns; i++) out[i][v] -= (F32 ? (T)o.liftf[q][i] : (T)o.lift[q][i]) * jump;
+            }
         }
     }
+#pragma unroll
     for (int i = 0; i < ns; i++)
-        for (int v = 0; v < 4; v++) R[((size_t)e * ns + i) * 4 + v] = out[i][v];
+#pragma unroll
+        for (int v = 0; v < 4; v++) R[((size_t)e * ns + i) * 4 + v] = kbl_dev::to_f64<T>(out[i][v]);
 }
 
 // SSP-RK3 combination (Shu-Osher form), element-wise.
@@ -420,7 +480,7 @@ struct kbl_tri {
     int* d_nbr = nullptr;
     int* d_nbr_edge = nullptr;
     double* d_bc = nullptr;
-    double *d_wf = nullptr, *d_S = nullptr, *d_bnd = nullptr, *d_R = nullptr, *d_wa = nullptr, *d_wb = nullptr;
+    double *d_wf = nullptr, *d_bnd = nullptr, *d_R = nullptr, *d_wa = nullptr, *d_wb = nullptr;
     unsigned long long* d_bits = nullptr;
     std::string err;
 };
@@ -468,8 +528,7 @@ kbl_status kbl_tri_points(int p, double* rs, double* w)
 kbl_status kbl_tri_destroy(kbl_tri* t)
 {
     if (!t) return KBL_EINVAL;
-    void* ptrs[] = {t->d_geo, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_wf, t->d_S, t->d_bnd, t->d_R, t->d_wa, t->d_wb,
-                    t->d_bits};
+    void* ptrs[] = {t->d_geo, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_wf, t->d_bnd, t->d_R, t->d_wa, t->d_wb, t->d_bits};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (t->ctx) kbl_destroy(t->ctx);
@@ -540,7 +599,6 @@ kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, cons
     A((void**)&t->d_nbr_edge, E * 3 * sizeof(int));
     A((void**)&t->d_bc, (size_t)std::max(1, n_bc) * 4 * sizeof(double));
     A((void**)&t->d_wf, E * nfp * 4 * sizeof(double));
-    A((void**)&t->d_S, E * (ns + 2 * nfp) * 4 * sizeof(double));
     A((void**)&t->d_bnd, E * 8 * sizeof(double));
     A((void**)&t->d_R, E * ns * 4 * sizeof(double));
     A((void**)&t->d_wa, E * ns * 4 * sizeof(double));
@@ -582,12 +640,17 @@ kbl_status kbl_tri_gather_stencil(kbl_tri* t, const double* w, const double* wf,
 kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R)
 {
     if (!t || (t->E > 0 && (!w || !wf || !R))) return tfail(t, KBL_EINVAL, "null array");
-    if (t->E && t->cfg.p == 1)
-        k_tri_rhs<1><<<blocks_for(t->E, 128), 128, 0, t->stream>>>(w, wf, tri_dev(t), t->ops, t->cfg.gamma,
-                                                                    t->cfg.flux, R);
-    else if (t->E)
-        k_tri_rhs<2><<<blocks_for(t->E, 128), 128, 0, t->stream>>>(w, wf, tri_dev(t), t->ops, t->cfg.gamma,
-                                                                    t->cfg.flux, R);
+    if (t->E) {
+        const unsigned grid = blocks_for(t->E, 128);
+        const bool f32 = t->cfg.precision == KBL_FP32_MIXED;
+        const TriMeshDev md = tri_dev(t);
+        const double gam = t->cfg.gamma;
+        const int fl = t->cfg.flux;
+        if (t->cfg.p == 1 && f32) k_tri_rhs<1, float><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
+        else if (t->cfg.p == 1) k_tri_rhs<1, double><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
+        else if (f32) k_tri_rhs<2, float><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
+        else k_tri_rhs<2, double><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
+    }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
 }
@@ -611,29 +674,30 @@ kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host)
     return KBL_OK;
 }
 
-// One SSP-RK3 step with a given dt: per stage the traces and stencils of its input, the kinetic
-// bounds of every stencil (kbl_bounds_stencil: the configured precision and quadrature), the
-// residual, the combination, the traces of the combined state and the node-set limiter
-// (kbl_limit_nodes, mean weights = the Williams-Shunn weights).
+// One SSP-RK3 step with a given dt: per stage the kinetic bounds of every stencil of the stage
+// input (gathered inside the bounds kernel from the state and its traces; the configured
+// precision and quadrature), the residual, the combination, the traces of the combined state
+// and the node-set limiter (the mean weights = the Williams-Shunn weights), which also writes the
+// limited face values: the traces of the next stage's input.
 kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
 {
     if (!t || (t->E > 0 && !w) || !(dt >= 0.0)) return tfail(t, KBL_EINVAL, "bad argument");
     if (t->E == 0) return KBL_OK;
-    const int ns = t->ops.ns, nfp = t->ops.nfp, nst = ns + 2 * nfp;
+    const int ns = t->ops.ns, nfp = t->ops.nfp;
     const size_t N = (size_t)t->E * ns * 4;
     const double* ws = w;
     double* outs[3] = {t->d_wa, t->d_wb, w};
     kbl_status st;
+    if ((st = kbl_tri_traces(t, w, t->d_wf)) != KBL_OK) return st;
     for (int s = 0; s < 3; s++) {
-        if ((st = kbl_tri_traces(t, ws, t->d_wf)) != KBL_OK) return st;
-        if ((st = kbl_tri_gather_stencil(t, ws, t->d_wf, t->d_S)) != KBL_OK) return st;
-        if ((st = kbl_bounds_stencil(t->ctx, t->E, nst, t->d_S, t->d_bnd)) != KBL_OK)
-            return tfail(t, st, kbl_last_error(t->ctx));
+        if (launch_bounds_tri(t->ctx, t->E, t->cfg.p, ws, t->d_wf, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_bnd,
+                              t->stream) < 0)
+            return tfail(t, KBL_EINVAL, "bounds of this order not compiled in");
         if ((st = kbl_tri_residual(t, ws, t->d_wf, t->d_R)) != KBL_OK) return st;
         k_tri_combine<<<blocks_for(N, 256), 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], N);
         if ((st = kbl_tri_traces(t, outs[s], t->d_wf)) != KBL_OK) return st;
-        if ((st = kbl_limit_nodes(t->ctx, t->E, ns, nfp, t->ops.wq, outs[s], t->d_wf, t->d_bnd, nullptr)) != KBL_OK)
-            return tfail(t, st, kbl_last_error(t->ctx));
+        launch_limit_nodes(t->ctx, t->E, ns, nfp, t->ops.wq, outs[s], t->d_wf, t->d_bnd, nullptr, t->stream,
+                           t->d_wf);
         ws = outs[s];
     }
     const cudaError_t e = cudaGetLastError();

@@ -4,10 +4,11 @@
   traces     kbl_tri_traces(w)              vs orc.tri_traces        1e-14 of the element's scale
   stencils   kbl_tri_gather_stencil(w, wf)  vs orc.tri_gather_stencil, same inputs: bit-exact
   residual   kbl_tri_residual(w, wf)        vs orc.tri_rhs, same inputs: 1e-12 of the term scale
+             (FP64), 1e-5 (FP32-mixed: FP32 arithmetic on FP64 storage)
   dt         kbl_tri_dt                     vs orc.tri_dt            1e-14
   bounds     kbl_bounds_stencil of the device's stencils vs orc.bounds_stencil: 1e-12 / 1e-5
-  step       kbl_tri_step                   vs orc.tri_ssprk3_step   1e-12 FP64; FP32-mixed bounds:
-             1e-5 where the step is well conditioned (a blast with density >= 0.125)
+  step       kbl_tri_step                   vs orc.tri_ssprk3_step   1e-12 FP64; FP32-mixed (bounds
+             and residual): 1e-5 where the step is well conditioned (a blast, density >= 0.125)
 Meshes of 2 x nx x ny jittered triangles span several thread blocks with a ragged tail, periodic
 and with boundary states, for every common flux.
 """
@@ -139,6 +140,25 @@ def test_traces_stencils_residual_dt(orc, p, nx, ny, periodic, flux):
     assert abs(dt - dt_ref) <= 1e-14 * dt_ref
 
 
+@pytest.mark.parametrize("p,flux,periodic", [(1, 0, True), (2, 1, False), (2, 2, True), (1, 1, False)])
+def test_residual_fp32(orc, p, flux, periodic):
+    """FP32-mixed: the residual in FP32 arithmetic on FP64 storage, against the checker's FP64
+    residual on the same inputs, to 1e-5 of the size of the terms it sums."""
+    import torch
+    m, om, cfg, tm, w = _setup(orc, p, 13, 11, periodic, flux, precision=1)
+    E = m.n_elem
+    wf_ref = orc.tri_traces(cfg, om, w)
+    wd, wf_in = _dev(w), _dev(wf_ref)
+    S_d = torch.zeros(E, tm.nstencil, 4, dtype=torch.float64, device="cuda")
+    tm.gather_stencil(wd, wf_in, S_d)
+    R_d = torch.zeros_like(wd)
+    tm.residual(wd, wf_in, R_d)
+    R_ref = orc.tri_rhs(cfg, om, w, wf_ref)
+    err = np.abs(R_d.cpu().numpy() - R_ref) / np.maximum(np.abs(R_ref), _residual_scale(m, w, S_d.cpu().numpy()))
+    assert err.max() < TOL_FP32, err.max()
+    assert err.max() > 1e-12   # FP32 arithmetic is in use
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("p", [1, 2])
 def test_stencil_bounds(orc, p, precision):
@@ -177,7 +197,7 @@ def test_step_fp64(orc, p, flux, periodic):
 
 
 @pytest.mark.parametrize("p", [1, 2])
-def test_step_fp32_bounds(orc, p):
+def test_step_fp32_mixed(orc, p):
     m, om, cfg, tm, w = _setup(orc, p, 12, 11, True, flux=1, precision=1)
     wd = _dev(w)
     dt = orc.tri_dt(cfg, om, w, 0.2)
