@@ -452,10 +452,15 @@ int run_rhs_tc(const kbl_ctx* c, const double* w, const double* wf, double* R, c
         cudaFuncSetAttribute(k_rhs_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
             cudaSuccess)
         return -2;
-    int dev = 0, nsm = 0, per = 0;
+    // resident blocks per SM from the device's limits: the occupancy query does not see the
+    // shared-memory carveout set above and answers 1.  Registers: __launch_bounds__(TC_NT,
+    // TC_MINB); shared memory: the per-SM capacity over the block's share (plus the 1 KB the
+    // runtime reserves per block); tensor memory: 512 columns per SM.
+    int dev = 0, nsm = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rhs_tc<N>, TC_NT, SH::BYTES);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    int per = std::min(TC_MINB, smem_sm / (SH::BYTES + 1024));
     per = std::max(1, std::min(per, 512 / TC_TMEM_COLS));
     const int ntiles = (c->E + TC_EL - 1) / TC_EL;
     const int grid = std::min(ntiles, nsm * per);
