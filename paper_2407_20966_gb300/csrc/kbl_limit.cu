@@ -104,6 +104,7 @@ struct NodeWeights {
 // - the pressure test of Eq. 47 without divisions: gm1 (E rho - |m|^2 / 2) >= p_floor rho plus a
 //   margin of 16 ulp of the terms proves P >= p_floor as the exact formula rounds it; only an
 //   element that fails this test forms P_min with the divisions.
+// - where alpha = 1 for every component, Eq. 47 screened in FP32 (below) and the values kept.
 // F_out (may be NULL; may alias F): the limited face values mean + alpha (f - mean), then the
 // pressure step, as for the solution values: the traces of the limited state, whose
 // interpolation weights sum to one.
@@ -160,8 +161,55 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
     if (!ph.uncoupled)
 #pragma unroll
         for (int v = 0; v < NV; v++) av[v] = alpha;
-    // Eq. 47 over V of the limited values: first without divisions
     const double gm1 = ph.gamma - 1.0;
+    // alpha = 1 for every component (the common case): V limited is mean + (x - mean) = x up to
+    // FP64 rounding of |x| + |mean|.  Screen Eq. 47 in FP32 on the truncated x: with A_v =
+    // |x_v| + |mean_v|, the FP32 value of (gamma - 1)(E rho - |m|^2 / 2) differs from the FP64
+    // one of the limited state by at most 2^-19 (gamma - 1)(A_E A_rho + A_m^2) (inputs truncated
+    // to 2^-23, the limited state within 2^-52 A of x, a few FP32 roundings); a margin of 2^-16
+    // of that, plus 2^-16 p_floor A_rho for the density's own error, then proves P >= p_floor as
+    // the exact formula rounds it.  Magnitudes are held inside [2^-40, 2^40] so that nothing
+    // overflows or loses its terms to underflow.  Such an element keeps its values (the FP64
+    // mean + (x - mean) would move them by rounding only) and skips the FP64 steps below.
+    if (alpha == 1.0) {
+        float mf[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) mf[v] = fabsf(f32_trunc(mean[v]));
+        const float gf = f32_trunc(gm1), pf = f32_trunc(ph.p_floor) * (1.0f + 0x1p-20f);
+        bool ok = true;
+        for (int n = 0; n < ns + nf && ok; n++) {
+            const double* x = n < ns ? u + n * NV : f + (n - ns) * NV;
+            float q[NV], A[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                q[v] = f32_trunc(x[v]);
+                A[v] = fabsf(q[v]) + mf[v];
+            }
+            float mm = q[1] * q[1], am = A[1] * A[1];
+            if (DIM == 2) {
+                mm += q[2] * q[2];
+                am += A[2] * A[2];
+            }
+            const float X = gf * (q[DIM + 1] * q[0] - 0.5f * mm);
+            const float margin = 0x1p-16f * gf * (A[DIM + 1] * A[0] + am) + 0x1p-16f * pf * A[0];
+            bool in_range = q[0] > 0x1p-40f && q[0] > 0x1p-10f * A[0] && A[DIM + 1] > 0x1p-40f;
+#pragma unroll
+            for (int v = 0; v < NV; v++) in_range = in_range && A[v] < 0x1p40f;
+            ok = in_range && X >= pf * q[0] + margin;
+        }
+        if (ok) {
+            if (F_out && F_out != F) {
+                double* fo = F_out + (size_t)e * nf * NV;
+                for (int n = 0; n < nf * NV; n++) fo[n] = f[n];
+            }
+            if (alpha_out) {
+                alpha_out[e] = 1.0;
+                alpha_out[(size_t)E + e] = 1.0;
+            }
+            return;
+        }
+    }
+    // Eq. 47 over V of the limited values: first without divisions
     bool sure = true;
     for (int n = 0; n < ns + nf && sure; n++) {
         const double* x = n < ns ? u + n * NV : f + (n - ns) * NV;
