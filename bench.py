@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-subworkloads", action="store_true",
                     help="vortex only: skip the Sedov and batched sub-objects of the default line")
     ap.add_argument("--bounds-tile", type=int, default=-1, help="FP32 bounds thread tile (0: 4x4, 1: 4x2, 2: 2x4; -1: default)")
+    ap.add_argument("--rhs-overlap", type=int, default=1, choices=[0, 1],
+                    help="1: each stage's residual on a graph branch beside its bounds (default); 0: serial")
     ap.add_argument("--rhs-tc", action="store_true",
                     help="FP32-mixed residual of P2/P3 on the tensor cores (off by default: slower, see the header)")
     return ap.parse_args()
@@ -208,6 +210,8 @@ def run_ours(args, rank, world):
         ctx.set_tuning(kbl.TUNE_BOUNDS_TILE, args.bounds_tile)
     if args.rhs_tc:
         ctx.set_tuning(kbl.TUNE_RHS_TC, 1)
+    if not args.rhs_overlap:
+        ctx.set_tuning(kbl.TUNE_RHS_OVERLAP, 0)
     xi = ctx.operator(kbl.OP_NODES)
     w0 = inputs.nodal_field(mesh, xi, wl["ic"])
     w_dev = torch.from_numpy(w0).to(dev)

@@ -107,8 +107,8 @@ typedef struct kbl_ctx kbl_ctx;
 /* Counters of the limiter since the last read (kbl_read_counters clears them). */
 typedef struct {
     int32_t nonphysical;      /* a stencil state with rho <= 0 or P <= 0 was met */
-    int32_t timeout;          /* a bounded device wait gave up (no kernel of this
-                                 version waits on another; kept for the ABI) */
+    int32_t timeout;          /* a bounded device wait gave up: an mbarrier wait of the
+                                 tensor-core residual (KBL_TUNE_RHS_TC) that ran out */
     int64_t limited_elements; /* element-stages with alpha_min < 1 (Eq. 39) */
     int64_t pressure_relimits;/* element-stages where the step of Eq. 48 was taken */
     int64_t eps_rule_activations; /* (element, component) pairs where the epsilon rule stated
@@ -277,12 +277,16 @@ int64_t kbl_launch_count(const kbl_ctx* ctx);
  * bounds thread tile for grids of 32 or 64 points per axis: 0 = 4 x 4 velocity
  * nodes per thread, 1 = 4 x 2, 2 = 2 x 4.  Setting a knob drops the captured
  * step graph. */
-typedef enum { KBL_TUNE_BOUNDS_TILE = 0, KBL_TUNE_RHS_TC = 1 } kbl_tune_key;
+typedef enum { KBL_TUNE_BOUNDS_TILE = 0, KBL_TUNE_RHS_TC = 1, KBL_TUNE_RHS_OVERLAP = 2 } kbl_tune_key;
 /* KBL_TUNE_RHS_TC: 1 runs the FP32-mixed 2D residual of orders 2 and 3 with its operator
  * product (operator 7 of kbl_get_operator) on the tensor cores (tcgen05, TF32 split into
  * hi + lo pairs, FP32 accumulation; element tiles staged by TMA), 0 on the CUDA cores.  Other
  * orders, 1D and FP64 always use the CUDA cores.  Default 0 (CUDA cores: measured faster on the
  * benchmark workloads).  Setting it drops the captured step graph. */
+/* KBL_TUNE_RHS_OVERLAP: 1 (default) the step graph runs each stage's residual on a branch of its
+ * own beside the stage's bounds (both read only the stage input and its traces; the stage
+ * kernel waits for both), 0 one after the other.  The same kernels run either way: results are
+ * identical.  Setting it drops the captured step graph. */
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);   /* KBL_EINVAL for an unknown key or value */
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 

@@ -226,7 +226,12 @@ cudaError_t dalloc(T** p, size_t count)
 // Issue one full SSP-RK3 step on stream s (for capture): the traces and the clipped time step of w
 // in one kernel, then per stage the bounds, the residual and the stage + limiter kernel, which also
 // writes the next stage's traces (stages 0 and 1) or advances the clock (stage 2): 10 kernels.
-int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s)
+// The kernels of one step, for capture into the step graph.  With a side stream s2 and its
+// events, each stage's residual runs on a branch of its own beside the bounds (both read only
+// the stage input and its traces): the residual is latency-bound and fills issue slots the
+// ALU-bound bounds kernel leaves, instead of running after it.
+int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s, cudaStream_t s2 = nullptr,
+               cudaEvent_t* ev = nullptr)
 {
     int n = 0, r;
     if ((r = launch_traces_dt(c, w, c->d_wf, cfl, s)) < 0) return -1;
@@ -235,10 +240,21 @@ int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s)
     const double* ws = w;
     double* outs[3] = {c->d_wa, c->d_wb, w};
     for (int st = 0; st < 3; st++) {
-        if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
-        n += r;
-        if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
-        n += r;
+        if (s2) {
+            if (cudaEventRecord(ev[2 * st], s) != cudaSuccess || cudaStreamWaitEvent(s2, ev[2 * st], 0) != cudaSuccess)
+                return -1;
+            if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s2)) < 0) return -1;
+            n += r;
+            if (cudaEventRecord(ev[2 * st + 1], s2) != cudaSuccess) return -1;
+            if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
+            n += r;
+            if (cudaStreamWaitEvent(s, ev[2 * st + 1], 0) != cudaSuccess) return -1;
+        } else {
+            if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
+            n += r;
+            if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
+            n += r;
+        }
         if ((r = launch_stage_step(c, st, wn, ws, c->d_R, c->d_bnd, outs[st], st < 2 ? c->d_wf : nullptr, st == 2, s)) <
             0)
             return -1;
@@ -610,18 +626,36 @@ kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
         c->graph2_kernels = c->graph_kernels;
         c->graph = nullptr;
         c->graph_w = nullptr;
-        cudaStream_t cap;
+        cudaStream_t cap = nullptr, side = nullptr;
+        cudaEvent_t ev[6] = {};
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+        // the residual's branch at the highest priority: its blocks are placed as soon as the
+        // bounds kernel's blocks retire, instead of after all of them
+        int prio_lo = 0, prio_hi = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+        if (e == cudaSuccess && c->overlap_rhs)
+            e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_hi);
+        for (int k = 0; k < 6 && e == cudaSuccess && side; k++)
+            e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        auto release = [&]() {
+            for (int k = 0; k < 6; k++)
+                if (ev[k]) cudaEventDestroy(ev[k]);
+            if (side) cudaStreamDestroy(side);
+            if (cap) cudaStreamDestroy(cap);
+        };
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(c, e, "capture stream");
+        }
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
-            cudaStreamDestroy(cap);
+            release();
             return cuda_fail(c, e, "begin capture");
         }
-        const int n = issue_step(c, w, cfl, cap);
+        const int n = issue_step(c, w, cfl, cap, side, ev);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap, &g);
-        cudaStreamDestroy(cap);
+        release();
         if (n < 0) {
             if (g) cudaGraphDestroy(g);
             return fail(c, KBL_EINVAL, "order/dimension not compiled in");
@@ -743,6 +777,11 @@ kbl_status kbl_set_tuning(kbl_ctx* c, int key, int value)
         drop_graphs(c);
         return KBL_OK;
     }
+    if (key == KBL_TUNE_RHS_OVERLAP && (value == 0 || value == 1)) {
+        c->overlap_rhs = value;
+        drop_graphs(c);
+        return KBL_OK;
+    }
     if (key != KBL_TUNE_BOUNDS_TILE || value < 0 || value > 2) return fail(c, KBL_EINVAL, "unknown tuning knob or value");
     c->bounds_tile = value;
     drop_graphs(c);
@@ -754,6 +793,7 @@ kbl_status kbl_get_tuning(const kbl_ctx* c, int key, int* value)
     if (!c || !value) return KBL_EINVAL;
     if (key == KBL_TUNE_BOUNDS_TILE) *value = c->bounds_tile;
     else if (key == KBL_TUNE_RHS_TC) *value = c->rhs_tc;
+    else if (key == KBL_TUNE_RHS_OVERLAP) *value = c->overlap_rhs;
     else return KBL_EINVAL;
     return KBL_OK;
 }

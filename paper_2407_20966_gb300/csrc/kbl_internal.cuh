@@ -237,6 +237,7 @@ struct kbl_ctx {
     double* d_qw = nullptr;     // velocity quadrature weights (Romberg), or nullptr
     float* d_tcop = nullptr;    // split residual operator of the tensor-core residual, or nullptr
     int rhs_tc = 0;             // knob: 1 residual products on the tensor cores where covered, 0 CUDA cores
+    int overlap_rhs = 1;        // knob: 1 each stage's residual on a graph branch beside its bounds
     std::string err;
     int64_t launches = 0;
     int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes
@@ -308,12 +309,20 @@ int launch_stage(const kbl_ctx* c, int mode, int stage, const double* wn, const 
 // ---- device helpers ----------------------------------------------------------
 #define KBL_PI 3.14159265358979323846
 
+// a / b: the IEEE division in FP64; in FP32 a times the special-function unit's reciprocal
+// (about 1 ulp; the same reciprocal of a density is formed once and shared by every use), which
+// keeps the FP32 residual off the multi-instruction IEEE division.
+template <typename T>
+__device__ __forceinline__ T kbl_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float kbl_div<float>(float a, float b) { return a * __fdividef(1.0f, b); }
+
 template <int DIM, typename T = double>
 __device__ __forceinline__ T kbl_pressure(const T* q, T gm1)
 {
     T mm = q[1] * q[1];
     if (DIM == 2) mm += q[2] * q[2];
-    return gm1 * (q[DIM + 1] - T(0.5) * mm / q[0]);
+    return gm1 * (q[DIM + 1] - kbl_div(T(0.5) * mm, q[0]));
 }
 
 // Flux along axis `dir` (Eq. 2).
@@ -321,7 +330,7 @@ template <int DIM, typename T = double>
 __device__ __forceinline__ void kbl_flux(const T* q, int dir, T gm1, T* F)
 {
     const T P = kbl_pressure<DIM, T>(q, gm1);
-    const T u = q[1 + dir] / q[0];
+    const T u = kbl_div(q[1 + dir], q[0]);
     F[0] = q[1 + dir];
     F[1] = q[1] * u + (dir == 0 ? P : T(0));
     if (DIM == 2) F[2] = q[2] * u + (dir == 1 ? P : T(0));
@@ -338,8 +347,8 @@ __device__ __forceinline__ void kbl_rusanov(const T* ql, const T* qr, int dir, T
     kbl_flux<DIM, T>(ql, dir, gm1, Fl);
     kbl_flux<DIM, T>(qr, dir, gm1, Fr);
     const T Pl = kbl_pressure<DIM, T>(ql, gm1), Pr = kbl_pressure<DIM, T>(qr, gm1);
-    const T sl = fabs(ql[1 + dir] / ql[0]) + sqrt(gamma * Pl / ql[0]);
-    const T sr = fabs(qr[1 + dir] / qr[0]) + sqrt(gamma * Pr / qr[0]);
+    const T sl = fabs(kbl_div(ql[1 + dir], ql[0])) + sqrt(kbl_div(gamma * Pl, ql[0]));
+    const T sr = fabs(kbl_div(qr[1 + dir], qr[0])) + sqrt(kbl_div(gamma * Pr, qr[0]));
     const T lam = fmax(sl, sr);
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] = T(0.5) * (Fl[v] + Fr[v]) - T(0.5) * lam * (qr[v] - ql[v]);
@@ -357,11 +366,11 @@ __device__ __forceinline__ void kbl_hllc(const T* ql, const T* qr, int dir, T ga
     constexpr int NV = DIM + 2;
     const T gm1 = gamma - T(1);
     const T Pl = kbl_pressure<DIM, T>(ql, gm1), Pr = kbl_pressure<DIM, T>(qr, gm1);
-    const T Ul = ql[1 + dir] / ql[0], Ur = qr[1 + dir] / qr[0];
-    const T cl = sqrt(gamma * Pl / ql[0]), cr = sqrt(gamma * Pr / qr[0]);
+    const T Ul = kbl_div(ql[1 + dir], ql[0]), Ur = kbl_div(qr[1 + dir], qr[0]);
+    const T cl = sqrt(kbl_div(gamma * Pl, ql[0])), cr = sqrt(kbl_div(gamma * Pr, qr[0]));
     const T Sl = fmin(Ul - cl, Ur - cr), Sr = fmax(Ul + cl, Ur + cr);
-    const T Ss = (Pr - Pl + ql[0] * Ul * (Sl - Ul) - qr[0] * Ur * (Sr - Ur)) /
-                 (ql[0] * (Sl - Ul) - qr[0] * (Sr - Ur));
+    const T Ss = kbl_div(Pr - Pl + ql[0] * Ul * (Sl - Ul) - qr[0] * Ur * (Sr - Ur),
+                         ql[0] * (Sl - Ul) - qr[0] * (Sr - Ur));
     if (T(0) <= Sl) {
         kbl_flux<DIM, T>(ql, dir, gm1, F);
         return;
@@ -374,12 +383,12 @@ __device__ __forceinline__ void kbl_hllc(const T* ql, const T* qr, int dir, T ga
     const T* q = left ? ql : qr;
     const T S = left ? Sl : Sr, U = left ? Ul : Ur, P = left ? Pl : Pr;
     kbl_flux<DIM, T>(q, dir, gm1, F);
-    const T f = q[0] * (S - U) / (S - Ss);
+    const T f = kbl_div(q[0] * (S - U), S - Ss);
     T qs[NV];
     qs[0] = f;
 #pragma unroll
-    for (int k = 0; k < DIM; k++) qs[1 + k] = f * (k == dir ? Ss : q[1 + k] / q[0]);
-    qs[DIM + 1] = f * (q[DIM + 1] / q[0] + (Ss - U) * (Ss + P / (q[0] * (S - U))));
+    for (int k = 0; k < DIM; k++) qs[1 + k] = f * (k == dir ? Ss : kbl_div(q[1 + k], q[0]));
+    qs[DIM + 1] = f * (kbl_div(q[DIM + 1], q[0]) + (Ss - U) * (Ss + kbl_div(P, q[0] * (S - U))));
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] += S * (qs[v] - q[v]);
 }
@@ -393,8 +402,8 @@ __device__ __forceinline__ void kbl_hll(const T* ql, const T* qr, int dir, T gam
     constexpr int NV = DIM + 2;
     const T gm1 = gamma - T(1);
     const T Pl = kbl_pressure<DIM, T>(ql, gm1), Pr = kbl_pressure<DIM, T>(qr, gm1);
-    const T Ul = ql[1 + dir] / ql[0], Ur = qr[1 + dir] / qr[0];
-    const T cl = sqrt(gamma * Pl / ql[0]), cr = sqrt(gamma * Pr / qr[0]);
+    const T Ul = kbl_div(ql[1 + dir], ql[0]), Ur = kbl_div(qr[1 + dir], qr[0]);
+    const T cl = sqrt(kbl_div(gamma * Pl, ql[0])), cr = sqrt(kbl_div(gamma * Pr, qr[0]));
     const T Sl = fmin(Ul - cl, Ur - cr), Sr = fmax(Ul + cl, Ur + cr);
     if (T(0) <= Sl) {
         kbl_flux<DIM, T>(ql, dir, gm1, F);
@@ -407,7 +416,7 @@ __device__ __forceinline__ void kbl_hll(const T* ql, const T* qr, int dir, T gam
     T Fr[NV];
     kbl_flux<DIM, T>(ql, dir, gm1, F);
     kbl_flux<DIM, T>(qr, dir, gm1, Fr);
-    const T inv = T(1) / (Sr - Sl);
+    const T inv = kbl_div(T(1), Sr - Sl);
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] = (Sr * F[v] - Sl * Fr[v] + Sl * Sr * (qr[v] - ql[v])) * inv;
 }

@@ -482,6 +482,10 @@ struct kbl_tri {
     double* d_bc = nullptr;
     double *d_wf = nullptr, *d_bnd = nullptr, *d_R = nullptr, *d_wa = nullptr, *d_wb = nullptr;
     unsigned long long* d_bits = nullptr;
+    // the residual's branch: it runs beside the bounds of the same stage (both read only the
+    // stage input and its traces)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 };
 
@@ -531,6 +535,9 @@ kbl_status kbl_tri_destroy(kbl_tri* t)
     void* ptrs[] = {t->d_geo, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_wf, t->d_bnd, t->d_R, t->d_wa, t->d_wb, t->d_bits};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    if (t->ev_join) cudaEventDestroy(t->ev_join);
+    if (t->side) cudaStreamDestroy(t->side);
     if (t->ctx) kbl_destroy(t->ctx);
     delete t;
     return KBL_OK;
@@ -604,6 +611,11 @@ kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, cons
     A((void**)&t->d_wa, E * ns * 4 * sizeof(double));
     A((void**)&t->d_wb, E * ns * 4 * sizeof(double));
     A((void**)&t->d_bits, sizeof(unsigned long long));
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, prio_hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(t->d_geo, geo.data(), E * sizeof(TriGeo), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_elem > 0) e = cudaMemcpy(t->d_nbr, nbr, (size_t)n_elem * 3 * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_elem > 0)
@@ -676,7 +688,7 @@ kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host)
 
 // One SSP-RK3 step with a given dt: per stage the kinetic bounds of every stencil of the stage
 // input (gathered inside the bounds kernel from the state and its traces; the configured
-// precision and quadrature), the residual, the combination, the traces of the combined state
+// precision and quadrature), the residual (on a side stream, beside the bounds), the combination, the traces of the combined state
 // and the node-set limiter (the mean weights = the Williams-Shunn weights), which also writes the
 // limited face values: the traces of the next stage's input.
 kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
@@ -690,10 +702,22 @@ kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
     kbl_status st;
     if ((st = kbl_tri_traces(t, w, t->d_wf)) != KBL_OK) return st;
     for (int s = 0; s < 3; s++) {
+        // the residual on the side stream, beside the bounds; the combination waits for both
+        cudaError_t ce = cudaEventRecord(t->ev_fork, t->stream);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(t->side, t->ev_fork, 0);
+        if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
+        cudaStream_t own = t->stream;
+        t->stream = t->side;
+        st = kbl_tri_residual(t, ws, t->d_wf, t->d_R);
+        t->stream = own;
+        if (st != KBL_OK) return st;
+        ce = cudaEventRecord(t->ev_join, t->side);
+        if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
         if (launch_bounds_tri(t->ctx, t->E, t->cfg.p, ws, t->d_wf, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_bnd,
                               t->stream) < 0)
             return tfail(t, KBL_EINVAL, "bounds of this order not compiled in");
-        if ((st = kbl_tri_residual(t, ws, t->d_wf, t->d_R)) != KBL_OK) return st;
+        ce = cudaStreamWaitEvent(t->stream, t->ev_join, 0);
+        if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
         k_tri_combine<<<blocks_for(N, 256), 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], N);
         if ((st = kbl_tri_traces(t, outs[s], t->d_wf)) != KBL_OK) return st;
         launch_limit_nodes(t->ctx, t->E, ns, nfp, t->ops.wq, outs[s], t->d_wf, t->d_bnd, nullptr, t->stream,

@@ -126,6 +126,7 @@ _SIGS = {
 
 TUNE_BOUNDS_TILE = 0
 TUNE_RHS_TC = 1
+TUNE_RHS_OVERLAP = 2
 
 
 def exported_symbols():

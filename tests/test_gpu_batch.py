@@ -173,7 +173,7 @@ def test_batch_autotune_keeps_results(orc):
     ms, cmp = b.autotune(torch.from_numpy(w0).cuda(), with_cmp=True)
     assert cmp > 0
     t = b.tuning()
-    assert ms > 0 and t["tile"] in (0, 1) and t["elements_per_item"] in (4, 16, 64) and t["blocks_per_sm"] >= 1
+    assert ms > 0 and t["tile"] in (0, 1, 2) and t["elements_per_item"] in (4, 16, 64) and t["blocks_per_sm"] >= 1
     wd2 = torch.from_numpy(w0).cuda()
     b.step(wd2, 0.2)
     b.check()

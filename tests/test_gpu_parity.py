@@ -512,3 +512,24 @@ def test_run_host_ensemble_matches_device_steps(orc):
     ctx.run_host_ensemble(inout, inout, 2, 0.1)
     np.testing.assert_array_equal(inout, ref)
     ctx.check()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_residual_branch_is_bitwise_serial(orc, precision):
+    """The step graph with each stage's residual on a branch beside its bounds (the default)
+    gives the serial graph's state bit for bit: the same kernels read the same inputs."""
+    from paper_2407_20966_gb300 import kbl
+    ctx, _ = both(orc, 2, 3, (32, 32), precision=precision)
+    mesh, w = mesh_and_field(orc, 2, 3, (13, 11), seed=21, kind="disc", periodic=True)
+    upload(ctx, orc, mesh)
+    out = []
+    for ov in (1, 0):
+        ctx.set_tuning(kbl.TUNE_RHS_OVERLAP, ov)
+        assert ctx.get_tuning(kbl.TUNE_RHS_OVERLAP) == ov
+        wd = to_dev(w)
+        ctx.set_time(0.0)
+        for _ in range(3):
+            ctx.step(wd, 0.05)
+        ctx.check()
+        out.append(wd.cpu().numpy())
+    np.testing.assert_array_equal(out[0], out[1])
