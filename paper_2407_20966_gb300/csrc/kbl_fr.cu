@@ -103,8 +103,13 @@ struct RhsShape {
     static constexpr int NT = EPB * NS;
 };
 
+#ifdef KBL_RHS_MINB
+#define KBL_RHS_BOUNDS(...) __launch_bounds__(__VA_ARGS__, KBL_RHS_MINB)
+#else
+#define KBL_RHS_BOUNDS(...) __launch_bounds__(__VA_ARGS__)
+#endif
 template <int DIM, int N, typename T>
-__global__ void __launch_bounds__(RhsShape<DIM, N>::NT)
+__global__ void KBL_RHS_BOUNDS(RhsShape<DIM, N>::NT)
 k_rhs(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, FrOps ops,
       double gamma_d, double* __restrict__ R, int flux)
 {

@@ -42,8 +42,13 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
 
 // The stage kernel of kbl_step: the stage and limiter, then (wf_next) the next stage's face traces
 // from the limited state still in shared memory, or (advance) the clock of the step.
+#ifdef KBL_STAGE_MINB
+#define KBL_STAGE_BOUNDS(...) __launch_bounds__(__VA_ARGS__, KBL_STAGE_MINB)
+#else
+#define KBL_STAGE_BOUNDS(...) __launch_bounds__(__VA_ARGS__)
+#endif
 template <int DIM, int N>
-__global__ void __launch_bounds__(LimShape<DIM, N>::NT)
+__global__ void KBL_STAGE_BOUNDS(LimShape<DIM, N>::NT)
 k_stage_limit_step(int stage, const double* wn, const double* ws, const double* __restrict__ R,
                    const double* __restrict__ bnd, double* scal, double* wout, double* __restrict__ wf_next,
                    int advance, int E, FrOps ops, Phys ph, DevFlags* flags)
