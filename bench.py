@@ -615,24 +615,13 @@ def run_sub_mesh(args, name, steps, warmup, dev):
             "clocks": clk.summary()}
 
 
-def _tri_blast(x, y, gamma=1.4):
-    """Smoothed circular blast (tanh front about 2.5 cells wide at 256^2) with a weak shear, on [0,1]^2."""
-    import numpy as np
-    s = 0.5 * (1 - np.tanh((np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2) - 0.25) / 0.01))
-    rho = 0.125 + 0.875 * s
-    P = 0.1 + 0.9 * s
-    u = 0.2 * np.sin(2 * np.pi * y)
-    v = -0.2 * np.sin(2 * np.pi * x)
-    return np.stack([rho, rho * u, rho * v, P / (gamma - 1) + 0.5 * rho * (u * u + v * v)])
-
-
 def run_triangles(args, steps, warmup, dev):
     """Affine triangles (Sec. 5: Williams-Shunn P2 solution points, 3 Gauss-Legendre points per
     edge): 2 x 256 x 256 jittered periodic triangles on [0,1]^2, 32 x 32 velocity grid, FP32-mixed
     bounds, FP64 residual and limiter, HLLC, fixed dt at CFL 0.05.  One step is kbl_tri_step:
     per stage traces, stencils, bounds of the 24-state stencils, residual, combination, traces,
     node-set limiter.  Timed like the headline (L2 flushed between steps); the roofline is the
-    explicit-stencil bounds launch over the whole mesh, timed alone with CUDA events."""
+    step's bounds launch (kbl_tri_bounds) over the whole mesh, timed alone with CUDA events."""
     import numpy as np
     import torch
     from paper_2407_20966_gb300 import inputs, kbl
@@ -640,7 +629,7 @@ def run_triangles(args, steps, warmup, dev):
     E = m.n_elem
     tm = kbl.TriMesh(2, m.xy, m.nbr, m.nbr_edge, m.bc, precision=kbl.FP32_MIXED, flux=1, nu=(32, 32))
     rs, _ = kbl.tri_points(2)
-    w0 = inputs.tri_nodal_field(m, rs, _tri_blast)
+    w0 = inputs.tri_nodal_field(m, rs, inputs.tri_blast)
     wd = torch.from_numpy(w0).to(dev)
     dt = tm.dt(wd, 0.05)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -658,26 +647,22 @@ def run_triangles(args, steps, warmup, dev):
         torch.cuda.synchronize()
     tm.check()
     ms = sum(a.elapsed_time(z) for a, z in evs)
-    # dominant kernel: bounds of the gathered stencils over the whole mesh
+    # dominant kernel: the step's bounds launch (stencils gathered in the kernel) over the whole mesh
     wf = torch.zeros(E, tm.nfp, 4, dtype=torch.float64, device=dev)
-    S = torch.zeros(E, tm.nstencil, 4, dtype=torch.float64, device=dev)
     bnd = torch.zeros(2, 4, E, dtype=torch.float64, device=dev)
     tm.traces(wd, wf)
-    tm.gather_stencil(wd, wf, S)
-    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=kbl.FP32_MIXED)
-    ctx.bounds_stencil(S, bnd)
+    tm.bounds(wd, wf, bnd)
     bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
     for a, z in bev:
         flush.zero_()
         a.record(stream)
-        ctx.bounds_stencil(S, bnd)
+        tm.bounds(wd, wf, bnd)
         z.record(stream)
     torch.cuda.synchronize()
-    ctx.check()
+    tm.check()
     bounds_ms = sum(a.elapsed_time(z) for a, z in bev) / len(bev)
     achieved = OPS_PER_STATE_NODE * tm.nstencil * 32 * 32 * E / (bounds_ms * 1e-3) / 1e12
     peak = LANE_OPS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12
-    ctx.close()
     # end to end: pinned host state in, one step, pinned host state out
     w_pin = torch.from_numpy(w0).pin_memory()
     out_pin = torch.empty_like(w_pin).pin_memory()
@@ -700,7 +685,7 @@ def run_triangles(args, steps, warmup, dev):
                     "call": "pinned host copy in, kbl_tri_step, pinned host copy out"},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                          "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "kernel": "k_bounds_stencil_f32", "bounds_ms_per_launch": round(bounds_ms, 4),
+                         "kernel": "k_bounds_tri_f32", "bounds_ms_per_launch": round(bounds_ms, 4),
                          "work": "6 lane-ops per (stencil state, velocity node), 24 states per element",
                          "peak_source": PEAK_SOURCE},
             "clocks": clk.summary()}

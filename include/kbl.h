@@ -540,6 +540,12 @@ kbl_status kbl_tri_traces(kbl_tri* t, const double* w, double* wf);
 /* Stencils of Sec. 5 for every element, from w and its traces wf. */
 kbl_status kbl_tri_gather_stencil(kbl_tri* t, const double* w, const double* wf, double* S);
 
+/* Kinetic bounds bnd[2][4][E] (the layout of kbl_bounds) of every element's stencil, gathered
+ * inside the bounds kernel from w and its traces wf: equal bit for bit to
+ * kbl_tri_gather_stencil followed by kbl_bounds_stencil with the mesh's configuration, without
+ * the stencil array.  The bounds of kbl_tri_step. */
+kbl_status kbl_tri_bounds(kbl_tri* t, const double* w, const double* wf, double* bnd);
+
 /* Residual R[E][ns][4] = -div F_h - sum_q lift (F*_n - F_h . n): the
  * interpolated flux's divergence and the DG lifting of the flux-point jumps, with
  * the configured common flux of the states rotated into each edge's normal frame.
@@ -551,9 +557,8 @@ kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, doubl
 kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host);
 
 /* One SSP-RK3 step of w (in place) with the given dt: per stage the kinetic
- * bounds of the stencils of the stage input (the stencils of kbl_tri_gather_stencil,
- * gathered inside the bounds kernel; the bounds of kbl_bounds_stencil with the
- * mesh's configuration), the residual, the Shu-Osher combination, the traces of
+ * bounds of the stencils of the stage input (kbl_tri_bounds), the residual (on a
+ * second stream, beside the bounds), the Shu-Osher combination, the traces of
  * the combined state and the node-set limiter (kbl_limit_nodes with the solution
  * points' weights), whose limited face values are the next stage's traces.
  * Non-physical states raise the flag kbl_tri_check reports. */

@@ -419,3 +419,16 @@ def tri_nodal_field(mesh, rs, ic):
     y = X0[:, None, 1] + rs[None, :, 0] * J1[:, None, 1] + rs[None, :, 1] * J2[:, None, 1]
     q = np.asarray(ic(x, y), dtype=np.float64)          # [4][E][ns]
     return np.ascontiguousarray(np.moveaxis(q, 0, -1))  # [E][ns][4]
+
+
+def tri_blast(x, y, gamma=1.4):
+    """Smoothed circular blast on [0,1]^2 with a weak shear: density 1 / 0.125 and pressure 1 / 0.1
+    inside / outside radius 0.25 about (0.5, 0.5), joined by a tanh front of width 0.01 (about 2.5
+    cells of a 256^2 mesh), velocity (0.2 sin 2 pi y, -0.2 sin 2 pi x).  Conservative state
+    (4, ...)."""
+    s = 0.5 * (1 - np.tanh((np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2) - 0.25) / 0.01))
+    rho = 0.125 + 0.875 * s
+    P = 0.1 + 0.9 * s
+    u = 0.2 * np.sin(2 * np.pi * y)
+    v = -0.2 * np.sin(2 * np.pi * x)
+    return np.stack([rho, rho * u, rho * v, P / (gamma - 1) + 0.5 * rho * (u * u + v * v)])

@@ -119,6 +119,7 @@ _SIGS = {
     "kbl_tri_traces": (C.c_int, [_P, _P, _P]),
     "kbl_tri_gather_stencil": (C.c_int, [_P, _P, _P, _P]),
     "kbl_tri_residual": (C.c_int, [_P, _P, _P, _P]),
+    "kbl_tri_bounds": (C.c_int, [_P, _P, _P, _P]),
     "kbl_tri_dt": (C.c_int, [_P, _P, C.c_double, C.POINTER(C.c_double)]),
     "kbl_tri_step": (C.c_int, [_P, _P, C.c_double]),
     "kbl_tri_check": (C.c_int, [_P]),
@@ -609,6 +610,10 @@ class TriMesh:
     def gather_stencil(self, w, wf, S):
         self._check(self._lib.kbl_tri_gather_stencil(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(S, "S")),
                     "tri_gather_stencil")
+
+    def bounds(self, w, wf, bnd):
+        """Bounds [2][4][E] of every stencil, gathered inside the kernel (kbl_tri_bounds)."""
+        self._check(self._lib.kbl_tri_bounds(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(bnd, "bnd")), "tri_bounds")
 
     def residual(self, w, wf, R):
         self._check(self._lib.kbl_tri_residual(self._h, _dev(w, "w"), _dev(wf, "wf"), _dev(R, "R")),

@@ -228,3 +228,88 @@ def test_empty_and_invalid_meshes(orc):
     nb[0, 0] = m.n_elem                 # out of range
     with pytest.raises(kbl.KblError):
         kbl.TriMesh(1, m.xy, nb, m.nbr_edge, m.bc)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("p,periodic", [(1, False), (2, True), (2, False)])
+def test_fused_bounds_equal_gathered_stencil_bounds(orc, p, periodic, precision):
+    """kbl_tri_bounds (stencils gathered inside the bounds kernel, the step's bounds) equals
+    kbl_tri_gather_stencil + kbl_bounds_stencil bit for bit."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    m, om, cfg, tm, w = _setup(orc, p, 11, 13, periodic, precision=precision)
+    E = m.n_elem
+    wd = _dev(w)
+    wf = torch.zeros(E, tm.nfp, 4, dtype=torch.float64, device="cuda")
+    tm.traces(wd, wf)
+    fused = torch.zeros(2, 4, E, dtype=torch.float64, device="cuda")
+    tm.bounds(wd, wf, fused)
+    S = torch.zeros(E, tm.nstencil, 4, dtype=torch.float64, device="cuda")
+    tm.gather_stencil(wd, wf, S)
+    ctx = kbl.Context(dim=2, p=p, nu=(16, 16), precision=precision)
+    ref = torch.zeros_like(fused)
+    ctx.bounds_stencil(S, ref)
+    tm.check()
+    ctx.check()
+    assert torch.equal(fused, ref)
+
+
+def test_full_size_workload_per_call(orc):
+    """The benchmark's triangle workload at full size (2 x 256^2 jittered periodic P2 triangles,
+    32 x 32 grid, FP32-mixed, HLLC), each call of a stage on the checker's inputs: traces of the
+    whole mesh (1e-14), residual of the whole mesh (1e-5 of the term scale), bounds of 192
+    sampled elements (1e-5) and the node-set limiter of the whole mesh with the device's bounds
+    against the checker's limiter on 192 sampled elements (1e-12: FP64)."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    m = inputs.tri_mesh_2d(256, 256, 0.0, 1.0, 0.0, 1.0, jitter=0.2, seed=17)
+    E = m.n_elem
+    om = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc)
+    cfg = orc.Config(dim=2, p=2, nu=(32, 32), flux=1)
+    tm = kbl.TriMesh(2, m.xy, m.nbr, m.nbr_edge, m.bc, precision=kbl.FP32_MIXED, flux=1, nu=(32, 32))
+    rs, wq = orc.tri_points(2)
+    w = inputs.tri_nodal_field(m, rs, inputs.tri_blast)
+    wd = _dev(w)
+    wf_d = torch.zeros(E, tm.nfp, 4, dtype=torch.float64, device="cuda")
+    tm.traces(wd, wf_d)
+    wf_ref = orc.tri_traces(cfg, om, w)
+    assert (np.abs(wf_d.cpu().numpy() - wf_ref) / _elem_scale(wf_ref)).max() < 1e-14
+    wf_in = _dev(wf_ref)
+    R_d = torch.zeros_like(wd)
+    tm.residual(wd, wf_in, R_d)
+    S_d = torch.zeros(E, tm.nstencil, 4, dtype=torch.float64, device="cuda")
+    tm.gather_stencil(wd, wf_in, S_d)
+    S = S_d.cpu().numpy()
+    R_ref = orc.tri_rhs(cfg, om, w, wf_ref)
+    err = np.abs(R_d.cpu().numpy() - R_ref) / np.maximum(np.abs(R_ref), _residual_scale(m, w, S))
+    assert err.max() < TOL_FP32, err.max()
+    bnd = torch.zeros(2, 4, E, dtype=torch.float64, device="cuda")
+    tm.bounds(wd, wf_in, bnd)
+    tm.check()
+    bnd_h = bnd.cpu().numpy()
+    sample = np.random.default_rng(3).choice(E, 192, replace=False)
+    ref = np.zeros((2, 4, len(sample)))
+    for k, e in enumerate(sample):
+        ref[0, :, k], ref[1, :, k] = orc.bounds_stencil(cfg, S[e])
+    assert bounds_error(bnd_h[:, :, sample], ref).max() < TOL_FP32
+    # limiter of a perturbed state (zero weighted mean per element) against the device's bounds
+    d = np.sin(3.0 * np.arange(len(wq)))
+    d = d - (wq * d).sum() / wq.sum()
+    amp = np.abs(w).max(axis=1, keepdims=True)
+    wp = np.ascontiguousarray(w + 0.05 * amp * d[None, :, None])
+    wfp = orc.tri_traces(cfg, om, wp)
+    ctx = kbl.Context(dim=2, p=2, nu=(32, 32), precision=kbl.FP32_MIXED)
+    U = _dev(wp)
+    alpha = torch.zeros(2, E, dtype=torch.float64, device="cuda")
+    ctx.limit_nodes(wq, U, _dev(wfp), bnd, alpha)
+    ctx.check()
+    U_h, a_h = U.cpu().numpy(), alpha.cpu().numpy()
+    limited = 0
+    for e in sample:
+        lim, a = orc.limit_nodes(cfg, wq, np.ascontiguousarray(wp[e].T), np.ascontiguousarray(wfp[e].T),
+                                 bnd_h[0, :, e], bnd_h[1, :, e])
+        limited += a[0] < 1
+        err = np.abs(U_h[e].T - lim) / _elem_scale(lim.T[None])[0].T
+        assert err.max() < TOL_FP64, (e, err.max())
+        assert abs(a_h[0, e] - a[0]) < 1e-12 and abs(a_h[1, e] - a[1]) < 1e-12
+    assert limited > 0
