@@ -435,14 +435,34 @@ __global__ void __launch_bounds__(128) k_tri_rhs(const double* __restrict__ w, c
         for (int v = 0; v < 4; v++) R[((size_t)e * ns + i) * 4 + v] = kbl_dev::to_f64<T>(out[i][v]);
 }
 
-// SSP-RK3 combination (Shu-Osher form), element-wise.
-__global__ void k_tri_combine(int s, const double* __restrict__ wn, const double* ws, const double* __restrict__ R,
-                              double dt, double* wout, size_t n)
+// SSP-RK3 combination (Shu-Osher form) and the traces of its result (k_tri_traces' arithmetic,
+// in its order) in one pass: a block combines the values of 32 elements, keeps them in shared
+// memory and interpolates them to the flux points.
+template <int P>
+__global__ void __launch_bounds__(256) k_tri_combine_traces(int s, const double* __restrict__ wn, const double* ws,
+                                                           const double* __restrict__ R, double dt, double* wout,
+                                                           double* __restrict__ wf, int E, TriOps o)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const double v = ws[t] + dt * R[t];
-    wout[t] = s == 0 ? v : (s == 1 ? 0.75 * wn[t] + 0.25 * v : (1.0 / 3.0) * wn[t] + (2.0 / 3.0) * v);
+    constexpr int ns = (P + 1) * (P + 2) / 2, nfp = 3 * (P + 1), EPB = 32;
+    __shared__ double sw[EPB * ns * 4];
+    const int e0 = blockIdx.x * EPB;
+    const int ne = min(EPB, E - e0);
+    const size_t base = (size_t)e0 * ns * 4;
+    for (int i = threadIdx.x; i < ne * ns * 4; i += blockDim.x) {
+        const size_t t = base + i;
+        const double v = ws[t] + dt * R[t];
+        const double r = s == 0 ? v : (s == 1 ? 0.75 * wn[t] + 0.25 * v : (1.0 / 3.0) * wn[t] + (2.0 / 3.0) * v);
+        wout[t] = r;
+        sw[i] = r;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ne * nfp * 4; i += blockDim.x) {
+        const int el = i / (nfp * 4), rem = i - el * (nfp * 4), q = rem >> 2, v = rem & 3;
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < ns; j++) acc += o.phif[q][j] * sw[(el * ns + j) * 4 + v];
+        wf[(size_t)(e0 + el) * nfp * 4 + rem] = acc;
+    }
 }
 
 // dt bits: min over elements and solution points of h / (|U| + c) (positive doubles order as their bits).
@@ -649,6 +669,15 @@ kbl_status kbl_tri_gather_stencil(kbl_tri* t, const double* w, const double* wf,
     return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
 }
 
+kbl_status kbl_tri_bounds(kbl_tri* t, const double* w, const double* wf, double* bnd)
+{
+    if (!t || (t->E > 0 && (!w || !wf || !bnd))) return tfail(t, KBL_EINVAL, "null array");
+    if (launch_bounds_tri(t->ctx, t->E, t->cfg.p, w, wf, t->d_nbr, t->d_nbr_edge, t->d_bc, bnd, t->stream) < 0)
+        return tfail(t, KBL_EINVAL, "bounds of this order not compiled in");
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+}
+
 kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R)
 {
     if (!t || (t->E > 0 && (!w || !wf || !R))) return tfail(t, KBL_EINVAL, "null array");
@@ -696,7 +725,6 @@ kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
     if (!t || (t->E > 0 && !w) || !(dt >= 0.0)) return tfail(t, KBL_EINVAL, "bad argument");
     if (t->E == 0) return KBL_OK;
     const int ns = t->ops.ns, nfp = t->ops.nfp;
-    const size_t N = (size_t)t->E * ns * 4;
     const double* ws = w;
     double* outs[3] = {t->d_wa, t->d_wb, w};
     kbl_status st;
@@ -713,13 +741,14 @@ kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
         if (st != KBL_OK) return st;
         ce = cudaEventRecord(t->ev_join, t->side);
         if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
-        if (launch_bounds_tri(t->ctx, t->E, t->cfg.p, ws, t->d_wf, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_bnd,
-                              t->stream) < 0)
-            return tfail(t, KBL_EINVAL, "bounds of this order not compiled in");
+        if ((st = kbl_tri_bounds(t, ws, t->d_wf, t->d_bnd)) != KBL_OK) return st;
         ce = cudaStreamWaitEvent(t->stream, t->ev_join, 0);
         if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
-        k_tri_combine<<<blocks_for(N, 256), 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], N);
-        if ((st = kbl_tri_traces(t, outs[s], t->d_wf)) != KBL_OK) return st;
+        const unsigned gct = blocks_for((size_t)t->E, 32);
+        if (t->cfg.p == 1)
+            k_tri_combine_traces<1><<<gct, 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], t->d_wf, t->E, t->ops);
+        else
+            k_tri_combine_traces<2><<<gct, 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], t->d_wf, t->E, t->ops);
         launch_limit_nodes(t->ctx, t->E, ns, nfp, t->ops.wq, outs[s], t->d_wf, t->d_bnd, nullptr, t->stream,
                            t->d_wf);
         ws = outs[s];
