@@ -180,6 +180,15 @@ def max_over_ranks(ms, device=None):
     return float(t.item())
 
 
+def _barrier_world():
+    """Barrier over the process group (if any) and its size."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+        return dist.get_world_size()
+    return 1
+
+
 def job_throughput(units_per_rank, ms_max, world):
     """Whole-job units per second: every rank's units over the slowest rank's time."""
     return units_per_rank * world / (ms_max * 1e-3)
@@ -568,6 +577,7 @@ def run_sub_mesh(args, name, steps, warmup, dev):
         for _ in range(W):
             c.step(w, wl["cfl"])
         torch.cuda.synchronize()
+        _barrier_world()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for k in range(K):
             flush.zero_()
@@ -576,7 +586,7 @@ def run_sub_mesh(args, name, steps, warmup, dev):
             evs[k][1].record(stream)
         torch.cuda.synchronize()
         c.check()
-        return sum(a.elapsed_time(b) for a, b in evs)
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
 
     ctx = make_ctx(kbl.FP32_MIXED)
     w0 = inputs.nodal_field(mesh, ctx.operator(kbl.OP_NODES), wl["ic"])
@@ -604,10 +614,11 @@ def run_sub_mesh(args, name, steps, warmup, dev):
     k64 = 2
     ms64 = timed(c64, torch.from_numpy(w0).to(dev), k64, 1)
     c64.close()
-    return {"workload": wl["name"], "elements": E, "value": E * 3 * steps / (ms * 1e-3), "unit": UNIT,
+    world = _barrier_world()
+    return {"workload": wl["name"], "elements": E, "value": job_throughput(E * 3 * steps, ms, world), "unit": UNIT,
             "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "precision": "fp32",
             "l2": "flushed between timed steps (256 MB write)",
-            "fp64": {"value": E * 3 * k64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / k64},
+            "fp64": {"value": job_throughput(E * 3 * k64, ms64, world), "unit": UNIT, "ms_per_step": ms64 / k64},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                          "unit": "T FP32 lane-ops/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "kernel": "k_bounds2d_f32", "bounds_ms_per_launch": round(bounds_ms, 4),
@@ -618,9 +629,9 @@ def run_sub_mesh(args, name, steps, warmup, dev):
 def run_triangles(args, steps, warmup, dev):
     """Affine triangles (Sec. 5: Williams-Shunn P2 solution points, 3 Gauss-Legendre points per
     edge): 2 x 256 x 256 jittered periodic triangles on [0,1]^2, 32 x 32 velocity grid, FP32-mixed
-    bounds, FP64 residual and limiter, HLLC, fixed dt at CFL 0.05.  One step is kbl_tri_step:
-    per stage traces, stencils, bounds of the 24-state stencils, residual, combination, traces,
-    node-set limiter.  Timed like the headline (L2 flushed between steps); the roofline is the
+    bounds and residual, FP64 traces and limiter, HLLC, fixed dt at CFL 0.05.  One step is
+    kbl_tri_step: per stage the bounds of the 24-state stencils (gathered in the kernel), the
+    residual beside them, the combination with the traces of its result, the node-set limiter.  Timed like the headline (L2 flushed between steps); the roofline is the
     step's bounds launch (kbl_tri_bounds) over the whole mesh, timed alone with CUDA events."""
     import numpy as np
     import torch
@@ -637,6 +648,7 @@ def run_triangles(args, steps, warmup, dev):
     for _ in range(warmup):
         tm.step(wd, dt)
     torch.cuda.synchronize()
+    world = _barrier_world()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler(dev.index) as clk:
         for k in range(steps):
@@ -646,7 +658,7 @@ def run_triangles(args, steps, warmup, dev):
             evs[k][1].record(stream)
         torch.cuda.synchronize()
     tm.check()
-    ms = sum(a.elapsed_time(z) for a, z in evs)
+    ms = max_over_ranks(sum(a.elapsed_time(z) for a, z in evs), dev)
     # dominant kernel: the step's bounds launch (stencils gathered in the kernel) over the whole mesh
     wf = torch.zeros(E, tm.nfp, 4, dtype=torch.float64, device=dev)
     bnd = torch.zeros(2, 4, E, dtype=torch.float64, device=dev)
@@ -678,9 +690,10 @@ def run_triangles(args, steps, warmup, dev):
     tm.close()
     return {"workload": f"triangles: {E} periodic jittered P2 triangles (Williams-Shunn points), 32x32 velocity "
                         f"grid, FP32-mixed bounds, HLLC, smoothed blast", "elements": E,
-            "value": E * 3 * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
-            "warmup": warmup, "l2": "flushed between timed steps (256 MB write)",
-            "e2e": {"value": E * 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(w0.nbytes),
+            "value": job_throughput(E * 3 * steps, ms, world), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "warmup": warmup, "l2": "flushed between timed steps (256 MB write)",
+            "e2e": {"value": job_throughput(E * 3, max_over_ranks(e2e_s * 1e3, dev), world), "unit": UNIT,
+                    "h2d_bytes_per_step": int(w0.nbytes),
                     "d2h_bytes_per_step": int(w0.nbytes),
                     "call": "pinned host copy in, kbl_tri_step, pinned host copy out"},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),

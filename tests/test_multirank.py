@@ -21,6 +21,7 @@ def _rank_main(rank, world, port, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    assert bench._barrier_world() == world          # the sub-workloads' barrier and world size
     ms_local = 10.0 + 5.0 * rank                     # rank 1 is the slow one
     ms = bench.max_over_ranks(ms_local)
     value = bench.job_throughput(1000, ms, world)
@@ -49,4 +50,5 @@ def test_two_rank_replicas_take_the_slowest_time():
 def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(7.5) == 7.5
+    assert bench._barrier_world() == 1
     assert bench.job_throughput(300, 1.5, 1) == pytest.approx(2e5)
