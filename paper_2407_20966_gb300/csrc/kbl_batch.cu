@@ -681,7 +681,11 @@ ItemSet all_items(const kbl_batch* b)
 }
 
 // One SSP-RK3 step of the problems of `is` on stream s (also used for capture).
-int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const ItemSet& is)
+// One step of the item set as per-phase persistent launches.  With a side stream s2 and its
+// events, each stage's residual runs on a branch of its own beside the stage's bounds (both read
+// only the stage input and its traces); the stage kernel waits for both.
+int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const ItemSet& is,
+                     cudaStream_t s2 = nullptr, cudaEvent_t* ev = nullptr)
 {
     const BatchDev bd = dev_of(b);
     const int np = is.p1 - is.p0;
@@ -700,9 +704,17 @@ int issue_batch_step(kbl_batch* b, double* w, double cfl, cudaStream_t s, const 
     double* outs[3] = {b->d_wa, b->d_wb, w};
     for (int st = 0; st < 3; st++) {
         k_batch_traces<<<g_tr, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 1 + 4 * st, b->ops, ws, b->d_wf);
+        cudaStream_t sr = s;
+        if (s2) {
+            cudaEventRecord(ev[2 * st], s);
+            cudaStreamWaitEvent(s2, ev[2 * st], 0);
+            sr = s2;
+        }
+        k_batch_rhs<<<g_rhs, NTB, 0, sr>>>(bd, is.fr, is.n_fr, is.counters + 3 + 4 * st, b->ops, b->phys.gamma,
+                                           b->phys.flux, ws, b->d_wf, b->d_R);
+        if (s2) cudaEventRecord(ev[2 * st + 1], s2);
         n += launch_bounds_phase(b, ws, b->d_wf, b->d_bnd, is.counters + 2 + 4 * st, s, is.bi, is.n_bi);
-        k_batch_rhs<<<g_rhs, NTB, 0, s>>>(bd, is.fr, is.n_fr, is.counters + 3 + 4 * st, b->ops, b->phys.gamma,
-                                          b->phys.flux, ws, b->d_wf, b->d_R);
+        if (s2) cudaStreamWaitEvent(s, ev[2 * st + 1], 0);
         k_batch_stage<<<g_st, NTB, sizeof(LimUnion<>), s>>>(bd, is.fr, is.n_fr, is.counters + 4 + 4 * st, b->ops,
                                                           b->phys, st, wn, ws, b->d_R, b->d_bnd, b->d_dt, outs[st],
                                                           b->d_flags);
@@ -719,18 +731,29 @@ int issue_batch_step_fused(kbl_batch* b, double* w, double cfl, cudaStream_t s, 
 cudaError_t capture_step(kbl_batch* b, double* w, double cfl, const ItemSet& is, cudaGraphExec_t* out, int* kernels)
 {
     *out = nullptr;
-    cudaStream_t cap;
+    cudaStream_t cap = nullptr, side = nullptr;
+    cudaEvent_t ev[6] = {};
+    int prio_lo = 0, prio_hi = 0;
     cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess && !b->fused) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_hi);
+    for (int k = 0; k < 6 && e == cudaSuccess && side; k++) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    auto release = [&]() {
+        for (int k = 0; k < 6; k++)
+            if (ev[k]) cudaEventDestroy(ev[k]);
+        if (side) cudaStreamDestroy(side);
+        if (cap) cudaStreamDestroy(cap);
+    };
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
-        cudaStreamDestroy(cap);
+        release();
         return e;
     }
-    *kernels = b->fused ? issue_batch_step_fused(b, w, cfl, cap, is, is.counters) : issue_batch_step(b, w, cfl, cap, is);
+    *kernels = b->fused ? issue_batch_step_fused(b, w, cfl, cap, is, is.counters)
+                        : issue_batch_step(b, w, cfl, cap, is, side, ev);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cap, &g);
-    cudaStreamDestroy(cap);
+    release();
     if (e != cudaSuccess) return e;
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
