@@ -42,7 +42,7 @@ class _Cfg(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nu", C.c_int * 2), ("gamma", C.c_double),
                 ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
-                ("uncoupled", C.c_int), ("flux", C.c_int), ("quadrature", C.c_int)]
+                ("uncoupled", C.c_int), ("flux", C.c_int), ("quadrature", C.c_int), ("stencil", C.c_int)]
 
 
 class _Mesh(C.Structure):
@@ -126,6 +126,7 @@ class Config:
     uncoupled: int = 0
     flux: int = 0
     quadrature: int = 0
+    stencil: int = 0      # 1 (1D): own solution points and both face neighbours' solution points
 
     @property
     def nv(self):
@@ -141,13 +142,13 @@ class Config:
 
     @property
     def nstencil(self):
-        return self.ns + 2 * self.nfp
+        return 3 * self.ns if self.stencil == 1 else self.ns + 2 * self.nfp
 
     def _c(self):
         nu = list(self.nu) + [1] * (2 - len(self.nu))
         return _Cfg(self.dim, self.p, (C.c_int * 2)(*nu[:2]), self.gamma, self.k, self.r_fac,
                     self.eps, self.rho_floor, self.p_floor, self.eps_rule, self.uncoupled, self.flux,
-                    self.quadrature)
+                    self.quadrature, self.stencil)
 
 
 class Mesh:

@@ -17,7 +17,7 @@
 int orc_nv(const orc_cfg* c) { return c->dim + 2; }
 int orc_ns(const orc_cfg* c) { return c->dim == 1 ? c->p + 1 : (c->p + 1) * (c->p + 1); }
 int orc_nfp(const orc_cfg* c) { return c->dim == 1 ? 2 : 4 * (c->p + 1); }
-int orc_nstencil(const orc_cfg* c) { return orc_ns(c) + 2 * orc_nfp(c); }
+int orc_nstencil(const orc_cfg* c) { return c->stencil == 1 ? 3 * orc_ns(c) : orc_ns(c) + 2 * orc_nfp(c); }
 static int nfp_face(const orc_cfg* c) { return c->dim == 1 ? 1 : c->p + 1; }
 
 /* ===================================================================== */
@@ -511,6 +511,21 @@ void orc_gather_stencil(const orc_cfg* c, const orc_mesh* m, const double* w,
                         const double* wf, int e, double* S)
 {
     int nv = orc_nv(c), ns = orc_ns(c), nfp = orc_nfp(c), E = m->n_elem;
+    if (c->stencil == 1) {
+        /* the wider 1D stencil: own solution points, then those of the left (face 0) and the
+         * right (face 1) neighbour; a boundary face contributes its boundary state, once per
+         * point (a repeated state changes neither an envelope nor the velocity box) */
+        for (int n = 0; n < ns; n++)
+            for (int v = 0; v < nv; v++) S[n * nv + v] = w[((size_t)v * E + e) * ns + n];
+        for (int f = 0; f < 2; f++) {
+            const int nb = m->nbr[e * 2 + f];
+            for (int n = 0; n < ns; n++)
+                for (int v = 0; v < nv; v++)
+                    S[((1 + f) * ns + n) * nv + v] = nb >= 0 ? w[((size_t)v * E + nb) * ns + n]
+                                                              : m->bc[(-nb - 1) * nv + v];
+        }
+        return;
+    }
     for (int n = 0; n < ns; n++)
         for (int v = 0; v < nv; v++) S[n * nv + v] = w[((size_t)v * E + e) * ns + n];
     for (int fp = 0; fp < nfp; fp++)

@@ -54,6 +54,9 @@ typedef struct {
                          (the flux of the experiments, Sec. 5), 2 HLL (the Sedov run, Sec. 6.6) */
     int quadrature;   /* velocity quadrature: 0 trapezoidal (Sec. 3.7), 1 Romberg (named in
                          Sec. 5; needs nu - 1 even on every axis) */
+    int stencil;      /* 0: the numerical stencil of Sec. 5 (own solution and face points, the
+                         exterior face values); 1 (1D only): the element's own solution points
+                         and all solution points of both face neighbours */
 } orc_cfg;
 
 typedef struct {
@@ -68,7 +71,7 @@ typedef struct {
 int orc_nv(const orc_cfg* c);
 int orc_ns(const orc_cfg* c);        /* solution points per element */
 int orc_nfp(const orc_cfg* c);       /* face points per element */
-int orc_nstencil(const orc_cfg* c);  /* |S| = Ns + 2 Nfp */
+int orc_nstencil(const orc_cfg* c);  /* |S| = Ns + 2 Nfp (stencil 0), 3 Ns (stencil 1) */
 
 /* ---- one-dimensional polynomial tools (Sec. 2.3, Sec. 5) ------------- */
 void orc_legendre(int n, double x, double* P, double* dP);
