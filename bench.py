@@ -93,15 +93,16 @@ def workload(name):
         return dict(name="Sedov blast 512x512 P2, 32x32 velocity grid, HLL flux", dim=2, p=2, nu=(32, 32),
                     mesh=mesh, ic=ic, cfl=0.05, flux=2)
     mesh, ic = inputs.sod(200)
-    return dict(name="Sod shock tube 200 P3, 64 velocity points", dim=1, p=3, nu=(64,), mesh=mesh,
-                ic=ic, cfl=0.1)
+    # the stencil this configuration names: own nodes and both face-neighbour elements' nodes
+    return dict(name="Sod shock tube 200 P3, 64 velocity points, stencil of own and both neighbours' nodes",
+                dim=1, p=3, nu=(64,), mesh=mesh, ic=ic, cfl=0.1, stencil=1)
 
 
 def stencil_size(wl):
     n = wl["p"] + 1
     ns = n ** wl["dim"]
     nfp = 2 if wl["dim"] == 1 else 4 * n
-    return ns + 2 * nfp
+    return 3 * ns if wl.get("stencil", 0) == 1 else ns + 2 * nfp
 
 
 def nu_total(wl):
@@ -210,7 +211,8 @@ def run_ours(args, rank, world):
     E = mesh.n_elem
 
     def make_ctx(prec):
-        ctx = kbl.Context(dim=wl["dim"], p=wl["p"], nu=wl["nu"], precision=prec, flux=wl.get("flux", 0))
+        ctx = kbl.Context(dim=wl["dim"], p=wl["p"], nu=wl["nu"], precision=prec, flux=wl.get("flux", 0),
+                          stencil=wl.get("stencil", 0))
         ctx.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
         return ctx
 
@@ -337,7 +339,8 @@ def _oracle_block(wl):
     (periodic within the block), or the whole 1D mesh."""
     import oracle as orc
     from paper_2407_20966_gb300 import inputs
-    cfg = orc.Config(dim=wl["dim"], p=wl["p"], nu=tuple(wl["nu"]), flux=wl.get("flux", 0))
+    cfg = orc.Config(dim=wl["dim"], p=wl["p"], nu=tuple(wl["nu"]), flux=wl.get("flux", 0),
+                     stencil=wl.get("stencil", 0))
     xi, _ = orc.gauss_legendre(wl["p"] + 1)
     mesh = wl["mesh"]
     if wl["dim"] == 2:
@@ -568,7 +571,8 @@ def run_sub_mesh(args, name, steps, warmup, dev):
     stream = torch.cuda.current_stream()
 
     def make_ctx(prec):
-        c = kbl.Context(dim=wl["dim"], p=wl["p"], nu=wl["nu"], precision=prec, flux=wl.get("flux", 0))
+        c = kbl.Context(dim=wl["dim"], p=wl["p"], nu=wl["nu"], precision=prec, flux=wl.get("flux", 0),
+                        stencil=wl.get("stencil", 0))
         c.mesh_upload(mesh.nbr, mesh.h, mesh.bc)
         return c
 

@@ -100,6 +100,11 @@ typedef struct {
                          trapezoidal sums of steps 2^L h .. h; needs nu - 1 even (KBL_EINVAL
                          otherwise).  Its weights are positive, so every envelope argument
                          of Sec. 4 holds unchanged.  The bounds adjoint covers 0. */
+    int stencil;      /* 0: the numerical stencil of Sec. 5 (the |S| = Ns + 2 Nfp rows above);
+                         1 (1D only, else KBL_EINVAL): the element's own solution points and all
+                         solution points of both face neighbours, |S| = 3 Ns (a boundary face
+                         contributes its boundary state Ns times); V, the limiting set, is
+                         unchanged.  Bounds, gather and step follow it. */
 } kbl_config;
 
 typedef struct kbl_ctx kbl_ctx;
@@ -122,7 +127,8 @@ typedef struct {
 
 /* Fill cfg with the paper's defaults for dimension d and order p: gamma 1.4,
  * k = 4, nu = 32 per axis in 2D and 64 in 1D, r_fac = 1e-3, eps = 1e-13,
- * floors 1e-12, eps_rule 0, FP64, coupled limiting, Rusanov flux. */
+ * floors 1e-12, eps_rule 0, FP64, coupled limiting, Rusanov flux, trapezoidal rule, the
+ * stencil of Sec. 5. */
 kbl_status kbl_config_default(kbl_config* cfg, int dim, int p);
 
 /* Create a context bound to `cuda_stream` (a cudaStream_t, NULL = legacy

@@ -283,6 +283,7 @@ bool kbl_config_valid(const kbl_config* cfg)
         !(cfg->eps >= 0.0) || !(cfg->rho_floor >= 0.0) || !(cfg->p_floor >= 0.0))
         return false;
     if (cfg->eps_rule != 0 && cfg->eps_rule != 1) return false;
+    if (cfg->stencil != 0 && !(cfg->stencil == 1 && cfg->dim == 1)) return false;
     if (cfg->precision != KBL_FP64 && cfg->precision != KBL_FP32_MIXED) return false;
     if (cfg->uncoupled != 0 && cfg->uncoupled != 1) return false;
     if (cfg->flux < 0 || cfg->flux > 2) return false;
@@ -314,6 +315,7 @@ kbl_status kbl_config_default(kbl_config* cfg, int dim, int p)
     cfg->uncoupled = 0;
     cfg->flux = 0;
     cfg->quadrature = 0;
+    cfg->stencil = 0;
     return KBL_OK;
 }
 
@@ -345,7 +347,7 @@ kbl_status kbl_create(kbl_ctx** out, const kbl_config* cfg, void* cuda_stream)
     c->nv = cfg->dim + 2;
     c->ns = cfg->dim == 1 ? n : n * n;
     c->nfp = cfg->dim == 1 ? 2 : 4 * n;
-    c->nsten = c->ns + 2 * c->nfp;
+    c->nsten = cfg->stencil == 1 ? 3 * c->ns : c->ns + 2 * c->nfp;
     cudaError_t e;
     if ((e = dalloc(&c->d_scal, 4)) != cudaSuccess || (e = dalloc(&c->d_dtbits, 1)) != cudaSuccess ||
         (e = dalloc(&c->d_blocks_done, 1)) != cudaSuccess ||

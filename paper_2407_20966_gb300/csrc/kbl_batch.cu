@@ -885,7 +885,7 @@ kbl_status kbl_batch_create(kbl_batch** out, const kbl_config* cfg, int P, const
         return KBL_EINVAL;
     if (!(cfg->gamma > 1.0) || !(cfg->k > 0.0) || !(cfg->r_fac >= 0.0 && cfg->r_fac < 1.0) || !(cfg->eps >= 0.0))
         return KBL_EINVAL;
-    if (cfg->flux < 0 || cfg->flux > 2 || cfg->quadrature != 0) return KBL_EINVAL;
+    if (cfg->flux < 0 || cfg->flux > 2 || cfg->quadrature != 0 || cfg->stencil != 0) return KBL_EINVAL;
     if (P < 1 || !p || !n_elem || !nbr || !h || !n_bc) return KBL_EINVAL;
     kbl_batch* b = new (std::nothrow) kbl_batch();
     if (!b) return KBL_ENOMEM;

@@ -77,12 +77,12 @@ k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, Mesh
 // ---------------------------------------------------------------------------
 constexpr int NT1 = 128;
 
-template <int N, bool F32>
+template <int N, bool F32, bool WIDE = false>
 __global__ void __launch_bounds__(NT1)
 k_bounds1d(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
            double* __restrict__ bnd, DevFlags* flags)
 {
-    constexpr int NS = N, NFP = 2, NST = NS + 2 * NFP, NV = 3;
+    constexpr int NS = N, NFP = 2, NST = WIDE ? 3 * NS : NS + 2 * NFP, NV = 3;
     constexpr int NW = NT1 / 32;
     __shared__ double sS[NST][NV];
     __shared__ StatePrim sP[NST];
@@ -92,7 +92,12 @@ k_bounds1d(const double* __restrict__ w, const double* __restrict__ wf, MeshDev 
     const int e = blockIdx.x, tid = threadIdx.x;
     const int NU = ph.nu[0];
     if (tid == 0) sbad = 0;
-    gather_states<1, N, NT1>(w, wf, m, e, sS);
+    if (WIDE) {
+        for (int idx = tid; idx < NST * NV; idx += NT1)
+            sS[idx / NV][idx % NV] = kbl_wide1d<N>(w, m, e, idx / NV, idx % NV);
+    } else {
+        gather_states<1, N, NT1>(w, wf, m, e, sS);
+    }
     __syncthreads();
     for (int i = tid; i < NST; i += NT1)
         if (!prim_of<1>(sS[i], ph, sP[i])) atomicOr(&sbad, 1);
@@ -207,10 +212,12 @@ int run_bounds(const kbl_ctx* c, const double* w, const double* wf, double* bnd,
 {
     if (c->E == 0) return 0;
     if (DIM == 1) {
-        if (c->cfg.precision == KBL_FP32_MIXED)
-            k_bounds1d<N, true><<<c->E, NT1, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
-        else
-            k_bounds1d<N, false><<<c->E, NT1, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+        const bool f32 = c->cfg.precision == KBL_FP32_MIXED, wide = c->cfg.stencil == 1;
+        const MeshDev m = mesh_of(c);
+        if (f32 && wide) k_bounds1d<N, true, true><<<c->E, NT1, 0, s>>>(w, wf, m, c->phys, bnd, c->d_flags);
+        else if (f32) k_bounds1d<N, true><<<c->E, NT1, 0, s>>>(w, wf, m, c->phys, bnd, c->d_flags);
+        else if (wide) k_bounds1d<N, false, true><<<c->E, NT1, 0, s>>>(w, wf, m, c->phys, bnd, c->d_flags);
+        else k_bounds1d<N, false><<<c->E, NT1, 0, s>>>(w, wf, m, c->phys, bnd, c->d_flags);
         return 1;
     }
     switch (kbl_tile_nx(c->cfg.nu[0])) {

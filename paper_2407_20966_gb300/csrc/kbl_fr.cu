@@ -59,19 +59,20 @@ int run_traces(const kbl_ctx* c, const double* w, double* wf, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // gather: S[e - e0][r][v] for the stencil rows of kbl.h (plain copies)
 // ---------------------------------------------------------------------------
-template <int DIM, int N>
+template <int DIM, int N, bool WIDE = false>
 __global__ void k_gather(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m,
                          int e0, int n, double* __restrict__ S)
 {
     constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
-    constexpr int NST = NS + 2 * NFP;
+    constexpr int NST = WIDE ? 3 * NS : NS + 2 * NFP;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)n * NST * NV) return;
     const int v = (int)(t % NV);
     const int r = (int)((t / NV) % NST);
     const int e = e0 + (int)(t / ((size_t)NV * NST));
     double val;
-    if (r < NS) val = w[((size_t)v * m.E + e) * NS + r];
+    if (WIDE) val = kbl_wide1d<N>(w, m, e, r, v);
+    else if (r < NS) val = w[((size_t)v * m.E + e) * NS + r];
     else if (r < NS + NFP) val = wf[((size_t)v * m.E + e) * NFP + (r - NS)];
     else val = kbl_exterior<DIM, N>(wf, m, e, r - NS - NFP, v);
     S[t] = val;
@@ -81,10 +82,13 @@ template <int DIM, int N>
 int run_gather(const kbl_ctx* c, const double* w, const double* wf, int e0, int n, double* S,
                cudaStream_t s)
 {
-    constexpr int NST = kbl_ns<DIM>(N) + 2 * kbl_nfp<DIM>(N);
+    const bool wide = DIM == 1 && c->cfg.stencil == 1;
+    const int NST = wide ? 3 * kbl_ns<DIM>(N) : kbl_ns<DIM>(N) + 2 * kbl_nfp<DIM>(N);
     const size_t total = (size_t)n * NST * (DIM + 2);
     if (total == 0) return 0;
-    k_gather<DIM, N><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(w, wf, mesh_of(c), e0, n, S);
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    if (wide) k_gather<DIM, N, true><<<grid, 256, 0, s>>>(w, wf, mesh_of(c), e0, n, S);
+    else k_gather<DIM, N, false><<<grid, 256, 0, s>>>(w, wf, mesh_of(c), e0, n, S);
     return 1;
 }
 

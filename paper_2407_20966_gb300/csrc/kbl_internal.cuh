@@ -421,6 +421,17 @@ __device__ __forceinline__ void kbl_hll(const T* ql, const T* qr, int dir, T gam
     for (int v = 0; v < NV; v++) F[v] = (Sr * F[v] - Sl * Fr[v] + Sl * Sr * (qr[v] - ql[v])) * inv;
 }
 
+// Row r, component v of the wider 1D stencil of element e: the element's N solution points, then
+// those of the left (face 0) and the right (face 1) neighbour; a boundary face gives its state.
+template <int N>
+__device__ __forceinline__ double kbl_wide1d(const double* __restrict__ w, const MeshDev& m, int e, int r, int v)
+{
+    const int blk = r / N, n = r - blk * N;
+    if (blk == 0) return w[((size_t)v * m.E + e) * N + n];
+    const int nb = m.nbr[e * 2 + (blk - 1)];
+    return nb >= 0 ? w[((size_t)v * m.E + nb) * N + n] : m.bc[(size_t)(-nb - 1) * 3 + v];
+}
+
 // Exterior value of component v at face point fp of element e.
 template <int DIM, int N>
 __device__ __forceinline__ double kbl_exterior(const double* __restrict__ wf, const MeshDev& m,

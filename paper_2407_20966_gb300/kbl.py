@@ -35,7 +35,7 @@ class KblConfig(C.Structure):
                 ("k", C.c_double), ("r_fac", C.c_double), ("eps", C.c_double),
                 ("rho_floor", C.c_double), ("p_floor", C.c_double), ("eps_rule", C.c_int),
                 ("precision", C.c_int), ("uncoupled", C.c_int), ("flux", C.c_int),
-                ("quadrature", C.c_int)]
+                ("quadrature", C.c_int), ("stencil", C.c_int)]
 
 
 class KblCounters(C.Structure):
