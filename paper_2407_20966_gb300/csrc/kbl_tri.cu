@@ -678,22 +678,32 @@ kbl_status kbl_tri_bounds(kbl_tri* t, const double* w, const double* wf, double*
     return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
 }
 
-kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R)
+namespace {
+
+// The residual of kbl_tri_residual on a given stream.
+kbl_status tri_residual_on(kbl_tri* t, const double* w, const double* wf, double* R, cudaStream_t s)
 {
-    if (!t || (t->E > 0 && (!w || !wf || !R))) return tfail(t, KBL_EINVAL, "null array");
     if (t->E) {
         const unsigned grid = blocks_for(t->E, 128);
         const bool f32 = t->cfg.precision == KBL_FP32_MIXED;
         const TriMeshDev md = tri_dev(t);
         const double gam = t->cfg.gamma;
         const int fl = t->cfg.flux;
-        if (t->cfg.p == 1 && f32) k_tri_rhs<1, float><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
-        else if (t->cfg.p == 1) k_tri_rhs<1, double><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
-        else if (f32) k_tri_rhs<2, float><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
-        else k_tri_rhs<2, double><<<grid, 128, 0, t->stream>>>(w, wf, md, t->ops, gam, fl, R);
+        if (t->cfg.p == 1 && f32) k_tri_rhs<1, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        else if (t->cfg.p == 1) k_tri_rhs<1, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        else if (f32) k_tri_rhs<2, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        else k_tri_rhs<2, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+kbl_status kbl_tri_residual(kbl_tri* t, const double* w, const double* wf, double* R)
+{
+    if (!t || (t->E > 0 && (!w || !wf || !R))) return tfail(t, KBL_EINVAL, "null array");
+    return tri_residual_on(t, w, wf, R, t->stream);
 }
 
 kbl_status kbl_tri_dt(kbl_tri* t, const double* w, double cfl, double* dt_host)
@@ -734,11 +744,7 @@ kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
         cudaError_t ce = cudaEventRecord(t->ev_fork, t->stream);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(t->side, t->ev_fork, 0);
         if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
-        cudaStream_t own = t->stream;
-        t->stream = t->side;
-        st = kbl_tri_residual(t, ws, t->d_wf, t->d_R);
-        t->stream = own;
-        if (st != KBL_OK) return st;
+        if ((st = tri_residual_on(t, ws, t->d_wf, t->d_R, t->side)) != KBL_OK) return st;
         ce = cudaEventRecord(t->ev_join, t->side);
         if (ce != cudaSuccess) return tfail(t, KBL_ECUDA, cudaGetErrorString(ce));
         if ((st = kbl_tri_bounds(t, ws, t->d_wf, t->d_bnd)) != KBL_OK) return st;

@@ -256,3 +256,63 @@ def test_fullsize_stage_parity_identical_inputs(orc, workload):
               f"composed {ec.max():.2e} on {len(idx)} elements")
         ws = got
     print(f"{workload}: limited element-stages in the sample", limited)
+
+
+def test_fullsize_batch_phase_parity_identical_inputs(orc):
+    """The 4096-problem batch at full size (25.8 M elements, orders P1..P4), in the launch shape
+    the autotuner picks and bench.py times, after two steps of the batch itself: one stage's
+    bounds, residual and stage + limiter, each on identical inputs, against the checker on 16
+    sampled problems of every order: bounds of 48 sampled elements per problem to 1e-5, the
+    residual of the whole problem to 1e-5 per element and component, and the limited state of
+    the whole problem to 1e-12 when both sides limit against the device's bounds."""
+    import torch
+    from paper_2407_20966_gb300 import kbl
+    from tests.gpu_helpers import rhs_error, state_error
+    probs = inputs.four_quadrant_batch(0x5EED, 4096)
+    b = kbl.Batch([(p, m.nbr, m.h, m.bc) for p, m, _ in probs])
+    E = int(b.elem_offsets[-1])
+    assert E > 25_000_000
+    wd = torch.from_numpy(inputs.batch_state(probs, b.nodes, b.state_offsets)).cuda()
+    b.autotune(wd)
+    for _ in range(2):
+        b.step(wd, 0.05)
+    b.check()
+    dts = np.asarray(b.dt(), dtype=np.float64)
+    rng = np.random.default_rng(5)
+    sample = []
+    for p in (1, 2, 3, 4):
+        cand = np.flatnonzero(np.asarray(b.p) == p)
+        sample += list(rng.choice(cand, 4, replace=False))
+    bnd = torch.zeros(8 * E, dtype=torch.float64, device="cuda")
+    R = torch.zeros_like(wd)
+    b.bounds(wd, bnd)
+    b.rhs(wd, R)
+    out = torch.zeros_like(wd)
+    b.stage(0, wd, wd, R, bnd, torch.from_numpy(dts).cuda(), out)
+    b.check()
+    limited = 0
+    for i in sample:
+        p, mesh, _ = probs[i]
+        cfg = orc.Config(dim=2, p=p, nu=(32, 32))
+        om = orc.Mesh(mesh.nbr, mesh.h, mesh.bc)
+        ws = np.ascontiguousarray(b.state_view(wd, i).cpu().numpy())
+        wf = orc.traces(cfg, om, ws)
+        bg = b.bounds_view(bnd, i).cpu().numpy()
+        idx = rng.choice(mesh.n_elem, min(48, mesh.n_elem), replace=False)
+        bref = np.zeros((2, 4, len(idx)))
+        for k, e in enumerate(idx):
+            bref[0, :, k], bref[1, :, k] = orc.bounds_stencil(cfg, orc.gather_stencil(cfg, om, ws, wf, int(e)))
+        eb = bounds_error(bg[:, :, idx], bref)
+        assert eb.max() < TOL_FP32, ("bounds", i, p, eb.max())
+        Rg = np.ascontiguousarray(b.state_view(R, i).cpu().numpy())
+        R_ref = orc.rhs(cfg, om, ws, wf)
+        er = rhs_error(Rg, R_ref, ws, wf, om)
+        assert er.max() < TOL_FP32, ("residual", i, p, er.max())
+        comb = orc.stage_combine(cfg, om, 0, ws, ws, Rg, dts[i])
+        ref, a = orc.limit(cfg, om, comb, bg)
+        limited += int((a[0] < 1).sum())
+        got = b.state_view(out, i).cpu().numpy()
+        es = state_error(got, ref).max()
+        assert es < TOL_FP64, ("stage", i, p, es)
+    assert limited > 0
+    print(f"batch: {len(sample)} sampled problems, limited elements {limited}")
