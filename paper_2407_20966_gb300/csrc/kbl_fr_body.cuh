@@ -66,6 +66,21 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
     const int e = e0 + el;
     const bool node_thread = el < EPB && el < nmax && e < m.E;
     const T gamma = from_f64<T>(gamma_d), gm1 = F32 ? gamma - T(1) : from_f64<T>(gamma_d - 1.0);
+    // the first face point of this thread: its interior and exterior values are loaded now, so
+    // that their latency (the exterior one behind the neighbour index) overlaps step 1
+    double pi[NV], pe[NV];
+    bool pre = false;
+    {
+        const int ell = tid / NFP, fp = tid % NFP, ee = e0 + ell;
+        if (tid < EPB * NFP && ee < m.E && ell < nmax) {
+            pre = true;
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                pi[v] = wf[((size_t)v * m.E + ee) * NFP + fp];
+                pe[v] = kbl_exterior<DIM, N>(wf, m, ee, fp, v);
+            }
+        }
+    }
     if (node_thread) {
         T q[NV];
 #pragma unroll
@@ -85,10 +100,18 @@ __device__ __forceinline__ void rhs_block(RhsSmem<DIM, N, T, EPB>& sm, int NT, c
         if (ee >= m.E || ell >= nmax) continue;
         const int f = fp / NFPF, k = fp % NFPF, dir = f >> 1, side = f & 1;
         T qi[NV], qe[NV], Fc[NV];
+        if (pre && t == tid) {
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-            qi[v] = from_f64<T>(wf[((size_t)v * m.E + ee) * NFP + fp]);
-            qe[v] = from_f64<T>(kbl_exterior<DIM, N>(wf, m, ee, fp, v));
+            for (int v = 0; v < NV; v++) {
+                qi[v] = from_f64<T>(pi[v]);
+                qe[v] = from_f64<T>(pe[v]);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                qi[v] = from_f64<T>(wf[((size_t)v * m.E + ee) * NFP + fp]);
+                qe[v] = from_f64<T>(kbl_exterior<DIM, N>(wf, m, ee, fp, v));
+            }
         }
         if (flux == 1) {
             if (side == 0) kbl_hllc<DIM, T>(qe, qi, dir, gamma, Fc);
