@@ -353,11 +353,12 @@ __device__ __forceinline__ void bounds2d_f32_core(Bounds2dF32SmemS<NST_, NX, TYS
             tlo[a][b] = FLT_MAX; ilo[a][b] = FLT_MAX;
             thi[a][b] = 0.0f; ihi[a][b] = 0.0f;
         }
-    // unrolled by 8, or by 12 for 24 or 48 pairs: measured fastest (2, 4 and 6 keep loop and
-    // address arithmetic on the ALU pipe the min/max need; a full unroll overflows the
-    // instruction cache; 12 is faster on the 24 pairs of a P3 element, 146.0 against 147.6 us at
-    // 128^2, and slower for the pair counts it does not divide)
-    constexpr int ENV_UNROLL = (NPAIR % 12 == 0 && NPAIR >= 24) ? 12 : 8;
+    // unroll factor by pair count, measured (fractions of the envelope-pattern peak on the bench
+    // workloads): 12 for 24 or 48 pairs (P3 quads: 0.676 against 0.669 at 8), 4 for odd counts
+    // (P2 quads, 17 pairs: 0.625 against 0.609 at 8), 8 otherwise (P2 triangles, 12 pairs:
+    // 0.574 against 0.553 at 4 and 0.548 at 12); 2 keeps loop and address arithmetic on the ALU
+    // pipe the min/max need, and a full unroll overflows the instruction cache
+    constexpr int ENV_UNROLL = (NPAIR % 12 == 0 && NPAIR >= 24) ? 12 : (NPAIR % 2 == 1 ? 4 : 8);
 #pragma unroll ENV_UNROLL
     for (int pi = 0; pi < NPAIR; pi++) {
         float2 ex[TX], ey[TY];
