@@ -53,7 +53,9 @@ def test_invalid_configs_rejected_before_any_device_call(lib):
     bad = []
     for field, val in (("nu", (65, 65)), ("nu", (17, 33)), ("gamma", 1.0), ("r_fac", 1.0), ("k", 0.0),
                        ("precision", 7), ("flux", 3), ("quadrature", 2),
-                       ("quadrature", 1)):   # 31 intervals: no coarser grid for Romberg
+                       ("quadrature", 1),    # 31 intervals: no coarser grid for Romberg
+                       ("stencil", 1),       # the wider stencil is 1D only
+                       ("stencil", 2), ("eps_rule", 2), ("uncoupled", 2)):
         c2 = kbl.KblConfig()
         C.pointer(c2)[0] = cfg
         if field == "nu":
@@ -63,6 +65,31 @@ def test_invalid_configs_rejected_before_any_device_call(lib):
         bad.append(lib.kbl_create(C.byref(h), C.byref(c2), None))
     assert all(st == kbl.EINVAL for st in bad)
     assert lib.kbl_destroy(None) == kbl.EINVAL
+    # the triangle mesh refuses orders outside {1, 2} and 1D configurations before any device call
+    t = C.c_void_p()
+    tri = kbl.KblConfig()
+    lib.kbl_config_default(C.byref(tri), 2, 3)
+    assert lib.kbl_tri_create(C.byref(t), C.byref(tri), 0, None, None, None, 0, None, None) == kbl.EINVAL
+    lib.kbl_config_default(C.byref(tri), 1, 2)
+    assert lib.kbl_tri_create(C.byref(t), C.byref(tri), 0, None, None, None, 0, None, None) == kbl.EINVAL
+    rs, w = (C.c_double * 12)(), (C.c_double * 6)()
+    assert lib.kbl_tri_points(3, rs, w) == kbl.EINVAL
+
+
+def test_triangle_points_on_the_host(lib):
+    """kbl_tri_points runs on the host: the 3- and 6-point rules, interior, weights summing to the
+    area, exact to degree 2p."""
+    import numpy as np
+    from paper_2407_20966_gb300 import kbl
+    for p in (1, 2):
+        rs, w = kbl.tri_points(p)
+        assert abs(w.sum() - 0.5) < 1e-15 and (w > 0).all()
+        assert (1 - rs.sum(axis=1)).min() > 0 and rs.min() > 0
+        for i in range(2 * p + 1):
+            for j in range(2 * p + 1 - i):
+                from math import factorial
+                exact = factorial(i) * factorial(j) / factorial(i + j + 2)
+                assert abs((w * rs[:, 0] ** i * rs[:, 1] ** j).sum() - exact) < 1e-15
 
 
 def test_product_path_has_no_cpu_fallback():
