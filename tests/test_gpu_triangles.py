@@ -45,7 +45,13 @@ def _blast(x, y):
     return np.stack([rho, rho * u, rho * v, P / (G - 1) + 0.5 * rho * (u * u + v * v)])
 
 
-def _setup(orc, p, nx, ny, periodic, flux=0, precision=0, seed=5):
+def _smooth(x, y):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    u, v, P = 0.3 + 0 * x, -0.2 + 0 * x, 1.0 + 0.1 * np.cos(2 * np.pi * x)
+    return np.stack([rho, rho * u, rho * v, P / (G - 1) + 0.5 * rho * (u * u + v * v)])
+
+
+def _setup(orc, p, nx, ny, periodic, flux=0, precision=0, seed=5, ic=None):
     from paper_2407_20966_gb300 import kbl
     m = inputs.tri_mesh_2d(nx, ny, 0.0, 1.0, 0.0, 0.9, jitter=0.2, seed=seed, periodic=(periodic, periodic))
     rng = np.random.default_rng(seed)
@@ -55,7 +61,7 @@ def _setup(orc, p, nx, ny, periodic, flux=0, precision=0, seed=5):
     cfg = orc.Config(dim=2, p=p, nu=(16, 16), flux=flux)
     tm = kbl.TriMesh(p, m.xy, m.nbr, m.nbr_edge, m.bc, precision=precision, flux=flux, nu=(16, 16))
     rs, _ = orc.tri_points(p)
-    w = inputs.tri_nodal_field(m, rs, _blast)
+    w = inputs.tri_nodal_field(m, rs, ic if ic is not None else _blast)
     w = w * (1 + 0.02 * rng.uniform(-1, 1, w.shape))   # discontinuous across elements
     return m, om, cfg, tm, np.ascontiguousarray(w)
 
@@ -313,3 +319,20 @@ def test_full_size_workload_per_call(orc):
         assert err.max() < TOL_FP64, (e, err.max())
         assert abs(a_h[0, e] - a[0]) < 1e-12 and abs(a_h[1, e] - a[1]) < 1e-12
     assert limited > 0
+
+
+@pytest.mark.parametrize("p,nx,ny,periodic", [(1, 1, 1, True), (2, 1, 1, True), (2, 2, 1, False), (1, 3, 2, False)])
+def test_tiny_meshes_step(orc, p, nx, ny, periodic):
+    """Meshes of 2 to 12 triangles (one partial block everywhere; on the 1 x 1 periodic mesh both
+    elements are each other's neighbours across all three edges), a smooth field perturbed per
+    node: two FP64 steps against the checker."""
+    m, om, cfg, tm, w = _setup(orc, p, nx, ny, periodic, flux=1, seed=9, ic=_smooth)
+    wd = _dev(w)
+    dt = orc.tri_dt(cfg, om, w, 0.2)
+    ref = w
+    for _ in range(2):
+        tm.step(wd, dt)
+        ref, _ = orc.tri_ssprk3_step(cfg, om, ref, dt)
+    tm.check()
+    err = np.abs(wd.cpu().numpy() - ref) / _elem_scale(ref)
+    assert err.max() < TOL_FP64, err.max()
