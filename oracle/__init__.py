@@ -52,7 +52,8 @@ class _Mesh(C.Structure):
 
 class _TriMesh(C.Structure):
     _fields_ = [("n_elem", C.c_int), ("xy", C.POINTER(C.c_double)), ("nbr", C.POINTER(C.c_int)),
-                ("nbr_edge", C.POINTER(C.c_int)), ("n_bc", C.c_int), ("bc", C.POINTER(C.c_double))]
+                ("nbr_edge", C.POINTER(C.c_int)), ("n_bc", C.c_int), ("bc", C.POINTER(C.c_double)),
+                ("xy6", C.POINTER(C.c_double))]
 
 
 def _load():
@@ -371,16 +372,20 @@ class TriMesh:
     """Affine triangles: xy[E][3][2] (counterclockwise), nbr[E][3] (element across edge f from vertex f
     to vertex f+1, < 0 boundary id -(nbr+1)), nbr_edge[E][3] (the neighbour's matched edge), bc."""
 
-    def __init__(self, xy, nbr, nbr_edge, bc=None):
+    def __init__(self, xy, nbr, nbr_edge, bc=None, xy6=None):
+        """xy6: [E][6][2] curved (quadratic) elements, the corners then the mid-parameter points
+        of edges 0, 1, 2 (xy then holds the corners); None for affine elements."""
         self.xy = np.ascontiguousarray(xy, dtype=np.float64)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
         self.nbr_edge = np.ascontiguousarray(nbr_edge, dtype=np.int32)
         self.n_elem = self.nbr.shape[0]
         self.bc = np.ascontiguousarray(bc if bc is not None else np.zeros((1, 4)), dtype=np.float64)
+        self.xy6 = None if xy6 is None else np.ascontiguousarray(xy6, dtype=np.float64)
 
     def _c(self):
         return _TriMesh(self.n_elem, _dp(self.xy), self.nbr.ctypes.data_as(C.POINTER(C.c_int)),
-                        self.nbr_edge.ctypes.data_as(C.POINTER(C.c_int)), self.bc.shape[0], _dp(self.bc))
+                        self.nbr_edge.ctypes.data_as(C.POINTER(C.c_int)), self.bc.shape[0], _dp(self.bc),
+                        None if self.xy6 is None else _dp(self.xy6))
 
 
 def tri_ns(p):

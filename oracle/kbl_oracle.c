@@ -1020,6 +1020,24 @@ static void orc_tri_geometry(const orc_trimesh* m, int e, orc_trigeo* g)
     }
 }
 
+/* Curved elements: x(r, s) = sum_k N_k(r, s) X_k with the six quadratic Lagrange shape
+ * functions of the corners and the edge mid-parameter points (barycentrics l1 = 1 - r - s,
+ * l2 = r, l3 = s: N0 = l1 (2 l1 - 1), N1 = l2 (2 l2 - 1), N2 = l3 (2 l3 - 1), N3 = 4 l1 l2,
+ * N4 = 4 l2 l3, N5 = 4 l3 l1); the derivatives x_r, x_s, y_r, y_s of the map at (r, s). */
+static void orc_tri_map_deriv(const double* X, double r, double s, double* xr, double* xs, double* yr, double* ys)
+{
+    const double l1 = 1.0 - r - s, l2 = r, l3 = s;
+    const double dr[6] = {-(4.0 * l1 - 1.0), 4.0 * l2 - 1.0, 0.0, 4.0 * (l1 - l2), 4.0 * l3, -4.0 * l3};
+    const double ds[6] = {-(4.0 * l1 - 1.0), 0.0, 4.0 * l3 - 1.0, -4.0 * l2, 4.0 * l2, 4.0 * (l1 - l3)};
+    *xr = *xs = *yr = *ys = 0.0;
+    for (int k = 0; k < 6; k++) {
+        *xr += dr[k] * X[2 * k];
+        *xs += ds[k] * X[2 * k];
+        *yr += dr[k] * X[2 * k + 1];
+        *ys += ds[k] * X[2 * k + 1];
+    }
+}
+
 /* Interior values at the flux points: interpolation of the solution polynomial. */
 void orc_tri_traces(const orc_cfg* c, const orc_trimesh* m, const double* w, double* wf)
 {
@@ -1078,6 +1096,78 @@ static void orc_tri_common_flux(const orc_cfg* c, const double* qi, const double
     F[3] = Fl[3];
 }
 
+/* The residual of a curved element (FR with the DG correction on the mapped element, the
+ * transformed-flux form): with adj J = |J| J^-1 at each point, the transformed flux
+ * Ft = adj J F, and at each flux point the reference unit normal nh of its edge, the physical
+ * unit normal n and the stretch sigma = |dx/dt| / |dxi/dt| along the edge (Nanson: Ft . nh =
+ * sigma F . n),
+ *   R_i = -(1/|J_i|) [ sum_j (Dr_ij Ft_r,j + Ds_ij Ft_s,j)
+ *                      + sum_q phi_i(x_q) gw_q L_f / (2 w_i) (sigma_q F*_n,q - (Ft_h . nh)(x_q)) ],
+ * L_f the reference edge's length.  The solution points carry the lumped mass w_i |J_i| (the
+ * collocated quadrature of FR; exact for affine elements). */
+static void orc_tri_rhs_curved(const orc_cfg* c, const orc_trimesh* m, const orc_triops* o, int e,
+                               double Fx[6][4], double Fy[6][4], const double* wf, double* Re)
+{
+    const int ns = o->ns, nfp = o->nfp, p = c->p;
+    const double* X = m->xy6 + (size_t)e * 12;
+    double Fr[6][4], Fs[6][4], detJ[6];
+    for (int j = 0; j < ns; j++) {
+        double xr, xs, yr, ys;
+        orc_tri_map_deriv(X, o->rs[j][0], o->rs[j][1], &xr, &xs, &yr, &ys);
+        detJ[j] = xr * ys - xs * yr;
+        for (int v = 0; v < 4; v++) {
+            Fr[j][v] = ys * Fx[j][v] - xs * Fy[j][v];
+            Fs[j][v] = -yr * Fx[j][v] + xr * Fy[j][v];
+        }
+    }
+    double acc[6][4];
+    for (int i = 0; i < ns; i++)
+        for (int v = 0; v < 4; v++) {
+            double d = 0.0;
+            for (int j = 0; j < ns; j++) d += o->dr[i][j] * Fr[j][v] + o->ds[i][j] * Fs[j][v];
+            acc[i][v] = d;
+        }
+    const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+    for (int f = 0; f < 3; f++) {
+        const double dvx = V[(f + 1) % 3][0] - V[f][0], dvy = V[(f + 1) % 3][1] - V[f][1];
+        const double L = sqrt(dvx * dvx + dvy * dvy);
+        const double nhx = dvy / L, nhy = -dvx / L;
+        for (int k = 0; k <= p; k++) {
+            const int q = f * (p + 1) + k;
+            double xr, xs, yr, ys;
+            orc_tri_map_deriv(X, o->fr[q][0], o->fr[q][1], &xr, &xs, &yr, &ys);
+            const double tx = xr * dvx + xs * dvy, ty = yr * dvx + ys * dvy;
+            const double ds = sqrt(tx * tx + ty * ty);
+            const double nx = ty / ds, ny = -tx / ds, sigma = ds / L;
+            double qe[4], Fstar[4];
+            orc_tri_exterior(m, p, wf, e, f, k, qe);
+            orc_tri_common_flux(c, wf + ((size_t)e * nfp + q) * 4, qe, nx, ny, Fstar);
+            for (int v = 0; v < 4; v++) {
+                double Fn = 0.0;
+                for (int j = 0; j < ns; j++) Fn += o->phi_f[q][j] * (Fr[j][v] * nhx + Fs[j][v] * nhy);
+                const double jump = sigma * Fstar[v] - Fn;
+                for (int i = 0; i < ns; i++) acc[i][v] += o->phi_f[q][i] * o->gw[q] * L / (2.0 * o->wq[i]) * jump;
+            }
+        }
+    }
+    for (int i = 0; i < ns; i++)
+        for (int v = 0; v < 4; v++) Re[i * 4 + v] = -acc[i][v] / detJ[i];
+}
+
+/* Mean weights of element e for the limiter: the lumped mass w_i |J_i| of a curved element, the
+ * rule's weights w_i of an affine one (the same mean: |J| is constant there). */
+static void orc_tri_mean_weights(const orc_trimesh* m, const orc_triops* o, int e, double* W)
+{
+    for (int i = 0; i < o->ns; i++) {
+        W[i] = o->wq[i];
+        if (m->xy6) {
+            double xr, xs, yr, ys;
+            orc_tri_map_deriv(m->xy6 + (size_t)e * 12, o->rs[i][0], o->rs[i][1], &xr, &xs, &yr, &ys);
+            W[i] *= xr * ys - xs * yr;
+        }
+    }
+}
+
 /* Strong-form nodal DG residual (FR with the DG correction) of an affine triangle:
  *   R_i = -div F_h(x_i) - sum_q phi_i(x_q) (|e_q| gw_q / 2) / (det J w_i) (F*_n - F_h . n)(x_q)
  * with F_h the interpolation of the solution-point fluxes (Eq. 2), x_q the flux points and
@@ -1095,6 +1185,10 @@ void orc_tri_rhs(const orc_cfg* c, const orc_trimesh* m, const double* w, const 
         for (int j = 0; j < ns; j++) {
             orc_flux(c, w + ((size_t)e * ns + j) * 4, 0, Fx[j]);
             orc_flux(c, w + ((size_t)e * ns + j) * 4, 1, Fy[j]);
+        }
+        if (m->xy6) {
+            orc_tri_rhs_curved(c, m, &o, e, Fx, Fy, wf, R + (size_t)e * ns * 4);
+            continue;
         }
         for (int i = 0; i < ns; i++)
             for (int v = 0; v < 4; v++) {
@@ -1150,8 +1244,9 @@ double orc_tri_dt(const orc_cfg* c, const orc_trimesh* m, const double* w, doubl
 
 /* One SSP-RK3 step on triangles, limited after every stage as on quads (Sec. 3.9, Sec. 5):
  * bounds of each element's stencil (orc_bounds_stencil), the residual, the Shu-Osher
- * combination, then the limiter of the node set (orc_limit_nodes) with the Williams-Shunn
- * weights for the mean and the flux-point values of the combined state. */
+ * combination, then the limiter of the node set (orc_limit_nodes) with the element's mean
+ * weights (the Williams-Shunn weights, times |J_i| on a curved element) and the flux-point
+ * values of the combined state. */
 int orc_tri_ssprk3_step(const orc_cfg* c, const orc_trimesh* m, double* w, double dt, double* alpha)
 {
     const int p = c->p, ns = orc_tri_ns(p), nfp = orc_tri_nfp(p), E = m->n_elem, nst = ns + 2 * nfp;
@@ -1188,7 +1283,9 @@ int orc_tri_ssprk3_step(const orc_cfg* c, const orc_trimesh* m, double* w, doubl
                 for (int i = 0; i < ns; i++) wel[v * ns + i] = ws[((size_t)e * ns + i) * 4 + v];
                 for (int q = 0; q < nfp; q++) wfel[v * nfp + q] = wf[((size_t)e * nfp + q) * 4 + v];
             }
-            orc_limit_nodes(c, ns, nfp, o.wq, wel, wfel, lo + 4 * e, hi + 4 * e, a);
+            double W[6];
+            orc_tri_mean_weights(m, &o, e, W);
+            orc_limit_nodes(c, ns, nfp, W, wel, wfel, lo + 4 * e, hi + 4 * e, a);
             for (int v = 0; v < 4; v++)
                 for (int i = 0; i < ns; i++) ws[((size_t)e * ns + i) * 4 + v] = wel[v * ns + i];
             if (alpha && s == 2) { alpha[e] = a[0]; alpha[E + e] = a[1]; }

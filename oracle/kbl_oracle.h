@@ -139,6 +139,8 @@ typedef struct {
     const int* nbr_edge;  /* [E][3] the neighbour's edge matched to edge f */
     int n_bc;
     const double* bc;     /* [n_bc][4] */
+    const double* xy6;    /* curved (quadratic) elements, or NULL for affine ones: [E][6][2], the
+                             corners (as in xy) then the points of edges 0, 1, 2 at mid-parameter */
 } orc_trimesh;
 
 int orc_tri_ns(int p);    /* (p+1)(p+2)/2 solution points */

@@ -345,8 +345,9 @@ class TriMeshData:
     edge f, from vertex f to vertex f+1; negative = boundary id -(nbr+1)), nbr_edge[E][3] (the
     neighbour's matched edge), bc[n_bc][4]."""
 
-    def __init__(self, xy, nbr, nbr_edge, bc):
+    def __init__(self, xy, nbr, nbr_edge, bc, xy6=None):
         self.xy, self.nbr, self.nbr_edge, self.bc = xy, nbr, nbr_edge, bc
+        self.xy6 = xy6   # curved elements: [E][6][2], the corners then the edges' mid-parameter points
         self.n_elem = nbr.shape[0]
 
 
@@ -409,14 +410,46 @@ def tri_mesh_2d(nx, ny, x0, x1, y0, y1, jitter=0.0, seed=0, periodic=(True, True
     return TriMeshData(xy, nbr, nbr_edge, bc)
 
 
-def tri_nodal_field(mesh, rs, ic):
-    """Initial state at the solution points of every triangle, w[E][ns][4]; rs[ns][2] reference
-    points on (0,0), (1,0), (0,1), ic(x, y) -> (4, ...) conservative state."""
+def tri_curved_mesh(nx, ny, x0, x1, y0, y1, jitter=0.0, bump=0.15, seed=0, periodic=(True, True)):
+    """tri_mesh_2d with curved (quadratic) elements: each edge's mid-parameter point is its
+    midpoint moved by bump cell widths times a smooth field periodic over the domain, evaluated at
+    the midpoint itself, so that the two elements of an edge (and periodic images) agree."""
+    m = tri_mesh_2d(nx, ny, x0, x1, y0, y1, jitter=jitter, seed=seed, periodic=periodic)
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    Lx, Ly = x1 - x0, y1 - y0
+    xy6 = np.zeros((m.n_elem, 6, 2))
+    xy6[:, :3] = m.xy
+    for f in range(3):
+        mid = 0.5 * (m.xy[:, f] + m.xy[:, (f + 1) % 3])
+        px, py = 2 * np.pi * (mid[:, 0] - x0) / Lx, 2 * np.pi * (mid[:, 1] - y0) / Ly
+        xy6[:, 3 + f, 0] = mid[:, 0] + bump * hx * np.sin(py) * np.cos(px + 0.3)
+        xy6[:, 3 + f, 1] = mid[:, 1] + bump * hy * np.sin(px) * np.cos(py + 0.7)
+    m.xy6 = xy6
+    return m
+
+
+def tri_positions(mesh, rs):
+    """Physical positions x[E][n], y[E][n] of reference points rs[n][2] on every triangle: the
+    affine map of the corners, or the quadratic map of xy6 on curved meshes."""
+    r, s = rs[None, :, 0], rs[None, :, 1]
+    if getattr(mesh, "xy6", None) is not None:
+        l1, l2, l3 = 1 - r - s, r, s
+        N = [l1 * (2 * l1 - 1), l2 * (2 * l2 - 1), l3 * (2 * l3 - 1), 4 * l1 * l2, 4 * l2 * l3, 4 * l3 * l1]
+        x = sum(N[k] * mesh.xy6[:, k, 0][:, None] for k in range(6))
+        y = sum(N[k] * mesh.xy6[:, k, 1][:, None] for k in range(6))
+        return x, y
     X0 = mesh.xy[:, 0, :]
     J1 = mesh.xy[:, 1, :] - X0
     J2 = mesh.xy[:, 2, :] - X0
-    x = X0[:, None, 0] + rs[None, :, 0] * J1[:, None, 0] + rs[None, :, 1] * J2[:, None, 0]
-    y = X0[:, None, 1] + rs[None, :, 0] * J1[:, None, 1] + rs[None, :, 1] * J2[:, None, 1]
+    x = X0[:, None, 0] + r * J1[:, None, 0] + s * J2[:, None, 0]
+    y = X0[:, None, 1] + r * J1[:, None, 1] + s * J2[:, None, 1]
+    return x, y
+
+
+def tri_nodal_field(mesh, rs, ic):
+    """Initial state at the solution points of every triangle, w[E][ns][4]; rs[ns][2] reference
+    points on (0,0), (1,0), (0,1), ic(x, y) -> (4, ...) conservative state."""
+    x, y = tri_positions(mesh, rs)
     q = np.asarray(ic(x, y), dtype=np.float64)          # [4][E][ns]
     return np.ascontiguousarray(np.moveaxis(q, 0, -1))  # [E][ns][4]
 

@@ -142,3 +142,90 @@ def test_limited_step_keeps_means_positivity_and_bounds(orc, p):
         tol = 1e-12 * np.maximum(np.abs(lo), np.abs(hi))
         assert np.all(lim.min(axis=1) >= lo - tol) and np.all(lim.max(axis=1) <= hi + tol), e
     assert limited > 0
+
+
+# ---- curved (quadratic) elements --------------------------------------------------------------
+def _jacobians(xy6, rs):
+    """|J| of the quadratic map at reference points rs[n][2] of every element: [E][n]."""
+    r, s = rs[None, :, 0], rs[None, :, 1]
+    l1, l2, l3 = 1 - r - s, r, s
+    dr = [-(4 * l1 - 1), 4 * l2 - 1, 0 * r, 4 * (l1 - l2), 4 * l3, -4 * l3]
+    ds = [-(4 * l1 - 1), 0 * r, 4 * l3 - 1, -4 * l2, 4 * l2, 4 * (l1 - l3)]
+    xr = sum(dr[k] * xy6[:, k, 0][:, None] for k in range(6))
+    xs = sum(ds[k] * xy6[:, k, 0][:, None] for k in range(6))
+    yr = sum(dr[k] * xy6[:, k, 1][:, None] for k in range(6))
+    ys = sum(ds[k] * xy6[:, k, 1][:, None] for k in range(6))
+    return xr * ys - xs * yr
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_curved_with_straight_edges_is_the_affine_scheme(orc, p):
+    """Mid-parameter points on the straight edges make the quadratic map affine: the curved
+    residual and limited step equal the affine ones to rounding."""
+    m = inputs.tri_mesh_2d(6, 5, 0.0, 1.0, 0.0, 0.8, jitter=0.25, seed=3, periodic=(False, False))
+    xy6 = np.concatenate([m.xy, 0.5 * (m.xy + np.roll(m.xy, -1, axis=1))], axis=1)
+    om = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc)
+    oc = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc, xy6=xy6)
+    cfg = _cfg(orc, p, flux=1)
+    rs, _ = orc.tri_points(p)
+    rng = np.random.default_rng(p)
+    w = inputs.tri_nodal_field(m, rs, lambda x, y: _state(x, y, lambda a, b: 1.0 + 0.3 * a - 0.2 * b))
+    w = np.ascontiguousarray(w * (1 + 0.1 * rng.uniform(-1, 1, w.shape)))
+    wf = orc.tri_traces(cfg, om, w)
+    Ra, Rc = orc.tri_rhs(cfg, om, w, wf), orc.tri_rhs(cfg, oc, w, wf)
+    assert np.abs(Ra - Rc).max() < 1e-11 * np.abs(Ra).max()
+    dt = orc.tri_dt(cfg, om, w, 0.1)
+    wa, _ = orc.tri_ssprk3_step(cfg, om, w, dt)
+    wc, _ = orc.tri_ssprk3_step(cfg, oc, w, dt)
+    assert np.abs(wa - wc).max() < 1e-12 * np.abs(wa).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("flux", [0, 1, 2])
+def test_curved_free_stream_and_conservation(orc, p, flux):
+    """On a periodic mesh of curved elements: a constant state has zero residual (the discrete
+    metric identity of the transformed-flux form), and the residual of a discontinuous field
+    weighted by the lumped mass w_i |J_i| sums to zero (the surface terms of the two sides of an
+    edge cancel)."""
+    m = inputs.tri_curved_mesh(6, 5, 0.0, 1.0, 0.0, 0.8, jitter=0.2, bump=0.15, seed=3)
+    om = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc, xy6=m.xy6)
+    cfg = _cfg(orc, p, flux)
+    rs, wq = orc.tri_points(p)
+    J = _jacobians(m.xy6, rs)
+    assert J.min() > 0
+    w = inputs.tri_nodal_field(m, rs, lambda x, y: _state(x, y, lambda a, b: 1.3))
+    R0 = orc.tri_rhs(cfg, om, w, orc.tri_traces(cfg, om, w))
+    rng = np.random.default_rng(p)
+    w = np.ascontiguousarray(w * (1 + 0.2 * rng.uniform(-1, 1, w.shape)))
+    R = orc.tri_rhs(cfg, om, w, orc.tri_traces(cfg, om, w))
+    # free stream to rounding of the terms the residual sums (their size: a discontinuous field's)
+    assert np.abs(R0).max() < 1e-13 * np.abs(R).max(), np.abs(R0).max() / np.abs(R).max()
+    total = np.einsum("en,n,env->v", J, wq, R)
+    scale = np.einsum("en,n,env->v", J, wq, np.abs(R))
+    assert np.all(np.abs(total) < 1e-13 * scale), total / scale
+    # the curvature matters: the affine scheme on the corners gives a different residual
+    oa = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc)
+    Ra = orc.tri_rhs(cfg, oa, w, orc.tri_traces(cfg, oa, w))
+    assert np.abs(Ra - R).max() > 1e-3 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_curved_limited_step_keeps_totals_and_positivity(orc, p):
+    m = inputs.tri_curved_mesh(8, 7, 0.0, 1.0, 0.0, 1.0, jitter=0.2, bump=0.15, seed=11)
+    om = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc, xy6=m.xy6)
+    cfg = _cfg(orc, p, flux=1)
+    rs, wq = orc.tri_points(p)
+    J = _jacobians(m.xy6, rs)
+
+    def ic(x, y):
+        s = 0.5 * (1 - np.tanh((np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2) - 0.25) / 0.06))
+        return np.stack([0.125 + 0.875 * s, 0 * x, 0 * x, (0.1 + 0.9 * s) / (G - 1)])
+    w = inputs.tri_nodal_field(m, rs, ic)
+    tot0 = np.einsum("en,n,env->v", J, wq, w)
+    dt = orc.tri_dt(cfg, om, w, 0.1)
+    w1, alpha = orc.tri_ssprk3_step(cfg, om, w, dt)
+    assert (alpha[0] < 1).any()
+    tot1 = np.einsum("en,n,env->v", J, wq, w1)
+    assert abs(tot1[0] - tot0[0]) < 1e-13 * abs(tot0[0]) and abs(tot1[3] - tot0[3]) < 1e-13 * abs(tot0[3])
+    P = (G - 1) * (w1[..., 3] - 0.5 * (w1[..., 1] ** 2 + w1[..., 2] ** 2) / w1[..., 0])
+    assert w1[..., 0].min() > 0 and P.min() > 0
