@@ -537,6 +537,20 @@ kbl_status kbl_tri_points(int p, double* rs, double* w);
 kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy,
                           const int32_t* nbr, const int32_t* nbr_edge, int n_bc, const double* bc,
                           void* cuda_stream);
+/* Curved (quadratic) triangles, as the paper's triangle run uses: xy6[E][6][2] (HOST), the three
+ * corners counterclockwise, then the points of edges 0, 1, 2 at mid-parameter; the element is the
+ * image of the reference triangle under the quadratic Lagrange map of these six points.  The
+ * residual takes the transformed-flux form: with adj J = |J| J^-1 at each solution point and the
+ * edge's stretch sigma = |dx/dt| / |dxi/dt| and physical unit normal at each flux point,
+ *   R_i = -(1/|J_i|) [ sum_j (Dr_ij (adj J F)_r,j + Ds_ij (adj J F)_s,j)
+ *                      + sum_q phi_i(x_q) gw_q L_f / (2 w_i) (sigma_q F*_n,q - ((adj J F)_h . nh)(x_q)) ],
+ * the solution points carrying the lumped mass w_i |J_i|, which the limiter's mean then uses;
+ * h of the time step comes from the corners.  Neighbours must share their edges' three points.
+ * Otherwise as kbl_tri_create; KBL_EINVAL also for a map that folds (|J| <= 0 at a solution
+ * point). */
+kbl_status kbl_tri_create_curved(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy6,
+                                 const int32_t* nbr, const int32_t* nbr_edge, int n_bc, const double* bc,
+                                 void* cuda_stream);
 kbl_status kbl_tri_destroy(kbl_tri* t);
 const char* kbl_tri_last_error(const kbl_tri* t);
 

@@ -294,7 +294,8 @@ int launch_bounds(const kbl_ctx* c, const double* w, const double* wf, double* b
                   cudaStream_t s);
 // limiting of explicit node sets U[E][ns][nv] (in place) with faces F[E][nf][nv], W[ns] host
 int launch_limit_nodes(const kbl_ctx* c, int E, int ns, int nf, const double* W, double* U, const double* F,
-                       const double* bnd, double* alpha, cudaStream_t s, double* F_out = nullptr);
+                       const double* bnd, double* alpha, cudaStream_t s, double* F_out = nullptr,
+                       const double* We = nullptr);
 // Bounds of the Sec. 5 stencils of affine triangles of order p (1 or 2), gathered in the kernel
 // from w[E][ns][4], wf[E][nfp][4] and the connectivity of kbl_tri (kbl_tri.cu); -1 if not covered.
 int launch_bounds_tri(const kbl_ctx* c, int E, int p, const double* w, const double* wf, const int* nbr,

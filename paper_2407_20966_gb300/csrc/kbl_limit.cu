@@ -110,6 +110,7 @@ struct NodeWeights {
 //   margin of 16 ulp of the terms proves P >= p_floor as the exact formula rounds it; only an
 //   element that fails this test forms P_min with the divisions.
 // - where alpha = 1 for every component, Eq. 47 screened in FP32 (below) and the values kept.
+// We (may be NULL): per-element mean weights We[E][ns] in place of W (curved elements: w_i |J_i|).
 // F_out (may be NULL; may alias F): the limited face values mean + alpha (f - mean), then the
 // pressure step, as for the solution values: the traces of the limited state, whose
 // interpolation weights sum to one.
@@ -117,20 +118,22 @@ template <int NV>
 __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, NodeWeights W, double* __restrict__ U,
                                                      const double* F, const double* __restrict__ bnd,
                                                      double* __restrict__ alpha_out, Phys ph, DevFlags* flags,
-                                                     double* F_out)
+                                                     double* F_out, const double* __restrict__ We)
 {
     constexpr int DIM = NV - 2;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     double* u = U + (size_t)e * ns * NV;
     const double* f = F + (size_t)e * nf * NV;
+    const double* we = We ? We + (size_t)e * ns : nullptr;   // per-element mean weights, if given
     double mean[NV], av[NV], alpha = 1.0;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         double s = 0.0, sw = 0.0;
         for (int n = 0; n < ns; n++) {
-            s += W.w[n] * u[n * NV + v];
-            sw += W.w[n];
+            const double wn = we ? we[n] : W.w[n];
+            s += wn * u[n * NV + v];
+            sw += wn;
         }
         mean[v] = s / sw;
         long long kmx = kbl_dev::dkey(u[v]), kmn = kmx;
@@ -273,16 +276,16 @@ __global__ void __launch_bounds__(128) k_limit_nodes(int E, int ns, int nf, Node
 }  // namespace
 
 int launch_limit_nodes(const kbl_ctx* c, int E, int ns, int nf, const double* W, double* U, const double* F,
-                       const double* bnd, double* alpha, cudaStream_t s, double* F_out)
+                       const double* bnd, double* alpha, cudaStream_t s, double* F_out, const double* We)
 {
     if (E == 0) return 0;
     NodeWeights nw;
     for (int n = 0; n < 64; n++) nw.w[n] = n < ns ? W[n] : 0.0;
     const unsigned grid = (unsigned)((E + 127) / 128);
     if (c->cfg.dim == 2)
-        k_limit_nodes<4><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags, F_out);
+        k_limit_nodes<4><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags, F_out, We);
     else
-        k_limit_nodes<3><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags, F_out);
+        k_limit_nodes<3><<<grid, 128, 0, s>>>(E, ns, nf, nw, U, F, bnd, alpha, c->phys, c->d_flags, F_out, We);
     return 1;
 }
 

@@ -285,6 +285,10 @@ struct TriMeshDev {
     const int* nbr;
     const int* nbr_edge;
     const double* bc;
+    // curved elements: per solution point (adj J = |J| J^-1 row by row, |J|): pj[E][ns][5]; per
+    // flux point (physical unit normal, stretch |dx/dt| / |dxi/dt|): fq[E][nfp][3]
+    const double* pj;
+    const double* fq;
 };
 
 __device__ __forceinline__ const double* tri_exterior(const TriMeshDev& m, const double* __restrict__ wf, int e,
@@ -435,6 +439,94 @@ __global__ void __launch_bounds__(128) k_tri_rhs(const double* __restrict__ w, c
         for (int v = 0; v < 4; v++) R[((size_t)e * ns + i) * 4 + v] = kbl_dev::to_f64<T>(out[i][v]);
 }
 
+// The residual on curved elements (transformed-flux form): with adj J = |J| J^-1 at each
+// solution point, Ft = adj J F; at each flux point the physical unit normal n and the stretch
+// sigma = |dx/dt| / |dxi/dt| of its edge; nh the reference edge's unit normal, L its length:
+//   R_i = -(1/|J_i|) [ sum_j (Dr_ij Ft_r,j + Ds_ij Ft_s,j)
+//                      + sum_q phi_i(x_q) gw_q L / (2 w_i) (sigma_q F*_n,q - (Ft_h . nh)(x_q)) ].
+// One thread per element, as the affine kernel.
+template <int P, typename T>
+__global__ void __launch_bounds__(128) k_tri_rhs_curved(const double* __restrict__ w, const double* __restrict__ wf,
+                                                        TriMeshDev m, TriOps o, double gamma_d, int flux,
+                                                        double* __restrict__ R)
+{
+    constexpr bool F32 = sizeof(T) == sizeof(float);
+    constexpr int ns = (P + 1) * (P + 2) / 2, nfp = 3 * (P + 1);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m.E) return;
+    const double* pj = m.pj + (size_t)e * ns * 5;
+    const double* fq = m.fq + (size_t)e * nfp * 3;
+    const T gamma = tri_in<T>(gamma_d), gm1 = F32 ? gamma - T(1) : tri_in<T>(gamma_d - 1.0);
+    T Fr[ns][4], Fs[ns][4], acc[ns][4];
+#pragma unroll
+    for (int j = 0; j < ns; j++) {
+        T q[4], Fx[4], Fy[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) q[v] = tri_in<T>(w[((size_t)e * ns + j) * 4 + v]);
+        kbl_flux<2, T>(q, 0, gm1, Fx);
+        kbl_flux<2, T>(q, 1, gm1, Fy);
+        const T a0 = tri_in<T>(pj[j * 5 + 0]), a1 = tri_in<T>(pj[j * 5 + 1]);
+        const T a2 = tri_in<T>(pj[j * 5 + 2]), a3 = tri_in<T>(pj[j * 5 + 3]);
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            Fr[j][v] = a0 * Fx[v] + a1 * Fy[v];
+            Fs[j][v] = a2 * Fx[v] + a3 * Fy[v];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < ns; i++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            T div = T(0);
+#pragma unroll
+            for (int j = 0; j < ns; j++) {
+                const T dr = F32 ? (T)o.drf[i][j] : (T)o.dr[i][j];
+                const T ds = F32 ? (T)o.dsf[i][j] : (T)o.ds[i][j];
+                div += dr * Fr[j][v] + ds * Fs[j][v];
+            }
+            acc[i][v] = div;
+        }
+#pragma unroll 1
+    for (int f = 0; f < 3; f++) {
+        // reference edges: (0,0)->(1,0), (1,0)->(0,1), (0,1)->(0,0); unit normals and lengths
+        const T nhx = f == 0 ? T(0) : (f == 1 ? T(0.70710678118654752) : T(-1));
+        const T nhy = f == 0 ? T(-1) : (f == 1 ? T(0.70710678118654752) : T(0));
+        const T L = f == 1 ? T(1.4142135623730951) : T(1);
+#pragma unroll
+        for (int k = 0; k <= P; k++) {
+            const int q = f * (P + 1) + k;
+            const T nx = tri_in<T>(fq[q * 3 + 0]), ny = tri_in<T>(fq[q * 3 + 1]), sig = tri_in<T>(fq[q * 3 + 2]);
+            T qi[4], qe[4], Fc[4];
+            const double* ext = tri_exterior(m, wf, e, f, k);
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                qi[v] = tri_in<T>(wf[((size_t)e * nfp + q) * 4 + v]);
+                qe[v] = tri_in<T>(ext[v]);
+            }
+            tri_common_flux<T>(qi, qe, nx, ny, gamma, flux, Fc);
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                T fr = T(0), fs = T(0);
+#pragma unroll
+                for (int j = 0; j < ns; j++) {
+                    const T ph = F32 ? (T)o.phiff[q][j] : (T)o.phif[q][j];
+                    fr += ph * Fr[j][v];
+                    fs += ph * Fs[j][v];
+                }
+                const T jump = L * (sig * Fc[v] - (nhx * fr + nhy * fs));
+#pragma unroll
+                for (int i = 0; i < ns; i++) acc[i][v] += (F32 ? (T)o.liftf[q][i] : (T)o.lift[q][i]) * jump;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < ns; i++) {
+        const T det = tri_in<T>(pj[i * 5 + 4]);
+#pragma unroll
+        for (int v = 0; v < 4; v++) R[((size_t)e * ns + i) * 4 + v] = kbl_dev::to_f64<T>(-acc[i][v] / det);
+    }
+}
+
 // SSP-RK3 combination (Shu-Osher form) and the traces of its result (k_tri_traces' arithmetic,
 // in its order) in one pass: a block combines the values of 32 elements, keeps them in shared
 // memory and interpolates them to the flux points.
@@ -497,6 +589,10 @@ struct kbl_tri {
     int E = 0, n_bc = 0;
     cudaStream_t stream = nullptr;
     TriGeo* d_geo = nullptr;
+    bool curved = false;
+    double* d_pj = nullptr;     // curved: [E][ns][5] adj J and |J| at the solution points
+    double* d_fq = nullptr;     // curved: [E][nfp][3] unit normal and stretch at the flux points
+    double* d_wlim = nullptr;   // curved: [E][ns] the limiter's mean weights w_i |J_i|
     int* d_nbr = nullptr;
     int* d_nbr_edge = nullptr;
     double* d_bc = nullptr;
@@ -526,6 +622,8 @@ TriMeshDev tri_dev(const kbl_tri* t)
     m.nbr = t->d_nbr;
     m.nbr_edge = t->d_nbr_edge;
     m.bc = t->d_bc;
+    m.pj = t->d_pj;
+    m.fq = t->d_fq;
     return m;
 }
 
@@ -552,7 +650,8 @@ kbl_status kbl_tri_points(int p, double* rs, double* w)
 kbl_status kbl_tri_destroy(kbl_tri* t)
 {
     if (!t) return KBL_EINVAL;
-    void* ptrs[] = {t->d_geo, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_wf, t->d_bnd, t->d_R, t->d_wa, t->d_wb, t->d_bits};
+    void* ptrs[] = {t->d_geo, t->d_nbr, t->d_nbr_edge, t->d_bc, t->d_wf,   t->d_bnd,  t->d_R,
+                    t->d_wa,  t->d_wb,  t->d_bits,     t->d_pj, t->d_fq, t->d_wlim};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (t->ev_fork) cudaEventDestroy(t->ev_fork);
@@ -563,8 +662,30 @@ kbl_status kbl_tri_destroy(kbl_tri* t)
     return KBL_OK;
 }
 
-kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy, const int32_t* nbr,
-                          const int32_t* nbr_edge, int n_bc, const double* bc, void* cuda_stream)
+}  // extern "C"
+
+namespace {
+
+// Derivatives x_r, x_s, y_r, y_s at (r, s) of the quadratic map of the six points X[6][2] (the
+// corners, then the mid-parameter points of edges 0, 1, 2): with barycentrics b1 = 1 - r - s,
+// b2 = r, b3 = s the shape functions are b1 (2 b1 - 1), b2 (2 b2 - 1), b3 (2 b3 - 1), 4 b1 b2,
+// 4 b2 b3, 4 b3 b1.
+void quad_map_deriv(const double* X, double r, double s, double d[4])
+{
+    const double b1 = 1.0 - r - s;
+    const double gr[6] = {1.0 - 4.0 * b1, 4.0 * r - 1.0, 0.0, 4.0 * (b1 - r), 4.0 * s, -4.0 * s};
+    const double gs[6] = {1.0 - 4.0 * b1, 0.0, 4.0 * s - 1.0, -4.0 * r, 4.0 * r, 4.0 * (b1 - s)};
+    d[0] = d[1] = d[2] = d[3] = 0.0;
+    for (int k = 0; k < 6; k++) {
+        d[0] += gr[k] * X[2 * k];       // x_r
+        d[1] += gs[k] * X[2 * k];       // x_s
+        d[2] += gr[k] * X[2 * k + 1];   // y_r
+        d[3] += gs[k] * X[2 * k + 1];   // y_s
+    }
+}
+
+kbl_status tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy, const double* xy6,
+                      const int32_t* nbr, const int32_t* nbr_edge, int n_bc, const double* bc, void* cuda_stream)
 {
     if (!out) return KBL_EINVAL;
     *out = nullptr;
@@ -641,12 +762,87 @@ kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, cons
     if (e == cudaSuccess && n_elem > 0)
         e = cudaMemcpy(t->d_nbr_edge, nbr_edge, (size_t)n_elem * 3 * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_bc > 0) e = cudaMemcpy(t->d_bc, bc, (size_t)n_bc * 4 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && xy6 && n_elem > 0) {
+        // curved elements: metric terms at the solution points, normals and stretch at the
+        // flux points, the limiter's mean weights
+        double rs[TRI_NSMAX][2], wq[TRI_NSMAX];
+        ws_points(cfg->p, rs, wq);
+        const int p1 = cfg->p + 1;
+        std::vector<double> pj((size_t)n_elem * ns * 5), fq((size_t)n_elem * nfp * 3), wl((size_t)n_elem * ns);
+        const double V[3][2] = {{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}};
+        bool ok = true;
+        for (int el = 0; el < n_elem && ok; el++) {
+            const double* X = xy6 + (size_t)el * 12;
+            for (size_t i = 0; i < ns; i++) {
+                double d[4];
+                quad_map_deriv(X, rs[i][0], rs[i][1], d);
+                const double det = d[0] * d[3] - d[1] * d[2];
+                ok = ok && det > 0.0;
+                double* o = &pj[((size_t)el * ns + i) * 5];
+                o[0] = d[3];    // adj J = [[y_s, -x_s], [-y_r, x_r]]
+                o[1] = -d[1];
+                o[2] = -d[2];
+                o[3] = d[0];
+                o[4] = det;
+                wl[(size_t)el * ns + i] = wq[i] * det;
+            }
+            for (int f = 0; f < 3; f++) {
+                const double dvx = V[(f + 1) % 3][0] - V[f][0], dvy = V[(f + 1) % 3][1] - V[f][1];
+                const double L = std::sqrt(dvx * dvx + dvy * dvy);
+                for (int k = 0; k < p1; k++) {
+                    const double tt = 0.5 * (1.0 + gl.x[k]);
+                    double d[4];
+                    quad_map_deriv(X, V[f][0] + tt * dvx, V[f][1] + tt * dvy, d);
+                    const double tx = d[0] * dvx + d[1] * dvy, ty = d[2] * dvx + d[3] * dvy;
+                    const double len = std::sqrt(tx * tx + ty * ty);
+                    ok = ok && len > 0.0;
+                    double* o = &fq[((size_t)el * nfp + f * p1 + k) * 3];
+                    o[0] = ty / len;
+                    o[1] = -tx / len;
+                    o[2] = len / L;
+                }
+            }
+        }
+        if (!ok) {
+            kbl_tri_destroy(t);
+            return KBL_EINVAL;   // a folded or degenerate curved element
+        }
+        t->curved = true;
+        A((void**)&t->d_pj, pj.size() * sizeof(double));
+        A((void**)&t->d_fq, fq.size() * sizeof(double));
+        A((void**)&t->d_wlim, wl.size() * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemcpy(t->d_pj, pj.data(), pj.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(t->d_fq, fq.data(), fq.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(t->d_wlim, wl.data(), wl.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         kbl_tri_destroy(t);
         return e == cudaErrorMemoryAllocation ? KBL_ENOMEM : KBL_ECUDA;
     }
     *out = t;
     return KBL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kbl_status kbl_tri_create(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy, const int32_t* nbr,
+                          const int32_t* nbr_edge, int n_bc, const double* bc, void* cuda_stream)
+{
+    return tri_create(out, cfg, n_elem, xy, nullptr, nbr, nbr_edge, n_bc, bc, cuda_stream);
+}
+
+kbl_status kbl_tri_create_curved(kbl_tri** out, const kbl_config* cfg, int n_elem, const double* xy6,
+                                 const int32_t* nbr, const int32_t* nbr_edge, int n_bc, const double* bc,
+                                 void* cuda_stream)
+{
+    if (!out) return KBL_EINVAL;
+    *out = nullptr;
+    if (n_elem < 0 || (n_elem > 0 && !xy6)) return KBL_EINVAL;
+    std::vector<double> corners((size_t)std::max(1, n_elem) * 6);
+    for (long i = 0; i < (long)n_elem * 6; i++) corners[i] = xy6[(i / 6) * 12 + i % 6];
+    return tri_create(out, cfg, n_elem, corners.data(), xy6, nbr, nbr_edge, n_bc, bc, cuda_stream);
 }
 
 const char* kbl_tri_last_error(const kbl_tri* t) { return t ? t->err.c_str() : "null triangle mesh"; }
@@ -689,10 +885,20 @@ kbl_status tri_residual_on(kbl_tri* t, const double* w, const double* wf, double
         const TriMeshDev md = tri_dev(t);
         const double gam = t->cfg.gamma;
         const int fl = t->cfg.flux;
-        if (t->cfg.p == 1 && f32) k_tri_rhs<1, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
-        else if (t->cfg.p == 1) k_tri_rhs<1, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
-        else if (f32) k_tri_rhs<2, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
-        else k_tri_rhs<2, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        if (t->curved) {
+            if (t->cfg.p == 1 && f32) k_tri_rhs_curved<1, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+            else if (t->cfg.p == 1) k_tri_rhs_curved<1, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+            else if (f32) k_tri_rhs_curved<2, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+            else k_tri_rhs_curved<2, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        } else if (t->cfg.p == 1 && f32) {
+            k_tri_rhs<1, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        } else if (t->cfg.p == 1) {
+            k_tri_rhs<1, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        } else if (f32) {
+            k_tri_rhs<2, float><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        } else {
+            k_tri_rhs<2, double><<<grid, 128, 0, s>>>(w, wf, md, t->ops, gam, fl, R);
+        }
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
@@ -756,7 +962,7 @@ kbl_status kbl_tri_step(kbl_tri* t, double* w, double dt)
         else
             k_tri_combine_traces<2><<<gct, 256, 0, t->stream>>>(s, w, ws, t->d_R, dt, outs[s], t->d_wf, t->E, t->ops);
         launch_limit_nodes(t->ctx, t->E, ns, nfp, t->ops.wq, outs[s], t->d_wf, t->d_bnd, nullptr, t->stream,
-                           t->d_wf);
+                           t->d_wf, t->curved ? t->d_wlim : nullptr);
         ws = outs[s];
     }
     const cudaError_t e = cudaGetLastError();

@@ -114,6 +114,8 @@ _SIGS = {
     "kbl_forward_segment": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "kbl_tri_points": (C.c_int, [C.c_int, _P, _P]),
     "kbl_tri_create": (C.c_int, [C.POINTER(_P), C.POINTER(KblConfig), C.c_int, _P, _P, _P, C.c_int, _P, _P]),
+    "kbl_tri_create_curved": (C.c_int, [C.POINTER(_P), C.POINTER(KblConfig), C.c_int, _P, _P, _P, C.c_int, _P,
+                                        _P]),
     "kbl_tri_destroy": (C.c_int, [_P]),
     "kbl_tri_last_error": (C.c_char_p, [_P]),
     "kbl_tri_traces": (C.c_int, [_P, _P, _P]),
@@ -562,7 +564,7 @@ class TriMesh:
     nbr[E][3] (neighbour or -(b+1)), nbr_edge[E][3], bc[n_bc][4] -- host arrays.  Solution
     arrays are CUDA float64 tensors w[E][ns][4]."""
 
-    def __init__(self, p, xy, nbr, nbr_edge, bc, precision=FP64, stream=None, **overrides):
+    def __init__(self, p, xy, nbr, nbr_edge, bc, precision=FP64, stream=None, xy6=None, **overrides):
         lib = load()
         cfg = KblConfig()
         if lib.kbl_config_default(C.byref(cfg), 2, int(p)) != OK:
@@ -578,8 +580,13 @@ class TriMesh:
         self.E = int(xy.reshape(-1, 6).shape[0])
         n_bc = int(bc.reshape(-1, 4).shape[0]) if bc.size else 0
         h = C.c_void_p()
-        st = lib.kbl_tri_create(C.byref(h), C.byref(cfg), self.E, px, pn, pe, n_bc, pb if n_bc else None,
-                                stream if stream is not None else _current_stream())
+        s = stream if stream is not None else _current_stream()
+        if xy6 is None:
+            st = lib.kbl_tri_create(C.byref(h), C.byref(cfg), self.E, px, pn, pe, n_bc, pb if n_bc else None, s)
+        else:   # curved elements: the corners and the edges' mid-parameter points
+            x6, p6 = _host(xy6, np.float64, "xy6")
+            st = lib.kbl_tri_create_curved(C.byref(h), C.byref(cfg), self.E, p6, pn, pe, n_bc,
+                                           pb if n_bc else None, s)
         if st != OK:
             raise KblError(st, "tri_create")
         self._h, self._lib = h, lib

@@ -9,6 +9,9 @@
   bounds     kbl_bounds_stencil of the device's stencils vs orc.bounds_stencil: 1e-12 / 1e-5
   step       kbl_tri_step                   vs orc.tri_ssprk3_step   1e-12 FP64; FP32-mixed (bounds
              and residual): 1e-5 where the step is well conditioned (a blast, density >= 0.125)
+  curved     kbl_tri_create_curved meshes (quadratic edges): residual 1e-12 / 1e-5 and steps
+             1e-12 / 1e-5 against the checker's curved scheme; straight midpoints reproduce the
+             affine path to 1e-12; a folded element is KBL_EINVAL
 Meshes of 2 x nx x ny jittered triangles span several thread blocks with a ragged tail, periodic
 and with boundary states, for every common flux.
 """
@@ -336,3 +339,81 @@ def test_tiny_meshes_step(orc, p, nx, ny, periodic):
     tm.check()
     err = np.abs(wd.cpu().numpy() - ref) / _elem_scale(ref)
     assert err.max() < TOL_FP64, err.max()
+
+
+# ---- curved (quadratic) elements --------------------------------------------------------------
+def _setup_curved(orc, p, nx, ny, periodic, flux=0, precision=0, seed=5, bump=0.15, straight=False):
+    from paper_2407_20966_gb300 import kbl
+    m = inputs.tri_curved_mesh(nx, ny, 0.0, 1.0, 0.0, 0.9, jitter=0.2, bump=bump, seed=seed,
+                               periodic=(periodic, periodic))
+    if straight:
+        m.xy6 = np.concatenate([m.xy, 0.5 * (m.xy + np.roll(m.xy, -1, axis=1))], axis=1)
+    rng = np.random.default_rng(seed)
+    m.bc = np.stack([_blast(np.array(0.0), np.array(0.0)), _blast(np.array(1.0), np.array(0.5))])
+    om = orc.TriMesh(m.xy, m.nbr, m.nbr_edge, m.bc, xy6=m.xy6)
+    cfg = orc.Config(dim=2, p=p, nu=(16, 16), flux=flux)
+    tm = kbl.TriMesh(p, m.xy, m.nbr, m.nbr_edge, m.bc, precision=precision, flux=flux, nu=(16, 16), xy6=m.xy6)
+    rs, _ = orc.tri_points(p)
+    w = inputs.tri_nodal_field(m, rs, _blast)
+    w = w * (1 + 0.02 * rng.uniform(-1, 1, w.shape))
+    return m, om, cfg, tm, np.ascontiguousarray(w)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("p,flux,periodic", [(1, 0, True), (2, 1, False), (2, 2, True)])
+def test_curved_residual(orc, p, flux, periodic, precision):
+    import torch
+    m, om, cfg, tm, w = _setup_curved(orc, p, 13, 11, periodic, flux, precision)
+    E = m.n_elem
+    wf_ref = orc.tri_traces(cfg, om, w)
+    wd, wf_in = _dev(w), _dev(wf_ref)
+    S_d = torch.zeros(E, tm.nstencil, 4, dtype=torch.float64, device="cuda")
+    tm.gather_stencil(wd, wf_in, S_d)
+    R_d = torch.zeros_like(wd)
+    tm.residual(wd, wf_in, R_d)
+    R_ref = orc.tri_rhs(cfg, om, w, wf_ref)
+    err = np.abs(R_d.cpu().numpy() - R_ref) / np.maximum(np.abs(R_ref), _residual_scale(m, w, S_d.cpu().numpy()))
+    assert err.max() < (TOL_FP64 if precision == 0 else TOL_FP32), err.max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("p,flux,periodic", [(1, 1, True), (2, 1, False), (2, 0, True)])
+def test_curved_step(orc, p, flux, periodic, precision):
+    m, om, cfg, tm, w = _setup_curved(orc, p, 12, 11, periodic, flux, precision)
+    wd = _dev(w)
+    dt = orc.tri_dt(cfg, om, w, 0.2)
+    ref, alpha = w, None
+    for _ in range(2 if precision == 0 else 1):   # FP32-mixed: one step, as on affine meshes
+        tm.step(wd, dt)
+        ref, alpha = orc.tri_ssprk3_step(cfg, om, ref, dt)
+    tm.check()
+    assert (alpha[0] < 1).any()
+    err = np.abs(wd.cpu().numpy() - ref) / _elem_scale(ref)
+    assert err.max() < (TOL_FP64 if precision == 0 else TOL_FP32), err.max()
+
+
+def test_curved_with_straight_edges_equals_affine_on_the_device(orc):
+    """The quadratic map of straight edges is the affine one: the curved path's step equals the
+    affine path's to rounding."""
+    from paper_2407_20966_gb300 import kbl
+    m, om, cfg, tc, w = _setup_curved(orc, 2, 9, 8, True, flux=1, straight=True)
+    ta = kbl.TriMesh(2, m.xy, m.nbr, m.nbr_edge, m.bc, flux=1, nu=(16, 16))
+    wc, wa = _dev(w), _dev(w)
+    dt = orc.tri_dt(cfg, om, w, 0.2)
+    for _ in range(2):
+        tc.step(wc, dt)
+        ta.step(wa, dt)
+    tc.check()
+    ta.check()
+    a = wa.cpu().numpy()
+    err = np.abs(wc.cpu().numpy() - a) / _elem_scale(a)
+    assert err.max() < 1e-12, err.max()
+
+
+def test_curved_rejects_a_folded_element(orc):
+    from paper_2407_20966_gb300 import kbl
+    m = inputs.tri_curved_mesh(3, 3, 0.0, 1.0, 0.0, 1.0, bump=0.15)
+    xy6 = m.xy6.copy()
+    xy6[0, 3] = xy6[0, 2] + 2.0 * (xy6[0, 2] - 0.5 * (xy6[0, 0] + xy6[0, 1]))   # edge 0 pulled past the opposite corner
+    with pytest.raises(kbl.KblError):
+        kbl.TriMesh(1, m.xy, m.nbr, m.nbr_edge, m.bc, xy6=xy6)
