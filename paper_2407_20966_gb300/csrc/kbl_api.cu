@@ -224,8 +224,9 @@ cudaError_t dalloc(T** p, size_t count)
 }
 
 // Issue one full SSP-RK3 step on stream s (for capture): the traces and the clipped time step of w
-// in one kernel, then per stage the bounds, the residual and the stage + limiter kernel, which also
-// writes the next stage's traces (stages 0 and 1) or advances the clock (stage 2): 10 kernels.
+// (one kernel; with a side stream, two kernels on two branches), then per stage the bounds, the
+// residual and the stage + limiter kernel, which also writes the next stage's traces (stages 0
+// and 1) or advances the clock (stage 2): 10 kernels, 11 with a side stream.
 // The kernels of one step, for capture into the step graph.  With a side stream s2 and its
 // events, each stage's residual runs on a branch of its own beside the bounds (both read only
 // the stage input and its traces): the residual is latency-bound and fills issue slots the
@@ -234,8 +235,18 @@ int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s, cudaStream_t s
                cudaEvent_t* ev = nullptr)
 {
     int n = 0, r;
-    if ((r = launch_traces_dt(c, w, c->d_wf, cfl, s)) < 0) return -1;
-    n += r;
+    if (s2) {
+        // the time step on the side branch, beside the traces: only the stage kernels read it, and
+        // they run after the branch joins (the first residual follows it on the same stream)
+        if (cudaEventRecord(ev[6], s) != cudaSuccess || cudaStreamWaitEvent(s2, ev[6], 0) != cudaSuccess) return -1;
+        if ((r = launch_dt_step(c, w, cfl, s2)) < 0) return -1;
+        n += r;
+        if ((r = launch_traces(c, w, c->d_wf, s)) < 0) return -1;
+        n += r;
+    } else {
+        if ((r = launch_traces_dt(c, w, c->d_wf, cfl, s)) < 0) return -1;
+        n += r;
+    }
     const double* wn = w;
     const double* ws = w;
     double* outs[3] = {c->d_wa, c->d_wb, w};
@@ -629,7 +640,7 @@ kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
         c->graph = nullptr;
         c->graph_w = nullptr;
         cudaStream_t cap = nullptr, side = nullptr;
-        cudaEvent_t ev[6] = {};
+        cudaEvent_t ev[7] = {};
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         // the residual's branch at the highest priority: its blocks are placed as soon as the
         // bounds kernel's blocks retire, instead of after all of them
@@ -637,10 +648,10 @@ kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
         if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
         if (e == cudaSuccess && c->overlap_rhs)
             e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_hi);
-        for (int k = 0; k < 6 && e == cudaSuccess && side; k++)
+        for (int k = 0; k < 7 && e == cudaSuccess && side; k++)
             e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
         auto release = [&]() {
-            for (int k = 0; k < 6; k++)
+            for (int k = 0; k < 7; k++)
                 if (ev[k]) cudaEventDestroy(ev[k]);
             if (side) cudaStreamDestroy(side);
             if (cap) cudaStreamDestroy(cap);

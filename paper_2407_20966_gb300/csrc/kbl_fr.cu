@@ -200,19 +200,20 @@ __global__ void k_time_advance(double* scal) { scal[1] += scal[0]; }
 // step (as k_dt with its arithmetic type T), whose block minima meet in dtbits; the last block to
 // finish (a counter of finished blocks) decodes the step, clips it to the end time and resets the
 // reduction word and the counter for the next step, so that neither a memset nor a finalizing
-// kernel is needed.
+// kernel is needed.  TRACES = false: the time step alone (one thread per solution point), for
+// a step graph that runs it on a branch beside k_traces: only the stage kernels read it.
 // ---------------------------------------------------------------------------
-template <int DIM, int N, typename T>
+template <int DIM, int N, typename T, bool TRACES = true>
 __global__ void __launch_bounds__(256) k_traces_dt(const double* __restrict__ w, double* __restrict__ wf, MeshDev m,
                                                    FrOps ops, double gamma_d, double cfl,
                                                    unsigned long long* dtbits, unsigned* blocks_done, double* scal)
 {
     constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
-    constexpr int NK = NS > NFP ? NS : NFP;
+    constexpr int NK = (TRACES && NFP > NS) ? NFP : NS;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = t < (size_t)m.E * NK;
     const int e = in ? (int)(t / NK) : 0, k = (int)(t % NK);
-    if (in && k < NFP) {   // traces: the operations and order of k_traces
+    if (TRACES && in && k < NFP) {   // traces: the operations and order of k_traces
         const int fp = k;
         const int f = (DIM == 1) ? fp : fp / N;
         const int kk = (DIM == 1) ? 0 : fp % N;
@@ -311,11 +312,33 @@ int run_traces_dt(const kbl_ctx* c, const double* w, double* wf, double cfl, cud
     return 1;
 }
 
+// The time step of k_traces_dt alone: the same per-node arithmetic and the same exact minimum,
+// so the same dt bit for bit.
+template <int DIM, int N>
+int run_dt_step(const kbl_ctx* c, const double* w, double cfl, cudaStream_t s)
+{
+    const size_t total = (size_t)c->E * kbl_ns<DIM>(N);
+    if (total == 0) return 0;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    if (c->cfg.precision == KBL_FP32_MIXED)
+        k_traces_dt<DIM, N, float, false><<<grid, 256, 0, s>>>(w, nullptr, mesh_of(c), c->ops, c->phys.gamma, cfl,
+                                                               c->d_dtbits, c->d_blocks_done, c->d_scal);
+    else
+        k_traces_dt<DIM, N, double, false><<<grid, 256, 0, s>>>(w, nullptr, mesh_of(c), c->ops, c->phys.gamma, cfl,
+                                                                c->d_dtbits, c->d_blocks_done, c->d_scal);
+    return 1;
+}
+
 }  // namespace
 
 int launch_traces_dt(const kbl_ctx* c, const double* w, double* wf, double cfl, cudaStream_t s)
 {
     KBL_DISPATCH(c->cfg.dim, c->cfg.p + 1, run_traces_dt, c, w, wf, cfl, s);
+}
+
+int launch_dt_step(const kbl_ctx* c, const double* w, double cfl, cudaStream_t s)
+{
+    KBL_DISPATCH(c->cfg.dim, c->cfg.p + 1, run_dt_step, c, w, cfl, s);
 }
 
 MeshDev mesh_of(const kbl_ctx* c)

@@ -286,6 +286,8 @@ int launch_dt(const kbl_ctx* c, const double* w, double cfl, double* dt_out, int
 int launch_time_advance(const kbl_ctx* c, cudaStream_t s);
 // the first kernel of kbl_step: face traces of w and the clipped time step into scal[0] in one pass
 int launch_traces_dt(const kbl_ctx* c, const double* w, double* wf, double cfl, cudaStream_t s);
+// the time step of launch_traces_dt alone (the same dt bit for bit), for a branch beside launch_traces
+int launch_dt_step(const kbl_ctx* c, const double* w, double cfl, cudaStream_t s);
 // the stage kernel of kbl_step (dt from scal[0]): stage + limiter, then the next stage's traces
 // (wf_next, may be nullptr) or the clock update (advance)
 int launch_stage_step(const kbl_ctx* c, int stage, const double* wn, const double* ws, const double* R,
