@@ -514,22 +514,41 @@ def test_run_host_ensemble_matches_device_steps(orc):
     ctx.check()
 
 
+@pytest.mark.parametrize("strict", [False, True])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_step_residual_branch_is_bitwise_serial(orc, precision):
-    """The step graph with each stage's residual on a branch beside its bounds (the default)
-    gives the serial graph's state bit for bit: the same kernels read the same inputs."""
+@pytest.mark.parametrize("dim,p,n", [(2, 3, (13, 11)), (2, 1, (9, 7)), (2, 2, (12, 10)), (2, 4, (11, 9)),
+                                     (1, 3, 45)])
+def test_step_residual_branch_is_bitwise_serial(orc, precision, dim, p, n, strict):
+    """The step graph with branches (the default: each stage's residual beside its bounds, the time
+    step beside the traces) gives the serial graph's state and limiter counters bit for bit: the
+    same arithmetic and the same decisions.  Discontinuous fields, so that the screen leaves elements
+    to the exact limiter; element counts that end in a partial block; with the strict bounds
+    (r = 0, k = 8) the limiter cuts elements."""
     from paper_2407_20966_gb300 import kbl
-    ctx, _ = both(orc, 2, 3, (32, 32), precision=precision)
-    mesh, w = mesh_and_field(orc, 2, 3, (13, 11), seed=21, kind="disc", periodic=True)
+    nu = (64,) if dim == 1 else (16, 16)
+    kw = dict(r_fac=0.0, k=8.0) if strict else {}
+    ctx, _ = both(orc, dim, p, nu, precision=precision, **kw)
+    mesh, w = mesh_and_field(orc, dim, p, n, seed=21, kind="disc", periodic=True)
+    if strict:   # blasts in every seventh element: shocks the limiter has to cut
+        w = w.copy()
+        w[-1, ::7] *= 1e3
     upload(ctx, orc, mesh)
-    out = []
+    out, cnt = [], []
     for ov in (1, 0):
         ctx.set_tuning(kbl.TUNE_RHS_OVERLAP, ov)
         assert ctx.get_tuning(kbl.TUNE_RHS_OVERLAP) == ov
         wd = to_dev(w)
         ctx.set_time(0.0)
+        ctx.counters()   # reading the counters clears them
         for _ in range(3):
             ctx.step(wd, 0.05)
-        ctx.check()
+        st, c1 = ctx.counters()
+        assert st == 0, st
         out.append(wd.cpu().numpy())
+        cnt.append({k: np.asarray(c1[k]) for k in c1})
+        assert ctx.time() > 0.0
     np.testing.assert_array_equal(out[0], out[1])
+    if strict:
+        assert cnt[0]["limited_elements"] > 0 and cnt[0]["pressure_relimits"] > 0   # the exact limiter cut
+    for k in cnt[0]:
+        np.testing.assert_array_equal(cnt[0][k], cnt[1][k], err_msg=k)
