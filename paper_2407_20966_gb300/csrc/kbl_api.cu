@@ -665,7 +665,9 @@ kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
             release();
             return cuda_fail(c, e, "begin capture");
         }
+        c->pdl = side != nullptr;   // the main chain of the branched graph as programmatic dependents
         const int n = issue_step(c, w, cfl, cap, side, ev);
+        c->pdl = false;
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap, &g);
         release();

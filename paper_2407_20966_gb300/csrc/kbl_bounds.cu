@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(B2f32<NX, TYSEL>::NT, B2f32<NX, TYSEL>::MINB)
 k_bounds2d_f32(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Phys ph,
                double* __restrict__ bnd, DevFlags* flags)
 {
+    kbl_grid_dep_sync();
     __shared__ Bounds2dF32Smem<N, NX, TYSEL> sm;
     bounds2d_f32_element<N, NX, TYSEL, PAD>(sm, w, wf, m, blockIdx.x, ph, bnd, flags);
 }
@@ -193,15 +194,19 @@ template <int N, int NX>
 int run2d(const kbl_ctx* c, const double* w, const double* wf, double* bnd, cudaStream_t s)
 {
     if (c->cfg.precision == KBL_FP32_MIXED) {
+        const MeshDev m = mesh_of(c);
         if (c->cfg.nu[0] != NX || c->phys.qwf)   // padded tile or weight table: the 4x4 (or narrower) tile
-            k_bounds2d_f32<N, NX, 0, true><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd,
-                                                                            c->d_flags);
+            kbl_launch(k_bounds2d_f32<N, NX, 0, true>, c->E, B2f32<NX, 0>::NT, 0, s, c->pdl, w, wf, m, c->phys, bnd,
+                       c->d_flags);
         else if (NX >= 32 && c->bounds_tile == 1)
-            k_bounds2d_f32<N, NX, 2><<<c->E, B2f32<NX, 2>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+            kbl_launch(k_bounds2d_f32<N, NX, 2>, c->E, B2f32<NX, 2>::NT, 0, s, c->pdl, w, wf, m, c->phys, bnd,
+                       c->d_flags);
         else if (NX >= 32 && c->bounds_tile == 2)
-            k_bounds2d_f32<N, NX, 3><<<c->E, B2f32<NX, 3>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+            kbl_launch(k_bounds2d_f32<N, NX, 3>, c->E, B2f32<NX, 3>::NT, 0, s, c->pdl, w, wf, m, c->phys, bnd,
+                       c->d_flags);
         else
-            k_bounds2d_f32<N, NX, 0><<<c->E, B2f32<NX, 0>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
+            kbl_launch(k_bounds2d_f32<N, NX, 0>, c->E, B2f32<NX, 0>::NT, 0, s, c->pdl, w, wf, m, c->phys, bnd,
+                       c->d_flags);
     } else
         k_bounds2d_f64<N, NX><<<c->E, B2f64<NX>::NT, 0, s>>>(w, wf, mesh_of(c), c->phys, bnd, c->d_flags);
     return 1;

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256) k_traces(const double* __restrict__ w, do
                                                 int E, FrOps ops)
 {
     constexpr int NS = kbl_ns<DIM>(N), NFP = kbl_nfp<DIM>(N), NV = DIM + 2;
+    kbl_grid_dep_sync();
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)E * NFP) return;
     const int e = (int)(t / NFP), fp = (int)(t % NFP);
@@ -52,7 +53,7 @@ int run_traces(const kbl_ctx* c, const double* w, double* wf, cudaStream_t s)
     const unsigned grid = (unsigned)((total + bs - 1) / bs);
     // FP64 in both precision modes: converting each input to FP32 costs an FP64-pipe slot
     // on GB300, as much as the FP64 multiply-add it would replace.
-    k_traces<DIM, N, double><<<grid, bs, 0, s>>>(w, wf, c->E, c->ops);
+    kbl_launch(k_traces<DIM, N, double>, grid, bs, 0, s, c->pdl, w, wf, c->E, c->ops);
     return 1;
 }
 

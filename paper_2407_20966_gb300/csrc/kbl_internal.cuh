@@ -84,6 +84,35 @@ inline void kbl_phys_derive(Phys& p)
     p.rel_hif = (float)p.rel_hi;
 }
 
+// Programmatic dependent launch inside a step graph: a kernel of the step's main chain first
+// waits until the grids it depends on have completed and their writes are visible (it reads
+// their outputs and overwrites buffers they read), then lets its own dependent grid be
+// launched, whose blocks take SM slots as this grid's blocks retire and wait there in turn.
+// Launched without the programmatic attribute, both are no-ops.
+__device__ __forceinline__ void kbl_grid_dep_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `kernel` on s; with pdl, as a programmatic dependent of the work before it on s.
+template <typename... KArgs, typename... Args>
+cudaError_t kbl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // FP32 approximation of a double by truncating its significand, with integer operations only
 // (a conversion instruction would cost an FP64-pipe slot): |result - x| <= 2^-23 |x| for
 // 2^-126 <= |x| < 2^128, 0 below that range (|error| < 2^-126), infinity above it.
@@ -238,6 +267,8 @@ struct kbl_ctx {
     float* d_tcop = nullptr;    // split residual operator of the tensor-core residual, or nullptr
     int rhs_tc = 0;             // knob: 1 residual products on the tensor cores where covered, 0 CUDA cores
     int overlap_rhs = 1;        // knob: 1 each stage's residual on a graph branch beside its bounds
+    mutable bool pdl = false;   // set while the branched step graph is captured: the main chain's
+                                // launches are programmatic dependents (kbl_grid_dep_sync)
     std::string err;
     int64_t launches = 0;
     int bounds_tile = 0;        // FP32 bounds thread tile: 0 = 4x4 nodes, 1 = 4x2 nodes

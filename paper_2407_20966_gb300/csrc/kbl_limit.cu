@@ -54,6 +54,7 @@ k_stage_limit_step(int stage, const double* wn, const double* ws, const double* 
                    int advance, int E, FrOps ops, Phys ph, DevFlags* flags)
 {
     using SH = LimShape<DIM, N>;
+    kbl_grid_dep_sync();
     __shared__ kbl_dev::LimSmem<DIM, N, SH::EPB> sm;
     const double dt = scal[0];
     const int e0 = blockIdx.x * SH::EPB;
@@ -71,8 +72,8 @@ int run_stage_step(const kbl_ctx* c, int stage, const double* wn, const double* 
     using SH = LimShape<DIM, N>;
     if (c->E == 0) return 0;
     const unsigned grid = (unsigned)((c->E + SH::EPB - 1) / SH::EPB);
-    k_stage_limit_step<DIM, N><<<grid, SH::NT, 0, s>>>(stage, wn, ws, R, bnd, c->d_scal, wout, wf_next, advance, c->E,
-                                                     c->ops, c->phys, c->d_flags);
+    kbl_launch(k_stage_limit_step<DIM, N>, grid, SH::NT, 0, s, c->pdl, stage, wn, ws, R, bnd, c->d_scal, wout, wf_next,
+               advance, c->E, c->ops, c->phys, c->d_flags);
     return 1;
 }
 
