@@ -228,9 +228,11 @@ cudaError_t dalloc(T** p, size_t count)
 // residual and the stage + limiter kernel, which also writes the next stage's traces (stages 0
 // and 1) or advances the clock (stage 2): 10 kernels, 11 with a side stream.
 // The kernels of one step, for capture into the step graph.  With a side stream s2 and its
-// events, each stage's residual runs on a branch of its own beside the bounds (both read only
-// the stage input and its traces): the residual is latency-bound and fills issue slots the
-// ALU-bound bounds kernel leaves, instead of running after it.
+// events, the time step and each stage's residual run on a branch of their own beside the
+// traces and the bounds (they read only the stage input and its traces).  The bounds kernel
+// holds most issue slots and residency, so a residual beside it still costs about its own time;
+// the branch mainly takes the launches off the main chain, whose kernels (traces, bounds, stage)
+// are programmatic dependents (ctx->pdl).
 int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s, cudaStream_t s2 = nullptr,
                cudaEvent_t* ev = nullptr)
 {
