@@ -289,10 +289,14 @@ typedef enum { KBL_TUNE_BOUNDS_TILE = 0, KBL_TUNE_RHS_TC = 1, KBL_TUNE_RHS_OVERL
  * hi + lo pairs, FP32 accumulation; element tiles staged by TMA), 0 on the CUDA cores.  Other
  * orders, 1D and FP64 always use the CUDA cores.  Default 0 (CUDA cores: measured faster on the
  * benchmark workloads).  Setting it drops the captured step graph. */
-/* KBL_TUNE_RHS_OVERLAP: 1 (default) the step graph runs each stage's residual on a branch of its
- * own beside the stage's bounds (both read only the stage input and its traces; the stage
- * kernel waits for both), 0 one after the other.  The same kernels run either way: results are
- * identical.  Setting it drops the captured step graph. */
+/* KBL_TUNE_RHS_OVERLAP: 1 (default) the step graph overlaps its kernels: the time step runs on a
+ * branch of its own beside the traces, and the main chain (traces, then per stage residual,
+ * bounds, stage + limiter) launches each kernel as a programmatic dependent of the one before,
+ * so that its blocks start as the previous kernel's last blocks finish; the stage kernel forms
+ * the stage combination and the bound-free part of its screen before the bounds kernel has
+ * finished, and waits for it before it reads the bounds.  0: one ordinary launch after the
+ * other.  The same arithmetic runs either way: results are identical.  Setting it drops the
+ * captured step graph. */
 kbl_status kbl_set_tuning(kbl_ctx* ctx, int key, int value);   /* KBL_EINVAL for an unknown key or value */
 kbl_status kbl_get_tuning(const kbl_ctx* ctx, int key, int* value);
 

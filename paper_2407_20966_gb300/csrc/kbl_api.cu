@@ -223,16 +223,17 @@ cudaError_t dalloc(T** p, size_t count)
     return cudaMalloc((void**)p, count * sizeof(T));
 }
 
-// Issue one full SSP-RK3 step on stream s (for capture): the traces and the clipped time step of w
-// (one kernel; with a side stream, two kernels on two branches), then per stage the bounds, the
-// residual and the stage + limiter kernel, which also writes the next stage's traces (stages 0
-// and 1) or advances the clock (stage 2): 10 kernels, 11 with a side stream.
-// The kernels of one step, for capture into the step graph.  With a side stream s2 and its
-// events, the time step and each stage's residual run on a branch of their own beside the
-// traces and the bounds (they read only the stage input and its traces).  The bounds kernel
-// holds most issue slots and residency, so a residual beside it still costs about its own time;
-// the branch mainly takes the launches off the main chain, whose kernels (traces, bounds, stage)
-// are programmatic dependents (ctx->pdl).
+// Issue one full SSP-RK3 step on stream s (for capture): the traces and the clipped time step of w,
+// then per stage the residual, the bounds and the stage + limiter kernel, which also writes the
+// next stage's traces (stages 0 and 1) or advances the clock (stage 2).  Without a side stream:
+// 10 ordinary launches in one chain (traces and time step in one kernel).  With a side stream s2
+// and its events (ctx->pdl set): the time step runs on the side branch beside the traces, and the
+// main chain's kernels (traces, residual, bounds, stage) are programmatic dependents, each
+// waiting for its predecessor before it touches memory and letting its own dependent launch at
+// once; the stage kernel waits only before it reads the bounds (kbl_limit_body.cuh), so its
+// combination and screen overlap the bounds launch's last blocks: 11 kernels.  A residual on a
+// branch beside the bounds measured no better than in the chain: the bounds kernel holds the
+// issue slots and the residency either way.
 int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s, cudaStream_t s2 = nullptr,
                cudaEvent_t* ev = nullptr)
 {
@@ -252,22 +253,16 @@ int issue_step(kbl_ctx* c, double* w, double cfl, cudaStream_t s, cudaStream_t s
     const double* wn = w;
     const double* ws = w;
     double* outs[3] = {c->d_wa, c->d_wb, w};
+    // with a side stream the main chain is residual -> bounds -> stage per stage, each a
+    // programmatic dependent of the one before; the time step (side branch) joins before the
+    // first residual
+    if (s2 && cudaEventRecord(ev[0], s2) != cudaSuccess) return -1;
     for (int st = 0; st < 3; st++) {
-        if (s2) {
-            if (cudaEventRecord(ev[2 * st], s) != cudaSuccess || cudaStreamWaitEvent(s2, ev[2 * st], 0) != cudaSuccess)
-                return -1;
-            if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s2)) < 0) return -1;
-            n += r;
-            if (cudaEventRecord(ev[2 * st + 1], s2) != cudaSuccess) return -1;
-            if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
-            n += r;
-            if (cudaStreamWaitEvent(s, ev[2 * st + 1], 0) != cudaSuccess) return -1;
-        } else {
-            if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
-            n += r;
-            if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
-            n += r;
-        }
+        if (s2 && st == 0 && cudaStreamWaitEvent(s, ev[0], 0) != cudaSuccess) return -1;
+        if ((r = launch_rhs(c, ws, c->d_wf, c->d_R, s)) < 0) return -1;
+        n += r;
+        if ((r = launch_bounds(c, ws, c->d_wf, c->d_bnd, s)) < 0) return -1;
+        n += r;
         if ((r = launch_stage_step(c, st, wn, ws, c->d_R, c->d_bnd, outs[st], st < 2 ? c->d_wf : nullptr, st == 2, s)) <
             0)
             return -1;

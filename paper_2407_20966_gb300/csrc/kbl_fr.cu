@@ -119,6 +119,7 @@ k_rhs(const double* __restrict__ w, const double* __restrict__ wf, MeshDev m, Fr
       double gamma_d, double* __restrict__ R, int flux)
 {
     using SH = RhsShape<DIM, N>;
+    kbl_grid_dep_sync();
     __shared__ kbl_dev::RhsSmem<DIM, N, T, SH::EPB> sm;
     kbl_dev::rhs_block<DIM, N, T, SH::EPB>(sm, SH::NT, w, wf, m, ops, gamma_d, R, blockIdx.x * SH::EPB, SH::EPB,
                                             flux);
@@ -131,9 +132,11 @@ int run_rhs(const kbl_ctx* c, const double* w, const double* wf, double* R, cuda
     if (c->E == 0) return 0;
     const unsigned grid = (unsigned)((c->E + SH::EPB - 1) / SH::EPB);
     if (c->cfg.precision == KBL_FP32_MIXED)
-        k_rhs<DIM, N, float><<<grid, SH::NT, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, R, c->phys.flux);
+        kbl_launch(k_rhs<DIM, N, float>, grid, SH::NT, 0, s, c->pdl, w, wf, mesh_of(c), c->ops, c->phys.gamma, R,
+                   c->phys.flux);
     else
-        k_rhs<DIM, N, double><<<grid, SH::NT, 0, s>>>(w, wf, mesh_of(c), c->ops, c->phys.gamma, R, c->phys.flux);
+        kbl_launch(k_rhs<DIM, N, double>, grid, SH::NT, 0, s, c->pdl, w, wf, mesh_of(c), c->ops, c->phys.gamma, R,
+                   c->phys.flux);
     return 1;
 }
 

@@ -89,10 +89,12 @@ inline void kbl_phys_derive(Phys& p)
 // their outputs and overwrites buffers they read), then lets its own dependent grid be
 // launched, whose blocks take SM slots as this grid's blocks retire and wait there in turn.
 // Launched without the programmatic attribute, both are no-ops.
+__device__ __forceinline__ void kbl_grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void kbl_grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void kbl_grid_dep_sync()
 {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    kbl_grid_dep_wait();
+    kbl_grid_dep_trigger();
 }
 
 // Launch `kernel` on s; with pdl, as a programmatic dependent of the work before it on s.

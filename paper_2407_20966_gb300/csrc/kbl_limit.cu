@@ -54,7 +54,10 @@ k_stage_limit_step(int stage, const double* wn, const double* ws, const double* 
                    int advance, int E, FrOps ops, Phys ph, DevFlags* flags)
 {
     using SH = LimShape<DIM, N>;
-    kbl_grid_dep_sync();
+    // a programmatic dependent of the bounds launch: the stage combination and the screen's first
+    // phases read only what was complete before that launch began (wn, ws, R, dt), so they run
+    // while its last blocks finish; the body waits for it before its first read of the bounds
+    kbl_grid_dep_trigger();
     __shared__ kbl_dev::LimSmem<DIM, N, SH::EPB> sm;
     const double dt = scal[0];
     const int e0 = blockIdx.x * SH::EPB;

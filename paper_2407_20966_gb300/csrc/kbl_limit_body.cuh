@@ -190,6 +190,9 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         }
     }
     __syncthreads();
+    // the bounds are the first input that a programmatic predecessor (the bounds launch) writes:
+    // wait for that grid here (a no-op in an ordinary launch)
+    kbl_grid_dep_wait();
     for (int t = tid; t < EPB * NV; t += NT) {
         const int ell = t / NV, v = t % NV;
         const int ee = e0 + ell;
