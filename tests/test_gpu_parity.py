@@ -159,6 +159,37 @@ def test_rhs(orc, dim, p, n):
     assert err.max() < TOL_FP64, err.max()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rhs_non_finite_input_stays_local(orc, precision):
+    """A NaN in one element's energy reaches the residual of that element as a non-finite value
+    (the FP32 path truncates it to an infinity and widens the non-finite results back to FP64
+    with integer operations), and the residual of every element that shares no face with it is
+    bit for bit the one of the clean field: the FR residual reads only the element's own nodes and
+    the traces across its faces (Sec. 2.3)."""
+    ctx, ocfg = both(orc, 2, 3, (16, 16), precision=precision)
+    mesh, w = mesh_and_field(orc, 2, 3, (7, 6), seed=61, kind="smooth")
+    upload(ctx, orc, mesh)
+    e_bad = 17
+
+    def residual(field):
+        wd = to_dev(field)
+        wf = zeros_dev(field.shape[0], field.shape[1], 4 * 4)
+        ctx.traces(wd, wf)
+        R = zeros_dev(*field.shape)
+        ctx.rhs(wd, wf, R)
+        return R.cpu().numpy()
+
+    clean = residual(w)
+    w_bad = w.copy()
+    w_bad[3, e_bad, 5] = np.nan
+    got = residual(w_bad)
+    assert not np.isfinite(got[:, e_bad]).all()
+    touched = {e_bad} | {int(nb) for nb in np.asarray(mesh.nbr).reshape(-1, 4)[e_bad] if nb >= 0}
+    rest = [e for e in range(w.shape[1]) if e not in touched]
+    np.testing.assert_array_equal(got[:, rest], clean[:, rest])
+    assert np.isfinite(clean).all()
+
+
 @pytest.mark.parametrize("dim,p,n", [(1, 3, 37), (2, 3, (9, 7)), (2, 2, (4, 13))])
 def test_fp32_mixed_traces_rhs_dt(orc, dim, p, n):
     """FP32-mixed contexts run the residual and the time step in FP32 arithmetic (FP64 storage)."""
