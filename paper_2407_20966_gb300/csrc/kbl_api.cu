@@ -639,8 +639,8 @@ kbl_status kbl_step(kbl_ctx* c, double* w, double cfl)
         cudaStream_t cap = nullptr, side = nullptr;
         cudaEvent_t ev[7] = {};
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        // the residual's branch at the highest priority: its blocks are placed as soon as the
-        // bounds kernel's blocks retire, instead of after all of them
+        // the side branch (the time step, beside the first traces) at the highest priority, so
+        // that its blocks are placed before the traces kernel's later blocks
         int prio_lo = 0, prio_hi = 0;
         if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
         if (e == cudaSuccess && c->overlap_rhs)
