@@ -46,7 +46,7 @@ PEAK_SOURCE = ("measured envelope-pattern rate 155.5 FP32 lane-ops/clk/SM (bench
 # DRAM bytes (read + write) of one launch of the FP32 2D bounds kernel on the vortex workload,
 # from an ncu capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum).  Must be
 # reset to None whenever that kernel changes, until it is captured again.
-BOUNDS_F32_VORTEX_TRAFFIC = 17077248
+BOUNDS_F32_VORTEX_TRAFFIC = 17076992
 
 
 def parse():
