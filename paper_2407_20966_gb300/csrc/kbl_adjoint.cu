@@ -468,12 +468,7 @@ k_stage_vjp(int stage, double dt, const double* __restrict__ wn, const double* _
     if (live)
         for (int v = 0; v < NV; v++) {
             const size_t g = ((size_t)v * E + e) * NS + nd;
-            const double t = ws[g] + dt * R[g];
-            double val;
-            if (stage == 0) val = t;
-            else if (stage == 1) val = 0.75 * wn[g] + 0.25 * t;
-            else val = (1.0 / 3.0) * wn[g] + (2.0 / 3.0) * t;
-            sw[el][v][nd] = val;
+            sw[el][v][nd] = kbl_ssprk3(stage, wn, ws, R, g, dt);
         }
     __syncthreads();
     // 2. face values

@@ -127,6 +127,19 @@ __device__ __forceinline__ float f32_trunc(double x)
     return __uint_as_float((hi & 0x80000000u) | ((unsigned)e32 << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
+// One SSP-RK3 stage in Shu-Osher form (Sec. 5) at index g: t = ws + dt R, then t (stage 0),
+// 3/4 wn + 1/4 t (stage 1) or 1/3 wn + 2/3 t (stage 2).  The FMAs are written out so that every
+// kernel that forms a stage (the stage kernels, with the stage known at compile time or not, and
+// the adjoint's recomputation of the forward step) gets the same bits.
+__device__ __forceinline__ double kbl_ssprk3(int stage, const double* wn, const double* ws, const double* R,
+                                             size_t g, double dt)
+{
+    const double t = fma(dt, R[g], ws[g]);
+    if (stage == 0) return t;
+    if (stage == 1) return fma(0.75, wn[g], 0.25 * t);
+    return fma(1.0 / 3.0, wn[g], (2.0 / 3.0) * t);
+}
+
 // x > 0.0 decided on the bit pattern with integer operations (true for +inf, false for
 // zeros, negatives and NaN), which keeps the test off the FP64 pipe.
 __device__ __forceinline__ bool kbl_positive(double x)

@@ -47,9 +47,9 @@ k_stage_limit(int mode, int stage, const double* wn, const double* ws, const dou
 #else
 #define KBL_STAGE_BOUNDS(...) __launch_bounds__(__VA_ARGS__)
 #endif
-template <int DIM, int N>
+template <int DIM, int N, int STAGE>
 __global__ void KBL_STAGE_BOUNDS(LimShape<DIM, N>::NT)
-k_stage_limit_step(int stage, const double* wn, const double* ws, const double* __restrict__ R,
+k_stage_limit_step(const double* wn, const double* ws, const double* __restrict__ R,
                    const double* __restrict__ bnd, double* scal, double* wout, double* __restrict__ wf_next,
                    int advance, int E, FrOps ops, Phys ph, DevFlags* flags)
 {
@@ -61,8 +61,8 @@ k_stage_limit_step(int stage, const double* wn, const double* ws, const double* 
     __shared__ kbl_dev::LimSmem<DIM, N, SH::EPB> sm;
     const double dt = scal[0];
     const int e0 = blockIdx.x * SH::EPB;
-    kbl_dev::stage_limit_block<DIM, N, SH::EPB, true>(sm, SH::NT, 0, stage, wn, ws, R, bnd, dt, wout, nullptr, E,
-                                                      ops, ph, flags, e0, SH::EPB);
+    kbl_dev::stage_limit_block<DIM, N, SH::EPB, true, STAGE>(sm, SH::NT, 0, STAGE, wn, ws, R, bnd, dt, wout, nullptr,
+                                                             E, ops, ph, flags, e0, SH::EPB);
     if (wf_next) kbl_dev::traces_of_block<DIM, N, SH::EPB>(sm, SH::NT, E, e0, SH::EPB, wf_next);
     // the clock: t += dt, once (no block of this launch reads t)
     if (advance && blockIdx.x == 0 && threadIdx.x == 0) scal[1] += dt;
@@ -75,8 +75,16 @@ int run_stage_step(const kbl_ctx* c, int stage, const double* wn, const double* 
     using SH = LimShape<DIM, N>;
     if (c->E == 0) return 0;
     const unsigned grid = (unsigned)((c->E + SH::EPB - 1) / SH::EPB);
-    kbl_launch(k_stage_limit_step<DIM, N>, grid, SH::NT, 0, s, c->pdl, stage, wn, ws, R, bnd, c->d_scal, wout, wf_next,
-               advance, c->E, c->ops, c->phys, c->d_flags);
+    // one kernel per stage: the stage's combination is fixed at compile time
+    if (stage == 0)
+        kbl_launch(k_stage_limit_step<DIM, N, 0>, grid, SH::NT, 0, s, c->pdl, wn, ws, R, bnd, c->d_scal, wout, wf_next,
+                   advance, c->E, c->ops, c->phys, c->d_flags);
+    else if (stage == 1)
+        kbl_launch(k_stage_limit_step<DIM, N, 1>, grid, SH::NT, 0, s, c->pdl, wn, ws, R, bnd, c->d_scal, wout, wf_next,
+                   advance, c->E, c->ops, c->phys, c->d_flags);
+    else
+        kbl_launch(k_stage_limit_step<DIM, N, 2>, grid, SH::NT, 0, s, c->pdl, wn, ws, R, bnd, c->d_scal, wout, wf_next,
+                   advance, c->E, c->ops, c->phys, c->d_flags);
     return 1;
 }
 

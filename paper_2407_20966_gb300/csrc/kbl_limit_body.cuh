@@ -30,7 +30,6 @@ struct LimSmem {
     double salpha[EPB];
     int slow[EPB];               // some point of V failed the division-free pressure screen
     double saP[EPB];
-    int sPtaken[EPB];
     double slm[N], slp[N], sW[NS];
     // FP32 screen (exact for alpha = 1 and the pressure test, see stage_limit_block)
     double sc[EPB][NV];                    // reference value c of each component
@@ -42,13 +41,18 @@ struct LimSmem {
     float sfdev[EPB][NV][NFP];             // face deviations from m' (FP32 interpolation)
     float sbl[EPB][NV], sbh[EPB][NV];      // a box that holds every value of V
     int sfv[EPB][NV], sfast[EPB];
+    // the elements the screen did not pass, and those whose pressure re-limit is taken, listed
+    // (in any order) so that the exact path's loops run over them alone: FP64 instructions that a
+    // warp issues with every lane predicated off still hold the slow FP64 pipe
+    int sslow[EPB], staken[EPB], snslow, sntaken;
 
 };
 
 // SSP-RK3 stage (mode 0) or limiter only (mode 1, ws = w in place) for elements
 // e0 .. e0+min(EPB, nmax)-1 of one mesh, by a block of NT >= EPB*Ns threads.  Starts with a
-// barrier so that a block can call it repeatedly.
-template <int DIM, int N, int EPB, bool KEEP = false>
+// barrier so that a block can call it repeatedly.  STAGE >= 0 fixes the stage (and mode 0) at
+// compile time, so that the other stages' combinations are not in the code at all.
+template <int DIM, int N, int EPB, bool KEEP = false, int STAGE = -1>
 __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int NT, int mode, int stage,
                                                   const double* wn, const double* ws,
                                                   const double* __restrict__ R,
@@ -65,7 +69,6 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     auto& salpha = sm.salpha;
     auto& slow = sm.slow;
     auto& saP = sm.saP;
-    auto& sPtaken = sm.sPtaken;
     auto& slm = sm.slm;
     auto& slp = sm.slp;
     auto& sW = sm.sW;
@@ -84,7 +87,15 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     auto& sdev = sm.sdev;
     auto& sfdev = sm.sfdev;
     const int tid = threadIdx.x;
+    if (STAGE >= 0) {
+        mode = 0;
+        stage = STAGE;
+    }
     __syncthreads();   // the block may call this for consecutive element blocks
+    if (tid == 0) {
+        sm.snslow = 0;
+        sm.sntaken = 0;
+    }
     if (tid < N) {
         slm[tid] = ops.lm[tid];
         slp[tid] = ops.lp[tid];
@@ -104,10 +115,7 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             const size_t g = ((size_t)v * E + e) * NS + nd;
             double val;
             if (mode == 0) {
-                const double t = ws[g] + dt * R[g];
-                if (stage == 0) val = t;
-                else if (stage == 1) val = 0.75 * wn[g] + 0.25 * t;
-                else val = (1.0 / 3.0) * wn[g] + (2.0 / 3.0) * t;
+                val = kbl_ssprk3(stage, wn, ws, R, g, dt);
             } else {
                 val = ws[g];
             }
@@ -253,24 +261,24 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
             const float eabs = fmaxf(fabsf(elo), fabsf(sbh[ell][DIM + 1]));
             const float Y = fmaf(elo, rlo, -0.5f * mm) - 1e-6f * fmaf(eabs, rlo, mm);
             if (!(rlo > 0.0f) || !(ph.gm1f_down * Y >= 2.0f * ph.pfloorf_up * rlo + 1e-36f)) fast = 0;
+            if (!fast) sm.sslow[atomicAdd(&sm.snslow, 1)] = ell;
         }
         sfast[ell] = fast;
         slow[ell] = 0;
     }
     __syncthreads();
+    const int nslow = sm.snslow;
     // 2. the exact path, for the elements the screen did not pass: the FP64 mean (the weights
     //    in order, then 1 / sum W) and the face values (interpolation along the line normal to
     //    each face)
-    for (int t = tid; t < EPB * NV; t += NT) {
-        const int ell = t / NV, v = t % NV;
-        if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
+    for (int t = tid; t < nslow * NV; t += NT) {
+        const int ell = sm.sslow[t / NV], v = t % NV;
         double sum = 0.0;
         for (int n2 = 0; n2 < NS; n2++) sum += sW[n2] * sw[ell][v][n2];
         smean[ell][v] = sum * winv;
     }
-    for (int t = tid; t < EPB * NFP; t += NT) {
-        const int ell = t / NFP, fp = t % NFP;
-        if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
+    for (int t = tid; t < nslow * NFP; t += NT) {
+        const int ell = sm.sslow[t / NFP], fp = t % NFP;
         const int f = fp / NFPF, k = fp % NFPF;
         const double* l = (f & 1) ? slp : slm;
         const bool along_x = (DIM == 1) || f < 2;
@@ -286,10 +294,12 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     // 3. mean, extrema over V and alpha_i, one thread per (element, component)
     for (int t = tid; t < EPB * NV; t += NT) {
         const int ell = t / NV, v = t % NV;
+        if (e0 + ell < E && ell < nmax && sfast[ell]) salpha_v[ell][v] = 1.0;
+    }
+    for (int t = tid; t < nslow * NV; t += NT) {
+        const int ell = sm.sslow[t / NV], v = t % NV;
         const int ee = e0 + ell;
-        if (ee < E && ell < nmax && sfast[ell]) {
-            salpha_v[ell][v] = 1.0;
-        } else if (ee < E && ell < nmax) {
+        {
             const double mean = smean[ell][v];
             long long kmx = dkey(sw[ell][v][0]), kmn = kmx;
             for (int n2 = 1; n2 < NS; n2++) {
@@ -344,24 +354,24 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
     //    flags gets the exact P_min of Eq. 47 below.  Elements that passed the exact screen
     //    (alpha = 1 and the box test) keep w~ = w and need no pressure re-limit.
     const double gm1 = ph.gamma - 1.0;
-    if (live && !sfast[el]) {
+    for (int t = tid; t < nslow * NS; t += NT) {
+        const int ell = sm.sslow[t / NS], n2 = t % NS;
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            const double a = ph.uncoupled ? salpha_v[el][v] : salpha[el];   // Eq. 38 (or per component)
-            const double m = smean[el][v];
-            q[v] = m + a * (sw[el][v][nd] - m);
-            sw[el][v][nd] = q[v];
+            const double a = ph.uncoupled ? salpha_v[ell][v] : salpha[ell];   // Eq. 38 (or per component)
+            const double m = smean[ell][v];
+            q[v] = m + a * (sw[ell][v][n2] - m);
+            sw[ell][v][n2] = q[v];
         }
         double mm = q[1] * q[1];
         if (DIM == 2) mm += q[2] * q[2];
         const double X = fma(q[DIM + 1], q[0], -0.5 * mm);
         const double tol = 4e-15 * (fabs(q[DIM + 1] * q[0]) + 0.5 * mm);
-        if (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) slow[el] = 1;
+        if (!(q[0] > 0.0) || gm1 * (X - tol) < ph.p_floor * q[0]) slow[ell] = 1;
     }
-    for (int t = tid; t < EPB * NFP; t += NT) {
-        const int ell = t / NFP, fp = t % NFP;
-        if (e0 + ell >= E || ell >= nmax || sfast[ell]) continue;
+    for (int t = tid; t < nslow * NFP; t += NT) {
+        const int ell = sm.sslow[t / NFP], fp = t % NFP;
         double q[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
@@ -396,10 +406,10 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
                 const double Pbar = kbl_pressure<DIM>(q, gm1);
                 aP = (Pbar > ph.p_floor) ? fabs((ph.p_floor - Pbar) / (pmin - Pbar)) : 0.0;
                 taken = 1;
+                sm.staken[atomicAdd(&sm.sntaken, 1)] = tid;
                 atomicAdd(&flags->prelimit, 1ull);
             }
         }
-        sPtaken[tid] = taken;
         saP[tid] = aP;
         const int ee = e0 + tid;
         // alpha in [0, 1]: alpha < 1 on the bit patterns
@@ -413,19 +423,24 @@ __device__ __forceinline__ void stage_limit_block(LimSmem<DIM, N, EPB>& sm, int 
         }
     }
     __syncthreads();
-    // 5. write (with KEEP the written state also stays in sw, for a caller that continues with it)
-    if (live) {
-        const double aP = saP[el];
+    // 5. the pressure re-limit (Eq. 49) in sw for the elements that take it, then write sw (with
+    //    KEEP the written state stays in sw, for a caller that continues with it)
+    const int ntaken = sm.sntaken;
+    if (ntaken > 0) {   // block-uniform
+        for (int t = tid; t < ntaken * NS; t += NT) {
+            const int ell = sm.staken[t / NS], n2 = t % NS;
+            const double aP = saP[ell];
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-            double val = sw[el][v][nd];
-            if (sPtaken[el]) {
-                const double m = smean[el][v];
-                val = m + aP * (val - m);
+            for (int v = 0; v < NV; v++) {
+                const double m = smean[ell][v];
+                sw[ell][v][n2] = m + aP * (sw[ell][v][n2] - m);
             }
-            wout[((size_t)v * E + e) * NS + nd] = val;
-            if (KEEP) sw[el][v][nd] = val;
         }
+        __syncthreads();
+    }
+    if (live) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) wout[((size_t)v * E + e) * NS + nd] = sw[el][v][nd];
     }
 }
 
