@@ -299,16 +299,21 @@ __device__ __forceinline__ const double* tri_exterior(const TriMeshDev& m, const
     return m.bc + (size_t)(-nb - 1) * 4;
 }
 
+// NS: the solution points per element, fixed at compile time so that the sum unrolls whole (a
+// run-time count leaves a remainder the compiler predicates, and FP64 instructions issued with
+// every lane off still take the slow FP64 pipe)
+template <int NS>
 __global__ void k_tri_traces(const double* __restrict__ w, double* __restrict__ wf, int E, TriOps o)
 {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (size_t)E * o.nfp) return;
     const int e = (int)(t / o.nfp), q = (int)(t % o.nfp);
-    const double* we = w + (size_t)e * o.ns * 4;
+    const double* we = w + (size_t)e * NS * 4;
 #pragma unroll
     for (int v = 0; v < 4; v++) {
         double s = 0.0;
-        for (int j = 0; j < o.ns; j++) s += o.phif[q][j] * we[j * 4 + v];
+#pragma unroll
+        for (int j = 0; j < NS; j++) s += o.phif[q][j] * we[j * 4 + v];
         wf[((size_t)e * o.nfp + q) * 4 + v] = s;
     }
 }
@@ -851,7 +856,8 @@ kbl_status kbl_tri_traces(kbl_tri* t, const double* w, double* wf)
 {
     if (!t || (t->E > 0 && (!w || !wf))) return tfail(t, KBL_EINVAL, "null array");
     const size_t n = (size_t)t->E * t->ops.nfp;
-    if (n) k_tri_traces<<<blocks_for(n, 256), 256, 0, t->stream>>>(w, wf, t->E, t->ops);
+    if (n && t->ops.ns == 3) k_tri_traces<3><<<blocks_for(n, 256), 256, 0, t->stream>>>(w, wf, t->E, t->ops);
+    else if (n) k_tri_traces<6><<<blocks_for(n, 256), 256, 0, t->stream>>>(w, wf, t->E, t->ops);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KBL_OK : tfail(t, KBL_ECUDA, cudaGetErrorString(e));
 }
